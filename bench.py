@@ -1,0 +1,274 @@
+"""Benchmark: transitive-closure least models at N = 8192 on one GB300 (and N GPUs as replicas).
+
+Workload (a step): the least models of r2 <- r1; r2 <- r1, r2 (Sec. 3) for three seeded
+Erdos-Renyi digraphs with N = 8192 and p = 1e-4, 1e-3, 1e-2 (seeds 2, 3, 4; i != j), the
+paper's ER workload shape (Sec. 6.1).  Metric: TFLOP/s-equivalent = (8/3) N^3 per model
+(the cost of the dense direct solve of Proposition 1) / wall time, whole job.
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+`value`: inputs resident in HBM (three 64 MiB matrices, 192 MiB > the 129 MB L2, cycled
+each step), one C-ABI call per model on the FP8 tensor-core path.  `e2e`: the same through
+host buffers (H2D of E and D2H of the model bits inside the timed region).  The plain FP64
+path (Proposition 1 in FP64) is timed beside it for the "vs plain FP64" comparison.
+`--impl reference` times the CPU oracle (semi-naive evaluation) on the host cores.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+N = 8192
+PS = (1e-4, 1e-3, 1e-2)
+SEEDS = (2, 3, 4)
+METRIC = "TC least-model TFLOP/s-equiv (N=8192) vs plain FP64 path; served p50/p99 latency"
+UNIT = "TFLOP/s-equiv"
+
+
+def flops_equiv(n: int) -> float:
+    return (8.0 / 3.0) * float(n) ** 3
+
+
+def peaks() -> dict:
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return {"bf16": float(d["bf16_tflops"]), "bf16_sustained": float(d["bf16_tflops_sustained"]),
+                "hbm": float(d["hbm_gbs"]), "source": "measured"}
+    except Exception:
+        return {"bf16": 1900.0, "bf16_sustained": 1700.0, "hbm": 6800.0, "source": "fallback"}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def graphs(rank: int):
+    from paper_1608_00139_gb300 import inputs
+    return [inputs.er_digraph(N, p, s + 1000 * rank) for p, s in zip(PS, SEEDS)]
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.tmp = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-i", str(self.device)], stdout=self.tmp, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except Exception:
+                self.proc.kill()
+
+    def summary(self) -> dict:
+        self.tmp.flush()
+        rows = []
+        with open(self.tmp.name) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) >= 9 and parts[1].isdigit():
+                    rows.append(parts)
+        os.unlink(self.tmp.name)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"], "samples": 0}
+        sm = [int(r[1]) for r in rows]
+        smax = max(int(r[2]) for r in rows)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        loaded = [s for s in sm if s > 0.5 * smax] or sm
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": smax, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def cpu_baseline(gs, budget_s: float = 30.0) -> dict:
+    import oracle
+    threads = oracle.set_threads(os.cpu_count() or 1)
+    t0 = time.perf_counter()
+    done = 0
+    for e in gs:
+        oracle.tc_model(e)
+        done += 1
+        if time.perf_counter() - t0 > budget_s:
+            break
+    dt = time.perf_counter() - t0
+    return {"value": done * flops_equiv(N) / dt / 1e12, "unit": UNIT, "cores": threads,
+            "kind": "oracle",
+            "sample": f"{done} of the 3 N=8192 graphs (one full step), semi-naive evaluation, "
+                      f"{dt:.2f} s"}
+
+
+def run_reference(args, rank: int, world: int) -> None:
+    if rank != 0:
+        return
+    import oracle
+    gs = graphs(0)
+    threads = oracle.set_threads(os.cpu_count() or 1)
+    for _ in range(args.warmup):
+        for e in gs:
+            oracle.tc_model(e)
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        for e in gs:
+            oracle.tc_model(e)
+    dt = (time.perf_counter() - t0) / max(args.steps, 1)
+    value = len(gs) * flops_equiv(N) / dt / 1e12
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "impl": "reference", "n_gpus": 0,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u8",
+            "data": "synthetic (seeded Erdos-Renyi, i != j)",
+            "config": {"workload": "TC ER N=8192 x p in {1e-4,1e-3,1e-2}, seeds 2/3/4"},
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                             "sample": "whole step: the 3 N=8192 graphs"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main() -> None:
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    args = ap.parse_args()
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+        return
+
+    import torch
+    import torch.distributed as tdist
+
+    from paper_1608_00139_gb300 import dl
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        tdist.init_process_group("nccl")
+    stream = torch.cuda.current_stream()
+    ctx = dl.Context(local, stream=stream)
+    gs = graphs(rank)
+    dev = [torch.from_numpy(e).cuda() for e in gs]
+    torch.cuda.synchronize()
+
+    def step(inputs):
+        out = []
+        for x in inputs:
+            out.append(ctx.tc_closure(x, path="bool_fp8"))
+        return out
+
+    for _ in range(max(args.warmup, 3)):
+        step(dev)
+    launches = 0
+    gemm_ms = 0.0
+    gemm_flops = 0.0
+    gemm_n = 0
+    squarings = []
+    with ClockSampler(local) as clk:
+        if world > 1:
+            tdist.barrier()
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record(stream)
+        for _ in range(args.steps):
+            for _, st in step(dev):
+                launches += st["gpu_launches"]
+                gemm_ms += st["ms_gemm"]
+                gemm_flops += st["gemm_flops"]
+                gemm_n += st["gemm_launches"]
+                squarings.append(st["iters"])
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        if world > 1:
+            tdist.barrier()
+        ms_total = ev0.elapsed_time(ev1)
+        # end to end through host buffers (H2D of E, D2H of bits inside the timed region)
+        e2e_steps = max(1, min(args.steps, 20))
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(e2e_steps):
+            for e in gs:
+                ctx.tc_closure(e, path="bool_fp8")
+        torch.cuda.synchronize()
+        e2e_s = (time.perf_counter() - t0) / e2e_steps
+    clocks = clk.summary()
+    ms_step = ms_total / args.steps
+    if world > 1:
+        t = torch.tensor([ms_step, e2e_s], device="cuda", dtype=torch.float64)
+        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+        ms_step, e2e_s = float(t[0]), float(t[1])
+    units = world * len(gs)
+    value = units * flops_equiv(N) / (ms_step * 1e-3) / 1e12
+    e2e_value = units * flops_equiv(N) / e2e_s / 1e12
+
+    fp64 = None
+    if not args.no_fp64 and rank == 0:
+        _, st64 = ctx.tc_closure(dev[1], path="fp64")  # warm
+        _, st64 = ctx.tc_closure(dev[1], path="fp64")
+        fp64 = {"ms": st64["ms_total"], "tflops_equiv": st64["tflops_equiv"],
+                "graph": "p=1e-3 seed 3", "rechecked_rows": st64["rows_rechecked"]}
+
+    pk = peaks()
+    fp8_peak = 2.0 * pk["bf16"]  # FP8 dense = 2 x BF16 dense (nominal ratio)
+    achieved = (gemm_flops / (gemm_ms * 1e-3) / 1e12) if gemm_ms > 0 else 0.0
+    roofline = {"bound": "tensor", "kernel": "umma_gemm_kernel<FP8,256,MN-major B,bool epilogue>",
+                "achieved": achieved, "peak": fp8_peak, "unit": "TFLOP/s",
+                "frac": achieved / fp8_peak, "traffic": None,
+                "peak_source": f"2 x bf16_tflops of {pk['source']} MEASURED_PEAKS (burst)",
+                "gemm_launches": gemm_n, "avg_launch_ms": gemm_ms / max(gemm_n, 1)}
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "e4m3 (0/1, FP32 accumulate)",
+            "data": "synthetic (seeded Erdos-Renyi, i != j)",
+            "config": {"workload": "TC ER N=8192 x p in {1e-4,1e-3,1e-2}, seeds 2/3/4 (+1000*rank)",
+                       "path": "bool_fp8", "l2": "inputs 3 x 64 MiB > L2, cycled each step",
+                       "squarings_per_model": sorted(set(squarings))},
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": len(gs) * N * N,
+                    "d2h_bytes_per_step": len(gs) * N * ((N + 63) // 64) * 8},
+            "gpu_launches": launches, "roofline": roofline, "clocks": clocks}
+    if fp64:
+        line["fp64_path"] = fp64
+        line["speedup_vs_fp64"] = fp64["ms"] / (ms_step / len(gs))
+    if rank == 0 and world == 1 and not args.no_cpu:
+        line["cpu_baseline"] = cpu_baseline(gs)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        tdist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

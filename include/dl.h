@@ -1,0 +1,197 @@
+/*
+ * dl.h -- C ABI of libdl: least Herbrand models of linear Datalog programs over N constants
+ * and binary predicates, computed on one GB300 GPU (sm_103a) the way Sato, "A Linear
+ * Algebraic Approach to Datalog Evaluation" (TPLP) states the problem:
+ *
+ *   - constants are one-hot vectors and a binary relation r is its N x N adjacency matrix
+ *     R with R[i][j] = 1 iff r(e_i, e_j) (Sec. 2);
+ *   - the iff-completion of a program gives a matrix equation with the clamp
+ *     min1(x) = min(x, 1) (Sec. 3), e.g. R2 = min1(R1 + R1 R2) for transitive closure;
+ *   - its linearisation R~ = eps (R1 + R1 R~) (Sec. 4) has the least solution
+ *     R~ = (I - eps R1)^-1 eps R1 when 0 < eps <= 1/(1 + ||R1||_inf) (Lemma 1,
+ *     Proposition 1), and thresholding R~ at 0 gives the least model (Theorem 1).
+ *
+ * Conventions shared by every call:
+ *   - Every call returns a dl_status; dl_last_error() gives a message for the last failed
+ *     call on the calling thread.  No C++ exception crosses this boundary.
+ *   - Matrices are dense, row-major, n*n bytes, each byte 0 or 1 (any other byte value is
+ *     rejected with DL_EINVAL).  Bit matrices ("bits") hold ceil(n/64) uint64 words per row;
+ *     entry (i, j) is bit (j mod 64) of word i*ceil(n/64) + j/64, least significant first.
+ *   - dl_mem says where input and output pointers live: DL_MEM_HOST (ordinary host memory;
+ *     the call copies in and out) or DL_MEM_DEVICE (device memory of the context's GPU,
+ *     e.g. a torch CUDA tensor's data pointer).  Inputs and outputs of one call share it.
+ *   - The caller owns every buffer.  Synchronous calls have read their inputs and written
+ *     their outputs when they return (device outputs: complete on the context's stream,
+ *     which the call synchronises before returning).
+ *   - n == 0 returns DL_OK and writes nothing.  n < 0 or a NULL required pointer returns
+ *     DL_EINVAL.
+ *   - Calls on one context are serialised by the context; contexts are independent.
+ */
+#ifndef DL_H
+#define DL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define DL_API __attribute__((visibility("default")))
+#else
+#define DL_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dl_ctx dl_ctx;
+
+typedef enum {
+    DL_OK = 0,
+    DL_EINVAL = 1,     /* bad argument (size, pointer, eps, threshold, non-0/1 input) */
+    DL_ENOMEM = 2,     /* device or host allocation failed, or a request can never fit */
+    DL_EDEVICE = 3,    /* CUDA error, or no usable sm_103 device */
+    DL_ETIMEOUT = 4,   /* a bounded device-side wait expired, or dl_poll timed out */
+    DL_EBUSY = 5,      /* dl_poll: the request is still running */
+    DL_ENOTCONV = 6,   /* an iteration did not converge within its limit */
+    DL_ECANCELED = 7,  /* the request was cancelled */
+    DL_ENOTIMPL = 8    /* the requested path does not exist for this call */
+} dl_status;
+
+/* Which numerical route computes the model (all give the same, exact model). */
+typedef enum {
+    DL_PATH_AUTO = 0,      /* the library chooses (currently DL_PATH_BOOL_FP8) */
+    DL_PATH_FP64 = 1,      /* plain FP64 inverse of I - eps E (Prop. 1), threshold > 0 */
+    DL_PATH_MIXED = 2,     /* TF32 tensor-core LU + FP64 iterative refinement + guard */
+    DL_PATH_BOOL_FP8 = 3   /* boolean repeated squaring on FP8 e4m3 tensor cores */
+} dl_path;
+
+typedef enum { DL_MEM_HOST = 0, DL_MEM_DEVICE = 1 } dl_mem;
+
+typedef struct {
+    void *stream;              /* cudaStream_t to run on; NULL = the context's own stream */
+    size_t hbm_budget_bytes;   /* serving admission budget; 0 = 90% of free device memory */
+    int32_t max_slots;         /* serving: requests in flight at once; 0 = 4 */
+    double refine_tol;         /* mixed path: stop when max|R| <= tol * max|eps E|; 0 = 1e-12 */
+    int32_t refine_max_iters;  /* mixed path: refinement step limit; 0 = 30 */
+    double guard_tau;          /* entries with |R~| <= tau are flagged for recheck; 0 = 1e-30 */
+    double wait_timeout_s;     /* limit of every device-side wait; 0 = 2 s */
+} dl_config;
+
+typedef struct {
+    int32_t path_used;       /* dl_path that ran */
+    double eps_used;         /* epsilon of the linearised equation (reported for every path) */
+    int32_t iters;           /* squarings (FP8), doubling steps (SG), or refinement steps */
+    double final_resid;      /* mixed/FP64: max|eps E - (I - eps E) X| / max|eps E| */
+    int64_t guard_flagged;   /* entries in the guard band (|X| <= tau or X < 0) */
+    int64_t rows_rechecked;  /* rows corrected by the exact boolean recheck */
+    int32_t recheck_sweeps;  /* sweeps of the certificate/recheck kernel */
+    int64_t model_ones;      /* number of 1 bits in the model */
+    double ms_total;         /* device time of the call (CUDA events), ms */
+    double ms_factor;        /* LU factorisation (FP64/mixed) or ingest (FP8) */
+    double ms_solve;         /* triangular solves (FP64/mixed) or squarings (FP8/SG) */
+    double ms_refine;        /* refinement (mixed) */
+    double ms_epilogue;      /* threshold, bit packing, certificate and recheck */
+    double tflops_equiv;     /* (8/3) n^3 / ms_total, TC only */
+    int32_t gpu_launches;    /* kernels this call launched */
+    int32_t gemm_launches;   /* tensor-core GEMM launches among them */
+    double ms_gemm;          /* summed device time of those GEMM launches (CUDA events on the
+                                launching stream), ms */
+    double gemm_flops;       /* 2*M*N*K summed over those GEMM launches (padded sizes) */
+} dl_stats;
+
+/* Create a context on CUDA device `device` (cfg may be NULL for defaults).  Fails with
+ * DL_EDEVICE unless the device is compute capability 10.3 (GB300). */
+DL_API dl_status dl_create(dl_ctx **out, int device, const dl_config *cfg);
+
+/* Wait for outstanding work, free every device buffer of the context, free the context. */
+DL_API dl_status dl_destroy(dl_ctx *ctx);
+
+/* Message for the last failed call on this thread ("" if none).  Valid until the next call
+ * on this thread. */
+DL_API const char *dl_last_error(void);
+
+/* Run subsequent synchronous calls on `stream` (a cudaStream_t of the context's device;
+ * NULL = the context's own stream). */
+DL_API dl_status dl_set_stream(dl_ctx *ctx, void *stream);
+
+/*
+ * Transitive closure, the program of Sec. 3 (eq. prog:trcl):
+ *     r2(x,z) <- r1(x,z).     r2(x,z) <- r1(x,y), r2(y,z).
+ * E: the n x n 0/1 matrix of r1.  Output: the least model of r2, i.e. the least solution
+ * of R2 = min1(E + E R2) (eq. matrixeq:trcl), as bits (n * ceil(n/64) words).
+ *
+ * eps <= 0 selects eps = 1/(1 + ||E||_inf) (Sec. 4 after Prop. 1; Sec. 6.1); otherwise
+ * 0 < eps <= 1/(1 + ||E||_inf) is required (Lemma 1), else DL_EINVAL.  The model does not
+ * depend on eps (Theorem 1).
+ * thr must be 0 (the threshold "> 0" of Theorem 1); other values return DL_EINVAL.
+ * out_rtilde (optional, n*n doubles, NULL allowed): the real least solution
+ * R~ = (I - eps E)^-1 eps E (Prop. 1); only the FP64 and mixed paths produce it (with
+ * DL_PATH_BOOL_FP8 or AUTO a non-NULL out_rtilde returns DL_EINVAL).
+ * stats (optional): filled on DL_OK.
+ */
+DL_API dl_status dl_tc_closure(dl_ctx *ctx, int32_t n, const uint8_t *E, dl_mem mem, double eps,
+                        double thr, dl_path path, uint64_t *out_bits, double *out_rtilde,
+                        dl_stats *stats);
+
+/*
+ * Same generation, the right-hand program of Sec. 6.2 (Fig. "Tested programs"):
+ *     sg(x,w) <- b(x,w).     sg(x,w) <- p(x,y), sg(y,z), p(w,z).
+ * i.e. the least solution of S = min1(B + P S P^T) (two-sided class, Sec. 5.3;
+ * Sec. 6.2 with B = I).  P: n x n 0/1; B: n x n 0/1, or NULL for the identity
+ * (the paper's diag facts).  eps <= 0 selects 1/(1 + ||P||_inf^2) (Sec. 6.2; reported
+ * only, the model does not depend on it); thr must be 0.  Only DL_PATH_BOOL_FP8 and
+ * DL_PATH_AUTO exist (others: DL_ENOTIMPL).  Output: bits of S.
+ */
+DL_API dl_status dl_sg_least_model(dl_ctx *ctx, int32_t n, const uint8_t *P, const uint8_t *B,
+                            dl_mem mem, double eps, double thr, dl_path path,
+                            uint64_t *out_bits, dl_stats *stats);
+
+/*
+ * Relational composition, the denotation of an existential join (Sec. 2,
+ * eq. denote:quant):  [[exists y r1(x,y) and r2(y,z)]] = min1(R1 R2).
+ * R1, R2: n x n 0/1.  Output: bits of min1(R1 R2).  Runs on the FP8 tensor-core path.
+ */
+DL_API dl_status dl_compose(dl_ctx *ctx, int32_t n, const uint8_t *R1, const uint8_t *R2,
+                     dl_mem mem, uint64_t *out_bits, dl_stats *stats);
+
+/*
+ * Batch of independent transitive-closure problems of uneven size (each as
+ * dl_tc_closure with eps <= 0, thr = 0, DL_PATH_BOOL_FP8).  ns[k], Es[k], out_bits[k]
+ * describe problem k; all live in `mem`.  Every squaring round of all unfinished
+ * problems runs as one persistent grouped launch, replayed from a captured CUDA graph.
+ * stats (optional, one for the whole batch): iters = squaring rounds.
+ */
+DL_API dl_status dl_tc_batch(dl_ctx *ctx, int32_t count, const int32_t *ns, const uint8_t *const *Es,
+                      dl_mem mem, uint64_t *const *out_bits, dl_stats *stats);
+
+/* ---- asynchronous serving (continuous batching) ------------------------------------ */
+
+typedef struct {
+    int32_t kind;            /* 0 = transitive closure, 1 = same generation */
+    int32_t n;
+    const uint8_t *base;     /* E (closure) or P (same generation), n*n bytes */
+    const uint8_t *B;        /* same generation only: base relation or NULL (identity) */
+    dl_mem mem;              /* where base, B and out_bits live */
+    dl_path path;            /* DL_PATH_AUTO or DL_PATH_BOOL_FP8 */
+    uint64_t *out_bits;      /* n * ceil(n/64) words */
+} dl_request;
+
+/* Queue a request.  The caller keeps base, B and out_bits alive until dl_poll returns
+ * DL_OK or an error for it, or dl_cancel succeeds.  The request is admitted to the GPU
+ * when a slot and its HBM footprint (n^2 bytes per dense operand plus workspace) are free;
+ * DL_ENOMEM if it can never fit the budget. *ticket receives its id. */
+DL_API dl_status dl_submit(dl_ctx *ctx, const dl_request *req, uint64_t *ticket);
+
+/* Wait up to timeout_us microseconds (0 = just test, <0 = forever) for a request.
+ * DL_EBUSY while it is queued or running; on completion returns its final status once
+ * (later polls of the same ticket return DL_EINVAL).  stats may be NULL. */
+DL_API dl_status dl_poll(dl_ctx *ctx, uint64_t ticket, int64_t timeout_us, dl_stats *stats);
+
+/* Cancel a request that has not been admitted yet: DL_OK if cancelled (its ticket then
+ * polls DL_ECANCELED), DL_EBUSY if it is already running or done. */
+DL_API dl_status dl_cancel(dl_ctx *ctx, uint64_t ticket);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DL_H */

@@ -1,0 +1,270 @@
+// dl_capi.cu -- the extern "C" entry points of libdl (declared in include/dl.h): argument
+// checks, context management, and dispatch to the drivers in dl_solve.cu / dl_serve.cu.
+#include <cuda_runtime.h>
+
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "dl_ctx.h"
+
+namespace dl {
+
+namespace {
+thread_local std::string g_last_error;
+}
+
+void set_error(const char *fmt, ...) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+}
+
+const char *last_error() { return g_last_error.c_str(); }
+void clear_error() { g_last_error.clear(); }
+
+int num_sms() {
+    int dev = 0, sms = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    return sms;
+}
+
+}  // namespace dl
+
+using namespace dl;
+
+#define GUARD_CTX(ctx)                                \
+    do {                                              \
+        if (!(ctx)) {                                 \
+            set_error("ctx is NULL");                 \
+            return DL_EINVAL;                         \
+        }                                             \
+    } while (0)
+
+namespace {
+
+dl_status set_device(dl_ctx *ctx) {
+    cudaError_t e = cudaSetDevice(ctx->device);
+    if (e != cudaSuccess) {
+        set_error("cudaSetDevice(%d): %s", ctx->device, cudaGetErrorString(e));
+        return DL_EDEVICE;
+    }
+    return DL_OK;
+}
+
+bool valid_mem(dl_mem m) { return m == DL_MEM_HOST || m == DL_MEM_DEVICE; }
+
+template <class F>
+dl_status run_sync(dl_ctx *ctx, dl_stats *stats, F &&f) {
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    dl_status rc = set_device(ctx);
+    if (rc) return rc;
+    cudaError_t e = ctx->ws.init();
+    if (e != cudaSuccess) {
+        set_error("workspace init: %s", cudaGetErrorString(e));
+        return DL_ENOMEM;
+    }
+    dl_stats local{};
+    rc = f(ctx->ws, ctx->stream, stats ? stats : &local);
+    if (rc != DL_OK) {
+        // leave the stream idle and usable after a failure
+        cudaStreamSynchronize(ctx->stream);
+        cudaGetLastError();
+    }
+    return rc;
+}
+
+}  // namespace
+
+extern "C" {
+
+dl_status dl_create(dl_ctx **out, int device, const dl_config *cfg) {
+    clear_error();
+    if (!out) {
+        set_error("out is NULL");
+        return DL_EINVAL;
+    }
+    *out = nullptr;
+    int count = 0;
+    if (cudaGetDeviceCount(&count) != cudaSuccess || count == 0) {
+        cudaGetLastError();
+        set_error("no CUDA device");
+        return DL_EDEVICE;
+    }
+    if (device < 0 || device >= count) {
+        set_error("device %d out of range [0, %d)", device, count);
+        return DL_EINVAL;
+    }
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, device) != cudaSuccess) {
+        set_error("cudaGetDeviceProperties failed");
+        return DL_EDEVICE;
+    }
+    if (prop.major != 10 || prop.minor != 3) {
+        set_error("device %d is sm_%d%d; this library is built for sm_103a (GB300)", device, prop.major,
+                  prop.minor);
+        return DL_EDEVICE;
+    }
+    auto *ctx = new (std::nothrow) dl_ctx();
+    if (!ctx) {
+        set_error("out of host memory");
+        return DL_ENOMEM;
+    }
+    ctx->device = device;
+    if (cfg) ctx->cfg = *cfg;
+    if (ctx->cfg.wait_timeout_s > 0) ctx->budget_ns = static_cast<uint64_t>(ctx->cfg.wait_timeout_s * 1e9);
+    if (set_device(ctx) != DL_OK) {
+        delete ctx;
+        return DL_EDEVICE;
+    }
+    ctx->sms = prop.multiProcessorCount;
+    if (cudaStreamCreateWithFlags(&ctx->own_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        set_error("cudaStreamCreate failed");
+        delete ctx;
+        return DL_EDEVICE;
+    }
+    ctx->stream = ctx->cfg.stream ? static_cast<cudaStream_t>(ctx->cfg.stream) : ctx->own_stream;
+    *out = ctx;
+    return DL_OK;
+}
+
+dl_status dl_destroy(dl_ctx *ctx) {
+    clear_error();
+    if (!ctx) return DL_OK;
+    dl_serve_shutdown(ctx);
+    {
+        std::lock_guard<std::mutex> lk(ctx->mu);
+        cudaSetDevice(ctx->device);
+        cudaStreamSynchronize(ctx->stream);
+        ctx->ws.release();
+        if (ctx->own_stream) cudaStreamDestroy(ctx->own_stream);
+    }
+    delete ctx;
+    return DL_OK;
+}
+
+const char *dl_last_error(void) { return last_error(); }
+
+dl_status dl_set_stream(dl_ctx *ctx, void *stream) {
+    clear_error();
+    GUARD_CTX(ctx);
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    ctx->stream = stream ? static_cast<cudaStream_t>(stream) : ctx->own_stream;
+    return DL_OK;
+}
+
+dl_status dl_tc_closure(dl_ctx *ctx, int32_t n, const uint8_t *E, dl_mem mem, double eps,
+                        double thr, dl_path path, uint64_t *out_bits, double *out_rtilde,
+                        dl_stats *stats) {
+    clear_error();
+    GUARD_CTX(ctx);
+    if (stats) std::memset(stats, 0, sizeof(*stats));
+    if (n < 0 || !valid_mem(mem)) {
+        set_error("bad n (%d) or memory kind", n);
+        return DL_EINVAL;
+    }
+    if (n == 0) return DL_OK;
+    if (!E || !out_bits) {
+        set_error("E and out_bits must not be NULL");
+        return DL_EINVAL;
+    }
+    SolveArgs a;
+    a.n = n;
+    a.E = E;
+    a.mem = mem;
+    a.eps = eps;
+    a.thr = thr;
+    a.path = path;
+    a.out_bits = out_bits;
+    a.out_rtilde = out_rtilde;
+    return run_sync(ctx, stats, [&](Workspace &ws, cudaStream_t s, dl_stats *st) {
+        return solve_tc(ctx, ws, s, a, st);
+    });
+}
+
+dl_status dl_sg_least_model(dl_ctx *ctx, int32_t n, const uint8_t *P, const uint8_t *B,
+                            dl_mem mem, double eps, double thr, dl_path path,
+                            uint64_t *out_bits, dl_stats *stats) {
+    clear_error();
+    GUARD_CTX(ctx);
+    if (stats) std::memset(stats, 0, sizeof(*stats));
+    if (n < 0 || !valid_mem(mem)) {
+        set_error("bad n (%d) or memory kind", n);
+        return DL_EINVAL;
+    }
+    if (n == 0) return DL_OK;
+    if (!P || !out_bits) {
+        set_error("P and out_bits must not be NULL");
+        return DL_EINVAL;
+    }
+    SolveArgs a;
+    a.n = n;
+    a.E = P;
+    a.E2 = B;
+    a.mem = mem;
+    a.eps = eps;
+    a.thr = thr;
+    a.path = path;
+    a.out_bits = out_bits;
+    return run_sync(ctx, stats, [&](Workspace &ws, cudaStream_t s, dl_stats *st) {
+        return solve_sg(ctx, ws, s, a, st);
+    });
+}
+
+dl_status dl_compose(dl_ctx *ctx, int32_t n, const uint8_t *R1, const uint8_t *R2, dl_mem mem,
+                     uint64_t *out_bits, dl_stats *stats) {
+    clear_error();
+    GUARD_CTX(ctx);
+    if (stats) std::memset(stats, 0, sizeof(*stats));
+    if (n < 0 || !valid_mem(mem)) {
+        set_error("bad n (%d) or memory kind", n);
+        return DL_EINVAL;
+    }
+    if (n == 0) return DL_OK;
+    if (!R1 || !R2 || !out_bits) {
+        set_error("R1, R2 and out_bits must not be NULL");
+        return DL_EINVAL;
+    }
+    SolveArgs a;
+    a.n = n;
+    a.E = R1;
+    a.E2 = R2;
+    a.mem = mem;
+    a.out_bits = out_bits;
+    return run_sync(ctx, stats, [&](Workspace &ws, cudaStream_t s, dl_stats *st) {
+        return solve_compose(ctx, ws, s, a, st);
+    });
+}
+
+dl_status dl_tc_batch(dl_ctx *ctx, int32_t count, const int32_t *ns, const uint8_t *const *Es,
+                      dl_mem mem, uint64_t *const *out_bits, dl_stats *stats) {
+    clear_error();
+    GUARD_CTX(ctx);
+    if (stats) std::memset(stats, 0, sizeof(*stats));
+    if (count < 0 || !valid_mem(mem)) {
+        set_error("bad count (%d) or memory kind", count);
+        return DL_EINVAL;
+    }
+    if (count == 0) return DL_OK;
+    if (!ns || !Es || !out_bits) {
+        set_error("ns, Es and out_bits must not be NULL");
+        return DL_EINVAL;
+    }
+    for (int32_t k = 0; k < count; ++k) {
+        if (ns[k] < 0 || (ns[k] > 0 && (!Es[k] || !out_bits[k]))) {
+            set_error("problem %d: bad n or NULL pointer", k);
+            return DL_EINVAL;
+        }
+    }
+    return run_sync(ctx, stats, [&](Workspace &ws, cudaStream_t s, dl_stats *st) {
+        return solve_tc_batch(ctx, ws, s, count, ns, Es, mem, out_bits, st);
+    });
+}
+
+}  // extern "C"

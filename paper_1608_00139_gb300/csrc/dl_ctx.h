@@ -1,0 +1,101 @@
+// dl_ctx.h -- the context behind the opaque dl_ctx handle and the per-call solve drivers.
+#pragma once
+#include <cuda_runtime.h>
+
+#include <condition_variable>
+#include <cstdarg>
+#include <cstdint>
+#include <deque>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "../../include/dl.h"
+#include "dl_internal.h"
+
+namespace dl {
+
+void set_error(const char *fmt, ...);
+
+// Grow-only device buffers, one set per execution slot (a synchronous call or one serving
+// slot), so concurrent slots never share scratch memory.
+struct Workspace {
+    struct Buf {
+        void *p = nullptr;
+        size_t bytes = 0;
+    };
+    std::map<std::string, Buf> bufs;
+    void *host_pinned = nullptr;  // small pinned staging for scalars and GEMM tables
+    size_t host_bytes = 0;
+    int *status = nullptr;         // device status word
+    unsigned long long *scal = nullptr;  // device scalars (counters)
+    cudaEvent_t ev[8] = {};
+    static constexpr int kGemmEvents = 128;  // start/stop pairs of timed GEMM launches
+    cudaEvent_t gev[kGemmEvents] = {};
+    bool ready = false;
+
+    cudaError_t init();
+    void release();
+    // device buffer of at least `bytes` (contents undefined); nullptr on failure
+    void *get(const std::string &name, size_t bytes);
+    size_t footprint() const;
+};
+
+struct Request;  // serving
+
+}  // namespace dl
+
+struct dl_ctx {
+    int device = 0;
+    int sms = 0;
+    cudaStream_t own_stream = nullptr;
+    cudaStream_t stream = nullptr;
+    dl_config cfg{};
+    uint64_t budget_ns = 2000000000ull;
+    std::mutex mu;  // serialises synchronous calls
+    dl::Workspace ws;
+
+    // serving state (dl_serve.cpp)
+    struct Serve;
+    Serve *serve = nullptr;  // owned; freed by dl_serve_shutdown
+};
+
+namespace dl {
+
+constexpr int kScalars = 64;  // device scalar slots per workspace
+// scalar slot indices
+enum : int {
+    SC_DMAX = 0, SC_NNZ = 1, SC_COUNT0 = 2, SC_VIOL = 3, SC_ONES = 4, SC_GUARD = 5,
+    SC_DMAX2 = 6, SC_NNZ2 = 7, SC_COUNT2 = 8, SC_CQ = 9, SC_CS = 10, SC_STEP0 = 16
+};
+
+struct SolveArgs {
+    int32_t n = 0;
+    const uint8_t *E = nullptr;   // closure: E; same generation: P; compose: R1
+    const uint8_t *E2 = nullptr;  // same generation: B (may be null); compose: R2
+    dl_mem mem = DL_MEM_HOST;
+    double eps = 0.0;
+    double thr = 0.0;
+    dl_path path = DL_PATH_AUTO;
+    uint64_t *out_bits = nullptr;
+    double *out_rtilde = nullptr;
+};
+
+// Drivers: run on (ws, stream); return a dl_status and fill stats.
+dl_status solve_tc(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &a, dl_stats *st);
+dl_status solve_sg(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &a, dl_stats *st);
+dl_status solve_compose(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &a,
+                        dl_stats *st);
+dl_status solve_tc_batch(dl_ctx *ctx, Workspace &ws, cudaStream_t s, int32_t count,
+                         const int32_t *ns, const uint8_t *const *Es, dl_mem mem,
+                         uint64_t *const *out_bits, dl_stats *st);
+// Device bytes a request of this kind and size needs (serving admission).
+size_t footprint_bytes(int kind, int32_t n);
+
+}  // namespace dl
+
+// Stop the serving threads of a context (no-op if serving never started).
+void dl_serve_shutdown(dl_ctx *ctx);

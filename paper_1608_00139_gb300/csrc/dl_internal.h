@@ -1,0 +1,104 @@
+// dl_internal.h -- declarations shared by the translation units of libdl (not installed).
+#pragma once
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+
+namespace dl {
+
+// Device status word bits (the host reads the word after a call).
+enum : int {
+    ST_TIMEOUT_FULL = 1,       // MMA warp: operand stage never arrived
+    ST_TIMEOUT_EMPTY = 2,      // producer: stage never released
+    ST_TIMEOUT_ACC_FULL = 4,   // epilogue: accumulator never completed
+    ST_TIMEOUT_ACC_EMPTY = 8,  // MMA warp: accumulator never drained
+    ST_TIMEOUT_DRAIN = 16,     // teardown drain expired
+    ST_BAD_INPUT = 32,         // an input byte was not 0/1
+    ST_TIMEOUT_DEP = 64,       // a dependency counter never reached its target
+};
+
+// ---------------------------------------------------------------------------------------
+// tcgen05 GEMM (dl_umma.cu)
+// ---------------------------------------------------------------------------------------
+enum GemmKind : int { KIND_F8 = 0, KIND_TF32 = 1 };
+enum GemmEpi : int { EPI_BOOL = 0, EPI_SUB_F32 = 1 };
+
+// Boolean epilogue: v = [acc > 0] OR [add8 != 0]; writes e4m3 1.0/0.0 bytes, packed bits,
+// and adds the number of ones to *count.  SUB_F32 epilogue: c32 -= acc (in place).
+struct GemmEpilogue {
+    uint8_t *out8;            // may be null
+    int64_t ld_out8;          // bytes per row
+    const uint8_t *add8;      // may be null
+    int64_t ld_add8;
+    uint32_t *bits;           // may be null; 32-bit words, bit j of word c/32 = column c+j
+    int64_t ld_bits32;        // 32-bit words per row
+    unsigned long long *count;  // may be null
+    float *c32;               // SUB_F32 only
+    int64_t ld_c32;           // floats per row
+    int32_t out_row0, out_col0;  // output coordinates of the problem's (0, 0)
+};
+
+// One GEMM problem D(MxN) = A(MxK) * B(KxN).  Lives in device memory (tensor maps are read
+// by TMA from global memory; CUtensorMap carries the descriptor alignment).
+struct GemmProblem {  // CUtensorMap members carry the TMA descriptor alignment
+    CUtensorMap tmA;  // A: K-major (row-major M x K); box {128 bytes of K, 128 rows}
+    CUtensorMap tmB;  // B: MN-major (row-major K x N; box {128 bytes of N, BK rows of K}) or
+                      //    K-major (row-major N x K; box {128 bytes of K, BN rows})
+    int32_t M, N, K;
+    int32_t tiles_m, tiles_n, tile_start;
+    int32_t a_row0, a_col0;  // A(0,0) at tensor coordinates (x = a_col0, y = a_row0)
+    int32_t b_row0, b_col0;  // B: MN-major (x = n, y = k); K-major (x = k, y = n)
+    GemmEpilogue epi;
+};
+
+struct Operand {
+    const void *base;   // start of the whole matrix (16-byte aligned)
+    int64_t rows, cols; // extents of the whole matrix, elements
+    int64_t ld;         // elements per row (row stride), ld*elem multiple of 16 bytes
+    int32_t row0, col0; // where the operand starts inside that matrix
+};
+
+// Host: fill one problem (tensor maps + tiling).  bn: 128 or 256.  Returns false and sets
+// *err on an unsupported shape.
+bool gemm_make_problem(GemmProblem *p, GemmKind kind, bool b_kmajor, int bn, int M, int N, int K,
+                       const Operand &A, const Operand &B, const GemmEpilogue &epi,
+                       std::string *err);
+// Launch over problems already in device memory.  total_tiles = sum of tiles.
+cudaError_t gemm_launch(GemmKind kind, bool b_kmajor, int bn, GemmEpi epi,
+                        const GemmProblem *d_probs, int nprob, int total_tiles, int grid,
+                        int *d_status, uint64_t budget_ns, cudaStream_t stream);
+int gemm_tile_m();
+
+// ---------------------------------------------------------------------------------------
+// Boolean / streaming kernels (dl_bool.cu)
+// ---------------------------------------------------------------------------------------
+// Validate 0/1 input, reduce row sums (max into *dmax, total into *nnz), and write the
+// e4m3 operand of size np x np: value 1.0 where src is 1, plus 1.0 on the diagonal if
+// add_identity; zero padding outside n x n.  *count gets the number of ones written.
+cudaError_t ingest_u8_to_e4m3(const uint8_t *src, int n, int np, uint8_t *dst, int add_identity,
+                              unsigned long long *dmax, unsigned long long *nnz,
+                              unsigned long long *count, int *status, cudaStream_t s);
+// One sweep of the certificate / recheck kernel on bits (64-bit words, wp words per row):
+//   mode 0 (reflexive check):  out_i = OR_{k in succ(i)} M_k;  violation iff (out_i | e_i) != M_i
+//   mode 1 (closure sweep):    out_i = M_i | E_i | OR_{k in succ(i)} M_k (in place allowed);
+//                              violation iff out_i != M_i (row changed)
+// E: n x n bytes (row stride lde).  stop_early: rows are skipped once a violation is seen.
+cudaError_t bits_sweep(const uint8_t *E, int64_t lde, int n, const uint64_t *M, uint64_t *out,
+                       int64_t wp, int mode, int stop_early, unsigned long long *violations,
+                       unsigned long long *ones, cudaStream_t s);
+
+// ---------------------------------------------------------------------------------------
+// FP64 path (dl_fp64.cu)
+// ---------------------------------------------------------------------------------------
+cudaError_t fp64_build(const uint8_t *E, int n, int np, double eps, double *G, int64_t ldg,
+                       cudaStream_t s);
+cudaError_t fp64_solve(double *G, int64_t ldg, int np, int *launches, cudaStream_t s);
+// threshold X > 0 into bits, count guard-band entries (|X| <= tau or X < 0)
+cudaError_t thresh_pack_f64(const double *X, int64_t ldx, int n, int np, double tau, uint64_t *bits,
+                            int64_t wp, unsigned long long *guard, cudaStream_t s);
+
+int num_sms();
+
+}  // namespace dl

@@ -1,0 +1,677 @@
+// dl_solve.cu -- per-call drivers: which kernels run, in which order, on which buffers.
+//
+// Closure on the FP8 tensor cores (DL_PATH_BOOL_FP8): the reflexive closure
+// C* = min1(I + E + E^2 + ...) is reached by repeated squaring, C_0 = I + E,
+// C_{t+1} = min1(C_t C_t), which covers paths of length up to 2^t after t squarings; every
+// squaring is one tcgen05 launch whose epilogue clamps (min1), packs bits and counts ones.
+// The least model of eq. matrixeq:trcl is then R2 = min1(E C*) (one step from E, then any
+// path), computed on bits by the sweep kernel, which at the same time checks that C_t
+// already satisfies C = min1(I + E C): if it does, C_t is the reflexive closure and the
+// squarings stop early; if a squaring adds no new one, they stop as well.
+//
+// Closure in FP64 (DL_PATH_FP64): Proposition 1 literally (dl_fp64.cu), threshold > 0
+// (Theorem 1), then the same sweep in its in-place "recheck" mode confirms the model
+// satisfies R2 = min1(E + E R2) and adds any fact the rounding lost (e.g. an underflowed
+// eps^d, Lemma 2 footnote); the number of corrected rows is reported.
+//
+// Same generation (Sec. 6.2): the least S = min1(B + P S P^T) by doubling on boolean
+// matrices: S_1 = B, Q_1 = P, S_{2m} = min1(S_m + Q_m S_m Q_m^T), Q_{2m} = min1(Q_m Q_m).
+// S_m collects the facts derivable through at most m-1 nested applications of the
+// recursive clause; when a step adds nothing (S_{2m} = S_m) or Q becomes 0, S is the
+// fixpoint.  Each step: one grouped launch {T = Q S, Q' = Q Q} and one launch
+// {S' = T Q^T OR S}.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <string>
+
+#include "dl_ctx.h"
+#include "dl_internal.h"
+
+namespace dl {
+
+namespace {
+
+constexpr size_t kHostPinned = 8u << 20;
+constexpr size_t kTableOffset = 4096;
+
+int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
+
+struct Timer {
+    cudaEvent_t *ev;
+    cudaStream_t s;
+    void mark(int i) { cudaEventRecord(ev[i], s); }
+    double ms(int a, int b) {
+        float t = 0.f;
+        cudaEventElapsedTime(&t, ev[a], ev[b]);
+        return t;
+    }
+};
+
+// Start/stop events around each tensor-core GEMM launch, on the launching stream.
+struct GemmClock {
+    Workspace &ws;
+    cudaStream_t s;
+    int k = 0, launches = 0;
+    double flops = 0.0;
+    void start() {
+        if (2 * k + 1 < Workspace::kGemmEvents) cudaEventRecord(ws.gev[2 * k], s);
+    }
+    void stop(double f) {
+        if (2 * k + 1 < Workspace::kGemmEvents) {
+            cudaEventRecord(ws.gev[2 * k + 1], s);
+            ++k;
+        }
+        ++launches;
+        flops += f;
+    }
+    // valid once the stream has been synchronised
+    double ms() const {
+        double t = 0.0;
+        for (int i = 0; i < k; ++i) {
+            float x = 0.f;
+            cudaEventElapsedTime(&x, ws.gev[2 * i], ws.gev[2 * i + 1]);
+            t += x;
+        }
+        return t;
+    }
+    void fill(dl_stats *st) const {
+        st->gemm_launches = launches;
+        st->ms_gemm = ms() * (k > 0 ? static_cast<double>(launches) / k : 0.0);
+        st->gemm_flops = flops;
+    }
+};
+
+#define CK(x)                                                                          \
+    do {                                                                               \
+        cudaError_t e_ = (x);                                                          \
+        if (e_ != cudaSuccess) {                                                       \
+            set_error("%s failed: %s (%s:%d)", #x, cudaGetErrorString(e_), __FILE__, __LINE__); \
+            return DL_EDEVICE;                                                         \
+        }                                                                              \
+    } while (0)
+
+#define NEED(p)                                                                        \
+    do {                                                                               \
+        if (!(p)) {                                                                    \
+            set_error("device allocation failed (%s)", #p);                            \
+            return DL_ENOMEM;                                                          \
+        }                                                                              \
+    } while (0)
+
+unsigned long long *host_scal(Workspace &ws) {
+    return static_cast<unsigned long long *>(ws.host_pinned);
+}
+
+dl_status read_scalars(Workspace &ws, cudaStream_t s) {
+    CK(cudaMemcpyAsync(ws.host_pinned, ws.scal, kScalars * sizeof(unsigned long long),
+                       cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    return DL_OK;
+}
+
+dl_status check_status(Workspace &ws, cudaStream_t s) {
+    int st = 0;
+    CK(cudaMemcpyAsync(&st, ws.status, sizeof(int), cudaMemcpyDeviceToHost, s));
+    CK(cudaStreamSynchronize(s));
+    if (st & ST_BAD_INPUT) {
+        set_error("input matrix holds a byte that is neither 0 nor 1");
+        return DL_EINVAL;
+    }
+    if (st) {
+        set_error("a device-side wait expired (status word 0x%x)", st);
+        return DL_ETIMEOUT;
+    }
+    return DL_OK;
+}
+
+// Upload `count` GEMM problems into the workspace table (device) and return it.
+dl_status upload_problems(Workspace &ws, cudaStream_t s, const GemmProblem *probs, int count,
+                          GemmProblem **out) {
+    const size_t bytes = sizeof(GemmProblem) * static_cast<size_t>(count);
+    if (kTableOffset + bytes > ws.host_bytes) {
+        set_error("GEMM table too large");
+        return DL_ENOMEM;
+    }
+    auto *d = static_cast<GemmProblem *>(ws.get("gemm_table", std::max<size_t>(bytes, 4096)));
+    NEED(d);
+    std::memcpy(static_cast<char *>(ws.host_pinned) + kTableOffset, probs, bytes);
+    CK(cudaMemcpyAsync(d, static_cast<char *>(ws.host_pinned) + kTableOffset, bytes,
+                       cudaMemcpyHostToDevice, s));
+    *out = d;
+    return DL_OK;
+}
+
+// Bring an n x n input to the device (copy if it is host memory).
+dl_status stage_input(Workspace &ws, cudaStream_t s, const uint8_t *src, int32_t n, dl_mem mem,
+                      const char *name, const uint8_t **dev) {
+    if (mem == DL_MEM_DEVICE) {
+        *dev = src;
+        return DL_OK;
+    }
+    const size_t bytes = static_cast<size_t>(n) * n;
+    auto *d = static_cast<uint8_t *>(ws.get(name, std::max<size_t>(bytes, 16)));
+    NEED(d);
+    CK(cudaMemcpyAsync(d, src, bytes, cudaMemcpyHostToDevice, s));
+    *dev = d;
+    return DL_OK;
+}
+
+dl_status write_bits(cudaStream_t s, const uint64_t *src, int64_t wp, uint64_t *dst, int32_t n,
+                     dl_mem mem) {
+    const int64_t w = (n + 63) / 64;
+    CK(cudaMemcpy2DAsync(dst, w * 8, src, wp * 8, w * 8, n,
+                         mem == DL_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+    return DL_OK;
+}
+
+Operand square_op(const void *base, int64_t np) { return Operand{base, np, np, np, 0, 0}; }
+
+GemmEpilogue bool_epi(uint8_t *out8, int64_t np, uint64_t *bits, int64_t wp,
+                      unsigned long long *count, const uint8_t *add8) {
+    GemmEpilogue e{};
+    e.out8 = out8;
+    e.ld_out8 = np;
+    e.add8 = add8;
+    e.ld_add8 = np;
+    e.bits = reinterpret_cast<uint32_t *>(bits);
+    e.ld_bits32 = 2 * wp;
+    e.count = count;
+    return e;
+}
+
+int bool_bn(int64_t np) { return np % 256 == 0 ? 256 : 128; }
+
+// Validate eps against ||E||_inf (Lemma 1) or pick the paper's default.
+dl_status choose_eps(double user, double dflt, const char *what, double *out) {
+    if (user <= 0.0) {
+        *out = dflt;
+        return DL_OK;
+    }
+    if (!(user <= dflt) || !std::isfinite(user)) {
+        set_error("eps = %g exceeds the bound %g of %s", user, dflt, what);
+        return DL_EINVAL;
+    }
+    *out = user;
+    return DL_OK;
+}
+
+// Ingest (validation, row sums, e4m3 operand).  Sets *dmax, *nnz, *count.
+dl_status ingest(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const uint8_t *dev, int32_t n,
+                 int64_t np, uint8_t *dst, int add_identity, int slot_dmax, int slot_nnz,
+                 int slot_count, int *launches) {
+    (void)ctx;
+    CK(ingest_u8_to_e4m3(dev, n, static_cast<int>(np), dst, add_identity, ws.scal + slot_dmax,
+                         ws.scal + slot_nnz, ws.scal + slot_count, ws.status, s));
+    ++*launches;
+    return DL_OK;
+}
+
+dl_status tc_bool(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &a, dl_stats *st) {
+    const int32_t n = a.n;
+    const int64_t np = round_up(std::max<int64_t>(n, 1), 256);
+    const int64_t wp = np / 64;
+    Timer tm{ws.ev, s};
+    int launches = 0;
+    tm.mark(0);
+    const uint8_t *E = nullptr;
+    dl_status rc = stage_input(ws, s, a.E, n, a.mem, "in0", &E);
+    if (rc) return rc;
+    auto *C0 = static_cast<uint8_t *>(ws.get("c0", np * np));
+    auto *C1 = static_cast<uint8_t *>(ws.get("c1", np * np));
+    auto *rbits = static_cast<uint64_t *>(ws.get("bits0", np * wp * 8));
+    auto *mbits = static_cast<uint64_t *>(ws.get("bits1", np * wp * 8));
+    NEED(C0 && C1 && rbits && mbits);
+    CK(cudaMemsetAsync(ws.scal, 0, kScalars * sizeof(unsigned long long), s));
+    CK(cudaMemsetAsync(ws.status, 0, sizeof(int), s));
+    if ((rc = ingest(ctx, ws, s, E, n, np, C0, 1, SC_DMAX, SC_NNZ, SC_COUNT0, &launches))) return rc;
+    tm.mark(1);
+    if ((rc = read_scalars(ws, s))) return rc;
+    if ((rc = check_status(ws, s))) return rc;
+    const unsigned long long dmax = host_scal(ws)[SC_DMAX];
+    double eps = 0;
+    if ((rc = choose_eps(a.eps, 1.0 / (1.0 + static_cast<double>(dmax)), "Lemma 1 (1/(1+||E||))", &eps)))
+        return rc;
+    unsigned long long prev = host_scal(ws)[SC_COUNT0];
+
+    // GEMM tables: squaring C0 -> C1 and C1 -> C0, bits into rbits, count into slot
+    GemmProblem probs[2];
+    std::string err;
+    const int bn = bool_bn(np);
+    for (int p = 0; p < 2; ++p) {
+        const uint8_t *src = p == 0 ? C0 : C1;
+        uint8_t *dst = p == 0 ? C1 : C0;
+        if (!gemm_make_problem(&probs[p], KIND_F8, false, bn, static_cast<int>(np), static_cast<int>(np),
+                               static_cast<int>(np), square_op(src, np), square_op(src, np),
+                               bool_epi(dst, np, rbits, wp, ws.scal + SC_STEP0, nullptr), &err)) {
+            set_error("%s", err.c_str());
+            return DL_EDEVICE;
+        }
+    }
+    GemmProblem *dprobs = nullptr;
+    if ((rc = upload_problems(ws, s, probs, 2, &dprobs))) return rc;
+    const int tiles = probs[0].tiles_m * probs[0].tiles_n;
+    const int grid = std::min(tiles, ctx->sms);
+
+    GemmClock gc{ws, s};
+    int t = 0;
+    bool have_model = false;
+    int sweeps = 0;
+    const int max_squarings = 2 + static_cast<int>(std::ceil(std::log2(static_cast<double>(np) + 1.0)));
+    for (;;) {
+        if (t >= max_squarings) {
+            set_error("closure did not converge in %d squarings", t);
+            return DL_ENOTCONV;
+        }
+        CK(cudaMemsetAsync(ws.scal + SC_STEP0, 0, sizeof(unsigned long long), s));
+        gc.start();
+        CK(gemm_launch(KIND_F8, false, bn, EPI_BOOL, dprobs + (t & 1), 1, tiles, grid, ws.status,
+                       ctx->budget_ns, s));
+        gc.stop(2.0 * np * np * np);
+        ++launches;
+        ++t;
+        if ((rc = read_scalars(ws, s))) return rc;
+        const unsigned long long cnt = host_scal(ws)[SC_STEP0];
+        if (cnt == prev) break;  // C_t = C_{t-1}: reflexive closure reached
+        prev = cnt;
+        // certificate: does C_t satisfy C = min1(I + E C)?  (stops at the first violation)
+        CK(cudaMemsetAsync(ws.scal + SC_VIOL, 0, 2 * sizeof(unsigned long long), s));
+        CK(bits_sweep(E, n, n, rbits, mbits, wp, 0, 1, ws.scal + SC_VIOL, ws.scal + SC_ONES, s));
+        ++launches;
+        ++sweeps;
+        if ((rc = read_scalars(ws, s))) return rc;
+        if (host_scal(ws)[SC_VIOL] == 0) {
+            have_model = true;
+            break;
+        }
+    }
+    tm.mark(2);
+    if (!have_model) {
+        CK(cudaMemsetAsync(ws.scal + SC_VIOL, 0, 2 * sizeof(unsigned long long), s));
+        CK(bits_sweep(E, n, n, rbits, mbits, wp, 0, 0, ws.scal + SC_VIOL, ws.scal + SC_ONES, s));
+        ++launches;
+        ++sweeps;
+        if ((rc = read_scalars(ws, s))) return rc;
+        if (host_scal(ws)[SC_VIOL] != 0) {
+            set_error("internal: converged closure failed its certificate");
+            return DL_EDEVICE;
+        }
+    }
+    if ((rc = write_bits(s, mbits, wp, a.out_bits, n, a.mem))) return rc;
+    tm.mark(3);
+    if ((rc = check_status(ws, s))) return rc;
+    if (st) {
+        st->path_used = DL_PATH_BOOL_FP8;
+        st->eps_used = eps;
+        st->iters = t;
+        gc.fill(st);
+        st->final_resid = 0.0;
+        st->recheck_sweeps = sweeps;
+        st->model_ones = static_cast<int64_t>(host_scal(ws)[SC_ONES]);
+        st->ms_factor = tm.ms(0, 1);
+        st->ms_solve = tm.ms(1, 2);
+        st->ms_epilogue = tm.ms(2, 3);
+        st->ms_total = tm.ms(0, 3);
+        st->gpu_launches = launches;
+    }
+    return DL_OK;
+}
+
+dl_status tc_fp64(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &a, dl_stats *st) {
+    const int32_t n = a.n;
+    const int64_t np = round_up(std::max<int64_t>(n, 1), 64);
+    const int64_t npb = round_up(std::max<int64_t>(n, 1), 256);
+    const int64_t wp = npb / 64;
+    Timer tm{ws.ev, s};
+    int launches = 0;
+    tm.mark(0);
+    const uint8_t *E = nullptr;
+    dl_status rc = stage_input(ws, s, a.E, n, a.mem, "in0", &E);
+    if (rc) return rc;
+    auto *C0 = static_cast<uint8_t *>(ws.get("c0", npb * npb));
+    auto *mbits = static_cast<uint64_t *>(ws.get("bits1", npb * wp * 8));
+    const int64_t ldg = 2 * np;
+    auto *G = static_cast<double *>(ws.get("fp64_G", np * ldg * 8));
+    NEED(C0 && mbits && G);
+    CK(cudaMemsetAsync(ws.scal, 0, kScalars * sizeof(unsigned long long), s));
+    CK(cudaMemsetAsync(ws.status, 0, sizeof(int), s));
+    // validation and row sums (the e4m3 copy is not used by this path)
+    if ((rc = ingest(ctx, ws, s, E, n, npb, C0, 0, SC_DMAX, SC_NNZ, SC_COUNT0, &launches))) return rc;
+    if ((rc = read_scalars(ws, s))) return rc;
+    if ((rc = check_status(ws, s))) return rc;
+    const unsigned long long dmax = host_scal(ws)[SC_DMAX];
+    double eps = 0;
+    if ((rc = choose_eps(a.eps, 1.0 / (1.0 + static_cast<double>(dmax)), "Lemma 1 (1/(1+||E||))", &eps)))
+        return rc;
+    CK(fp64_build(E, n, static_cast<int>(np), eps, G, ldg, s));
+    ++launches;
+    tm.mark(1);
+    CK(fp64_solve(G, ldg, static_cast<int>(np), &launches, s));
+    tm.mark(2);
+    const double *X = G + np;
+    const double tau = ctx->cfg.guard_tau > 0 ? ctx->cfg.guard_tau : 1e-30;
+    CK(thresh_pack_f64(X, ldg, n, static_cast<int>(np), tau, mbits, wp, ws.scal + SC_GUARD, s));
+    ++launches;
+    // recheck: in-place sweeps until the model satisfies R2 = min1(E + E R2)
+    int sweeps = 0;
+    unsigned long long corrected = 0;
+    for (;;) {
+        CK(cudaMemsetAsync(ws.scal + SC_VIOL, 0, 2 * sizeof(unsigned long long), s));
+        CK(bits_sweep(E, n, n, mbits, mbits, wp, 1, 0, ws.scal + SC_VIOL, ws.scal + SC_ONES, s));
+        ++launches;
+        ++sweeps;
+        if ((rc = read_scalars(ws, s))) return rc;
+        const unsigned long long v = host_scal(ws)[SC_VIOL];
+        if (v == 0) break;
+        corrected += v;
+        if (sweeps > n + 1) {
+            set_error("recheck did not converge");
+            return DL_ENOTCONV;
+        }
+    }
+    if ((rc = write_bits(s, mbits, wp, a.out_bits, n, a.mem))) return rc;
+    if (a.out_rtilde) {
+        CK(cudaMemcpy2DAsync(a.out_rtilde, static_cast<size_t>(n) * 8, X, ldg * 8,
+                             static_cast<size_t>(n) * 8, n,
+                             a.mem == DL_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+    }
+    tm.mark(3);
+    if ((rc = check_status(ws, s))) return rc;
+    if (st) {
+        st->path_used = DL_PATH_FP64;
+        st->eps_used = eps;
+        st->iters = 0;
+        st->final_resid = -1.0;
+        st->guard_flagged = static_cast<int64_t>(host_scal(ws)[SC_GUARD]);
+        st->rows_rechecked = static_cast<int64_t>(corrected);
+        st->recheck_sweeps = sweeps;
+        st->model_ones = static_cast<int64_t>(host_scal(ws)[SC_ONES]);
+        st->ms_factor = tm.ms(0, 1);
+        st->ms_solve = tm.ms(1, 2);
+        st->ms_epilogue = tm.ms(2, 3);
+        st->ms_total = tm.ms(0, 3);
+        st->gpu_launches = launches;
+    }
+    return DL_OK;
+}
+
+}  // namespace
+
+dl_status solve_tc(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &a, dl_stats *st) {
+    if (a.thr != 0.0) {
+        set_error("thr must be 0: the model is R~ > 0 (Theorem 1)");
+        return DL_EINVAL;
+    }
+    dl_status rc;
+    switch (a.path) {
+        case DL_PATH_AUTO:
+        case DL_PATH_BOOL_FP8:
+            if (a.out_rtilde) {
+                set_error("the boolean path computes no real-valued R~; use DL_PATH_FP64");
+                return DL_EINVAL;
+            }
+            rc = tc_bool(ctx, ws, s, a, st);
+            break;
+        case DL_PATH_FP64:
+            rc = tc_fp64(ctx, ws, s, a, st);
+            break;
+        case DL_PATH_MIXED:
+            set_error("DL_PATH_MIXED is not available in this build");
+            return DL_ENOTIMPL;
+        default:
+            set_error("unknown path %d", static_cast<int>(a.path));
+            return DL_EINVAL;
+    }
+    if (rc == DL_OK && st && st->ms_total > 0) {
+        const double nn = static_cast<double>(a.n);
+        st->tflops_equiv = (8.0 / 3.0) * nn * nn * nn / (st->ms_total * 1e-3) / 1e12;
+    }
+    return rc;
+}
+
+dl_status solve_sg(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &a, dl_stats *st) {
+    if (a.thr != 0.0) {
+        set_error("thr must be 0: the model is S~ > 0 (Theorem 2)");
+        return DL_EINVAL;
+    }
+    if (a.path != DL_PATH_AUTO && a.path != DL_PATH_BOOL_FP8) {
+        set_error("same generation runs on DL_PATH_BOOL_FP8 only");
+        return DL_ENOTIMPL;
+    }
+    const int32_t n = a.n;
+    const int64_t np = round_up(std::max<int64_t>(n, 1), 256);
+    const int64_t wp = np / 64;
+    Timer tm{ws.ev, s};
+    int launches = 0;
+    tm.mark(0);
+    const uint8_t *P = nullptr, *Bm = nullptr;
+    dl_status rc = stage_input(ws, s, a.E, n, a.mem, "in0", &P);
+    if (rc) return rc;
+    if (a.E2 && (rc = stage_input(ws, s, a.E2, n, a.mem, "in1", &Bm))) return rc;
+    uint8_t *Sa = static_cast<uint8_t *>(ws.get("c0", np * np));
+    uint8_t *Sb = static_cast<uint8_t *>(ws.get("c1", np * np));
+    uint8_t *Qa = static_cast<uint8_t *>(ws.get("c2", np * np));
+    uint8_t *Qb = static_cast<uint8_t *>(ws.get("c3", np * np));
+    uint8_t *T = static_cast<uint8_t *>(ws.get("c4", np * np));
+    auto *sbits = static_cast<uint64_t *>(ws.get("bits0", np * wp * 8));
+    NEED(Sa && Sb && Qa && Qb && T && sbits);
+    CK(cudaMemsetAsync(ws.scal, 0, kScalars * sizeof(unsigned long long), s));
+    CK(cudaMemsetAsync(ws.status, 0, sizeof(int), s));
+    if ((rc = ingest(ctx, ws, s, P, n, np, Qa, 0, SC_DMAX, SC_NNZ, SC_COUNT0, &launches))) return rc;
+    if (Bm) {
+        if ((rc = ingest(ctx, ws, s, Bm, n, np, Sa, 0, SC_DMAX2, SC_NNZ2, SC_COUNT2, &launches))) return rc;
+    } else {
+        // identity: no source rows, diagonal added (rows past n are padding)
+        if ((rc = ingest(ctx, ws, s, nullptr, 0, np, Sa, 1, SC_DMAX2, SC_NNZ2, SC_COUNT2, &launches)))
+            return rc;
+    }
+    tm.mark(1);
+    if ((rc = read_scalars(ws, s))) return rc;
+    if ((rc = check_status(ws, s))) return rc;
+    const double dmax = static_cast<double>(host_scal(ws)[SC_DMAX]);
+    double eps = 0;
+    if ((rc = choose_eps(a.eps, 1.0 / (1.0 + dmax * dmax), "Sec. 6.2 (1/(1+||P||^2))", &eps))) return rc;
+    unsigned long long s_count = host_scal(ws)[SC_COUNT2];
+    if (!Bm) s_count = static_cast<unsigned long long>(np);  // identity over padded size
+    const unsigned long long q_count0 = host_scal(ws)[SC_COUNT0];
+
+    // Tables per parity: [T = Q S, Q' = Q Q] (MN-major B) and [S' = T Q^T | S] (K-major B).
+    const int bn = bool_bn(np);
+    GemmProblem g1[4], g2[2];
+    std::string err;
+    for (int p = 0; p < 2; ++p) {
+        uint8_t *Sc = p ? Sb : Sa, *Sn = p ? Sa : Sb, *Qc = p ? Qb : Qa, *Qn = p ? Qa : Qb;
+        const int N = static_cast<int>(np);
+        bool ok = gemm_make_problem(&g1[2 * p], KIND_F8, false, bn, N, N, N, square_op(Qc, np),
+                                    square_op(Sc, np), bool_epi(T, np, nullptr, wp, nullptr, nullptr), &err) &&
+                  gemm_make_problem(&g1[2 * p + 1], KIND_F8, false, bn, N, N, N, square_op(Qc, np),
+                                    square_op(Qc, np), bool_epi(Qn, np, nullptr, wp, ws.scal + SC_CQ, nullptr),
+                                    &err) &&
+                  gemm_make_problem(&g2[p], KIND_F8, true, bn, N, N, N, square_op(T, np), square_op(Qc, np),
+                                    bool_epi(Sn, np, sbits, wp, ws.scal + SC_CS, Sc), &err);
+        if (!ok) {
+            set_error("%s", err.c_str());
+            return DL_EDEVICE;
+        }
+        g1[2 * p + 1].tile_start = g1[2 * p].tiles_m * g1[2 * p].tiles_n;
+    }
+    GemmProblem all[6] = {g1[0], g1[1], g1[2], g1[3], g2[0], g2[1]};
+    GemmProblem *d = nullptr;
+    if ((rc = upload_problems(ws, s, all, 6, &d))) return rc;
+    const int tiles1 = g1[0].tiles_m * g1[0].tiles_n;
+    const int grid1 = std::min(2 * tiles1, ctx->sms), grid2 = std::min(tiles1, ctx->sms);
+
+    GemmClock gc{ws, s};
+    int step = 0;
+    (void)q_count0;  // P = 0 ends after one step (Q' = 0, S' = B)
+    const int max_steps = 2 + static_cast<int>(std::ceil(std::log2(static_cast<double>(np) + 1.0)));
+    for (;;) {
+        if (step >= max_steps) {
+            set_error("same-generation doubling did not converge in %d steps", step);
+            return DL_ENOTCONV;
+        }
+        const int p = step & 1;
+        CK(cudaMemsetAsync(ws.scal + SC_CQ, 0, 2 * sizeof(unsigned long long), s));
+        gc.start();
+        CK(gemm_launch(KIND_F8, false, bn, EPI_BOOL, d + 2 * p, 2, 2 * tiles1, grid1, ws.status,
+                       ctx->budget_ns, s));
+        gc.stop(4.0 * np * np * np);
+        gc.start();
+        CK(gemm_launch(KIND_F8, true, bn, EPI_BOOL, d + 4 + p, 1, tiles1, grid2, ws.status,
+                       ctx->budget_ns, s));
+        gc.stop(2.0 * np * np * np);
+        launches += 2;
+        ++step;
+        if ((rc = read_scalars(ws, s))) return rc;
+        const unsigned long long cs = host_scal(ws)[SC_CS], cq = host_scal(ws)[SC_CQ];
+        if (cs == s_count || cq == 0) break;
+        s_count = cs;
+    }
+    tm.mark(2);
+    if ((rc = write_bits(s, sbits, wp, a.out_bits, n, a.mem))) return rc;
+    tm.mark(3);
+    if ((rc = check_status(ws, s))) return rc;
+    if (st) {
+        st->path_used = DL_PATH_BOOL_FP8;
+        st->eps_used = eps;
+        st->iters = step;
+        gc.fill(st);
+        st->ms_factor = tm.ms(0, 1);
+        st->ms_solve = tm.ms(1, 2);
+        st->ms_epilogue = tm.ms(2, 3);
+        st->ms_total = tm.ms(0, 3);
+        st->gpu_launches = launches;
+    }
+    return DL_OK;
+}
+
+dl_status solve_compose(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &a,
+                        dl_stats *st) {
+    const int32_t n = a.n;
+    const int64_t np = round_up(std::max<int64_t>(n, 1), 256);
+    const int64_t wp = np / 64;
+    Timer tm{ws.ev, s};
+    int launches = 0;
+    tm.mark(0);
+    const uint8_t *R1 = nullptr, *R2 = nullptr;
+    dl_status rc = stage_input(ws, s, a.E, n, a.mem, "in0", &R1);
+    if (rc) return rc;
+    if ((rc = stage_input(ws, s, a.E2, n, a.mem, "in1", &R2))) return rc;
+    auto *A8 = static_cast<uint8_t *>(ws.get("c0", np * np));
+    auto *B8 = static_cast<uint8_t *>(ws.get("c1", np * np));
+    auto *bits = static_cast<uint64_t *>(ws.get("bits0", np * wp * 8));
+    NEED(A8 && B8 && bits);
+    CK(cudaMemsetAsync(ws.scal, 0, kScalars * sizeof(unsigned long long), s));
+    CK(cudaMemsetAsync(ws.status, 0, sizeof(int), s));
+    if ((rc = ingest(ctx, ws, s, R1, n, np, A8, 0, SC_DMAX, SC_NNZ, SC_COUNT0, &launches))) return rc;
+    if ((rc = ingest(ctx, ws, s, R2, n, np, B8, 0, SC_DMAX2, SC_NNZ2, SC_COUNT2, &launches))) return rc;
+    tm.mark(1);
+    GemmProblem pr;
+    std::string err;
+    const int bn = bool_bn(np);
+    if (!gemm_make_problem(&pr, KIND_F8, false, bn, static_cast<int>(np), static_cast<int>(np),
+                           static_cast<int>(np), square_op(A8, np), square_op(B8, np),
+                           bool_epi(nullptr, np, bits, wp, ws.scal + SC_ONES, nullptr), &err)) {
+        set_error("%s", err.c_str());
+        return DL_EDEVICE;
+    }
+    GemmProblem *d = nullptr;
+    if ((rc = upload_problems(ws, s, &pr, 1, &d))) return rc;
+    const int tiles = pr.tiles_m * pr.tiles_n;
+    GemmClock gc{ws, s};
+    gc.start();
+    CK(gemm_launch(KIND_F8, false, bn, EPI_BOOL, d, 1, tiles, std::min(tiles, ctx->sms), ws.status,
+                   ctx->budget_ns, s));
+    gc.stop(2.0 * np * np * np);
+    ++launches;
+    tm.mark(2);
+    if ((rc = write_bits(s, bits, wp, a.out_bits, n, a.mem))) return rc;
+    tm.mark(3);
+    if ((rc = read_scalars(ws, s))) return rc;
+    if ((rc = check_status(ws, s))) return rc;
+    if (st) {
+        st->path_used = DL_PATH_BOOL_FP8;
+        gc.fill(st);
+        st->model_ones = static_cast<int64_t>(host_scal(ws)[SC_ONES]);
+        st->ms_factor = tm.ms(0, 1);
+        st->ms_solve = tm.ms(1, 2);
+        st->ms_epilogue = tm.ms(2, 3);
+        st->ms_total = tm.ms(0, 3);
+        st->gpu_launches = launches;
+    }
+    return DL_OK;
+}
+
+dl_status solve_tc_batch(dl_ctx *, Workspace &, cudaStream_t, int32_t, const int32_t *,
+                         const uint8_t *const *, dl_mem, uint64_t *const *, dl_stats *) {
+    set_error("dl_tc_batch is not available in this build");
+    return DL_ENOTIMPL;
+}
+
+size_t footprint_bytes(int kind, int32_t n) {
+    const size_t np = static_cast<size_t>(round_up(std::max<int64_t>(n, 1), 256));
+    const size_t mats = kind == 0 ? 3 : 6;  // staged input + ping-pong (+ Q pair, T for SG)
+    return mats * np * np + 2 * np * (np / 8) + (1u << 20);
+}
+
+// ---- workspace ------------------------------------------------------------------------
+
+cudaError_t Workspace::init() {
+    if (ready) return cudaSuccess;
+    cudaError_t e;
+    if ((e = cudaMallocHost(&host_pinned, kHostPinned)) != cudaSuccess) return e;
+    host_bytes = kHostPinned;
+    if ((e = cudaMalloc(&status, 256)) != cudaSuccess) return e;
+    if ((e = cudaMalloc(&scal, kScalars * sizeof(unsigned long long))) != cudaSuccess) return e;
+    for (auto &x : ev)
+        if ((e = cudaEventCreate(&x)) != cudaSuccess) return e;
+    for (auto &x : gev)
+        if ((e = cudaEventCreate(&x)) != cudaSuccess) return e;
+    ready = true;
+    return cudaSuccess;
+}
+
+void Workspace::release() {
+    for (auto &kv : bufs)
+        if (kv.second.p) cudaFree(kv.second.p);
+    bufs.clear();
+    if (host_pinned) cudaFreeHost(host_pinned);
+    if (status) cudaFree(status);
+    if (scal) cudaFree(scal);
+    for (auto &x : ev)
+        if (x) cudaEventDestroy(x);
+    for (auto &x : gev)
+        if (x) cudaEventDestroy(x);
+    host_pinned = nullptr;
+    status = nullptr;
+    scal = nullptr;
+    ready = false;
+}
+
+void *Workspace::get(const std::string &name, size_t bytes) {
+    Buf &b = bufs[name];
+    if (b.p && b.bytes >= bytes) return b.p;
+    if (b.p) {
+        cudaFree(b.p);
+        b.p = nullptr;
+        b.bytes = 0;
+    }
+    size_t want = (bytes + 4095) & ~static_cast<size_t>(4095);
+    if (cudaMalloc(&b.p, want) != cudaSuccess) {
+        cudaGetLastError();
+        b.p = nullptr;
+        return nullptr;
+    }
+    b.bytes = want;
+    return b.p;
+}
+
+size_t Workspace::footprint() const {
+    size_t t = 0;
+    for (auto &kv : bufs) t += kv.second.bytes;
+    return t;
+}
+
+}  // namespace dl

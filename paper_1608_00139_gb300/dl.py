@@ -1,0 +1,265 @@
+"""Python binding of libdl (include/dl.h): argument marshalling only.
+
+Every step of every path runs in the CUDA library; this module converts numpy arrays (host
+memory, DL_MEM_HOST) or torch CUDA tensors (device memory, DL_MEM_DEVICE) into pointers and
+sizes, calls the C ABI and raises :class:`DLError` on a non-zero status.  There is no CPU
+fallback: if libdl.so is missing or the GPU is not an sm_103 part, calls fail loudly.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libdl.so")
+
+DL_OK, DL_EINVAL, DL_ENOMEM, DL_EDEVICE, DL_ETIMEOUT, DL_EBUSY, DL_ENOTCONV, DL_ECANCELED, \
+    DL_ENOTIMPL = range(9)
+STATUS_NAMES = ["DL_OK", "DL_EINVAL", "DL_ENOMEM", "DL_EDEVICE", "DL_ETIMEOUT", "DL_EBUSY",
+                "DL_ENOTCONV", "DL_ECANCELED", "DL_ENOTIMPL"]
+PATHS = {"auto": 0, "fp64": 1, "mixed": 2, "bool_fp8": 3, "fp8": 3}
+DL_MEM_HOST, DL_MEM_DEVICE = 0, 1
+
+EXPORTED = ["dl_create", "dl_destroy", "dl_last_error", "dl_set_stream", "dl_tc_closure",
+            "dl_sg_least_model", "dl_compose", "dl_tc_batch", "dl_submit", "dl_poll", "dl_cancel"]
+
+
+class DLError(RuntimeError):
+    def __init__(self, status: int, message: str):
+        name = STATUS_NAMES[status] if 0 <= status < len(STATUS_NAMES) else str(status)
+        super().__init__(f"{name}: {message}")
+        self.status = status
+        self.message = message
+
+
+class Config(ctypes.Structure):
+    _fields_ = [("stream", ctypes.c_void_p), ("hbm_budget_bytes", ctypes.c_size_t),
+                ("max_slots", ctypes.c_int32), ("refine_tol", ctypes.c_double),
+                ("refine_max_iters", ctypes.c_int32), ("guard_tau", ctypes.c_double),
+                ("wait_timeout_s", ctypes.c_double)]
+
+
+class Stats(ctypes.Structure):
+    _fields_ = [("path_used", ctypes.c_int32), ("eps_used", ctypes.c_double),
+                ("iters", ctypes.c_int32), ("final_resid", ctypes.c_double),
+                ("guard_flagged", ctypes.c_int64), ("rows_rechecked", ctypes.c_int64),
+                ("recheck_sweeps", ctypes.c_int32), ("model_ones", ctypes.c_int64),
+                ("ms_total", ctypes.c_double), ("ms_factor", ctypes.c_double),
+                ("ms_solve", ctypes.c_double), ("ms_refine", ctypes.c_double),
+                ("ms_epilogue", ctypes.c_double), ("tflops_equiv", ctypes.c_double),
+                ("gpu_launches", ctypes.c_int32), ("gemm_launches", ctypes.c_int32),
+                ("ms_gemm", ctypes.c_double), ("gemm_flops", ctypes.c_double)]
+
+    def as_dict(self) -> dict:
+        return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class Request(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int32), ("n", ctypes.c_int32), ("base", ctypes.c_void_p),
+                ("B", ctypes.c_void_p), ("mem", ctypes.c_int), ("path", ctypes.c_int),
+                ("out_bits", ctypes.c_void_p)]
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def lib() -> ctypes.CDLL:
+    """Load libdl.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                                   "`python -m paper_1608_00139_gb300.build`")
+            L = ctypes.CDLL(LIB_PATH)
+            vp, i32, i64, f64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_double
+            L.dl_create.argtypes = [ctypes.POINTER(vp), ctypes.c_int, ctypes.POINTER(Config)]
+            L.dl_destroy.argtypes = [vp]
+            L.dl_last_error.argtypes = []
+            L.dl_last_error.restype = ctypes.c_char_p
+            L.dl_set_stream.argtypes = [vp, vp]
+            L.dl_tc_closure.argtypes = [vp, i32, vp, ctypes.c_int, f64, f64, ctypes.c_int, vp, vp,
+                                        ctypes.POINTER(Stats)]
+            L.dl_sg_least_model.argtypes = [vp, i32, vp, vp, ctypes.c_int, f64, f64, ctypes.c_int,
+                                            vp, ctypes.POINTER(Stats)]
+            L.dl_compose.argtypes = [vp, i32, vp, vp, ctypes.c_int, vp, ctypes.POINTER(Stats)]
+            L.dl_tc_batch.argtypes = [vp, i32, vp, vp, ctypes.c_int, vp, ctypes.POINTER(Stats)]
+            L.dl_submit.argtypes = [vp, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_uint64)]
+            L.dl_poll.argtypes = [vp, ctypes.c_uint64, i64, ctypes.POINTER(Stats)]
+            L.dl_cancel.argtypes = [vp, ctypes.c_uint64]
+            for f in EXPORTED:
+                if f != "dl_last_error":
+                    getattr(L, f).restype = ctypes.c_int
+            _lib = L
+    return _lib
+
+
+def _check(rc: int) -> None:
+    if rc != DL_OK:
+        msg = lib().dl_last_error() or b""
+        raise DLError(rc, msg.decode(errors="replace"))
+
+
+def words(n: int) -> int:
+    return (n + 63) // 64
+
+
+def _is_torch(x) -> bool:
+    return type(x).__module__.startswith("torch")
+
+
+def _square_u8(x):
+    """(pointer, n, mem, keepalive) of a square 0/1 uint8 matrix (numpy or torch CUDA)."""
+    if _is_torch(x):
+        import torch
+        if not x.is_cuda:
+            x = x.numpy()
+        else:
+            if x.dtype != torch.uint8 or x.dim() != 2 or x.shape[0] != x.shape[1]:
+                raise ValueError("expected a square torch.uint8 CUDA tensor")
+            x = x.contiguous()
+            return x.data_ptr(), int(x.shape[0]), DL_MEM_DEVICE, x
+    a = np.ascontiguousarray(x, dtype=np.uint8)
+    if a.ndim != 2 or a.shape[0] != a.shape[1]:
+        raise ValueError("expected a square matrix")
+    return a.ctypes.data, int(a.shape[0]), DL_MEM_HOST, a
+
+
+def _alloc_bits(n: int, mem: int, like=None):
+    if mem == DL_MEM_DEVICE:
+        import torch
+        t = torch.zeros((n, words(n)), dtype=torch.int64, device=like.device)
+        return t, t.data_ptr()
+    a = np.zeros((n, words(n)), dtype=np.uint64)
+    return a, a.ctypes.data
+
+
+class Context:
+    """A libdl context on one GPU.  ``stream``: a torch.cuda.Stream or raw cudaStream_t."""
+
+    def __init__(self, device: int = 0, stream=None, **cfg):
+        c = Config()
+        for k, v in cfg.items():
+            setattr(c, k, v)
+        h = ctypes.c_void_p()
+        _check(lib().dl_create(ctypes.byref(h), int(device), ctypes.byref(c)))
+        self._h = h
+        if stream is not None:
+            self.set_stream(stream)
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            lib().dl_destroy(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_stream(self, stream) -> None:
+        raw = getattr(stream, "cuda_stream", stream)
+        _check(lib().dl_set_stream(self._h, ctypes.c_void_p(raw or 0)))
+
+    def tc_closure(self, E, eps: float = 0.0, thr: float = 0.0, path: str = "auto",
+                   rtilde: bool = False):
+        """Least model of the closure program; returns (bits, stats[, R~])."""
+        p, n, mem, keep = _square_u8(E)
+        bits, bp = _alloc_bits(n, mem, keep)
+        rt, rp = None, None
+        if rtilde:
+            if mem == DL_MEM_DEVICE:
+                import torch
+                rt = torch.zeros((n, n), dtype=torch.float64, device=keep.device)
+                rp = rt.data_ptr()
+            else:
+                rt = np.zeros((n, n), dtype=np.float64)
+                rp = rt.ctypes.data
+        st = Stats()
+        _check(lib().dl_tc_closure(self._h, n, p, mem, float(eps), float(thr), PATHS[path], bp, rp,
+                                   ctypes.byref(st)))
+        return (bits, st.as_dict(), rt) if rtilde else (bits, st.as_dict())
+
+    def sg_least_model(self, P, B=None, eps: float = 0.0, thr: float = 0.0,
+                       path: str = "auto"):
+        """Least model of the same-generation program; returns (bits, stats)."""
+        p, n, mem, keep = _square_u8(P)
+        bptr, keepb = None, None
+        if B is not None:
+            bptr, nb, memb, keepb = _square_u8(B)
+            if nb != n or memb != mem:
+                raise ValueError("B must match P in size and memory kind")
+        bits, bp = _alloc_bits(n, mem, keep)
+        st = Stats()
+        _check(lib().dl_sg_least_model(self._h, n, p, bptr, mem, float(eps), float(thr),
+                                       PATHS[path], bp, ctypes.byref(st)))
+        return bits, st.as_dict()
+
+    def compose(self, R1, R2):
+        """Bits of min1(R1 R2), the join of Sec. 2; returns (bits, stats)."""
+        p1, n, mem, k1 = _square_u8(R1)
+        p2, n2, mem2, k2 = _square_u8(R2)
+        if n2 != n or mem2 != mem:
+            raise ValueError("R1 and R2 must match in size and memory kind")
+        bits, bp = _alloc_bits(n, mem, k1)
+        st = Stats()
+        _check(lib().dl_compose(self._h, n, p1, p2, mem, bp, ctypes.byref(st)))
+        return bits, st.as_dict()
+
+    def tc_batch(self, Es):
+        """Closure of each matrix in ``Es`` in one batched call; returns (bits list, stats)."""
+        parts = [_square_u8(e) for e in Es]
+        if not parts:
+            return [], Stats().as_dict()
+        mems = {m for _, _, m, _ in parts}
+        if len(mems) != 1:
+            raise ValueError("all matrices must live in the same memory kind")
+        mem = mems.pop()
+        outs = [_alloc_bits(n, mem, keep) for _, n, _, keep in parts]
+        cnt = len(parts)
+        ns = (ctypes.c_int32 * cnt)(*[n for _, n, _, _ in parts])
+        ptrs = (ctypes.c_void_p * cnt)(*[p for p, _, _, _ in parts])
+        optrs = (ctypes.c_void_p * cnt)(*[bp for _, bp in outs])
+        st = Stats()
+        _check(lib().dl_tc_batch(self._h, cnt, ns, ptrs, mem, optrs, ctypes.byref(st)))
+        return [b for b, _ in outs], st.as_dict()
+
+    # ---- serving -------------------------------------------------------------------
+    def submit(self, kind: int, base, B=None, path: str = "auto"):
+        """Queue a request (0 = closure, 1 = same generation); returns (ticket, handle).
+
+        Keep ``handle`` alive until :meth:`poll` has returned for the ticket: it owns the
+        input and output buffers.  ``handle['bits']`` is the output.
+        """
+        p, n, mem, keep = _square_u8(base)
+        bptr, keepb = None, None
+        if B is not None:
+            bptr, _, _, keepb = _square_u8(B)
+        bits, bp = _alloc_bits(n, mem, keep)
+        req = Request(int(kind), n, p, bptr, mem, PATHS[path], bp)
+        t = ctypes.c_uint64(0)
+        _check(lib().dl_submit(self._h, ctypes.byref(req), ctypes.byref(t)))
+        return t.value, {"bits": bits, "keep": (keep, keepb), "n": n}
+
+    def poll(self, ticket: int, timeout_us: int = 0):
+        """(status, stats): status DL_OK when done, DL_EBUSY while running; raises on errors."""
+        st = Stats()
+        rc = lib().dl_poll(self._h, ctypes.c_uint64(ticket), int(timeout_us), ctypes.byref(st))
+        if rc == DL_EBUSY:
+            return DL_EBUSY, None
+        _check(rc)
+        return DL_OK, st.as_dict()
+
+    def cancel(self, ticket: int) -> int:
+        return lib().dl_cancel(self._h, ctypes.c_uint64(ticket))

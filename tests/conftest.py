@@ -18,3 +18,14 @@ def oracle_lib():
     import oracle
     oracle.build()
     return oracle
+
+
+@pytest.fixture(scope="session")
+def ctx():
+    """A libdl context on cuda:0 (GPU tests only)."""
+    from paper_1608_00139_gb300 import build as libbuild
+    from paper_1608_00139_gb300 import dl
+    libbuild.build()
+    c = dl.Context(0)
+    yield c
+    c.close()

@@ -1,0 +1,200 @@
+"""GPU parity at sizes the oracle finishes in well under a second: every path, tile edges,
+ragged tails, degenerate inputs and argument errors.  Bits must equal the oracle's bits."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1608_00139_gb300 import dl, inputs
+from tests.golden.load import read
+
+pytestmark = pytest.mark.gpu
+
+EDGE_SIZES = [1, 2, 31, 32, 33, 63, 64, 65, 127, 128, 129, 255, 256, 257, 300, 511, 513]
+
+
+def ref_compose(a, b):
+    return oracle.pack((a.astype(np.int64) @ b.astype(np.int64)) > 0)
+
+
+# --- tensor-core boolean product (the join of Sec. 2) ---------------------------------
+
+@pytest.mark.parametrize("n", EDGE_SIZES)
+def test_compose_tile_edges(ctx, n):
+    rng = np.random.default_rng(n)
+    a = (rng.random((n, n)) < 0.05).astype(np.uint8)
+    b = (rng.random((n, n)) < 0.05).astype(np.uint8)
+    bits, st = ctx.compose(a, b)
+    assert np.array_equal(bits, ref_compose(a, b))
+
+
+def test_compose_dense_counts_and_device_memory(ctx):
+    n = 700
+    rng = np.random.default_rng(3)
+    a = (rng.random((n, n)) < 0.5).astype(np.uint8)
+    b = (rng.random((n, n)) < 0.002).astype(np.uint8)
+    ref = ref_compose(a, b)
+    bits_h, st = ctx.compose(a, b)
+    bits_d, _ = ctx.compose(torch.from_numpy(a).cuda(), torch.from_numpy(b).cuda())
+    assert np.array_equal(bits_h, ref)
+    assert np.array_equal(bits_d.cpu().numpy().view(np.uint64), ref)
+    assert st["model_ones"] == int(oracle.unpack(ref, n).sum())
+
+
+# --- transitive closure ---------------------------------------------------------------
+
+def test_worked_example_all_paths(ctx):
+    g = read("worked_example_tc.txt")
+    e = g["R1"].astype(np.uint8)
+    want = oracle.pack(g["R2"])
+    b8, st8 = ctx.tc_closure(e, path="bool_fp8")
+    assert np.array_equal(b8, want)
+    assert st8["eps_used"] == 0.5
+    b64, st64, x = ctx.tc_closure(e, path="fp64", rtilde=True)
+    assert np.array_equal(b64, want)
+    exact = np.array([[1, 4, 2, 0], [2, 1, 4, 0], [4, 2, 1, 0], [4, 2, 1, 0]]) / 7.0
+    assert np.max(np.abs(x - exact)) < 1e-14
+    assert np.array_equal(np.floor(x * 1e4 + 1e-9) / 1e4, g["Rtilde_printed"])
+
+
+@pytest.mark.parametrize("n", EDGE_SIZES)
+@pytest.mark.parametrize("path", ["bool_fp8", "fp64"])
+def test_closure_tile_edges(ctx, n, path):
+    e = inputs.er_digraph(n, min(0.5, 3.0 / n), 100 + n)
+    bits, st = ctx.tc_closure(e, path=path)
+    assert np.array_equal(bits, oracle.tc_model(e))
+    assert st["path_used"] == dl.PATHS[path]
+
+
+@pytest.mark.parametrize("kind", ["empty", "ones_loops", "complete", "chain", "cycle",
+                                  "self_loops", "star_in", "two_chains"])
+def test_closure_degenerate_graphs(ctx, kind):
+    n = 300
+    e = np.zeros((n, n), dtype=np.uint8)
+    if kind == "ones_loops":
+        e[:] = 1
+    elif kind == "complete":
+        e[:] = 1
+        np.fill_diagonal(e, 0)
+    elif kind == "chain":
+        e[np.arange(n - 1), np.arange(1, n)] = 1
+    elif kind == "cycle":
+        e[np.arange(n), (np.arange(n) + 1) % n] = 1
+    elif kind == "self_loops":
+        np.fill_diagonal(e, 1)
+    elif kind == "star_in":
+        e[1:, 0] = 1
+    elif kind == "two_chains":
+        e[np.arange(0, n - 2, 2), np.arange(2, n, 2)] = 1
+    ref = oracle.tc_model(e)
+    for path in ("bool_fp8", "fp64"):
+        bits, st = ctx.tc_closure(e, path=path)
+        assert np.array_equal(bits, ref), path
+
+
+def test_chain_needs_log_squarings(ctx):
+    n = 1000
+    e = np.zeros((n, n), dtype=np.uint8)
+    e[np.arange(n - 1), np.arange(1, n)] = 1
+    bits, st = ctx.tc_closure(e, path="bool_fp8")
+    assert np.array_equal(bits, oracle.tc_model(e))
+    assert st["iters"] == 10  # paths up to 999 need 2^t >= 999
+
+
+def test_fp64_path_underflow_is_repaired_by_recheck(ctx):
+    """A chain of 1100 constants: eps = 1/2 and eps^d underflows FP64 for d > 1074, so the
+    threshold misses facts; the exact recheck must restore them (Lemma 2 footnote)."""
+    n = 1100
+    e = np.zeros((n, n), dtype=np.uint8)
+    e[np.arange(n - 1), np.arange(1, n)] = 1
+    bits, st = ctx.tc_closure(e, path="fp64")
+    assert np.array_equal(bits, oracle.tc_model(e))
+    assert st["rows_rechecked"] > 0
+
+
+@pytest.mark.parametrize("n,p,seed", [(256, 0.02, 1), (400, 0.01, 2), (600, 0.005, 3)])
+def test_fp64_rtilde_matches_oracle(ctx, n, p, seed):
+    e = inputs.er_digraph(n, p, seed)
+    bits, st, x = ctx.tc_closure(e, path="fp64", rtilde=True)
+    xr = oracle.tc_rtilde_lu(e, st["eps_used"])
+    assert st["eps_used"] == oracle.tc_eps(e)
+    err = np.abs(x - xr).max() / np.abs(xr).max()
+    assert err <= 1e-10
+    assert np.array_equal(bits, oracle.tc_model(e))
+    assert np.array_equal(oracle.pack(x > 0), bits)
+
+
+def test_user_eps(ctx):
+    e = inputs.er_digraph(200, 0.02, 5)
+    e0 = oracle.tc_eps(e)
+    bits, st, x = ctx.tc_closure(e, eps=e0 / 2, path="fp64", rtilde=True)
+    assert st["eps_used"] == e0 / 2
+    xr = oracle.tc_rtilde_lu(e, e0 / 2)
+    assert np.abs(x - xr).max() <= 1e-10 * np.abs(xr).max()
+    assert np.array_equal(bits, oracle.tc_model(e))
+
+
+def test_device_and_host_memory_agree(ctx):
+    e = inputs.er_digraph(777, 0.004, 9)
+    bh, _ = ctx.tc_closure(e)
+    bd, _ = ctx.tc_closure(torch.from_numpy(e).cuda())
+    assert np.array_equal(bh, bd.cpu().numpy().view(np.uint64))
+    assert np.array_equal(bh, oracle.tc_model(e))
+
+
+def test_argument_errors(ctx):
+    e = inputs.er_digraph(50, 0.1, 1)
+    bad = e.copy()
+    bad[3, 4] = 2
+    for path in ("bool_fp8", "fp64"):
+        with pytest.raises(dl.DLError) as ei:
+            ctx.tc_closure(bad, path=path)
+        assert ei.value.status == dl.DL_EINVAL
+    with pytest.raises(dl.DLError) as ei:
+        ctx.tc_closure(e, eps=0.9)
+    assert ei.value.status == dl.DL_EINVAL
+    with pytest.raises(dl.DLError) as ei:
+        ctx.tc_closure(e, thr=0.1)
+    assert ei.value.status == dl.DL_EINVAL
+    with pytest.raises(dl.DLError) as ei:
+        ctx.tc_closure(e, path="bool_fp8", rtilde=True)
+    assert ei.value.status == dl.DL_EINVAL
+    bits, st = ctx.tc_closure(np.zeros((0, 0), dtype=np.uint8))
+    assert bits.shape == (0, 0)
+    # the context still works after errors
+    bits, _ = ctx.tc_closure(e)
+    assert np.array_equal(bits, oracle.tc_model(e))
+
+
+# --- same generation ------------------------------------------------------------------
+
+@pytest.mark.parametrize("n", [1, 2, 33, 100, 256, 257, 700])
+def test_sg_forest(ctx, n):
+    p = inputs.forest_dag(n, 7 + n, extra_prob=0.02)
+    bits, st = ctx.sg_least_model(p)
+    assert np.array_equal(bits, oracle.sg_model(p))
+
+
+@pytest.mark.parametrize("n,pe", [(50, 0.05), (200, 0.01), (300, 0.004)])
+def test_sg_general_digraph(ctx, n, pe):
+    p = inputs.er_digraph(n, pe, n, self_loops=True)
+    bits, st = ctx.sg_least_model(p)
+    assert np.array_equal(bits, oracle.sg_model(p))
+
+
+def test_sg_with_base_relation_and_degenerate(ctx):
+    n = 150
+    p = inputs.er_digraph(n, 0.02, 4)
+    b = inputs.er_digraph(n, 0.01, 5, self_loops=True)
+    bits, _ = ctx.sg_least_model(p, b)
+    assert np.array_equal(bits, oracle.sg_model(p, b))
+    z = np.zeros((n, n), dtype=np.uint8)
+    bits, st = ctx.sg_least_model(z)
+    assert np.array_equal(bits, oracle.pack(np.eye(n)))
+    tree = np.zeros((n, n), dtype=np.uint8)
+    tree[np.arange(1, n), (np.arange(1, n) - 1) // 2] = 1
+    bits, st = ctx.sg_least_model(tree)
+    assert np.array_equal(bits, oracle.sg_model(tree))
+    with pytest.raises(dl.DLError) as ei:
+        ctx.sg_least_model(p, path="fp64")
+    assert ei.value.status == dl.DL_ENOTIMPL
