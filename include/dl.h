@@ -191,6 +191,34 @@ DL_API dl_status dl_poll(dl_ctx *ctx, uint64_t ticket, int64_t timeout_us, dl_st
  * polls DL_ECANCELED), DL_EBUSY if it is already running or done. */
 DL_API dl_status dl_cancel(dl_ctx *ctx, uint64_t ticket);
 
+/* ---- closure without device allocation ------------------------------------------- */
+
+/* Largest n that dl_tc_closure_noalloc accepts. */
+#define DL_NOALLOC_MAX_N 2048
+
+/*
+ * Transitive closure (as dl_tc_closure with eps <= 0, thr = 0, DL_PATH_BOOL_FP8) for callers
+ * that cannot allocate device memory: it calls no cudaMalloc, cudaFree or other allocating
+ * routine and needs no context.  The paper has no counterpart; it exists for callers whose
+ * device memory is owned by someone else (another framework's pool, a host application
+ * that forbids library allocations) or that cannot afford the device synchronisation a
+ * cudaMalloc implies.
+ *
+ * E (n*n bytes, 0/1) and out_bits (n * ceil(n/64) words) are device pointers on the current
+ * device; stream is a cudaStream_t (NULL = the legacy default stream); *squarings (may be
+ * NULL) receives the number of tensor-core squarings.  n > DL_NOALLOC_MAX_N returns
+ * DL_EINVAL.  The call returns after its work on `stream` has finished.
+ *
+ * Its scratch is one fixed array (about 9 MiB) compiled into the library; every GPU that
+ * loads the library keeps it until the process exits.  The first call on each device looks
+ * up the array's device address (cudaGetSymbolAddress) with that device current: make that
+ * first call before any stream capture.  All calls on a device share the array and it keeps
+ * the previous call's contents (each call clears what it needs zeroed); calls whose work
+ * overlaps on the GPU race on it and must be serialised by the caller.
+ */
+DL_API dl_status dl_tc_closure_noalloc(int32_t n, const uint8_t *E, uint64_t *out_bits,
+                                       void *stream, int32_t *squarings);
+
 #ifdef __cplusplus
 }
 #endif

@@ -24,7 +24,9 @@ PATHS = {"auto": 0, "fp64": 1, "mixed": 2, "bool_fp8": 3, "fp8": 3}
 DL_MEM_HOST, DL_MEM_DEVICE = 0, 1
 
 EXPORTED = ["dl_create", "dl_destroy", "dl_last_error", "dl_set_stream", "dl_tc_closure",
-            "dl_sg_least_model", "dl_compose", "dl_tc_batch", "dl_submit", "dl_poll", "dl_cancel"]
+            "dl_sg_least_model", "dl_compose", "dl_tc_batch", "dl_submit", "dl_poll", "dl_cancel",
+            "dl_tc_closure_noalloc"]
+NOALLOC_MAX_N = 2048
 
 
 class DLError(RuntimeError):
@@ -91,6 +93,7 @@ def lib() -> ctypes.CDLL:
             L.dl_submit.argtypes = [vp, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_uint64)]
             L.dl_poll.argtypes = [vp, ctypes.c_uint64, i64, ctypes.POINTER(Stats)]
             L.dl_cancel.argtypes = [vp, ctypes.c_uint64]
+            L.dl_tc_closure_noalloc.argtypes = [i32, vp, vp, vp, ctypes.POINTER(i32)]
             for f in EXPORTED:
                 if f != "dl_last_error":
                     getattr(L, f).restype = ctypes.c_int
@@ -263,3 +266,20 @@ class Context:
 
     def cancel(self, ticket: int) -> int:
         return lib().dl_cancel(self._h, ctypes.c_uint64(ticket))
+
+
+def tc_closure_noalloc(E, stream=None):
+    """Closure of a square torch.uint8 CUDA tensor without any device allocation inside the
+    library (n <= NOALLOC_MAX_N); returns (bits as an int64 CUDA tensor, squarings).  The
+    output tensor is allocated here, by the caller's side (torch), not by the library."""
+    import torch
+    if not (_is_torch(E) and E.is_cuda):
+        raise ValueError("expected a CUDA tensor")
+    p, n, mem, keep = _square_u8(E)
+    bits = torch.zeros((n, words(n)), dtype=torch.int64, device=keep.device)
+    raw = getattr(stream, "cuda_stream", stream) if stream is not None else \
+        torch.cuda.current_stream(keep.device).cuda_stream
+    sq = ctypes.c_int32(0)
+    _check(lib().dl_tc_closure_noalloc(n, p, bits.data_ptr(), ctypes.c_void_p(raw),
+                                       ctypes.byref(sq)))
+    return bits, sq.value
