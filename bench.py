@@ -37,6 +37,22 @@ METRIC = "TC least-model TFLOP/s-equiv (N=8192) vs plain FP64 path; served p50/p
 UNIT = "TFLOP/s-equiv"
 
 
+# DRAM bytes per launch of the dominant kernel from the ncu capture summarised in
+# profiles/umma_gemm_fp8_n8192.md; only valid for the kernel source it was taken on.
+GEMM_TRAFFIC = {"sources": {"dl_umma.cu": "b03e74adf4e37b05", "dl_ptx.cuh": "b4fd45714c88d2fc"},
+                "bytes_per_launch": 404.2e6}
+
+
+def gemm_traffic():
+    import hashlib
+    csrc = os.path.join(ROOT, "paper_1608_00139_gb300", "csrc")
+    for f, h in GEMM_TRAFFIC["sources"].items():
+        with open(os.path.join(csrc, f), "rb") as fh:
+            if hashlib.sha256(fh.read()).hexdigest()[:16] != h:
+                return None  # kernel changed since the counters were taken
+    return GEMM_TRAFFIC["bytes_per_launch"]
+
+
 def flops_equiv(n: int) -> float:
     return (8.0 / 3.0) * float(n) ** 3
 
@@ -245,7 +261,7 @@ def main() -> None:
     achieved = (gemm_flops / (gemm_ms * 1e-3) / 1e12) if gemm_ms > 0 else 0.0
     roofline = {"bound": "tensor", "kernel": "umma_gemm_kernel<FP8,256,MN-major B,bool epilogue>",
                 "achieved": achieved, "peak": fp8_peak, "unit": "TFLOP/s",
-                "frac": achieved / fp8_peak, "traffic": None,
+                "frac": achieved / fp8_peak, "traffic": gemm_traffic(),
                 "peak_source": f"2 x bf16_tflops of {pk['source']} MEASURED_PEAKS (burst)",
                 "gemm_launches": gemm_n, "avg_launch_ms": gemm_ms / max(gemm_n, 1)}
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,

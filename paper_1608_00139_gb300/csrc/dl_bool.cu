@@ -114,11 +114,32 @@ __global__ void __launch_bounds__(256)
     const uint64_t *mrow = M + static_cast<int64_t>(row) * wp;
     bool viol = false;
     uint32_t cnt = 0;
+    // A row whose accumulator already holds all n columns cannot change any more: stop its
+    // scan (single-pass rows only).  Most rows of a closure with a giant component are full.
+    const bool single_pass = wp <= 32 * kWpl;
+    uint64_t full[kWpl];
+#pragma unroll
+    for (int q = 0; q < kWpl; ++q) {
+        const int64_t w = lane + 32 * q;
+        const int64_t lo = w * 64;
+        full[q] = (w >= wp || lo >= n) ? 0ull : (n - lo >= 64 ? ~0ull : ((1ull << (n - lo)) - 1ull));
+    }
     for (int64_t w0 = 0; w0 < wp; w0 += 32 * kWpl) {
         uint64_t acc[kWpl];
 #pragma unroll
         for (int t = 0; t < kWpl; ++t) acc[t] = 0;
-        for (int c0 = 0; c0 < n; c0 += 512) {
+        bool saturated = false;
+        if (single_pass && mode == 1) {  // the row itself may already be full
+            bool mine = true;
+#pragma unroll
+            for (int q = 0; q < kWpl; ++q) {
+                const int64_t w = lane + 32 * q;
+                if (w < wp) acc[q] = mrow[w];
+                mine &= acc[q] == full[q];
+            }
+            saturated = __all_sync(0xffffffffu, mine);
+        }
+        for (int c0 = 0; c0 < n && !saturated; c0 += 512) {
             // lane looks at bytes c0 + 16*lane .. +15
             uint32_t mask = 0;
             const int base = c0 + 16 * lane;
@@ -147,6 +168,16 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
                             for (int q = 0; q < kWpl; ++q)
                                 if (q == qk) acc[q] |= 1ull << (k & 63);
+                        }
+                    }
+                    if (single_pass) {
+                        bool mine = true;
+#pragma unroll
+                        for (int q = 0; q < kWpl; ++q) mine &= acc[q] == full[q];
+                        if (__all_sync(0xffffffffu, mine)) {
+                            saturated = true;
+                            m = 0;
+                            who = 0;
                         }
                     }
                 }
