@@ -193,7 +193,7 @@ def main() -> None:
     torch.cuda.set_device(local)
     if world > 1:
         tdist.init_process_group("nccl")
-    stream = torch.cuda.current_stream()
+    stream = torch.cuda.Stream()  # the library's kernels and the timing events share it
     ctx = dl.Context(local, stream=stream)
     gs = graphs(rank)
     dev = [torch.from_numpy(e).cuda() for e in gs]

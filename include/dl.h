@@ -97,6 +97,8 @@ typedef struct {
     double ms_gemm;          /* summed device time of those GEMM launches (CUDA events on the
                                 launching stream), ms */
     double gemm_flops;       /* 2*M*N*K summed over those GEMM launches (padded sizes) */
+    double ms_queue;         /* serving: dl_submit -> admission to the GPU (host clock), ms */
+    double ms_latency;       /* serving: dl_submit -> completion (host clock), ms */
 } dl_stats;
 
 /* Create a context on CUDA device `device` (cfg may be NULL for defaults).  Fails with

@@ -20,6 +20,9 @@ namespace dl {
 
 void set_error(const char *fmt, ...);
 
+struct BatchPlan;  // cached CUDA graph of the last dl_tc_batch call (dl_batch.cu)
+void batch_plan_release(BatchPlan *p);
+
 // Grow-only device buffers, one set per execution slot (a synchronous call or one serving
 // slot), so concurrent slots never share scratch memory.
 struct Workspace {
@@ -36,6 +39,7 @@ struct Workspace {
     static constexpr int kGemmEvents = 128;  // start/stop pairs of timed GEMM launches
     cudaEvent_t gev[kGemmEvents] = {};
     bool ready = false;
+    BatchPlan *batch_plan = nullptr;
 
     cudaError_t init();
     void release();

@@ -50,6 +50,7 @@ struct GemmProblem {  // CUtensorMap members carry the TMA descriptor alignment
     int32_t tiles_m, tiles_n, tile_start;
     int32_t a_row0, a_col0;  // A(0,0) at tensor coordinates (x = a_col0, y = a_row0)
     int32_t b_row0, b_col0;  // B: MN-major (x = n, y = k); K-major (x = k, y = n)
+    const int *gate;         // may be null; tiles of this problem are skipped while *gate != 0
     GemmEpilogue epi;
 };
 
@@ -70,6 +71,8 @@ cudaError_t gemm_launch(GemmKind kind, bool b_kmajor, int bn, GemmEpi epi,
                         const GemmProblem *d_probs, int nprob, int total_tiles, int grid,
                         int *d_status, uint64_t budget_ns, cudaStream_t stream);
 int gemm_tile_m();
+// Set the kernel's shared-memory attribute ahead of time (e.g. before a stream capture).
+cudaError_t gemm_prepare(GemmKind kind, bool b_kmajor, int bn, GemmEpi epi);
 
 // ---------------------------------------------------------------------------------------
 // Boolean / streaming kernels (dl_bool.cu)

@@ -604,15 +604,9 @@ dl_status solve_compose(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveA
     return DL_OK;
 }
 
-dl_status solve_tc_batch(dl_ctx *, Workspace &, cudaStream_t, int32_t, const int32_t *,
-                         const uint8_t *const *, dl_mem, uint64_t *const *, dl_stats *) {
-    set_error("dl_tc_batch is not available in this build");
-    return DL_ENOTIMPL;
-}
-
 size_t footprint_bytes(int kind, int32_t n) {
     const size_t np = static_cast<size_t>(round_up(std::max<int64_t>(n, 1), 256));
-    const size_t mats = kind == 0 ? 3 : 6;  // staged input + ping-pong (+ Q pair, T for SG)
+    const size_t mats = kind == 0 ? 3 : 7;  // staged inputs + operand buffers of the path
     return mats * np * np + 2 * np * (np / 8) + (1u << 20);
 }
 
@@ -634,6 +628,8 @@ cudaError_t Workspace::init() {
 }
 
 void Workspace::release() {
+    batch_plan_release(batch_plan);
+    batch_plan = nullptr;
     for (auto &kv : bufs)
         if (kv.second.p) cudaFree(kv.second.p);
     bufs.clear();

@@ -70,6 +70,12 @@ __device__ __forceinline__ const GemmProblem *find_problem(const GemmProblem *pr
     return probs + lo;
 }
 
+// A gated problem's tiles are skipped while its gate word is non-zero (finished batch
+// instances).  Gates only change between launches, so all roles agree.
+__device__ __forceinline__ bool gated_off(const GemmProblem *P) {
+    return P->gate != nullptr && *reinterpret_cast<const volatile int *>(P->gate) != 0;
+}
+
 __device__ __forceinline__ void epi_bool_chunk(const GemmEpilogue &e, int row, int col,
                                                const uint32_t (&v)[32], uint32_t &cnt) {
     uint32_t word = 0;
@@ -170,6 +176,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             bool ok = true;
             for (int tile = blockIdx.x; tile < total_tiles && ok; tile += gridDim.x) {
                 const GemmProblem *P = find_problem(probs, nprob, tile);
+                if (gated_off(P)) continue;
                 const int local = tile - P->tile_start;
                 const int mb = local % P->tiles_m, nb = local / P->tiles_m;
                 const int nkb = P->K / C::BK;
@@ -215,6 +222,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             bool ok = true;
             for (int tile = blockIdx.x; tile < total_tiles && ok; tile += gridDim.x) {
                 const GemmProblem *P = find_problem(probs, nprob, tile);
+                if (gated_off(P)) continue;
                 const int nkb = P->K / C::BK;
                 if (!mbar_wait_bounded(&acce[acc], acc_ph ^ 1u, budget_ns, status,
                                        ST_TIMEOUT_ACC_EMPTY)) {
@@ -263,6 +271,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         uint32_t acc_ph = 0;
         for (int tile = blockIdx.x; tile < total_tiles; tile += gridDim.x) {
             const GemmProblem *P = find_problem(probs, nprob, tile);
+            if (gated_off(P)) continue;
             const int local = tile - P->tile_start;
             const int mb = local % P->tiles_m, nb = local / P->tiles_m;
             if (!mbar_wait_bounded(&accf[acc], acc_ph, budget_ns, status, ST_TIMEOUT_ACC_FULL))
@@ -351,23 +360,41 @@ bool make_map(CUtensorMap *m, CUtensorMapDataType dt, int elem, const Operand &o
 }
 
 template <int KIND, int BN, bool BK_, int EPI>
-cudaError_t launch_t(const GemmProblem *d_probs, int nprob, int total_tiles, int grid, int *status,
-                     uint64_t budget, cudaStream_t s) {
+cudaError_t prepare_t() {
     using C = Cfg<KIND, BN>;
-    auto k = umma_gemm_kernel<KIND, BN, BK_, EPI>;
     static std::once_flag once;
     static cudaError_t attr_err = cudaSuccess;
     std::call_once(once, [&] {
-        attr_err = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
+        attr_err = cudaFuncSetAttribute(umma_gemm_kernel<KIND, BN, BK_, EPI>,
+                                        cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM);
     });
+    return attr_err;
+}
+
+template <int KIND, int BN, bool BK_, int EPI>
+cudaError_t launch_t(const GemmProblem *d_probs, int nprob, int total_tiles, int grid, int *status,
+                     uint64_t budget, cudaStream_t s) {
+    using C = Cfg<KIND, BN>;
+    const cudaError_t attr_err = prepare_t<KIND, BN, BK_, EPI>();
     if (attr_err != cudaSuccess) return attr_err;
-    k<<<grid, kThreads, C::SMEM, s>>>(d_probs, nprob, total_tiles, status, budget);
+    umma_gemm_kernel<KIND, BN, BK_, EPI><<<grid, kThreads, C::SMEM, s>>>(d_probs, nprob, total_tiles,
+                                                                         status, budget);
     return cudaGetLastError();
 }
 
 }  // namespace
 
 int gemm_tile_m() { return BM; }
+
+cudaError_t gemm_prepare(GemmKind kind, bool b_kmajor, int bn, GemmEpi epi) {
+    if (kind == KIND_F8 && epi == EPI_BOOL) {
+        if (bn == 256) return b_kmajor ? prepare_t<KIND_F8, 256, true, EPI_BOOL>() : prepare_t<KIND_F8, 256, false, EPI_BOOL>();
+        if (bn == 128) return b_kmajor ? prepare_t<KIND_F8, 128, true, EPI_BOOL>() : prepare_t<KIND_F8, 128, false, EPI_BOOL>();
+    }
+    if (kind == KIND_TF32 && epi == EPI_SUB_F32 && bn == 128 && !b_kmajor)
+        return prepare_t<KIND_TF32, 128, false, EPI_SUB_F32>();
+    return cudaErrorInvalidValue;
+}
 
 bool gemm_make_problem(GemmProblem *p, GemmKind kind, bool b_kmajor, int bn, int M, int N, int K,
                        const Operand &A, const Operand &B, const GemmEpilogue &epi,

@@ -53,7 +53,8 @@ class Stats(ctypes.Structure):
                 ("ms_solve", ctypes.c_double), ("ms_refine", ctypes.c_double),
                 ("ms_epilogue", ctypes.c_double), ("tflops_equiv", ctypes.c_double),
                 ("gpu_launches", ctypes.c_int32), ("gemm_launches", ctypes.c_int32),
-                ("ms_gemm", ctypes.c_double), ("gemm_flops", ctypes.c_double)]
+                ("ms_gemm", ctypes.c_double), ("gemm_flops", ctypes.c_double),
+                ("ms_queue", ctypes.c_double), ("ms_latency", ctypes.c_double)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -151,13 +152,15 @@ class Context:
         h = ctypes.c_void_p()
         _check(lib().dl_create(ctypes.byref(h), int(device), ctypes.byref(c)))
         self._h = h
+        self._inflight = {}  # ticket -> buffers the library may still read or write
         if stream is not None:
             self.set_stream(stream)
 
     def close(self) -> None:
         if getattr(self, "_h", None):
-            lib().dl_destroy(self._h)
+            lib().dl_destroy(self._h)  # waits for running requests
             self._h = None
+            self._inflight = {}
 
     def __enter__(self):
         return self
@@ -253,7 +256,9 @@ class Context:
         req = Request(int(kind), n, p, bptr, mem, PATHS[path], bp)
         t = ctypes.c_uint64(0)
         _check(lib().dl_submit(self._h, ctypes.byref(req), ctypes.byref(t)))
-        return t.value, {"bits": bits, "keep": (keep, keepb), "n": n}
+        handle = {"bits": bits, "keep": (keep, keepb), "n": n}
+        self._inflight[t.value] = handle
+        return t.value, handle
 
     def poll(self, ticket: int, timeout_us: int = 0):
         """(status, stats): status DL_OK when done, DL_EBUSY while running; raises on errors."""
@@ -261,6 +266,7 @@ class Context:
         rc = lib().dl_poll(self._h, ctypes.c_uint64(ticket), int(timeout_us), ctypes.byref(st))
         if rc == DL_EBUSY:
             return DL_EBUSY, None
+        self._inflight.pop(ticket, None)
         _check(rc)
         return DL_OK, st.as_dict()
 

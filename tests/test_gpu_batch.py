@@ -1,0 +1,70 @@
+"""GPU parity of dl_tc_batch: many closures of uneven size in one call (grouped tcgen05
+launches per squaring round, replayed from a captured CUDA graph).  Every model must equal
+the oracle's bits and the result of the same problem solved alone."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1608_00139_gb300 import dl, inputs
+
+pytestmark = pytest.mark.gpu
+
+
+def small_batch(count=40, seed0=500):
+    gs = []
+    for n, p, seed in inputs.batch_specs(count, seed0, n_lo=1, n_hi=700):
+        gs.append(inputs.er_digraph(n, p, seed))
+    gs[3] = np.zeros((0, 0), dtype=np.uint8)           # empty problem
+    chain = np.zeros((300, 300), dtype=np.uint8)       # long paths: many rounds
+    chain[np.arange(299), np.arange(1, 300)] = 1
+    gs[5] = chain
+    return gs
+
+
+def test_batch_host_memory_matches_oracle(ctx):
+    gs = small_batch()
+    outs, st = ctx.tc_batch(gs)
+    for e, b in zip(gs, outs):
+        assert np.array_equal(b, oracle.tc_model(e))
+    assert st["iters"] >= 9  # the 300-chain needs 2^t >= 299
+    assert st["model_ones"] == sum(int(np.unpackbits(oracle.tc_model(e).view(np.uint8)).sum())
+                                   for e in gs if e.shape[0])
+
+
+def test_batch_device_memory_repeat_and_alone(ctx):
+    gs = small_batch(24, 900)
+    dev = [torch.from_numpy(e).cuda() for e in gs]
+    outs1, _ = ctx.tc_batch(dev)
+    outs2, _ = ctx.tc_batch(dev)  # same buffers: the cached graph is relaunched
+    for e, d, a, b in zip(gs, dev, outs1, outs2):
+        ref = oracle.tc_model(e)
+        assert np.array_equal(a.cpu().numpy().view(np.uint64), ref)
+        assert torch.equal(a, b)
+        if e.shape[0]:
+            alone, _ = ctx.tc_closure(d)
+            assert torch.equal(alone, a)
+
+
+def test_batch_rejects_bad_input(ctx):
+    gs = small_batch(6, 1200)
+    bad = gs[1].copy()
+    bad[0, 0] = 7
+    gs[1] = bad
+    with pytest.raises(dl.DLError) as ei:
+        ctx.tc_batch(gs)
+    assert ei.value.status == dl.DL_EINVAL
+    outs, _ = ctx.tc_batch(small_batch(6, 1300))  # the context still works
+
+
+def test_batch_config_1024_uneven(ctx):
+    """The uneven batch workload: 1024 ER closures, N ~ U{32..2048}, mean degree ~ U[1, 8]."""
+    specs = inputs.batch_specs(1024, 1000)
+    gs = [torch.from_numpy(inputs.er_digraph(n, p, s)).cuda() for n, p, s in specs]
+    outs, st = ctx.tc_batch(gs)
+    oracle.set_threads(0)
+    rng = np.random.default_rng(0)
+    check = set(rng.choice(1024, size=128, replace=False).tolist()) | {0, 1023}
+    for k in sorted(check):
+        e = gs[k].cpu().numpy()
+        assert np.array_equal(outs[k].cpu().numpy().view(np.uint64), oracle.tc_model(e)), k
