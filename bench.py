@@ -250,11 +250,22 @@ def main() -> None:
     e2e_value = units * flops_equiv(N) / e2e_s / 1e12
 
     fp64 = None
+    mixed = None
     if not args.no_fp64 and rank == 0:
         _, st64 = ctx.tc_closure(dev[1], path="fp64")  # warm
         _, st64 = ctx.tc_closure(dev[1], path="fp64")
         fp64 = {"ms": st64["ms_total"], "tflops_equiv": st64["tflops_equiv"],
                 "graph": "p=1e-3 seed 3", "rechecked_rows": st64["rows_rechecked"]}
+        mixed = {}
+        for name, x in zip(("p=1e-4", "p=1e-3", "p=1e-2"), dev):
+            ctx.tc_closure(x, path="mixed")  # warm
+            _, stm = ctx.tc_closure(x, path="mixed")
+            mixed[name] = {"ms": stm["ms_total"], "tflops_equiv": stm["tflops_equiv"],
+                           "refine_steps": stm["iters"], "final_resid": stm["final_resid"],
+                           "ms_factor": stm["ms_factor"], "ms_solve": stm["ms_solve"],
+                           "ms_refine": stm["ms_refine"], "guard_flagged": stm["guard_flagged"],
+                           "rechecked_rows": stm["rows_rechecked"],
+                           "tf32_tflops": stm["gemm_flops"] / (stm["ms_total"] * 1e-3) / 1e12}
 
     pk = peaks()
     fp8_peak = 2.0 * pk["bf16"]  # FP8 dense = 2 x BF16 dense (nominal ratio)
@@ -274,6 +285,8 @@ def main() -> None:
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": len(gs) * N * N,
                     "d2h_bytes_per_step": len(gs) * N * ((N + 63) // 64) * 8},
             "gpu_launches": launches, "roofline": roofline, "clocks": clocks}
+    if mixed:
+        line["mixed_path"] = mixed
     if fp64:
         line["fp64_path"] = fp64
         line["speedup_vs_fp64"] = fp64["ms"] / (ms_step / len(gs))

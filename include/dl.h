@@ -71,7 +71,7 @@ typedef struct {
     void *stream;              /* cudaStream_t to run on; NULL = the context's own stream */
     size_t hbm_budget_bytes;   /* serving admission budget; 0 = 90% of free device memory */
     int32_t max_slots;         /* serving: requests in flight at once; 0 = 4 */
-    double refine_tol;         /* mixed path: stop when max|R| <= tol * max|eps E|; 0 = 1e-12 */
+    double refine_tol;         /* mixed path: stop when max|R| <= tol * max|eps E|; 0 = 1e-13 */
     int32_t refine_max_iters;  /* mixed path: refinement step limit; 0 = 30 */
     double guard_tau;          /* entries with |R~| <= tau are flagged for recheck; 0 = 1e-30 */
     double wait_timeout_s;     /* limit of every device-side wait; 0 = 2 s */

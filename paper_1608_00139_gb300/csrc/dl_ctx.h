@@ -96,6 +96,9 @@ dl_status solve_compose(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveA
 dl_status solve_tc_batch(dl_ctx *ctx, Workspace &ws, cudaStream_t s, int32_t count,
                          const int32_t *ns, const uint8_t *const *Es, dl_mem mem,
                          uint64_t *const *out_bits, dl_stats *st);
+// Mixed-precision solve (dl_mixed.cu): leaves X in the "mx_X64" buffer (np x np doubles).
+dl_status tc_mixed(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &a, dl_stats *st,
+                   const uint8_t *E, double eps, int *launches_io);
 // Device bytes a request of this kind and size needs (serving admission).
 size_t footprint_bytes(int kind, int32_t n);
 

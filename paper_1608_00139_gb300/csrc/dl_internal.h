@@ -23,10 +23,11 @@ enum : int {
 // tcgen05 GEMM (dl_umma.cu)
 // ---------------------------------------------------------------------------------------
 enum GemmKind : int { KIND_F8 = 0, KIND_TF32 = 1 };
-enum GemmEpi : int { EPI_BOOL = 0, EPI_SUB_F32 = 1 };
+enum GemmEpi : int { EPI_BOOL = 0, EPI_SUB_F32 = 1, EPI_STORE_F32 = 2 };
 
 // Boolean epilogue: v = [acc > 0] OR [add8 != 0]; writes e4m3 1.0/0.0 bytes, packed bits,
-// and adds the number of ones to *count.  SUB_F32 epilogue: c32 -= acc (in place).
+// and adds the number of ones to *count.  SUB_F32 epilogue: c32 -= acc (in place);
+// STORE_F32 epilogue: c32 = acc.
 struct GemmEpilogue {
     uint8_t *out8;            // may be null
     int64_t ld_out8;          // bytes per row

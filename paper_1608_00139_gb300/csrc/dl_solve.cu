@@ -397,6 +397,74 @@ dl_status tc_fp64(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &a
     return DL_OK;
 }
 
+dl_status tc_mixed_path(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &a, dl_stats *st) {
+    const int32_t n = a.n;
+    const int64_t np = round_up(std::max<int64_t>(n, 1), 256);
+    const int64_t wp = np / 64;
+    Timer tm{ws.ev, s};
+    int launches = 0;
+    tm.mark(0);
+    const uint8_t *E = nullptr;
+    dl_status rc = stage_input(ws, s, a.E, n, a.mem, "in0", &E);
+    if (rc) return rc;
+    auto *C0 = static_cast<uint8_t *>(ws.get("c0", np * np));
+    auto *mbits = static_cast<uint64_t *>(ws.get("bits1", np * wp * 8));
+    NEED(C0 && mbits);
+    CK(cudaMemsetAsync(ws.scal, 0, kScalars * sizeof(unsigned long long), s));
+    CK(cudaMemsetAsync(ws.status, 0, sizeof(int), s));
+    // validation and row sums (the e4m3 copy is not used by this path)
+    if ((rc = ingest(ctx, ws, s, E, n, np, C0, 0, SC_DMAX, SC_NNZ, SC_COUNT0, &launches))) return rc;
+    if ((rc = read_scalars(ws, s))) return rc;
+    if ((rc = check_status(ws, s))) return rc;
+    const unsigned long long dmax = host_scal(ws)[SC_DMAX];
+    double eps = 0;
+    if ((rc = choose_eps(a.eps, 1.0 / (1.0 + static_cast<double>(dmax)), "Lemma 1 (1/(1+||E||))", &eps)))
+        return rc;
+    dl_stats local{};
+    dl_stats *sx = st ? st : &local;
+    if ((rc = tc_mixed(ctx, ws, s, a, sx, E, eps, &launches))) return rc;
+    tm.mark(2);
+    const auto *X = static_cast<const double *>(ws.get("mx_X64", np * np * 8));
+    const double tau = ctx->cfg.guard_tau > 0 ? ctx->cfg.guard_tau : 1e-30;
+    CK(thresh_pack_f64(X, np, n, static_cast<int>(np), tau, mbits, wp, ws.scal + SC_GUARD, s));
+    ++launches;
+    int sweeps = 0;
+    unsigned long long corrected = 0;
+    for (;;) {
+        CK(cudaMemsetAsync(ws.scal + SC_VIOL, 0, 2 * sizeof(unsigned long long), s));
+        CK(bits_sweep(E, n, n, mbits, mbits, wp, 1, 0, ws.scal + SC_VIOL, ws.scal + SC_ONES, s));
+        ++launches;
+        ++sweeps;
+        if ((rc = read_scalars(ws, s))) return rc;
+        const unsigned long long v = host_scal(ws)[SC_VIOL];
+        if (v == 0) break;
+        corrected += v;
+        if (sweeps > n + 1) {
+            set_error("recheck did not converge");
+            return DL_ENOTCONV;
+        }
+    }
+    if ((rc = write_bits(s, mbits, wp, a.out_bits, n, a.mem))) return rc;
+    if (a.out_rtilde) {
+        CK(cudaMemcpy2DAsync(a.out_rtilde, static_cast<size_t>(n) * 8, X, np * 8, static_cast<size_t>(n) * 8, n,
+                             a.mem == DL_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+    }
+    tm.mark(3);
+    if ((rc = check_status(ws, s))) return rc;
+    if (st) {
+        st->path_used = DL_PATH_MIXED;
+        st->eps_used = eps;
+        st->guard_flagged = static_cast<int64_t>(host_scal(ws)[SC_GUARD]);
+        st->rows_rechecked = static_cast<int64_t>(corrected);
+        st->recheck_sweeps = sweeps;
+        st->model_ones = static_cast<int64_t>(host_scal(ws)[SC_ONES]);
+        st->ms_epilogue = tm.ms(2, 3);
+        st->ms_total = tm.ms(0, 3);
+        st->gpu_launches = launches;
+    }
+    return DL_OK;
+}
+
 }  // namespace
 
 dl_status solve_tc(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &a, dl_stats *st) {
@@ -418,8 +486,8 @@ dl_status solve_tc(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &
             rc = tc_fp64(ctx, ws, s, a, st);
             break;
         case DL_PATH_MIXED:
-            set_error("DL_PATH_MIXED is not available in this build");
-            return DL_ENOTIMPL;
+            rc = tc_mixed_path(ctx, ws, s, a, st);
+            break;
         default:
             set_error("unknown path %d", static_cast<int>(a.path));
             return DL_EINVAL;

@@ -6,7 +6,8 @@
 //     squaring steps of the transitive closure and the same-generation doubling steps.
 //     0/1 operands are exact in e4m3, products are 0/1 and FP32 sums of at most 2^24 ones are
 //     exact, so the epilogue's test acc > 0 is the exact boolean OR of ANDs;
-//   * TF32 rank-k updates C -= A B of the blocked LU of I - eps E (Proposition 1).
+//   * TF32 products of the blocked LU of I - eps E and its triangular solves (Proposition 1),
+//     C = A B^T or C -= A B^T with both operands K-major.
 //
 // Structure (one CTA per SM, persistent over output tiles of 128 x BN):
 //   warp 0      TMA producer: A tile (128 rows x 128 bytes of K, 128-byte swizzle) and the
@@ -107,6 +108,17 @@ __device__ __forceinline__ void epi_bool_chunk(const GemmEpilogue &e, int row, i
     }
     if (e.bits) e.bits[r * e.ld_bits32 + (c >> 5)] = word;
     cnt += __popc(word);
+}
+
+__device__ __forceinline__ void epi_store_chunk(const GemmEpilogue &e, int row, int col,
+                                                const uint32_t (&v)[32]) {
+    const int64_t r = static_cast<int64_t>(e.out_row0) + row;
+    const int64_t c = static_cast<int64_t>(e.out_col0) + col;
+    float4 *p = reinterpret_cast<float4 *>(e.c32 + r * e.ld_c32 + c);
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+        p[q] = make_float4(__uint_as_float(v[4 * q + 0]), __uint_as_float(v[4 * q + 1]),
+                           __uint_as_float(v[4 * q + 2]), __uint_as_float(v[4 * q + 3]));
 }
 
 __device__ __forceinline__ void epi_sub_chunk(const GemmEpilogue &e, int row, int col,
@@ -290,7 +302,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const int col = nb * BN + c * 32;
                 if (row_ok && col < P->N) {
                     if (EPI == EPI_BOOL) epi_bool_chunk(P->epi, row, col, v, cnt);
-                    else epi_sub_chunk(P->epi, row, col, v);
+                    else if (EPI == EPI_SUB_F32) epi_sub_chunk(P->epi, row, col, v);
+                    else epi_store_chunk(P->epi, row, col, v);
                 }
             }
             tc_fence_before();
@@ -391,8 +404,11 @@ cudaError_t gemm_prepare(GemmKind kind, bool b_kmajor, int bn, GemmEpi epi) {
         if (bn == 256) return b_kmajor ? prepare_t<KIND_F8, 256, true, EPI_BOOL>() : prepare_t<KIND_F8, 256, false, EPI_BOOL>();
         if (bn == 128) return b_kmajor ? prepare_t<KIND_F8, 128, true, EPI_BOOL>() : prepare_t<KIND_F8, 128, false, EPI_BOOL>();
     }
-    if (kind == KIND_TF32 && epi == EPI_SUB_F32 && bn == 128 && !b_kmajor)
-        return prepare_t<KIND_TF32, 128, false, EPI_SUB_F32>();
+    // TF32 runs with K-major operands only (both operands row-major with K contiguous)
+    if (kind == KIND_TF32 && epi == EPI_SUB_F32 && bn == 128 && b_kmajor)
+        return prepare_t<KIND_TF32, 128, true, EPI_SUB_F32>();
+    if (kind == KIND_TF32 && epi == EPI_STORE_F32 && bn == 128 && b_kmajor)
+        return prepare_t<KIND_TF32, 128, true, EPI_STORE_F32>();
     return cudaErrorInvalidValue;
 }
 
@@ -449,9 +465,12 @@ cudaError_t gemm_launch(GemmKind kind, bool b_kmajor, int bn, GemmEpi epi, const
                                                                        grid, d_status, budget_ns,
                                                                        stream);
     }
-    if (kind == KIND_TF32 && epi == EPI_SUB_F32 && bn == 128 && !b_kmajor)
-        return launch_t<KIND_TF32, 128, false, EPI_SUB_F32>(d_probs, nprob, total_tiles, grid,
-                                                             d_status, budget_ns, stream);
+    if (kind == KIND_TF32 && epi == EPI_SUB_F32 && bn == 128 && b_kmajor)
+        return launch_t<KIND_TF32, 128, true, EPI_SUB_F32>(d_probs, nprob, total_tiles, grid,
+                                                            d_status, budget_ns, stream);
+    if (kind == KIND_TF32 && epi == EPI_STORE_F32 && bn == 128 && b_kmajor)
+        return launch_t<KIND_TF32, 128, true, EPI_STORE_F32>(d_probs, nprob, total_tiles, grid,
+                                                              d_status, budget_ns, stream);
     return cudaErrorInvalidValue;
 }
 

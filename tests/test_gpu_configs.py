@@ -58,3 +58,17 @@ def test_config_sg4096(ctx):
     p = inputs.forest_dag(4096, 5)
     bits, st = ctx.sg_least_model(p)
     assert np.array_equal(bits, oracle.sg_model(p))
+
+
+@pytest.mark.parametrize("p", [p for p, _ in BIG])
+def test_config_er8192_mixed(ctx, big_graphs, big_models, p):
+    """TF32 tensor-core LU + FP64 refinement at N = 8192: every model bit, and sampled
+    columns of R~ against the Lemma-1 series within 1e-10 of max |R~|."""
+    e = big_graphs[p]
+    bits, st, x = ctx.tc_closure(e, path="mixed", rtilde=True)
+    assert np.array_equal(bits, big_models[p])
+    eps = st["eps_used"]
+    scale = np.abs(x).max()
+    for j in (0, 4095, 8191):
+        col = oracle.tc_rtilde_col(e, eps, j)
+        assert np.abs(x[:, j] - col).max() <= 1e-10 * scale

@@ -55,10 +55,14 @@ def test_worked_example_all_paths(ctx):
     exact = np.array([[1, 4, 2, 0], [2, 1, 4, 0], [4, 2, 1, 0], [4, 2, 1, 0]]) / 7.0
     assert np.max(np.abs(x - exact)) < 1e-14
     assert np.array_equal(np.floor(x * 1e4 + 1e-9) / 1e4, g["Rtilde_printed"])
+    bm, stm, xm = ctx.tc_closure(e, path="mixed", rtilde=True)
+    assert np.array_equal(bm, want)
+    assert np.max(np.abs(xm - exact)) < 1e-10
+    assert np.array_equal(np.floor(xm * 1e4 + 1e-9) / 1e4, g["Rtilde_printed"])
 
 
 @pytest.mark.parametrize("n", EDGE_SIZES)
-@pytest.mark.parametrize("path", ["bool_fp8", "fp64"])
+@pytest.mark.parametrize("path", ["bool_fp8", "fp64", "mixed"])
 def test_closure_tile_edges(ctx, n, path):
     e = inputs.er_digraph(n, min(0.5, 3.0 / n), 100 + n)
     bits, st = ctx.tc_closure(e, path=path)
@@ -87,9 +91,23 @@ def test_closure_degenerate_graphs(ctx, kind):
     elif kind == "two_chains":
         e[np.arange(0, n - 2, 2), np.arange(2, n, 2)] = 1
     ref = oracle.tc_model(e)
-    for path in ("bool_fp8", "fp64"):
+    for path in ("bool_fp8", "fp64", "mixed"):
         bits, st = ctx.tc_closure(e, path=path)
         assert np.array_equal(bits, ref), path
+
+
+@pytest.mark.parametrize("n", [64, 300])
+def test_mixed_dense_complete_digraph_closed_form(ctx, n):
+    """E = ones - I: R~_ii = (n-1)/(n+1), R~_ij = n/(n+1).  Dense rows put the FP64 residual
+    at its rounding floor (about n u max|X|); the stated bound is kappa_inf(A) * resid."""
+    e = (1 - np.eye(n)).astype(np.uint8)
+    bits, st, x = ctx.tc_closure(e, path="mixed", rtilde=True)
+    want = np.full((n, n), n / (n + 1.0))
+    np.fill_diagonal(want, (n - 1) / (n + 1.0))
+    kappa = 2.0 * n  # kappa_inf(I - eps E) <= (1 + eps ||E||) / eps
+    assert np.abs(x - want).max() <= max(1e-10, 4 * kappa * st["final_resid"])
+    assert np.abs(x - want).max() <= 1e-9
+    assert np.array_equal(bits, oracle.pack(np.ones((n, n))))
 
 
 def test_chain_needs_log_squarings(ctx):
@@ -101,13 +119,15 @@ def test_chain_needs_log_squarings(ctx):
     assert st["iters"] == 10  # paths up to 999 need 2^t >= 999
 
 
-def test_fp64_path_underflow_is_repaired_by_recheck(ctx):
-    """A chain of 1100 constants: eps = 1/2 and eps^d underflows FP64 for d > 1074, so the
-    threshold misses facts; the exact recheck must restore them (Lemma 2 footnote)."""
+@pytest.mark.parametrize("path", ["fp64", "mixed"])
+def test_underflow_is_repaired_by_recheck(ctx, path):
+    """A chain of 1100 constants: eps = 1/2 and eps^d underflows FP64 for d > 1074 (FP32 /
+    TF32 far earlier), so the threshold misses facts; the exact recheck must restore them
+    (Lemma 2 footnote: reachable entries are >= eps^d, which can be below the format's range)."""
     n = 1100
     e = np.zeros((n, n), dtype=np.uint8)
     e[np.arange(n - 1), np.arange(1, n)] = 1
-    bits, st = ctx.tc_closure(e, path="fp64")
+    bits, st = ctx.tc_closure(e, path=path)
     assert np.array_equal(bits, oracle.tc_model(e))
     assert st["rows_rechecked"] > 0
 
@@ -122,6 +142,19 @@ def test_fp64_rtilde_matches_oracle(ctx, n, p, seed):
     assert err <= 1e-10
     assert np.array_equal(bits, oracle.tc_model(e))
     assert np.array_equal(oracle.pack(x > 0), bits)
+
+
+@pytest.mark.parametrize("n,p,seed", [(256, 0.02, 1), (300, 0.05, 2), (640, 0.01, 3), (513, 0.002, 4)])
+def test_mixed_rtilde_matches_oracle(ctx, n, p, seed):
+    """TF32 LU + FP64 refinement: R~ within 1e-10 (max-abs error / max-abs value)."""
+    e = inputs.er_digraph(n, p, seed)
+    bits, st, x = ctx.tc_closure(e, path="mixed", rtilde=True)
+    xr = oracle.tc_rtilde_lu(e, st["eps_used"])
+    assert np.abs(x - xr).max() <= 1e-10 * np.abs(xr).max()
+    assert np.array_equal(bits, oracle.tc_model(e))
+    assert st["path_used"] == dl.PATHS["mixed"]
+    assert st["final_resid"] <= 1e-13
+    assert st["iters"] >= 1
 
 
 def test_user_eps(ctx):
