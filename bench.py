@@ -128,6 +128,95 @@ class ClockSampler:
                 "samples": len(rows)}
 
 
+def bench_sg(ctx, torch, reps: int = 10) -> dict:
+    """Same generation on the N = 4096 forest + DAG edges (seed 5), device-resident input."""
+    from paper_1608_00139_gb300 import inputs
+    p = torch.from_numpy(inputs.forest_dag(4096, 5)).cuda()
+    torch.cuda.synchronize()
+    ctx.sg_least_model(p)
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        _, st = ctx.sg_least_model(p)
+    ms = (time.perf_counter() - t0) / reps * 1e3
+    return {"workload": "SG forest+DAG N=4096 seed 5", "ms": ms, "doubling_steps": st["iters"],
+            "gemm_tflops": st["gemm_flops"] / (st["ms_gemm"] * 1e-3) / 1e12 if st["ms_gemm"] else None,
+            "device_ms": st["ms_total"]}
+
+
+def bench_batch(ctx, torch, reps: int = 3) -> dict:
+    """1024 uneven ER closures (N ~ U{32..2048}, mean degree ~ U[1,8], seeds 1000+k)."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    from paper_1608_00139_gb300 import inputs
+    specs = inputs.batch_specs(1024, 1000)
+    with ThreadPoolExecutor(max_workers=os.cpu_count() or 4) as ex:
+        host = list(ex.map(lambda s: inputs.er_digraph(s[0], s[1], s[2]), specs))
+    dev = [torch.from_numpy(e).cuda() for e in host]
+    torch.cuda.synchronize()
+    ctx.tc_batch(dev)  # captures the graph
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        _, st = ctx.tc_batch(dev)
+    ms = (time.perf_counter() - t0) / reps * 1e3
+    equiv = sum(flops_equiv(n) for n, _, _ in specs)
+    return {"workload": "1024 ER closures, N~U{32..2048}, degree~U[1,8]", "ms": ms,
+            "tflops_equiv": equiv / (ms * 1e-3) / 1e12, "rounds": st["iters"],
+            "tensor_tflops": st["gemm_flops"] / (ms * 1e-3) / 1e12, "device_ms": st["ms_total"]}
+
+
+def bench_serving(dl, torch, device: int, seconds: float) -> dict:
+    """Poisson stream (200 req/s), 80% closure / 20% same generation, PA-DAG inputs with N
+    log-uniform in [512, 16384] (a pool of 32 resident graphs, seed 6)."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    from paper_1608_00139_gb300 import inputs
+    sizes = np.unique(np.round(np.exp(np.linspace(np.log(512), np.log(16384), 32))).astype(int))
+    with ThreadPoolExecutor(max_workers=os.cpu_count() or 4) as ex:
+        pool_h = list(ex.map(lambda n: inputs.pa_dag(int(n), 6_000 + int(n)), sizes))
+    pool = [torch.from_numpy(e).cuda() for e in pool_h]
+    torch.cuda.synchronize()
+    times, kinds, ns, _ = inputs.poisson_stream(200.0, seconds, 6)
+    pick = np.searchsorted(sizes, ns).clip(0, len(sizes) - 1)
+    lat, queue, errors = [], [], 0
+    with dl.Context(device, max_slots=4) as c:
+        for k in (0, 1):  # warm both kernels outside the stream
+            t, _ = c.submit(k, pool[0])
+            c.poll(t, -1)
+        outstanding = []
+        t0 = time.perf_counter()
+        for t_arr, kind, j in zip(times, kinds, pick):
+            while True:
+                now = time.perf_counter() - t0
+                if now >= t_arr:
+                    break
+                keep = []
+                for tk in outstanding:
+                    rc, st = c.poll(tk, 0)
+                    if rc == dl.DL_OK:
+                        lat.append(st["ms_latency"])
+                        queue.append(st["ms_queue"])
+                    else:
+                        keep.append(tk)
+                outstanding = keep
+                time.sleep(min(0.0005, max(0.0, t_arr - now)))
+            tk, _ = c.submit(int(kind), pool[j])
+            outstanding.append(tk)
+        for tk in outstanding:
+            try:
+                rc, st = c.poll(tk, -1)
+                lat.append(st["ms_latency"])
+                queue.append(st["ms_queue"])
+            except dl.DLError:
+                errors += 1
+        wall = time.perf_counter() - t0
+    lat_a = np.array(lat)
+    return {"workload": f"Poisson 200 req/s for {seconds:g} s, 80% TC / 20% SG, PA DAGs N in [512,16384]",
+            "requests": int(len(times)), "completed": int(len(lat)), "errors": errors,
+            "p50_ms": float(np.percentile(lat_a, 50)), "p99_ms": float(np.percentile(lat_a, 99)),
+            "p50_queue_ms": float(np.percentile(np.array(queue), 50)),
+            "solves_per_s": len(lat) / wall, "slots": 4}
+
+
 def cpu_baseline(gs, budget_s: float = 30.0) -> dict:
     import oracle
     threads = oracle.set_threads(os.cpu_count() or 1)
@@ -179,6 +268,10 @@ def main() -> None:
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the same-generation, batch and serving measurements")
+    ap.add_argument("--serve-seconds", type=float, default=10.0,
+                    help="length of the serving stream (the full workload is 60 s)")
     args = ap.parse_args()
     rank, world, local = dist_env()
     if args.impl == "reference":
@@ -285,6 +378,10 @@ def main() -> None:
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": len(gs) * N * N,
                     "d2h_bytes_per_step": len(gs) * N * ((N + 63) // 64) * 8},
             "gpu_launches": launches, "roofline": roofline, "clocks": clocks}
+    if not args.no_extra and rank == 0:
+        line["same_generation"] = bench_sg(ctx, torch)
+        line["batch"] = bench_batch(ctx, torch)
+        line["serving"] = bench_serving(dl, torch, local, args.serve_seconds)
     if mixed:
         line["mixed_path"] = mixed
     if fp64:

@@ -126,6 +126,8 @@ def _square_u8(x):
             if x.dtype != torch.uint8 or x.dim() != 2 or x.shape[0] != x.shape[1]:
                 raise ValueError("expected a square torch.uint8 CUDA tensor")
             x = x.contiguous()
+            # the library reads on its own stream: finish torch's pending writes first
+            torch.cuda.current_stream(x.device).synchronize()
             return x.data_ptr(), int(x.shape[0]), DL_MEM_DEVICE, x
     a = np.ascontiguousarray(x, dtype=np.uint8)
     if a.ndim != 2 or a.shape[0] != a.shape[1]:
@@ -136,7 +138,8 @@ def _square_u8(x):
 def _alloc_bits(n: int, mem: int, like=None):
     if mem == DL_MEM_DEVICE:
         import torch
-        t = torch.zeros((n, words(n)), dtype=torch.int64, device=like.device)
+        # no fill kernel: the library writes every word, on its own stream
+        t = torch.empty((n, words(n)), dtype=torch.int64, device=like.device)
         return t, t.data_ptr()
     a = np.zeros((n, words(n)), dtype=np.uint64)
     return a, a.ctypes.data
@@ -187,7 +190,7 @@ class Context:
         if rtilde:
             if mem == DL_MEM_DEVICE:
                 import torch
-                rt = torch.zeros((n, n), dtype=torch.float64, device=keep.device)
+                rt = torch.empty((n, n), dtype=torch.float64, device=keep.device)
                 rp = rt.data_ptr()
             else:
                 rt = np.zeros((n, n), dtype=np.float64)

@@ -25,6 +25,8 @@ Workloads (the paper's experiments, Sec. 6):
 from __future__ import annotations
 
 import math
+import os
+from concurrent.futures import ThreadPoolExecutor
 
 import numpy as np
 
@@ -89,11 +91,22 @@ def er_digraph(n: int, p: float, seed: int, self_loops: bool = False,
         return e
     key = stream_key(seed, STREAM_ER)
     cols = np.arange(n, dtype=np.uint64)
-    for r0 in range(0, n, rows_per_chunk):
+    # u < p with u = (draw >> 11) * 2^-53  <=>  (draw >> 11) < ceil(p * 2^53)  (p * 2^53 is exact)
+    thr = np.uint64(min(int(np.ceil(p * 2.0 ** 53)), 1 << 53))
+
+    def fill(r0: int) -> None:
         r1 = min(n, r0 + rows_per_chunk)
         rows = np.arange(r0, r1, dtype=np.uint64)[:, None]
-        u = uniforms(key, rows * np.uint64(n) + cols[None, :])
-        e[r0:r1] = (u < p)
+        d = draws(key, rows * np.uint64(n) + cols[None, :])
+        e[r0:r1] = (d >> np.uint64(11)) < thr
+
+    starts = range(0, n, rows_per_chunk)
+    if n * n >= (1 << 22) and len(starts) > 1:  # numpy releases the GIL: chunks in threads
+        with ThreadPoolExecutor(max_workers=min(len(starts), os.cpu_count() or 1)) as ex:
+            list(ex.map(fill, starts))
+    else:
+        for r0 in starts:
+            fill(r0)
     if not self_loops:
         np.fill_diagonal(e, 0)
     return e
@@ -185,11 +198,22 @@ def pa_dag(n: int, seed: int, zipf_a: float = 2.1, mean_deg: float = 5.0) -> np.
     cdf = np.cumsum(ks ** (-zipf_a))
     cdf /= cdf[-1]
     key = stream_key(seed, STREAM_PA)
-    counter = 0
+    block = 1 << 16
+    buf: list[float] = []
+    pos = [0, 0]  # next counter, index into buf
+
+    def nxt() -> float:  # the draws of the stream in counter order, fetched in blocks
+        if pos[1] >= len(buf):
+            buf[:] = uniforms(key, np.arange(pos[0], pos[0] + block, dtype=np.uint64)).tolist()
+            pos[0] += block
+            pos[1] = 0
+        v = buf[pos[1]]
+        pos[1] += 1
+        return v
+
     urn = [0]  # node j appears in_degree(j) + 1 times
     for i in range(1, n):
-        u = float(uniforms(key, np.array([counter]))[0])
-        counter += 1
+        u = nxt()
         k = int(np.searchsorted(cdf, u, side="right")) + 1
         k = min(k, kmax, i)
         if k == i:
@@ -197,9 +221,8 @@ def pa_dag(n: int, seed: int, zipf_a: float = 2.1, mean_deg: float = 5.0) -> np.
         else:
             chosen_set: set[int] = set()
             while len(chosen_set) < k:
-                u = float(uniforms(key, np.array([counter]))[0])
-                counter += 1
-                chosen_set.add(urn[min(int(u * len(urn)), len(urn) - 1)])
+                m = len(urn)
+                chosen_set.add(urn[min(int(nxt() * m), m - 1)])
             chosen = sorted(chosen_set)
         e[i, chosen] = 1
         urn.extend(chosen)
