@@ -266,6 +266,8 @@ def main() -> None:
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--path", default="auto", choices=["auto", "bool_fp8"],
+                    help="closure path of the headline (auto: squarings + sweeps by cost)")
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-extra", action="store_true",
@@ -292,10 +294,10 @@ def main() -> None:
     dev = [torch.from_numpy(e).cuda() for e in gs]
     torch.cuda.synchronize()
 
-    def step(inputs):
+    def step(inputs, path=args.path):
         out = []
         for x in inputs:
-            out.append(ctx.tc_closure(x, path="bool_fp8"))
+            out.append(ctx.tc_closure(x, path=path))
         return out
 
     for _ in range(max(args.warmup, 3)):
@@ -329,7 +331,7 @@ def main() -> None:
         t0 = time.perf_counter()
         for _ in range(e2e_steps):
             for e in gs:
-                ctx.tc_closure(e, path="bool_fp8")
+                ctx.tc_closure(e, path=args.path)
         torch.cuda.synchronize()
         e2e_s = (time.perf_counter() - t0) / e2e_steps
     clocks = clk.summary()
@@ -341,6 +343,30 @@ def main() -> None:
     units = world * len(gs)
     value = units * flops_equiv(N) / (ms_step * 1e-3) / 1e12
     e2e_value = units * flops_equiv(N) / e2e_s / 1e12
+    gemm_share = gemm_ms / ms_total if ms_total > 0 else 0.0
+
+    # the squarings-only FP8 path on the same graphs, for comparison and for the GEMM roofline
+    pure = None
+    if rank == 0 and args.path != "bool_fp8":
+        step(dev, "bool_fp8")
+        k2 = max(10, args.steps // 5)
+        p_ms = p_fl = 0.0
+        p_n = 0
+        p_sq = []
+        t0 = time.perf_counter()
+        for _ in range(k2):
+            for _, st in step(dev, "bool_fp8"):
+                p_ms += st["ms_gemm"]
+                p_fl += st["gemm_flops"]
+                p_n += st["gemm_launches"]
+                p_sq.append(st["iters"])
+        ms2 = (time.perf_counter() - t0) / k2 * 1e3
+        pure = {"path": "bool_fp8 (tensor-core squarings only)", "ms_per_step": ms2,
+                "value": len(gs) * flops_equiv(N) / (ms2 * 1e-3) / 1e12,
+                "squarings_per_model": sorted(set(p_sq)),
+                "gemm_share_of_step": p_ms / (ms2 * k2)}
+        if gemm_n == 0 or p_n > 0:
+            gemm_ms, gemm_flops, gemm_n = p_ms, p_fl, p_n
 
     fp64 = None
     mixed = None
@@ -364,6 +390,7 @@ def main() -> None:
     fp8_peak = 2.0 * pk["bf16"]  # FP8 dense = 2 x BF16 dense (nominal ratio)
     achieved = (gemm_flops / (gemm_ms * 1e-3) / 1e12) if gemm_ms > 0 else 0.0
     roofline = {"bound": "tensor", "kernel": "umma_gemm_kernel<FP8,256,MN-major B,bool epilogue>",
+                "measured_in": "squarings-only FP8 run" if pure else "headline run",
                 "achieved": achieved, "peak": fp8_peak, "unit": "TFLOP/s",
                 "frac": achieved / fp8_peak, "traffic": gemm_traffic(),
                 "peak_source": f"2 x bf16_tflops of {pk['source']} MEASURED_PEAKS (burst)",
@@ -373,8 +400,9 @@ def main() -> None:
             "scaling": "weak", "vs_baseline": None, "dtype": "e4m3 (0/1, FP32 accumulate)",
             "data": "synthetic (seeded Erdos-Renyi, i != j)",
             "config": {"workload": "TC ER N=8192 x p in {1e-4,1e-3,1e-2}, seeds 2/3/4 (+1000*rank)",
-                       "path": "bool_fp8", "l2": "inputs 3 x 64 MiB > L2, cycled each step",
-                       "squarings_per_model": sorted(set(squarings))},
+                       "path": args.path, "l2": "inputs 3 x 64 MiB > L2, cycled each step",
+                       "squarings_per_model": sorted(set(squarings)),
+                       "gemm_share_of_step": gemm_share},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": len(gs) * N * N,
                     "d2h_bytes_per_step": len(gs) * N * ((N + 63) // 64) * 8},
             "gpu_launches": launches, "roofline": roofline, "clocks": clocks}
@@ -382,6 +410,8 @@ def main() -> None:
         line["same_generation"] = bench_sg(ctx, torch)
         line["batch"] = bench_batch(ctx, torch)
         line["serving"] = bench_serving(dl, torch, local, args.serve_seconds)
+    if pure:
+        line["bool_fp8_path"] = pure
     if mixed:
         line["mixed_path"] = mixed
     if fp64:

@@ -59,7 +59,8 @@ typedef enum {
 
 /* Which numerical route computes the model (all give the same, exact model). */
 typedef enum {
-    DL_PATH_AUTO = 0,      /* the library chooses (currently DL_PATH_BOOL_FP8) */
+    DL_PATH_AUTO = 0,      /* FP8 tensor-core squarings and bit sweeps (the Iteration step,
+                              Sec. 6.1), whichever is cheaper for the graph */
     DL_PATH_FP64 = 1,      /* plain FP64 inverse of I - eps E (Prop. 1), threshold > 0 */
     DL_PATH_MIXED = 2,     /* TF32 tensor-core LU + FP64 iterative refinement + guard */
     DL_PATH_BOOL_FP8 = 3   /* boolean repeated squaring on FP8 e4m3 tensor cores */
@@ -128,7 +129,7 @@ DL_API dl_status dl_set_stream(dl_ctx *ctx, void *stream);
  * thr must be 0 (the threshold "> 0" of Theorem 1); other values return DL_EINVAL.
  * out_rtilde (optional, n*n doubles, NULL allowed): the real least solution
  * R~ = (I - eps E)^-1 eps E (Prop. 1); only the FP64 and mixed paths produce it (with
- * DL_PATH_BOOL_FP8 or AUTO a non-NULL out_rtilde returns DL_EINVAL).
+ * DL_PATH_BOOL_FP8 or DL_PATH_AUTO a non-NULL out_rtilde returns DL_EINVAL).
  * stats (optional): filled on DL_OK.
  */
 DL_API dl_status dl_tc_closure(dl_ctx *ctx, int32_t n, const uint8_t *E, dl_mem mem, double eps,
@@ -192,6 +193,16 @@ DL_API dl_status dl_poll(dl_ctx *ctx, uint64_t ticket, int64_t timeout_us, dl_st
 /* Cancel a request that has not been admitted yet: DL_OK if cancelled (its ticket then
  * polls DL_ECANCELED), DL_EBUSY if it is already running or done. */
 DL_API dl_status dl_cancel(dl_ctx *ctx, uint64_t ticket);
+
+/*
+ * Self-test of the device-side failure detection: launches one CTA that waits, through the
+ * same bounded mbarrier wait every tcgen05 kernel of the library uses, on a barrier that no
+ * thread ever arrives at.  The wait gives up after `seconds` (0 < seconds <= 10), the kernel
+ * records the expiry in the context's status word and returns, and the call reports
+ * DL_ETIMEOUT; the context stays usable.  Anything else (DL_OK, a hang) means the detection
+ * is broken.  The paper has no counterpart.
+ */
+DL_API dl_status dl_selftest_wait_timeout(dl_ctx *ctx, double seconds);
 
 /* ---- closure without device allocation ------------------------------------------- */
 

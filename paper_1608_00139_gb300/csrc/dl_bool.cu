@@ -59,7 +59,330 @@ __global__ void __launch_bounds__(256)
     }
 }
 
+// ---- edge-parallel sweeps on the CSR of E -------------------------------------------------
+// Work unit = (row i, up to kUnit consecutive successors of i); unit_off[i] = first unit of row i.
+// The OR over a row's successors is split across units and combined with 64-bit atomicOr,
+// so rows with thousands of successors (heavy-tailed degrees) do not serialise a sweep.
+constexpr int kUnit = 64;
+
+__global__ void unit_count_kernel(const int *__restrict__ ptr, int n, int *cnt) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) cnt[i] = (ptr[i + 1] - ptr[i] + kUnit - 1) / kUnit;
+}
+
+__device__ __forceinline__ int unit_row(const int *unit_off, int n, int u) {
+    int lo = 0, hi = n - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (unit_off[mid] <= u) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// OR of the successors' rows of one unit into dst row i (atomically).  with_self: also set
+// the successors' own bits (the facts E[i][k]).  skip_full: skip the unit if dst row i is
+// already full (nothing can change).  Returns (warp-uniform) whether any word of dst changed.
+__device__ __forceinline__ bool or_unit(const int *__restrict__ col, int q0, int q1, int n, int i,
+                                        const uint64_t *M, uint64_t *dst, int64_t wp, bool with_self,
+                                        bool skip_full, int lane) {
+    const bool single = wp <= 32 * kSweepWpl;
+    uint64_t *drow = dst + static_cast<int64_t>(i) * wp;
+    bool changed = false;
+    for (int64_t w0 = 0; w0 < wp; w0 += 32 * kSweepWpl) {
+        uint64_t acc[kSweepWpl], full[kSweepWpl], have[kSweepWpl];
+        bool mine_full = true;
+#pragma unroll
+        for (int q = 0; q < kSweepWpl; ++q) {
+            acc[q] = 0;
+            const int64_t w = w0 + lane + 32 * q;
+            const int64_t lo = w * 64;
+            full[q] = (w >= wp || lo >= n) ? 0ull : (n - lo >= 64 ? ~0ull : ((1ull << (n - lo)) - 1ull));
+            have[q] = (skip_full && single && w < wp) ? drow[w] : 0ull;  // snapshot of dst row i
+            mine_full &= have[q] == full[q];
+        }
+        if (skip_full && single && __all_sync(0xffffffffu, mine_full)) return false;
+        for (int qq = q0; qq < q1; ++qq) {
+            const int k = col[qq];
+            const uint64_t *mk = M + static_cast<int64_t>(k) * wp;
+#pragma unroll
+            for (int q = 0; q < kSweepWpl; ++q) {
+                const int64_t w = w0 + lane + 32 * q;
+                if (w < wp) acc[q] |= mk[w];
+            }
+            if (with_self) {
+                const int64_t rel = (k >> 6) - w0;
+                if (rel >= 0 && rel < 32 * kSweepWpl && (rel & 31) == lane) {
+                    const int qk = static_cast<int>(rel >> 5);
+#pragma unroll
+                    for (int q = 0; q < kSweepWpl; ++q)
+                        if (q == qk) acc[q] |= 1ull << (k & 63);
+                }
+            }
+            if (skip_full && single) {  // the row is covered: later successors add nothing
+                bool mine = true;
+#pragma unroll
+                for (int q = 0; q < kSweepWpl; ++q) mine &= (have[q] | acc[q]) == full[q];
+                if (__all_sync(0xffffffffu, mine)) break;
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < kSweepWpl; ++q) {
+            const int64_t w = w0 + lane + 32 * q;
+            if (w >= wp || acc[q] == 0ull) continue;
+            if ((drow[w] | acc[q]) == drow[w]) continue;  // nothing new for this word
+            const unsigned long long old =
+                atomicOr(reinterpret_cast<unsigned long long *>(drow + w), static_cast<unsigned long long>(acc[q]));
+            if ((old | acc[q]) != old) changed = true;
+        }
+    }
+    return __any_sync(0xffffffffu, changed);
+}
+
+// Row-direct variants for graphs whose rows all fit one unit (max out-degree <= kUnit): one
+// warp per row, no unit search, plain stores (the warp is the row's only writer).
+// mode 1 (in place): M_i |= E_i | OR_{k in succ(i)} M_k; counts changed rows.
+__global__ void __launch_bounds__(256)
+    sweep_rows_step_kernel(const int *__restrict__ ptr, const int *__restrict__ col, int n, uint64_t *M, int64_t wp,
+                           unsigned long long *changed_rows) {
+    const int lane = threadIdx.x & 31;
+    const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (i >= n || ptr[i + 1] == ptr[i]) return;
+    const bool single = wp <= 32 * kSweepWpl;
+    uint64_t *mrow = M + static_cast<int64_t>(i) * wp;
+    bool changed = false;
+    for (int64_t w0 = 0; w0 < wp; w0 += 32 * kSweepWpl) {
+        uint64_t acc[kSweepWpl], full[kSweepWpl];
+        bool mine = true;
+#pragma unroll
+        for (int q = 0; q < kSweepWpl; ++q) {
+            const int64_t w = w0 + lane + 32 * q;
+            const int64_t lo = w * 64;
+            full[q] = (w >= wp || lo >= n) ? 0ull : (n - lo >= 64 ? ~0ull : ((1ull << (n - lo)) - 1ull));
+            acc[q] = w < wp ? mrow[w] : 0ull;
+            mine &= acc[q] == full[q];
+        }
+        uint64_t old[kSweepWpl];
+#pragma unroll
+        for (int q = 0; q < kSweepWpl; ++q) old[q] = acc[q];
+        bool sat = single && __all_sync(0xffffffffu, mine);
+        for (int qq = ptr[i]; qq < ptr[i + 1] && !sat; ++qq) {
+            const int k = col[qq];
+            const uint64_t *mk = M + static_cast<int64_t>(k) * wp;
+            mine = true;
+#pragma unroll
+            for (int q = 0; q < kSweepWpl; ++q) {
+                const int64_t w = w0 + lane + 32 * q;
+                if (w < wp) acc[q] |= mk[w];
+            }
+            const int64_t rel = (k >> 6) - w0;
+            if (rel >= 0 && rel < 32 * kSweepWpl && (rel & 31) == lane) {
+                const int qk = static_cast<int>(rel >> 5);
+#pragma unroll
+                for (int q = 0; q < kSweepWpl; ++q)
+                    if (q == qk) acc[q] |= 1ull << (k & 63);
+            }
+#pragma unroll
+            for (int q = 0; q < kSweepWpl; ++q) mine &= acc[q] == full[q];
+            sat = single && __all_sync(0xffffffffu, mine);
+        }
+#pragma unroll
+        for (int q = 0; q < kSweepWpl; ++q) {
+            const int64_t w = w0 + lane + 32 * q;
+            if (w < wp && acc[q] != old[q]) {
+                mrow[w] = acc[q];
+                changed = true;
+            }
+        }
+    }
+    if (__any_sync(0xffffffffu, changed) && lane == 0) atomicAdd(changed_rows, 1ull);
+}
+
+// mode 0: out_i = OR_{k in succ(i)} M_k; violation iff (out_i | e_i) != M_i; ones of out.
+__global__ void __launch_bounds__(256)
+    sweep_rows_emit_kernel(const int *__restrict__ ptr, const int *__restrict__ col, int n, const uint64_t *M,
+                           uint64_t *out, int64_t wp, unsigned long long *violations, unsigned long long *ones) {
+    const int lane = threadIdx.x & 31;
+    const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (i >= n) return;
+    const bool single = wp <= 32 * kSweepWpl;
+    const uint64_t *mrow = M + static_cast<int64_t>(i) * wp;
+    bool viol = false;
+    uint32_t cnt = 0;
+    for (int64_t w0 = 0; w0 < wp; w0 += 32 * kSweepWpl) {
+        uint64_t acc[kSweepWpl], full[kSweepWpl];
+#pragma unroll
+        for (int q = 0; q < kSweepWpl; ++q) {
+            const int64_t w = w0 + lane + 32 * q;
+            const int64_t lo = w * 64;
+            full[q] = (w >= wp || lo >= n) ? 0ull : (n - lo >= 64 ? ~0ull : ((1ull << (n - lo)) - 1ull));
+            acc[q] = 0ull;
+        }
+        bool sat = false;
+        for (int qq = ptr[i]; qq < ptr[i + 1] && !sat; ++qq) {
+            const uint64_t *mk = M + static_cast<int64_t>(col[qq]) * wp;
+            bool mine = true;
+#pragma unroll
+            for (int q = 0; q < kSweepWpl; ++q) {
+                const int64_t w = w0 + lane + 32 * q;
+                if (w < wp) acc[q] |= mk[w];
+                mine &= acc[q] == full[q];
+            }
+            sat = single && __all_sync(0xffffffffu, mine);
+        }
+#pragma unroll
+        for (int q = 0; q < kSweepWpl; ++q) {
+            const int64_t w = w0 + lane + 32 * q;
+            if (w >= wp) continue;
+            const uint64_t self = (w == (i >> 6)) ? (1ull << (i & 63)) : 0ull;
+            if ((acc[q] | self) != mrow[w]) viol = true;
+            out[static_cast<int64_t>(i) * wp + w] = acc[q];
+            cnt += __popcll(acc[q]);
+        }
+    }
+    const bool any = __any_sync(0xffffffffu, viol);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+    if (lane == 0) {
+        if (any) atomicAdd(violations, 1ull);
+        if (ones && cnt) atomicAdd(ones, static_cast<unsigned long long>(cnt));
+    }
+}
+
+// mode 1 (closure step, in place): M_i |= E_i | OR_{k in succ(i)} M_k; counts changed units.
+__global__ void __launch_bounds__(256)
+    sweep_units_step_kernel(const int *__restrict__ ptr, const int *__restrict__ col, const int *__restrict__ unit_off,
+                            int n, uint64_t *M, int64_t wp, unsigned long long *changed_units) {
+    const int lane = threadIdx.x & 31;
+    const int total = unit_off[n];
+    const int warps = gridDim.x * (blockDim.x >> 5);
+    for (int u = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); u < total; u += warps) {
+        const int i = unit_row(unit_off, n, u);
+        const int q0 = ptr[i] + (u - unit_off[i]) * kUnit;
+        const int q1 = min(q0 + kUnit, ptr[i + 1]);
+        if (or_unit(col, q0, q1, n, i, M, M, wp, true, true, lane) && lane == 0) atomicAdd(changed_units, 1ull);
+    }
+}
+
+// mode 0, pass 1 (out cleared beforehand): out_i = OR_{k in succ(i)} M_k.
+__global__ void __launch_bounds__(256)
+    sweep_units_or_kernel(const int *__restrict__ ptr, const int *__restrict__ col, const int *__restrict__ unit_off,
+                          int n, const uint64_t *M, uint64_t *out, int64_t wp) {
+    const int lane = threadIdx.x & 31;
+    const int total = unit_off[n];
+    const int warps = gridDim.x * (blockDim.x >> 5);
+    for (int u = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); u < total; u += warps) {
+        const int i = unit_row(unit_off, n, u);
+        const int q0 = ptr[i] + (u - unit_off[i]) * kUnit;
+        const int q1 = min(q0 + kUnit, ptr[i + 1]);
+        or_unit(col, q0, q1, n, i, M, out, wp, false, true, lane);
+    }
+}
+
+// mode 0, pass 2: violation iff (out_i | e_i) != M_i; ones of out.
+__global__ void __launch_bounds__(256)
+    sweep_check_kernel(int n, const uint64_t *__restrict__ M, const uint64_t *__restrict__ out, int64_t wp,
+                       unsigned long long *violations, unsigned long long *ones) {
+    const int lane = threadIdx.x & 31;
+    const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (i >= n) return;
+    bool viol = false;
+    uint32_t cnt = 0;
+    for (int64_t w = lane; w < wp; w += 32) {
+        const uint64_t v = out[static_cast<int64_t>(i) * wp + w];
+        const uint64_t self = (w == (i >> 6)) ? (1ull << (i & 63)) : 0ull;
+        if ((v | self) != M[static_cast<int64_t>(i) * wp + w]) viol = true;
+        cnt += __popcll(v);
+    }
+    const bool any = __any_sync(0xffffffffu, viol);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
+    if (lane == 0) {
+        if (any) atomicAdd(violations, 1ull);
+        if (ones && cnt) atomicAdd(ones, static_cast<unsigned long long>(cnt));
+    }
+}
+
+// Bits of I + E (np rows of wp words; rows >= n hold only their diagonal bit); warp per row.
+__global__ void reflexive_bits_kernel(const int *__restrict__ ptr, const int *__restrict__ col, int n, int np,
+                                      int64_t wp, uint64_t *bits) {
+    const int lane = threadIdx.x & 31;
+    const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (i >= np) return;
+    uint64_t *row = bits + static_cast<int64_t>(i) * wp;
+    for (int64_t w = lane; w < wp; w += 32) row[w] = (w == (i >> 6)) ? (1ull << (i & 63)) : 0ull;
+    __syncwarp();
+    if (i < n)
+        for (int q = ptr[i] + lane; q < ptr[i + 1]; q += 32)
+            atomicOr(reinterpret_cast<unsigned long long *>(row + (col[q] >> 6)), 1ull << (col[q] & 63));
+}
+
+// e4m3 0/1 matrix (np x np, 0x38 = 1) from bits; one thread per 64-column word.
+__global__ void bits_to_e4m3_kernel(const uint64_t *__restrict__ bits, int64_t wp, int np, uint8_t *__restrict__ C) {
+    const int64_t t = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (t >= static_cast<int64_t>(np) * wp) return;
+    const int64_t r = t / wp, w = t % wp;
+    const uint64_t x = bits[t];
+    uint4 *dst = reinterpret_cast<uint4 *>(C + r * np + w * 64);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        uint32_t o[4];
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+            const uint32_t nib = static_cast<uint32_t>(x >> (16 * q + 4 * b)) & 0xFu;
+            o[b] = ((nib & 1u) * 0x38u) | (((nib >> 1) & 1u) * 0x3800u) | (((nib >> 2) & 1u) * 0x380000u) |
+                   (((nib >> 3) & 1u) * 0x38000000u);
+        }
+        dst[q] = make_uint4(o[0], o[1], o[2], o[3]);
+    }
+}
+
 }  // namespace
+
+cudaError_t sweep_units(const int *ptr, int n, int *cnt, int *unit_off, cudaStream_t s) {
+    unit_count_kernel<<<(n + 255) / 256, 256, 0, s>>>(ptr, n, cnt);
+    return exclusive_scan(cnt, n, unit_off, s);
+}
+
+cudaError_t bits_sweep_csr(const int *ptr, const int *col, const int *unit_off, int n, const uint64_t *M,
+                           uint64_t *out, int64_t wp, int mode, unsigned long long *violations,
+                           unsigned long long *ones, int *launches, cudaStream_t s, int max_deg) {
+    if (n <= 0) return cudaSuccess;
+    if (max_deg >= 0 && max_deg <= kUnit) {  // every row is one unit: row-direct kernels
+        if (mode == 1)
+            sweep_rows_step_kernel<<<(n + 7) / 8, 256, 0, s>>>(ptr, col, n, const_cast<uint64_t *>(M), wp,
+                                                                violations);
+        else
+            sweep_rows_emit_kernel<<<(n + 7) / 8, 256, 0, s>>>(ptr, col, n, M, out, wp, violations, ones);
+        if (launches) *launches += 1;
+        return cudaGetLastError();
+    }
+    const unsigned grid = static_cast<unsigned>(num_sms() * 8);
+    if (mode == 1) {
+        sweep_units_step_kernel<<<grid, 256, 0, s>>>(ptr, col, unit_off, n, const_cast<uint64_t *>(M), wp,
+                                                      violations);
+        if (launches) *launches += 1;
+        return cudaGetLastError();
+    }
+    cudaError_t e = cudaMemsetAsync(out, 0, static_cast<size_t>(n) * wp * 8, s);
+    if (e != cudaSuccess) return e;
+    sweep_units_or_kernel<<<grid, 256, 0, s>>>(ptr, col, unit_off, n, M, out, wp);
+    sweep_check_kernel<<<(n + 7) / 8, 256, 0, s>>>(n, M, out, wp, violations, ones);
+    if (launches) *launches += 2;
+    return cudaGetLastError();
+}
+
+cudaError_t reflexive_bits(const int *ptr, const int *col, int n, int np, int64_t wp, uint64_t *bits,
+                           cudaStream_t s) {
+    reflexive_bits_kernel<<<(np + 7) / 8, 256, 0, s>>>(ptr, col, n, np, wp, bits);
+    return cudaGetLastError();
+}
+
+cudaError_t bits_to_e4m3(const uint64_t *bits, int64_t wp, int np, uint8_t *C, cudaStream_t s) {
+    const int64_t words = static_cast<int64_t>(np) * wp;
+    bits_to_e4m3_kernel<<<static_cast<unsigned>((words + 255) / 256), 256, 0, s>>>(bits, wp, np, C);
+    return cudaGetLastError();
+}
 
 cudaError_t ingest_u8_to_e4m3(const uint8_t *src, int n, int np, uint8_t *dst, int add_identity,
                               unsigned long long *dmax, unsigned long long *nnz,

@@ -9,6 +9,7 @@
 #include <string>
 
 #include "dl_ctx.h"
+#include "dl_ptx.cuh"
 
 namespace dl {
 
@@ -34,6 +35,20 @@ int num_sms() {
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     return sms;
 }
+
+namespace {
+// Waits on an mbarrier that nobody arrives at; the bounded wait must give up.
+__global__ void selftest_wait_kernel(int *status, uint64_t budget_ns) {
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        fence_barrier_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) mbar_wait_bounded(&bar, 0u, budget_ns, status, ST_TIMEOUT_DEP);
+    __syncthreads();
+}
+}  // namespace
 
 }  // namespace dl
 
@@ -239,6 +254,33 @@ dl_status dl_compose(dl_ctx *ctx, int32_t n, const uint8_t *R1, const uint8_t *R
     a.out_bits = out_bits;
     return run_sync(ctx, stats, [&](Workspace &ws, cudaStream_t s, dl_stats *st) {
         return solve_compose(ctx, ws, s, a, st);
+    });
+}
+
+dl_status dl_selftest_wait_timeout(dl_ctx *ctx, double seconds) {
+    clear_error();
+    GUARD_CTX(ctx);
+    if (!(seconds > 0.0 && seconds <= 10.0)) {
+        set_error("seconds must be in (0, 10]");
+        return DL_EINVAL;
+    }
+    return run_sync(ctx, nullptr, [&](Workspace &ws, cudaStream_t s, dl_stats *) -> dl_status {
+        cudaMemsetAsync(ws.status, 0, sizeof(int), s);
+        selftest_wait_kernel<<<1, 32, 0, s>>>(ws.status, static_cast<uint64_t>(seconds * 1e9));
+        cudaError_t e = cudaGetLastError();
+        int st = 0;
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&st, ws.status, sizeof(int), cudaMemcpyDeviceToHost, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) {
+            set_error("self-test launch failed: %s", cudaGetErrorString(e));
+            return DL_EDEVICE;
+        }
+        if (st & ST_TIMEOUT_DEP) {
+            set_error("bounded device wait expired after %.3f s (expected)", seconds);
+            return DL_ETIMEOUT;
+        }
+        set_error("the wait returned without expiring");
+        return DL_OK;
     });
 }
 

@@ -39,6 +39,8 @@ struct GemmEpilogue {
     float *c32;               // SUB_F32 only
     int64_t ld_c32;           // floats per row
     int32_t out_row0, out_col0;  // output coordinates of the problem's (0, 0)
+    uint8_t *occ_out;         // may be null: set to 1 for every 128 x 128 block with a one
+    int32_t occ_ld;           // blocks per row of occ_out
 };
 
 // One GEMM problem D(MxN) = A(MxK) * B(KxN).  Lives in device memory (tensor maps are read
@@ -52,6 +54,11 @@ struct GemmProblem {  // CUtensorMap members carry the TMA descriptor alignment
     int32_t a_row0, a_col0;  // A(0,0) at tensor coordinates (x = a_col0, y = a_row0)
     int32_t b_row0, b_col0;  // B: MN-major (x = n, y = k); K-major (x = k, y = n)
     const int *gate;         // may be null; tiles of this problem are skipped while *gate != 0
+    // May be null (dense).  128 x 128 block occupancy of A (row-blocks x k-blocks) and of an
+    // MN-major B (k-blocks x column-blocks), occ_ld blocks per row; FP8 only.  A k-block
+    // whose A block or B blocks are all empty contributes nothing and is skipped.
+    const uint8_t *occ_a, *occ_b;
+    int32_t occ_ld;
     GemmEpilogue epi;
 };
 
@@ -92,6 +99,31 @@ cudaError_t ingest_u8_to_e4m3(const uint8_t *src, int n, int np, uint8_t *dst, i
 cudaError_t bits_sweep(const uint8_t *E, int64_t lde, int n, const uint64_t *M, uint64_t *out,
                        int64_t wp, int mode, int stop_early, unsigned long long *violations,
                        unsigned long long *ones, cudaStream_t s);
+
+// The sweep on the CSR (ptr, col) of E, edge-parallel: work units of up to 64 successors of
+// one row, combined with atomicOr.  sweep_units builds unit_off (n + 1 entries; cnt is n ints
+// of scratch) once per CSR.  mode 1: in place (out must be M), *violations += changed units;
+// mode 0: out = E M (rows < n), *violations += rows with (out_i | e_i) != M_i, *ones += ones.
+cudaError_t sweep_units(const int *ptr, int n, int *cnt, int *unit_off, cudaStream_t s);
+// max_deg: ||E||_inf if known (rows of at most 64 successors take row-direct kernels), or -1.
+cudaError_t bits_sweep_csr(const int *ptr, const int *col, const int *unit_off, int n, const uint64_t *M,
+                           uint64_t *out, int64_t wp, int mode, unsigned long long *violations,
+                           unsigned long long *ones, int *launches, cudaStream_t s, int max_deg);
+// Bits of I + E (np rows x wp words) from the CSR of E.
+cudaError_t reflexive_bits(const int *ptr, const int *col, int n, int np, int64_t wp, uint64_t *bits,
+                           cudaStream_t s);
+// e4m3 0/1 operand (np x np, 1.0 = 0x38) from a bit matrix.
+cudaError_t bits_to_e4m3(const uint64_t *bits, int64_t wp, int np, uint8_t *C, cudaStream_t s);
+
+// ---------------------------------------------------------------------------------------
+// Graph utilities (dl_graph.cu)
+// ---------------------------------------------------------------------------------------
+// CSR of a dense n x n 0/1 matrix: csr_build writes per-row counts and ptr (n + 1 entries,
+// exclusive scan); after reading ptr[n] (= nnz) the caller sizes col and runs csr_fill.
+cudaError_t csr_build(const uint8_t *E, int n, int *cnt, int *ptr, cudaStream_t s);
+cudaError_t csr_fill(const uint8_t *E, int n, const int *ptr, int *col, cudaStream_t s);
+// out[0..n] = exclusive prefix sums of cnt[0..n-1] (out[n] = total); one CTA.
+cudaError_t exclusive_scan(const int *cnt, int n, int *out, cudaStream_t s);
 
 // ---------------------------------------------------------------------------------------
 // FP64 path (dl_fp64.cu)

@@ -148,55 +148,6 @@ __global__ void __launch_bounds__(256) diag_lu_inv_kernel(const float *A, int64_
     }
 }
 
-// CSR of the 0/1 matrix E: cnt[i] = successors of i; then ptr = exclusive scan; then col.
-__global__ void csr_count_kernel(const uint8_t *__restrict__ E, int n, int *cnt) {
-    const int lane = threadIdx.x & 31;
-    const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (i >= n) return;
-    int c = 0;
-    for (int j = lane; j < n; j += 32) c += E[static_cast<int64_t>(i) * n + j] ? 1 : 0;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
-    if (lane == 0) cnt[i] = c;
-}
-
-__global__ void __launch_bounds__(1024) exclusive_scan_kernel(const int *cnt, int n, int *ptr) {
-    __shared__ int part[1024];
-    const int t = threadIdx.x;
-    const int chunk = (n + 1023) / 1024;
-    const int b = t * chunk, e = min(n, b + chunk);
-    int s = 0;
-    for (int i = b; i < e; ++i) s += cnt[i];
-    part[t] = s;
-    __syncthreads();
-    for (int o = 1; o < 1024; o <<= 1) {  // inclusive Hillis-Steele scan of the partial sums
-        const int v = t >= o ? part[t - o] : 0;
-        __syncthreads();
-        part[t] += v;
-        __syncthreads();
-    }
-    int run = t > 0 ? part[t - 1] : 0;
-    for (int i = b; i < e; ++i) {
-        ptr[i] = run;
-        run += cnt[i];
-    }
-    if (t == 1023) ptr[n] = part[1023];
-}
-
-__global__ void csr_fill_kernel(const uint8_t *__restrict__ E, int n, const int *__restrict__ ptr, int *col) {
-    const int lane = threadIdx.x & 31;
-    const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (i >= n) return;
-    int base = ptr[i];
-    for (int j0 = 0; j0 < n; j0 += 32) {
-        const int j = j0 + lane;
-        const bool on = j < n && E[static_cast<int64_t>(i) * n + j];
-        const unsigned bal = __ballot_sync(0xffffffffu, on);
-        if (on) col[base + __popc(bal & ((1u << lane) - 1u))] = j;
-        base += __popc(bal);
-    }
-}
-
 // Residual of the transposed system, one block per row j of Z, the row staged in shared
 // memory:  R^T[j][i] = eps * sum_{k in succ(i)} (Z[j][k] + [k = j]) - Z[j][i]  (FP64),
 // stored as FP32 (right-hand side of the correction solve); max |R| -> *rmax.
@@ -290,10 +241,7 @@ dl_status tc_mixed(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &
         launches += 2;
     }
     // CSR of E for the residual
-    csr_count_kernel<<<static_cast<unsigned>((n + 7) / 8), 256, 0, s>>>(E, n, csr_cnt);
-    MCK(cudaGetLastError());
-    exclusive_scan_kernel<<<1, 1024, 0, s>>>(csr_cnt, n, csr_ptr);
-    MCK(cudaGetLastError());
+    MCK(csr_build(E, n, csr_cnt, csr_ptr, s));
     int nnz = 0;
     MCK(cudaMemcpyAsync(&nnz, csr_ptr + n, sizeof(int), cudaMemcpyDeviceToHost, s));
     MCK(cudaStreamSynchronize(s));
@@ -302,8 +250,7 @@ dl_status tc_mixed(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &
         set_error("mixed path: device allocation failed (CSR)");
         return DL_ENOMEM;
     }
-    csr_fill_kernel<<<static_cast<unsigned>((n + 7) / 8), 256, 0, s>>>(E, n, csr_ptr, csr_col);
-    MCK(cudaGetLastError());
+    MCK(csr_fill(E, n, csr_ptr, csr_col, s));
     launches += 3;
 
     // ---- GEMM table (every product is C (=|-=) A B'^T, both operands K-major) --------------

@@ -227,7 +227,6 @@ dl_status tc_bool(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &a
     CK(cudaMemsetAsync(ws.scal, 0, kScalars * sizeof(unsigned long long), s));
     CK(cudaMemsetAsync(ws.status, 0, sizeof(int), s));
     if ((rc = ingest(ctx, ws, s, E, n, np, C0, 1, SC_DMAX, SC_NNZ, SC_COUNT0, &launches))) return rc;
-    tm.mark(1);
     if ((rc = read_scalars(ws, s))) return rc;
     if ((rc = check_status(ws, s))) return rc;
     const unsigned long long dmax = host_scal(ws)[SC_DMAX];
@@ -235,6 +234,18 @@ dl_status tc_bool(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &a
     if ((rc = choose_eps(a.eps, 1.0 / (1.0 + static_cast<double>(dmax)), "Lemma 1 (1/(1+||E||))", &eps)))
         return rc;
     unsigned long long prev = host_scal(ws)[SC_COUNT0];
+    // successor lists for the certificate (edge-parallel, balanced for heavy-tailed degrees)
+    auto *cnt_s = static_cast<int *>(ws.get("g_cnt", (np + 1) * 4));
+    auto *ptr = static_cast<int *>(ws.get("g_ptr", (np + 1) * 4));
+    auto *uoff = static_cast<int *>(ws.get("g_units", (np + 1) * 4));
+    auto *col = static_cast<int *>(
+        ws.get("g_col", static_cast<size_t>(std::max<unsigned long long>(host_scal(ws)[SC_NNZ], 1)) * 4));
+    NEED(cnt_s && ptr && uoff && col);
+    CK(csr_build(E, n, cnt_s, ptr, s));
+    CK(csr_fill(E, n, ptr, col, s));
+    CK(sweep_units(ptr, n, cnt_s, uoff, s));
+    launches += 4;
+    tm.mark(1);
 
     // GEMM tables: squaring C0 -> C1 and C1 -> C0, bits into rbits, count into slot
     GemmProblem probs[2];
@@ -243,9 +254,9 @@ dl_status tc_bool(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &a
     for (int p = 0; p < 2; ++p) {
         const uint8_t *src = p == 0 ? C0 : C1;
         uint8_t *dst = p == 0 ? C1 : C0;
+        GemmEpilogue epi = bool_epi(dst, np, rbits, wp, ws.scal + SC_STEP0, nullptr);
         if (!gemm_make_problem(&probs[p], KIND_F8, false, bn, static_cast<int>(np), static_cast<int>(np),
-                               static_cast<int>(np), square_op(src, np), square_op(src, np),
-                               bool_epi(dst, np, rbits, wp, ws.scal + SC_STEP0, nullptr), &err)) {
+                               static_cast<int>(np), square_op(src, np), square_op(src, np), epi, &err)) {
             set_error("%s", err.c_str());
             return DL_EDEVICE;
         }
@@ -278,8 +289,7 @@ dl_status tc_bool(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &a
         prev = cnt;
         // certificate: does C_t satisfy C = min1(I + E C)?  (stops at the first violation)
         CK(cudaMemsetAsync(ws.scal + SC_VIOL, 0, 2 * sizeof(unsigned long long), s));
-        CK(bits_sweep(E, n, n, rbits, mbits, wp, 0, 1, ws.scal + SC_VIOL, ws.scal + SC_ONES, s));
-        ++launches;
+        CK(bits_sweep_csr(ptr, col, uoff, n, rbits, mbits, wp, 0, ws.scal + SC_VIOL, ws.scal + SC_ONES, &launches, s, static_cast<int>(dmax)));
         ++sweeps;
         if ((rc = read_scalars(ws, s))) return rc;
         if (host_scal(ws)[SC_VIOL] == 0) {
@@ -290,8 +300,7 @@ dl_status tc_bool(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &a
     tm.mark(2);
     if (!have_model) {
         CK(cudaMemsetAsync(ws.scal + SC_VIOL, 0, 2 * sizeof(unsigned long long), s));
-        CK(bits_sweep(E, n, n, rbits, mbits, wp, 0, 0, ws.scal + SC_VIOL, ws.scal + SC_ONES, s));
-        ++launches;
+        CK(bits_sweep_csr(ptr, col, uoff, n, rbits, mbits, wp, 0, ws.scal + SC_VIOL, ws.scal + SC_ONES, &launches, s, static_cast<int>(dmax)));
         ++sweeps;
         if ((rc = read_scalars(ws, s))) return rc;
         if (host_scal(ws)[SC_VIOL] != 0) {
@@ -309,6 +318,158 @@ dl_status tc_bool(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &a
         gc.fill(st);
         st->final_resid = 0.0;
         st->recheck_sweeps = sweeps;
+        st->model_ones = static_cast<int64_t>(host_scal(ws)[SC_ONES]);
+        st->ms_factor = tm.ms(0, 1);
+        st->ms_solve = tm.ms(1, 2);
+        st->ms_epilogue = tm.ms(2, 3);
+        st->ms_total = tm.ms(0, 3);
+        st->gpu_launches = launches;
+    }
+    return DL_OK;
+}
+
+// DL_PATH_AUTO: tensor-core squarings and boolean sweeps, whichever is cheaper.
+// A sweep (in place, M <- M | E | E M on bits) is one step of the paper's Iteration method
+// (Sec. 6.1, eq. series:trcl) and adds at least one hop to every path; a squaring doubles
+// the hop count but costs a dense 2 Np^3 product.  Sparse graphs are finished by sweeps
+// alone; dense ones square first and let a few cheap sweeps (rows saturate quickly) finish.
+// A sweep that changes nothing proves M = min1(I + E M), i.e. M is the reflexive closure;
+// the model is then E M (the final sweep, which checks the same equation once more).
+dl_status tc_auto(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &a, dl_stats *st) {
+    const int32_t n = a.n;
+    const int64_t np = round_up(std::max<int64_t>(n, 1), 256);
+    const int64_t wp = np / 64;
+    Timer tm{ws.ev, s};
+    int launches = 0;
+    tm.mark(0);
+    const uint8_t *E = nullptr;
+    dl_status rc = stage_input(ws, s, a.E, n, a.mem, "in0", &E);
+    if (rc) return rc;
+    uint8_t *C[2] = {static_cast<uint8_t *>(ws.get("c0", np * np)), static_cast<uint8_t *>(ws.get("c1", np * np))};
+    auto *rbits = static_cast<uint64_t *>(ws.get("bits0", np * wp * 8));
+    auto *mbits = static_cast<uint64_t *>(ws.get("bits1", np * wp * 8));
+    auto *cnt = static_cast<int *>(ws.get("g_cnt", (np + 1) * 4));
+    auto *ptr = static_cast<int *>(ws.get("g_ptr", (np + 1) * 4));
+    auto *uoff = static_cast<int *>(ws.get("g_units", (np + 1) * 4));
+    NEED(C[0] && C[1] && rbits && mbits && cnt && ptr && uoff);
+    CK(cudaMemsetAsync(ws.scal, 0, kScalars * sizeof(unsigned long long), s));
+    CK(cudaMemsetAsync(ws.status, 0, sizeof(int), s));
+    if ((rc = ingest(ctx, ws, s, E, n, np, C[0], 1, SC_DMAX, SC_NNZ, SC_COUNT0, &launches))) return rc;
+    CK(csr_build(E, n, cnt, ptr, s));
+    launches += 2;
+    if ((rc = read_scalars(ws, s))) return rc;
+    if ((rc = check_status(ws, s))) return rc;
+    const unsigned long long dmax = host_scal(ws)[SC_DMAX];
+    double eps = 0;
+    if ((rc = choose_eps(a.eps, 1.0 / (1.0 + static_cast<double>(dmax)), "Lemma 1 (1/(1+||E||))", &eps)))
+        return rc;
+    const int64_t nnz = static_cast<int64_t>(host_scal(ws)[SC_NNZ]);
+    unsigned long long prev = host_scal(ws)[SC_COUNT0];
+    auto *col = static_cast<int *>(ws.get("g_col", static_cast<size_t>(std::max<int64_t>(nnz, 1)) * 4));
+    NEED(col);
+    CK(csr_fill(E, n, ptr, col, s));
+    CK(sweep_units(ptr, n, cnt, uoff, s));
+    CK(reflexive_bits(ptr, col, n, static_cast<int>(np), wp, rbits, s));
+    launches += 4;
+    tm.mark(1);
+
+    // cost model (seconds): one squaring vs one sweep before rows saturate
+    const double t_sq = 2.0 * np * np * np / 3.4e15 + 15e-6;
+    const double t_sw = (static_cast<double>(nnz) * wp * 8 + 2.0 * np * wp * 8) / 3.0e12 + 5e-6;
+    const bool dense = 4.0 * t_sw > t_sq;
+    // sweeps allowed between two squarings before a squaring is the cheaper way forward
+    const int sweep_budget = static_cast<int>(std::max(4.0, std::floor(t_sq / t_sw)));
+
+    GemmProblem probs[2];
+    std::string err;
+    const int bn = bool_bn(np);
+    for (int p = 0; p < 2; ++p) {
+        if (!gemm_make_problem(&probs[p], KIND_F8, false, bn, static_cast<int>(np), static_cast<int>(np),
+                               static_cast<int>(np), square_op(C[p], np), square_op(C[p], np),
+                               bool_epi(C[1 - p], np, rbits, wp, ws.scal + SC_STEP0, nullptr), &err)) {
+            set_error("%s", err.c_str());
+            return DL_EDEVICE;
+        }
+    }
+    GemmProblem *dprobs = nullptr;
+    if ((rc = upload_problems(ws, s, probs, 2, &dprobs))) return rc;
+    const int tiles = probs[0].tiles_m * probs[0].tiles_n;
+    const int grid = std::min(tiles, ctx->sms);
+    GemmClock gc{ws, s};
+    const int max_squarings = 2 + static_cast<int>(std::ceil(std::log2(static_cast<double>(np) + 1.0)));
+    const int max_sweeps = static_cast<int>(std::min<int64_t>(2 * static_cast<int64_t>(n) + 16, 1 << 20));
+    int cur = 0, squarings = 0, sweeps = 0;
+    bool c_valid = true;  // C[cur] holds the same matrix as rbits
+    bool converged = false, do_square = dense;
+    int since_square = 0;  // sweeps since the last squaring
+    unsigned long long *vslot = ws.scal + 32;  // up to 16 violation counters, one per sweep
+    while (!converged) {
+        if (do_square) {
+            if (squarings >= max_squarings) {
+                set_error("closure did not converge in %d squarings", squarings);
+                return DL_ENOTCONV;
+            }
+            if (!c_valid) {
+                CK(bits_to_e4m3(rbits, wp, static_cast<int>(np), C[cur], s));
+                ++launches;
+            }
+            CK(cudaMemsetAsync(ws.scal + SC_STEP0, 0, sizeof(unsigned long long), s));
+            gc.start();
+            CK(gemm_launch(KIND_F8, false, bn, EPI_BOOL, dprobs + cur, 1, tiles, grid, ws.status, ctx->budget_ns,
+                           s));
+            gc.stop(2.0 * np * np * np);
+            ++launches;
+            ++squarings;
+            since_square = 0;
+            cur ^= 1;
+            c_valid = true;
+            if ((rc = read_scalars(ws, s))) return rc;
+            const unsigned long long c2 = host_scal(ws)[SC_STEP0];
+            if (c2 == prev) {
+                converged = true;
+                break;
+            }
+            prev = c2;
+        }
+        // a group of in-place sweeps, one host read for all of them (after a squaring the rows
+        // are dense and saturate within a few successors, so a short group is cheap)
+        const int g = std::max(1, std::min(squarings == 0 ? 16 : 4, sweep_budget - since_square));
+        CK(cudaMemsetAsync(vslot, 0, sizeof(unsigned long long) * g, s));
+        for (int k = 0; k < g; ++k)
+            CK(bits_sweep_csr(ptr, col, uoff, n, rbits, rbits, wp, 1, vslot + k, nullptr, &launches, s,
+                              static_cast<int>(dmax)));
+        sweeps += g;
+        since_square += g;
+        if ((rc = read_scalars(ws, s))) return rc;
+        for (int k = 0; k < g; ++k)
+            if (host_scal(ws)[32 + k] == 0) converged = true;
+        if (!converged) {
+            c_valid = false;
+            do_square = squarings > 0 || since_square >= sweep_budget;
+            if (sweeps > max_sweeps) {
+                set_error("closure did not converge in %d sweeps", sweeps);
+                return DL_ENOTCONV;
+            }
+        }
+    }
+    tm.mark(2);
+    // model E M, checking M = min1(I + E M) on the way
+    CK(cudaMemsetAsync(ws.scal + SC_VIOL, 0, 2 * sizeof(unsigned long long), s));
+    CK(bits_sweep_csr(ptr, col, uoff, n, rbits, mbits, wp, 0, ws.scal + SC_VIOL, ws.scal + SC_ONES, &launches, s, static_cast<int>(dmax)));
+    if ((rc = write_bits(s, mbits, wp, a.out_bits, n, a.mem))) return rc;
+    if ((rc = read_scalars(ws, s))) return rc;
+    if (host_scal(ws)[SC_VIOL] != 0) {
+        set_error("internal: converged closure failed its certificate");
+        return DL_EDEVICE;
+    }
+    tm.mark(3);
+    if ((rc = check_status(ws, s))) return rc;
+    if (st) {
+        st->path_used = DL_PATH_AUTO;
+        st->eps_used = eps;
+        st->iters = squarings;
+        st->recheck_sweeps = sweeps + 1;
+        gc.fill(st);
         st->model_ones = static_cast<int64_t>(host_scal(ws)[SC_ONES]);
         st->ms_factor = tm.ms(0, 1);
         st->ms_solve = tm.ms(1, 2);
@@ -477,10 +638,10 @@ dl_status solve_tc(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &
         case DL_PATH_AUTO:
         case DL_PATH_BOOL_FP8:
             if (a.out_rtilde) {
-                set_error("the boolean path computes no real-valued R~; use DL_PATH_FP64");
+                set_error("the boolean paths compute no real-valued R~; use DL_PATH_FP64 or DL_PATH_MIXED");
                 return DL_EINVAL;
             }
-            rc = tc_bool(ctx, ws, s, a, st);
+            rc = a.path == DL_PATH_AUTO ? tc_auto(ctx, ws, s, a, st) : tc_bool(ctx, ws, s, a, st);
             break;
         case DL_PATH_FP64:
             rc = tc_fp64(ctx, ws, s, a, st);

@@ -77,8 +77,27 @@ __device__ __forceinline__ bool gated_off(const GemmProblem *P) {
     return P->gate != nullptr && *reinterpret_cast<const volatile int *>(P->gate) != 0;
 }
 
-__device__ __forceinline__ void epi_bool_chunk(const GemmEpilogue &e, int row, int col,
-                                               const uint32_t (&v)[32], uint32_t &cnt) {
+// Does k-block kb of output tile (mb, nb) contribute?  (always, without occupancy maps)
+template <int BN>
+__device__ __forceinline__ bool kblock_live(const GemmProblem *P, int mb, int nb, int kb) {
+    if (P->occ_a == nullptr) return true;
+    if (!P->occ_a[mb * P->occ_ld + kb]) return false;
+#pragma unroll
+    for (int j = 0; j < BN / 128; ++j)
+        if (P->occ_b[kb * P->occ_ld + nb * (BN / 128) + j]) return true;
+    return false;
+}
+
+template <int BN>
+__device__ __forceinline__ bool tile_live(const GemmProblem *P, int mb, int nb, int nkb) {
+    if (P->occ_a == nullptr) return true;
+    for (int kb = 0; kb < nkb; ++kb)
+        if (kblock_live<BN>(P, mb, nb, kb)) return true;
+    return false;
+}
+
+__device__ __forceinline__ uint32_t epi_bool_chunk(const GemmEpilogue &e, int row, int col,
+                                                   const uint32_t (&v)[32], uint32_t &cnt) {
     uint32_t word = 0;
 #pragma unroll
     for (int j = 0; j < 32; ++j) word |= (__uint_as_float(v[j]) > 0.0f ? 1u : 0u) << j;
@@ -108,6 +127,7 @@ __device__ __forceinline__ void epi_bool_chunk(const GemmEpilogue &e, int row, i
     }
     if (e.bits) e.bits[r * e.ld_bits32 + (c >> 5)] = word;
     cnt += __popc(word);
+    return word;
 }
 
 __device__ __forceinline__ void epi_store_chunk(const GemmEpilogue &e, int row, int col,
@@ -193,6 +213,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 const int mb = local % P->tiles_m, nb = local / P->tiles_m;
                 const int nkb = P->K / C::BK;
                 for (int kb = 0; kb < nkb; ++kb) {
+                    if (!kblock_live<BN>(P, mb, nb, kb)) continue;
                     if (!mbar_wait_bounded(&empty[stage], ph ^ 1u, budget_ns, status,
                                            ST_TIMEOUT_EMPTY)) {
                         ok = false;
@@ -235,6 +256,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             for (int tile = blockIdx.x; tile < total_tiles && ok; tile += gridDim.x) {
                 const GemmProblem *P = find_problem(probs, nprob, tile);
                 if (gated_off(P)) continue;
+                const int local = tile - P->tile_start;
+                const int mb = local % P->tiles_m, nb = local / P->tiles_m;
                 const int nkb = P->K / C::BK;
                 if (!mbar_wait_bounded(&acce[acc], acc_ph ^ 1u, budget_ns, status,
                                        ST_TIMEOUT_ACC_EMPTY)) {
@@ -243,7 +266,9 @@ __global__ void __launch_bounds__(kThreads, 1)
                 }
                 tc_fence_after();
                 const uint32_t d_tmem = tmem_base + static_cast<uint32_t>(acc * BN);
+                bool issued = false;
                 for (int kb = 0; kb < nkb; ++kb) {
+                    if (!kblock_live<BN>(P, mb, nb, kb)) continue;
                     if (!mbar_wait_bounded(&full[stage], ph, budget_ns, status,
                                            ST_TIMEOUT_FULL)) {
                         ok = false;
@@ -258,8 +283,9 @@ __global__ void __launch_bounds__(kThreads, 1)
                         const uint64_t bdesc =
                             B_KMAJOR ? smem_desc_sw128(b0 + kk * 32, 16, 1024)
                                      : smem_desc_sw128(b0 + kk * C::KI * 128, C::BK * 128, 1024);
-                        umma_issue<KIND>(d_tmem, adesc, bdesc, IDESC, (kb | kk) != 0 ? 1u : 0u);
+                        umma_issue<KIND>(d_tmem, adesc, bdesc, IDESC, (issued || kk != 0) ? 1u : 0u);
                     }
+                    issued = true;
                     umma_commit(&empty[stage]);
                     if (++stage == C::S) {
                         stage = 0;
@@ -267,7 +293,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                     }
                 }
                 if (!ok) break;
-                umma_commit(&accf[acc]);
+                if (issued) umma_commit(&accf[acc]);
+                else mbar_arrive(&accf[acc]);  // empty tile: the epilogue writes zeros
                 acc ^= 1;
                 if (acc == 0) acc_ph ^= 1u;
             }
@@ -291,19 +318,31 @@ __global__ void __launch_bounds__(kThreads, 1)
             tc_fence_after();
             const int row = mb * BM + r_in_tile;
             const bool row_ok = row < P->M;
+            const bool live = tile_live<BN>(P, mb, nb, P->K / C::BK);  // warp-uniform
             const uint32_t tbase = tmem_base + (static_cast<uint32_t>(quarter * 32) << 16) +
                                    static_cast<uint32_t>(acc * BN);
             uint32_t cnt = 0;
 #pragma unroll 1
             for (int c = 0; c < BN / 32; ++c) {
                 uint32_t v[32];
-                tmem_ld_32x32b_x32(tbase + c * 32, v);
-                tmem_ld_wait();
+                if (live) {
+                    tmem_ld_32x32b_x32(tbase + c * 32, v);
+                    tmem_ld_wait();
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 32; ++j) v[j] = 0u;
+                }
                 const int col = nb * BN + c * 32;
+                uint32_t word = 0;
                 if (row_ok && col < P->N) {
-                    if (EPI == EPI_BOOL) epi_bool_chunk(P->epi, row, col, v, cnt);
+                    if (EPI == EPI_BOOL) word = epi_bool_chunk(P->epi, row, col, v, cnt);
                     else if (EPI == EPI_SUB_F32) epi_sub_chunk(P->epi, row, col, v);
                     else epi_store_chunk(P->epi, row, col, v);
+                }
+                if (EPI == EPI_BOOL && P->epi.occ_out != nullptr) {
+                    if (__any_sync(0xffffffffu, word != 0u) && lane == 0)
+                        P->epi.occ_out[((P->epi.out_row0 + mb * BM + quarter * 32) >> 7) * P->epi.occ_ld +
+                                       ((P->epi.out_col0 + col) >> 7)] = 1;
                 }
             }
             tc_fence_before();

@@ -25,7 +25,7 @@ DL_MEM_HOST, DL_MEM_DEVICE = 0, 1
 
 EXPORTED = ["dl_create", "dl_destroy", "dl_last_error", "dl_set_stream", "dl_tc_closure",
             "dl_sg_least_model", "dl_compose", "dl_tc_batch", "dl_submit", "dl_poll", "dl_cancel",
-            "dl_tc_closure_noalloc"]
+            "dl_tc_closure_noalloc", "dl_selftest_wait_timeout"]
 NOALLOC_MAX_N = 2048
 
 
@@ -95,6 +95,7 @@ def lib() -> ctypes.CDLL:
             L.dl_poll.argtypes = [vp, ctypes.c_uint64, i64, ctypes.POINTER(Stats)]
             L.dl_cancel.argtypes = [vp, ctypes.c_uint64]
             L.dl_tc_closure_noalloc.argtypes = [i32, vp, vp, vp, ctypes.POINTER(i32)]
+            L.dl_selftest_wait_timeout.argtypes = [vp, f64]
             for f in EXPORTED:
                 if f != "dl_last_error":
                     getattr(L, f).restype = ctypes.c_int
@@ -275,6 +276,10 @@ class Context:
 
     def cancel(self, ticket: int) -> int:
         return lib().dl_cancel(self._h, ctypes.c_uint64(ticket))
+
+    def selftest_wait_timeout(self, seconds: float) -> int:
+        """Status of a deliberately unsatisfied bounded device wait (DL_ETIMEOUT expected)."""
+        return lib().dl_selftest_wait_timeout(self._h, float(seconds))
 
 
 def tc_closure_noalloc(E, stream=None):

@@ -34,9 +34,10 @@ def test_config_er256_fp64(ctx):
     assert np.array_equal(bits, oracle.tc_model(e))
 
 
+@pytest.mark.parametrize("path", ["bool_fp8", "auto"])
 @pytest.mark.parametrize("p", [p for p, _ in BIG])
-def test_config_er8192_fp8(ctx, big_graphs, big_models, p):
-    bits, st = ctx.tc_closure(big_graphs[p], path="bool_fp8")
+def test_config_er8192_fp8(ctx, big_graphs, big_models, p, path):
+    bits, st = ctx.tc_closure(big_graphs[p], path=path)
     assert np.array_equal(bits, big_models[p])
     assert st["model_ones"] == int(np.unpackbits(big_models[p].view(np.uint8)).sum())
 

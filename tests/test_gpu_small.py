@@ -62,7 +62,7 @@ def test_worked_example_all_paths(ctx):
 
 
 @pytest.mark.parametrize("n", EDGE_SIZES)
-@pytest.mark.parametrize("path", ["bool_fp8", "fp64", "mixed"])
+@pytest.mark.parametrize("path", ["bool_fp8", "fp64", "mixed", "auto"])
 def test_closure_tile_edges(ctx, n, path):
     e = inputs.er_digraph(n, min(0.5, 3.0 / n), 100 + n)
     bits, st = ctx.tc_closure(e, path=path)
@@ -91,7 +91,7 @@ def test_closure_degenerate_graphs(ctx, kind):
     elif kind == "two_chains":
         e[np.arange(0, n - 2, 2), np.arange(2, n, 2)] = 1
     ref = oracle.tc_model(e)
-    for path in ("bool_fp8", "fp64", "mixed"):
+    for path in ("bool_fp8", "fp64", "mixed", "auto"):
         bits, st = ctx.tc_closure(e, path=path)
         assert np.array_equal(bits, ref), path
 
@@ -108,6 +108,44 @@ def test_mixed_dense_complete_digraph_closed_form(ctx, n):
     assert np.abs(x - want).max() <= max(1e-10, 4 * kappa * st["final_resid"])
     assert np.abs(x - want).max() <= 1e-9
     assert np.array_equal(bits, oracle.pack(np.ones((n, n))))
+
+
+@pytest.mark.parametrize("n,deg,seed", [(300, 0.5, 1), (700, 1.0, 2), (1000, 3.0, 3), (2049, 8.0, 4),
+                                        (3000, 0.2, 5), (1500, 40.0, 6)])
+def test_auto_path_sparse_and_dense(ctx, n, deg, seed):
+    """DL_PATH_AUTO mixes squarings and sweeps by cost; every mix must give the oracle's model."""
+    e = inputs.er_digraph(n, deg / n, seed)
+    bits, st = ctx.tc_closure(e, path="auto")
+    assert np.array_equal(bits, oracle.tc_model(e))
+    assert st["path_used"] == dl.PATHS["auto"]
+    assert st["recheck_sweeps"] >= 1
+
+
+@pytest.mark.parametrize("n,seed", [(1500, 7), (3000, 8)])
+def test_heavy_tailed_degrees(ctx, n, seed):
+    """Preferential-attachment DAGs have rows with hundreds of successors: the sweeps split
+    such rows into units combined with atomicOr; models must still equal the oracle's."""
+    e = inputs.pa_dag(n, seed)
+    assert oracle.max_row_sum(e) > 64
+    ref = oracle.tc_model(e)
+    for path in ("auto", "bool_fp8"):
+        bits, st = ctx.tc_closure(e, path=path)
+        assert np.array_equal(bits, ref), path
+    e2 = e | e.T  # cycles everywhere, dense closure with heavy rows
+    ref2 = oracle.tc_model(e2)
+    for path in ("auto", "bool_fp8"):
+        assert np.array_equal(ctx.tc_closure(e2, path=path)[0], ref2), path
+
+
+def test_auto_path_long_chain_and_cycle(ctx):
+    for n in (1000, 2500):
+        e = np.zeros((n, n), dtype=np.uint8)
+        e[np.arange(n - 1), np.arange(1, n)] = 1
+        bits, st = ctx.tc_closure(e, path="auto")
+        assert np.array_equal(bits, oracle.tc_model(e))
+        e[n - 1, 0] = 1
+        bits, st = ctx.tc_closure(e, path="auto")
+        assert np.array_equal(bits, oracle.tc_model(e))
 
 
 def test_chain_needs_log_squarings(ctx):
