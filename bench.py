@@ -37,20 +37,26 @@ METRIC = "TC least-model TFLOP/s-equiv (N=8192) vs plain FP64 path; served p50/p
 UNIT = "TFLOP/s-equiv"
 
 
-# DRAM bytes per launch of the dominant kernel from the ncu capture summarised in
-# profiles/umma_gemm_fp8_n8192.md; only valid for the kernel source it was taken on.
-GEMM_TRAFFIC = {"sources": {"dl_umma.cu": "b03e74adf4e37b05", "dl_ptx.cuh": "b4fd45714c88d2fc"},
-                "bytes_per_launch": 404.2e6}
+# DRAM bytes per launch from the ncu captures summarised under profiles/; each is only valid
+# for the kernel source it was taken on (sha256 prefixes).
+TRAFFIC = {
+    "gemm": {"sources": {"dl_umma.cu": "bf1ef1b8f47bb7b3", "dl_ptx.cuh": "b4fd45714c88d2fc"},
+             "bytes_per_launch": 476.6e6},   # profiles/umma_gemm_fp8_n8192.md
+    "sweep": {"sources": {"dl_bool.cu": "787acf21ffebdce6", "dl_rows.cuh": None},
+              "bytes_per_launch": 6.8e6},     # profiles/sweep_rows_step_n8192.md (p = 1e-3)
+}
 
 
-def gemm_traffic():
+def traffic(kind: str):
     import hashlib
     csrc = os.path.join(ROOT, "paper_1608_00139_gb300", "csrc")
-    for f, h in GEMM_TRAFFIC["sources"].items():
+    for f, h in TRAFFIC[kind]["sources"].items():
+        if h is None:
+            continue
         with open(os.path.join(csrc, f), "rb") as fh:
             if hashlib.sha256(fh.read()).hexdigest()[:16] != h:
                 return None  # kernel changed since the counters were taken
-    return GEMM_TRAFFIC["bytes_per_launch"]
+    return TRAFFIC[kind]["bytes_per_launch"]
 
 
 def flops_equiv(n: int) -> float:
@@ -270,6 +276,8 @@ def main() -> None:
                     help="closure path of the headline (auto: squarings + sweeps by cost)")
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    ap.add_argument("--no-compare", action="store_true",
+                    help="skip the squarings-only FP8 comparison run")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the same-generation, batch and serving measurements")
     ap.add_argument("--serve-seconds", type=float, default=10.0,
@@ -288,53 +296,66 @@ def main() -> None:
     torch.cuda.set_device(local)
     if world > 1:
         tdist.init_process_group("nccl")
-    stream = torch.cuda.Stream()  # the library's kernels and the timing events share it
-    ctx = dl.Context(local, stream=stream)
+    from concurrent.futures import ThreadPoolExecutor
     gs = graphs(rank)
     dev = [torch.from_numpy(e).cuda() for e in gs]
+    # pinned host copies for the end-to-end leg (inputs and outputs)
+    host, host_out = [], []
+    for e in gs:
+        t = torch.empty(e.shape, dtype=torch.uint8, pin_memory=True)
+        t.numpy()[:] = e
+        host.append(t.numpy())
+        o = torch.empty((N, (N + 63) // 64), dtype=torch.int64, pin_memory=True)
+        host_out.append(o.numpy().view(np.uint64))
     torch.cuda.synchronize()
+    # one context and one stream per model; three host threads keep the three in flight
+    streams = [torch.cuda.Stream() for _ in gs]
+    ctxs = [dl.Context(local, stream=st_) for st_ in streams]
+    pool = ThreadPoolExecutor(max_workers=len(gs))
+    main_stream = torch.cuda.current_stream()
 
     def step(inputs, path=args.path):
+        outs = host_out if inputs is host else [None] * len(inputs)
+        return list(pool.map(lambda i: ctxs[i].tc_closure(inputs[i], path=path, out=outs[i]),
+                             range(len(inputs))))
+
+    def timed(inputs, path, k):
+        """Device time of k steps: events fork/join the per-model streams."""
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ends = [torch.cuda.Event() for _ in streams]
+        torch.cuda.synchronize()
+        ev0.record(main_stream)
+        for st_ in streams:
+            st_.wait_event(ev0)
         out = []
-        for x in inputs:
-            out.append(ctx.tc_closure(x, path=path))
-        return out
+        for _ in range(k):
+            out.extend(step(inputs, path))
+        for e_, st_ in zip(ends, streams):
+            e_.record(st_)
+            main_stream.wait_event(e_)
+        ev1.record(main_stream)
+        torch.cuda.synchronize()
+        return ev0.elapsed_time(ev1), [st for _, st in out]
 
     for _ in range(max(args.warmup, 3)):
         step(dev)
-    launches = 0
-    gemm_ms = 0.0
-    gemm_flops = 0.0
-    gemm_n = 0
-    squarings = []
     with ClockSampler(local) as clk:
         if world > 1:
             tdist.barrier()
-        torch.cuda.synchronize()
-        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        ev0.record(stream)
-        for _ in range(args.steps):
-            for _, st in step(dev):
-                launches += st["gpu_launches"]
-                gemm_ms += st["ms_gemm"]
-                gemm_flops += st["gemm_flops"]
-                gemm_n += st["gemm_launches"]
-                squarings.append(st["iters"])
-        ev1.record(stream)
-        torch.cuda.synchronize()
+        ms_total, stats = timed(dev, args.path, args.steps)
         if world > 1:
             tdist.barrier()
-        ms_total = ev0.elapsed_time(ev1)
-        # end to end through host buffers (H2D of E, D2H of bits inside the timed region)
+        # end to end through pinned host buffers (H2D of E, D2H of bits inside the timed region)
         e2e_steps = max(1, min(args.steps, 20))
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        for _ in range(e2e_steps):
-            for e in gs:
-                ctx.tc_closure(e, path=args.path)
-        torch.cuda.synchronize()
-        e2e_s = (time.perf_counter() - t0) / e2e_steps
+        step(host)
+        e2e_ms, _ = timed(host, args.path, e2e_steps)
+        e2e_s = e2e_ms * 1e-3 / e2e_steps
     clocks = clk.summary()
+    launches = sum(st["gpu_launches"] for st in stats)
+    gemm_ms = sum(st["ms_gemm"] for st in stats)
+    gemm_flops = sum(st["gemm_flops"] for st in stats)
+    gemm_n = sum(st["gemm_launches"] for st in stats)
+    squarings = [st["iters"] for st in stats]
     ms_step = ms_total / args.steps
     if world > 1:
         t = torch.tensor([ms_step, e2e_s], device="cuda", dtype=torch.float64)
@@ -343,34 +364,36 @@ def main() -> None:
     units = world * len(gs)
     value = units * flops_equiv(N) / (ms_step * 1e-3) / 1e12
     e2e_value = units * flops_equiv(N) / e2e_s / 1e12
-    gemm_share = gemm_ms / ms_total if ms_total > 0 else 0.0
+    gemm_share = gemm_ms / (ms_total * len(gs)) if ms_total > 0 else 0.0
 
     # the squarings-only FP8 path on the same graphs, for comparison and for the GEMM roofline
     pure = None
-    if rank == 0 and args.path != "bool_fp8":
-        step(dev, "bool_fp8")
+    if rank == 0 and args.path != "bool_fp8" and not args.no_compare:
+        # one context, models in sequence: every GEMM launch runs alone (burst roofline)
+        for x in dev:
+            ctxs[0].tc_closure(x, path="bool_fp8")
         k2 = max(10, args.steps // 5)
-        p_ms = p_fl = 0.0
-        p_n = 0
-        p_sq = []
+        p_stats = []
+        torch.cuda.synchronize()
         t0 = time.perf_counter()
         for _ in range(k2):
-            for _, st in step(dev, "bool_fp8"):
-                p_ms += st["ms_gemm"]
-                p_fl += st["gemm_flops"]
-                p_n += st["gemm_launches"]
-                p_sq.append(st["iters"])
+            for x in dev:
+                p_stats.append(ctxs[0].tc_closure(x, path="bool_fp8")[1])
+        torch.cuda.synchronize()
         ms2 = (time.perf_counter() - t0) / k2 * 1e3
-        pure = {"path": "bool_fp8 (tensor-core squarings only)", "ms_per_step": ms2,
+        p_ms = sum(st["ms_gemm"] for st in p_stats)
+        pure = {"path": "bool_fp8 (tensor-core squarings only), models in sequence", "ms_per_step": ms2,
                 "value": len(gs) * flops_equiv(N) / (ms2 * 1e-3) / 1e12,
-                "squarings_per_model": sorted(set(p_sq)),
-                "gemm_share_of_step": p_ms / (ms2 * k2)}
-        if gemm_n == 0 or p_n > 0:
-            gemm_ms, gemm_flops, gemm_n = p_ms, p_fl, p_n
+                "squarings_per_model": sorted(set(st["iters"] for st in p_stats)),
+                "gemm_fraction_of_step": p_ms / (ms2 * k2)}
+        gemm_ms = p_ms
+        gemm_flops = sum(st["gemm_flops"] for st in p_stats)
+        gemm_n = sum(st["gemm_launches"] for st in p_stats)
 
     fp64 = None
     mixed = None
     if not args.no_fp64 and rank == 0:
+        ctx = ctxs[0]
         _, st64 = ctx.tc_closure(dev[1], path="fp64")  # warm
         _, st64 = ctx.tc_closure(dev[1], path="fp64")
         fp64 = {"ms": st64["ms_total"], "tflops_equiv": st64["tflops_equiv"],
@@ -386,15 +409,30 @@ def main() -> None:
                            "rechecked_rows": stm["rows_rechecked"],
                            "tf32_tflops": stm["gemm_flops"] / (stm["ms_total"] * 1e-3) / 1e12}
 
+    sweep_ms = sum(st["ms_sweep"] for st in stats)
+    sweep_bytes = sum(st["sweep_bytes"] for st in stats)
+    sweep_n = sum(st["sweep_launches"] for st in stats)
     pk = peaks()
     fp8_peak = 2.0 * pk["bf16"]  # FP8 dense = 2 x BF16 dense (nominal ratio)
     achieved = (gemm_flops / (gemm_ms * 1e-3) / 1e12) if gemm_ms > 0 else 0.0
     roofline = {"bound": "tensor", "kernel": "umma_gemm_kernel<FP8,256,MN-major B,bool epilogue>",
                 "measured_in": "squarings-only FP8 run" if pure else "headline run",
                 "achieved": achieved, "peak": fp8_peak, "unit": "TFLOP/s",
-                "frac": achieved / fp8_peak, "traffic": gemm_traffic(),
+                "frac": achieved / fp8_peak, "traffic": traffic("gemm"),
                 "peak_source": f"2 x bf16_tflops of {pk['source']} MEASURED_PEAKS (burst)",
                 "gemm_launches": gemm_n, "avg_launch_ms": gemm_ms / max(gemm_n, 1)}
+    roofline_sweep = None
+    if sweep_ms > 0:
+        ach = sweep_bytes / (sweep_ms * 1e-3) / 1e9
+        roofline_sweep = {"bound": "hbm", "kernel": "bit sweeps (sweep_rows_step / sweep_units_step + final E M)",
+                          "achieved": ach, "peak": pk["hbm"], "unit": "GB/s", "frac": ach / pk["hbm"],
+                          "bytes_definition": "CSR of E + one read of every bit-matrix row per sweep (minimum)",
+                          "launches": sweep_n, "traffic": traffic("sweep"),
+                          "share_of_busy_time": sweep_ms / (ms_total * len(gs)) if ms_total else None}
+    # the headline's dominant kernel by device time
+    dominant = roofline
+    if roofline_sweep and sweep_ms > gemm_share * ms_total * len(gs):
+        dominant = roofline_sweep
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "e4m3 (0/1, FP32 accumulate)",
@@ -402,13 +440,16 @@ def main() -> None:
             "config": {"workload": "TC ER N=8192 x p in {1e-4,1e-3,1e-2}, seeds 2/3/4 (+1000*rank)",
                        "path": args.path, "l2": "inputs 3 x 64 MiB > L2, cycled each step",
                        "squarings_per_model": sorted(set(squarings)),
-                       "gemm_share_of_step": gemm_share},
+                       "concurrency": f"{len(gs)} models in flight (one context and stream each)",
+                       "gemm_busy_fraction": gemm_share},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": len(gs) * N * N,
                     "d2h_bytes_per_step": len(gs) * N * ((N + 63) // 64) * 8},
-            "gpu_launches": launches, "roofline": roofline, "clocks": clocks}
+            "gpu_launches": launches, "roofline": dominant, "roofline_gemm": roofline,
+            "roofline_sweep": roofline_sweep,
+            "clocks": clocks}
     if not args.no_extra and rank == 0:
-        line["same_generation"] = bench_sg(ctx, torch)
-        line["batch"] = bench_batch(ctx, torch)
+        line["same_generation"] = bench_sg(ctxs[0], torch)
+        line["batch"] = bench_batch(ctxs[0], torch)
         line["serving"] = bench_serving(dl, torch, local, args.serve_seconds)
     if pure:
         line["bool_fp8_path"] = pure
@@ -421,7 +462,8 @@ def main() -> None:
         line["cpu_baseline"] = cpu_baseline(gs)
     if rank == 0:
         print(json.dumps(line), flush=True)
-    ctx.close()
+    for c in ctxs:
+        c.close()
     if world > 1:
         tdist.destroy_process_group()
 

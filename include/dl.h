@@ -100,6 +100,10 @@ typedef struct {
     double gemm_flops;       /* 2*M*N*K summed over those GEMM launches (padded sizes) */
     double ms_queue;         /* serving: dl_submit -> admission to the GPU (host clock), ms */
     double ms_latency;       /* serving: dl_submit -> completion (host clock), ms */
+    int32_t sweep_launches;  /* bit-sweep kernels (AUTO path: Iteration steps and the final E M) */
+    double ms_sweep;         /* their summed device time (CUDA events on the launching stream) */
+    double sweep_bytes;      /* bytes every one of those sweeps must read at least: the CSR of E
+                                and each row of the bit matrix once */
 } dl_stats;
 
 /* Create a context on CUDA device `device` (cfg may be NULL for defaults).  Fails with

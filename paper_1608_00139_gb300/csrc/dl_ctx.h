@@ -38,6 +38,7 @@ struct Workspace {
     cudaEvent_t ev[8] = {};
     static constexpr int kGemmEvents = 128;  // start/stop pairs of timed GEMM launches
     cudaEvent_t gev[kGemmEvents] = {};
+    cudaEvent_t sev[kGemmEvents] = {};       // start/stop pairs of timed sweep groups
     bool ready = false;
     BatchPlan *batch_plan = nullptr;
 

@@ -50,6 +50,36 @@ struct Timer {
     }
 };
 
+// Start/stop events around each group of sweep launches, on the launching stream.
+struct SweepClock {
+    Workspace &ws;
+    cudaStream_t s;
+    int k = 0, launches = 0;
+    double bytes = 0.0;
+    void start() {
+        if (2 * k + 1 < Workspace::kGemmEvents) cudaEventRecord(ws.sev[2 * k], s);
+    }
+    void stop(int count, double bytes_each) {
+        if (2 * k + 1 < Workspace::kGemmEvents) {
+            cudaEventRecord(ws.sev[2 * k + 1], s);
+            ++k;
+        }
+        launches += count;
+        bytes += count * bytes_each;
+    }
+    void fill(dl_stats *st) const {  // valid once the stream has been synchronised
+        double t = 0.0;
+        for (int i = 0; i < k; ++i) {
+            float x = 0.f;
+            cudaEventElapsedTime(&x, ws.sev[2 * i], ws.sev[2 * i + 1]);
+            t += x;
+        }
+        st->sweep_launches = launches;
+        st->ms_sweep = t;
+        st->sweep_bytes = bytes;
+    }
+};
+
 // Start/stop events around each tensor-core GEMM launch, on the launching stream.
 struct GemmClock {
     Workspace &ws;
@@ -396,6 +426,9 @@ dl_status tc_auto(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &a
     const int tiles = probs[0].tiles_m * probs[0].tiles_n;
     const int grid = std::min(tiles, ctx->sms);
     GemmClock gc{ws, s};
+    SweepClock sc{ws, s};
+    // bytes a sweep reads at least: the CSR of E and every row of the bit matrix once
+    const double sweep_min_bytes = 4.0 * (static_cast<double>(nnz) + n + 1) + static_cast<double>(n) * wp * 8.0;
     const int max_squarings = 2 + static_cast<int>(std::ceil(std::log2(static_cast<double>(np) + 1.0)));
     const int max_sweeps = static_cast<int>(std::min<int64_t>(2 * static_cast<int64_t>(n) + 16, 1 << 20));
     int cur = 0, squarings = 0, sweeps = 0;
@@ -435,9 +468,11 @@ dl_status tc_auto(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &a
         // are dense and saturate within a few successors, so a short group is cheap)
         const int g = std::max(1, std::min(squarings == 0 ? 16 : 4, sweep_budget - since_square));
         CK(cudaMemsetAsync(vslot, 0, sizeof(unsigned long long) * g, s));
+        sc.start();
         for (int k = 0; k < g; ++k)
             CK(bits_sweep_csr(ptr, col, uoff, n, rbits, rbits, wp, 1, vslot + k, nullptr, &launches, s,
                               static_cast<int>(dmax)));
+        sc.stop(g, sweep_min_bytes);
         sweeps += g;
         since_square += g;
         if ((rc = read_scalars(ws, s))) return rc;
@@ -455,7 +490,9 @@ dl_status tc_auto(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &a
     tm.mark(2);
     // model E M, checking M = min1(I + E M) on the way
     CK(cudaMemsetAsync(ws.scal + SC_VIOL, 0, 2 * sizeof(unsigned long long), s));
+    sc.start();
     CK(bits_sweep_csr(ptr, col, uoff, n, rbits, mbits, wp, 0, ws.scal + SC_VIOL, ws.scal + SC_ONES, &launches, s, static_cast<int>(dmax)));
+    sc.stop(1, sweep_min_bytes);
     if ((rc = write_bits(s, mbits, wp, a.out_bits, n, a.mem))) return rc;
     if ((rc = read_scalars(ws, s))) return rc;
     if (host_scal(ws)[SC_VIOL] != 0) {
@@ -470,6 +507,7 @@ dl_status tc_auto(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &a
         st->iters = squarings;
         st->recheck_sweeps = sweeps + 1;
         gc.fill(st);
+        sc.fill(st);
         st->model_ones = static_cast<int64_t>(host_scal(ws)[SC_ONES]);
         st->ms_factor = tm.ms(0, 1);
         st->ms_solve = tm.ms(1, 2);
@@ -852,6 +890,8 @@ cudaError_t Workspace::init() {
         if ((e = cudaEventCreate(&x)) != cudaSuccess) return e;
     for (auto &x : gev)
         if ((e = cudaEventCreate(&x)) != cudaSuccess) return e;
+    for (auto &x : sev)
+        if ((e = cudaEventCreate(&x)) != cudaSuccess) return e;
     ready = true;
     return cudaSuccess;
 }
@@ -868,6 +908,8 @@ void Workspace::release() {
     for (auto &x : ev)
         if (x) cudaEventDestroy(x);
     for (auto &x : gev)
+        if (x) cudaEventDestroy(x);
+    for (auto &x : sev)
         if (x) cudaEventDestroy(x);
     host_pinned = nullptr;
     status = nullptr;

@@ -54,7 +54,9 @@ class Stats(ctypes.Structure):
                 ("ms_epilogue", ctypes.c_double), ("tflops_equiv", ctypes.c_double),
                 ("gpu_launches", ctypes.c_int32), ("gemm_launches", ctypes.c_int32),
                 ("ms_gemm", ctypes.c_double), ("gemm_flops", ctypes.c_double),
-                ("ms_queue", ctypes.c_double), ("ms_latency", ctypes.c_double)]
+                ("ms_queue", ctypes.c_double), ("ms_latency", ctypes.c_double),
+                ("sweep_launches", ctypes.c_int32), ("ms_sweep", ctypes.c_double),
+                ("sweep_bytes", ctypes.c_double)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -183,10 +185,19 @@ class Context:
         _check(lib().dl_set_stream(self._h, ctypes.c_void_p(raw or 0)))
 
     def tc_closure(self, E, eps: float = 0.0, thr: float = 0.0, path: str = "auto",
-                   rtilde: bool = False):
-        """Least model of the closure program; returns (bits, stats[, R~])."""
+                   rtilde: bool = False, out=None):
+        """Least model of the closure program; returns (bits, stats[, R~]).
+
+        ``out``: optional preallocated output (same memory kind as E, n x ceil(n/64) 64-bit
+        words, e.g. a pinned numpy array), written in place."""
         p, n, mem, keep = _square_u8(E)
-        bits, bp = _alloc_bits(n, mem, keep)
+        if out is None:
+            bits, bp = _alloc_bits(n, mem, keep)
+        else:
+            if tuple(out.shape) != (n, words(n)):
+                raise ValueError("out must have shape (n, ceil(n/64))")
+            bits = out
+            bp = out.data_ptr() if _is_torch(out) else out.ctypes.data
         rt, rp = None, None
         if rtilde:
             if mem == DL_MEM_DEVICE:
