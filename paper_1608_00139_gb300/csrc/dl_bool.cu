@@ -139,106 +139,125 @@ __device__ __forceinline__ bool or_unit(const int *__restrict__ col, int q0, int
     return __any_sync(0xffffffffu, changed);
 }
 
-// Row-direct variants for graphs whose rows all fit one unit (max out-degree <= kUnit): one
-// warp per row, no unit search, plain stores (the warp is the row's only writer).
+// Row-direct variants (used when every row has at most kRowDirect successors): one warp per
+// row, lanes own WPL words each (the whole row in one pass, wp <= 32 * WPL), successor rows
+// loaded two at a time, stop as soon as the row is full, plain stores (the warp is the row's
+// only writer).
+constexpr int kRowDirect = 256;
+
+template <int WPL>
+__device__ __forceinline__ void full_mask(int n, int64_t wp, int lane, uint64_t (&full)[WPL]) {
+#pragma unroll
+    for (int q = 0; q < WPL; ++q) {
+        const int64_t w = lane + 32 * q;
+        const int64_t lo = w * 64;
+        full[q] = (w >= wp || lo >= n) ? 0ull : (n - lo >= 64 ? ~0ull : ((1ull << (n - lo)) - 1ull));
+    }
+}
+
+// acc |= rows k (and, if with_self, bit k) for the successors [q0, q1), stopping when full.
+template <int WPL>
+__device__ __forceinline__ void or_successors(const int *__restrict__ col, int q0, int q1, const uint64_t *M,
+                                              int64_t wp, int lane, bool with_self, const uint64_t (&full)[WPL],
+                                              uint64_t (&acc)[WPL]) {
+    int qq = q0;
+    for (; qq + 1 < q1; qq += 2) {
+        const int k1 = col[qq], k2 = col[qq + 1];
+        const uint64_t *m1 = M + static_cast<int64_t>(k1) * wp;
+        const uint64_t *m2 = M + static_cast<int64_t>(k2) * wp;
+        uint64_t a[WPL], b[WPL];
+#pragma unroll
+        for (int q = 0; q < WPL; ++q) {
+            const int64_t w = lane + 32 * q;
+            a[q] = w < wp ? m1[w] : 0ull;
+            b[q] = w < wp ? m2[w] : 0ull;
+        }
+        bool mine = true;
+#pragma unroll
+        for (int q = 0; q < WPL; ++q) {
+            const int64_t w = lane + 32 * q;
+            acc[q] |= a[q] | b[q];
+            if (with_self) {
+                if (w == (k1 >> 6)) acc[q] |= 1ull << (k1 & 63);
+                if (w == (k2 >> 6)) acc[q] |= 1ull << (k2 & 63);
+            }
+            mine &= acc[q] == full[q];
+        }
+        if (__all_sync(0xffffffffu, mine)) return;
+    }
+    if (qq < q1) {
+        const int k = col[qq];
+        const uint64_t *m = M + static_cast<int64_t>(k) * wp;
+#pragma unroll
+        for (int q = 0; q < WPL; ++q) {
+            const int64_t w = lane + 32 * q;
+            if (w < wp) acc[q] |= m[w];
+            if (with_self && w == (k >> 6)) acc[q] |= 1ull << (k & 63);
+        }
+    }
+}
+
 // mode 1 (in place): M_i |= E_i | OR_{k in succ(i)} M_k; counts changed rows.
+template <int WPL>
 __global__ void __launch_bounds__(256)
     sweep_rows_step_kernel(const int *__restrict__ ptr, const int *__restrict__ col, int n, uint64_t *M, int64_t wp,
                            unsigned long long *changed_rows) {
     const int lane = threadIdx.x & 31;
     const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (i >= n || ptr[i + 1] == ptr[i]) return;
-    const bool single = wp <= 32 * kSweepWpl;
+    if (i >= n) return;
+    const int q0 = ptr[i], q1 = ptr[i + 1];
+    if (q0 == q1) return;
     uint64_t *mrow = M + static_cast<int64_t>(i) * wp;
+    uint64_t full[WPL], acc[WPL];
+    full_mask<WPL>(n, wp, lane, full);
+    bool mine = true;
+#pragma unroll
+    for (int q = 0; q < WPL; ++q) {
+        const int64_t w = lane + 32 * q;
+        acc[q] = w < wp ? mrow[w] : 0ull;
+        mine &= acc[q] == full[q];
+    }
+    if (__all_sync(0xffffffffu, mine)) return;  // already full
+    uint64_t before[WPL];
+#pragma unroll
+    for (int q = 0; q < WPL; ++q) before[q] = acc[q];
+    or_successors<WPL>(col, q0, q1, M, wp, lane, true, full, acc);
     bool changed = false;
-    for (int64_t w0 = 0; w0 < wp; w0 += 32 * kSweepWpl) {
-        uint64_t acc[kSweepWpl], full[kSweepWpl];
-        bool mine = true;
 #pragma unroll
-        for (int q = 0; q < kSweepWpl; ++q) {
-            const int64_t w = w0 + lane + 32 * q;
-            const int64_t lo = w * 64;
-            full[q] = (w >= wp || lo >= n) ? 0ull : (n - lo >= 64 ? ~0ull : ((1ull << (n - lo)) - 1ull));
-            acc[q] = w < wp ? mrow[w] : 0ull;
-            mine &= acc[q] == full[q];
-        }
-        uint64_t old[kSweepWpl];
-#pragma unroll
-        for (int q = 0; q < kSweepWpl; ++q) old[q] = acc[q];
-        bool sat = single && __all_sync(0xffffffffu, mine);
-        for (int qq = ptr[i]; qq < ptr[i + 1] && !sat; ++qq) {
-            const int k = col[qq];
-            const uint64_t *mk = M + static_cast<int64_t>(k) * wp;
-            mine = true;
-#pragma unroll
-            for (int q = 0; q < kSweepWpl; ++q) {
-                const int64_t w = w0 + lane + 32 * q;
-                if (w < wp) acc[q] |= mk[w];
-            }
-            const int64_t rel = (k >> 6) - w0;
-            if (rel >= 0 && rel < 32 * kSweepWpl && (rel & 31) == lane) {
-                const int qk = static_cast<int>(rel >> 5);
-#pragma unroll
-                for (int q = 0; q < kSweepWpl; ++q)
-                    if (q == qk) acc[q] |= 1ull << (k & 63);
-            }
-#pragma unroll
-            for (int q = 0; q < kSweepWpl; ++q) mine &= acc[q] == full[q];
-            sat = single && __all_sync(0xffffffffu, mine);
-        }
-#pragma unroll
-        for (int q = 0; q < kSweepWpl; ++q) {
-            const int64_t w = w0 + lane + 32 * q;
-            if (w < wp && acc[q] != old[q]) {
-                mrow[w] = acc[q];
-                changed = true;
-            }
+    for (int q = 0; q < WPL; ++q) {
+        const int64_t w = lane + 32 * q;
+        if (w < wp && acc[q] != before[q]) {
+            mrow[w] = acc[q];
+            changed = true;
         }
     }
     if (__any_sync(0xffffffffu, changed) && lane == 0) atomicAdd(changed_rows, 1ull);
 }
 
 // mode 0: out_i = OR_{k in succ(i)} M_k; violation iff (out_i | e_i) != M_i; ones of out.
+template <int WPL>
 __global__ void __launch_bounds__(256)
     sweep_rows_emit_kernel(const int *__restrict__ ptr, const int *__restrict__ col, int n, const uint64_t *M,
                            uint64_t *out, int64_t wp, unsigned long long *violations, unsigned long long *ones) {
     const int lane = threadIdx.x & 31;
     const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (i >= n) return;
-    const bool single = wp <= 32 * kSweepWpl;
+    uint64_t full[WPL], acc[WPL];
+    full_mask<WPL>(n, wp, lane, full);
+#pragma unroll
+    for (int q = 0; q < WPL; ++q) acc[q] = 0ull;
+    or_successors<WPL>(col, ptr[i], ptr[i + 1], M, wp, lane, false, full, acc);
     const uint64_t *mrow = M + static_cast<int64_t>(i) * wp;
     bool viol = false;
     uint32_t cnt = 0;
-    for (int64_t w0 = 0; w0 < wp; w0 += 32 * kSweepWpl) {
-        uint64_t acc[kSweepWpl], full[kSweepWpl];
 #pragma unroll
-        for (int q = 0; q < kSweepWpl; ++q) {
-            const int64_t w = w0 + lane + 32 * q;
-            const int64_t lo = w * 64;
-            full[q] = (w >= wp || lo >= n) ? 0ull : (n - lo >= 64 ? ~0ull : ((1ull << (n - lo)) - 1ull));
-            acc[q] = 0ull;
-        }
-        bool sat = false;
-        for (int qq = ptr[i]; qq < ptr[i + 1] && !sat; ++qq) {
-            const uint64_t *mk = M + static_cast<int64_t>(col[qq]) * wp;
-            bool mine = true;
-#pragma unroll
-            for (int q = 0; q < kSweepWpl; ++q) {
-                const int64_t w = w0 + lane + 32 * q;
-                if (w < wp) acc[q] |= mk[w];
-                mine &= acc[q] == full[q];
-            }
-            sat = single && __all_sync(0xffffffffu, mine);
-        }
-#pragma unroll
-        for (int q = 0; q < kSweepWpl; ++q) {
-            const int64_t w = w0 + lane + 32 * q;
-            if (w >= wp) continue;
-            const uint64_t self = (w == (i >> 6)) ? (1ull << (i & 63)) : 0ull;
-            if ((acc[q] | self) != mrow[w]) viol = true;
-            out[static_cast<int64_t>(i) * wp + w] = acc[q];
-            cnt += __popcll(acc[q]);
-        }
+    for (int q = 0; q < WPL; ++q) {
+        const int64_t w = lane + 32 * q;
+        if (w >= wp) continue;
+        const uint64_t self = (w == (i >> 6)) ? (1ull << (i & 63)) : 0ull;
+        if ((acc[q] | self) != mrow[w]) viol = true;
+        out[static_cast<int64_t>(i) * wp + w] = acc[q];
+        cnt += __popcll(acc[q]);
     }
     const bool any = __any_sync(0xffffffffu, viol);
 #pragma unroll
@@ -247,6 +266,17 @@ __global__ void __launch_bounds__(256)
         if (any) atomicAdd(violations, 1ull);
         if (ones && cnt) atomicAdd(ones, static_cast<unsigned long long>(cnt));
     }
+}
+
+template <int WPL>
+cudaError_t launch_rows(const int *ptr, const int *col, int n, const uint64_t *M, uint64_t *out, int64_t wp,
+                        int mode, unsigned long long *violations, unsigned long long *ones, cudaStream_t s) {
+    if (mode == 1)
+        sweep_rows_step_kernel<WPL><<<(n + 7) / 8, 256, 0, s>>>(ptr, col, n, const_cast<uint64_t *>(M), wp,
+                                                                 violations);
+    else
+        sweep_rows_emit_kernel<WPL><<<(n + 7) / 8, 256, 0, s>>>(ptr, col, n, M, out, wp, violations, ones);
+    return cudaGetLastError();
 }
 
 // mode 1 (closure step, in place): M_i |= E_i | OR_{k in succ(i)} M_k; counts changed units.
@@ -348,14 +378,11 @@ cudaError_t bits_sweep_csr(const int *ptr, const int *col, const int *unit_off, 
                            uint64_t *out, int64_t wp, int mode, unsigned long long *violations,
                            unsigned long long *ones, int *launches, cudaStream_t s, int max_deg) {
     if (n <= 0) return cudaSuccess;
-    if (max_deg >= 0 && max_deg <= kUnit) {  // every row is one unit: row-direct kernels
-        if (mode == 1)
-            sweep_rows_step_kernel<<<(n + 7) / 8, 256, 0, s>>>(ptr, col, n, const_cast<uint64_t *>(M), wp,
-                                                                violations);
-        else
-            sweep_rows_emit_kernel<<<(n + 7) / 8, 256, 0, s>>>(ptr, col, n, M, out, wp, violations, ones);
+    if (max_deg >= 0 && max_deg <= kRowDirect && wp <= 256) {  // no heavy rows: row-direct kernels
         if (launches) *launches += 1;
-        return cudaGetLastError();
+        if (wp <= 64) return launch_rows<2>(ptr, col, n, M, out, wp, mode, violations, ones, s);
+        if (wp <= 128) return launch_rows<4>(ptr, col, n, M, out, wp, mode, violations, ones, s);
+        return launch_rows<8>(ptr, col, n, M, out, wp, mode, violations, ones, s);
     }
     const unsigned grid = static_cast<unsigned>(num_sms() * 8);
     if (mode == 1) {

@@ -105,7 +105,7 @@ cudaError_t bits_sweep(const uint8_t *E, int64_t lde, int n, const uint64_t *M, 
 // of scratch) once per CSR.  mode 1: in place (out must be M), *violations += changed units;
 // mode 0: out = E M (rows < n), *violations += rows with (out_i | e_i) != M_i, *ones += ones.
 cudaError_t sweep_units(const int *ptr, int n, int *cnt, int *unit_off, cudaStream_t s);
-// max_deg: ||E||_inf if known (rows of at most 64 successors take row-direct kernels), or -1.
+// max_deg: ||E||_inf if known (rows of at most 256 successors take row-direct kernels), or -1.
 cudaError_t bits_sweep_csr(const int *ptr, const int *col, const int *unit_off, int n, const uint64_t *M,
                            uint64_t *out, int64_t wp, int mode, unsigned long long *violations,
                            unsigned long long *ones, int *launches, cudaStream_t s, int max_deg);
