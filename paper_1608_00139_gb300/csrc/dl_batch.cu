@@ -1,15 +1,20 @@
 // dl_batch.cu -- many independent closure problems of uneven size in one call (dl_tc_batch).
 //
-// Every instance k runs the FP8 closure of dl_solve.cu (C_0 = I + E_k, C_{t+1} = min1(C_t^2),
-// certificate C = min1(I + E C), model E C*), but all instances advance together in rounds:
-//   round r:  one persistent grouped tcgen05 launch squares every still-active instance
-//             (finished instances are gated off inside the kernel), a decide kernel marks
-//             instances whose squaring added nothing, one batched sweep checks the
-//             certificate of the others (and emits the model), a second decide kernel
-//             retires instances whose certificate held.
-// All decisions live on the device, so the rounds need no host round trip: the whole
-// schedule (ingest + R rounds + copy-out) is captured once into a CUDA graph and launched
-// as one unit; a repeated call on the same buffers relaunches the cached graph.
+// Every instance k gets the AUTO closure of dl_solve.cu (Iteration steps on bits, with
+// repeated squaring of the reflexive closure for the instances that keep changing), but all
+// instances advance together and every decision is taken on the device:
+//   1. (every call) one pass over all inputs packs the bits of I + E_k, checks that every
+//      byte is 0/1 and counts successors; a scan gives one CSR over all instances' rows.
+//   2. (captured CUDA graph) fill the CSR column indices from the packed bits; 24 batched
+//      in-place sweeps M <- M | E | E M; an instance whose sweep changes nothing holds its
+//      reflexive closure and leaves the active list.  Then rounds for the instances still
+//      active: their bits become e4m3 operands, one persistent grouped tcgen05 launch squares
+//      exactly those instances (a tile schedule written on the device), 4 more sweeps.
+//      Finally the model E_k C_k* of every instance with its certificate C = min1(I + E C).
+// After every sweep a single-CTA kernel rebuilds the list of active instances (their rows,
+// padded rows and GEMM tiles as prefix sums), so that later kernels touch only live rows and
+// a round with nothing left active costs a few empty launches.  The graph is cached and
+// relaunched while the inputs and outputs stay the same buffers.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -20,125 +25,440 @@
 
 #include "dl_ctx.h"
 #include "dl_internal.h"
-#include "dl_ptx.cuh"
-#include "dl_rows.cuh"
 
 namespace dl {
 
 namespace {
 
+constexpr unsigned kFull = 0xffffffffu;
 enum : int { B_ACTIVE = 0, B_EMIT = 1, B_DONE = 2 };
+constexpr int kFirstSweeps = 24;  // sweeps before any squaring
+constexpr int kRoundSweeps = 4;   // sweeps after each squaring round
+constexpr int kChunk = 32;        // rows a warp claims at a time in the row kernels
+constexpr int kListThreads = 1024;
 
 struct BatchInst {
-    const uint8_t *E;  // n x n input on the device
-    uint8_t *c0, *c1;  // ping-pong e4m3 operands, np x np
-    uint64_t *rbits;   // bits of the latest C_t, np x wp
-    uint64_t *mbits;   // model bits, np x wp
-    uint64_t *out;     // user output (device memory) or null
+    const uint8_t *E;  // n x n input bytes on the device (row stride n)
+    uint8_t *c0;       // e4m3 operand, np x np
+    uint64_t *rbits;   // reflexive-closure candidate M, np x wp
+    uint64_t *mbits;   // model bits, np x wp (host outputs are copied from here)
+    uint64_t *out;     // user output (device memory, n rows of ceil(n/64) words) or null
     int32_t n, np;
-    int64_t wp;
-    int64_t prow0;  // first padded row of this instance in the global padded-row order
-    int64_t row0;   // first real row in the global real-row order
+    int32_t wp;
+    int32_t tiles;  // GEMM tiles of the squaring
+    int32_t prow0;  // first padded row in the order of all instances
+    int32_t row0;   // first real row in the order of all instances
 };
 
-// Per-instance device counters, laid out as arrays of `count` entries.
+// Per-instance counters (arrays of `count` entries) and the active-instance counter.
 struct BatchCounters {
     int *state;
-    unsigned long long *cnt_new, *cnt_old, *viol, *ones, *squarings;
+    unsigned long long *chg, *viol, *ones, *squarings, *sweeps;
+};
+constexpr int kCounterArrays = 5;
+
+// The instances in one state, as prefix sums over the selected instances.
+//   hdr[0] entries A, hdr[1] rows, hdr[2] padded rows, hdr[3] tiles, hdr[4] chunk counter
+//   k[j] instance of entry j; row[j], prow[j] exclusive prefixes (A + 1 entries)
+//   sched: the GEMM schedule (see gemm_launch) over the same entries
+struct BatchList {
+    int *hdr;
+    int *k, *row, *prow;
+    int *sched;
 };
 
-__device__ __forceinline__ int find_by_prow(const BatchInst *inst, int count, int64_t g) {
+__device__ __forceinline__ int last_le(const int *pre, int count, int x) {  // largest j: pre[j] <= x
     int lo = 0, hi = count - 1;
     while (lo < hi) {
         const int mid = (lo + hi + 1) >> 1;
-        if (inst[mid].prow0 <= g) lo = mid;
+        if (pre[mid] <= x) lo = mid;
         else hi = mid - 1;
     }
     return lo;
 }
 
-__device__ __forceinline__ int find_by_row(const BatchInst *inst, int count, int64_t g) {
-    int lo = 0, hi = count - 1;
-    while (lo < hi) {
-        const int mid = (lo + hi + 1) >> 1;
-        if (inst[mid].row0 <= g) lo = mid;
-        else hi = mid - 1;
-    }
-    return lo;
+// Padded row -> instance, rebuilt every call (one CTA per instance).
+__global__ void batch_map_kernel(const BatchInst *__restrict__ inst, int *pinst) {
+    const BatchInst I = inst[blockIdx.x];
+    for (int r = threadIdx.x; r < I.np; r += blockDim.x) pinst[I.prow0 + r] = blockIdx.x;
 }
 
-__global__ void __launch_bounds__(256)
-    ingest_batch_kernel(const BatchInst *__restrict__ inst, int count, BatchCounters c, int *status) {
-    const int64_t g = blockIdx.x;
-    const int k = find_by_prow(inst, count, g);
-    const BatchInst I = inst[k];
-    const int r = static_cast<int>(g - I.prow0);
-    uint32_t sum = 0, bad = 0, extra = 0;
-    ingest_row(I.E, I.n, I.np, I.c0, 1, r, sum, bad, extra);
-    block_reduce_sum_or(sum, bad);
-    if (threadIdx.x == 0) {
-        if (bad) atomicOr(status, ST_BAD_INPUT);
-        if (sum + extra) atomicAdd(&c.cnt_old[k], static_cast<unsigned long long>(sum + extra));
-    }
+// Low bits of the four bytes of x as a 4-bit mask (byte b -> bit b).
+__device__ __forceinline__ uint32_t byte_lsbs(uint32_t x) { return ((x & 0x01010101u) * 0x01020408u) >> 24; }
+// Bytes of x with any of bits 1..7 set, as a 4-bit mask.
+__device__ __forceinline__ uint32_t byte_bad(uint32_t x) {
+    const uint32_t t = (x >> 1) & 0x7F7F7F7Fu;
+    return byte_lsbs(((t + 0x7F7F7F7Fu) | t) >> 7);
 }
 
+// Bits of row r of I + E_k into M (one warp per padded row), the row's successor count and
+// the 0/1 check.  The row is read as aligned 16-byte chunks; lane L of segment s holds the
+// 64 bytes that start 64 (32 s + L) bytes after the aligned address below the row, and the
+// model words are those 64-bit groups shifted by the row's misalignment.
 __global__ void __launch_bounds__(256)
-    sweep_batch_kernel(const BatchInst *__restrict__ inst, int count, int64_t total_rows, BatchCounters c) {
+    batch_pack_kernel(const BatchInst *__restrict__ inst, const int *__restrict__ pinst, int total_prows,
+                      int *cnt, int *status) {
     const int lane = threadIdx.x & 31;
-    const int64_t g = static_cast<int64_t>(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (g >= total_rows) return;
-    const int k = find_by_row(inst, count, g);
-    const int st = c.state[k];
-    if (st == B_DONE) return;
-    if (st == B_ACTIVE && warp_read_u64(&c.viol[k]) != 0ull) return;  // certificate already failed
-    const BatchInst I = inst[k];
-    const int r = static_cast<int>(g - I.row0);
-    bool viol = false;
-    uint32_t cnt = 0;
-    sweep_row(I.E + static_cast<int64_t>(r) * I.n, I.n, I.rbits, I.mbits, I.wp, 0, r, lane, viol, cnt);
+    const int g = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (g >= total_prows) return;
+    const BatchInst I = inst[pinst[g]];
+    const int r = g - I.prow0;
+    uint64_t *row = I.rbits + static_cast<int64_t>(r) * I.wp;
+    const int idw = r >> 6;
+    const uint64_t idb = 1ull << (r & 63);
+    if (r >= I.n) {  // padding: identity only
+        for (int w = lane; w < I.wp; w += 32) row[w] = w == idw ? idb : 0ull;
+        return;
+    }
+    const uint8_t *a = I.E + static_cast<int64_t>(r) * I.n;
+    const int off = static_cast<int>(reinterpret_cast<uintptr_t>(a) & 15);
+    const uint8_t *base = a - off;
+    const int lim = off + I.n;  // bytes of the row occupy [off, lim) from base
+    const int nseg = I.wp / 32 + 1;
+    uint32_t bad = 0;
+    int c = 0;
+    uint64_t carry = 0;
+    auto shifted = [off](uint64_t lo, uint64_t hi) { return off ? (lo >> off) | (hi << (64 - off)) : lo; };
+    for (int sg = 0; sg < nseg; ++sg) {
+        const int u = 32 * sg + lane;
+        uint64_t vw = 0;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int v0 = 64 * u + 16 * j;
+            if (v0 < lim) {
+                const uint4 x = *reinterpret_cast<const uint4 *>(base + v0);
+                const int lo = max(0, off - v0), hi = min(16, lim - v0);
+                const uint32_t valid = ((1u << hi) - 1u) & ~((1u << lo) - 1u);
+                const uint32_t m = byte_lsbs(x.x) | (byte_lsbs(x.y) << 4) | (byte_lsbs(x.z) << 8) |
+                                   (byte_lsbs(x.w) << 12);
+                const uint32_t b = byte_bad(x.x) | (byte_bad(x.y) << 4) | (byte_bad(x.z) << 8) |
+                                   (byte_bad(x.w) << 12);
+                vw |= static_cast<uint64_t>(m & valid) << (16 * j);
+                bad |= b & valid;
+            }
+        }
+        c += __popcll(vw);
+        const uint64_t nxt = __shfl_down_sync(kFull, vw, 1);
+        const uint64_t first = __shfl_sync(kFull, vw, 0);
+        if (sg > 0 && lane == 31) {
+            const int w = 32 * (sg - 1) + 31;
+            if (w < I.wp) row[w] = shifted(carry, first) | (w == idw ? idb : 0ull);
+        }
+        if (lane < 31) {
+            const int w = 32 * sg + lane;
+            if (w < I.wp) row[w] = shifted(vw, nxt) | (w == idw ? idb : 0ull);
+        }
+        carry = vw;
+    }
+    if (lane == 31) {
+        const int w = 32 * (nseg - 1) + 31;
+        if (w < I.wp) row[w] = shifted(carry, 0ull) | (w == idw ? idb : 0ull);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        c += __shfl_xor_sync(kFull, c, o);
+        bad |= __shfl_xor_sync(kFull, bad, o);
+    }
     if (lane == 0) {
-        if (viol) atomicAdd(&c.viol[k], 1ull);
-        if (cnt) atomicAdd(&c.ones[k], static_cast<unsigned long long>(cnt));
+        cnt[I.row0 + r] = c;
+        if (bad) atomicOr(status, ST_BAD_INPUT);
     }
 }
 
-// After a squaring: an active instance whose count of ones did not grow has reached its
-// reflexive closure (it only needs the model emitted); the others record their new count.
-__global__ void decide_after_square(int count, BatchCounters c) {
-    const int k = blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= count || c.state[k] != B_ACTIVE) return;
-    c.squarings[k] += 1;
-    if (c.cnt_new[k] == c.cnt_old[k]) c.state[k] = B_EMIT;
-    else c.cnt_old[k] = c.cnt_new[k];
-    c.cnt_new[k] = 0;
+// Successor lists from the packed bits (one warp per padded row, real rows only).  The
+// identity bit belongs to E only when E has the self-loop: then the packed row holds exactly
+// the row's count of ones.
+__global__ void __launch_bounds__(256)
+    batch_fill_kernel(const BatchInst *__restrict__ inst, const int *__restrict__ pinst, int total_prows,
+                      const int *__restrict__ ptr, int *col) {
+    const int lane = threadIdx.x & 31;
+    const int g = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (g >= total_prows) return;
+    const BatchInst I = inst[pinst[g]];
+    const int r = g - I.prow0;
+    if (r >= I.n) return;
+    const uint64_t *row = I.rbits + static_cast<int64_t>(r) * I.wp;
+    const int gr = I.row0 + r;
+    int ones = 0;
+    for (int w = lane; w < I.wp; w += 32) ones += __popcll(row[w]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) ones += __shfl_xor_sync(kFull, ones, o);
+    int pos = ptr[gr];
+    const bool self = ones == ptr[gr + 1] - pos;
+    for (int w0 = 0; w0 < I.wp; w0 += 32) {
+        const int w = w0 + lane;
+        uint64_t x = w < I.wp ? row[w] : 0ull;
+        if (!self && w == (r >> 6)) x &= ~(1ull << (r & 63));
+        const int c = __popcll(x);
+        int inc = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(kFull, inc, o);
+            if (lane >= o) inc += t;
+        }
+        int p = pos + inc - c;
+        while (x) {
+            const int b = __ffsll(static_cast<long long>(x)) - 1;
+            x &= x - 1;
+            col[p++] = 64 * w + b;
+        }
+        pos += __shfl_sync(kFull, inc, 31);
+    }
 }
 
-// After the sweep: a certificate that held, or an emission, retires the instance.
-__global__ void decide_after_sweep(int count, BatchCounters c, int *status) {
+// Block-wide exclusive scan of four counters at once (kListThreads threads).
+__device__ __forceinline__ int4 block_scan4(int4 v, int4 *total) {
+    __shared__ int4 part[kListThreads / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    int4 inc = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int a = __shfl_up_sync(kFull, inc.x, o), b = __shfl_up_sync(kFull, inc.y, o);
+        const int c = __shfl_up_sync(kFull, inc.z, o), d = __shfl_up_sync(kFull, inc.w, o);
+        if (lane >= o) inc = make_int4(inc.x + a, inc.y + b, inc.z + c, inc.w + d);
+    }
+    if (lane == 31) part[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        int4 p = part[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int a = __shfl_up_sync(kFull, p.x, o), b = __shfl_up_sync(kFull, p.y, o);
+            const int c = __shfl_up_sync(kFull, p.z, o), d = __shfl_up_sync(kFull, p.w, o);
+            if (lane >= o) p = make_int4(p.x + a, p.y + b, p.z + c, p.w + d);
+        }
+        part[lane] = p;
+    }
+    __syncthreads();
+    const int4 before = warp > 0 ? part[warp - 1] : make_int4(0, 0, 0, 0);
+    *total = part[kListThreads / 32 - 1];
+    return make_int4(before.x + inc.x - v.x, before.y + inc.y - v.y, before.z + inc.z - v.z,
+                     before.w + inc.w - v.w);
+}
+
+// The list of instances in state `target` (single CTA).  With decide set, first the verdict of
+// the sweep that just ran: an active instance whose sweep changed no row is converged.
+__global__ void __launch_bounds__(kListThreads)
+    batch_list_kernel(const BatchInst *__restrict__ inst, int L, BatchCounters c, BatchList list, int target,
+                      int decide) {
+    const int per = (L + kListThreads - 1) / kListThreads;
+    const int k0 = min(L, static_cast<int>(threadIdx.x) * per), k1 = min(L, k0 + per);
+    int4 mine = make_int4(0, 0, 0, 0);
+    for (int k = k0; k < k1; ++k) {
+        if (decide && c.state[k] == B_ACTIVE) {
+            c.sweeps[k] += 1;
+            if (c.chg[k] == 0) c.state[k] = B_EMIT;
+            c.chg[k] = 0;
+        }
+        if (c.state[k] == target) {
+            const BatchInst &I = inst[k];
+            mine = make_int4(mine.x + 1, mine.y + I.n, mine.z + I.np, mine.w + I.tiles);
+        }
+    }
+    int4 tot;
+    int4 at = block_scan4(mine, &tot);
+    int *tile_start = list.sched + 2 + L;
+    for (int k = k0; k < k1; ++k) {
+        if (c.state[k] != target) continue;
+        const BatchInst &I = inst[k];
+        list.k[at.x] = k;
+        list.row[at.x] = at.y;
+        list.prow[at.x] = at.z;
+        list.sched[2 + at.x] = k;
+        tile_start[at.x] = at.w;
+        at = make_int4(at.x + 1, at.y + I.n, at.z + I.np, at.w + I.tiles);
+    }
+    if (threadIdx.x == 0) {
+        list.hdr[0] = tot.x;
+        list.hdr[1] = tot.y;
+        list.hdr[2] = tot.z;
+        list.hdr[3] = tot.w;
+        list.hdr[4] = 0;
+        list.row[tot.x] = tot.y;
+        list.prow[tot.x] = tot.z;
+        list.sched[0] = tot.x;
+        list.sched[1] = tot.w;
+        tile_start[tot.x] = tot.w;
+    }
+}
+
+__device__ __forceinline__ uint64_t full_word(int n, int w) {
+    const int lo = 64 * w;
+    return lo >= n ? 0ull : (n - lo >= 64 ? ~0ull : ((1ull << (n - lo)) - 1ull));
+}
+
+// Rows of the listed instances, claimed kChunk at a time.  With WPL == 1 a row takes G lanes
+// (G = wp rounded up to a power of two) and a warp works on 32 / G rows of one instance at
+// once; with WPL > 1 a row takes the warp and each lane WPL words.  Successors are taken U at
+// a time, their rows loaded before any is combined.
+//   EMIT == false (sweep):  M_i <- M_i | E_i | OR_{s in succ(i)} M_s in place; a group stops
+//                           once its row is full; instance k's change counter counts steps
+//                           that changed a row.
+//   EMIT == true:           out_i = OR_{s in succ(i)} M_s; violation iff (out_i | e_i) != M_i.
+template <int WPL, bool EMIT>
+__global__ void __launch_bounds__(256)
+    batch_rows_kernel(const BatchInst *__restrict__ inst, BatchList list, const int *__restrict__ ptr,
+                      const int *__restrict__ col, BatchCounters c) {
+    constexpr int U = WPL <= 2 ? 4 : 2;
+    const int lane = threadIdx.x & 31;
+    const int nrows = list.hdr[1];
+    const int entries = list.hdr[0];
+    if (nrows == 0) return;
+    for (;;) {
+        int chunk = 0;
+        if (lane == 0) chunk = atomicAdd(list.hdr + 4, 1);
+        chunk = __shfl_sync(kFull, chunk, 0);
+        int r = chunk * kChunk;
+        if (r >= nrows) return;
+        const int rend = min(nrows, r + kChunk);
+        int j = last_le(list.row, entries, r);
+        while (r < rend) {
+            const int k = list.k[j];
+            const int ib = list.row[j];
+            const int lim = min(rend, list.row[j + 1]);
+            const BatchInst I = inst[k];
+            const uint64_t *M = I.rbits;
+            int G = 32;
+            if (WPL == 1)
+                while (G > 1 && (G >> 1) >= I.wp) G >>= 1;
+            const int grp = lane / G, w0 = lane % G;
+            const unsigned gmask = G == 32 ? kFull : (((1u << G) - 1u) << (grp * G));
+            const int wout = (I.n + 63) >> 6;
+            for (; r < lim; r += 32 / G) {
+                const int i = r + grp - ib;
+                const bool act = r + grp < lim;
+                int q0 = 0, q1 = 0;
+                if (act) {
+                    q0 = ptr[I.row0 + i];
+                    q1 = ptr[I.row0 + i + 1];
+                }
+                uint64_t acc[WPL], mi[WPL], fullw[WPL];
+                bool sat = true;
+#pragma unroll
+                for (int q = 0; q < WPL; ++q) {
+                    const int w = w0 + G * q;
+                    const bool v = act && w < I.wp;
+                    fullw[q] = v ? full_word(I.n, w) : 0ull;
+                    mi[q] = v ? M[static_cast<int64_t>(i) * I.wp + w] : 0ull;
+                    acc[q] = EMIT ? 0ull : mi[q];
+                    sat &= acc[q] == fullw[q];
+                }
+                unsigned bal = __ballot_sync(kFull, sat);
+                int deg = act ? q1 - q0 : 0;
+                if (!EMIT && (bal & gmask) == gmask) deg = 0;
+                for (int t = 0; __any_sync(kFull, t < deg); t += U) {
+                    int s[U];
+#pragma unroll
+                    for (int u = 0; u < U; ++u) s[u] = t + u < deg ? col[q0 + t + u] : -1;
+                    uint64_t v[U][WPL];
+#pragma unroll
+                    for (int u = 0; u < U; ++u)
+#pragma unroll
+                        for (int q = 0; q < WPL; ++q) {
+                            const int w = w0 + G * q;
+                            v[u][q] = (s[u] >= 0 && w < I.wp) ? M[static_cast<int64_t>(s[u]) * I.wp + w] : 0ull;
+                        }
+                    sat = true;
+#pragma unroll
+                    for (int q = 0; q < WPL; ++q) {
+                        const int w = w0 + G * q;
+#pragma unroll
+                        for (int u = 0; u < U; ++u) {
+                            acc[q] |= v[u][q];
+                            if (!EMIT && s[u] >= 0 && w == (s[u] >> 6)) acc[q] |= 1ull << (s[u] & 63);
+                        }
+                        sat &= acc[q] == fullw[q];
+                    }
+                    bal = __ballot_sync(kFull, sat);
+                    if ((bal & gmask) == gmask) deg = 0;  // the row is full: nothing more can be added
+                }
+                if (!EMIT) {
+                    bool changed = false;
+#pragma unroll
+                    for (int q = 0; q < WPL; ++q) {
+                        const int w = w0 + G * q;
+                        if (act && w < I.wp && acc[q] != mi[q]) {
+                            I.rbits[static_cast<int64_t>(i) * I.wp + w] = acc[q];
+                            changed = true;
+                        }
+                    }
+                    if (__any_sync(kFull, changed) && lane == 0) atomicAdd(&c.chg[k], 1ull);
+                } else {
+                    bool viol = false;
+                    uint32_t ones = 0;
+#pragma unroll
+                    for (int q = 0; q < WPL; ++q) {
+                        const int w = w0 + G * q;
+                        if (!act || w >= I.wp) continue;
+                        const uint64_t self = w == (i >> 6) ? 1ull << (i & 63) : 0ull;
+                        viol |= (acc[q] | self) != mi[q];
+                        ones += __popcll(acc[q]);
+                        if (I.out) {
+                            if (w < wout) I.out[static_cast<int64_t>(i) * wout + w] = acc[q];
+                        } else {
+                            I.mbits[static_cast<int64_t>(i) * I.wp + w] = acc[q];
+                        }
+                    }
+                    const bool any = __any_sync(kFull, viol);
+#pragma unroll
+                    for (int o = 16; o > 0; o >>= 1) ones += __shfl_xor_sync(kFull, ones, o);
+                    if (lane == 0) {
+                        if (any) atomicAdd(&c.viol[k], 1ull);
+                        if (ones) atomicAdd(&c.ones[k], static_cast<unsigned long long>(ones));
+                    }
+                }
+            }
+            r = lim;
+            ++j;
+        }
+    }
+}
+
+// e4m3 operands of the listed instances from their bits (warp per padded row, 16 rows per
+// claim); an instance's first row counts its squaring.
+__global__ void __launch_bounds__(256)
+    batch_to_e4m3_kernel(const BatchInst *__restrict__ inst, BatchList list, BatchCounters c) {
+    const int lane = threadIdx.x & 31;
+    const int nprows = list.hdr[2];
+    if (nprows == 0) return;
+    const int entries = list.hdr[0];
+    const int warps = gridDim.x * (blockDim.x >> 5);
+    for (int p0 = (blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 16; p0 < nprows; p0 += warps * 16) {
+        int j = last_le(list.prow, entries, p0);
+        for (int p = p0; p < min(nprows, p0 + 16); ++p) {
+            while (list.prow[j + 1] <= p) ++j;
+            const int k = list.k[j];
+            const BatchInst &I = inst[k];
+            const int r = p - list.prow[j];
+            if (r == 0 && lane == 0) c.squarings[k] += 1;
+            const uint64_t *src = I.rbits + static_cast<int64_t>(r) * I.wp;
+            uint4 *dst = reinterpret_cast<uint4 *>(I.c0 + static_cast<int64_t>(r) * I.np);
+            for (int w = lane; w < I.wp; w += 32) {
+                const uint64_t x = src[w];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    uint32_t o[4];
+#pragma unroll
+                    for (int b = 0; b < 4; ++b) {
+                        const uint32_t nib = static_cast<uint32_t>(x >> (16 * q + 4 * b)) & 0xFu;
+                        o[b] = ((nib & 1u) * 0x38u) | (((nib >> 1) & 1u) * 0x3800u) |
+                               (((nib >> 2) & 1u) * 0x380000u) | (((nib >> 3) & 1u) * 0x38000000u);
+                    }
+                    dst[4 * w + q] = make_uint4(o[0], o[1], o[2], o[3]);
+                }
+            }
+        }
+    }
+}
+
+// After the emission: a certificate that failed is an internal error; all instances retire.
+__global__ void decide_final(int count, BatchCounters c, int *status) {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     if (k >= count) return;
-    const int st = c.state[k];
-    if (st == B_ACTIVE) {
-        if (c.viol[k] == 0) c.state[k] = B_DONE;
-        else c.ones[k] = 0;
-    } else if (st == B_EMIT) {
+    if (c.state[k] == B_EMIT) {
         c.state[k] = B_DONE;
-        if (c.viol[k] != 0) atomicOr(status, ST_TIMEOUT_DEP);  // converged closure failed its check
+        if (c.viol[k] != 0) atomicOr(status, ST_TIMEOUT_DEP);
     }
-    c.viol[k] = 0;
-}
-
-// Copy each model (n rows of ceil(n/64) words) to its device output.
-__global__ void copy_out_kernel(const BatchInst *__restrict__ inst, int count, int64_t total_rows) {
-    const int lane = threadIdx.x & 31;
-    const int64_t g = static_cast<int64_t>(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (g >= total_rows) return;
-    const int k = find_by_row(inst, count, g);
-    const BatchInst I = inst[k];
-    if (!I.out) return;
-    const int r = static_cast<int>(g - I.row0);
-    const int64_t w = (I.n + 63) / 64;
-    for (int64_t q = lane; q < w; q += 32) I.out[r * w + q] = I.mbits[r * I.wp + q];
 }
 
 int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
@@ -152,6 +472,15 @@ int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
         }                                                                                       \
     } while (0)
 
+template <bool EMIT>
+void launch_rows(int wpl, int grid, const BatchInst *d, const BatchList &l, const int *ptr, const int *col,
+                 const BatchCounters &bc, cudaStream_t s) {
+    if (wpl == 1) batch_rows_kernel<1, EMIT><<<grid, 256, 0, s>>>(d, l, ptr, col, bc);
+    else if (wpl == 2) batch_rows_kernel<2, EMIT><<<grid, 256, 0, s>>>(d, l, ptr, col, bc);
+    else if (wpl == 4) batch_rows_kernel<4, EMIT><<<grid, 256, 0, s>>>(d, l, ptr, col, bc);
+    else batch_rows_kernel<8, EMIT><<<grid, 256, 0, s>>>(d, l, ptr, col, bc);
+}
+
 }  // namespace
 
 // Cached schedule of the last batch (graph + the buffers it was built on).
@@ -159,10 +488,11 @@ struct BatchPlan {
     std::vector<int32_t> ns;
     std::vector<const void *> ins;
     std::vector<void *> outs;
+    const void *col = nullptr;
     int mem = -1;
-    int bn = 0;
     cudaGraphExec_t exec = nullptr;
     int rounds = 0;
+    int launches = 0;  // kernels in the graph
     ~BatchPlan() {
         if (exec) cudaGraphExecDestroy(exec);
     }
@@ -176,45 +506,63 @@ dl_status solve_tc_batch(dl_ctx *ctx, Workspace &ws, cudaStream_t s, int32_t cou
         if (ns[k] > 0) live.push_back(k);
     if (live.empty()) return DL_OK;
     const int L = static_cast<int>(live.size());
-    const int bn = 128;  // tile width for the batch (small instances waste less padding)
+    const int bn = 128;  // GEMM tile width for the batch (small instances waste less padding)
+    const int tm = gemm_tile_m();
     std::vector<BatchInst> inst(L);
-    int64_t in_bytes = 0, mat_bytes = 0, bit_words = 0, prow = 0, row = 0;
-    int64_t max_np = 0;
+    int64_t in_bytes = 0, mat_bytes = 0, bit_words = 0, prow = 0, row = 0, max_np = 0, max_wp = 0, tiles = 0;
     for (int i = 0; i < L; ++i) {
         const int32_t n = ns[live[i]];
         const int64_t np = round_up(n, 128);
         inst[i].n = n;
         inst[i].np = static_cast<int32_t>(np);
-        inst[i].wp = np / 64;
-        inst[i].prow0 = prow;
-        inst[i].row0 = row;
+        inst[i].wp = static_cast<int32_t>(np / 64);
+        inst[i].tiles = static_cast<int32_t>(((np + tm - 1) / tm) * ((np + bn - 1) / bn));
+        inst[i].prow0 = static_cast<int32_t>(std::min<int64_t>(prow, INT32_MAX));
+        inst[i].row0 = static_cast<int32_t>(std::min<int64_t>(row, INT32_MAX));
         prow += np;
         row += n;
+        tiles += inst[i].tiles;
         in_bytes += round_up(static_cast<int64_t>(n) * n, 256);
         mat_bytes += np * np;
         bit_words += np * (np / 64);
         max_np = std::max(max_np, np);
+        max_wp = std::max(max_wp, np / 64);
     }
     const int64_t total_prows = prow, total_rows = row;
+    if (max_wp > 256) {
+        set_error("batch: instances are limited to n <= 16384");
+        return DL_EINVAL;
+    }
+    if (total_prows > (1ll << 31) - 2 || tiles > (1ll << 31) - 1) {
+        set_error("batch: too many rows (%lld padded rows)", static_cast<long long>(total_prows));
+        return DL_EINVAL;
+    }
+    const int wpl = max_wp <= 32 ? 1 : max_wp <= 64 ? 2 : max_wp <= 128 ? 4 : 8;
+    const int scan_blocks = static_cast<int>((total_rows + 1023) / 1024);
     auto *c0 = static_cast<uint8_t *>(ws.get("batch_c0", mat_bytes));
-    auto *c1 = static_cast<uint8_t *>(ws.get("batch_c1", mat_bytes));
     auto *rb = static_cast<uint64_t *>(ws.get("batch_rbits", bit_words * 8));
     auto *mb = static_cast<uint64_t *>(ws.get("batch_mbits", bit_words * 8));
-    auto *ctr = static_cast<unsigned long long *>(ws.get("batch_ctr", 5 * sizeof(unsigned long long) * L + 256));
-    auto *state = static_cast<int *>(ws.get("batch_state", sizeof(int) * L + 256));
+    auto *ctr = static_cast<unsigned long long *>(ws.get("batch_ctr", kCounterArrays * sizeof(unsigned long long) * L));
+    auto *state = static_cast<int *>(ws.get("batch_state", sizeof(int) * L));
+    auto *lists = static_cast<int *>(ws.get("batch_list", sizeof(int) * (8 + 3 * (L + 1) + 2 + 2 * L + 1)));
     auto *dinst = static_cast<BatchInst *>(ws.get("batch_inst", sizeof(BatchInst) * L));
-    auto *dprob = static_cast<GemmProblem *>(ws.get("batch_probs", sizeof(GemmProblem) * 2 * L));
+    auto *dprob = static_cast<GemmProblem *>(ws.get("batch_probs", sizeof(GemmProblem) * L));
+    auto *pinst = static_cast<int *>(ws.get("batch_pinst", sizeof(int) * total_prows));
+    auto *gcnt = static_cast<int *>(ws.get("batch_cnt", sizeof(int) * (total_rows + 1)));
+    auto *gptr = static_cast<int *>(ws.get("batch_ptr", sizeof(int) * (total_rows + 1)));
+    auto *scratch = static_cast<int *>(ws.get("batch_scan", sizeof(int) * 2 * (scan_blocks + 1)));
     uint8_t *staging = nullptr;
     if (mem == DL_MEM_HOST) staging = static_cast<uint8_t *>(ws.get("batch_in", std::max<int64_t>(in_bytes, 256)));
-    if (!c0 || !c1 || !rb || !mb || !ctr || !state || !dinst || !dprob || (mem == DL_MEM_HOST && !staging)) {
-        set_error("batch: device allocation failed (%.2f GB of operands)", 2.0 * mat_bytes / 1e9);
+    if (!c0 || !rb || !mb || !ctr || !state || !lists || !dinst || !dprob || !pinst || !gcnt || !gptr ||
+        !scratch || (mem == DL_MEM_HOST && !staging)) {
+        set_error("batch: device allocation failed (%.2f GB of operands)", 1.0 * mat_bytes / 1e9);
         return DL_ENOMEM;
     }
-    BatchCounters bc{state, ctr, ctr + L, ctr + 2 * L, ctr + 3 * L, ctr + 4 * L};
+    const BatchCounters bc{state, ctr, ctr + L, ctr + 2 * L, ctr + 3 * L, ctr + 4 * L};
+    const BatchList bl{lists, lists + 8, lists + 8 + (L + 1), lists + 8 + 2 * (L + 1), lists + 8 + 3 * (L + 1)};
 
     cudaEvent_t ev0 = ws.ev[0], ev1 = ws.ev[1];
     BCK(cudaEventRecord(ev0, s));
-    // inputs on the device
     int64_t mo = 0, bo = 0, io = 0;
     for (int i = 0; i < L; ++i) {
         const int k = live[i];
@@ -227,15 +575,38 @@ dl_status solve_tc_batch(dl_ctx *ctx, Workspace &ws, cudaStream_t s, int32_t cou
             inst[i].E = Es[k];
         }
         inst[i].c0 = c0 + mo;
-        inst[i].c1 = c1 + mo;
         inst[i].rbits = rb + bo;
         inst[i].mbits = mb + bo;
         inst[i].out = mem == DL_MEM_DEVICE ? out_bits[k] : nullptr;
         mo += np * np;
         bo += np * (np / 64);
     }
+    BCK(cudaMemcpyAsync(dinst, inst.data(), sizeof(BatchInst) * L, cudaMemcpyHostToDevice, s));
 
-    // reuse the captured schedule when the call repeats on the same buffers
+    // 1. bits of I + E, counts and checks over all inputs, then the CSR row pointers (every
+    //    call: the contents, hence the number of facts, may differ between calls)
+    BCK(cudaMemsetAsync(ws.status, 0, sizeof(int), s));
+    batch_map_kernel<<<L, 256, 0, s>>>(dinst, pinst);
+    const unsigned prow_blocks = static_cast<unsigned>((total_prows + 7) / 8);
+    batch_pack_kernel<<<prow_blocks, 256, 0, s>>>(dinst, pinst, static_cast<int>(total_prows), gcnt, ws.status);
+    BCK(cudaGetLastError());
+    BCK(exclusive_scan_large(gcnt, static_cast<int>(total_rows), gptr, scratch, s));
+    const int pre_launches = 2 + (total_rows > 64 * 1024 ? 3 : 1);
+    int nnz_total = 0, hst = 0;
+    BCK(cudaMemcpyAsync(&nnz_total, gptr + total_rows, sizeof(int), cudaMemcpyDeviceToHost, s));
+    BCK(cudaMemcpyAsync(&hst, ws.status, sizeof(int), cudaMemcpyDeviceToHost, s));
+    BCK(cudaStreamSynchronize(s));
+    if (hst & ST_BAD_INPUT) {
+        set_error("batch: an input matrix holds a byte that is neither 0 nor 1");
+        return DL_EINVAL;
+    }
+    auto *gcol = static_cast<int *>(ws.get("batch_col", sizeof(int) * static_cast<size_t>(std::max(nnz_total, 1))));
+    if (!gcol) {
+        set_error("batch: device allocation failed (CSR of %d facts)", nnz_total);
+        return DL_ENOMEM;
+    }
+
+    // 2. the captured schedule (rebuilt when the buffers change)
     std::vector<int32_t> key_ns(L);
     std::vector<const void *> key_in(L);
     std::vector<void *> key_out(L);
@@ -245,68 +616,67 @@ dl_status solve_tc_batch(dl_ctx *ctx, Workspace &ws, cudaStream_t s, int32_t cou
         key_out[i] = out_bits[live[i]];
     }
     BatchPlan *&plan = ws.batch_plan;
-    const bool reuse = plan && plan->mem == static_cast<int>(mem) && plan->bn == bn && plan->ns == key_ns &&
-                       plan->ins == key_in && plan->outs == key_out;
+    const bool reuse = plan && plan->mem == static_cast<int>(mem) && plan->ns == key_ns && plan->ins == key_in &&
+                       plan->outs == key_out && plan->col == gcol;
     if (!reuse) {
         delete plan;
         plan = nullptr;
-        BCK(cudaMemcpyAsync(dinst, inst.data(), sizeof(BatchInst) * L, cudaMemcpyHostToDevice, s));
-        std::vector<GemmProblem> probs(2 * L);
+        std::vector<GemmProblem> probs(L);
         std::string err;
-        int tiles = 0;
-        for (int p = 0; p < 2; ++p) {
-            int start = 0;
-            for (int i = 0; i < L; ++i) {
-                const int64_t np = inst[i].np;
-                GemmEpilogue e{};
-                e.out8 = p == 0 ? inst[i].c1 : inst[i].c0;
-                e.ld_out8 = np;
-                e.bits = reinterpret_cast<uint32_t *>(inst[i].rbits);
-                e.ld_bits32 = 2 * inst[i].wp;
-                e.count = bc.cnt_new + i;
-                const Operand op{p == 0 ? inst[i].c0 : inst[i].c1, np, np, np, 0, 0};
-                GemmProblem &pr = probs[p * L + i];
-                if (!gemm_make_problem(&pr, KIND_F8, false, bn, static_cast<int>(np), static_cast<int>(np),
-                                       static_cast<int>(np), op, op, e, &err)) {
-                    set_error("batch: %s", err.c_str());
-                    return DL_EDEVICE;
-                }
-                pr.gate = state + i;
-                pr.tile_start = start;
-                start += pr.tiles_m * pr.tiles_n;
+        int64_t tile0 = 0;
+        for (int i = 0; i < L; ++i) {
+            const int64_t np = inst[i].np;
+            GemmEpilogue e{};
+            e.bits = reinterpret_cast<uint32_t *>(inst[i].rbits);  // M <- min1(M^2), bits only
+            e.ld_bits32 = 2 * inst[i].wp;
+            const Operand op{inst[i].c0, np, np, np, 0, 0};
+            GemmProblem &pr = probs[i];
+            if (!gemm_make_problem(&pr, KIND_F8, false, bn, static_cast<int>(np), static_cast<int>(np),
+                                   static_cast<int>(np), op, op, e, &err)) {
+                set_error("batch: %s", err.c_str());
+                return DL_EDEVICE;
             }
-            tiles = start;
+            pr.tile_start = static_cast<int>(tile0);
+            tile0 += pr.tiles_m * pr.tiles_n;
         }
         // pageable source: the copy has read `probs` when cudaMemcpyAsync returns
-        BCK(cudaMemcpyAsync(dprob, probs.data(), sizeof(GemmProblem) * 2 * L, cudaMemcpyHostToDevice, s));
+        BCK(cudaMemcpyAsync(dprob, probs.data(), sizeof(GemmProblem) * L, cudaMemcpyHostToDevice, s));
         BCK(gemm_prepare(KIND_F8, false, bn, EPI_BOOL));
-        const int rounds = 2 + static_cast<int>(std::ceil(std::log2(static_cast<double>(max_np) + 1.0)));
-        const int grid = std::min(tiles, ctx->sms);
-        const int dgrid = (L + 255) / 256;
-        const unsigned sweep_blocks = static_cast<unsigned>((total_rows + 7) / 8);
-        // capture the schedule
+        const int rounds = 1 + static_cast<int>(std::ceil(std::log2(static_cast<double>(max_np) + 1.0)));
+        const int ggrid = static_cast<int>(std::min<int64_t>(tiles, ctx->sms));
+        const int rgrid = ctx->sms * 8;  // row kernels: 8 CTAs of 8 warps per SM, rows claimed in chunks
+        const unsigned prow_grid = static_cast<unsigned>((total_prows + 7) / 8);
+        int launches = 0;
+        auto sweep = [&]() {
+            launch_rows<false>(wpl, rgrid, dinst, bl, gptr, gcol, bc, s);
+            batch_list_kernel<<<1, kListThreads, 0, s>>>(dinst, L, bc, bl, B_ACTIVE, 1);
+            launches += 2;
+        };
         cudaGraph_t graph = nullptr;
         BCK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
         bool cap_ok = true;
         auto cap = [&](cudaError_t e) { cap_ok = cap_ok && e == cudaSuccess; };
         cap(cudaMemsetAsync(state, 0, sizeof(int) * L, s));
-        cap(cudaMemsetAsync(ctr, 0, 5 * sizeof(unsigned long long) * L, s));
-        ingest_batch_kernel<<<static_cast<unsigned>(total_prows), 256, 0, s>>>(dinst, L, bc, ws.status);
+        cap(cudaMemsetAsync(ctr, 0, kCounterArrays * sizeof(unsigned long long) * L, s));
+        batch_fill_kernel<<<prow_grid, 256, 0, s>>>(dinst, pinst, static_cast<int>(total_prows), gptr, gcol);
+        batch_list_kernel<<<1, kListThreads, 0, s>>>(dinst, L, bc, bl, B_ACTIVE, 0);
+        launches += 2;
+        cap(cudaGetLastError());
+        for (int k = 0; k < kFirstSweeps; ++k) sweep();
         cap(cudaGetLastError());
         for (int r = 0; r < rounds; ++r) {
-            cap(gemm_launch(KIND_F8, false, bn, EPI_BOOL, dprob + (r & 1) * L, L, tiles, grid, ws.status,
-                            ctx->budget_ns, s));
-            decide_after_square<<<dgrid, 256, 0, s>>>(L, bc);
-            cap(cudaGetLastError());
-            sweep_batch_kernel<<<sweep_blocks, 256, 0, s>>>(dinst, L, total_rows, bc);
-            cap(cudaGetLastError());
-            decide_after_sweep<<<dgrid, 256, 0, s>>>(L, bc, ws.status);
+            batch_to_e4m3_kernel<<<rgrid, 256, 0, s>>>(dinst, bl, bc);
+            cap(gemm_launch(KIND_F8, false, bn, EPI_BOOL, dprob, L, static_cast<int>(tiles), ggrid, ws.status,
+                            ctx->budget_ns, s, bl.sched));
+            launches += 2;
+            for (int k = 0; k < kRoundSweeps; ++k) sweep();
             cap(cudaGetLastError());
         }
-        if (mem == DL_MEM_DEVICE) {
-            copy_out_kernel<<<sweep_blocks, 256, 0, s>>>(dinst, L, total_rows);
-            cap(cudaGetLastError());
-        }
+        batch_list_kernel<<<1, kListThreads, 0, s>>>(dinst, L, bc, bl, B_EMIT, 0);
+        launch_rows<true>(wpl, rgrid, dinst, bl, gptr, gcol, bc, s);
+        decide_final<<<(L + 255) / 256, 256, 0, s>>>(L, bc, ws.status);
+        launches += 3;
+        cap(cudaGetLastError());
         const cudaError_t ec = cudaStreamEndCapture(s, &graph);
         if (!cap_ok || ec != cudaSuccess) {
             if (graph) cudaGraphDestroy(graph);
@@ -318,9 +688,10 @@ dl_status solve_tc_batch(dl_ctx *ctx, Workspace &ws, cudaStream_t s, int32_t cou
         plan->ns = key_ns;
         plan->ins = key_in;
         plan->outs = key_out;
+        plan->col = gcol;
         plan->mem = static_cast<int>(mem);
-        plan->bn = bn;
         plan->rounds = rounds;
+        plan->launches = launches;
         const cudaError_t ei = cudaGraphInstantiate(&plan->exec, graph, 0);
         cudaGraphDestroy(graph);
         if (ei != cudaSuccess) {
@@ -330,7 +701,6 @@ dl_status solve_tc_batch(dl_ctx *ctx, Workspace &ws, cudaStream_t s, int32_t cou
             return DL_EDEVICE;
         }
     }
-    BCK(cudaMemsetAsync(ws.status, 0, sizeof(int), s));
     BCK(cudaGraphLaunch(plan->exec, s));
     if (mem == DL_MEM_HOST) {
         for (int i = 0; i < L; ++i) {
@@ -341,31 +711,28 @@ dl_status solve_tc_batch(dl_ctx *ctx, Workspace &ws, cudaStream_t s, int32_t cou
     }
     BCK(cudaEventRecord(ev1, s));
     std::vector<int> hstate(L);
-    std::vector<unsigned long long> hctr(5 * static_cast<size_t>(L));
+    std::vector<unsigned long long> hctr(kCounterArrays * static_cast<size_t>(L));
     BCK(cudaMemcpyAsync(hstate.data(), state, sizeof(int) * L, cudaMemcpyDeviceToHost, s));
-    BCK(cudaMemcpyAsync(hctr.data(), ctr, sizeof(unsigned long long) * 5 * L, cudaMemcpyDeviceToHost, s));
-    int hst = 0;
+    BCK(cudaMemcpyAsync(hctr.data(), ctr, sizeof(unsigned long long) * kCounterArrays * L, cudaMemcpyDeviceToHost,
+                        s));
     BCK(cudaMemcpyAsync(&hst, ws.status, sizeof(int), cudaMemcpyDeviceToHost, s));
     BCK(cudaStreamSynchronize(s));
-    if (hst & ST_BAD_INPUT) {
-        set_error("batch: an input matrix holds a byte that is neither 0 nor 1");
-        return DL_EINVAL;
-    }
     if (hst) {
         set_error("batch: device status 0x%x (a wait expired or a certificate failed)", hst);
         return DL_ETIMEOUT;
     }
-    int max_sq = 0;
+    int max_sq = 0, max_sw = 0;
     int64_t ones = 0;
     double flops = 0.0;
     for (int i = 0; i < L; ++i) {
         if (hstate[i] != B_DONE) {
-            set_error("batch: instance %d did not converge in %d rounds", live[i], plan->rounds);
+            set_error("batch: instance %d did not converge", live[i]);
             return DL_ENOTCONV;
         }
-        const int sq = static_cast<int>(hctr[4 * L + i]);
+        const int sq = static_cast<int>(hctr[3 * L + i]);
         max_sq = std::max(max_sq, sq);
-        ones += static_cast<int64_t>(hctr[3 * L + i]);
+        max_sw = std::max(max_sw, static_cast<int>(hctr[4 * L + i]));
+        ones += static_cast<int64_t>(hctr[2 * L + i]);
         const double np = inst[i].np;
         flops += 2.0 * np * np * np * sq;
     }
@@ -377,15 +744,16 @@ dl_status solve_tc_batch(dl_ctx *ctx, Workspace &ws, cudaStream_t s, int32_t cou
             const double n = inst[i].n;
             equiv += (8.0 / 3.0) * n * n * n;
         }
-        st->path_used = DL_PATH_BOOL_FP8;
+        st->path_used = DL_PATH_AUTO;
         st->iters = max_sq;
+        st->recheck_sweeps = max_sw;
         st->model_ones = ones;
         st->ms_total = ms;
         st->ms_solve = ms;
         st->tflops_equiv = ms > 0 ? equiv / (ms * 1e-3) / 1e12 : 0.0;
         st->gemm_launches = plan->rounds;
         st->gemm_flops = flops;
-        st->gpu_launches = 1 + plan->rounds * 4 + (mem == DL_MEM_DEVICE ? 1 : 0);
+        st->gpu_launches = pre_launches + plan->launches;
     }
     return DL_OK;
 }

@@ -33,6 +33,47 @@ __global__ void csr_count_kernel(const uint8_t *__restrict__ E, int n, int *cnt)
     if (lane == 0) cnt[i] = c;
 }
 
+// Successor counts plus the ingest's checks in the same pass: bytes other than 0/1 set the
+// status bit, row counts reduce to max (||E||_inf) and total (nnz), and the diagonal facts
+// (self-loops) are counted.
+__global__ void csr_count_check_kernel(const uint8_t *__restrict__ E, int n, int *cnt, unsigned long long *dmax,
+                                       unsigned long long *nnz, unsigned long long *diag, int *status) {
+    const int lane = threadIdx.x & 31;
+    const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (i >= n) return;
+    const uint8_t *row = E + static_cast<int64_t>(i) * n;
+    int c = 0;
+    uint32_t bad = 0;
+    if ((n & 15) == 0 && (reinterpret_cast<uintptr_t>(E) & 15) == 0) {
+        const uint4 *r4 = reinterpret_cast<const uint4 *>(row);
+        for (int q = lane; q < n / 16; q += 32) {
+            const uint4 x = r4[q];
+            bad |= (x.x | x.y | x.z | x.w) & 0xFEFEFEFEu;
+            c += __popc(x.x & 0x01010101u) + __popc(x.y & 0x01010101u) + __popc(x.z & 0x01010101u) +
+                 __popc(x.w & 0x01010101u);
+        }
+    } else {
+        for (int j = lane; j < n; j += 32) {
+            bad |= row[j] & 0xFEu;
+            c += row[j] & 1;
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        c += __shfl_xor_sync(0xffffffffu, c, o);
+        bad |= __shfl_xor_sync(0xffffffffu, bad, o);
+    }
+    if (lane == 0) {
+        cnt[i] = c;
+        if (bad) atomicOr(status, ST_BAD_INPUT);
+        if (c) {
+            atomicMax(dmax, static_cast<unsigned long long>(c));
+            atomicAdd(nnz, static_cast<unsigned long long>(c));
+        }
+        if (row[i] & 1) atomicAdd(diag, 1ull);
+    }
+}
+
 __global__ void __launch_bounds__(1024) exclusive_scan_kernel(const int *cnt, int n, int *ptr) {
     __shared__ int part[1024];
     const int t = threadIdx.x;
@@ -107,8 +148,70 @@ cudaError_t csr_build(const uint8_t *E, int n, int *cnt, int *ptr, cudaStream_t 
     return cudaGetLastError();
 }
 
+cudaError_t csr_build_checked(const uint8_t *E, int n, int *cnt, int *ptr, unsigned long long *dmax,
+                              unsigned long long *nnz, unsigned long long *diag, int *status, cudaStream_t s) {
+    csr_count_check_kernel<<<static_cast<unsigned>((n + 7) / 8), 256, 0, s>>>(E, n, cnt, dmax, nnz, diag, status);
+    exclusive_scan_kernel<<<1, 1024, 0, s>>>(cnt, n, ptr);
+    return cudaGetLastError();
+}
+
+// Two-level scan for long arrays: block sums of 1024 elements, a scan of those sums (the
+// single-CTA kernel), then every block rescans its elements from its offset.
+__global__ void __launch_bounds__(1024) block_sums_kernel(const int *cnt, int n, int *sums) {
+    __shared__ int part[32];
+    const int i = blockIdx.x * 1024 + threadIdx.x;
+    int v = i < n ? cnt[i] : 0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) part[threadIdx.x >> 5] = v;
+    __syncthreads();
+    if (threadIdx.x < 32) {
+        int w = part[threadIdx.x];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) w += __shfl_xor_sync(0xffffffffu, w, o);
+        if (threadIdx.x == 0) sums[blockIdx.x] = w;
+    }
+}
+
+__global__ void __launch_bounds__(1024) block_scan_kernel(const int *cnt, int n, const int *offs, int *out) {
+    __shared__ int part[32];
+    const int i = blockIdx.x * 1024 + threadIdx.x;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int v = i < n ? cnt[i] : 0;
+    int inc = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const int t = __shfl_up_sync(0xffffffffu, inc, o);
+        if (lane >= o) inc += t;
+    }
+    if (lane == 31) part[warp] = inc;
+    __syncthreads();
+    if (warp == 0) {
+        int w = part[lane];
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, w, o);
+            if (lane >= o) w += t;
+        }
+        part[lane] = w;  // inclusive prefix of warp totals
+    }
+    __syncthreads();
+    const int before = offs[blockIdx.x] + (warp > 0 ? part[warp - 1] : 0) + inc - v;
+    if (i < n) out[i] = before;
+    if (i == n - 1) out[n] = before + v;
+}
+
 cudaError_t exclusive_scan(const int *cnt, int n, int *out, cudaStream_t s) {
     exclusive_scan_kernel<<<1, 1024, 0, s>>>(cnt, n, out);
+    return cudaGetLastError();
+}
+
+cudaError_t exclusive_scan_large(const int *cnt, int n, int *out, int *scratch, cudaStream_t s) {
+    if (n <= 64 * 1024) return exclusive_scan(cnt, n, out, s);
+    const int blocks = (n + 1023) / 1024;  // scratch: 2 * (blocks + 1) ints
+    block_sums_kernel<<<blocks, 1024, 0, s>>>(cnt, n, scratch);
+    exclusive_scan_kernel<<<1, 1024, 0, s>>>(scratch, blocks, scratch + blocks + 1);
+    block_scan_kernel<<<blocks, 1024, 0, s>>>(cnt, n, scratch + blocks + 1, out);
     return cudaGetLastError();
 }
 

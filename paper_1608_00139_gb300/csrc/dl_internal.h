@@ -74,10 +74,14 @@ struct Operand {
 bool gemm_make_problem(GemmProblem *p, GemmKind kind, bool b_kmajor, int bn, int M, int N, int K,
                        const Operand &A, const Operand &B, const GemmEpilogue &epi,
                        std::string *err);
-// Launch over problems already in device memory.  total_tiles = sum of tiles.
+// Launch over problems already in device memory.  total_tiles = sum of tiles.  With d_sched
+// (device ints, written by an earlier kernel) only the problems it lists are computed:
+// d_sched[0] = count A, d_sched[1] = their tiles, d_sched[2 + j] = problem index of entry j,
+// d_sched[2 + nprob + j] = first tile of entry j; total_tiles and grid are then upper bounds.
 cudaError_t gemm_launch(GemmKind kind, bool b_kmajor, int bn, GemmEpi epi,
                         const GemmProblem *d_probs, int nprob, int total_tiles, int grid,
-                        int *d_status, uint64_t budget_ns, cudaStream_t stream);
+                        int *d_status, uint64_t budget_ns, cudaStream_t stream,
+                        const int *d_sched = nullptr);
 int gemm_tile_m();
 // Set the kernel's shared-memory attribute ahead of time (e.g. before a stream capture).
 cudaError_t gemm_prepare(GemmKind kind, bool b_kmajor, int bn, GemmEpi epi);
@@ -122,8 +126,14 @@ cudaError_t bits_to_e4m3(const uint64_t *bits, int64_t wp, int np, uint8_t *C, c
 // exclusive scan); after reading ptr[n] (= nnz) the caller sizes col and runs csr_fill.
 cudaError_t csr_build(const uint8_t *E, int n, int *cnt, int *ptr, cudaStream_t s);
 cudaError_t csr_fill(const uint8_t *E, int n, const int *ptr, int *col, cudaStream_t s);
+// csr_build plus the ingest's checks in the same pass: status |= ST_BAD_INPUT on a byte other
+// than 0/1, *dmax = ||E||_inf, *nnz += facts, *diag += self-loops (counters zeroed by the caller).
+cudaError_t csr_build_checked(const uint8_t *E, int n, int *cnt, int *ptr, unsigned long long *dmax,
+                              unsigned long long *nnz, unsigned long long *diag, int *status, cudaStream_t s);
 // out[0..n] = exclusive prefix sums of cnt[0..n-1] (out[n] = total); one CTA.
 cudaError_t exclusive_scan(const int *cnt, int n, int *out, cudaStream_t s);
+// The same with every SM taking part, for long arrays (scratch: 2 * (ceil(n / 1024) + 1) ints).
+cudaError_t exclusive_scan_large(const int *cnt, int n, int *out, int *scratch, cudaStream_t s);
 
 // ---------------------------------------------------------------------------------------
 // FP64 path (dl_fp64.cu)

@@ -384,8 +384,9 @@ dl_status tc_auto(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &a
     NEED(C[0] && C[1] && rbits && mbits && cnt && ptr && uoff);
     CK(cudaMemsetAsync(ws.scal, 0, kScalars * sizeof(unsigned long long), s));
     CK(cudaMemsetAsync(ws.status, 0, sizeof(int), s));
-    if ((rc = ingest(ctx, ws, s, E, n, np, C[0], 1, SC_DMAX, SC_NNZ, SC_COUNT0, &launches))) return rc;
-    CK(csr_build(E, n, cnt, ptr, s));
+    // one pass over E: 0/1 check, row counts, ||E||_inf, nnz, self-loops (the e4m3 operand is
+    // only built if a squaring happens)
+    CK(csr_build_checked(E, n, cnt, ptr, ws.scal + SC_DMAX, ws.scal + SC_NNZ, ws.scal + SC_COUNT0, ws.status, s));
     launches += 2;
     if ((rc = read_scalars(ws, s))) return rc;
     if ((rc = check_status(ws, s))) return rc;
@@ -394,7 +395,8 @@ dl_status tc_auto(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &a
     if ((rc = choose_eps(a.eps, 1.0 / (1.0 + static_cast<double>(dmax)), "Lemma 1 (1/(1+||E||))", &eps)))
         return rc;
     const int64_t nnz = static_cast<int64_t>(host_scal(ws)[SC_NNZ]);
-    unsigned long long prev = host_scal(ws)[SC_COUNT0];
+    // ones of C_0 = I + E over the padded size: the diagonal plus the facts off it
+    unsigned long long prev = static_cast<unsigned long long>(np) + host_scal(ws)[SC_NNZ] - host_scal(ws)[SC_COUNT0];
     auto *col = static_cast<int *>(ws.get("g_col", static_cast<size_t>(std::max<int64_t>(nnz, 1)) * 4));
     NEED(col);
     CK(csr_fill(E, n, ptr, col, s));
@@ -432,7 +434,7 @@ dl_status tc_auto(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &a
     const int max_squarings = 2 + static_cast<int>(std::ceil(std::log2(static_cast<double>(np) + 1.0)));
     const int max_sweeps = static_cast<int>(std::min<int64_t>(2 * static_cast<int64_t>(n) + 16, 1 << 20));
     int cur = 0, squarings = 0, sweeps = 0;
-    bool c_valid = true;  // C[cur] holds the same matrix as rbits
+    bool c_valid = false;  // C[cur] holds the same matrix as rbits
     bool converged = false, do_square = dense;
     int since_square = 0;  // sweeps since the last squaring
     unsigned long long *vslot = ws.scal + 32;  // up to 16 violation counters, one per sweep

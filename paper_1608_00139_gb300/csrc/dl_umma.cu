@@ -77,6 +77,28 @@ __device__ __forceinline__ bool gated_off(const GemmProblem *P) {
     return P->gate != nullptr && *reinterpret_cast<const volatile int *>(P->gate) != 0;
 }
 
+// Tile `tile` of the launch: its problem (null if gated off) and its index inside that
+// problem.  With a device schedule the tile space is that of the listed problems only:
+// sched[0] = count A, sched[1] = tiles, sched[2 + j] = problem of entry j (j < A), and
+// sched[2 + nprob + j] = first tile of entry j.
+__device__ __forceinline__ const GemmProblem *resolve_tile(const GemmProblem *probs, int nprob,
+                                                           const int *sched, int tile, int *local) {
+    if (sched == nullptr) {
+        const GemmProblem *P = find_problem(probs, nprob, tile);
+        *local = tile - P->tile_start;
+        return gated_off(P) ? nullptr : P;
+    }
+    const int *start = sched + 2 + nprob;
+    int lo = 0, hi = sched[0] - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (start[mid] <= tile) lo = mid;
+        else hi = mid - 1;
+    }
+    *local = tile - start[lo];
+    return probs + sched[2 + lo];
+}
+
 // Does k-block kb of output tile (mb, nb) contribute?  (always, without occupancy maps)
 template <int BN>
 __device__ __forceinline__ bool kblock_live(const GemmProblem *P, int mb, int nb, int kb) {
@@ -160,8 +182,14 @@ __device__ __forceinline__ void epi_sub_chunk(const GemmEpilogue &e, int row, in
 template <int KIND, int BN, bool B_KMAJOR, int EPI>
 __global__ void __launch_bounds__(kThreads, 1)
     umma_gemm_kernel(const GemmProblem *__restrict__ probs, int nprob, int total_tiles,
-                     int *status, uint64_t budget_ns) {
+                     const int *__restrict__ sched, int *status, uint64_t budget_ns) {
     using C = Cfg<KIND, BN>;
+    // A device schedule fixes the tile count; CTAs without a tile leave before any setup
+    // (the value is the same for every thread of the CTA).
+    if (sched != nullptr) {
+        total_tiles = sched[1];
+        if (static_cast<int>(blockIdx.x) >= total_tiles) return;
+    }
     constexpr uint32_t IDESC = make_idesc<KIND, BN, B_KMAJOR>();
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) &
@@ -207,9 +235,9 @@ __global__ void __launch_bounds__(kThreads, 1)
             uint64_t issued = 0;
             bool ok = true;
             for (int tile = blockIdx.x; tile < total_tiles && ok; tile += gridDim.x) {
-                const GemmProblem *P = find_problem(probs, nprob, tile);
-                if (gated_off(P)) continue;
-                const int local = tile - P->tile_start;
+                int local = 0;
+                const GemmProblem *P = resolve_tile(probs, nprob, sched, tile, &local);
+                if (P == nullptr) continue;
                 const int mb = local % P->tiles_m, nb = local / P->tiles_m;
                 const int nkb = P->K / C::BK;
                 for (int kb = 0; kb < nkb; ++kb) {
@@ -254,9 +282,9 @@ __global__ void __launch_bounds__(kThreads, 1)
             uint32_t acc_ph = 0;
             bool ok = true;
             for (int tile = blockIdx.x; tile < total_tiles && ok; tile += gridDim.x) {
-                const GemmProblem *P = find_problem(probs, nprob, tile);
-                if (gated_off(P)) continue;
-                const int local = tile - P->tile_start;
+                int local = 0;
+                const GemmProblem *P = resolve_tile(probs, nprob, sched, tile, &local);
+                if (P == nullptr) continue;
                 const int mb = local % P->tiles_m, nb = local / P->tiles_m;
                 const int nkb = P->K / C::BK;
                 if (!mbar_wait_bounded(&acce[acc], acc_ph ^ 1u, budget_ns, status,
@@ -309,9 +337,9 @@ __global__ void __launch_bounds__(kThreads, 1)
         int acc = 0;
         uint32_t acc_ph = 0;
         for (int tile = blockIdx.x; tile < total_tiles; tile += gridDim.x) {
-            const GemmProblem *P = find_problem(probs, nprob, tile);
-            if (gated_off(P)) continue;
-            const int local = tile - P->tile_start;
+            int local = 0;
+            const GemmProblem *P = resolve_tile(probs, nprob, sched, tile, &local);
+            if (P == nullptr) continue;
             const int mb = local % P->tiles_m, nb = local / P->tiles_m;
             if (!mbar_wait_bounded(&accf[acc], acc_ph, budget_ns, status, ST_TIMEOUT_ACC_FULL))
                 break;
@@ -424,13 +452,13 @@ cudaError_t prepare_t() {
 }
 
 template <int KIND, int BN, bool BK_, int EPI>
-cudaError_t launch_t(const GemmProblem *d_probs, int nprob, int total_tiles, int grid, int *status,
-                     uint64_t budget, cudaStream_t s) {
+cudaError_t launch_t(const GemmProblem *d_probs, int nprob, int total_tiles, const int *sched, int grid,
+                     int *status, uint64_t budget, cudaStream_t s) {
     using C = Cfg<KIND, BN>;
     const cudaError_t attr_err = prepare_t<KIND, BN, BK_, EPI>();
     if (attr_err != cudaSuccess) return attr_err;
     umma_gemm_kernel<KIND, BN, BK_, EPI><<<grid, kThreads, C::SMEM, s>>>(d_probs, nprob, total_tiles,
-                                                                         status, budget);
+                                                                         sched, status, budget);
     return cudaGetLastError();
 }
 
@@ -487,29 +515,23 @@ bool gemm_make_problem(GemmProblem *p, GemmKind kind, bool b_kmajor, int bn, int
 
 cudaError_t gemm_launch(GemmKind kind, bool b_kmajor, int bn, GemmEpi epi, const GemmProblem *d_probs,
                         int nprob, int total_tiles, int grid, int *d_status, uint64_t budget_ns,
-                        cudaStream_t stream) {
+                        cudaStream_t stream, const int *d_sched) {
     if (total_tiles <= 0) return cudaSuccess;
     if (grid > total_tiles) grid = total_tiles;
+    const int *sc = d_sched;
+#define DL_GEMM_T(K_, BN_, BKM_, EPI_) \
+    launch_t<K_, BN_, BKM_, EPI_>(d_probs, nprob, total_tiles, sc, grid, d_status, budget_ns, stream)
     if (kind == KIND_F8 && epi == EPI_BOOL) {
         if (bn == 256)
-            return b_kmajor ? launch_t<KIND_F8, 256, true, EPI_BOOL>(d_probs, nprob, total_tiles, grid,
-                                                                      d_status, budget_ns, stream)
-                            : launch_t<KIND_F8, 256, false, EPI_BOOL>(d_probs, nprob, total_tiles,
-                                                                       grid, d_status, budget_ns,
-                                                                       stream);
+            return b_kmajor ? DL_GEMM_T(KIND_F8, 256, true, EPI_BOOL) : DL_GEMM_T(KIND_F8, 256, false, EPI_BOOL);
         if (bn == 128)
-            return b_kmajor ? launch_t<KIND_F8, 128, true, EPI_BOOL>(d_probs, nprob, total_tiles, grid,
-                                                                      d_status, budget_ns, stream)
-                            : launch_t<KIND_F8, 128, false, EPI_BOOL>(d_probs, nprob, total_tiles,
-                                                                       grid, d_status, budget_ns,
-                                                                       stream);
+            return b_kmajor ? DL_GEMM_T(KIND_F8, 128, true, EPI_BOOL) : DL_GEMM_T(KIND_F8, 128, false, EPI_BOOL);
     }
     if (kind == KIND_TF32 && epi == EPI_SUB_F32 && bn == 128 && b_kmajor)
-        return launch_t<KIND_TF32, 128, true, EPI_SUB_F32>(d_probs, nprob, total_tiles, grid,
-                                                            d_status, budget_ns, stream);
+        return DL_GEMM_T(KIND_TF32, 128, true, EPI_SUB_F32);
     if (kind == KIND_TF32 && epi == EPI_STORE_F32 && bn == 128 && b_kmajor)
-        return launch_t<KIND_TF32, 128, true, EPI_STORE_F32>(d_probs, nprob, total_tiles, grid,
-                                                              d_status, budget_ns, stream);
+        return DL_GEMM_T(KIND_TF32, 128, true, EPI_STORE_F32);
+#undef DL_GEMM_T
     return cudaErrorInvalidValue;
 }
 

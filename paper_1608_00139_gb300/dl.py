@@ -119,8 +119,9 @@ def _is_torch(x) -> bool:
     return type(x).__module__.startswith("torch")
 
 
-def _square_u8(x):
-    """(pointer, n, mem, keepalive) of a square 0/1 uint8 matrix (numpy or torch CUDA)."""
+def _square_u8(x, sync=True):
+    """(pointer, n, mem, keepalive) of a square 0/1 uint8 matrix (numpy or torch CUDA).
+    sync=False leaves the wait for torch's pending writes to the caller."""
     if _is_torch(x):
         import torch
         if not x.is_cuda:
@@ -130,7 +131,8 @@ def _square_u8(x):
                 raise ValueError("expected a square torch.uint8 CUDA tensor")
             x = x.contiguous()
             # the library reads on its own stream: finish torch's pending writes first
-            torch.cuda.current_stream(x.device).synchronize()
+            if sync:
+                torch.cuda.current_stream(x.device).synchronize()
             return x.data_ptr(), int(x.shape[0]), DL_MEM_DEVICE, x
     a = np.ascontiguousarray(x, dtype=np.uint8)
     if a.ndim != 2 or a.shape[0] != a.shape[1]:
@@ -240,14 +242,28 @@ class Context:
 
     def tc_batch(self, Es):
         """Closure of each matrix in ``Es`` in one batched call; returns (bits list, stats)."""
-        parts = [_square_u8(e) for e in Es]
+        parts = [_square_u8(e, sync=False) for e in Es]
         if not parts:
             return [], Stats().as_dict()
         mems = {m for _, _, m, _ in parts}
         if len(mems) != 1:
             raise ValueError("all matrices must live in the same memory kind")
         mem = mems.pop()
-        outs = [_alloc_bits(n, mem, keep) for _, n, _, keep in parts]
+        if mem == DL_MEM_DEVICE:
+            import torch
+            devs = {keep.device for _, _, _, keep in parts}
+            for d in devs:
+                torch.cuda.current_stream(d).synchronize()
+            if len(devs) == 1:
+                # one allocation, one view per model (the library writes every word)
+                sizes = [n * words(n) for _, n, _, _ in parts]
+                flat = torch.empty(sum(sizes), dtype=torch.int64, device=devs.pop())
+                views = [v.view(n, words(n)) for v, (_, n, _, _) in zip(flat.split(sizes), parts)]
+                outs = [(v, v.data_ptr()) for v in views]
+            else:
+                outs = [_alloc_bits(n, mem, keep) for _, n, _, keep in parts]
+        else:
+            outs = [_alloc_bits(n, mem, keep) for _, n, _, keep in parts]
         cnt = len(parts)
         ns = (ctypes.c_int32 * cnt)(*[n for _, n, _, _ in parts])
         ptrs = (ctypes.c_void_p * cnt)(*[p for p, _, _, _ in parts])
