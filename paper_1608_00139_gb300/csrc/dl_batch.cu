@@ -25,6 +25,7 @@
 
 #include "dl_ctx.h"
 #include "dl_internal.h"
+#include "dl_rows.cuh"
 
 namespace dl {
 
@@ -83,18 +84,8 @@ __global__ void batch_map_kernel(const BatchInst *__restrict__ inst, int *pinst)
     for (int r = threadIdx.x; r < I.np; r += blockDim.x) pinst[I.prow0 + r] = blockIdx.x;
 }
 
-// Low bits of the four bytes of x as a 4-bit mask (byte b -> bit b).
-__device__ __forceinline__ uint32_t byte_lsbs(uint32_t x) { return ((x & 0x01010101u) * 0x01020408u) >> 24; }
-// Bytes of x with any of bits 1..7 set, as a 4-bit mask.
-__device__ __forceinline__ uint32_t byte_bad(uint32_t x) {
-    const uint32_t t = (x >> 1) & 0x7F7F7F7Fu;
-    return byte_lsbs(((t + 0x7F7F7F7Fu) | t) >> 7);
-}
-
 // Bits of row r of I + E_k into M (one warp per padded row), the row's successor count and
-// the 0/1 check.  The row is read as aligned 16-byte chunks; lane L of segment s holds the
-// 64 bytes that start 64 (32 s + L) bytes after the aligned address below the row, and the
-// model words are those 64-bit groups shifted by the row's misalignment.
+// the 0/1 check.
 __global__ void __launch_bounds__(256)
     batch_pack_kernel(const BatchInst *__restrict__ inst, const int *__restrict__ pinst, int total_prows,
                       int *cnt, int *status) {
@@ -104,70 +95,20 @@ __global__ void __launch_bounds__(256)
     const BatchInst I = inst[pinst[g]];
     const int r = g - I.prow0;
     uint64_t *row = I.rbits + static_cast<int64_t>(r) * I.wp;
-    const int idw = r >> 6;
-    const uint64_t idb = 1ull << (r & 63);
     if (r >= I.n) {  // padding: identity only
-        for (int w = lane; w < I.wp; w += 32) row[w] = w == idw ? idb : 0ull;
+        for (int w = lane; w < I.wp; w += 32) row[w] = w == (r >> 6) ? 1ull << (r & 63) : 0ull;
         return;
     }
-    const uint8_t *a = I.E + static_cast<int64_t>(r) * I.n;
-    const int off = static_cast<int>(reinterpret_cast<uintptr_t>(a) & 15);
-    const uint8_t *base = a - off;
-    const int lim = off + I.n;  // bytes of the row occupy [off, lim) from base
-    const int nseg = I.wp / 32 + 1;
-    uint32_t bad = 0;
     int c = 0;
-    uint64_t carry = 0;
-    auto shifted = [off](uint64_t lo, uint64_t hi) { return off ? (lo >> off) | (hi << (64 - off)) : lo; };
-    for (int sg = 0; sg < nseg; ++sg) {
-        const int u = 32 * sg + lane;
-        uint64_t vw = 0;
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-            const int v0 = 64 * u + 16 * j;
-            if (v0 < lim) {
-                const uint4 x = *reinterpret_cast<const uint4 *>(base + v0);
-                const int lo = max(0, off - v0), hi = min(16, lim - v0);
-                const uint32_t valid = ((1u << hi) - 1u) & ~((1u << lo) - 1u);
-                const uint32_t m = byte_lsbs(x.x) | (byte_lsbs(x.y) << 4) | (byte_lsbs(x.z) << 8) |
-                                   (byte_lsbs(x.w) << 12);
-                const uint32_t b = byte_bad(x.x) | (byte_bad(x.y) << 4) | (byte_bad(x.z) << 8) |
-                                   (byte_bad(x.w) << 12);
-                vw |= static_cast<uint64_t>(m & valid) << (16 * j);
-                bad |= b & valid;
-            }
-        }
-        c += __popcll(vw);
-        const uint64_t nxt = __shfl_down_sync(kFull, vw, 1);
-        const uint64_t first = __shfl_sync(kFull, vw, 0);
-        if (sg > 0 && lane == 31) {
-            const int w = 32 * (sg - 1) + 31;
-            if (w < I.wp) row[w] = shifted(carry, first) | (w == idw ? idb : 0ull);
-        }
-        if (lane < 31) {
-            const int w = 32 * sg + lane;
-            if (w < I.wp) row[w] = shifted(vw, nxt) | (w == idw ? idb : 0ull);
-        }
-        carry = vw;
-    }
-    if (lane == 31) {
-        const int w = 32 * (nseg - 1) + 31;
-        if (w < I.wp) row[w] = shifted(carry, 0ull) | (w == idw ? idb : 0ull);
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        c += __shfl_xor_sync(kFull, c, o);
-        bad |= __shfl_xor_sync(kFull, bad, o);
-    }
+    bool bad = false;
+    pack_row_bits(I.E + static_cast<int64_t>(r) * I.n, I.n, r, I.wp, row, lane, c, bad);
     if (lane == 0) {
         cnt[I.row0 + r] = c;
         if (bad) atomicOr(status, ST_BAD_INPUT);
     }
 }
 
-// Successor lists from the packed bits (one warp per padded row, real rows only).  The
-// identity bit belongs to E only when E has the self-loop: then the packed row holds exactly
-// the row's count of ones.
+// Successor lists from the packed bits (one warp per padded row, real rows only).
 __global__ void __launch_bounds__(256)
     batch_fill_kernel(const BatchInst *__restrict__ inst, const int *__restrict__ pinst, int total_prows,
                       const int *__restrict__ ptr, int *col) {
@@ -177,33 +118,8 @@ __global__ void __launch_bounds__(256)
     const BatchInst I = inst[pinst[g]];
     const int r = g - I.prow0;
     if (r >= I.n) return;
-    const uint64_t *row = I.rbits + static_cast<int64_t>(r) * I.wp;
     const int gr = I.row0 + r;
-    int ones = 0;
-    for (int w = lane; w < I.wp; w += 32) ones += __popcll(row[w]);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) ones += __shfl_xor_sync(kFull, ones, o);
-    int pos = ptr[gr];
-    const bool self = ones == ptr[gr + 1] - pos;
-    for (int w0 = 0; w0 < I.wp; w0 += 32) {
-        const int w = w0 + lane;
-        uint64_t x = w < I.wp ? row[w] : 0ull;
-        if (!self && w == (r >> 6)) x &= ~(1ull << (r & 63));
-        const int c = __popcll(x);
-        int inc = c;
-#pragma unroll
-        for (int o = 1; o < 32; o <<= 1) {
-            const int t = __shfl_up_sync(kFull, inc, o);
-            if (lane >= o) inc += t;
-        }
-        int p = pos + inc - c;
-        while (x) {
-            const int b = __ffsll(static_cast<long long>(x)) - 1;
-            x &= x - 1;
-            col[p++] = 64 * w + b;
-        }
-        pos += __shfl_sync(kFull, inc, 31);
-    }
+    fill_row_from_bits(I.rbits + static_cast<int64_t>(r) * I.wp, I.wp, r, ptr[gr], ptr[gr + 1], col, lane);
 }
 
 // Block-wide exclusive scan of four counters at once (kListThreads threads).

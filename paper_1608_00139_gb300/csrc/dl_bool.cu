@@ -197,14 +197,17 @@ __device__ __forceinline__ void or_successors(const int *__restrict__ col, int q
     }
 }
 
-// mode 1 (in place): M_i |= E_i | OR_{k in succ(i)} M_k; counts changed rows.
+// mode 1 (in place): M_i |= E_i | OR_{k in succ(i)} M_k; counts changed rows.  A sweep that
+// follows one which changed nothing has nothing to do: with skip_if_zero pointing at the
+// previous sweep's counter, the grid leaves at once.
 template <int WPL>
 __global__ void __launch_bounds__(256)
     sweep_rows_step_kernel(const int *__restrict__ ptr, const int *__restrict__ col, int n, uint64_t *M, int64_t wp,
-                           unsigned long long *changed_rows) {
+                           unsigned long long *changed_rows, const unsigned long long *skip_if_zero) {
     const int lane = threadIdx.x & 31;
     const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (i >= n) return;
+    if (skip_if_zero != nullptr && *skip_if_zero == 0) return;  // the previous sweep changed nothing
     const int q0 = ptr[i], q1 = ptr[i + 1];
     if (q0 == q1) return;
     uint64_t *mrow = M + static_cast<int64_t>(i) * wp;
@@ -270,10 +273,11 @@ __global__ void __launch_bounds__(256)
 
 template <int WPL>
 cudaError_t launch_rows(const int *ptr, const int *col, int n, const uint64_t *M, uint64_t *out, int64_t wp,
-                        int mode, unsigned long long *violations, unsigned long long *ones, cudaStream_t s) {
+                        int mode, unsigned long long *violations, unsigned long long *ones,
+                        const unsigned long long *skip, cudaStream_t s) {
     if (mode == 1)
         sweep_rows_step_kernel<WPL><<<(n + 7) / 8, 256, 0, s>>>(ptr, col, n, const_cast<uint64_t *>(M), wp,
-                                                                 violations);
+                                                                 violations, skip);
     else
         sweep_rows_emit_kernel<WPL><<<(n + 7) / 8, 256, 0, s>>>(ptr, col, n, M, out, wp, violations, ones);
     return cudaGetLastError();
@@ -282,8 +286,10 @@ cudaError_t launch_rows(const int *ptr, const int *col, int n, const uint64_t *M
 // mode 1 (closure step, in place): M_i |= E_i | OR_{k in succ(i)} M_k; counts changed units.
 __global__ void __launch_bounds__(256)
     sweep_units_step_kernel(const int *__restrict__ ptr, const int *__restrict__ col, const int *__restrict__ unit_off,
-                            int n, uint64_t *M, int64_t wp, unsigned long long *changed_units) {
+                            int n, uint64_t *M, int64_t wp, unsigned long long *changed_units,
+                            const unsigned long long *skip_if_zero) {
     const int lane = threadIdx.x & 31;
+    if (skip_if_zero != nullptr && *skip_if_zero == 0) return;  // the previous sweep changed nothing
     const int total = unit_off[n];
     const int warps = gridDim.x * (blockDim.x >> 5);
     for (int u = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); u < total; u += warps) {
@@ -369,6 +375,8 @@ __global__ void bits_to_e4m3_kernel(const uint64_t *__restrict__ bits, int64_t w
 
 }  // namespace
 
+bool row_direct(int max_deg, int64_t wp) { return max_deg >= 0 && max_deg <= kRowDirect && wp <= 256; }
+
 cudaError_t sweep_units(const int *ptr, int n, int *cnt, int *unit_off, cudaStream_t s) {
     unit_count_kernel<<<(n + 255) / 256, 256, 0, s>>>(ptr, n, cnt);
     return exclusive_scan(cnt, n, unit_off, s);
@@ -376,18 +384,19 @@ cudaError_t sweep_units(const int *ptr, int n, int *cnt, int *unit_off, cudaStre
 
 cudaError_t bits_sweep_csr(const int *ptr, const int *col, const int *unit_off, int n, const uint64_t *M,
                            uint64_t *out, int64_t wp, int mode, unsigned long long *violations,
-                           unsigned long long *ones, int *launches, cudaStream_t s, int max_deg) {
+                           unsigned long long *ones, int *launches, cudaStream_t s, int max_deg,
+                           const unsigned long long *skip_if_zero) {
     if (n <= 0) return cudaSuccess;
-    if (max_deg >= 0 && max_deg <= kRowDirect && wp <= 256) {  // no heavy rows: row-direct kernels
+    if (row_direct(max_deg, wp)) {  // no heavy rows: row-direct kernels
         if (launches) *launches += 1;
-        if (wp <= 64) return launch_rows<2>(ptr, col, n, M, out, wp, mode, violations, ones, s);
-        if (wp <= 128) return launch_rows<4>(ptr, col, n, M, out, wp, mode, violations, ones, s);
-        return launch_rows<8>(ptr, col, n, M, out, wp, mode, violations, ones, s);
+        if (wp <= 64) return launch_rows<2>(ptr, col, n, M, out, wp, mode, violations, ones, skip_if_zero, s);
+        if (wp <= 128) return launch_rows<4>(ptr, col, n, M, out, wp, mode, violations, ones, skip_if_zero, s);
+        return launch_rows<8>(ptr, col, n, M, out, wp, mode, violations, ones, skip_if_zero, s);
     }
     const unsigned grid = static_cast<unsigned>(num_sms() * 8);
     if (mode == 1) {
         sweep_units_step_kernel<<<grid, 256, 0, s>>>(ptr, col, unit_off, n, const_cast<uint64_t *>(M), wp,
-                                                      violations);
+                                                      violations, skip_if_zero);
         if (launches) *launches += 1;
         return cudaGetLastError();
     }

@@ -5,6 +5,7 @@
 #include <cstdint>
 
 #include "dl_internal.h"
+#include "dl_rows.cuh"
 
 namespace dl {
 
@@ -33,68 +34,98 @@ __global__ void csr_count_kernel(const uint8_t *__restrict__ E, int n, int *cnt)
     if (lane == 0) cnt[i] = c;
 }
 
-// Successor counts plus the ingest's checks in the same pass: bytes other than 0/1 set the
-// status bit, row counts reduce to max (||E||_inf) and total (nnz), and the diagonal facts
-// (self-loops) are counted.
-__global__ void csr_count_check_kernel(const uint8_t *__restrict__ E, int n, int *cnt, unsigned long long *dmax,
-                                       unsigned long long *nnz, unsigned long long *diag, int *status) {
+// One pass over E (warp per padded row): bits of I + E into M, successor counts, the 0/1
+// check, ||E||_inf (max row count), nnz and the number of self-loops.
+__global__ void __launch_bounds__(256)
+    csr_pack_check_kernel(const uint8_t *__restrict__ E, int n, int np, int wp, int *cnt, uint64_t *M,
+                          unsigned long long *dmax, unsigned long long *nnz, unsigned long long *diag,
+                          int *status) {
     const int lane = threadIdx.x & 31;
-    const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (i >= n) return;
-    const uint8_t *row = E + static_cast<int64_t>(i) * n;
+    const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (r >= np) return;
+    uint64_t *row = M + static_cast<int64_t>(r) * wp;
+    if (r >= n) {  // padding: identity only
+        for (int w = lane; w < wp; w += 32) row[w] = w == (r >> 6) ? 1ull << (r & 63) : 0ull;
+        return;
+    }
+    const uint8_t *a = E + static_cast<int64_t>(r) * n;
     int c = 0;
-    uint32_t bad = 0;
-    if ((n & 15) == 0 && (reinterpret_cast<uintptr_t>(E) & 15) == 0) {
-        const uint4 *r4 = reinterpret_cast<const uint4 *>(row);
-        for (int q = lane; q < n / 16; q += 32) {
-            const uint4 x = r4[q];
-            bad |= (x.x | x.y | x.z | x.w) & 0xFEFEFEFEu;
-            c += __popc(x.x & 0x01010101u) + __popc(x.y & 0x01010101u) + __popc(x.z & 0x01010101u) +
-                 __popc(x.w & 0x01010101u);
-        }
-    } else {
-        for (int j = lane; j < n; j += 32) {
-            bad |= row[j] & 0xFEu;
-            c += row[j] & 1;
-        }
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-        c += __shfl_xor_sync(0xffffffffu, c, o);
-        bad |= __shfl_xor_sync(0xffffffffu, bad, o);
-    }
+    bool bad = false;
+    pack_row_bits(a, n, r, wp, row, lane, c, bad);
     if (lane == 0) {
-        cnt[i] = c;
+        cnt[r] = c;
         if (bad) atomicOr(status, ST_BAD_INPUT);
         if (c) {
             atomicMax(dmax, static_cast<unsigned long long>(c));
             atomicAdd(nnz, static_cast<unsigned long long>(c));
         }
-        if (row[i] & 1) atomicAdd(diag, 1ull);
+        if (a[r] & 1) atomicAdd(diag, 1ull);
     }
 }
 
+__global__ void __launch_bounds__(256)
+    csr_fill_bits_kernel(const uint64_t *__restrict__ M, int n, int wp, const int *__restrict__ ptr, int *col) {
+    const int lane = threadIdx.x & 31;
+    const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (r >= n) return;
+    fill_row_from_bits(M + static_cast<int64_t>(r) * wp, wp, r, ptr[r], ptr[r + 1], col, lane);
+}
+
+// Exclusive scan in one CTA: each thread holds 16 consecutive counts in registers, a warp
+// scan and a scan of the warp totals place them; long inputs go round in tiles of 16384.
 __global__ void __launch_bounds__(1024) exclusive_scan_kernel(const int *cnt, int n, int *ptr) {
-    __shared__ int part[1024];
-    const int t = threadIdx.x;
-    const int chunk = (n + 1023) / 1024;
-    const int b = t * chunk, e = min(n, b + chunk);
-    int s = 0;
-    for (int i = b; i < e; ++i) s += cnt[i];
-    part[t] = s;
-    __syncthreads();
-    for (int o = 1; o < 1024; o <<= 1) {  // inclusive Hillis-Steele scan of the partial sums
-        const int v = t >= o ? part[t - o] : 0;
+    __shared__ int warp_tot[32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const bool vec = (reinterpret_cast<uintptr_t>(cnt) & 15) == 0;
+    int carry = 0;
+    for (int base = 0; base < n; base += 1024 * 16) {
+        const int b = base + static_cast<int>(threadIdx.x) * 16;
+        int v[16];
+        if (vec && b + 16 <= n) {
+            const int4 *c4 = reinterpret_cast<const int4 *>(cnt + b);
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+                const int4 x = c4[q];
+                v[4 * q] = x.x;
+                v[4 * q + 1] = x.y;
+                v[4 * q + 2] = x.z;
+                v[4 * q + 3] = x.w;
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < 16; ++j) v[j] = b + j < n ? cnt[b + j] : 0;
+        }
+        int sum = 0;
+#pragma unroll
+        for (int j = 0; j < 16; ++j) sum += v[j];
+        int inc = sum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += t;
+        }
+        if (lane == 31) warp_tot[warp] = inc;
         __syncthreads();
-        part[t] += v;
+        if (warp == 0) {
+            int w = warp_tot[lane];
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const int t = __shfl_up_sync(0xffffffffu, w, o);
+                if (lane >= o) w += t;
+            }
+            warp_tot[lane] = w;
+        }
         __syncthreads();
+        int run = carry + (warp > 0 ? warp_tot[warp - 1] : 0) + inc - sum;
+#pragma unroll
+        for (int j = 0; j < 16; ++j) {
+            if (b + j < n) ptr[b + j] = run;
+            run += v[j];
+        }
+        carry += warp_tot[31];
+        __syncthreads();  // warp_tot is rewritten by the next tile
     }
-    int run = t > 0 ? part[t - 1] : 0;
-    for (int i = b; i < e; ++i) {
-        ptr[i] = run;
-        run += cnt[i];
-    }
-    if (t == 1023) ptr[n] = part[1023];
+    if (threadIdx.x == 0) ptr[n] = carry;
 }
 
 // Column indices in increasing order, one warp per row: each lane takes 16 bytes of a
@@ -148,10 +179,17 @@ cudaError_t csr_build(const uint8_t *E, int n, int *cnt, int *ptr, cudaStream_t 
     return cudaGetLastError();
 }
 
-cudaError_t csr_build_checked(const uint8_t *E, int n, int *cnt, int *ptr, unsigned long long *dmax,
-                              unsigned long long *nnz, unsigned long long *diag, int *status, cudaStream_t s) {
-    csr_count_check_kernel<<<static_cast<unsigned>((n + 7) / 8), 256, 0, s>>>(E, n, cnt, dmax, nnz, diag, status);
+cudaError_t csr_pack_checked(const uint8_t *E, int n, int np, int64_t wp, int *cnt, int *ptr, uint64_t *M,
+                             unsigned long long *dmax, unsigned long long *nnz, unsigned long long *diag, int *status,
+                             cudaStream_t s) {
+    csr_pack_check_kernel<<<static_cast<unsigned>((np + 7) / 8), 256, 0, s>>>(E, n, np, static_cast<int>(wp), cnt,
+                                                                              M, dmax, nnz, diag, status);
     exclusive_scan_kernel<<<1, 1024, 0, s>>>(cnt, n, ptr);
+    return cudaGetLastError();
+}
+
+cudaError_t csr_fill_from_bits(const uint64_t *M, int n, int64_t wp, const int *ptr, int *col, cudaStream_t s) {
+    csr_fill_bits_kernel<<<static_cast<unsigned>((n + 7) / 8), 256, 0, s>>>(M, n, static_cast<int>(wp), ptr, col);
     return cudaGetLastError();
 }
 

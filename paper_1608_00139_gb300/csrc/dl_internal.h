@@ -109,10 +109,15 @@ cudaError_t bits_sweep(const uint8_t *E, int64_t lde, int n, const uint64_t *M, 
 // of scratch) once per CSR.  mode 1: in place (out must be M), *violations += changed units;
 // mode 0: out = E M (rows < n), *violations += rows with (out_i | e_i) != M_i, *ones += ones.
 cudaError_t sweep_units(const int *ptr, int n, int *cnt, int *unit_off, cudaStream_t s);
-// max_deg: ||E||_inf if known (rows of at most 256 successors take row-direct kernels), or -1.
+// max_deg: ||E||_inf if known (rows of at most 256 successors take row-direct kernels, which
+// need no unit_off), or -1.  skip_if_zero (mode 1): the previous sweep's counter; when it is
+// zero on the device the sweep does nothing (that sweep already proved convergence).
 cudaError_t bits_sweep_csr(const int *ptr, const int *col, const int *unit_off, int n, const uint64_t *M,
                            uint64_t *out, int64_t wp, int mode, unsigned long long *violations,
-                           unsigned long long *ones, int *launches, cudaStream_t s, int max_deg);
+                           unsigned long long *ones, int *launches, cudaStream_t s, int max_deg,
+                           const unsigned long long *skip_if_zero = nullptr);
+// Whether bits_sweep_csr takes the row-direct kernels (then unit_off is not read).
+bool row_direct(int max_deg, int64_t wp);
 // Bits of I + E (np rows x wp words) from the CSR of E.
 cudaError_t reflexive_bits(const int *ptr, const int *col, int n, int np, int64_t wp, uint64_t *bits,
                            cudaStream_t s);
@@ -126,10 +131,15 @@ cudaError_t bits_to_e4m3(const uint64_t *bits, int64_t wp, int np, uint8_t *C, c
 // exclusive scan); after reading ptr[n] (= nnz) the caller sizes col and runs csr_fill.
 cudaError_t csr_build(const uint8_t *E, int n, int *cnt, int *ptr, cudaStream_t s);
 cudaError_t csr_fill(const uint8_t *E, int n, const int *ptr, int *col, cudaStream_t s);
-// csr_build plus the ingest's checks in the same pass: status |= ST_BAD_INPUT on a byte other
-// than 0/1, *dmax = ||E||_inf, *nnz += facts, *diag += self-loops (counters zeroed by the caller).
-cudaError_t csr_build_checked(const uint8_t *E, int n, int *cnt, int *ptr, unsigned long long *dmax,
-                              unsigned long long *nnz, unsigned long long *diag, int *status, cudaStream_t s);
+// One pass over E: the bits of I + E into M (np rows of wp words; rows >= n hold only their
+// diagonal bit), the CSR row pointers, and the ingest's checks: status |= ST_BAD_INPUT on a
+// byte other than 0/1, *dmax = ||E||_inf, *nnz += facts, *diag += self-loops (counters zeroed
+// by the caller).  E's rows may have any alignment.
+cudaError_t csr_pack_checked(const uint8_t *E, int n, int np, int64_t wp, int *cnt, int *ptr, uint64_t *M,
+                             unsigned long long *dmax, unsigned long long *nnz, unsigned long long *diag, int *status,
+                             cudaStream_t s);
+// Column indices of E from the packed bits of I + E (as written by csr_pack_checked).
+cudaError_t csr_fill_from_bits(const uint64_t *M, int n, int64_t wp, const int *ptr, int *col, cudaStream_t s);
 // out[0..n] = exclusive prefix sums of cnt[0..n-1] (out[n] = total); one CTA.
 cudaError_t exclusive_scan(const int *cnt, int n, int *out, cudaStream_t s);
 // The same with every SM taking part, for long arrays (scratch: 2 * (ceil(n / 1024) + 1) ints).

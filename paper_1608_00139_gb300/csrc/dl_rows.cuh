@@ -1,5 +1,6 @@
 // dl_rows.cuh -- per-row device routines shared by the single-problem and batched kernels:
-// ingest of one row of a 0/1 base relation, and one row of the certificate / recheck sweep.
+// ingest of one row of a 0/1 base relation (as e4m3 or as bits), successor lists from bits,
+// and one row of the certificate / recheck sweep.
 #pragma once
 #include <cstdint>
 
@@ -192,6 +193,107 @@ __device__ __forceinline__ void sweep_row(const uint8_t *__restrict__ erow, int 
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) cnt += __shfl_xor_sync(0xffffffffu, cnt, o);
     cnt_out = cnt;
+}
+
+// Low bits of the four bytes of x as a 4-bit mask (byte b -> bit b).
+__device__ __forceinline__ uint32_t byte_lsbs(uint32_t x) { return ((x & 0x01010101u) * 0x01020408u) >> 24; }
+// Bytes of x with any of bits 1..7 set, as a 4-bit mask.
+__device__ __forceinline__ uint32_t byte_bad(uint32_t x) {
+    const uint32_t t = (x >> 1) & 0x7F7F7F7Fu;
+    return byte_lsbs(((t + 0x7F7F7F7Fu) | t) >> 7);
+}
+
+// One warp packs row r of a 0/1 byte matrix (the n bytes at a, any alignment) into wp 64-bit
+// words at `row`, plus the identity bit r.  The row is read as aligned 16-byte chunks: lane
+// L of segment s holds the 64 bytes that start 64 (32 s + L) bytes after the aligned address
+// below a, and each model word is two of those 64-bit groups shifted by the misalignment.
+// Bytes outside the row are masked off (they are never counted or checked).  Every lane
+// returns the row's count of ones (without the identity) and whether a byte was not 0/1.
+__device__ __forceinline__ void pack_row_bits(const uint8_t *a, int n, int r, int wp, uint64_t *row, int lane,
+                                              int &count, bool &bad_byte) {
+    const int idw = r >> 6;
+    const uint64_t idb = 1ull << (r & 63);
+    const int off = static_cast<int>(reinterpret_cast<uintptr_t>(a) & 15);
+    const uint8_t *base = a - off;
+    const int lim = off + n;  // the row occupies bytes [off, lim) from base
+    const int nseg = wp / 32 + 1;
+    uint32_t bad = 0;
+    int c = 0;
+    uint64_t carry = 0;
+    auto shifted = [off](uint64_t lo, uint64_t hi) { return off ? (lo >> off) | (hi << (64 - off)) : lo; };
+    for (int sg = 0; sg < nseg; ++sg) {
+        const int u = 32 * sg + lane;
+        uint64_t vw = 0;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int v0 = 64 * u + 16 * j;
+            if (v0 < lim) {
+                const uint4 x = *reinterpret_cast<const uint4 *>(base + v0);
+                const int lo = max(0, off - v0), hi = min(16, lim - v0);
+                const uint32_t valid = ((1u << hi) - 1u) & ~((1u << lo) - 1u);
+                const uint32_t m = byte_lsbs(x.x) | (byte_lsbs(x.y) << 4) | (byte_lsbs(x.z) << 8) |
+                                   (byte_lsbs(x.w) << 12);
+                const uint32_t b = byte_bad(x.x) | (byte_bad(x.y) << 4) | (byte_bad(x.z) << 8) |
+                                   (byte_bad(x.w) << 12);
+                vw |= static_cast<uint64_t>(m & valid) << (16 * j);
+                bad |= b & valid;
+            }
+        }
+        c += __popcll(vw);
+        const uint64_t nxt = __shfl_down_sync(0xffffffffu, vw, 1);
+        const uint64_t first = __shfl_sync(0xffffffffu, vw, 0);
+        if (sg > 0 && lane == 31) {
+            const int w = 32 * (sg - 1) + 31;
+            if (w < wp) row[w] = shifted(carry, first) | (w == idw ? idb : 0ull);
+        }
+        if (lane < 31) {
+            const int w = 32 * sg + lane;
+            if (w < wp) row[w] = shifted(vw, nxt) | (w == idw ? idb : 0ull);
+        }
+        carry = vw;
+    }
+    if (lane == 31) {
+        const int w = 32 * (nseg - 1) + 31;
+        if (w < wp) row[w] = shifted(carry, 0ull) | (w == idw ? idb : 0ull);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        c += __shfl_xor_sync(0xffffffffu, c, o);
+        bad |= __shfl_xor_sync(0xffffffffu, bad, o);
+    }
+    count = c;
+    bad_byte = bad != 0;
+}
+
+// One warp writes the successor list of row r into col[pos0 .. pos1) from its packed bits
+// (I + E: the identity bit belongs to E only when the row holds pos1 - pos0 ones).
+__device__ __forceinline__ void fill_row_from_bits(const uint64_t *row, int wp, int r, int pos0, int pos1, int *col,
+                                                   int lane) {
+    int ones = 0;
+    for (int w = lane; w < wp; w += 32) ones += __popcll(row[w]);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) ones += __shfl_xor_sync(0xffffffffu, ones, o);
+    const bool self = ones == pos1 - pos0;
+    int pos = pos0;
+    for (int w0 = 0; w0 < wp; w0 += 32) {
+        const int w = w0 + lane;
+        uint64_t x = w < wp ? row[w] : 0ull;
+        if (!self && w == (r >> 6)) x &= ~(1ull << (r & 63));
+        const int c = __popcll(x);
+        int inc = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int t = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += t;
+        }
+        int p = pos + inc - c;
+        while (x) {
+            const int b = __ffsll(static_cast<long long>(x)) - 1;
+            x &= x - 1;
+            col[p++] = 64 * w + b;
+        }
+        pos += __shfl_sync(0xffffffffu, inc, 31);
+    }
 }
 
 }  // namespace dl

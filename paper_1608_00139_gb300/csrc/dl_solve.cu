@@ -60,10 +60,16 @@ struct SweepClock {
         if (2 * k + 1 < Workspace::kGemmEvents) cudaEventRecord(ws.sev[2 * k], s);
     }
     void stop(int count, double bytes_each) {
+        stop();
+        account(count, bytes_each);
+    }
+    void stop() {
         if (2 * k + 1 < Workspace::kGemmEvents) {
             cudaEventRecord(ws.sev[2 * k + 1], s);
             ++k;
         }
+    }
+    void account(int count, double bytes_each) {  // sweeps that did their work
         launches += count;
         bytes += count * bytes_each;
     }
@@ -384,9 +390,10 @@ dl_status tc_auto(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &a
     NEED(C[0] && C[1] && rbits && mbits && cnt && ptr && uoff);
     CK(cudaMemsetAsync(ws.scal, 0, kScalars * sizeof(unsigned long long), s));
     CK(cudaMemsetAsync(ws.status, 0, sizeof(int), s));
-    // one pass over E: 0/1 check, row counts, ||E||_inf, nnz, self-loops (the e4m3 operand is
-    // only built if a squaring happens)
-    CK(csr_build_checked(E, n, cnt, ptr, ws.scal + SC_DMAX, ws.scal + SC_NNZ, ws.scal + SC_COUNT0, ws.status, s));
+    // one pass over E: the bits of C_0 = I + E, 0/1 check, row counts, ||E||_inf, nnz,
+    // self-loops (the e4m3 operand is only built if a squaring happens)
+    CK(csr_pack_checked(E, n, static_cast<int>(np), wp, cnt, ptr, rbits, ws.scal + SC_DMAX, ws.scal + SC_NNZ,
+                        ws.scal + SC_COUNT0, ws.status, s));
     launches += 2;
     if ((rc = read_scalars(ws, s))) return rc;
     if ((rc = check_status(ws, s))) return rc;
@@ -399,16 +406,23 @@ dl_status tc_auto(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &a
     unsigned long long prev = static_cast<unsigned long long>(np) + host_scal(ws)[SC_NNZ] - host_scal(ws)[SC_COUNT0];
     auto *col = static_cast<int *>(ws.get("g_col", static_cast<size_t>(std::max<int64_t>(nnz, 1)) * 4));
     NEED(col);
-    CK(csr_fill(E, n, ptr, col, s));
-    CK(sweep_units(ptr, n, cnt, uoff, s));
-    CK(reflexive_bits(ptr, col, n, static_cast<int>(np), wp, rbits, s));
-    launches += 4;
+    CK(csr_fill_from_bits(rbits, n, wp, ptr, col, s));
+    ++launches;
+    if (!row_direct(static_cast<int>(dmax), wp)) {  // heavy rows: edge-parallel work units
+        CK(sweep_units(ptr, n, cnt, uoff, s));
+        launches += 2;
+    }
     tm.mark(1);
 
-    // cost model (seconds): one squaring vs one sweep before rows saturate
+    // cost model (seconds): one squaring vs one sweep before rows saturate.  A sweep reads a
+    // successor's row per fact; the bit matrix is L2-resident up to a few tens of MB.
+    const double bit_bytes = static_cast<double>(np) * wp * 8;
+    const double sweep_rate = bit_bytes <= 48e6 ? 6.0e12 : 3.0e12;
     const double t_sq = 2.0 * np * np * np / 3.4e15 + 15e-6;
-    const double t_sw = (static_cast<double>(nnz) * wp * 8 + 2.0 * np * wp * 8) / 3.0e12 + 5e-6;
-    const bool dense = 4.0 * t_sw > t_sq;
+    const double t_sw = (static_cast<double>(nnz) * wp * 8 + 2.0 * bit_bytes) / sweep_rate + 5e-6;
+    // square first only when one unsaturated sweep costs more than a squaring (rows saturate
+    // within a sweep or two on dense graphs, so later sweeps are cheap)
+    const bool dense = t_sw > t_sq;
     // sweeps allowed between two squarings before a squaring is the cheaper way forward
     const int sweep_budget = static_cast<int>(std::max(4.0, std::floor(t_sq / t_sw)));
 
@@ -438,6 +452,19 @@ dl_status tc_auto(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &a
     bool converged = false, do_square = dense;
     int since_square = 0;  // sweeps since the last squaring
     unsigned long long *vslot = ws.scal + 32;  // up to 16 violation counters, one per sweep
+    // the model E M, checking M = min1(I + E M) on the way (straight into a device output whose
+    // rows have the same stride)
+    const bool direct = a.mem == DL_MEM_DEVICE && (n + 63) / 64 == wp;
+    uint64_t *model = direct ? a.out_bits : mbits;
+    auto emit = [&]() -> dl_status {
+        CK(cudaMemsetAsync(ws.scal + SC_VIOL, 0, 2 * sizeof(unsigned long long), s));
+        sc.start();
+        CK(bits_sweep_csr(ptr, col, uoff, n, rbits, model, wp, 0, ws.scal + SC_VIOL, ws.scal + SC_ONES, &launches, s,
+                          static_cast<int>(dmax)));
+        sc.stop(1, sweep_min_bytes);
+        return DL_OK;
+    };
+    bool emitted = false;
     while (!converged) {
         if (do_square) {
             if (squarings >= max_squarings) {
@@ -466,20 +493,29 @@ dl_status tc_auto(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &a
             }
             prev = c2;
         }
-        // a group of in-place sweeps, one host read for all of them (after a squaring the rows
-        // are dense and saturate within a few successors, so a short group is cheap)
+        // a group of in-place sweeps and, speculatively, the model (final if the group reached
+        // the fixpoint), then one host read for all of it (after a squaring the rows are dense
+        // and saturate within a few successors, so a short group is cheap)
         const int g = std::max(1, std::min(squarings == 0 ? 16 : 4, sweep_budget - since_square));
         CK(cudaMemsetAsync(vslot, 0, sizeof(unsigned long long) * g, s));
         sc.start();
-        for (int k = 0; k < g; ++k)
+        for (int k = 0; k < g; ++k)  // a sweep after one that changed nothing exits on the device
             CK(bits_sweep_csr(ptr, col, uoff, n, rbits, rbits, wp, 1, vslot + k, nullptr, &launches, s,
-                              static_cast<int>(dmax)));
-        sc.stop(g, sweep_min_bytes);
-        sweeps += g;
-        since_square += g;
+                              static_cast<int>(dmax), k > 0 ? vslot + k - 1 : nullptr));
+        sc.stop();
+        if ((rc = emit())) return rc;
         if ((rc = read_scalars(ws, s))) return rc;
+        int ran = g;
         for (int k = 0; k < g; ++k)
-            if (host_scal(ws)[32 + k] == 0) converged = true;
+            if (host_scal(ws)[32 + k] == 0) {
+                converged = true;
+                ran = k + 1;
+                break;
+            }
+        sc.account(ran, sweep_min_bytes);
+        sweeps += ran;
+        since_square += g;
+        emitted = converged;
         if (!converged) {
             c_valid = false;
             do_square = squarings > 0 || since_square >= sweep_budget;
@@ -490,17 +526,15 @@ dl_status tc_auto(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &a
         }
     }
     tm.mark(2);
-    // model E M, checking M = min1(I + E M) on the way
-    CK(cudaMemsetAsync(ws.scal + SC_VIOL, 0, 2 * sizeof(unsigned long long), s));
-    sc.start();
-    CK(bits_sweep_csr(ptr, col, uoff, n, rbits, mbits, wp, 0, ws.scal + SC_VIOL, ws.scal + SC_ONES, &launches, s, static_cast<int>(dmax)));
-    sc.stop(1, sweep_min_bytes);
-    if ((rc = write_bits(s, mbits, wp, a.out_bits, n, a.mem))) return rc;
-    if ((rc = read_scalars(ws, s))) return rc;
+    if (!emitted) {  // converged by a squaring
+        if ((rc = emit())) return rc;
+        if ((rc = read_scalars(ws, s))) return rc;
+    }
     if (host_scal(ws)[SC_VIOL] != 0) {
         set_error("internal: converged closure failed its certificate");
         return DL_EDEVICE;
     }
+    if (!direct && (rc = write_bits(s, mbits, wp, a.out_bits, n, a.mem))) return rc;
     tm.mark(3);
     if ((rc = check_status(ws, s))) return rc;
     if (st) {
