@@ -74,7 +74,7 @@ constexpr int kScalars = 64;  // device scalar slots per workspace
 // scalar slot indices
 enum : int {
     SC_DMAX = 0, SC_NNZ = 1, SC_COUNT0 = 2, SC_VIOL = 3, SC_ONES = 4, SC_GUARD = 5,
-    SC_DMAX2 = 6, SC_NNZ2 = 7, SC_COUNT2 = 8, SC_CQ = 9, SC_CS = 10, SC_STEP0 = 16
+    SC_DMAX2 = 6, SC_NNZ2 = 7, SC_COUNT2 = 8, SC_CQ = 9, SC_CS = 10, SC_OPEN = 11, SC_STEP0 = 16
 };
 
 struct SolveArgs {

@@ -118,6 +118,13 @@ cudaError_t bits_sweep_csr(const int *ptr, const int *col, const int *unit_off, 
                            const unsigned long long *skip_if_zero = nullptr);
 // Whether bits_sweep_csr takes the row-direct kernels (then unit_off is not read).
 bool row_direct(int max_deg, int64_t wp);
+// Rows i < n of the reflexive closure by the Iteration on single rows (one warp per row,
+// semi-naive frontier expansion over the CSR, row bits in shared memory): M_i gets every node
+// reached; a row whose frontier outgrows 256 nodes keeps what it reached (a subset of its
+// closure row) and counts in *open_rows.  Rows of at most 256 words (n <= 16384).
+bool row_iteration_fits(int64_t wp);
+cudaError_t row_iteration(const int *ptr, const int *col, int n, int64_t wp, uint64_t *M,
+                          unsigned long long *open_rows, cudaStream_t s);
 // Bits of I + E (np rows x wp words) from the CSR of E.
 cudaError_t reflexive_bits(const int *ptr, const int *col, int n, int np, int64_t wp, uint64_t *bits,
                            cudaStream_t s);

@@ -465,6 +465,20 @@ dl_status tc_auto(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &a
         return DL_OK;
     };
     bool emitted = false;
+    // sparse graphs (at most two facts per row on average, no heavy rows): the Iteration on
+    // single rows closes every row whose reachable set stays small in one launch; the rows it
+    // leaves open keep what they reached and the sweeps below finish them
+    if (!dense && nnz <= 2 * static_cast<int64_t>(n) && row_iteration_fits(wp) &&
+        row_direct(static_cast<int>(dmax), wp)) {
+        CK(cudaMemsetAsync(ws.scal + SC_OPEN, 0, sizeof(unsigned long long), s));
+        sc.start();
+        CK(row_iteration(ptr, col, n, wp, rbits, ws.scal + SC_OPEN, s));
+        sc.stop();
+        ++launches;
+        if ((rc = emit())) return rc;
+        if ((rc = read_scalars(ws, s))) return rc;
+        if (host_scal(ws)[SC_OPEN] == 0) converged = emitted = true;
+    }
     while (!converged) {
         if (do_square) {
             if (squarings >= max_squarings) {

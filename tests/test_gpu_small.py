@@ -148,6 +148,28 @@ def test_auto_path_long_chain_and_cycle(ctx):
         assert np.array_equal(bits, oracle.tc_model(e))
 
 
+@pytest.mark.parametrize("seed", [11, 12, 13])
+def test_auto_permuted_chains(ctx, seed):
+    """Chains under random labels (some hops go down in index, some up, so an in-place sweep
+    moves a fact one hop or many), joined by a few random edges and then by a cycle, keep
+    rows changing long after others have settled, and the long ones force squarings between
+    sweeps; every model must equal the oracle's."""
+    rng = np.random.default_rng(seed)
+    n = 1800
+    perm = rng.permutation(n)
+    e = np.zeros((n, n), dtype=np.uint8)
+    for a, b in ((0, 600), (600, 1500), (1500, n)):  # three chains of different lengths
+        idx = perm[a:b]
+        e[idx[:-1], idx[1:]] = 1
+    extra = rng.integers(0, n, size=(40, 2))
+    e[extra[:, 0], extra[:, 1]] = 1
+    bits, st = ctx.tc_closure(e, path="auto")
+    assert np.array_equal(bits, oracle.tc_model(e))
+    e[perm[1499], perm[0]] = 1  # close the second chain into the first
+    bits, st = ctx.tc_closure(e, path="auto")
+    assert np.array_equal(bits, oracle.tc_model(e))
+
+
 def test_chain_needs_log_squarings(ctx):
     n = 1000
     e = np.zeros((n, n), dtype=np.uint8)
