@@ -86,7 +86,7 @@ __global__ void batch_map_kernel(const BatchInst *__restrict__ inst, int *pinst)
 
 // Bits of row r of I + E_k into M (one warp per padded row), the row's successor count and
 // the 0/1 check.
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 4)
     batch_pack_kernel(const BatchInst *__restrict__ inst, const int *__restrict__ pinst, int total_prows,
                       int *cnt, int *status) {
     const int lane = threadIdx.x & 31;

@@ -36,7 +36,7 @@ __global__ void csr_count_kernel(const uint8_t *__restrict__ E, int n, int *cnt)
 
 // One pass over E (warp per padded row): bits of I + E into M, successor counts, the 0/1
 // check, ||E||_inf (max row count), nnz and the number of self-loops.
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 4)
     csr_pack_check_kernel(const uint8_t *__restrict__ E, int n, int np, int wp, int *cnt, uint64_t *M,
                           unsigned long long *dmax, unsigned long long *nnz, unsigned long long *diag,
                           int *status) {

@@ -221,14 +221,26 @@ __device__ __forceinline__ void pack_row_bits(const uint8_t *a, int n, int r, in
     int c = 0;
     uint64_t carry = 0;
     auto shifted = [off](uint64_t lo, uint64_t hi) { return off ? (lo >> off) | (hi << (64 - off)) : lo; };
+    // the next segment's chunks are loaded before this one is processed (two in flight)
+    uint4 cur[4];
+    auto load = [&](int sg, uint4 (&x)[4]) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int v0 = 64 * (32 * sg + lane) + 16 * j;
+            x[j] = v0 < lim ? *reinterpret_cast<const uint4 *>(base + v0) : make_uint4(0u, 0u, 0u, 0u);
+        }
+    };
+    load(0, cur);
     for (int sg = 0; sg < nseg; ++sg) {
         const int u = 32 * sg + lane;
+        uint4 nx[4] = {};
+        if (sg + 1 < nseg) load(sg + 1, nx);
         uint64_t vw = 0;
 #pragma unroll
         for (int j = 0; j < 4; ++j) {
             const int v0 = 64 * u + 16 * j;
             if (v0 < lim) {
-                const uint4 x = *reinterpret_cast<const uint4 *>(base + v0);
+                const uint4 x = cur[j];
                 const int lo = max(0, off - v0), hi = min(16, lim - v0);
                 const uint32_t valid = ((1u << hi) - 1u) & ~((1u << lo) - 1u);
                 const uint32_t m = byte_lsbs(x.x) | (byte_lsbs(x.y) << 4) | (byte_lsbs(x.z) << 8) |
@@ -251,6 +263,8 @@ __device__ __forceinline__ void pack_row_bits(const uint8_t *a, int n, int r, in
             if (w < wp) row[w] = shifted(vw, nxt) | (w == idw ? idb : 0ull);
         }
         carry = vw;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) cur[j] = nx[j];
     }
     if (lane == 31) {
         const int w = 32 * (nseg - 1) + 31;

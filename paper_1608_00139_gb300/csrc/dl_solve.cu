@@ -510,7 +510,7 @@ dl_status tc_auto(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &a
         // a group of in-place sweeps and, speculatively, the model (final if the group reached
         // the fixpoint), then one host read for all of it (after a squaring the rows are dense
         // and saturate within a few successors, so a short group is cheap)
-        const int g = std::max(1, std::min(squarings == 0 ? 16 : 4, sweep_budget - since_square));
+        const int g = std::max(1, std::min(squarings == 0 ? 8 : 4, sweep_budget - since_square));
         CK(cudaMemsetAsync(vslot, 0, sizeof(unsigned long long) * g, s));
         sc.start();
         for (int k = 0; k < g; ++k)  // a sweep after one that changed nothing exits on the device
