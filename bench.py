@@ -40,10 +40,10 @@ UNIT = "TFLOP/s-equiv"
 # DRAM bytes per launch from the ncu captures summarised under profiles/; each is only valid
 # for the kernel source it was taken on (sha256 prefixes).
 TRAFFIC = {
-    "gemm": {"sources": {"dl_umma.cu": "bf1ef1b8f47bb7b3", "dl_ptx.cuh": "b4fd45714c88d2fc"},
-             "bytes_per_launch": 476.6e6},   # profiles/umma_gemm_fp8_n8192.md
-    "sweep": {"sources": {"dl_bool.cu": "787acf21ffebdce6", "dl_rows.cuh": None},
-              "bytes_per_launch": 6.8e6},     # profiles/sweep_rows_step_n8192.md (p = 1e-3)
+    "gemm": {"sources": {"dl_umma.cu": "a0ca42a48c46c344", "dl_ptx.cuh": "b4fd45714c88d2fc"},
+             "bytes_per_launch": 444.5e6},   # ncu: DRAM read + write of one N = 8192 squaring
+    "sweep": {"sources": {"dl_bool.cu": "108ab3ac553b3493"},
+              "bytes_per_launch": 8.70e6},    # ncu: one working sweep, p = 1e-3, cold L2
 }
 
 
@@ -266,6 +266,20 @@ def run_reference(args, rank: int, world: int) -> None:
     print(json.dumps(line), flush=True)
 
 
+def run_part(args, device: int) -> None:
+    """One secondary measurement on its own (same functions as the full run)."""
+    import torch
+
+    from paper_1608_00139_gb300 import dl
+    torch.cuda.set_device(device)
+    if args.part == "serving":
+        out = bench_serving(dl, torch, device, args.serve_seconds)
+    else:
+        with dl.Context(device) as ctx:
+            out = bench_sg(ctx, torch) if args.part == "sg" else bench_batch(ctx, torch, reps=max(1, args.steps))
+    print(json.dumps({"part": args.part, args.part: out}), flush=True)
+
+
 def main() -> None:
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -282,10 +296,15 @@ def main() -> None:
                     help="skip the same-generation, batch and serving measurements")
     ap.add_argument("--serve-seconds", type=float, default=10.0,
                     help="length of the serving stream (the full workload is 60 s)")
+    ap.add_argument("--part", default="all", choices=["all", "sg", "batch", "serving"],
+                    help="run one secondary measurement alone and print its JSON (for profiling)")
     args = ap.parse_args()
     rank, world, local = dist_env()
     if args.impl == "reference":
         run_reference(args, rank, world)
+        return
+    if args.part != "all":
+        run_part(args, local)
         return
 
     import torch
