@@ -145,13 +145,23 @@ __device__ __forceinline__ bool or_unit(const int *__restrict__ col, int q0, int
 // only writer).
 constexpr int kRowDirect = 256;
 
+// The most a row can hold: the columns with an incoming edge (colmask), plus bit self if
+// self >= 0; all n columns without a mask.
 template <int WPL>
-__device__ __forceinline__ void full_mask(int n, int64_t wp, int lane, uint64_t (&full)[WPL]) {
+__device__ __forceinline__ void full_mask(int n, int64_t wp, int lane, const uint64_t *colmask, int self,
+                                          uint64_t (&full)[WPL]) {
 #pragma unroll
     for (int q = 0; q < WPL; ++q) {
         const int64_t w = lane + 32 * q;
         const int64_t lo = w * 64;
-        full[q] = (w >= wp || lo >= n) ? 0ull : (n - lo >= 64 ? ~0ull : ((1ull << (n - lo)) - 1ull));
+        if (w >= wp || lo >= n) {
+            full[q] = 0ull;
+        } else if (colmask != nullptr) {
+            full[q] = colmask[w] | ((self >= 0 && w == (self >> 6)) ? 1ull << (self & 63) : 0ull);
+        } else {
+            full[q] = n - lo >= 64 ? ~0ull : ((1ull << (n - lo)) - 1ull);
+        }
+        asm volatile("" : "+l"(full[q]));  // keep the bound in a register (no reloads in the loops)
     }
 }
 
@@ -203,7 +213,8 @@ __device__ __forceinline__ void or_successors(const int *__restrict__ col, int q
 template <int WPL>
 __global__ void __launch_bounds__(256)
     sweep_rows_step_kernel(const int *__restrict__ ptr, const int *__restrict__ col, int n, uint64_t *M, int64_t wp,
-                           unsigned long long *changed_rows, const unsigned long long *skip_if_zero) {
+                           unsigned long long *changed_rows, const unsigned long long *skip_if_zero,
+                           const uint64_t *__restrict__ colmask) {
     const int lane = threadIdx.x & 31;
     const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (i >= n) return;
@@ -212,7 +223,7 @@ __global__ void __launch_bounds__(256)
     if (q0 == q1) return;
     uint64_t *mrow = M + static_cast<int64_t>(i) * wp;
     uint64_t full[WPL], acc[WPL];
-    full_mask<WPL>(n, wp, lane, full);
+    full_mask<WPL>(n, wp, lane, colmask, i, full);
     bool mine = true;
 #pragma unroll
     for (int q = 0; q < WPL; ++q) {
@@ -241,12 +252,13 @@ __global__ void __launch_bounds__(256)
 template <int WPL>
 __global__ void __launch_bounds__(256)
     sweep_rows_emit_kernel(const int *__restrict__ ptr, const int *__restrict__ col, int n, const uint64_t *M,
-                           uint64_t *out, int64_t wp, unsigned long long *violations, unsigned long long *ones) {
+                           uint64_t *out, int64_t wp, unsigned long long *violations, unsigned long long *ones,
+                           const uint64_t *__restrict__ colmask) {
     const int lane = threadIdx.x & 31;
     const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (i >= n) return;
     uint64_t full[WPL], acc[WPL];
-    full_mask<WPL>(n, wp, lane, full);
+    full_mask<WPL>(n, wp, lane, colmask, -1, full);
 #pragma unroll
     for (int q = 0; q < WPL; ++q) acc[q] = 0ull;
     or_successors<WPL>(col, ptr[i], ptr[i + 1], M, wp, lane, false, full, acc);
@@ -274,12 +286,13 @@ __global__ void __launch_bounds__(256)
 template <int WPL>
 cudaError_t launch_rows(const int *ptr, const int *col, int n, const uint64_t *M, uint64_t *out, int64_t wp,
                         int mode, unsigned long long *violations, unsigned long long *ones,
-                        const unsigned long long *skip, cudaStream_t s) {
+                        const unsigned long long *skip, const uint64_t *colmask, cudaStream_t s) {
     if (mode == 1)
         sweep_rows_step_kernel<WPL><<<(n + 7) / 8, 256, 0, s>>>(ptr, col, n, const_cast<uint64_t *>(M), wp,
-                                                                 violations, skip);
+                                                                 violations, skip, colmask);
     else
-        sweep_rows_emit_kernel<WPL><<<(n + 7) / 8, 256, 0, s>>>(ptr, col, n, M, out, wp, violations, ones);
+        sweep_rows_emit_kernel<WPL><<<(n + 7) / 8, 256, 0, s>>>(ptr, col, n, M, out, wp, violations, ones,
+                                                                 colmask);
     return cudaGetLastError();
 }
 
@@ -447,13 +460,13 @@ cudaError_t sweep_units(const int *ptr, int n, int *cnt, int *unit_off, cudaStre
 cudaError_t bits_sweep_csr(const int *ptr, const int *col, const int *unit_off, int n, const uint64_t *M,
                            uint64_t *out, int64_t wp, int mode, unsigned long long *violations,
                            unsigned long long *ones, int *launches, cudaStream_t s, int max_deg,
-                           const unsigned long long *skip_if_zero) {
+                           const unsigned long long *skip_if_zero, const uint64_t *colmask) {
     if (n <= 0) return cudaSuccess;
     if (row_direct(max_deg, wp)) {  // no heavy rows: row-direct kernels
         if (launches) *launches += 1;
-        if (wp <= 64) return launch_rows<2>(ptr, col, n, M, out, wp, mode, violations, ones, skip_if_zero, s);
-        if (wp <= 128) return launch_rows<4>(ptr, col, n, M, out, wp, mode, violations, ones, skip_if_zero, s);
-        return launch_rows<8>(ptr, col, n, M, out, wp, mode, violations, ones, skip_if_zero, s);
+        if (wp <= 64) return launch_rows<2>(ptr, col, n, M, out, wp, mode, violations, ones, skip_if_zero, colmask, s);
+        if (wp <= 128) return launch_rows<4>(ptr, col, n, M, out, wp, mode, violations, ones, skip_if_zero, colmask, s);
+        return launch_rows<8>(ptr, col, n, M, out, wp, mode, violations, ones, skip_if_zero, colmask, s);
     }
     const unsigned grid = static_cast<unsigned>(num_sms() * 8);
     if (mode == 1) {

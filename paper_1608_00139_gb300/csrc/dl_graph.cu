@@ -39,28 +39,33 @@ __global__ void csr_count_kernel(const uint8_t *__restrict__ E, int n, int *cnt)
 __global__ void __launch_bounds__(256, 4)
     csr_pack_check_kernel(const uint8_t *__restrict__ E, int n, int np, int wp, int *cnt, uint64_t *M,
                           unsigned long long *dmax, unsigned long long *nnz, unsigned long long *diag,
-                          int *status) {
+                          int *status, uint64_t *colmask) {
+    extern __shared__ uint64_t colmask_s[];  // the CTA's rows' facts, merged into colmask at the end
+    for (int w = threadIdx.x; w < wp; w += blockDim.x) colmask_s[w] = 0ull;
+    __syncthreads();
     const int lane = threadIdx.x & 31;
     const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (r >= np) return;
     uint64_t *row = M + static_cast<int64_t>(r) * wp;
-    if (r >= n) {  // padding: identity only
+    if (r >= n && r < np) {  // padding: identity only
         for (int w = lane; w < wp; w += 32) row[w] = w == (r >> 6) ? 1ull << (r & 63) : 0ull;
-        return;
-    }
-    const uint8_t *a = E + static_cast<int64_t>(r) * n;
-    int c = 0;
-    bool bad = false;
-    pack_row_bits(a, n, r, wp, row, lane, c, bad);
-    if (lane == 0) {
-        cnt[r] = c;
-        if (bad) atomicOr(status, ST_BAD_INPUT);
-        if (c) {
-            atomicMax(dmax, static_cast<unsigned long long>(c));
-            atomicAdd(nnz, static_cast<unsigned long long>(c));
+    } else if (r < n) {
+        const uint8_t *a = E + static_cast<int64_t>(r) * n;
+        int c = 0;
+        bool bad = false;
+        pack_row_bits(a, n, r, wp, row, lane, c, bad, colmask_s);
+        if (lane == 0) {
+            cnt[r] = c;
+            if (bad) atomicOr(status, ST_BAD_INPUT);
+            if (c) {
+                atomicMax(dmax, static_cast<unsigned long long>(c));
+                atomicAdd(nnz, static_cast<unsigned long long>(c));
+            }
+            if (a[r] & 1) atomicAdd(diag, 1ull);
         }
-        if (a[r] & 1) atomicAdd(diag, 1ull);
     }
+    __syncthreads();
+    for (int w = threadIdx.x; w < wp; w += blockDim.x)
+        if (colmask_s[w] != 0ull) atomicOr(reinterpret_cast<unsigned long long *>(colmask + w), colmask_s[w]);
 }
 
 __global__ void __launch_bounds__(256)
@@ -181,9 +186,11 @@ cudaError_t csr_build(const uint8_t *E, int n, int *cnt, int *ptr, cudaStream_t 
 
 cudaError_t csr_pack_checked(const uint8_t *E, int n, int np, int64_t wp, int *cnt, int *ptr, uint64_t *M,
                              unsigned long long *dmax, unsigned long long *nnz, unsigned long long *diag, int *status,
-                             cudaStream_t s) {
-    csr_pack_check_kernel<<<static_cast<unsigned>((np + 7) / 8), 256, 0, s>>>(E, n, np, static_cast<int>(wp), cnt,
-                                                                              M, dmax, nnz, diag, status);
+                             uint64_t *colmask, cudaStream_t s) {
+    if (wp > 6144) return cudaErrorInvalidValue;  // the CTA's column mask lives in shared memory
+    const size_t smem = static_cast<size_t>(wp) * sizeof(uint64_t);
+    csr_pack_check_kernel<<<static_cast<unsigned>((np + 7) / 8), 256, smem, s>>>(
+        E, n, np, static_cast<int>(wp), cnt, M, dmax, nnz, diag, status, colmask);
     exclusive_scan_kernel<<<1, 1024, 0, s>>>(cnt, n, ptr);
     return cudaGetLastError();
 }

@@ -112,10 +112,13 @@ cudaError_t sweep_units(const int *ptr, int n, int *cnt, int *unit_off, cudaStre
 // max_deg: ||E||_inf if known (rows of at most 256 successors take row-direct kernels, which
 // need no unit_off), or -1.  skip_if_zero (mode 1): the previous sweep's counter; when it is
 // zero on the device the sweep does nothing (that sweep already proved convergence).
+// colmask (optional): the columns with an incoming edge.  Every row of E M lies inside it and
+// every row of the reflexive closure inside it plus the row's own bit, so a row-direct sweep
+// stops reading successors once a row covers that much (without it: all n columns).
 cudaError_t bits_sweep_csr(const int *ptr, const int *col, const int *unit_off, int n, const uint64_t *M,
                            uint64_t *out, int64_t wp, int mode, unsigned long long *violations,
                            unsigned long long *ones, int *launches, cudaStream_t s, int max_deg,
-                           const unsigned long long *skip_if_zero = nullptr);
+                           const unsigned long long *skip_if_zero = nullptr, const uint64_t *colmask = nullptr);
 // Whether bits_sweep_csr takes the row-direct kernels (then unit_off is not read).
 bool row_direct(int max_deg, int64_t wp);
 // Rows i < n of the reflexive closure by the Iteration on single rows (one warp per row,
@@ -141,10 +144,11 @@ cudaError_t csr_fill(const uint8_t *E, int n, const int *ptr, int *col, cudaStre
 // One pass over E: the bits of I + E into M (np rows of wp words; rows >= n hold only their
 // diagonal bit), the CSR row pointers, and the ingest's checks: status |= ST_BAD_INPUT on a
 // byte other than 0/1, *dmax = ||E||_inf, *nnz += facts, *diag += self-loops (counters zeroed
-// by the caller).  E's rows may have any alignment.
+// by the caller), and colmask |= the columns with an incoming edge (wp words, zeroed by the
+// caller; wp <= 6144).  E's rows may have any alignment.
 cudaError_t csr_pack_checked(const uint8_t *E, int n, int np, int64_t wp, int *cnt, int *ptr, uint64_t *M,
                              unsigned long long *dmax, unsigned long long *nnz, unsigned long long *diag, int *status,
-                             cudaStream_t s);
+                             uint64_t *colmask, cudaStream_t s);
 // Column indices of E from the packed bits of I + E (as written by csr_pack_checked).
 cudaError_t csr_fill_from_bits(const uint64_t *M, int n, int64_t wp, const int *ptr, int *col, cudaStream_t s);
 // out[0..n] = exclusive prefix sums of cnt[0..n-1] (out[n] = total); one CTA.

@@ -209,8 +209,9 @@ __device__ __forceinline__ uint32_t byte_bad(uint32_t x) {
 // below a, and each model word is two of those 64-bit groups shifted by the misalignment.
 // Bytes outside the row are masked off (they are never counted or checked).  Every lane
 // returns the row's count of ones (without the identity) and whether a byte was not 0/1.
+// With colmask (shared memory, wp words) the row's facts are also ORed into it.
 __device__ __forceinline__ void pack_row_bits(const uint8_t *a, int n, int r, int wp, uint64_t *row, int lane,
-                                              int &count, bool &bad_byte) {
+                                              int &count, bool &bad_byte, uint64_t *colmask = nullptr) {
     const int idw = r >> 6;
     const uint64_t idb = 1ull << (r & 63);
     const int off = static_cast<int>(reinterpret_cast<uintptr_t>(a) & 15);
@@ -254,13 +255,17 @@ __device__ __forceinline__ void pack_row_bits(const uint8_t *a, int n, int r, in
         c += __popcll(vw);
         const uint64_t nxt = __shfl_down_sync(0xffffffffu, vw, 1);
         const uint64_t first = __shfl_sync(0xffffffffu, vw, 0);
+        auto put = [&](int w, uint64_t e) {  // e: the facts of word w
+            row[w] = e | (w == idw ? idb : 0ull);
+            if (colmask != nullptr && e != 0ull) atomicOr(reinterpret_cast<unsigned long long *>(colmask + w), e);
+        };
         if (sg > 0 && lane == 31) {
             const int w = 32 * (sg - 1) + 31;
-            if (w < wp) row[w] = shifted(carry, first) | (w == idw ? idb : 0ull);
+            if (w < wp) put(w, shifted(carry, first));
         }
         if (lane < 31) {
             const int w = 32 * sg + lane;
-            if (w < wp) row[w] = shifted(vw, nxt) | (w == idw ? idb : 0ull);
+            if (w < wp) put(w, shifted(vw, nxt));
         }
         carry = vw;
 #pragma unroll
@@ -268,7 +273,11 @@ __device__ __forceinline__ void pack_row_bits(const uint8_t *a, int n, int r, in
     }
     if (lane == 31) {
         const int w = 32 * (nseg - 1) + 31;
-        if (w < wp) row[w] = shifted(carry, 0ull) | (w == idw ? idb : 0ull);
+        if (w < wp) {
+            const uint64_t e = shifted(carry, 0ull);
+            row[w] = e | (w == idw ? idb : 0ull);
+            if (colmask != nullptr && e != 0ull) atomicOr(reinterpret_cast<unsigned long long *>(colmask + w), e);
+        }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {

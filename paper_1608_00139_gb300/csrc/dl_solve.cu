@@ -387,13 +387,15 @@ dl_status tc_auto(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &a
     auto *cnt = static_cast<int *>(ws.get("g_cnt", (np + 1) * 4));
     auto *ptr = static_cast<int *>(ws.get("g_ptr", (np + 1) * 4));
     auto *uoff = static_cast<int *>(ws.get("g_units", (np + 1) * 4));
-    NEED(C[0] && C[1] && rbits && mbits && cnt && ptr && uoff);
+    auto *colmask = static_cast<uint64_t *>(ws.get("g_colmask", wp * 8));
+    NEED(C[0] && C[1] && rbits && mbits && cnt && ptr && uoff && colmask);
     CK(cudaMemsetAsync(ws.scal, 0, kScalars * sizeof(unsigned long long), s));
     CK(cudaMemsetAsync(ws.status, 0, sizeof(int), s));
+    CK(cudaMemsetAsync(colmask, 0, wp * 8, s));
     // one pass over E: the bits of C_0 = I + E, 0/1 check, row counts, ||E||_inf, nnz,
     // self-loops (the e4m3 operand is only built if a squaring happens)
     CK(csr_pack_checked(E, n, static_cast<int>(np), wp, cnt, ptr, rbits, ws.scal + SC_DMAX, ws.scal + SC_NNZ,
-                        ws.scal + SC_COUNT0, ws.status, s));
+                        ws.scal + SC_COUNT0, ws.status, colmask, s));
     launches += 2;
     if ((rc = read_scalars(ws, s))) return rc;
     if ((rc = check_status(ws, s))) return rc;
@@ -460,7 +462,7 @@ dl_status tc_auto(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &a
         CK(cudaMemsetAsync(ws.scal + SC_VIOL, 0, 2 * sizeof(unsigned long long), s));
         sc.start();
         CK(bits_sweep_csr(ptr, col, uoff, n, rbits, model, wp, 0, ws.scal + SC_VIOL, ws.scal + SC_ONES, &launches, s,
-                          static_cast<int>(dmax)));
+                          static_cast<int>(dmax), nullptr, colmask));
         sc.stop(1, sweep_min_bytes);
         return DL_OK;
     };
@@ -515,7 +517,7 @@ dl_status tc_auto(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &a
         sc.start();
         for (int k = 0; k < g; ++k)  // a sweep after one that changed nothing exits on the device
             CK(bits_sweep_csr(ptr, col, uoff, n, rbits, rbits, wp, 1, vslot + k, nullptr, &launches, s,
-                              static_cast<int>(dmax), k > 0 ? vslot + k - 1 : nullptr));
+                              static_cast<int>(dmax), k > 0 ? vslot + k - 1 : nullptr, colmask));
         sc.stop();
         if ((rc = emit())) return rc;
         if ((rc = read_scalars(ws, s))) return rc;
