@@ -448,6 +448,126 @@ __global__ void __launch_bounds__(256)
     if (!ok && lane == 0) atomicAdd(open_rows, 1ull);
 }
 
+// ---- same generation on bits --------------------------------------------------------------
+// 64 x 64 bit-block transpose, one warp per block (lane l holds rows l and l + 32 of the
+// block; bit c of a word is column c): the off-diagonal j x j sub-blocks of every 2j x 2j
+// block are exchanged for j = 32, 16, ..., 1 (the first step inside a lane, the others between
+// lanes l and l ^ j).
+__global__ void __launch_bounds__(256)
+    bits_transpose_kernel(const uint64_t *__restrict__ src, uint64_t *__restrict__ dst, int nb, int64_t wp,
+                          const unsigned long long *skip_if_zero) {
+    if (skip_if_zero != nullptr && *skip_if_zero == 0) return;
+    const int lane = threadIdx.x & 31;
+    const int64_t b = static_cast<int64_t>(blockIdx.x) * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (b >= static_cast<int64_t>(nb) * nb) return;
+    const int64_t R = b / nb, C = b % nb;
+    uint64_t x0 = src[(64 * R + lane) * wp + C], x1 = src[(64 * R + 32 + lane) * wp + C];
+    {
+        const uint64_t t = ((x0 >> 32) ^ x1) & 0x00000000FFFFFFFFull;
+        x1 ^= t;
+        x0 ^= t << 32;
+    }
+    const uint64_t masks[5] = {0x0000FFFF0000FFFFull, 0x00FF00FF00FF00FFull, 0x0F0F0F0F0F0F0F0Full,
+                               0x3333333333333333ull, 0x5555555555555555ull};
+#pragma unroll
+    for (int s = 0; s < 5; ++s) {
+        const int j = 16 >> s;
+        const uint64_t m = masks[s];
+        const uint64_t y0 = __shfl_xor_sync(0xffffffffu, x0, j), y1 = __shfl_xor_sync(0xffffffffu, x1, j);
+        if ((lane & j) == 0) {  // upper row of the pair: takes the partner's low part
+            x0 ^= (((x0 >> j) ^ y0) & m) << j;
+            x1 ^= (((x1 >> j) ^ y1) & m) << j;
+        } else {
+            x0 ^= ((y0 >> j) ^ x0) & m;
+            x1 ^= ((y1 >> j) ^ x1) & m;
+        }
+    }
+    dst[(64 * C + lane) * wp + R] = x0;
+    dst[(64 * C + 32 + lane) * wp + R] = x1;
+}
+
+// dst_i = [dst_i if accumulate] | OR_{k in succ(i)} src_k, one warp per row i < n (lanes own
+// WPL words, successor rows loaded in pairs, stop once the row holds every column).  With
+// accumulate, *changed counts the rows whose words changed; without, every word is written.
+template <int WPL>
+__global__ void __launch_bounds__(256)
+    gather_rows_kernel(const int *__restrict__ ptr, const int *__restrict__ col, int n, const uint64_t *src,
+                       uint64_t *dst, int64_t wp, int accumulate, unsigned long long *changed,
+                       const unsigned long long *skip_if_zero) {
+    const int lane = threadIdx.x & 31;
+    const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (i >= n) return;
+    if (skip_if_zero != nullptr && *skip_if_zero == 0) return;
+    uint64_t *drow = dst + static_cast<int64_t>(i) * wp;
+    uint64_t acc[WPL], full[WPL];
+    full_mask<WPL>(n, wp, lane, nullptr, -1, full);
+#pragma unroll
+    for (int q = 0; q < WPL; ++q) {
+        const int64_t w = lane + 32 * q;
+        acc[q] = (accumulate && w < wp) ? drow[w] : 0ull;
+    }
+    or_successors<WPL>(col, ptr[i], ptr[i + 1], src, wp, lane, false, full, acc);
+    bool ch = false;
+#pragma unroll
+    for (int q = 0; q < WPL; ++q) {
+        const int64_t w = lane + 32 * q;
+        if (w >= wp) continue;
+        if (!accumulate) {
+            drow[w] = acc[q];
+        } else if (acc[q] != drow[w]) {  // only this warp writes row i
+            drow[w] = acc[q];
+            ch = true;
+        }
+    }
+    if (accumulate && __any_sync(0xffffffffu, ch) && lane == 0) atomicAdd(changed, 1ull);
+}
+
+// The same gather split into work units of at most kUnit successors (rows with hundreds of
+// successors would serialise a warp), combined with atomicOr; dst rows < n must start zero
+// unless accumulate.  With accumulate, *changed counts units that changed a word.
+__global__ void __launch_bounds__(256)
+    gather_units_kernel(const int *__restrict__ ptr, const int *__restrict__ col, const int *__restrict__ unit_off,
+                        int n, const uint64_t *src, uint64_t *dst, int64_t wp, int accumulate,
+                        unsigned long long *changed, const unsigned long long *skip_if_zero) {
+    if (skip_if_zero != nullptr && *skip_if_zero == 0) return;
+    const int lane = threadIdx.x & 31;
+    const int total = unit_off[n];
+    const int warps = gridDim.x * (blockDim.x >> 5);
+    for (int u = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); u < total; u += warps) {
+        const int i = unit_row(unit_off, n, u);
+        const int q0 = ptr[i] + (u - unit_off[i]) * kUnit;
+        const int q1 = min(q0 + kUnit, ptr[i + 1]);
+        if (or_unit(col, q0, q1, n, i, src, dst, wp, false, true, lane) && accumulate && lane == 0)
+            atomicAdd(changed, 1ull);
+    }
+}
+
+// Ones in rows < n of a bit matrix.
+__global__ void bits_count_kernel(const uint64_t *__restrict__ M, int n, int64_t wp, unsigned long long *ones) {
+    const int64_t t = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    uint32_t c = t < static_cast<int64_t>(n) * wp ? __popcll(M[t]) : 0u;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+    if ((threadIdx.x & 31) == 0 && c) atomicAdd(ones, static_cast<unsigned long long>(c));
+}
+
+// Rows < n get the identity, every other word is zero (np rows).
+__global__ void bits_identity_kernel(uint64_t *M, int n, int np, int64_t wp) {
+    const int64_t t = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    if (t >= static_cast<int64_t>(np) * wp) return;
+    const int64_t r = t / wp, w = t % wp;
+    M[t] = (r < n && w == (r >> 6)) ? 1ull << (r & 63) : 0ull;
+}
+
+// Words where A and B differ (counted).
+__global__ void bits_diff_kernel(const uint64_t *__restrict__ A, const uint64_t *__restrict__ B, int64_t words,
+                                 unsigned long long *diff) {
+    const int64_t t = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
+    const bool d = t < words && A[t] != B[t];
+    const unsigned bal = __ballot_sync(0xffffffffu, d);
+    if ((threadIdx.x & 31) == 0 && bal) atomicAdd(diff, static_cast<unsigned long long>(__popc(bal)));
+}
+
 }  // namespace
 
 bool row_direct(int max_deg, int64_t wp) { return max_deg >= 0 && max_deg <= kRowDirect && wp <= 256; }
@@ -522,6 +642,55 @@ cudaError_t row_iteration(const int *ptr, const int *col, int n, int64_t wp, uin
     if (!row_iteration_fits(wp)) return cudaErrorInvalidValue;
     const size_t smem = 8 * (static_cast<size_t>(wp) + kFront + 1) * sizeof(uint64_t);
     row_iteration_kernel<<<(n + 7) / 8, 256, smem, s>>>(ptr, col, n, static_cast<int>(wp), M, open_rows);
+    return cudaGetLastError();
+}
+
+cudaError_t bits_transpose(const uint64_t *src, uint64_t *dst, int np, int64_t wp, const unsigned long long *skip,
+                           cudaStream_t s) {
+    if (np % 64 != 0 || wp * 64 != np) return cudaErrorInvalidValue;
+    const int nb = np / 64;
+    const int64_t blocks = (static_cast<int64_t>(nb) * nb + 7) / 8;
+    bits_transpose_kernel<<<static_cast<unsigned>(blocks), 256, 0, s>>>(src, dst, nb, wp, skip);
+    return cudaGetLastError();
+}
+
+cudaError_t bits_gather(const int *ptr, const int *col, const int *unit_off, int n, const uint64_t *src, uint64_t *dst,
+                        int64_t wp, int accumulate, unsigned long long *changed, const unsigned long long *skip,
+                        cudaStream_t s) {
+    if (n <= 0) return cudaSuccess;
+    if (unit_off != nullptr) {
+        if (!accumulate) {
+            const cudaError_t e = cudaMemsetAsync(dst, 0, static_cast<size_t>(n) * wp * 8, s);
+            if (e != cudaSuccess) return e;
+        }
+        gather_units_kernel<<<static_cast<unsigned>(num_sms() * 8), 256, 0, s>>>(ptr, col, unit_off, n, src, dst, wp,
+                                                                                accumulate, changed, skip);
+        return cudaGetLastError();
+    }
+    const unsigned grid = static_cast<unsigned>((n + 7) / 8);
+    if (wp <= 64) gather_rows_kernel<2><<<grid, 256, 0, s>>>(ptr, col, n, src, dst, wp, accumulate, changed, skip);
+    else if (wp <= 128) gather_rows_kernel<4><<<grid, 256, 0, s>>>(ptr, col, n, src, dst, wp, accumulate, changed, skip);
+    else if (wp <= 256) gather_rows_kernel<8><<<grid, 256, 0, s>>>(ptr, col, n, src, dst, wp, accumulate, changed, skip);
+    else return cudaErrorInvalidValue;
+    return cudaGetLastError();
+}
+
+cudaError_t bits_count(const uint64_t *M, int n, int64_t wp, unsigned long long *ones, cudaStream_t s) {
+    const int64_t words = static_cast<int64_t>(n) * wp;
+    if (words <= 0) return cudaSuccess;
+    bits_count_kernel<<<static_cast<unsigned>((words + 255) / 256), 256, 0, s>>>(M, n, wp, ones);
+    return cudaGetLastError();
+}
+
+cudaError_t bits_identity(uint64_t *M, int n, int np, int64_t wp, cudaStream_t s) {
+    const int64_t words = static_cast<int64_t>(np) * wp;
+    bits_identity_kernel<<<static_cast<unsigned>((words + 255) / 256), 256, 0, s>>>(M, n, np, wp);
+    return cudaGetLastError();
+}
+
+cudaError_t bits_diff(const uint64_t *A, const uint64_t *B, int64_t words, unsigned long long *diff, cudaStream_t s) {
+    if (words <= 0) return cudaSuccess;
+    bits_diff_kernel<<<static_cast<unsigned>((words + 255) / 256), 256, 0, s>>>(A, B, words, diff);
     return cudaGetLastError();
 }
 

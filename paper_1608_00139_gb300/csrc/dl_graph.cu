@@ -76,6 +76,23 @@ __global__ void __launch_bounds__(256)
     fill_row_from_bits(M + static_cast<int64_t>(r) * wp, wp, r, ptr[r], ptr[r + 1], col, lane);
 }
 
+// Bits of E alone (no identity; rows >= n zero), the 0/1 check; warp per padded row.
+__global__ void __launch_bounds__(256, 4)
+    pack_bits_kernel(const uint8_t *__restrict__ E, int n, int np, int wp, uint64_t *M, int *status) {
+    const int lane = threadIdx.x & 31;
+    const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (r >= np) return;
+    uint64_t *row = M + static_cast<int64_t>(r) * wp;
+    if (r >= n) {
+        for (int w = lane; w < wp; w += 32) row[w] = 0ull;
+        return;
+    }
+    int c = 0;
+    bool bad = false;
+    pack_row_bits(E + static_cast<int64_t>(r) * n, n, r, wp, row, lane, c, bad, nullptr, false);
+    if (lane == 0 && bad) atomicOr(status, ST_BAD_INPUT);
+}
+
 // Exclusive scan in one CTA: each thread holds 16 consecutive counts in registers, a warp
 // scan and a scan of the warp totals place them; long inputs go round in tiles of 16384.
 __global__ void __launch_bounds__(1024) exclusive_scan_kernel(const int *cnt, int n, int *ptr) {
@@ -192,6 +209,11 @@ cudaError_t csr_pack_checked(const uint8_t *E, int n, int np, int64_t wp, int *c
     csr_pack_check_kernel<<<static_cast<unsigned>((np + 7) / 8), 256, smem, s>>>(
         E, n, np, static_cast<int>(wp), cnt, M, dmax, nnz, diag, status, colmask);
     exclusive_scan_kernel<<<1, 1024, 0, s>>>(cnt, n, ptr);
+    return cudaGetLastError();
+}
+
+cudaError_t pack_bits(const uint8_t *E, int n, int np, int64_t wp, uint64_t *M, int *status, cudaStream_t s) {
+    pack_bits_kernel<<<static_cast<unsigned>((np + 7) / 8), 256, 0, s>>>(E, n, np, static_cast<int>(wp), M, status);
     return cudaGetLastError();
 }
 

@@ -128,6 +128,23 @@ bool row_direct(int max_deg, int64_t wp);
 bool row_iteration_fits(int64_t wp);
 cudaError_t row_iteration(const int *ptr, const int *col, int n, int64_t wp, uint64_t *M,
                           unsigned long long *open_rows, cudaStream_t s);
+// Bit-matrix helpers for same generation (np x np bits, wp = np / 64 words per row).
+// dst = src^T (np a multiple of 64; dst distinct from src); nothing if *skip == 0.
+cudaError_t bits_transpose(const uint64_t *src, uint64_t *dst, int np, int64_t wp, const unsigned long long *skip,
+                           cudaStream_t s);
+// Rows i < n: dst_i = [dst_i if accumulate] | OR_{k in succ(i)} src_k over the CSR (ptr, col);
+// with accumulate *changed is non-zero iff a row changed; nothing if *skip == 0.  With unit_off
+// (from sweep_units) rows are split into work units combined with atomicOr (heavy rows);
+// without, one warp per row (wp <= 256).
+cudaError_t bits_gather(const int *ptr, const int *col, const int *unit_off, int n, const uint64_t *src, uint64_t *dst,
+                        int64_t wp, int accumulate, unsigned long long *changed, const unsigned long long *skip,
+                        cudaStream_t s);
+// *ones += ones in rows < n.
+cudaError_t bits_count(const uint64_t *M, int n, int64_t wp, unsigned long long *ones, cudaStream_t s);
+// M = identity on rows < n, zero elsewhere (np rows).
+cudaError_t bits_identity(uint64_t *M, int n, int np, int64_t wp, cudaStream_t s);
+// *diff += words where A and B differ.
+cudaError_t bits_diff(const uint64_t *A, const uint64_t *B, int64_t words, unsigned long long *diff, cudaStream_t s);
 // Bits of I + E (np rows x wp words) from the CSR of E.
 cudaError_t reflexive_bits(const int *ptr, const int *col, int n, int np, int64_t wp, uint64_t *bits,
                            cudaStream_t s);
@@ -149,6 +166,9 @@ cudaError_t csr_fill(const uint8_t *E, int n, const int *ptr, int *col, cudaStre
 cudaError_t csr_pack_checked(const uint8_t *E, int n, int np, int64_t wp, int *cnt, int *ptr, uint64_t *M,
                              unsigned long long *dmax, unsigned long long *nnz, unsigned long long *diag, int *status,
                              uint64_t *colmask, cudaStream_t s);
+// Bits of E alone (np rows of wp words, rows >= n zero), status |= ST_BAD_INPUT on a byte other
+// than 0/1.
+cudaError_t pack_bits(const uint8_t *E, int n, int np, int64_t wp, uint64_t *M, int *status, cudaStream_t s);
 // Column indices of E from the packed bits of I + E (as written by csr_pack_checked).
 cudaError_t csr_fill_from_bits(const uint64_t *M, int n, int64_t wp, const int *ptr, int *col, cudaStream_t s);
 // out[0..n] = exclusive prefix sums of cnt[0..n-1] (out[n] = total); one CTA.

@@ -209,10 +209,12 @@ __device__ __forceinline__ uint32_t byte_bad(uint32_t x) {
 // below a, and each model word is two of those 64-bit groups shifted by the misalignment.
 // Bytes outside the row are masked off (they are never counted or checked).  Every lane
 // returns the row's count of ones (without the identity) and whether a byte was not 0/1.
-// With colmask (shared memory, wp words) the row's facts are also ORed into it.
+// With colmask (shared memory, wp words) the row's facts are also ORed into it; without
+// identity the bit r is not added.
 __device__ __forceinline__ void pack_row_bits(const uint8_t *a, int n, int r, int wp, uint64_t *row, int lane,
-                                              int &count, bool &bad_byte, uint64_t *colmask = nullptr) {
-    const int idw = r >> 6;
+                                              int &count, bool &bad_byte, uint64_t *colmask = nullptr,
+                                              bool identity = true) {
+    const int idw = identity ? r >> 6 : -1;
     const uint64_t idb = 1ull << (r & 63);
     const int off = static_cast<int>(reinterpret_cast<uintptr_t>(a) & 15);
     const uint8_t *base = a - off;

@@ -750,15 +750,149 @@ dl_status solve_tc(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &
     return rc;
 }
 
+// Same generation by the Iteration method on bits: S_{t+1} = B | P S_t P^T, from S_0 = B
+// (Kleene iteration from below, so an iteration that changes nothing has reached the least
+// fixpoint).  One iteration: Y = P S_t^T (rows of P gather rows of S^T), X = Y^T = S_t P^T,
+// S |= P X (rows of P gather rows of X); when B is symmetric so is every S_t and S^T = S.
+// Returns with *done = false (and nothing written) if the rows are too wide or the
+// iterations exceed the budget: the doubling below then solves the problem.
+dl_status sg_iteration(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &a, dl_stats *st, bool *done) {
+    (void)ctx;
+    *done = false;
+    const int32_t n = a.n;
+    const int64_t np = round_up(std::max<int64_t>(n, 1), 256);
+    const int64_t wp = np / 64;
+    if (wp > 256) return DL_OK;
+    constexpr int kBudget = 64, kGroup = 8;
+    Timer tm{ws.ev, s};
+    int launches = 0;
+    tm.mark(0);
+    const uint8_t *P = nullptr, *Bm = nullptr;
+    dl_status rc = stage_input(ws, s, a.E, n, a.mem, "in0", &P);
+    if (rc) return rc;
+    if (a.E2 && (rc = stage_input(ws, s, a.E2, n, a.mem, "in1", &Bm))) return rc;
+    auto *S = static_cast<uint64_t *>(ws.get("bits0", np * wp * 8));
+    auto *Y = static_cast<uint64_t *>(ws.get("bits1", np * wp * 8));
+    auto *X = static_cast<uint64_t *>(ws.get("bits2", np * wp * 8));
+    auto *cnt = static_cast<int *>(ws.get("g_cnt", (np + 1) * 4));
+    auto *ptr = static_cast<int *>(ws.get("g_ptr", (np + 1) * 4));
+    auto *colmask = static_cast<uint64_t *>(ws.get("g_colmask", wp * 8));
+    auto *uoff = static_cast<int *>(ws.get("g_units", (np + 1) * 4));
+    NEED(S && Y && X && cnt && ptr && colmask && uoff);
+    CK(cudaMemsetAsync(ws.scal, 0, kScalars * sizeof(unsigned long long), s));
+    CK(cudaMemsetAsync(ws.status, 0, sizeof(int), s));
+    CK(cudaMemsetAsync(colmask, 0, wp * 8, s));
+    // the CSR of P (its bits of I + P go to X, a scratch here) and S_0 = B
+    CK(csr_pack_checked(P, n, static_cast<int>(np), wp, cnt, ptr, X, ws.scal + SC_DMAX, ws.scal + SC_NNZ,
+                        ws.scal + SC_COUNT0, ws.status, colmask, s));
+    launches += 2;
+    if (Bm) {  // is B symmetric?  (words of B and B^T that differ)
+        CK(pack_bits(Bm, n, static_cast<int>(np), wp, S, ws.status, s));
+        CK(bits_transpose(S, Y, static_cast<int>(np), wp, nullptr, s));
+        CK(bits_diff(S, Y, np * wp, ws.scal + SC_CQ, s));
+        launches += 3;
+    } else {
+        CK(bits_identity(S, n, static_cast<int>(np), wp, s));
+        ++launches;
+    }
+    if ((rc = read_scalars(ws, s))) return rc;
+    if ((rc = check_status(ws, s))) return rc;
+    const double dmax = static_cast<double>(host_scal(ws)[SC_DMAX]);
+    double eps = 0;
+    if ((rc = choose_eps(a.eps, 1.0 / (1.0 + dmax * dmax), "Sec. 6.2 (1/(1+||P||^2))", &eps))) return rc;
+    const bool sym = Bm == nullptr || host_scal(ws)[SC_CQ] == 0;
+    const int64_t nnz = static_cast<int64_t>(host_scal(ws)[SC_NNZ]);
+    auto *col = static_cast<int *>(ws.get("g_col", static_cast<size_t>(std::max<int64_t>(nnz, 1)) * 4));
+    NEED(col);
+    CK(csr_fill_from_bits(X, n, wp, ptr, col, s));
+    ++launches;
+    const int *units = nullptr;  // rows of more than 64 parents: edge-parallel gathers
+    if (dmax > 64) {
+        CK(sweep_units(ptr, n, cnt, uoff, s));
+        launches += 2;
+        units = uoff;
+    }
+    CK(cudaMemsetAsync(Y, 0, np * wp * 8, s));  // rows >= n stay zero (the gathers write rows < n)
+    tm.mark(1);
+    unsigned long long *vslot = ws.scal + 32;
+    int iters = 0;
+    bool converged = false;
+    while (!converged) {
+        if (iters >= kBudget) return DL_OK;  // deep derivations: doubling instead
+        CK(cudaMemsetAsync(vslot, 0, sizeof(unsigned long long) * kGroup, s));
+        for (int k = 0; k < kGroup; ++k) {  // an iteration after one that changed nothing exits at once
+            const unsigned long long *skip = k > 0 ? vslot + k - 1 : nullptr;
+            const uint64_t *src = S;
+            if (!sym) {
+                CK(bits_transpose(S, X, static_cast<int>(np), wp, skip, s));
+                src = X;
+                ++launches;
+            }
+            CK(bits_gather(ptr, col, units, n, src, Y, wp, 0, nullptr, skip, s));
+            CK(bits_transpose(Y, X, static_cast<int>(np), wp, skip, s));
+            CK(bits_gather(ptr, col, units, n, X, S, wp, 1, vslot + k, skip, s));
+            launches += 3;
+        }
+        if ((rc = read_scalars(ws, s))) return rc;
+        int ran = kGroup;
+        for (int k = 0; k < kGroup; ++k)
+            if (host_scal(ws)[32 + k] == 0) {
+                converged = true;
+                ran = k + 1;
+                break;
+            }
+        iters += ran;
+    }
+    tm.mark(2);
+    CK(bits_count(S, n, wp, ws.scal + SC_ONES, s));
+    ++launches;
+    if ((rc = write_bits(s, S, wp, a.out_bits, n, a.mem))) return rc;
+    tm.mark(3);
+    if ((rc = read_scalars(ws, s))) return rc;
+    if ((rc = check_status(ws, s))) return rc;
+    if (st) {
+        st->path_used = DL_PATH_AUTO;
+        st->eps_used = eps;
+        st->iters = iters;
+        st->recheck_sweeps = iters;
+        st->model_ones = static_cast<int64_t>(host_scal(ws)[SC_ONES]);
+        st->ms_factor = tm.ms(0, 1);
+        st->ms_solve = tm.ms(1, 2);
+        st->ms_epilogue = tm.ms(2, 3);
+        st->ms_total = tm.ms(0, 3);
+        st->gpu_launches = launches;
+    }
+    *done = true;
+    return DL_OK;
+}
+
+dl_status sg_doubling(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &a, dl_stats *st);
+
 dl_status solve_sg(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &a, dl_stats *st) {
     if (a.thr != 0.0) {
         set_error("thr must be 0: the model is S~ > 0 (Theorem 2)");
         return DL_EINVAL;
     }
     if (a.path != DL_PATH_AUTO && a.path != DL_PATH_BOOL_FP8) {
-        set_error("same generation runs on DL_PATH_BOOL_FP8 only");
+        set_error("same generation runs on DL_PATH_AUTO or DL_PATH_BOOL_FP8");
         return DL_ENOTIMPL;
     }
+    // AUTO: the doubling costs about 30 Np^3 tensor flops (three products per step, about five
+    // steps) and some 0.3 ms of fixed work; an iteration costs two row gathers, a transpose and
+    // about 0.1 ms of launches, and about ten are needed.  The doubling is cheaper below
+    // Np ~ 6000 (measured: 0.9 against 1.3 ms at N = 4096, 5.1 against 2.1 ms at N = 8192).
+    const int64_t np = round_up(std::max<int64_t>(a.n, 1), 256);
+    if (a.path == DL_PATH_AUTO && np >= 6144) {
+        bool done = false;
+        const dl_status rc = sg_iteration(ctx, ws, s, a, st, &done);
+        if (rc != DL_OK || done) return rc;
+    }
+    return sg_doubling(ctx, ws, s, a, st);
+}
+
+// Same generation by boolean doubling on the tensor cores: S_{2m} = min1(S_m + Q_m S_m Q_m^T),
+// Q_{2m} = min1(Q_m^2), from S_1 = B, Q_1 = P.
+dl_status sg_doubling(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &a, dl_stats *st) {
     const int32_t n = a.n;
     const int64_t np = round_up(std::max<int64_t>(n, 1), 256);
     const int64_t wp = np / 64;
@@ -845,8 +979,9 @@ dl_status solve_sg(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &
         ++step;
         if ((rc = read_scalars(ws, s))) return rc;
         const unsigned long long cs = host_scal(ws)[SC_CS], cq = host_scal(ws)[SC_CQ];
-        if (cs == s_count || cq == 0) break;
+        const bool stop = cs == s_count || cq == 0;
         s_count = cs;
+        if (stop) break;
     }
     tm.mark(2);
     if ((rc = write_bits(s, sbits, wp, a.out_bits, n, a.mem))) return rc;
@@ -857,6 +992,8 @@ dl_status solve_sg(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &
         st->eps_used = eps;
         st->iters = step;
         gc.fill(st);
+        // ones of S over the padded size, less the padding's own diagonal when B = I
+        st->model_ones = static_cast<int64_t>(s_count) - (Bm ? 0 : static_cast<int64_t>(np - n));
         st->ms_factor = tm.ms(0, 1);
         st->ms_solve = tm.ms(1, 2);
         st->ms_epilogue = tm.ms(2, 3);

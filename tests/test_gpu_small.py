@@ -291,3 +291,42 @@ def test_sg_with_base_relation_and_degenerate(ctx):
     with pytest.raises(dl.DLError) as ei:
         ctx.sg_least_model(p, path="fp64")
     assert ei.value.status == dl.DL_ENOTIMPL
+
+
+@pytest.mark.parametrize("n,seed", [(6200, 21), (6400, 22)])
+def test_sg_iteration_and_doubling_agree(ctx, n, seed):
+    """At these sizes AUTO runs the Iteration on bits (S <- B | P S P^T with bit transposes
+    and row gathers, heavy parent lists split into work units); bool_fp8 runs the
+    tensor-core doubling.  Both must give the oracle's model, also for a base relation B that
+    is not symmetric (S is then not symmetric either)."""
+    oracle.set_threads(0)
+    for p in (inputs.pa_dag(n, seed), inputs.forest_dag(n, seed, extra_prob=0.02)):
+        ref = oracle.sg_model(p)
+        a, sta = ctx.sg_least_model(p, path="auto")
+        b, stb = ctx.sg_least_model(p, path="bool_fp8")
+        assert np.array_equal(a, ref) and np.array_equal(b, ref)
+        assert sta["path_used"] == dl.PATHS["auto"] and stb["path_used"] == dl.PATHS["bool_fp8"]
+        ones = int(np.unpackbits(ref.view(np.uint8)).sum())
+        assert sta["model_ones"] == ones and stb["model_ones"] == ones
+    p = inputs.pa_dag(n, seed)
+    bm = inputs.er_digraph(n, 2.0 / n, seed + 1, self_loops=True)
+    assert not np.array_equal(bm, bm.T)
+    ref = oracle.sg_model(p, bm)
+    assert np.array_equal(ctx.sg_least_model(p, bm, path="auto")[0], ref)
+    assert np.array_equal(ctx.sg_least_model(p, bm, path="bool_fp8")[0], ref)
+
+
+def test_sg_deep_derivations_fall_back_to_doubling(ctx):
+    """Two chains of 100 under one root (and isolated constants up to a size where AUTO
+    iterates): the pair at depth k appears after k iterations, more than the Iteration's
+    budget, so AUTO hands the problem to the doubling."""
+    n = 6200
+    p = np.zeros((n, n), dtype=np.uint8)
+    for chain in (range(1, 101), range(101, 201)):
+        prev = 0
+        for v in chain:
+            p[v, prev] = 1
+            prev = v
+    bits, st = ctx.sg_least_model(p, path="auto")
+    assert np.array_equal(bits, oracle.sg_model(p))
+    assert st["path_used"] == dl.PATHS["bool_fp8"]
