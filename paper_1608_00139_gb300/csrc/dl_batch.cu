@@ -44,6 +44,7 @@ struct BatchInst {
     uint64_t *rbits;   // reflexive-closure candidate M, np x wp
     uint64_t *mbits;   // model bits, np x wp (host outputs are copied from here)
     uint64_t *out;     // user output (device memory, n rows of ceil(n/64) words) or null
+    uint64_t *colmask; // the columns with an incoming edge, wp words
     int32_t n, np;
     int32_t wp;
     int32_t tiles;  // GEMM tiles of the squaring
@@ -122,6 +123,20 @@ __global__ void __launch_bounds__(256)
     fill_row_from_bits(I.rbits + static_cast<int64_t>(r) * I.wp, I.wp, r, ptr[gr], ptr[gr + 1], col, lane);
 }
 
+// Column mask of every instance (CTA per instance): the columns its CSR names.  No row of
+// the reflexive closure leaves the mask plus its own bit, no row of E M leaves the mask.
+__global__ void __launch_bounds__(256)
+    batch_colmask_kernel(const BatchInst *__restrict__ inst, const int *__restrict__ ptr, const int *__restrict__ col) {
+    extern __shared__ unsigned long long cm_s[];
+    const BatchInst I = inst[blockIdx.x];
+    for (int w = threadIdx.x; w < I.wp; w += blockDim.x) cm_s[w] = 0ull;
+    __syncthreads();
+    for (int q = ptr[I.row0] + threadIdx.x; q < ptr[I.row0 + I.n]; q += blockDim.x)
+        atomicOr(&cm_s[col[q] >> 6], 1ull << (col[q] & 63));
+    __syncthreads();
+    for (int w = threadIdx.x; w < I.wp; w += blockDim.x) I.colmask[w] = cm_s[w];
+}
+
 // Block-wide exclusive scan of four counters at once (kListThreads threads).
 __device__ __forceinline__ int4 block_scan4(int4 v, int4 *total) {
     __shared__ int4 part[kListThreads / 32];
@@ -198,11 +213,6 @@ __global__ void __launch_bounds__(kListThreads)
     }
 }
 
-__device__ __forceinline__ uint64_t full_word(int n, int w) {
-    const int lo = 64 * w;
-    return lo >= n ? 0ull : (n - lo >= 64 ? ~0ull : ((1ull << (n - lo)) - 1ull));
-}
-
 // Rows of the listed instances, claimed kChunk at a time.  With WPL == 1 a row takes G lanes
 // (G = wp rounded up to a power of two) and a warp works on 32 / G rows of one instance at
 // once; with WPL > 1 a row takes the warp and each lane WPL words.  Successors are taken U at
@@ -254,7 +264,9 @@ __global__ void __launch_bounds__(256)
                 for (int q = 0; q < WPL; ++q) {
                     const int w = w0 + G * q;
                     const bool v = act && w < I.wp;
-                    fullw[q] = v ? full_word(I.n, w) : 0ull;
+                    // the most the row can hold (kept in a register across the successor loop)
+                    fullw[q] = v ? I.colmask[w] | ((!EMIT && w == (i >> 6)) ? 1ull << (i & 63) : 0ull) : 0ull;
+                    asm volatile("" : "+l"(fullw[q]));
                     mi[q] = v ? M[static_cast<int64_t>(i) * I.wp + w] : 0ull;
                     acc[q] = EMIT ? 0ull : mi[q];
                     sat &= acc[q] == fullw[q];
@@ -425,7 +437,8 @@ dl_status solve_tc_batch(dl_ctx *ctx, Workspace &ws, cudaStream_t s, int32_t cou
     const int bn = 128;  // GEMM tile width for the batch (small instances waste less padding)
     const int tm = gemm_tile_m();
     std::vector<BatchInst> inst(L);
-    int64_t in_bytes = 0, mat_bytes = 0, bit_words = 0, prow = 0, row = 0, max_np = 0, max_wp = 0, tiles = 0;
+    int64_t in_bytes = 0, mat_bytes = 0, bit_words = 0, prow = 0, row = 0, max_np = 0, max_wp = 0, tiles = 0,
+            wp_words = 0;
     for (int i = 0; i < L; ++i) {
         const int32_t n = ns[live[i]];
         const int64_t np = round_up(n, 128);
@@ -441,6 +454,7 @@ dl_status solve_tc_batch(dl_ctx *ctx, Workspace &ws, cudaStream_t s, int32_t cou
         in_bytes += round_up(static_cast<int64_t>(n) * n, 256);
         mat_bytes += np * np;
         bit_words += np * (np / 64);
+        wp_words += np / 64;
         max_np = std::max(max_np, np);
         max_wp = std::max(max_wp, np / 64);
     }
@@ -458,6 +472,7 @@ dl_status solve_tc_batch(dl_ctx *ctx, Workspace &ws, cudaStream_t s, int32_t cou
     auto *c0 = static_cast<uint8_t *>(ws.get("batch_c0", mat_bytes));
     auto *rb = static_cast<uint64_t *>(ws.get("batch_rbits", bit_words * 8));
     auto *mb = static_cast<uint64_t *>(ws.get("batch_mbits", bit_words * 8));
+    auto *cmask = static_cast<uint64_t *>(ws.get("batch_colmask", std::max<int64_t>(wp_words, 1) * 8));
     auto *ctr = static_cast<unsigned long long *>(ws.get("batch_ctr", kCounterArrays * sizeof(unsigned long long) * L));
     auto *state = static_cast<int *>(ws.get("batch_state", sizeof(int) * L));
     auto *lists = static_cast<int *>(ws.get("batch_list", sizeof(int) * (8 + 3 * (L + 1) + 2 + 2 * L + 1)));
@@ -469,7 +484,7 @@ dl_status solve_tc_batch(dl_ctx *ctx, Workspace &ws, cudaStream_t s, int32_t cou
     auto *scratch = static_cast<int *>(ws.get("batch_scan", sizeof(int) * 2 * (scan_blocks + 1)));
     uint8_t *staging = nullptr;
     if (mem == DL_MEM_HOST) staging = static_cast<uint8_t *>(ws.get("batch_in", std::max<int64_t>(in_bytes, 256)));
-    if (!c0 || !rb || !mb || !ctr || !state || !lists || !dinst || !dprob || !pinst || !gcnt || !gptr ||
+    if (!c0 || !rb || !mb || !cmask || !ctr || !state || !lists || !dinst || !dprob || !pinst || !gcnt || !gptr ||
         !scratch || (mem == DL_MEM_HOST && !staging)) {
         set_error("batch: device allocation failed (%.2f GB of operands)", 1.0 * mat_bytes / 1e9);
         return DL_ENOMEM;
@@ -479,7 +494,7 @@ dl_status solve_tc_batch(dl_ctx *ctx, Workspace &ws, cudaStream_t s, int32_t cou
 
     cudaEvent_t ev0 = ws.ev[0], ev1 = ws.ev[1];
     BCK(cudaEventRecord(ev0, s));
-    int64_t mo = 0, bo = 0, io = 0;
+    int64_t mo = 0, bo = 0, io = 0, co = 0;
     for (int i = 0; i < L; ++i) {
         const int k = live[i];
         const int64_t np = inst[i].np, n = inst[i].n;
@@ -494,6 +509,8 @@ dl_status solve_tc_batch(dl_ctx *ctx, Workspace &ws, cudaStream_t s, int32_t cou
         inst[i].rbits = rb + bo;
         inst[i].mbits = mb + bo;
         inst[i].out = mem == DL_MEM_DEVICE ? out_bits[k] : nullptr;
+        inst[i].colmask = cmask + co;
+        co += np / 64;
         mo += np * np;
         bo += np * (np / 64);
     }
@@ -575,8 +592,9 @@ dl_status solve_tc_batch(dl_ctx *ctx, Workspace &ws, cudaStream_t s, int32_t cou
         cap(cudaMemsetAsync(state, 0, sizeof(int) * L, s));
         cap(cudaMemsetAsync(ctr, 0, kCounterArrays * sizeof(unsigned long long) * L, s));
         batch_fill_kernel<<<prow_grid, 256, 0, s>>>(dinst, pinst, static_cast<int>(total_prows), gptr, gcol);
+        batch_colmask_kernel<<<L, 256, static_cast<size_t>(max_wp) * 8, s>>>(dinst, gptr, gcol);
         batch_list_kernel<<<1, kListThreads, 0, s>>>(dinst, L, bc, bl, B_ACTIVE, 0);
-        launches += 2;
+        launches += 3;
         cap(cudaGetLastError());
         for (int k = 0; k < kFirstSweeps; ++k) sweep();
         cap(cudaGetLastError());

@@ -272,6 +272,49 @@ class Context:
         _check(lib().dl_tc_batch(self._h, cnt, ns, ptrs, mem, optrs, ctypes.byref(st)))
         return [b for b, _ in outs], st.as_dict()
 
+    def tc_batch_flat(self, buf, ns, offsets):
+        """dl_tc_batch over instances stored back to back in one buffer: instance k is the
+        ns[k] x ns[k] row-major matrix at byte offsets[k] of ``buf`` (a 1-D uint8 torch CUDA
+        tensor or numpy array).  Returns (out, out_offsets, stats): ``out`` is one int64 buffer
+        (same memory kind) holding model k as ns[k] rows of words(ns[k]) words from word
+        out_offsets[k].  The pointer arrays are built with numpy, so the call costs no Python
+        work per instance."""
+        ns = np.ascontiguousarray(ns, dtype=np.int32)
+        offsets = np.ascontiguousarray(offsets, dtype=np.uint64)
+        cnt = int(ns.shape[0])
+        if offsets.shape[0] != cnt:
+            raise ValueError("ns and offsets differ in length")
+        if cnt == 0:
+            return None, np.zeros(0, np.int64), Stats().as_dict()
+        wsz = ns.astype(np.int64) * ((ns.astype(np.int64) + 63) // 64)
+        out_offsets = np.concatenate(([0], np.cumsum(wsz)[:-1])).astype(np.int64)
+        total = int(wsz.sum())
+        if _is_torch(buf) and buf.is_cuda:
+            import torch
+            if buf.dtype != torch.uint8 or buf.dim() != 1 or not buf.is_contiguous():
+                raise ValueError("expected a contiguous 1-D torch.uint8 CUDA tensor")
+            torch.cuda.current_stream(buf.device).synchronize()
+            mem, base, size = DL_MEM_DEVICE, buf.data_ptr(), buf.numel()
+            out = torch.empty(max(total, 1), dtype=torch.int64, device=buf.device)
+            obase = out.data_ptr()
+        else:
+            a = buf.numpy() if _is_torch(buf) else buf
+            a = np.ascontiguousarray(a, dtype=np.uint8).reshape(-1)
+            mem, base, size, buf = DL_MEM_HOST, a.ctypes.data, a.size, a
+            out = np.zeros(max(total, 1), dtype=np.uint64)
+            obase = out.ctypes.data
+        end = offsets + (ns.astype(np.uint64) * ns.astype(np.uint64))
+        if cnt and int(end.max()) > size:
+            raise ValueError("an instance extends past the end of the buffer")
+        ptrs = (np.uint64(base) + offsets).astype(np.uint64)
+        optrs = (np.uint64(obase) + out_offsets.astype(np.uint64) * np.uint64(8)).astype(np.uint64)
+        c_ns = (ctypes.c_int32 * cnt).from_buffer(ns)
+        c_ptrs = (ctypes.c_void_p * cnt).from_buffer(ptrs)
+        c_optrs = (ctypes.c_void_p * cnt).from_buffer(optrs)
+        st = Stats()
+        _check(lib().dl_tc_batch(self._h, cnt, c_ns, c_ptrs, mem, c_optrs, ctypes.byref(st)))
+        return out[:total], out_offsets, st.as_dict()
+
     # ---- serving -------------------------------------------------------------------
     def submit(self, kind: int, base, B=None, path: str = "auto"):
         """Queue a request (0 = closure, 1 = same generation); returns (ticket, handle).

@@ -97,3 +97,25 @@ def test_batch_misaligned_rows_self_loops_wide_rows(ctx):
         ref = oracle.tc_model(e)
         assert np.array_equal(d.cpu().numpy().view(np.uint64), ref)
         assert np.array_equal(h, ref)
+
+
+def test_batch_flat_buffer_matches_list_call(ctx):
+    """tc_batch_flat: instances back to back in one buffer (odd offsets too), one output
+    buffer; every model equals the oracle's and the per-tensor call's."""
+    gs = small_batch(30, 700)
+    ns = np.array([g.shape[0] for g in gs], dtype=np.int32)
+    offsets, pos = [], 0
+    for k, g in enumerate(gs):
+        pos += k % 5  # misaligned starts
+        offsets.append(pos)
+        pos += g.size
+    flat = np.zeros(pos + 16, dtype=np.uint8)
+    for g, o in zip(gs, offsets):
+        flat[o:o + g.size] = g.reshape(-1)
+    for buf in (flat, torch.from_numpy(flat).cuda()):
+        out, ooff, st = ctx.tc_batch_flat(buf, ns, offsets)
+        out = out.cpu().numpy() if hasattr(out, "cpu") else out
+        for g, n, o in zip(gs, ns, ooff):
+            w = (int(n) + 63) // 64
+            got = out[o:o + int(n) * w].view(np.uint64).reshape(int(n), w)
+            assert np.array_equal(got, oracle.tc_model(g))
