@@ -35,6 +35,7 @@ constexpr unsigned kFull = 0xffffffffu;
 enum : int { B_ACTIVE = 0, B_EMIT = 1, B_DONE = 2 };
 constexpr int kFirstSweeps = 24;  // sweeps before any squaring
 constexpr int kRoundSweeps = 4;   // sweeps after each squaring round
+constexpr int kMainRounds = 2;    // squaring rounds in the main graph (the rest only if needed)
 constexpr int kChunk = 32;        // rows a warp claims at a time in the row kernels
 constexpr int kListThreads = 1024;
 
@@ -418,11 +419,15 @@ struct BatchPlan {
     std::vector<void *> outs;
     const void *col = nullptr;
     int mem = -1;
-    cudaGraphExec_t exec = nullptr;
-    int rounds = 0;
-    int launches = 0;  // kernels in the graph
+    // main: CSR fill, first sweeps, the first squaring rounds, emission of the converged
+    // instances; more: the remaining rounds and their emission (launched only if an instance
+    // is still active after main)
+    cudaGraphExec_t exec = nullptr, exec_more = nullptr;
+    int rounds = 0, rounds_more = 0;
+    int launches = 0, launches_more = 0;  // kernels in each graph
     ~BatchPlan() {
         if (exec) cudaGraphExecDestroy(exec);
+        if (exec_more) cudaGraphExecDestroy(exec_more);
     }
 };
 
@@ -585,57 +590,90 @@ dl_status solve_tc_batch(dl_ctx *ctx, Workspace &ws, cudaStream_t s, int32_t cou
             batch_list_kernel<<<1, kListThreads, 0, s>>>(dinst, L, bc, bl, B_ACTIVE, 1);
             launches += 2;
         };
-        cudaGraph_t graph = nullptr;
-        BCK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
-        bool cap_ok = true;
-        auto cap = [&](cudaError_t e) { cap_ok = cap_ok && e == cudaSuccess; };
-        cap(cudaMemsetAsync(state, 0, sizeof(int) * L, s));
-        cap(cudaMemsetAsync(ctr, 0, kCounterArrays * sizeof(unsigned long long) * L, s));
-        batch_fill_kernel<<<prow_grid, 256, 0, s>>>(dinst, pinst, static_cast<int>(total_prows), gptr, gcol);
-        batch_colmask_kernel<<<L, 256, static_cast<size_t>(max_wp) * 8, s>>>(dinst, gptr, gcol);
-        batch_list_kernel<<<1, kListThreads, 0, s>>>(dinst, L, bc, bl, B_ACTIVE, 0);
-        launches += 3;
-        cap(cudaGetLastError());
-        for (int k = 0; k < kFirstSweeps; ++k) sweep();
-        cap(cudaGetLastError());
-        for (int r = 0; r < rounds; ++r) {
+        const int rounds_main = std::min(rounds, kMainRounds);
+        auto round = [&]() {
             batch_to_e4m3_kernel<<<rgrid, 256, 0, s>>>(dinst, bl, bc);
-            cap(gemm_launch(KIND_F8, false, bn, EPI_BOOL, dprob, L, static_cast<int>(tiles), ggrid, ws.status,
-                            ctx->budget_ns, s, bl.sched));
+            const cudaError_t e = gemm_launch(KIND_F8, false, bn, EPI_BOOL, dprob, L, static_cast<int>(tiles), ggrid,
+                                              ws.status, ctx->budget_ns, s, bl.sched);
             launches += 2;
             for (int k = 0; k < kRoundSweeps; ++k) sweep();
-            cap(cudaGetLastError());
-        }
-        batch_list_kernel<<<1, kListThreads, 0, s>>>(dinst, L, bc, bl, B_EMIT, 0);
-        launch_rows<true>(wpl, rgrid, dinst, bl, gptr, gcol, bc, s);
-        decide_final<<<(L + 255) / 256, 256, 0, s>>>(L, bc, ws.status);
-        launches += 3;
-        cap(cudaGetLastError());
-        const cudaError_t ec = cudaStreamEndCapture(s, &graph);
-        if (!cap_ok || ec != cudaSuccess) {
-            if (graph) cudaGraphDestroy(graph);
-            cudaGetLastError();
-            set_error("batch: stream capture failed (%s)", cudaGetErrorString(ec));
-            return DL_EDEVICE;
-        }
+            return e;
+        };
+        auto emit = [&]() {
+            batch_list_kernel<<<1, kListThreads, 0, s>>>(dinst, L, bc, bl, B_EMIT, 0);
+            launch_rows<true>(wpl, rgrid, dinst, bl, gptr, gcol, bc, s);
+            decide_final<<<(L + 255) / 256, 256, 0, s>>>(L, bc, ws.status);
+            launches += 3;
+        };
+        // capture one schedule; body() issues its launches and returns the first error
+        auto capture = [&](auto body, cudaGraphExec_t *out) -> dl_status {
+            cudaGraph_t graph = nullptr;
+            BCK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+            cudaError_t e = body();
+            if (e == cudaSuccess) e = cudaGetLastError();
+            const cudaError_t ec = cudaStreamEndCapture(s, &graph);
+            if (e != cudaSuccess || ec != cudaSuccess) {
+                if (graph) cudaGraphDestroy(graph);
+                cudaGetLastError();
+                set_error("batch: stream capture failed (%s)", cudaGetErrorString(e != cudaSuccess ? e : ec));
+                return DL_EDEVICE;
+            }
+            const cudaError_t ei = cudaGraphInstantiate(out, graph, 0);
+            cudaGraphDestroy(graph);
+            if (ei != cudaSuccess) {
+                set_error("batch: graph instantiation failed (%s)", cudaGetErrorString(ei));
+                return DL_EDEVICE;
+            }
+            return DL_OK;
+        };
         plan = new BatchPlan();
         plan->ns = key_ns;
         plan->ins = key_in;
         plan->outs = key_out;
         plan->col = gcol;
         plan->mem = static_cast<int>(mem);
-        plan->rounds = rounds;
+        dl_status rc = capture(
+            [&]() -> cudaError_t {
+                cudaError_t e = cudaMemsetAsync(state, 0, sizeof(int) * L, s);
+                if (e == cudaSuccess) e = cudaMemsetAsync(ctr, 0, kCounterArrays * sizeof(unsigned long long) * L, s);
+                batch_fill_kernel<<<prow_grid, 256, 0, s>>>(dinst, pinst, static_cast<int>(total_prows), gptr, gcol);
+                batch_colmask_kernel<<<L, 256, static_cast<size_t>(max_wp) * 8, s>>>(dinst, gptr, gcol);
+                batch_list_kernel<<<1, kListThreads, 0, s>>>(dinst, L, bc, bl, B_ACTIVE, 0);
+                launches += 3;
+                for (int k = 0; k < kFirstSweeps; ++k) sweep();
+                for (int r = 0; r < rounds_main && e == cudaSuccess; ++r) e = round();
+                emit();
+                return e;
+            },
+            &plan->exec);
+        plan->rounds = rounds_main;
         plan->launches = launches;
-        const cudaError_t ei = cudaGraphInstantiate(&plan->exec, graph, 0);
-        cudaGraphDestroy(graph);
-        if (ei != cudaSuccess) {
+        launches = 0;
+        if (rc == DL_OK && rounds > rounds_main)
+            rc = capture(
+                [&]() -> cudaError_t {
+                    batch_list_kernel<<<1, kListThreads, 0, s>>>(dinst, L, bc, bl, B_ACTIVE, 0);
+                    ++launches;
+                    cudaError_t e = cudaSuccess;
+                    for (int r = rounds_main; r < rounds && e == cudaSuccess; ++r) e = round();
+                    emit();
+                    return e;
+                },
+                &plan->exec_more);
+        plan->rounds_more = rounds - rounds_main;
+        plan->launches_more = launches;
+        if (rc != DL_OK) {
             delete plan;
             plan = nullptr;
-            set_error("batch: graph instantiation failed (%s)", cudaGetErrorString(ei));
-            return DL_EDEVICE;
+            return rc;
         }
     }
     BCK(cudaGraphLaunch(plan->exec, s));
+    std::vector<int> hstate(L);
+    BCK(cudaMemcpyAsync(hstate.data(), state, sizeof(int) * L, cudaMemcpyDeviceToHost, s));
+    BCK(cudaStreamSynchronize(s));
+    const bool more = std::any_of(hstate.begin(), hstate.end(), [](int x) { return x == B_ACTIVE; });
+    if (more && plan->exec_more) BCK(cudaGraphLaunch(plan->exec_more, s));
     if (mem == DL_MEM_HOST) {
         for (int i = 0; i < L; ++i) {
             const int64_t n = inst[i].n, w = (n + 63) / 64;
@@ -644,7 +682,6 @@ dl_status solve_tc_batch(dl_ctx *ctx, Workspace &ws, cudaStream_t s, int32_t cou
         }
     }
     BCK(cudaEventRecord(ev1, s));
-    std::vector<int> hstate(L);
     std::vector<unsigned long long> hctr(kCounterArrays * static_cast<size_t>(L));
     BCK(cudaMemcpyAsync(hstate.data(), state, sizeof(int) * L, cudaMemcpyDeviceToHost, s));
     BCK(cudaMemcpyAsync(hctr.data(), ctr, sizeof(unsigned long long) * kCounterArrays * L, cudaMemcpyDeviceToHost,
@@ -685,9 +722,9 @@ dl_status solve_tc_batch(dl_ctx *ctx, Workspace &ws, cudaStream_t s, int32_t cou
         st->ms_total = ms;
         st->ms_solve = ms;
         st->tflops_equiv = ms > 0 ? equiv / (ms * 1e-3) / 1e12 : 0.0;
-        st->gemm_launches = plan->rounds;
+        st->gemm_launches = plan->rounds + (more ? plan->rounds_more : 0);
         st->gemm_flops = flops;
-        st->gpu_launches = pre_launches + plan->launches;
+        st->gpu_launches = pre_launches + plan->launches + (more ? plan->launches_more : 0);
     }
     return DL_OK;
 }

@@ -386,66 +386,17 @@ __global__ void bits_to_e4m3_kernel(const uint64_t *__restrict__ bits, int64_t w
     }
 }
 
-// Single-row Iteration (eq. series:trcl on one row vector x_i, x <- min1(e_i + x E) for the
-// successor relation), semi-naive: one warp per row keeps the row's bits in shared memory and
-// expands only the nodes that entered x in the last step, lanes taking frontier nodes and
-// setting their successors' bits with shared-memory atomicOr.  When the frontier empties, x
-// is the exact row i of the reflexive closure.  A frontier larger than kFront, or more than
-// kMaxSteps steps (long paths are left to squarings), ends the row early: its bits (all
-// reachable from i) are kept and *open_rows counts it.
-constexpr int kFront = 256;
-constexpr int kMaxSteps = 64;
-
+// Rows of the reflexive closure by the Iteration on single rows (see iterate_row).
 __global__ void __launch_bounds__(256)
     row_iteration_kernel(const int *__restrict__ ptr, const int *__restrict__ col, int n, int wp, uint64_t *M,
                          unsigned long long *open_rows) {
     extern __shared__ uint64_t row_smem[];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
-    uint64_t *bits = row_smem + static_cast<size_t>(wid) * (wp + kFront + 1);
-    int *front = reinterpret_cast<int *>(bits + wp);  // two frontiers of kFront
-    int *next_cnt = front + 2 * kFront;
+    uint64_t *bits = row_smem + static_cast<size_t>(wid) * (wp + kRowFront + 1);
     const int i = blockIdx.x * (blockDim.x >> 5) + wid;
     if (i >= n) return;
-    for (int w = lane; w < wp; w += 32) bits[w] = w == (i >> 6) ? 1ull << (i & 63) : 0ull;
-    if (lane == 0) front[0] = i;
-    int cur = 0, cnt = 1, steps = 0;
-    bool ok = true;
-    __syncwarp();
-    while (cnt > 0) {
-        if (++steps > kMaxSteps) {
-            ok = false;
-            break;
-        }
-        if (lane == 0) *next_cnt = 0;
-        __syncwarp();
-        const int *fc = front + cur * kFront;
-        int *fn = front + (cur ^ 1) * kFront;
-        for (int f = lane; f < cnt; f += 32) {
-            const int k = fc[f];
-            const int q1 = ptr[k + 1];
-            for (int q = ptr[k]; q < q1; ++q) {
-                const int j = col[q];
-                const unsigned long long b = 1ull << (j & 63);
-                const unsigned long long old = atomicOr(reinterpret_cast<unsigned long long *>(bits + (j >> 6)), b);
-                if (!(old & b)) {
-                    const int pos = atomicAdd(next_cnt, 1);
-                    if (pos < kFront) fn[pos] = j;
-                }
-            }
-        }
-        __syncwarp();
-        cnt = *next_cnt;
-        __syncwarp();  // every lane has read the count before lane 0 clears it
-        if (cnt > kFront) {
-            ok = false;
-            break;
-        }
-        cur ^= 1;
-    }
-    __syncwarp();
-    uint64_t *mrow = M + static_cast<int64_t>(i) * wp;
-    for (int w = lane; w < wp; w += 32) mrow[w] = bits[w];
-    if (!ok && lane == 0) atomicAdd(open_rows, 1ull);
+    if (!iterate_row(ptr, col, i, wp, bits, M + static_cast<int64_t>(i) * wp, lane) && lane == 0)
+        atomicAdd(open_rows, 1ull);
 }
 
 // ---- same generation on bits --------------------------------------------------------------
@@ -640,7 +591,7 @@ cudaError_t row_iteration(const int *ptr, const int *col, int n, int64_t wp, uin
                           unsigned long long *open_rows, cudaStream_t s) {
     if (n <= 0) return cudaSuccess;
     if (!row_iteration_fits(wp)) return cudaErrorInvalidValue;
-    const size_t smem = 8 * (static_cast<size_t>(wp) + kFront + 1) * sizeof(uint64_t);
+    const size_t smem = 8 * (static_cast<size_t>(wp) + kRowFront + 1) * sizeof(uint64_t);
     row_iteration_kernel<<<(n + 7) / 8, 256, smem, s>>>(ptr, col, n, static_cast<int>(wp), M, open_rows);
     return cudaGetLastError();
 }

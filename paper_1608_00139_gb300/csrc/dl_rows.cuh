@@ -321,4 +321,61 @@ __device__ __forceinline__ void fill_row_from_bits(const uint64_t *row, int wp, 
     }
 }
 
+// Single-row Iteration (eq. series:trcl on one row vector x_i, x <- min1(e_i + x E) for the
+// successor relation), semi-naive: one warp keeps the row's bits in shared memory (`bits`:
+// wp words, then two frontiers of kRowFront ints and a counter) and expands only the nodes
+// that entered x in the last step, lanes taking frontier nodes and setting their successors'
+// bits with shared-memory atomicOr.  ptr/col: the CSR with column indices local to the
+// problem (ptr may be offset so that ptr[k] is local row k).  When the frontier empties, x
+// is the exact row i of the reflexive closure; a frontier larger than kRowFront or more than
+// kRowSteps steps (long paths are left to squarings) ends the row early.  Either way the bits
+// reached (all reachable from i) go to mrow; returns whether the row is exact.
+constexpr int kRowFront = 256;
+constexpr int kRowSteps = 64;
+
+__device__ __forceinline__ bool iterate_row(const int *__restrict__ ptr, const int *__restrict__ col, int i, int wp,
+                                            uint64_t *bits, uint64_t *mrow, int lane) {
+    int *front = reinterpret_cast<int *>(bits + wp);  // two frontiers of kRowFront
+    int *next_cnt = front + 2 * kRowFront;
+    for (int w = lane; w < wp; w += 32) bits[w] = w == (i >> 6) ? 1ull << (i & 63) : 0ull;
+    if (lane == 0) front[0] = i;
+    int cur = 0, cnt = 1, steps = 0;
+    bool ok = true;
+    __syncwarp();
+    while (cnt > 0) {
+        if (++steps > kRowSteps) {
+            ok = false;
+            break;
+        }
+        if (lane == 0) *next_cnt = 0;
+        __syncwarp();
+        const int *fc = front + cur * kRowFront;
+        int *fn = front + (cur ^ 1) * kRowFront;
+        for (int f = lane; f < cnt; f += 32) {
+            const int k = fc[f];
+            const int q1 = ptr[k + 1];
+            for (int q = ptr[k]; q < q1; ++q) {
+                const int j = col[q];
+                const unsigned long long b = 1ull << (j & 63);
+                const unsigned long long old = atomicOr(reinterpret_cast<unsigned long long *>(bits + (j >> 6)), b);
+                if (!(old & b)) {
+                    const int pos = atomicAdd(next_cnt, 1);
+                    if (pos < kRowFront) fn[pos] = j;
+                }
+            }
+        }
+        __syncwarp();
+        cnt = *next_cnt;
+        __syncwarp();  // every lane has read the count before lane 0 clears it
+        if (cnt > kRowFront) {
+            ok = false;
+            break;
+        }
+        cur ^= 1;
+    }
+    __syncwarp();
+    for (int w = lane; w < wp; w += 32) mrow[w] = bits[w];
+    return ok;
+}
+
 }  // namespace dl
