@@ -89,62 +89,95 @@ cudaError_t transpose(const T *src, int64_t lds, int rows, int cols, T *dst, int
     return cudaGetLastError();
 }
 
-// Unpivoted LU of the BL x BL block at A (row stride lda) in shared memory (FP32), then the
-// inverses of its factors in place; writes L^-1 (unit lower), U^-1 and U^-T, BL x BL each.
-__global__ void __launch_bounds__(256) diag_lu_inv_kernel(const float *A, int64_t lda, float *Linv,
-                                                          float *Uinv, float *UinvT, int *status) {
-    extern __shared__ float sm[];
-    auto S = [&](int i, int j) -> float & { return sm[i * (BL + 1) + j]; };
-    for (int t = threadIdx.x; t < BL * BL; t += blockDim.x) S(t / BL, t % BL) = A[(t / BL) * lda + t % BL];
-    __syncthreads();
-    // Doolittle LU (unit L)
+// Unpivoted LU of the BL x BL block at A (row stride lda) with the inverses of its factors,
+// FP32, by Gauss-Jordan elimination held in registers: 1024 threads, thread t owns columns
+// (t & 7) + 8 q, q = 0 .. 31, of row t >> 3 of the augmented BL x 2BL matrix (interleaved, so
+// that the 8 threads of a row read 8 different shared-memory banks of the pivot row).
+//  1. forward elimination of [A | I] (row_r -= (a_rk / a_kk) row_k for r > k) leaves [U | L^-1];
+//  2. backward elimination of [U | I] (row_k /= u_kk, then row_i -= u_ik row_k for i < k; the
+//     multipliers are U's entries, unchanged by the later steps) leaves U^-1 on the right.
+// One barrier per step: the pivot row goes through a double-buffered shared row.
+// Writes L^-1 (unit lower), U^-1 and U^-T, BL x BL each.
+constexpr int kDiagThreads = 1024;
+constexpr int kSolveGroup = 8;  // panels per group of the N-RHS solves
+
+// v[j] for a runtime j (unrolled selects keep v in registers)
+__device__ __forceinline__ float pick32(const float (&v)[32], int j) {
+    float x = 0.0f;
+#pragma unroll
+    for (int q = 0; q < 32; ++q) x = q == j ? v[q] : x;
+    return x;
+}
+
+__global__ void __launch_bounds__(kDiagThreads) diag_lu_inv_kernel(const float *A, int64_t lda, float *Linv,
+                                                                   float *Uinv, float *UinvT, int *status) {
+    static_assert(BL == 128, "the thread layout assumes 128-row diagonal blocks");
+    __shared__ float piv[2][2 * BL];
+    const int t = threadIdx.x;
+    const int r = t >> 3, sg = t & 7;  // row r, columns sg + 8 q (q < 16: A / U, q >= 16: right half)
+    const int row_lane0 = (t & 31) & ~7;
+    float v[32];
+#pragma unroll
+    for (int q = 0; q < 32; ++q) {
+        const int c = sg + 8 * q;
+        v[q] = c < BL ? A[static_cast<int64_t>(r) * lda + c] : (c - BL == r ? 1.0f : 0.0f);
+    }
+    // 1. [A | I] -> [U | L^-1]
     for (int k = 0; k < BL; ++k) {
-        const float piv = S(k, k);
-        if (piv == 0.0f) {
-            if (threadIdx.x == 0) atomicOr(status, ST_BAD_INPUT);
+        float *p = piv[k & 1];
+        if (r == k) {
+#pragma unroll
+            for (int q = 0; q < 32; ++q) p[sg + 8 * q] = v[q];
+        }
+        __syncthreads();
+        const float pk = p[k];
+        if (pk == 0.0f) {  // zero pivot (the M-matrix has none): report and stop (uniform)
+            if (t == 0) atomicOr(status, ST_BAD_INPUT);
             return;
         }
-        for (int i = k + 1 + threadIdx.x; i < BL; i += blockDim.x) S(i, k) /= piv;
-        __syncthreads();
-        const int m = BL - k - 1;
-        for (int t = threadIdx.x; t < m * m; t += blockDim.x) {
-            const int i = k + 1 + t / m, j = k + 1 + t % m;
-            S(i, j) = fmaf(-S(i, k), S(k, j), S(i, j));
+        const float ark = __shfl_sync(0xffffffffu, pick32(v, k >> 3), row_lane0 + (k & 7));  // a_rk
+        if (r > k) {
+            const float m = ark / pk;
+#pragma unroll
+            for (int q = 0; q < 32; ++q) {
+                const int c = sg + 8 * q;
+                if (c > k) v[q] = fmaf(-m, p[c], v[q]);
+            }
+        }
+    }
+    // L^-1 is the right half now: write it, then start the right half over from I
+#pragma unroll
+    for (int q = 16; q < 32; ++q) {
+        const int c = sg + 8 * (q - 16);
+        Linv[r * BL + c] = c < r ? v[q] : (c == r ? 1.0f : 0.0f);
+        v[q] = c == r ? 1.0f : 0.0f;
+    }
+    __syncthreads();
+    // 2. [U | I] -> U^-1 on the right (only the right half is updated)
+    for (int k = BL - 1; k >= 0; --k) {
+        float *p = piv[k & 1];
+        const float ukk = __shfl_sync(0xffffffffu, pick32(v, k >> 3), row_lane0 + (k & 7));  // used in row k
+        if (r == k) {
+            const float inv = 1.0f / ukk;
+#pragma unroll
+            for (int q = 16; q < 32; ++q) {
+                v[q] *= inv;
+                p[sg + 8 * (q - 16)] = v[q];
+            }
         }
         __syncthreads();
-    }
-    // U^-1 in place, column by column: Uinv[i][j] = -(sum_{q=i}^{j-1} Uinv[i][q] U[q][j]) / U[j][j]
-    for (int j = 0; j < BL; ++j) {
-        float x = 0.0f;
-        const int i = threadIdx.x;
-        if (i < j) {
-            for (int q = i; q < j; ++q) x = fmaf(S(i, q), S(q, j), x);
-            x = -x / S(j, j);
+        const float uik = __shfl_sync(0xffffffffu, pick32(v, k >> 3), row_lane0 + (k & 7));  // U's entry (r, k)
+        if (r < k) {
+#pragma unroll
+            for (int q = 16; q < 32; ++q) v[q] = fmaf(-uik, p[sg + 8 * (q - 16)], v[q]);
         }
-        __syncthreads();
-        if (i < j) S(i, j) = x;
-        if (i == 0) S(j, j) = 1.0f / S(j, j);
-        __syncthreads();
     }
-    // L^-1 (unit lower) in place, columns from the right:
-    // Linv[i][j] = -(L[i][j] + sum_{q=j+1}^{i-1} Linv[i][q] L[q][j])
-    for (int j = BL - 2; j >= 0; --j) {
-        float x = 0.0f;
-        const int i = threadIdx.x;
-        if (i > j && i < BL) {
-            x = S(i, j);
-            for (int q = j + 1; q < i; ++q) x = fmaf(S(i, q), S(q, j), x);
-            x = -x;
-        }
-        __syncthreads();
-        if (i > j && i < BL) S(i, j) = x;
-        __syncthreads();
-    }
-    for (int t = threadIdx.x; t < BL * BL; t += blockDim.x) {
-        const int i = t / BL, j = t % BL;
-        Linv[t] = j < i ? S(i, j) : (j == i ? 1.0f : 0.0f);
-        Uinv[t] = j >= i ? S(i, j) : 0.0f;
-        UinvT[t] = i >= j ? S(j, i) : 0.0f;
+#pragma unroll
+    for (int q = 16; q < 32; ++q) {
+        const int c = sg + 8 * (q - 16);
+        const float x = c >= r ? v[q] : 0.0f;
+        Uinv[r * BL + c] = x;
+        UinvT[c * BL + r] = x;
     }
 }
 
@@ -308,18 +341,37 @@ dl_status tc_mixed(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &
         ok = ok && add(lu, EPI_SUB_F32, rem, rem, BL, at(opA, kb + BL, kb), opT, A32, np, kb + BL, kb + BL, false,
                        &flops_lu);
     }
-    for (int k = 0; k < nb && ok; ++k) {
-        const int kb = k * BL, rem = N - kb - BL;
-        ok = add(fwd, EPI_STORE_F32, N, BL, BL, at(opZ, 0, kb), at(opL, kb, 0), Z32, np, 0, kb, false, &flops_solve);
-        if (ok && rem > 0)
-            ok = add(fwd, EPI_SUB_F32, N, rem, BL, at(opZ, 0, kb), at(opA, kb + BL, kb), Z32, np, 0, kb + BL, false,
+    // The N-RHS solves run in groups of kSolveGroup panels: inside a group each panel is
+    // solved with its diagonal inverse and updates the group's later (forward) or earlier
+    // (backward) panels; one update with K = the group's width then carries the whole group to
+    // the columns beyond it, so the trailing part of Z is read and written once per group.
+    for (int g0 = 0; g0 < nb && ok; g0 += kSolveGroup) {
+        const int g1 = std::min(nb, g0 + kSolveGroup), gs = g0 * BL, ge = g1 * BL;
+        for (int k = g0; k < g1 && ok; ++k) {
+            const int kb = k * BL;
+            ok = add(fwd, EPI_STORE_F32, N, BL, BL, at(opZ, 0, kb), at(opL, kb, 0), Z32, np, 0, kb, false,
+                     &flops_solve);
+            if (ok && kb + BL < ge)
+                ok = add(fwd, EPI_SUB_F32, N, ge - kb - BL, BL, at(opZ, 0, kb), at(opA, kb + BL, kb), Z32, np, 0,
+                         kb + BL, false, &flops_solve);
+        }
+        if (ok && ge < N)
+            ok = add(fwd, EPI_SUB_F32, N, N - ge, ge - gs, at(opZ, 0, gs), at(opA, ge, gs), Z32, np, 0, ge, false,
                      &flops_solve);
     }
-    for (int k = nb - 1; k >= 0 && ok; --k) {
-        const int kb = k * BL;
-        ok = add(bwd, EPI_STORE_F32, N, BL, BL, at(opZ, 0, kb), at(opU, kb, 0), Z32, np, 0, kb, false, &flops_solve);
-        if (ok && kb > 0)
-            ok = add(bwd, EPI_SUB_F32, N, kb, BL, at(opZ, 0, kb), at(opA, 0, kb), Z32, np, 0, 0, false, &flops_solve);
+    for (int g1 = nb; g1 > 0 && ok; g1 -= kSolveGroup) {
+        const int g0 = std::max(0, g1 - kSolveGroup), gs = g0 * BL, ge = g1 * BL;
+        for (int k = g1 - 1; k >= g0 && ok; --k) {
+            const int kb = k * BL;
+            ok = add(bwd, EPI_STORE_F32, N, BL, BL, at(opZ, 0, kb), at(opU, kb, 0), Z32, np, 0, kb, false,
+                     &flops_solve);
+            if (ok && kb > gs)
+                ok = add(bwd, EPI_SUB_F32, N, kb - gs, BL, at(opZ, 0, kb), at(opA, gs, kb), Z32, np, 0, gs, false,
+                         &flops_solve);
+        }
+        if (ok && gs > 0)
+            ok = add(bwd, EPI_SUB_F32, N, gs, ge - gs, at(opZ, 0, gs), at(opA, 0, gs), Z32, np, 0, 0, false,
+                     &flops_solve);
     }
     if (!ok) {
         set_error("mixed path: %s", err.c_str());
@@ -333,9 +385,7 @@ dl_status tc_mixed(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &
     MCK(cudaMemcpyAsync(dprob, probs.data(), sizeof(GemmProblem) * probs.size(), cudaMemcpyHostToDevice, s));
     MCK(gemm_prepare(KIND_TF32, true, BL, EPI_STORE_F32));
     MCK(gemm_prepare(KIND_TF32, true, BL, EPI_SUB_F32));
-    const size_t diag_smem = sizeof(float) * BL * (BL + 1);
-    MCK(cudaFuncSetAttribute(diag_lu_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             static_cast<int>(diag_smem)));
+
     auto run = [&](const Launch &L) -> cudaError_t {
         ++launches;
         return gemm_launch(KIND_TF32, true, BL, L.epi, dprob + L.first, L.count, L.tiles,
@@ -345,8 +395,8 @@ dl_status tc_mixed(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &
     // ---- LU ----------------------------------------------------------------------------
     for (int k = 0; k < nb; ++k) {
         const int64_t kb = static_cast<int64_t>(k) * BL;
-        diag_lu_inv_kernel<<<1, 256, diag_smem, s>>>(A32 + kb * np + kb, np, Linv + kb * BL, Uinv + kb * BL,
-                                                     UinvT + kb * BL, ws.status);
+        diag_lu_inv_kernel<<<1, kDiagThreads, 0, s>>>(A32 + kb * np + kb, np, Linv + kb * BL, Uinv + kb * BL,
+                                                      UinvT + kb * BL, ws.status);
         MCK(cudaGetLastError());
         ++launches;
         if (lu_panel[k] >= 0) {
