@@ -214,11 +214,12 @@ template <int WPL>
 __global__ void __launch_bounds__(256)
     sweep_rows_step_kernel(const int *__restrict__ ptr, const int *__restrict__ col, int n, uint64_t *M, int64_t wp,
                            unsigned long long *changed_rows, const unsigned long long *skip_if_zero,
-                           const uint64_t *__restrict__ colmask) {
+                           const uint64_t *__restrict__ colmask, const int *gate) {
     const int lane = threadIdx.x & 31;
     const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (i >= n) return;
     if (skip_if_zero != nullptr && *skip_if_zero == 0) return;  // the previous sweep changed nothing
+    if (gate != nullptr && *gate != 0) return;
     const int q0 = ptr[i], q1 = ptr[i + 1];
     if (q0 == q1) return;
     uint64_t *mrow = M + static_cast<int64_t>(i) * wp;
@@ -253,10 +254,11 @@ template <int WPL>
 __global__ void __launch_bounds__(256)
     sweep_rows_emit_kernel(const int *__restrict__ ptr, const int *__restrict__ col, int n, const uint64_t *M,
                            uint64_t *out, int64_t wp, unsigned long long *violations, unsigned long long *ones,
-                           const uint64_t *__restrict__ colmask) {
+                           const uint64_t *__restrict__ colmask, const int *gate) {
     const int lane = threadIdx.x & 31;
     const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (i >= n) return;
+    if (gate != nullptr && *gate != 0) return;
     uint64_t full[WPL], acc[WPL];
     full_mask<WPL>(n, wp, lane, colmask, -1, full);
 #pragma unroll
@@ -286,13 +288,13 @@ __global__ void __launch_bounds__(256)
 template <int WPL>
 cudaError_t launch_rows(const int *ptr, const int *col, int n, const uint64_t *M, uint64_t *out, int64_t wp,
                         int mode, unsigned long long *violations, unsigned long long *ones,
-                        const unsigned long long *skip, const uint64_t *colmask, cudaStream_t s) {
+                        const unsigned long long *skip, const uint64_t *colmask, const int *gate, cudaStream_t s) {
     if (mode == 1)
         sweep_rows_step_kernel<WPL><<<(n + 7) / 8, 256, 0, s>>>(ptr, col, n, const_cast<uint64_t *>(M), wp,
-                                                                 violations, skip, colmask);
+                                                                 violations, skip, colmask, gate);
     else
         sweep_rows_emit_kernel<WPL><<<(n + 7) / 8, 256, 0, s>>>(ptr, col, n, M, out, wp, violations, ones,
-                                                                 colmask);
+                                                                 colmask, gate);
     return cudaGetLastError();
 }
 
@@ -386,10 +388,16 @@ __global__ void bits_to_e4m3_kernel(const uint64_t *__restrict__ bits, int64_t w
     }
 }
 
-// Rows of the reflexive closure by the Iteration on single rows (see iterate_row).
+// Rows of the reflexive closure by the Iteration on single rows (see iterate_row).  With a
+// gate the launch decides on the device: if *gate is set or the graph has more than two facts
+// per row it does nothing but count every row as open.
 __global__ void __launch_bounds__(256)
     row_iteration_kernel(const int *__restrict__ ptr, const int *__restrict__ col, int n, int wp, uint64_t *M,
-                         unsigned long long *open_rows) {
+                         unsigned long long *open_rows, const int *gate) {
+    if (gate != nullptr && (*gate != 0 || ptr[n] > 2 * n)) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) atomicAdd(open_rows, static_cast<unsigned long long>(n));
+        return;
+    }
     extern __shared__ uint64_t row_smem[];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     uint64_t *bits = row_smem + static_cast<size_t>(wid) * (wp + kRowFront + 1);
@@ -531,14 +539,17 @@ cudaError_t sweep_units(const int *ptr, int n, int *cnt, int *unit_off, cudaStre
 cudaError_t bits_sweep_csr(const int *ptr, const int *col, const int *unit_off, int n, const uint64_t *M,
                            uint64_t *out, int64_t wp, int mode, unsigned long long *violations,
                            unsigned long long *ones, int *launches, cudaStream_t s, int max_deg,
-                           const unsigned long long *skip_if_zero, const uint64_t *colmask) {
+                           const unsigned long long *skip_if_zero, const uint64_t *colmask, const int *gate) {
     if (n <= 0) return cudaSuccess;
     if (row_direct(max_deg, wp)) {  // no heavy rows: row-direct kernels
         if (launches) *launches += 1;
-        if (wp <= 64) return launch_rows<2>(ptr, col, n, M, out, wp, mode, violations, ones, skip_if_zero, colmask, s);
-        if (wp <= 128) return launch_rows<4>(ptr, col, n, M, out, wp, mode, violations, ones, skip_if_zero, colmask, s);
-        return launch_rows<8>(ptr, col, n, M, out, wp, mode, violations, ones, skip_if_zero, colmask, s);
+        if (wp <= 64)
+            return launch_rows<2>(ptr, col, n, M, out, wp, mode, violations, ones, skip_if_zero, colmask, gate, s);
+        if (wp <= 128)
+            return launch_rows<4>(ptr, col, n, M, out, wp, mode, violations, ones, skip_if_zero, colmask, gate, s);
+        return launch_rows<8>(ptr, col, n, M, out, wp, mode, violations, ones, skip_if_zero, colmask, gate, s);
     }
+    if (gate != nullptr) return cudaErrorInvalidValue;  // gated launches are row-direct only
     const unsigned grid = static_cast<unsigned>(num_sms() * 8);
     if (mode == 1) {
         sweep_units_step_kernel<<<grid, 256, 0, s>>>(ptr, col, unit_off, n, const_cast<uint64_t *>(M), wp,
@@ -588,11 +599,11 @@ cudaError_t bits_sweep(const uint8_t *E, int64_t lde, int n, const uint64_t *M, 
 bool row_iteration_fits(int64_t wp) { return wp <= 256; }
 
 cudaError_t row_iteration(const int *ptr, const int *col, int n, int64_t wp, uint64_t *M,
-                          unsigned long long *open_rows, cudaStream_t s) {
+                          unsigned long long *open_rows, cudaStream_t s, const int *gate) {
     if (n <= 0) return cudaSuccess;
     if (!row_iteration_fits(wp)) return cudaErrorInvalidValue;
     const size_t smem = 8 * (static_cast<size_t>(wp) + kRowFront + 1) * sizeof(uint64_t);
-    row_iteration_kernel<<<(n + 7) / 8, 256, smem, s>>>(ptr, col, n, static_cast<int>(wp), M, open_rows);
+    row_iteration_kernel<<<(n + 7) / 8, 256, smem, s>>>(ptr, col, n, static_cast<int>(wp), M, open_rows, gate);
     return cudaGetLastError();
 }
 

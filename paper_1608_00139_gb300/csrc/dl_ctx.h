@@ -41,11 +41,15 @@ struct Workspace {
     cudaEvent_t sev[kGemmEvents] = {};       // start/stop pairs of timed sweep groups
     bool ready = false;
     BatchPlan *batch_plan = nullptr;
+    bool last_heavy = false;  // the last closure on this workspace had rows of > 256 successors
+    bool last_rows_closed = false;  // ... was closed by the Iteration on single rows alone
 
     cudaError_t init();
     void release();
     // device buffer of at least `bytes` (contents undefined); nullptr on failure
     void *get(const std::string &name, size_t bytes);
+    // bytes held by buffer `name` (0 if it does not exist)
+    size_t capacity(const std::string &name) const;
     size_t footprint() const;
 };
 
@@ -74,7 +78,7 @@ constexpr int kScalars = 64;  // device scalar slots per workspace
 // scalar slot indices
 enum : int {
     SC_DMAX = 0, SC_NNZ = 1, SC_COUNT0 = 2, SC_VIOL = 3, SC_ONES = 4, SC_GUARD = 5,
-    SC_DMAX2 = 6, SC_NNZ2 = 7, SC_COUNT2 = 8, SC_CQ = 9, SC_CS = 10, SC_OPEN = 11, SC_STEP0 = 16
+    SC_DMAX2 = 6, SC_NNZ2 = 7, SC_COUNT2 = 8, SC_CQ = 9, SC_CS = 10, SC_OPEN = 11, SC_GATE = 12, SC_STEP0 = 16
 };
 
 struct SolveArgs {

@@ -68,8 +68,17 @@ __global__ void __launch_bounds__(256, 4)
         if (colmask_s[w] != 0ull) atomicOr(reinterpret_cast<unsigned long long *>(colmask + w), colmask_s[w]);
 }
 
+// Column indices from the packed bits.  Guarded form (cap >= 0): every thread first reads the
+// number of facts and ||E||_inf; if the facts do not fit cap entries or a row has more than
+// max_deg successors nothing is written and *gate = 1 (a later step re-plans on the host).
 __global__ void __launch_bounds__(256)
-    csr_fill_bits_kernel(const uint64_t *__restrict__ M, int n, int wp, const int *__restrict__ ptr, int *col) {
+    csr_fill_bits_kernel(const uint64_t *__restrict__ M, int n, int wp, const int *__restrict__ ptr, int *col,
+                         int64_t cap, const unsigned long long *dmax, int max_deg, int *gate) {
+    if (cap >= 0) {
+        const bool stop = ptr[n] > cap || *dmax > static_cast<unsigned long long>(max_deg);
+        if (blockIdx.x == 0 && threadIdx.x == 0) *gate = stop ? 1 : 0;
+        if (stop) return;
+    }
     const int lane = threadIdx.x & 31;
     const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
     if (r >= n) return;
@@ -218,7 +227,15 @@ cudaError_t pack_bits(const uint8_t *E, int n, int np, int64_t wp, uint64_t *M, 
 }
 
 cudaError_t csr_fill_from_bits(const uint64_t *M, int n, int64_t wp, const int *ptr, int *col, cudaStream_t s) {
-    csr_fill_bits_kernel<<<static_cast<unsigned>((n + 7) / 8), 256, 0, s>>>(M, n, static_cast<int>(wp), ptr, col);
+    csr_fill_bits_kernel<<<static_cast<unsigned>((n + 7) / 8), 256, 0, s>>>(M, n, static_cast<int>(wp), ptr, col, -1,
+                                                                           nullptr, 0, nullptr);
+    return cudaGetLastError();
+}
+
+cudaError_t csr_fill_from_bits_guarded(const uint64_t *M, int n, int64_t wp, const int *ptr, int *col, int64_t cap,
+                                       const unsigned long long *dmax, int max_deg, int *gate, cudaStream_t s) {
+    csr_fill_bits_kernel<<<static_cast<unsigned>((n + 7) / 8), 256, 0, s>>>(M, n, static_cast<int>(wp), ptr, col, cap,
+                                                                           dmax, max_deg, gate);
     return cudaGetLastError();
 }
 

@@ -115,10 +115,12 @@ cudaError_t sweep_units(const int *ptr, int n, int *cnt, int *unit_off, cudaStre
 // colmask (optional): the columns with an incoming edge.  Every row of E M lies inside it and
 // every row of the reflexive closure inside it plus the row's own bit, so a row-direct sweep
 // stops reading successors once a row covers that much (without it: all n columns).
+// gate (row-direct only): when *gate != 0 on the device the launch does nothing.
 cudaError_t bits_sweep_csr(const int *ptr, const int *col, const int *unit_off, int n, const uint64_t *M,
                            uint64_t *out, int64_t wp, int mode, unsigned long long *violations,
                            unsigned long long *ones, int *launches, cudaStream_t s, int max_deg,
-                           const unsigned long long *skip_if_zero = nullptr, const uint64_t *colmask = nullptr);
+                           const unsigned long long *skip_if_zero = nullptr, const uint64_t *colmask = nullptr,
+                           const int *gate = nullptr);
 // Whether bits_sweep_csr takes the row-direct kernels (then unit_off is not read).
 bool row_direct(int max_deg, int64_t wp);
 // Rows i < n of the reflexive closure by the Iteration on single rows (one warp per row,
@@ -126,8 +128,10 @@ bool row_direct(int max_deg, int64_t wp);
 // reached; a row whose frontier outgrows 256 nodes keeps what it reached (a subset of its
 // closure row) and counts in *open_rows.  Rows of at most 256 words (n <= 16384).
 bool row_iteration_fits(int64_t wp);
+// With gate: decided on the device; nothing but *open_rows += n if *gate != 0 or the graph
+// has more than two facts per row.
 cudaError_t row_iteration(const int *ptr, const int *col, int n, int64_t wp, uint64_t *M,
-                          unsigned long long *open_rows, cudaStream_t s);
+                          unsigned long long *open_rows, cudaStream_t s, const int *gate = nullptr);
 // Bit-matrix helpers for same generation (np x np bits, wp = np / 64 words per row).
 // dst = src^T (np a multiple of 64; dst distinct from src); nothing if *skip == 0.
 cudaError_t bits_transpose(const uint64_t *src, uint64_t *dst, int np, int64_t wp, const unsigned long long *skip,
@@ -171,6 +175,10 @@ cudaError_t csr_pack_checked(const uint8_t *E, int n, int np, int64_t wp, int *c
 cudaError_t pack_bits(const uint8_t *E, int n, int np, int64_t wp, uint64_t *M, int *status, cudaStream_t s);
 // Column indices of E from the packed bits of I + E (as written by csr_pack_checked).
 cudaError_t csr_fill_from_bits(const uint64_t *M, int n, int64_t wp, const int *ptr, int *col, cudaStream_t s);
+// The same before the host knows the CSR's size: if the facts exceed cap entries or *dmax
+// exceeds max_deg, nothing is written and *gate = 1, else *gate = 0.
+cudaError_t csr_fill_from_bits_guarded(const uint64_t *M, int n, int64_t wp, const int *ptr, int *col, int64_t cap,
+                                       const unsigned long long *dmax, int max_deg, int *gate, cudaStream_t s);
 // out[0..n] = exclusive prefix sums of cnt[0..n-1] (out[n] = total); one CTA.
 cudaError_t exclusive_scan(const int *cnt, int n, int *out, cudaStream_t s);
 // The same with every SM taking part, for long arrays (scratch: 2 * (ceil(n / 1024) + 1) ints).

@@ -397,30 +397,110 @@ dl_status tc_auto(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &a
     CK(csr_pack_checked(E, n, static_cast<int>(np), wp, cnt, ptr, rbits, ws.scal + SC_DMAX, ws.scal + SC_NNZ,
                         ws.scal + SC_COUNT0, ws.status, colmask, s));
     launches += 2;
-    if ((rc = read_scalars(ws, s))) return rc;
-    if ((rc = check_status(ws, s))) return rc;
-    const unsigned long long dmax = host_scal(ws)[SC_DMAX];
-    double eps = 0;
-    if ((rc = choose_eps(a.eps, 1.0 / (1.0 + static_cast<double>(dmax)), "Lemma 1 (1/(1+||E||))", &eps)))
-        return rc;
-    const int64_t nnz = static_cast<int64_t>(host_scal(ws)[SC_NNZ]);
-    // ones of C_0 = I + E over the padded size: the diagonal plus the facts off it
-    unsigned long long prev = static_cast<unsigned long long>(np) + host_scal(ws)[SC_NNZ] - host_scal(ws)[SC_COUNT0];
-    auto *col = static_cast<int *>(ws.get("g_col", static_cast<size_t>(std::max<int64_t>(nnz, 1)) * 4));
-    NEED(col);
-    CK(csr_fill_from_bits(rbits, n, wp, ptr, col, s));
-    ++launches;
-    if (!row_direct(static_cast<int>(dmax), wp)) {  // heavy rows: edge-parallel work units
-        CK(sweep_units(ptr, n, cnt, uoff, s));
-        launches += 2;
-    }
-    tm.mark(1);
 
+    SweepClock sc{ws, s};
+    unsigned long long *vslot = ws.scal + 32;  // up to 16 violation counters, one per sweep
+    constexpr int kFirstGroup = 8;
     // cost model (seconds): one squaring vs one sweep before rows saturate.  A sweep reads a
     // successor's row per fact; the bit matrix is L2-resident up to a few tens of MB.
     const double bit_bytes = static_cast<double>(np) * wp * 8;
     const double sweep_rate = bit_bytes <= 48e6 ? 6.0e12 : 3.0e12;
     const double t_sq = 2.0 * np * np * np / 3.4e15 + 15e-6;
+    const double t_sw_min = 2.0 * bit_bytes / sweep_rate + 5e-6;  // a sweep with no facts
+    // the speculative group never exceeds the sweeps a squaring is worth with no facts at all,
+    // and is empty when the last closure here was settled by the single-row Iteration alone
+    const int spec_group =
+        ws.last_rows_closed
+            ? 0
+            : static_cast<int>(std::max(4.0, std::min<double>(kFirstGroup, std::floor(t_sq / t_sw_min))));
+    // the model E M, checking M = min1(I + E M) on the way (straight into a device output whose
+    // rows have the same stride)
+    const bool direct = a.mem == DL_MEM_DEVICE && (n + 63) / 64 == wp;
+    uint64_t *model = direct ? a.out_bits : mbits;
+    int *gate = reinterpret_cast<int *>(ws.scal + SC_GATE);
+    int *col = nullptr;
+    unsigned long long dmax = 0;
+    auto emit = [&](const int *g) -> dl_status {
+        CK(cudaMemsetAsync(ws.scal + SC_VIOL, 0, 2 * sizeof(unsigned long long), s));
+        sc.start();
+        CK(bits_sweep_csr(ptr, col, uoff, n, rbits, model, wp, 0, ws.scal + SC_VIOL, ws.scal + SC_ONES, &launches, s,
+                          g ? 0 : static_cast<int>(dmax), nullptr, colmask, g));
+        sc.stop();
+        return DL_OK;
+    };
+
+    // Speculative start (rows of at most 256 words): the first steps run before the host knows
+    // the CSR's size or ||E||_inf, so that a closure settled in them costs one host read.  The
+    // CSR fill uses the column array as it is and, if the facts do not fit or a row has more
+    // than 256 successors, writes nothing and sets the gate; every launch after it reads the
+    // gate and does nothing then.  The single-row Iteration decides on the device whether the
+    // graph is sparse enough; its open-row count lets the sweeps skip when it closed every row.
+    // (not when the last closure on this workspace had heavy rows: they would stop it again)
+    bool spec = row_direct(0, wp) && !ws.last_heavy, converged = false, emitted = false, iterated = false;
+    int spec_sweeps = 0;
+    if (spec) {
+        const size_t want = std::max(ws.capacity("g_col"), static_cast<size_t>(np) * 8 * sizeof(int));
+        col = static_cast<int *>(ws.get("g_col", want));
+        NEED(col);
+        const int64_t cap = static_cast<int64_t>(ws.capacity("g_col") / sizeof(int));
+        CK(csr_fill_from_bits_guarded(rbits, n, wp, ptr, col, cap, ws.scal + SC_DMAX, 256, gate, s));
+        ++launches;
+        iterated = row_iteration_fits(wp);
+        if (iterated) {
+            CK(row_iteration(ptr, col, n, wp, rbits, ws.scal + SC_OPEN, s, gate));
+            ++launches;
+        }
+        sc.start();
+        for (int k = 0; k < spec_group; ++k) {
+            const unsigned long long *skip = k > 0 ? vslot + k - 1 : (iterated ? ws.scal + SC_OPEN : nullptr);
+            CK(bits_sweep_csr(ptr, col, uoff, n, rbits, rbits, wp, 1, vslot + k, nullptr, &launches, s, 0, skip,
+                              colmask, gate));
+        }
+        sc.stop();
+        if ((rc = emit(gate))) return rc;
+    }
+    if ((rc = read_scalars(ws, s))) return rc;
+    if ((rc = check_status(ws, s))) return rc;
+    dmax = host_scal(ws)[SC_DMAX];
+    ws.last_heavy = dmax > 256;
+    double eps = 0;
+    if ((rc = choose_eps(a.eps, 1.0 / (1.0 + static_cast<double>(dmax)), "Lemma 1 (1/(1+||E||))", &eps)))
+        return rc;
+    const int64_t nnz = static_cast<int64_t>(host_scal(ws)[SC_NNZ]);
+    // bytes a sweep reads at least: the CSR of E and every row of the bit matrix once
+    const double sweep_min_bytes = 4.0 * (static_cast<double>(nnz) + n + 1) + static_cast<double>(n) * wp * 8.0;
+    if (spec && *reinterpret_cast<const int *>(host_scal(ws) + SC_GATE) != 0) spec = false;  // nothing ran
+    ws.last_rows_closed = false;
+    if (spec) {
+        if (iterated && host_scal(ws)[SC_OPEN] == 0) {
+            converged = true;  // every row closed by the single-row Iteration (the sweeps skipped)
+            ws.last_rows_closed = true;
+        } else if (spec_group > 0) {
+            spec_sweeps = spec_group;
+            for (int k = 0; k < spec_group; ++k)
+                if (host_scal(ws)[32 + k] == 0) {
+                    converged = true;
+                    spec_sweeps = k + 1;
+                    break;
+                }
+        }
+        sc.account(spec_sweeps + 1, sweep_min_bytes);
+        emitted = converged;
+    } else {
+        // planned on the host: the column array sized to the facts, work units for heavy rows
+        col = static_cast<int *>(ws.get("g_col", static_cast<size_t>(std::max<int64_t>(nnz, 1)) * 4));
+        NEED(col);
+        CK(csr_fill_from_bits(rbits, n, wp, ptr, col, s));
+        ++launches;
+        if (!row_direct(static_cast<int>(dmax), wp)) {  // heavy rows: edge-parallel work units
+            CK(sweep_units(ptr, n, cnt, uoff, s));
+            launches += 2;
+        }
+    }
+    tm.mark(1);
+    // ones of C_0 = I + E over the padded size: the diagonal plus the facts off it
+    unsigned long long prev = static_cast<unsigned long long>(np) + host_scal(ws)[SC_NNZ] - host_scal(ws)[SC_COUNT0];
+
     const double t_sw = (static_cast<double>(nnz) * wp * 8 + 2.0 * bit_bytes) / sweep_rate + 5e-6;
     // square first only when one unsaturated sweep costs more than a squaring (rows saturate
     // within a sweep or two on dense graphs, so later sweeps are cheap)
@@ -428,58 +508,47 @@ dl_status tc_auto(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &a
     // sweeps allowed between two squarings before a squaring is the cheaper way forward
     const int sweep_budget = static_cast<int>(std::max(4.0, std::floor(t_sq / t_sw)));
 
-    GemmProblem probs[2];
-    std::string err;
-    const int bn = bool_bn(np);
-    for (int p = 0; p < 2; ++p) {
-        if (!gemm_make_problem(&probs[p], KIND_F8, false, bn, static_cast<int>(np), static_cast<int>(np),
-                               static_cast<int>(np), square_op(C[p], np), square_op(C[p], np),
-                               bool_epi(C[1 - p], np, rbits, wp, ws.scal + SC_STEP0, nullptr), &err)) {
-            set_error("%s", err.c_str());
-            return DL_EDEVICE;
-        }
-    }
-    GemmProblem *dprobs = nullptr;
-    if ((rc = upload_problems(ws, s, probs, 2, &dprobs))) return rc;
-    const int tiles = probs[0].tiles_m * probs[0].tiles_n;
-    const int grid = std::min(tiles, ctx->sms);
     GemmClock gc{ws, s};
-    SweepClock sc{ws, s};
-    // bytes a sweep reads at least: the CSR of E and every row of the bit matrix once
-    const double sweep_min_bytes = 4.0 * (static_cast<double>(nnz) + n + 1) + static_cast<double>(n) * wp * 8.0;
     const int max_squarings = 2 + static_cast<int>(std::ceil(std::log2(static_cast<double>(np) + 1.0)));
     const int max_sweeps = static_cast<int>(std::min<int64_t>(2 * static_cast<int64_t>(n) + 16, 1 << 20));
-    int cur = 0, squarings = 0, sweeps = 0;
+    int cur = 0, squarings = 0, sweeps = spec_sweeps;
     bool c_valid = false;  // C[cur] holds the same matrix as rbits
-    bool converged = false, do_square = dense;
-    int since_square = 0;  // sweeps since the last squaring
-    unsigned long long *vslot = ws.scal + 32;  // up to 16 violation counters, one per sweep
-    // the model E M, checking M = min1(I + E M) on the way (straight into a device output whose
-    // rows have the same stride)
-    const bool direct = a.mem == DL_MEM_DEVICE && (n + 63) / 64 == wp;
-    uint64_t *model = direct ? a.out_bits : mbits;
-    auto emit = [&]() -> dl_status {
-        CK(cudaMemsetAsync(ws.scal + SC_VIOL, 0, 2 * sizeof(unsigned long long), s));
-        sc.start();
-        CK(bits_sweep_csr(ptr, col, uoff, n, rbits, model, wp, 0, ws.scal + SC_VIOL, ws.scal + SC_ONES, &launches, s,
-                          static_cast<int>(dmax), nullptr, colmask));
-        sc.stop(1, sweep_min_bytes);
-        return DL_OK;
+    bool do_square = spec ? (!converged && sweeps >= sweep_budget) : dense;
+    int since_square = sweeps;  // sweeps since the last squaring
+    GemmProblem *dprobs = nullptr;
+    int tiles = 0, grid = 0;
+    const int bn = bool_bn(np);
+    auto gemm_setup = [&]() -> dl_status {  // the two squaring problems, uploaded on first use
+        if (dprobs) return DL_OK;
+        GemmProblem probs[2];
+        std::string err;
+        for (int p = 0; p < 2; ++p) {
+            if (!gemm_make_problem(&probs[p], KIND_F8, false, bn, static_cast<int>(np), static_cast<int>(np),
+                                   static_cast<int>(np), square_op(C[p], np), square_op(C[p], np),
+                                   bool_epi(C[1 - p], np, rbits, wp, ws.scal + SC_STEP0, nullptr), &err)) {
+                set_error("%s", err.c_str());
+                return DL_EDEVICE;
+            }
+        }
+        dl_status r = upload_problems(ws, s, probs, 2, &dprobs);
+        tiles = probs[0].tiles_m * probs[0].tiles_n;
+        grid = std::min(tiles, ctx->sms);
+        return r;
     };
-    bool emitted = false;
-    // sparse graphs (at most two facts per row on average, no heavy rows): the Iteration on
-    // single rows closes every row whose reachable set stays small in one launch; the rows it
-    // leaves open keep what they reached and the sweeps below finish them
-    if (!dense && nnz <= 2 * static_cast<int64_t>(n) && row_iteration_fits(wp) &&
+    // sparse graphs planned on the host (at most two facts per row on average, no heavy rows):
+    // the Iteration on single rows closes every row whose reachable set stays small in one
+    // launch; the rows it leaves open keep what they reached and the sweeps below finish them
+    if (!spec && !dense && nnz <= 2 * static_cast<int64_t>(n) && row_iteration_fits(wp) &&
         row_direct(static_cast<int>(dmax), wp)) {
         CK(cudaMemsetAsync(ws.scal + SC_OPEN, 0, sizeof(unsigned long long), s));
         sc.start();
         CK(row_iteration(ptr, col, n, wp, rbits, ws.scal + SC_OPEN, s));
         sc.stop();
         ++launches;
-        if ((rc = emit())) return rc;
+        if ((rc = emit(nullptr))) return rc;
+        sc.account(1, sweep_min_bytes);
         if ((rc = read_scalars(ws, s))) return rc;
-        if (host_scal(ws)[SC_OPEN] == 0) converged = emitted = true;
+        if (host_scal(ws)[SC_OPEN] == 0) converged = emitted = ws.last_rows_closed = true;
     }
     while (!converged) {
         if (do_square) {
@@ -487,6 +556,7 @@ dl_status tc_auto(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &a
                 set_error("closure did not converge in %d squarings", squarings);
                 return DL_ENOTCONV;
             }
+            if ((rc = gemm_setup())) return rc;
             if (!c_valid) {
                 CK(bits_to_e4m3(rbits, wp, static_cast<int>(np), C[cur], s));
                 ++launches;
@@ -512,14 +582,14 @@ dl_status tc_auto(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &a
         // a group of in-place sweeps and, speculatively, the model (final if the group reached
         // the fixpoint), then one host read for all of it (after a squaring the rows are dense
         // and saturate within a few successors, so a short group is cheap)
-        const int g = std::max(1, std::min(squarings == 0 ? 8 : 4, sweep_budget - since_square));
+        const int g = std::max(1, std::min(squarings == 0 ? kFirstGroup : 4, sweep_budget - since_square));
         CK(cudaMemsetAsync(vslot, 0, sizeof(unsigned long long) * g, s));
         sc.start();
         for (int k = 0; k < g; ++k)  // a sweep after one that changed nothing exits on the device
             CK(bits_sweep_csr(ptr, col, uoff, n, rbits, rbits, wp, 1, vslot + k, nullptr, &launches, s,
                               static_cast<int>(dmax), k > 0 ? vslot + k - 1 : nullptr, colmask));
         sc.stop();
-        if ((rc = emit())) return rc;
+        if ((rc = emit(nullptr))) return rc;
         if ((rc = read_scalars(ws, s))) return rc;
         int ran = g;
         for (int k = 0; k < g; ++k)
@@ -528,7 +598,7 @@ dl_status tc_auto(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &a
                 ran = k + 1;
                 break;
             }
-        sc.account(ran, sweep_min_bytes);
+        sc.account(ran + 1, sweep_min_bytes);
         sweeps += ran;
         since_square += g;
         emitted = converged;
@@ -543,7 +613,8 @@ dl_status tc_auto(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &a
     }
     tm.mark(2);
     if (!emitted) {  // converged by a squaring
-        if ((rc = emit())) return rc;
+        if ((rc = emit(nullptr))) return rc;
+        sc.account(1, sweep_min_bytes);
         if ((rc = read_scalars(ws, s))) return rc;
     }
     if (host_scal(ws)[SC_VIOL] != 0) {
@@ -1122,6 +1193,11 @@ void *Workspace::get(const std::string &name, size_t bytes) {
     }
     b.bytes = want;
     return b.p;
+}
+
+size_t Workspace::capacity(const std::string &name) const {
+    const auto it = bufs.find(name);
+    return it == bufs.end() ? 0 : it->second.bytes;
 }
 
 size_t Workspace::footprint() const {
