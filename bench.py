@@ -42,7 +42,7 @@ UNIT = "TFLOP/s-equiv"
 TRAFFIC = {
     "gemm": {"sources": {"dl_umma.cu": "a0ca42a48c46c344", "dl_ptx.cuh": "b4fd45714c88d2fc"},
              "bytes_per_launch": 444.5e6},   # ncu: DRAM read + write of one N = 8192 squaring
-    "sweep": {"sources": {"dl_bool.cu": "108ab3ac553b3493"},
+    "sweep": {"sources": {"dl_bool.cu": "22991da2571fe8a0"},
               "bytes_per_launch": 8.70e6},    # ncu: one working sweep, p = 1e-3, cold L2
 }
 
@@ -282,6 +282,16 @@ def run_part(args, device: int) -> None:
     torch.cuda.set_device(device)
     if args.part == "serving":
         out = bench_serving(dl, torch, device, args.serve_seconds)
+    elif args.part == "mixed":
+        out = {}
+        with dl.Context(device) as ctx:
+            for name, e in zip(("p=1e-4", "p=1e-3", "p=1e-2"), graphs(0)):
+                x = torch.from_numpy(e).cuda()
+                ctx.tc_closure(x, path="mixed")  # warm
+                _, stm = ctx.tc_closure(x, path="mixed")
+                out[name] = {"ms": stm["ms_total"], "ms_factor": stm["ms_factor"], "ms_solve": stm["ms_solve"],
+                             "ms_refine": stm["ms_refine"], "refine_steps": stm["iters"],
+                             "final_resid": stm["final_resid"]}
     else:
         with dl.Context(device) as ctx:
             out = bench_sg(ctx, torch) if args.part == "sg" else bench_batch(ctx, torch, reps=max(1, args.steps))
@@ -304,7 +314,7 @@ def main() -> None:
                     help="skip the same-generation, batch and serving measurements")
     ap.add_argument("--serve-seconds", type=float, default=10.0,
                     help="length of the serving stream (the full workload is 60 s)")
-    ap.add_argument("--part", default="all", choices=["all", "sg", "batch", "serving"],
+    ap.add_argument("--part", default="all", choices=["all", "sg", "batch", "serving", "mixed"],
                     help="run one secondary measurement alone and print its JSON (for profiling)")
     args = ap.parse_args()
     rank, world, local = dist_env()
