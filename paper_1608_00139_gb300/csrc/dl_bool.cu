@@ -354,20 +354,6 @@ __global__ void __launch_bounds__(256)
     }
 }
 
-// Bits of I + E (np rows of wp words; rows >= n hold only their diagonal bit); warp per row.
-__global__ void reflexive_bits_kernel(const int *__restrict__ ptr, const int *__restrict__ col, int n, int np,
-                                      int64_t wp, uint64_t *bits) {
-    const int lane = threadIdx.x & 31;
-    const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (i >= np) return;
-    uint64_t *row = bits + static_cast<int64_t>(i) * wp;
-    for (int64_t w = lane; w < wp; w += 32) row[w] = (w == (i >> 6)) ? (1ull << (i & 63)) : 0ull;
-    __syncwarp();
-    if (i < n)
-        for (int q = ptr[i] + lane; q < ptr[i + 1]; q += 32)
-            atomicOr(reinterpret_cast<unsigned long long *>(row + (col[q] >> 6)), 1ull << (col[q] & 63));
-}
-
 // e4m3 0/1 matrix (np x np, 0x38 = 1) from bits; one thread per 64-column word.
 __global__ void bits_to_e4m3_kernel(const uint64_t *__restrict__ bits, int64_t wp, int np, uint8_t *__restrict__ C) {
     const int64_t t = static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x;
@@ -562,12 +548,6 @@ cudaError_t bits_sweep_csr(const int *ptr, const int *col, const int *unit_off, 
     sweep_units_or_kernel<<<grid, 256, 0, s>>>(ptr, col, unit_off, n, M, out, wp);
     sweep_check_kernel<<<(n + 7) / 8, 256, 0, s>>>(n, M, out, wp, violations, ones);
     if (launches) *launches += 2;
-    return cudaGetLastError();
-}
-
-cudaError_t reflexive_bits(const int *ptr, const int *col, int n, int np, int64_t wp, uint64_t *bits,
-                           cudaStream_t s) {
-    reflexive_bits_kernel<<<(np + 7) / 8, 256, 0, s>>>(ptr, col, n, np, wp, bits);
     return cudaGetLastError();
 }
 

@@ -149,9 +149,6 @@ cudaError_t bits_count(const uint64_t *M, int n, int64_t wp, unsigned long long 
 cudaError_t bits_identity(uint64_t *M, int n, int np, int64_t wp, cudaStream_t s);
 // *diff += words where A and B differ.
 cudaError_t bits_diff(const uint64_t *A, const uint64_t *B, int64_t words, unsigned long long *diff, cudaStream_t s);
-// Bits of I + E (np rows x wp words) from the CSR of E.
-cudaError_t reflexive_bits(const int *ptr, const int *col, int n, int np, int64_t wp, uint64_t *bits,
-                           cudaStream_t s);
 // e4m3 0/1 operand (np x np, 1.0 = 0x38) from a bit matrix.
 cudaError_t bits_to_e4m3(const uint64_t *bits, int64_t wp, int np, uint8_t *C, cudaStream_t s);
 

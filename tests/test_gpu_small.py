@@ -330,3 +330,21 @@ def test_sg_deep_derivations_fall_back_to_doubling(ctx):
     bits, st = ctx.sg_least_model(p, path="auto")
     assert np.array_equal(bits, oracle.sg_model(p))
     assert st["path_used"] == dl.PATHS["bool_fp8"]
+
+
+def test_auto_speculative_start_fallbacks():
+    """The AUTO closure's first steps run before the host knows the number of facts or the
+    longest row.  On a fresh context: a dense graph overflows the column array (the host then
+    re-plans), the same graph again fits; a graph with rows of hundreds of successors stops the
+    speculative launches (heavy rows), the next graph then starts without speculating; a sparse
+    graph closed by the single-row Iteration is followed by one it cannot close.  Every model
+    must equal the oracle's."""
+    with dl.Context(0) as c:
+        graphs = [inputs.er_digraph(1500, 0.02, 31), inputs.er_digraph(1500, 0.02, 31),
+                  inputs.pa_dag(1500, 32), inputs.er_digraph(1500, 0.004, 33),
+                  inputs.er_digraph(1500, 0.0005, 34), inputs.er_digraph(1500, 0.003, 35),
+                  inputs.pa_dag(900, 36) | inputs.pa_dag(900, 36).T]
+        assert oracle.max_row_sum(graphs[2]) > 256
+        for e in graphs:
+            bits, st = c.tc_closure(e, path="auto")
+            assert np.array_equal(bits, oracle.tc_model(e))
