@@ -42,7 +42,7 @@ UNIT = "TFLOP/s-equiv"
 TRAFFIC = {
     "gemm": {"sources": {"dl_umma.cu": "a0ca42a48c46c344", "dl_ptx.cuh": "b4fd45714c88d2fc"},
              "bytes_per_launch": 444.5e6},   # ncu: DRAM read + write of one N = 8192 squaring
-    "sweep": {"sources": {"dl_bool.cu": "22991da2571fe8a0"},
+    "sweep": {"sources": {"dl_bool.cu": "bd4d428fec85b53d"},
               "bytes_per_launch": 8.70e6},    # ncu: one working sweep, p = 1e-3, cold L2
 }
 
