@@ -138,6 +138,95 @@ __global__ void __launch_bounds__(256)
     for (int w = threadIdx.x; w < I.wp; w += blockDim.x) I.colmask[w] = cm_s[w];
 }
 
+// Instances whose whole bit matrix fits in shared memory (at most kSmallNp padded rows of at
+// most 16 words: 128 KB) are closed by one CTA each, before the batched machinery: in-place
+// sweeps M_i |= E_i | OR_{s in succ(i)} M_s on the shared copy (rows of an instance share a
+// warp in lane groups sized to the row) until one changes nothing (__syncthreads_or over the
+// CTA), then the model E M with its certificate straight to the output.  An instance still
+// changing after kSmallSweeps sweeps writes its bits back and stays active for the batched
+// sweeps and squarings.
+constexpr int kSmallNp = 1024;
+constexpr int kSmallThreads = 1024;
+constexpr int kSmallSweeps = 64;
+
+__global__ void __launch_bounds__(kSmallThreads)
+    batch_small_kernel(const BatchInst *__restrict__ inst, const int *__restrict__ small_ids,
+                       const int *__restrict__ ptr, const int *__restrict__ col, BatchCounters c, int *status) {
+    extern __shared__ uint64_t small_s[];
+    __shared__ unsigned int ones_s;
+    const int k = small_ids[blockIdx.x];
+    const BatchInst I = inst[k];
+    const int wp = I.wp, n = I.n;
+    uint64_t *Ms = small_s;  // np x wp
+    for (int t = threadIdx.x; t < I.np * wp; t += blockDim.x) Ms[t] = I.rbits[t];
+    if (threadIdx.x == 0) ones_s = 0u;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+    int G = 32;
+    while (G > 1 && (G >> 1) >= wp) G >>= 1;
+    const int R = 32 / G, grp = lane / G, w = lane % G;
+    const bool wv = w < wp;
+    const uint64_t cm = wv ? I.colmask[w] : 0ull;
+    const int *iptr = ptr + I.row0;  // iptr[r]: local row r
+    __syncthreads();
+    int it = 0;
+    bool conv = false;
+    while (it < kSmallSweeps) {
+        bool ch = false;
+        for (int r = warp * R + grp; r < n; r += nwarps * R) {
+            if (!wv) continue;
+            uint64_t acc = Ms[r * wp + w];
+            const uint64_t before = acc;
+            const uint64_t full = cm | (w == (r >> 6) ? 1ull << (r & 63) : 0ull);
+            for (int q = iptr[r]; q < iptr[r + 1] && acc != full; ++q) {
+                const int sidx = col[q];
+                acc |= Ms[sidx * wp + w] | (w == (sidx >> 6) ? 1ull << (sidx & 63) : 0ull);
+            }
+            if (acc != before) {
+                Ms[r * wp + w] = acc;
+                ch = true;
+            }
+        }
+        ++it;
+        if (!__syncthreads_or(ch)) {
+            conv = true;
+            break;
+        }
+    }
+    if (!conv) {  // hand over: the batched machinery continues from these bits
+        for (int t = threadIdx.x; t < I.np * wp; t += blockDim.x) I.rbits[t] = Ms[t];
+        if (threadIdx.x == 0) c.sweeps[k] = it;
+        return;
+    }
+    // the model E M and the certificate (out_r | e_r) = M_r
+    const int wout = (n + 63) >> 6;
+    bool viol = false;
+    unsigned int ones = 0;
+    for (int r = warp * R + grp; r < n; r += nwarps * R) {
+        if (!wv) continue;
+        uint64_t out = 0ull;
+        for (int q = iptr[r]; q < iptr[r + 1] && out != cm; ++q) out |= Ms[col[q] * wp + w];
+        const uint64_t self = w == (r >> 6) ? 1ull << (r & 63) : 0ull;
+        viol |= (out | self) != Ms[r * wp + w];
+        ones += __popcll(out);
+        if (I.out) {
+            if (w < wout) I.out[static_cast<int64_t>(r) * wout + w] = out;
+        } else {
+            I.mbits[static_cast<int64_t>(r) * wp + w] = out;
+        }
+    }
+    if (ones) atomicAdd(&ones_s, ones);
+    const int any_viol = __syncthreads_or(viol);
+    if (threadIdx.x == 0) {
+        c.sweeps[k] = it;
+        c.ones[k] = ones_s;
+        c.state[k] = B_DONE;
+        if (any_viol) {  // a converged closure that fails its certificate: an internal error
+            c.viol[k] = 1;
+            atomicOr(status, ST_TIMEOUT_DEP);
+        }
+    }
+}
+
 // Block-wide exclusive scan of four counters at once (kListThreads threads).
 __device__ __forceinline__ int4 block_scan4(int4 v, int4 *total) {
     __shared__ int4 part[kListThreads / 32];
@@ -231,13 +320,17 @@ __global__ void __launch_bounds__(256)
     const int nrows = list.hdr[1];
     const int entries = list.hdr[0];
     if (nrows == 0) return;
+    // rows per claim: kChunk while there are plenty, fewer as the active rows thin out (every
+    // warp of the grid should have rows to work on)
+    const int warps = gridDim.x * (blockDim.x >> 5);
+    const int per = max(1, min(kChunk, nrows / warps));
     for (;;) {
         int chunk = 0;
         if (lane == 0) chunk = atomicAdd(list.hdr + 4, 1);
         chunk = __shfl_sync(kFull, chunk, 0);
-        int r = chunk * kChunk;
+        int r = chunk * per;
         if (r >= nrows) return;
-        const int rend = min(nrows, r + kChunk);
+        const int rend = min(nrows, r + per);
         int j = last_le(list.row, entries, r);
         while (r < rend) {
             const int k = list.k[j];
@@ -580,6 +673,25 @@ dl_status solve_tc_batch(dl_ctx *ctx, Workspace &ws, cudaStream_t s, int32_t cou
         // pageable source: the copy has read `probs` when cudaMemcpyAsync returns
         BCK(cudaMemcpyAsync(dprob, probs.data(), sizeof(GemmProblem) * L, cudaMemcpyHostToDevice, s));
         BCK(gemm_prepare(KIND_F8, false, bn, EPI_BOOL));
+        // instances closed in shared memory by one CTA each
+        std::vector<int> small;
+        size_t small_smem = 0;
+        for (int i = 0; i < L; ++i)
+            if (inst[i].np <= kSmallNp) {
+                small.push_back(i);
+                small_smem = std::max(small_smem, static_cast<size_t>(inst[i].np) * inst[i].wp * 8);
+            }
+        int *dsmall = nullptr;
+        if (!small.empty()) {
+            dsmall = static_cast<int *>(ws.get("batch_small", sizeof(int) * small.size()));
+            if (!dsmall) {
+                set_error("batch: device allocation failed (small-instance list)");
+                return DL_ENOMEM;
+            }
+            BCK(cudaMemcpyAsync(dsmall, small.data(), sizeof(int) * small.size(), cudaMemcpyHostToDevice, s));
+            BCK(cudaFuncSetAttribute(batch_small_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     static_cast<int>(small_smem)));
+        }
         const int rounds = 1 + static_cast<int>(std::ceil(std::log2(static_cast<double>(max_np) + 1.0)));
         const int ggrid = static_cast<int>(std::min<int64_t>(tiles, ctx->sms));
         const int rgrid = ctx->sms * 8;  // row kernels: 8 CTAs of 8 warps per SM, rows claimed in chunks
@@ -638,6 +750,11 @@ dl_status solve_tc_batch(dl_ctx *ctx, Workspace &ws, cudaStream_t s, int32_t cou
                 if (e == cudaSuccess) e = cudaMemsetAsync(ctr, 0, kCounterArrays * sizeof(unsigned long long) * L, s);
                 batch_fill_kernel<<<prow_grid, 256, 0, s>>>(dinst, pinst, static_cast<int>(total_prows), gptr, gcol);
                 batch_colmask_kernel<<<L, 256, static_cast<size_t>(max_wp) * 8, s>>>(dinst, gptr, gcol);
+                if (!small.empty()) {
+                    batch_small_kernel<<<static_cast<unsigned>(small.size()), kSmallThreads, small_smem, s>>>(
+                        dinst, dsmall, gptr, gcol, bc, ws.status);
+                    ++launches;
+                }
                 batch_list_kernel<<<1, kListThreads, 0, s>>>(dinst, L, bc, bl, B_ACTIVE, 0);
                 launches += 3;
                 for (int k = 0; k < kFirstSweeps; ++k) sweep();
