@@ -80,9 +80,25 @@ def dist_env():
     return rank, world, local
 
 
+def graph_seeds(rank: int):
+    """(p, seed) of each model a rank solves: every rank its own seeded replica."""
+    return [(p, s + 1000 * rank) for p, s in zip(PS, SEEDS)]
+
+
 def graphs(rank: int):
     from paper_1608_00139_gb300 import inputs
-    return [inputs.er_digraph(N, p, s + 1000 * rank) for p, s in zip(PS, SEEDS)]
+    return [inputs.er_digraph(N, p, s) for p, s in graph_seeds(rank)]
+
+
+def max_over_ranks(values, world: int, device: str):
+    """Element-wise maximum of the ranks' values (the job's time is its slowest rank's)."""
+    if world <= 1:
+        return list(values)
+    import torch
+    import torch.distributed as tdist
+    t = torch.tensor(list(values), device=device, dtype=torch.float64)
+    tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
+    return [float(x) for x in t.tolist()]
 
 
 class ClockSampler:
@@ -403,10 +419,7 @@ def main() -> None:
     gemm_n = sum(st["gemm_launches"] for st in stats)
     squarings = [st["iters"] for st in stats]
     ms_step = ms_total / args.steps
-    if world > 1:
-        t = torch.tensor([ms_step, e2e_s], device="cuda", dtype=torch.float64)
-        tdist.all_reduce(t, op=tdist.ReduceOp.MAX)
-        ms_step, e2e_s = float(t[0]), float(t[1])
+    ms_step, e2e_s = max_over_ranks([ms_step, e2e_s], world, "cuda")
     units = world * len(gs)
     value = units * flops_equiv(N) / (ms_step * 1e-3) / 1e12
     e2e_value = units * flops_equiv(N) / e2e_s / 1e12
