@@ -7,8 +7,9 @@ paper's ER workload shape (Sec. 6.1).  Metric: TFLOP/s-equivalent = (8/3) N^3 pe
 
   python bench.py [--gpus N --steps K --warmup W] [--impl reference]
 
-`value`: inputs resident in HBM (three 64 MiB matrices, 192 MiB > the 129 MB L2, cycled
-each step), one C-ABI call per model on the FP8 tensor-core path.  `e2e`: the same through
+`value`: inputs resident in HBM (three 64 MiB matrices, 192 MiB > the 129 MB L2, each read in
+every step), one C-ABI call per model on the AUTO path (single-row Iteration, bit sweeps, FP8
+tensor-core squarings by cost), 3 x INFLIGHT closures in flight.  `e2e`: the same through
 host buffers (H2D of E and D2H of the model bits inside the timed region).  The plain FP64
 path (Proposition 1 in FP64) is timed beside it for the "vs plain FP64" comparison.
 `--impl reference` times the CPU oracle (semi-naive evaluation) on the host cores.
@@ -31,6 +32,7 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 N = 8192
+INFLIGHT = 2  # contexts per model in the headline step (closures in flight = 3 x INFLIGHT)
 PS = (1e-4, 1e-3, 1e-2)
 SEEDS = (2, 3, 4)
 METRIC = "TC least-model TFLOP/s-equiv (N=8192) vs plain FP64 path; served p50/p99 latency"
@@ -358,15 +360,20 @@ def main() -> None:
         t = torch.empty(e.shape, dtype=torch.uint8, pin_memory=True)
         t.numpy()[:] = e
         host.append(t.numpy())
+    # INFLIGHT contexts per model (one stream and host thread each): every context solves its
+    # model back to back, so 3 x INFLIGHT closures are in flight; a step is still one solve of
+    # each of the three models (the contexts of a model share its solves)
+    nctx = len(gs) * INFLIGHT
+    model_of = [i % len(gs) for i in range(nctx)]
+    for _ in range(nctx):
         o = torch.empty((N, (N + 63) // 64), dtype=torch.int64, pin_memory=True)
         host_out.append(o.numpy().view(np.uint64))
     # device outputs allocated once (a step writes every word of each)
-    dev_out = [torch.empty((N, (N + 63) // 64), dtype=torch.int64, device="cuda") for _ in gs]
+    dev_out = [torch.empty((N, (N + 63) // 64), dtype=torch.int64, device="cuda") for _ in range(nctx)]
     torch.cuda.synchronize()
-    # one context and one stream per model; three host threads keep the three in flight
-    streams = [torch.cuda.Stream() for _ in gs]
+    streams = [torch.cuda.Stream() for _ in range(nctx)]
     ctxs = [dl.Context(local, stream=st_) for st_ in streams]
-    pool = ThreadPoolExecutor(max_workers=len(gs))
+    pool = ThreadPoolExecutor(max_workers=nctx)
     main_stream = torch.cuda.current_stream()
 
     def outs_for(inputs):
@@ -374,12 +381,12 @@ def main() -> None:
 
     def step(inputs, path=args.path):
         outs = outs_for(inputs)
-        return list(pool.map(lambda i: ctxs[i].tc_closure(inputs[i], path=path, out=outs[i]),
-                             range(len(inputs))))
+        return list(pool.map(lambda i: ctxs[i].tc_closure(inputs[model_of[i]], path=path, out=outs[i]),
+                             range(nctx)))
 
     def timed(inputs, path, k):
-        """Device time of k steps: events fork/join the per-model streams; each host thread
-        drives its model's k solves back to back (a step is one solve of every model)."""
+        """Device time of k steps: events fork/join the contexts' streams; each host thread
+        drives its share of its model's k solves back to back."""
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         ends = [torch.cuda.Event() for _ in streams]
         outs = outs_for(inputs)
@@ -389,15 +396,16 @@ def main() -> None:
             st_.wait_event(ev0)
 
         def run(i):
-            return [ctxs[i].tc_closure(inputs[i], path=path, out=outs[i])[1] for _ in range(k)]
+            share = k // INFLIGHT + (1 if i // len(gs) < k % INFLIGHT else 0)
+            return [ctxs[i].tc_closure(inputs[model_of[i]], path=path, out=outs[i])[1] for _ in range(share)]
 
-        per_model = list(pool.map(run, range(len(inputs))))
+        per_ctx = list(pool.map(run, range(nctx)))
         for e_, st_ in zip(ends, streams):
             e_.record(st_)
             main_stream.wait_event(e_)
         ev1.record(main_stream)
         torch.cuda.synchronize()
-        return ev0.elapsed_time(ev1), [st for sts in per_model for st in sts]
+        return ev0.elapsed_time(ev1), [st for sts in per_ctx for st in sts]
 
     for _ in range(max(args.warmup, 3)):
         step(dev)
@@ -423,7 +431,7 @@ def main() -> None:
     units = world * len(gs)
     value = units * flops_equiv(N) / (ms_step * 1e-3) / 1e12
     e2e_value = units * flops_equiv(N) / e2e_s / 1e12
-    gemm_share = gemm_ms / (ms_total * len(gs)) if ms_total > 0 else 0.0
+    gemm_share = gemm_ms / (ms_total * nctx) if ms_total > 0 else 0.0  # of the streams' time
 
     # the squarings-only FP8 path on the same graphs, for comparison and for the GEMM roofline
     pure = None
@@ -487,10 +495,10 @@ def main() -> None:
                           "achieved": ach, "peak": pk["hbm"], "unit": "GB/s", "frac": ach / pk["hbm"],
                           "bytes_definition": "CSR of E + one read of every bit-matrix row per sweep (minimum)",
                           "launches": sweep_n, "traffic": traffic("sweep"),
-                          "share_of_busy_time": sweep_ms / (ms_total * len(gs)) if ms_total else None}
+                          "share_of_busy_time": sweep_ms / (ms_total * nctx) if ms_total else None}
     # the headline's dominant kernel by device time
     dominant = roofline
-    if roofline_sweep and sweep_ms > gemm_share * ms_total * len(gs):
+    if roofline_sweep and sweep_ms > gemm_share * ms_total * nctx:
         dominant = roofline_sweep
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
@@ -499,7 +507,7 @@ def main() -> None:
             "config": {"workload": "TC ER N=8192 x p in {1e-4,1e-3,1e-2}, seeds 2/3/4 (+1000*rank)",
                        "path": args.path, "l2": "inputs 3 x 64 MiB > L2, cycled each step",
                        "squarings_per_model": sorted(set(squarings)),
-                       "concurrency": f"{len(gs)} models in flight (one context, stream and host thread each)",
+                       "concurrency": f"{nctx} closures in flight ({INFLIGHT} contexts per model, one stream and host thread each)",
                        "gemm_busy_fraction": gemm_share},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": len(gs) * N * N,
                     "d2h_bytes_per_step": len(gs) * N * ((N + 63) // 64) * 8},
