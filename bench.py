@@ -104,7 +104,8 @@ def max_over_ranks(values, world: int, device: str):
 
 
 class ClockSampler:
-    """nvidia-smi clocks and throttle reasons sampled every 200 ms while running."""
+    """nvidia-smi clocks and throttle reasons sampled every 100 ms while running; entering
+    waits (up to 5 s) for the first sample so that the sampler is live when timing starts."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
@@ -119,9 +120,16 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-                 "-lms", "200", "-i", str(self.device)], stdout=self.tmp, stderr=subprocess.DEVNULL)
+                 "-lms", "100", "-i", str(self.device)], stdout=self.tmp, stderr=subprocess.DEVNULL)
         except Exception:
             self.proc = None
+            return self
+        deadline = time.perf_counter() + 5.0
+        while time.perf_counter() < deadline and self.proc.poll() is None:
+            self.tmp.flush()
+            if os.path.getsize(self.tmp.name) > 0:
+                break
+            time.sleep(0.02)
         return self
 
     def __exit__(self, *exc):
@@ -167,7 +175,7 @@ def bench_sg(ctx, torch, reps: int = 10) -> dict:
             "device_ms": st["ms_total"]}
 
 
-def bench_batch(ctx, torch, reps: int = 3) -> dict:
+def bench_batch(ctx, torch, reps: int = 10) -> dict:
     """1024 uneven ER closures (N ~ U{32..2048}, mean degree ~ U[1,8], seeds 1000+k), resident
     back to back in one device buffer; each call writes every model to one device buffer."""
     from concurrent.futures import ThreadPoolExecutor
@@ -319,7 +327,7 @@ def run_part(args, device: int) -> None:
 def main() -> None:
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=400)
+    ap.add_argument("--steps", type=int, default=2000)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--path", default="auto", choices=["auto", "bool_fp8"],
