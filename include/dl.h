@@ -141,6 +141,21 @@ DL_API dl_status dl_tc_closure(dl_ctx *ctx, int32_t n, const uint8_t *E, dl_mem 
                         dl_stats *stats);
 
 /*
+ * The same closure with E given bit-packed, in the layout of the output: row r of E is the
+ * ceil(n/64) 64-bit words at E_bits + r * ceil(n/64), and bit (j mod 64) of word j/64 (least
+ * significant bit first) is E[r][j].  mem says where E_bits and out_bits live (both host or
+ * both device); the caller owns both.  A set bit at a column >= n in the last word of a row
+ * returns DL_EINVAL.  eps, thr, path, out_rtilde and stats as for dl_tc_closure; the model is
+ * the same as dl_tc_closure's on the unpacked bytes.  DL_PATH_AUTO reads the bits as they
+ * are; the other paths expand them to bytes on the device first.  (The paper's base relations
+ * are 0/1 matrices (Sec. 3); the packed form is this library's, an eighth of the bytes to
+ * move.)
+ */
+DL_API dl_status dl_tc_closure_bits(dl_ctx *ctx, int32_t n, const uint64_t *E_bits, dl_mem mem, double eps,
+                             double thr, dl_path path, uint64_t *out_bits, double *out_rtilde,
+                             dl_stats *stats);
+
+/*
  * Same generation, the right-hand program of Sec. 6.2 (Fig. "Tested programs"):
  *     sg(x,w) <- b(x,w).     sg(x,w) <- p(x,y), sg(y,z), p(w,z).
  * i.e. the least solution of S = min1(B + P S P^T) (two-sided class, Sec. 5.3;

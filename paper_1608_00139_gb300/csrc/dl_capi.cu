@@ -203,6 +203,35 @@ dl_status dl_tc_closure(dl_ctx *ctx, int32_t n, const uint8_t *E, dl_mem mem, do
     });
 }
 
+dl_status dl_tc_closure_bits(dl_ctx *ctx, int32_t n, const uint64_t *E_bits, dl_mem mem, double eps,
+                             double thr, dl_path path, uint64_t *out_bits, double *out_rtilde,
+                             dl_stats *stats) {
+    clear_error();
+    GUARD_CTX(ctx);
+    if (stats) std::memset(stats, 0, sizeof(*stats));
+    if (n < 0 || !valid_mem(mem)) {
+        set_error("bad n (%d) or memory kind", n);
+        return DL_EINVAL;
+    }
+    if (n == 0) return DL_OK;
+    if (!E_bits || !out_bits) {
+        set_error("E_bits and out_bits must not be NULL");
+        return DL_EINVAL;
+    }
+    SolveArgs a;
+    a.n = n;
+    a.E_bits = E_bits;
+    a.mem = mem;
+    a.eps = eps;
+    a.thr = thr;
+    a.path = path;
+    a.out_bits = out_bits;
+    a.out_rtilde = out_rtilde;
+    return run_sync(ctx, stats, [&](Workspace &ws, cudaStream_t s, dl_stats *st) {
+        return solve_tc(ctx, ws, s, a, st);
+    });
+}
+
 dl_status dl_sg_least_model(dl_ctx *ctx, int32_t n, const uint8_t *P, const uint8_t *B,
                             dl_mem mem, double eps, double thr, dl_path path,
                             uint64_t *out_bits, dl_stats *stats) {

@@ -84,6 +84,8 @@ enum : int {
 struct SolveArgs {
     int32_t n = 0;
     const uint8_t *E = nullptr;   // closure: E; same generation: P; compose: R1
+    const uint64_t *E_bits = nullptr;  // closure: E bit-packed (n rows of ceil(n/64) words) instead
+    bool e_device = false;        // E is on the device whatever mem says (unpacked from E_bits)
     const uint8_t *E2 = nullptr;  // same generation: B (may be null); compose: R2
     dl_mem mem = DL_MEM_HOST;
     double eps = 0.0;

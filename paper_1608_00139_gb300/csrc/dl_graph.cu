@@ -2,6 +2,7 @@
 // matrix, used by the FP64 residual of the mixed path and by the boolean sweeps.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 
 #include "dl_internal.h"
@@ -66,6 +67,96 @@ __global__ void __launch_bounds__(256, 4)
     __syncthreads();
     for (int w = threadIdx.x; w < wp; w += blockDim.x)
         if (colmask_s[w] != 0ull) atomicOr(reinterpret_cast<unsigned long long *>(colmask + w), colmask_s[w]);
+}
+
+// The same outputs from a bit-packed E: row r is ceil(n/64) words at Eb + r ceil(n/64), bit
+// (j mod 64) of word j/64 holding E[r][j].  A set bit at a column >= n is an input error
+// (ST_BAD_PAD) and is dropped.  Warp per padded row, a word per lane and step (coalesced).
+__global__ void __launch_bounds__(256, 4)
+    bits_ingest_check_kernel(const uint64_t *__restrict__ Eb, int n, int np, int wp, int *cnt, uint64_t *M,
+                             unsigned long long *dmax, unsigned long long *nnz, unsigned long long *diag,
+                             int *status, uint64_t *colmask) {
+    extern __shared__ uint64_t colmask_s[];
+    for (int w = threadIdx.x; w < wp; w += blockDim.x) colmask_s[w] = 0ull;
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    uint64_t *row = M + static_cast<int64_t>(r) * wp;
+    const int idw = r >> 6;
+    const uint64_t idb = 1ull << (r & 63);
+    if (r >= n && r < np) {
+        for (int w = lane; w < wp; w += 32) row[w] = w == idw ? idb : 0ull;
+    } else if (r < n) {
+        const int w_in = (n + 63) >> 6;
+        const uint64_t *a = Eb + static_cast<int64_t>(r) * w_in;
+        const uint64_t last = (n & 63) ? (1ull << (n & 63)) - 1ull : ~0ull;  // columns < n of the last word
+        int c = 0;
+        bool bad = false, self = false;
+        for (int w = lane; w < wp; w += 32) {
+            uint64_t e = w < w_in ? a[w] : 0ull;
+            if (w == w_in - 1) {
+                bad = (e & ~last) != 0ull;
+                e &= last;
+            }
+            if (w == idw) self = (e & idb) != 0ull;
+            c += __popcll(e);
+            if (e != 0ull) atomicOr(reinterpret_cast<unsigned long long *>(colmask_s + w), e);
+            row[w] = e | (w == idw ? idb : 0ull);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) c += __shfl_xor_sync(0xffffffffu, c, o);
+        bad = __any_sync(0xffffffffu, bad);
+        self = __any_sync(0xffffffffu, self);
+        if (lane == 0) {
+            cnt[r] = c;
+            if (bad) atomicOr(status, ST_BAD_PAD);
+            if (c) {
+                atomicMax(dmax, static_cast<unsigned long long>(c));
+                atomicAdd(nnz, static_cast<unsigned long long>(c));
+            }
+            if (self) atomicAdd(diag, 1ull);
+        }
+    }
+    __syncthreads();
+    for (int w = threadIdx.x; w < wp; w += blockDim.x)
+        if (colmask_s[w] != 0ull) atomicOr(reinterpret_cast<unsigned long long *>(colmask + w), colmask_s[w]);
+}
+
+// Byte (b) of a bit-packed row spread over 8 bytes, bit k to the low bit of byte k: the four
+// high bits move up 28 places, then pairs 14, then single bits 7.
+__device__ __forceinline__ uint64_t spread_byte(uint64_t b) {
+    b = (b | (b << 28)) & 0x0000000F0000000Full;
+    b = (b | (b << 14)) & 0x0003000300030003ull;
+    return (b | (b << 7)) & 0x0101010101010101ull;
+}
+
+// Bytes of a bit-packed E (n x n, row-major): thread per 8 columns of a row; 8-byte stores
+// when rows are 8-byte aligned, else byte stores.  The first thread of a row checks the bits
+// at columns >= n (ST_BAD_PAD).
+__global__ void __launch_bounds__(256) unpack_bits_u8_kernel(const uint64_t *__restrict__ Eb, int n, uint8_t *E,
+                                                             int *status) {
+    const int w_in = (n + 63) >> 6;
+    const int64_t groups = (static_cast<int64_t>(n) + 7) >> 3;
+    const int64_t total = groups * n;
+    const bool aligned = (n & 7) == 0 && (reinterpret_cast<uintptr_t>(E) & 7) == 0;
+    for (int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; t < total;
+         t += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const int64_t r = t / groups;
+        const int g = static_cast<int>(t - r * groups);
+        const uint64_t word = Eb[r * w_in + (g >> 3)];
+        if (g == 0 && (n & 63) != 0) {
+            const uint64_t tail = Eb[r * w_in + w_in - 1] >> (n & 63);
+            if (tail != 0ull) atomicOr(status, ST_BAD_PAD);
+        }
+        const uint64_t v = spread_byte((word >> (8 * (g & 7))) & 0xFFull);
+        uint8_t *dst = E + r * n + 8 * static_cast<int64_t>(g);
+        if (aligned) {
+            *reinterpret_cast<uint64_t *>(dst) = v;
+        } else {
+            const int m = min(8, n - 8 * g);
+            for (int k = 0; k < m; ++k) dst[k] = static_cast<uint8_t>((v >> (8 * k)) & 1ull);
+        }
+    }
 }
 
 // Column indices from the packed bits.  Guarded form (cap >= 0): every thread first reads the
@@ -218,6 +309,24 @@ cudaError_t csr_pack_checked(const uint8_t *E, int n, int np, int64_t wp, int *c
     csr_pack_check_kernel<<<static_cast<unsigned>((np + 7) / 8), 256, smem, s>>>(
         E, n, np, static_cast<int>(wp), cnt, M, dmax, nnz, diag, status, colmask);
     exclusive_scan_kernel<<<1, 1024, 0, s>>>(cnt, n, ptr);
+    return cudaGetLastError();
+}
+
+cudaError_t bits_ingest_checked(const uint64_t *Eb, int n, int np, int64_t wp, int *cnt, int *ptr, uint64_t *M,
+                                unsigned long long *dmax, unsigned long long *nnz, unsigned long long *diag,
+                                int *status, uint64_t *colmask, cudaStream_t s) {
+    if (wp > 6144) return cudaErrorInvalidValue;  // the CTA's column mask lives in shared memory
+    const size_t smem = static_cast<size_t>(wp) * sizeof(uint64_t);
+    bits_ingest_check_kernel<<<static_cast<unsigned>((np + 7) / 8), 256, smem, s>>>(
+        Eb, n, np, static_cast<int>(wp), cnt, M, dmax, nnz, diag, status, colmask);
+    exclusive_scan_kernel<<<1, 1024, 0, s>>>(cnt, n, ptr);
+    return cudaGetLastError();
+}
+
+cudaError_t unpack_bits_u8(const uint64_t *Eb, int n, uint8_t *E, int *status, cudaStream_t s) {
+    const int64_t total = ((static_cast<int64_t>(n) + 7) >> 3) * n;
+    const int64_t blocks = std::min<int64_t>((total + 255) / 256, 152 * 16);
+    unpack_bits_u8_kernel<<<static_cast<unsigned>(std::max<int64_t>(blocks, 1)), 256, 0, s>>>(Eb, n, E, status);
     return cudaGetLastError();
 }
 

@@ -17,6 +17,7 @@ enum : int {
     ST_TIMEOUT_DRAIN = 16,     // teardown drain expired
     ST_BAD_INPUT = 32,         // an input byte was not 0/1
     ST_TIMEOUT_DEP = 64,       // a dependency counter never reached its target
+    ST_BAD_PAD = 128,          // a bit-packed input row had a bit at a column >= n
 };
 
 // ---------------------------------------------------------------------------------------
@@ -167,6 +168,15 @@ cudaError_t csr_fill(const uint8_t *E, int n, const int *ptr, int *col, cudaStre
 cudaError_t csr_pack_checked(const uint8_t *E, int n, int np, int64_t wp, int *cnt, int *ptr, uint64_t *M,
                              unsigned long long *dmax, unsigned long long *nnz, unsigned long long *diag, int *status,
                              uint64_t *colmask, cudaStream_t s);
+// The same from a bit-packed E (row r: ceil(n/64) words at Eb + r ceil(n/64), bit j mod 64 of
+// word j/64 = E[r][j], the layout of the model bits): status |= ST_BAD_PAD if a bit at a
+// column >= n is set (the bit is dropped).  wp <= 6144.
+cudaError_t bits_ingest_checked(const uint64_t *Eb, int n, int np, int64_t wp, int *cnt, int *ptr, uint64_t *M,
+                                unsigned long long *dmax, unsigned long long *nnz, unsigned long long *diag,
+                                int *status, uint64_t *colmask, cudaStream_t s);
+// The n x n bytes (row-major 0/1) of a bit-packed E, for the paths that start from bytes;
+// status |= ST_BAD_PAD as above.
+cudaError_t unpack_bits_u8(const uint64_t *Eb, int n, uint8_t *E, int *status, cudaStream_t s);
 // Bits of E alone (np rows of wp words, rows >= n zero), status |= ST_BAD_INPUT on a byte other
 // than 0/1.
 cudaError_t pack_bits(const uint8_t *E, int n, int np, int64_t wp, uint64_t *M, int *status, cudaStream_t s);

@@ -156,6 +156,10 @@ dl_status check_status(Workspace &ws, cudaStream_t s) {
         set_error("input matrix holds a byte that is neither 0 nor 1");
         return DL_EINVAL;
     }
+    if (st & ST_BAD_PAD) {
+        set_error("bit-packed input has a bit set at a column >= n");
+        return DL_EINVAL;
+    }
     if (st) {
         set_error("a device-side wait expired (status word 0x%x)", st);
         return DL_ETIMEOUT;
@@ -194,6 +198,24 @@ dl_status stage_input(Workspace &ws, cudaStream_t s, const uint8_t *src, int32_t
     *dev = d;
     return DL_OK;
 }
+
+// Bring a bit-packed n x n input (n rows of ceil(n/64) words) to the device.
+dl_status stage_bits(Workspace &ws, cudaStream_t s, const uint64_t *src, int32_t n, dl_mem mem,
+                     const uint64_t **dev) {
+    if (mem == DL_MEM_DEVICE) {
+        *dev = src;
+        return DL_OK;
+    }
+    const size_t bytes = static_cast<size_t>(n) * ((n + 63) / 64) * sizeof(uint64_t);
+    auto *d = static_cast<uint64_t *>(ws.get("in0b", std::max<size_t>(bytes, 16)));
+    NEED(d);
+    CK(cudaMemcpyAsync(d, src, bytes, cudaMemcpyHostToDevice, s));
+    *dev = d;
+    return DL_OK;
+}
+
+// Memory kind of the closure input E as the paths see it.
+dl_mem in_mem(const SolveArgs &a) { return a.e_device ? DL_MEM_DEVICE : a.mem; }
 
 dl_status write_bits(cudaStream_t s, const uint64_t *src, int64_t wp, uint64_t *dst, int32_t n,
                      dl_mem mem) {
@@ -253,7 +275,7 @@ dl_status tc_bool(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &a
     int launches = 0;
     tm.mark(0);
     const uint8_t *E = nullptr;
-    dl_status rc = stage_input(ws, s, a.E, n, a.mem, "in0", &E);
+    dl_status rc = stage_input(ws, s, a.E, n, in_mem(a), "in0", &E);
     if (rc) return rc;
     auto *C0 = static_cast<uint8_t *>(ws.get("c0", np * np));
     auto *C1 = static_cast<uint8_t *>(ws.get("c1", np * np));
@@ -379,7 +401,8 @@ dl_status tc_auto(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &a
     int launches = 0;
     tm.mark(0);
     const uint8_t *E = nullptr;
-    dl_status rc = stage_input(ws, s, a.E, n, a.mem, "in0", &E);
+    const uint64_t *Eb = nullptr;
+    dl_status rc = a.E_bits ? stage_bits(ws, s, a.E_bits, n, a.mem, &Eb) : stage_input(ws, s, a.E, n, in_mem(a), "in0", &E);
     if (rc) return rc;
     uint8_t *C[2] = {static_cast<uint8_t *>(ws.get("c0", np * np)), static_cast<uint8_t *>(ws.get("c1", np * np))};
     auto *rbits = static_cast<uint64_t *>(ws.get("bits0", np * wp * 8));
@@ -394,8 +417,12 @@ dl_status tc_auto(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &a
     CK(cudaMemsetAsync(colmask, 0, wp * 8, s));
     // one pass over E: the bits of C_0 = I + E, 0/1 check, row counts, ||E||_inf, nnz,
     // self-loops (the e4m3 operand is only built if a squaring happens)
-    CK(csr_pack_checked(E, n, static_cast<int>(np), wp, cnt, ptr, rbits, ws.scal + SC_DMAX, ws.scal + SC_NNZ,
-                        ws.scal + SC_COUNT0, ws.status, colmask, s));
+    if (Eb)
+        CK(bits_ingest_checked(Eb, n, static_cast<int>(np), wp, cnt, ptr, rbits, ws.scal + SC_DMAX, ws.scal + SC_NNZ,
+                               ws.scal + SC_COUNT0, ws.status, colmask, s));
+    else
+        CK(csr_pack_checked(E, n, static_cast<int>(np), wp, cnt, ptr, rbits, ws.scal + SC_DMAX, ws.scal + SC_NNZ,
+                            ws.scal + SC_COUNT0, ws.status, colmask, s));
     launches += 2;
 
     SweepClock sc{ws, s};
@@ -650,7 +677,7 @@ dl_status tc_fp64(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &a
     int launches = 0;
     tm.mark(0);
     const uint8_t *E = nullptr;
-    dl_status rc = stage_input(ws, s, a.E, n, a.mem, "in0", &E);
+    dl_status rc = stage_input(ws, s, a.E, n, in_mem(a), "in0", &E);
     if (rc) return rc;
     auto *C0 = static_cast<uint8_t *>(ws.get("c0", npb * npb));
     auto *mbits = static_cast<uint64_t *>(ws.get("bits1", npb * wp * 8));
@@ -727,7 +754,7 @@ dl_status tc_mixed_path(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveA
     int launches = 0;
     tm.mark(0);
     const uint8_t *E = nullptr;
-    dl_status rc = stage_input(ws, s, a.E, n, a.mem, "in0", &E);
+    dl_status rc = stage_input(ws, s, a.E, n, in_mem(a), "in0", &E);
     if (rc) return rc;
     auto *C0 = static_cast<uint8_t *>(ws.get("c0", np * np));
     auto *mbits = static_cast<uint64_t *>(ws.get("bits1", np * wp * 8));
@@ -789,12 +816,39 @@ dl_status tc_mixed_path(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveA
 
 }  // namespace
 
-dl_status solve_tc(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &a, dl_stats *st) {
-    if (a.thr != 0.0) {
+// The bytes of a bit-packed E on the device (the non-AUTO paths start from bytes); an input
+// error is reported here, before the path runs.
+dl_status unpack_input(Workspace &ws, cudaStream_t s, const SolveArgs &a, const uint8_t **out) {
+    const uint64_t *Eb = nullptr;
+    dl_status rc = stage_bits(ws, s, a.E_bits, a.n, a.mem, &Eb);
+    if (rc) return rc;
+    auto *E = static_cast<uint8_t *>(ws.get("in0u", std::max<size_t>(static_cast<size_t>(a.n) * a.n, 16)));
+    NEED(E);
+    CK(cudaMemsetAsync(ws.status, 0, sizeof(int), s));
+    CK(unpack_bits_u8(Eb, a.n, E, ws.status, s));
+    if ((rc = check_status(ws, s))) return rc;
+    *out = E;
+    return DL_OK;
+}
+
+dl_status solve_tc(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &in, dl_stats *st) {
+    if (in.thr != 0.0) {
         set_error("thr must be 0: the model is R~ > 0 (Theorem 1)");
         return DL_EINVAL;
     }
     dl_status rc;
+    SolveArgs a = in;
+    if (a.E_bits && a.path != DL_PATH_AUTO) {  // AUTO ingests the bits as they are
+        if (a.path != DL_PATH_BOOL_FP8 && a.path != DL_PATH_FP64 && a.path != DL_PATH_MIXED) {
+            set_error("unknown path %d", static_cast<int>(a.path));
+            return DL_EINVAL;
+        }
+        const uint8_t *E = nullptr;
+        if ((rc = unpack_input(ws, s, a, &E))) return rc;
+        a.E = E;
+        a.E_bits = nullptr;
+        a.e_device = true;
+    }
     switch (a.path) {
         case DL_PATH_AUTO:
         case DL_PATH_BOOL_FP8:

@@ -23,7 +23,7 @@ STATUS_NAMES = ["DL_OK", "DL_EINVAL", "DL_ENOMEM", "DL_EDEVICE", "DL_ETIMEOUT", 
 PATHS = {"auto": 0, "fp64": 1, "mixed": 2, "bool_fp8": 3, "fp8": 3}
 DL_MEM_HOST, DL_MEM_DEVICE = 0, 1
 
-EXPORTED = ["dl_create", "dl_destroy", "dl_last_error", "dl_set_stream", "dl_tc_closure",
+EXPORTED = ["dl_create", "dl_destroy", "dl_last_error", "dl_set_stream", "dl_tc_closure", "dl_tc_closure_bits",
             "dl_sg_least_model", "dl_compose", "dl_tc_batch", "dl_submit", "dl_poll", "dl_cancel",
             "dl_tc_closure_noalloc", "dl_selftest_wait_timeout"]
 NOALLOC_MAX_N = 2048
@@ -89,6 +89,8 @@ def lib() -> ctypes.CDLL:
             L.dl_set_stream.argtypes = [vp, vp]
             L.dl_tc_closure.argtypes = [vp, i32, vp, ctypes.c_int, f64, f64, ctypes.c_int, vp, vp,
                                         ctypes.POINTER(Stats)]
+            L.dl_tc_closure_bits.argtypes = [vp, i32, vp, ctypes.c_int, f64, f64, ctypes.c_int, vp, vp,
+                                             ctypes.POINTER(Stats)]
             L.dl_sg_least_model.argtypes = [vp, i32, vp, vp, ctypes.c_int, f64, f64, ctypes.c_int,
                                             vp, ctypes.POINTER(Stats)]
             L.dl_compose.argtypes = [vp, i32, vp, vp, ctypes.c_int, vp, ctypes.POINTER(Stats)]
@@ -138,6 +140,27 @@ def _square_u8(x, sync=True):
     if a.ndim != 2 or a.shape[0] != a.shape[1]:
         raise ValueError("expected a square matrix")
     return a.ctypes.data, int(a.shape[0]), DL_MEM_HOST, a
+
+
+def _bits_u64(x, n: int, sync=True):
+    """(pointer, mem, keepalive) of an n x ceil(n/64) array of 64-bit words (numpy or torch
+    CUDA)."""
+    shape = (int(n), words(int(n)))
+    if _is_torch(x):
+        import torch
+        if not x.is_cuda:
+            x = x.numpy()
+        else:
+            if x.dtype not in (torch.int64, torch.uint64) or tuple(x.shape) != shape:
+                raise ValueError(f"expected a {shape} int64 CUDA tensor")
+            x = x.contiguous()
+            if sync:
+                torch.cuda.current_stream(x.device).synchronize()
+            return x.data_ptr(), DL_MEM_DEVICE, x
+    a = np.ascontiguousarray(x)
+    if a.dtype not in (np.uint64, np.int64) or a.shape != shape:
+        raise ValueError(f"expected a {shape} array of 64-bit words")
+    return a.ctypes.data, DL_MEM_HOST, a
 
 
 def _alloc_bits(n: int, mem: int, like=None):
@@ -212,6 +235,32 @@ class Context:
         st = Stats()
         _check(lib().dl_tc_closure(self._h, n, p, mem, float(eps), float(thr), PATHS[path], bp, rp,
                                    ctypes.byref(st)))
+        return (bits, st.as_dict(), rt) if rtilde else (bits, st.as_dict())
+
+    def tc_closure_bits(self, Eb, n: int, eps: float = 0.0, thr: float = 0.0, path: str = "auto",
+                        rtilde: bool = False, out=None):
+        """The closure of a bit-packed E (n x ceil(n/64) words, LSB first: a numpy uint64/int64
+        array or an int64 CUDA tensor); returns (bits, stats[, R~]) like tc_closure."""
+        p, mem, keep = _bits_u64(Eb, n)
+        if out is None:
+            bits, bp = _alloc_bits(n, mem, keep)
+        else:
+            if tuple(out.shape) != (n, words(n)):
+                raise ValueError("out must have shape (n, ceil(n/64))")
+            bits = out
+            bp = out.data_ptr() if _is_torch(out) else out.ctypes.data
+        rt, rp = None, None
+        if rtilde:
+            if mem == DL_MEM_DEVICE:
+                import torch
+                rt = torch.empty((n, n), dtype=torch.float64, device=keep.device)
+                rp = rt.data_ptr()
+            else:
+                rt = np.zeros((n, n), dtype=np.float64)
+                rp = rt.ctypes.data
+        st = Stats()
+        _check(lib().dl_tc_closure_bits(self._h, int(n), p, mem, float(eps), float(thr), PATHS[path], bp, rp,
+                                        ctypes.byref(st)))
         return (bits, st.as_dict(), rt) if rtilde else (bits, st.as_dict())
 
     def sg_least_model(self, P, B=None, eps: float = 0.0, thr: float = 0.0,
