@@ -363,11 +363,16 @@ def main() -> None:
     gs = graphs(rank)
     dev = [torch.from_numpy(e).cuda() for e in gs]
     # pinned host copies for the end-to-end leg (inputs and outputs)
-    host, host_out = [], []
+    host, host_bits, host_out = [], [], []
     for e in gs:
         t = torch.empty(e.shape, dtype=torch.uint8, pin_memory=True)
         t.numpy()[:] = e
         host.append(t.numpy())
+        # the same E bit-packed (row-major, LSB first), for the packed-input end-to-end leg
+        packed = np.packbits(e, axis=1, bitorder="little").view(np.uint64)
+        tb = torch.empty(packed.shape, dtype=torch.int64, pin_memory=True)
+        tb.numpy().view(np.uint64)[:] = packed
+        host_bits.append(tb.numpy().view(np.uint64))
     # INFLIGHT contexts per model (one stream and host thread each): every context solves its
     # model back to back, so 3 x INFLIGHT closures are in flight; a step is still one solve of
     # each of the three models (the contexts of a model share its solves)
@@ -385,19 +390,21 @@ def main() -> None:
     main_stream = torch.cuda.current_stream()
 
     def outs_for(inputs):
-        return host_out if inputs is host else dev_out
+        return dev_out if inputs is dev else host_out
+
+    def solve(i, inputs, path):
+        if inputs is host_bits:
+            return ctxs[i].tc_closure_bits(inputs[model_of[i]], N, path=path, out=host_out[i])
+        return ctxs[i].tc_closure(inputs[model_of[i]], path=path, out=outs_for(inputs)[i])
 
     def step(inputs, path=args.path):
-        outs = outs_for(inputs)
-        return list(pool.map(lambda i: ctxs[i].tc_closure(inputs[model_of[i]], path=path, out=outs[i]),
-                             range(nctx)))
+        return list(pool.map(lambda i: solve(i, inputs, path), range(nctx)))
 
     def timed(inputs, path, k):
         """Device time of k steps: events fork/join the contexts' streams; each host thread
         drives its share of its model's k solves back to back."""
         ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         ends = [torch.cuda.Event() for _ in streams]
-        outs = outs_for(inputs)
         torch.cuda.synchronize()
         ev0.record(main_stream)
         for st_ in streams:
@@ -405,7 +412,7 @@ def main() -> None:
 
         def run(i):
             share = k // INFLIGHT + (1 if i // len(gs) < k % INFLIGHT else 0)
-            return [ctxs[i].tc_closure(inputs[model_of[i]], path=path, out=outs[i])[1] for _ in range(share)]
+            return [solve(i, inputs, path)[1] for _ in range(share)]
 
         per_ctx = list(pool.map(run, range(nctx)))
         for e_, st_ in zip(ends, streams):
@@ -428,6 +435,10 @@ def main() -> None:
         step(host)
         e2e_ms, _ = timed(host, args.path, e2e_steps)
         e2e_s = e2e_ms * 1e-3 / e2e_steps
+        # the same with E bit-packed on the host (dl_tc_closure_bits): an eighth of the H2D bytes
+        step(host_bits)
+        e2e_bits_ms, _ = timed(host_bits, args.path, e2e_steps)
+        e2e_bits_s = e2e_bits_ms * 1e-3 / e2e_steps
     clocks = clk.summary()
     launches = sum(st["gpu_launches"] for st in stats)
     gemm_ms = sum(st["ms_gemm"] for st in stats)
@@ -435,7 +446,7 @@ def main() -> None:
     gemm_n = sum(st["gemm_launches"] for st in stats)
     squarings = [st["iters"] for st in stats]
     ms_step = ms_total / args.steps
-    ms_step, e2e_s = max_over_ranks([ms_step, e2e_s], world, "cuda")
+    ms_step, e2e_s, e2e_bits_s = max_over_ranks([ms_step, e2e_s, e2e_bits_s], world, "cuda")
     units = world * len(gs)
     value = units * flops_equiv(N) / (ms_step * 1e-3) / 1e12
     e2e_value = units * flops_equiv(N) / e2e_s / 1e12
@@ -519,6 +530,10 @@ def main() -> None:
                        "gemm_busy_fraction": gemm_share},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": len(gs) * N * N,
                     "d2h_bytes_per_step": len(gs) * N * ((N + 63) // 64) * 8},
+            "e2e_bits": {"value": units * flops_equiv(N) / e2e_bits_s / 1e12, "unit": UNIT,
+                         "input": "E bit-packed on the host (dl_tc_closure_bits)",
+                         "h2d_bytes_per_step": len(gs) * N * ((N + 63) // 64) * 8,
+                         "d2h_bytes_per_step": len(gs) * N * ((N + 63) // 64) * 8},
             "gpu_launches": launches, "roofline": dominant, "roofline_gemm": roofline,
             "roofline_sweep": roofline_sweep,
             "clocks": clocks}
