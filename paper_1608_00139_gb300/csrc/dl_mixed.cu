@@ -90,94 +90,204 @@ cudaError_t transpose(const T *src, int64_t lds, int rows, int cols, T *dst, int
 }
 
 // Unpivoted LU of the BL x BL block at A (row stride lda) with the inverses of its factors,
-// FP32, by Gauss-Jordan elimination held in registers: 1024 threads, thread t owns columns
-// (t & 7) + 8 q, q = 0 .. 31, of row t >> 3 of the augmented BL x 2BL matrix (interleaved, so
-// that the 8 threads of a row read 8 different shared-memory banks of the pivot row).
-//  1. forward elimination of [A | I] (row_r -= (a_rk / a_kk) row_k for r > k) leaves [U | L^-1];
-//  2. backward elimination of [U | I] (row_k /= u_kk, then row_i -= u_ik row_k for i < k; the
-//     multipliers are U's entries, unchanged by the later steps) leaves U^-1 on the right.
-// One barrier per step: the pivot row goes through a double-buffered shared row.
-// Writes L^-1 (unit lower), U^-1 and U^-T, BL x BL each.
+// FP32, blocked by 32 in shared memory: one CTA of 1024 threads holds the block, L^-1 and
+// U^-1 (three BL x (BL + 4) float arrays).
+//  1. right-looking LU by 32-column panels: warp 0 factors the panel's 32 x 32 diagonal block
+//     (lane = row; the pivot row, final once the earlier steps are done, is read back from
+//     shared memory), warps 1-3 form L21 = A21 U11^-1 (lane = row) and warps 4-6 form
+//     U12 = L11^-1 A12 (lane = column) by substitution, then all warps update A22 -= L21 U12
+//     in strips of 8 rows x 32 columns;
+//  2. the inverses of the 32 x 32 diagonal blocks of L and U by substitution (a warp each),
+//     then the blocks off the diagonal at distance d = 1, 2, 3 from it, each from blocks
+//     nearer the diagonal:  X_ij = -X_ii sum_{k=j..i-1} L_ik X_kj  (X = L^-1, i > j) and
+//     Y_ij = -Y_ii sum_{k=i+1..j} U_ik Y_kj  (Y = U^-1, i < j).
+// Writes L^-1 (unit lower), U^-1 and U^-T, BL x BL each; a zero pivot sets ST_BAD_INPUT.
 constexpr int kDiagThreads = 1024;
+constexpr int kDiagLd = BL + 4;  // padded shared-memory row (keeps float4 alignment)
+constexpr size_t kDiagSmem = 3ull * BL * kDiagLd * sizeof(float) + 16;
 constexpr int kSolveGroup = 8;  // panels per group of the N-RHS solves
 
-// v[j] for a runtime j (unrolled selects keep v in registers)
-__device__ __forceinline__ float pick32(const float (&v)[32], int j) {
-    float x = 0.0f;
+// acc[r] += sum_{k < 32} A[r][k] B[k][lane] for an 8 x 32 strip A and a 32 x 32 block B, both in
+// shared memory with row stride kDiagLd (A's rows read as broadcast float4s).
+__device__ __forceinline__ void strip_product(const float *A, const float *B, int lane, float (&acc)[8]) {
 #pragma unroll
-    for (int q = 0; q < 32; ++q) x = q == j ? v[q] : x;
-    return x;
+    for (int k = 0; k < 32; k += 4) {
+        const float b0 = B[(k + 0) * kDiagLd + lane], b1 = B[(k + 1) * kDiagLd + lane];
+        const float b2 = B[(k + 2) * kDiagLd + lane], b3 = B[(k + 3) * kDiagLd + lane];
+#pragma unroll
+        for (int r = 0; r < 8; ++r) {
+            const float4 a = *reinterpret_cast<const float4 *>(A + r * kDiagLd + k);
+            acc[r] = fmaf(a.x, b0, acc[r]);
+            acc[r] = fmaf(a.y, b1, acc[r]);
+            acc[r] = fmaf(a.z, b2, acc[r]);
+            acc[r] = fmaf(a.w, b3, acc[r]);
+        }
+    }
+}
+
+__device__ __forceinline__ void load_row32(const float *p, float (&r)[32]) {
+#pragma unroll
+    for (int c = 0; c < 32; c += 4) {
+        const float4 v = *reinterpret_cast<const float4 *>(p + c);
+        r[c] = v.x;
+        r[c + 1] = v.y;
+        r[c + 2] = v.z;
+        r[c + 3] = v.w;
+    }
+}
+
+__device__ __forceinline__ void store_row32(float *p, const float (&r)[32]) {
+#pragma unroll
+    for (int c = 0; c < 32; c += 4) *reinterpret_cast<float4 *>(p + c) = make_float4(r[c], r[c + 1], r[c + 2], r[c + 3]);
 }
 
 __global__ void __launch_bounds__(kDiagThreads) diag_lu_inv_kernel(const float *A, int64_t lda, float *Linv,
                                                                    float *Uinv, float *UinvT, int *status) {
-    static_assert(BL == 128, "the thread layout assumes 128-row diagonal blocks");
-    __shared__ float piv[2][2 * BL];
-    const int t = threadIdx.x;
-    const int r = t >> 3, sg = t & 7;  // row r, columns sg + 8 q (q < 16: A / U, q >= 16: right half)
-    const int row_lane0 = (t & 31) & ~7;
-    float v[32];
-#pragma unroll
-    for (int q = 0; q < 32; ++q) {
-        const int c = sg + 8 * q;
-        v[q] = c < BL ? A[static_cast<int64_t>(r) * lda + c] : (c - BL == r ? 1.0f : 0.0f);
+    static_assert(BL == 128, "four 32-column panels");
+    extern __shared__ float4 diag_smem[];
+    float *S = reinterpret_cast<float *>(diag_smem);  // the block; then L (strictly lower) and U in place
+    float *XL = S + BL * kDiagLd;                      // L^-1
+    float *XU = XL + BL * kDiagLd;                     // U^-1
+    int *bad = reinterpret_cast<int *>(XU + BL * kDiagLd);
+    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
+    if (t == 0) *bad = 0;
+    for (int e = t; e < BL * BL / 4; e += kDiagThreads) {
+        const int r = e >> 5, c = (e & 31) * 4;
+        *reinterpret_cast<float4 *>(S + r * kDiagLd + c) = *reinterpret_cast<const float4 *>(A + r * lda + c);
     }
-    // 1. [A | I] -> [U | L^-1]
-    for (int k = 0; k < BL; ++k) {
-        float *p = piv[k & 1];
-        if (r == k) {
+    __syncthreads();
+
+    // ---- 1. LU by 32-column panels ----
+    for (int o = 0; o < BL; o += 32) {
+        const int rem = BL - o - 32;  // rows (and columns) after the panel
+        if (warp == 0) {
+            float *rowp = S + (o + lane) * kDiagLd + o;
+            float r[32];
+            load_row32(rowp, r);
 #pragma unroll
-            for (int q = 0; q < 32; ++q) p[sg + 8 * q] = v[q];
+            for (int j = 0; j < 32; ++j) {
+                if (lane == j) store_row32(rowp, r);  // row j is final after steps 0 .. j-1
+                __syncwarp();
+                const float *pj = S + (o + j) * kDiagLd + o;
+                if (lane > j) {
+                    const float l = r[j] / pj[j];
+                    r[j] = l;
+#pragma unroll
+                    for (int c = j + 1; c < 32; ++c) r[c] = fmaf(-l, pj[c], r[c]);
+                }
+            }
+            store_row32(rowp, r);
+            const float d = S[(o + lane) * kDiagLd + o + lane];  // U_ii (this lane's row, stored above)
+            if (!(fabsf(d) > 0.0f) || !isfinite(d)) atomicOr(bad, 1);
         }
         __syncthreads();
-        const float pk = p[k];
-        if (pk == 0.0f) {  // zero pivot (the M-matrix has none): report and stop (uniform)
+        if (*bad) {  // uniform: every thread reads the flag after the barrier
             if (t == 0) atomicOr(status, ST_BAD_INPUT);
             return;
         }
-        const float ark = __shfl_sync(0xffffffffu, pick32(v, k >> 3), row_lane0 + (k & 7));  // a_rk
-        if (r > k) {
-            const float m = ark / pk;
+        if (rem == 0) break;
+        if (warp >= 1 && warp <= 3 && 32 * (warp - 1) < rem) {  // L21 = A21 U11^-1, lane = row
+            float *rowp = S + (o + 32 + 32 * (warp - 1) + lane) * kDiagLd + o;
+            float r[32];
+            load_row32(rowp, r);
 #pragma unroll
-            for (int q = 0; q < 32; ++q) {
-                const int c = sg + 8 * q;
-                if (c > k) v[q] = fmaf(-m, p[c], v[q]);
+            for (int j = 0; j < 32; ++j) {
+                const float *uj = S + (o + j) * kDiagLd + o;
+                r[j] = r[j] / uj[j];
+#pragma unroll
+                for (int c = j + 1; c < 32; ++c) r[c] = fmaf(-r[j], uj[c], r[c]);
             }
-        }
-    }
-    // L^-1 is the right half now: write it, then start the right half over from I
+            store_row32(rowp, r);
+        } else if (warp >= 4 && warp <= 6 && 32 * (warp - 4) < rem) {  // U12 = L11^-1 A12, lane = column
+            const int c = o + 32 + 32 * (warp - 4) + lane;
+            float x[32];
 #pragma unroll
-    for (int q = 16; q < 32; ++q) {
-        const int c = sg + 8 * (q - 16);
-        Linv[r * BL + c] = c < r ? v[q] : (c == r ? 1.0f : 0.0f);
-        v[q] = c == r ? 1.0f : 0.0f;
-    }
-    __syncthreads();
-    // 2. [U | I] -> U^-1 on the right (only the right half is updated)
-    for (int k = BL - 1; k >= 0; --k) {
-        float *p = piv[k & 1];
-        const float ukk = __shfl_sync(0xffffffffu, pick32(v, k >> 3), row_lane0 + (k & 7));  // used in row k
-        if (r == k) {
-            const float inv = 1.0f / ukk;
+            for (int i = 0; i < 32; ++i) x[i] = S[(o + i) * kDiagLd + c];
 #pragma unroll
-            for (int q = 16; q < 32; ++q) {
-                v[q] *= inv;
-                p[sg + 8 * (q - 16)] = v[q];
+            for (int j = 0; j < 32; ++j) {
+#pragma unroll
+                for (int i = j + 1; i < 32; ++i) x[i] = fmaf(-S[(o + i) * kDiagLd + o + j], x[j], x[i]);
             }
+#pragma unroll
+            for (int i = 0; i < 32; ++i) S[(o + i) * kDiagLd + c] = x[i];
         }
         __syncthreads();
-        const float uik = __shfl_sync(0xffffffffu, pick32(v, k >> 3), row_lane0 + (k & 7));  // U's entry (r, k)
-        if (r < k) {
+        const int nbk = rem / 32, tasks = nbk * nbk * 4;  // A22 -= L21 U12: 4 strips per 32 x 32 block
+        for (int task = warp; task < tasks; task += 32) {
+            const int blk = task >> 2, strip = task & 3;
+            const int row0 = o + 32 + 32 * (blk / nbk) + 8 * strip, col0 = o + 32 + 32 * (blk % nbk);
+            float acc[8] = {};
+            strip_product(S + row0 * kDiagLd + o, S + o * kDiagLd + col0, lane, acc);
 #pragma unroll
-            for (int q = 16; q < 32; ++q) v[q] = fmaf(-uik, p[sg + 8 * (q - 16)], v[q]);
+            for (int r = 0; r < 8; ++r) S[(row0 + r) * kDiagLd + col0 + lane] -= acc[r];
         }
+        __syncthreads();
     }
+
+    // ---- 2a. inverses of the diagonal blocks (lane = column) ----
+    if (warp < 4) {  // L_pp^-1, unit lower: forward substitution on e_lane
+        const int o = 32 * warp;
+        float x[32];
 #pragma unroll
-    for (int q = 16; q < 32; ++q) {
-        const int c = sg + 8 * (q - 16);
-        const float x = c >= r ? v[q] : 0.0f;
-        Uinv[r * BL + c] = x;
-        UinvT[c * BL + r] = x;
+        for (int i = 0; i < 32; ++i) x[i] = i == lane ? 1.0f : 0.0f;
+#pragma unroll
+        for (int k = 0; k < 32; ++k) {
+#pragma unroll
+            for (int i = k + 1; i < 32; ++i) x[i] = fmaf(-S[(o + i) * kDiagLd + o + k], x[k], x[i]);
+        }
+#pragma unroll
+        for (int i = 0; i < 32; ++i) XL[(o + i) * kDiagLd + o + lane] = x[i];
+    } else if (warp < 8) {  // U_pp^-1 by rows: row lane of U^-1 solves U^T z = e_lane (forward)
+        const int o = 32 * (warp - 4);
+        float z[32];
+#pragma unroll
+        for (int i = 0; i < 32; ++i) z[i] = i == lane ? 1.0f : 0.0f;
+#pragma unroll
+        for (int k = 0; k < 32; ++k) {
+            const float *uk = S + (o + k) * kDiagLd + o;  // row k of U
+            z[k] = z[k] / uk[k];
+#pragma unroll
+            for (int i = k + 1; i < 32; ++i) z[i] = fmaf(-uk[i], z[k], z[i]);
+        }
+        store_row32(XU + (o + lane) * kDiagLd + o, z);
+    }
+    __syncthreads();
+
+    // ---- 2b. blocks off the diagonal, by distance d: warp -> (side, j, strip) ----
+    for (int d = 1; d < 4; ++d) {
+        const int nblk = 4 - d, tasks = 2 * nblk * 4;  // at most 24 <= 32 warps
+        const bool has = warp < tasks;
+        const int task = has ? warp : 0;  // idle warps take task 0's indices and access nothing
+        const int side = task / (nblk * 4), j = (task % (nblk * 4)) >> 2, strip = task & 3;
+        // L side: block (j + d, j) of X;  U side: block (j, j + d) of Y
+        const int bi = side == 0 ? j + d : j, bj = side == 0 ? j : j + d;
+        float *X = side == 0 ? XL : XU;
+        float *dst = X + (32 * bi + 8 * strip) * kDiagLd + 32 * bj;
+        if (has) {  // T = sum_k L_{bi,k} X_{k,bj} (k = bj .. bi-1), or U_{bi,k} Y_{k,bj} (k = bi+1 .. bj)
+            float acc[8] = {};
+            const int k0 = side == 0 ? bj : bi + 1, k1 = side == 0 ? bi - 1 : bj;
+            for (int k = k0; k <= k1; ++k)
+                strip_product(S + (32 * bi + 8 * strip) * kDiagLd + 32 * k, X + 32 * k * kDiagLd + 32 * bj, lane, acc);
+#pragma unroll
+            for (int r = 0; r < 8; ++r) dst[r * kDiagLd + lane] = acc[r];
+        }
+        __syncthreads();
+        float acc[8] = {};
+        if (has)  // -X_{bi,bi} T (the whole T block is read: products first, stores after a barrier)
+            strip_product(X + (32 * bi + 8 * strip) * kDiagLd + 32 * bi, X + 32 * bi * kDiagLd + 32 * bj, lane, acc);
+        __syncthreads();
+        if (has) {
+#pragma unroll
+            for (int r = 0; r < 8; ++r) dst[r * kDiagLd + lane] = -acc[r];
+        }
+        __syncthreads();
+    }
+
+    for (int e = t; e < BL * BL; e += kDiagThreads) {
+        const int r = e >> 7, c = e & (BL - 1);
+        Linv[e] = c < r ? XL[r * kDiagLd + c] : (c == r ? 1.0f : 0.0f);
+        Uinv[e] = c >= r ? XU[r * kDiagLd + c] : 0.0f;
+        UinvT[e] = r >= c ? XU[c * kDiagLd + r] : 0.0f;  // U^-T[r][c] = U^-1[c][r]
     }
 }
 
@@ -393,9 +503,11 @@ dl_status tc_mixed(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &
     };
 
     // ---- LU ----------------------------------------------------------------------------
+    MCK(cudaFuncSetAttribute(diag_lu_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(kDiagSmem)));
     for (int k = 0; k < nb; ++k) {
         const int64_t kb = static_cast<int64_t>(k) * BL;
-        diag_lu_inv_kernel<<<1, kDiagThreads, 0, s>>>(A32 + kb * np + kb, np, Linv + kb * BL, Uinv + kb * BL,
+        diag_lu_inv_kernel<<<1, kDiagThreads, kDiagSmem, s>>>(A32 + kb * np + kb, np, Linv + kb * BL, Uinv + kb * BL,
                                                       UinvT + kb * BL, ws.status);
         MCK(cudaGetLastError());
         ++launches;
