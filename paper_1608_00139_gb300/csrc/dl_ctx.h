@@ -104,8 +104,9 @@ dl_status solve_tc_batch(dl_ctx *ctx, Workspace &ws, cudaStream_t s, int32_t cou
                          const int32_t *ns, const uint8_t *const *Es, dl_mem mem,
                          uint64_t *const *out_bits, dl_stats *st);
 // Mixed-precision solve (dl_mixed.cu): leaves X in the "mx_X64" buffer (np x np doubles).
+// dmax = ||E||_inf (bounds the terms of the residual's sums).
 dl_status tc_mixed(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &a, dl_stats *st,
-                   const uint8_t *E, double eps, int *launches_io);
+                   const uint8_t *E, double eps, unsigned long long dmax, int *launches_io);
 // Device bytes a request of this kind and size needs (serving admission).
 size_t footprint_bytes(int kind, int32_t n);
 

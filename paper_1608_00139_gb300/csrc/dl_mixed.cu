@@ -106,6 +106,7 @@ constexpr int kDiagThreads = 1024;
 constexpr int kDiagLd = BL + 4;  // padded shared-memory row (keeps float4 alignment)
 constexpr size_t kDiagSmem = 3ull * BL * kDiagLd * sizeof(float) + 16;
 constexpr int kSolveGroup = 8;  // panels per group of the N-RHS solves
+constexpr size_t kResidualSmem = 227 * 1024;  // dynamic shared memory of one residual block
 
 // acc[r] += sum_{k < 32} A[r][k] B[k][lane] for an 8 x 32 strip A and a 32 x 32 block B, both in
 // shared memory with row stride kDiagLd (A's rows read as broadcast float4s).
@@ -291,34 +292,96 @@ __global__ void __launch_bounds__(kDiagThreads) diag_lu_inv_kernel(const float *
     }
 }
 
-// Residual of the transposed system, one block per row j of Z, the row staged in shared
-// memory:  R^T[j][i] = eps * sum_{k in succ(i)} (Z[j][k] + [k = j]) - Z[j][i]  (FP64),
-// stored as FP32 (right-hand side of the correction solve); max |R| -> *rmax.
-__global__ void __launch_bounds__(256) residual_t_kernel(const int *__restrict__ ptr, const int *__restrict__ col,
-                                                         int n, int np, double eps, const double *__restrict__ Z,
-                                                         float *__restrict__ R, unsigned long long *rmax) {
-    extern __shared__ double zs[];
-    const int j = blockIdx.x;
-    const double *zrow = Z + static_cast<int64_t>(j) * np;
-    for (int t = threadIdx.x; t < np; t += blockDim.x) zs[t] = zrow[t];
+// round(z 2^e) from the bits of z with integer operations only (GB300's FP64 units are the scarce
+// resource of the residual); the caller keeps |z| 2^e below 2^62.  Zero and subnormal z give 0.
+__device__ __forceinline__ long long fixed_of(long long bits, int e) {
+    const int ex = static_cast<int>((bits >> 52) & 0x7FF);
+    if (ex == 0) return 0;
+    const long long m = (bits & 0xFFFFFFFFFFFFFll) | 0x10000000000000ll;  // |z| = m 2^(ex - 1075)
+    const int sh = ex - 1075 + e;
+    long long v = 0;
+    if (sh >= 0) v = m << sh;
+    else if (sh > -64) v = (m + (1ll << (-sh - 1))) >> (-sh);  // nearest, ties away from zero
+    return bits < 0 ? -v : v;
+}
+
+// Residual of the transposed system for G rows j of Z per block (the rows share each read of
+// the CSR):  R^T[j][i] = eps * sum_{k in succ(i)} (Z[j][k] + [k = j]) - Z[j][i],  stored as FP32
+// (right-hand side of the correction solve); max |R| -> *rmax.  The sums are exact in 64-bit
+// fixed point: row j sits in shared memory as round((Z[j][k] + [k = j]) 2^e_j), e_j chosen from
+// the row's largest exponent and 2^deg_bits >= ||E||_inf so that no sum reaches 2^62.  Each
+// term is rounded once (at most 2^-(e_j + 1), below one FP64 ulp of the row's largest entry);
+// the scaling by eps 2^-e_j and the subtraction are one FP64 fma.
+template <int G>
+__global__ void __launch_bounds__(1024, 1)
+    residual_fixed_kernel(const int *__restrict__ ptr, const int *__restrict__ col, int n, int np, int deg_bits,
+                          double eps, const double *__restrict__ Z, float *__restrict__ R, unsigned long long *rmax) {
+    extern __shared__ long long zi[];  // G rows of np entries
+    __shared__ int ex_max[G];
+    const int j0 = blockIdx.x * G;
+    if (threadIdx.x < G) ex_max[threadIdx.x] = 0;
     __syncthreads();
-    if (threadIdx.x == 0 && j < n) zs[j] += 1.0;  // the eps E[i][j] term, as k = j
-    __syncthreads();
-    double m = 0.0;
-    for (int i = threadIdx.x; i < np; i += blockDim.x) {
-        double r = 0.0;
-        if (i < n && j < n) {
-            double s = 0.0;
-            for (int q = ptr[i]; q < ptr[i + 1]; ++q) s += zs[col[q]];
-            r = eps * s - (zs[i] - (i == j ? 1.0 : 0.0));
+#pragma unroll
+    for (int g = 0; g < G; ++g) {  // stage the raw bits and find the largest exponent
+        const int j = j0 + g;
+        int ex = 0;
+        if (j < np) {
+            const long long *zb = reinterpret_cast<const long long *>(Z + static_cast<int64_t>(j) * np);
+            for (int k = threadIdx.x; k < np; k += blockDim.x) {
+                const long long b = zb[k];
+                zi[g * np + k] = b;
+                ex = max(ex, static_cast<int>((b >> 52) & 0x7FF));
+            }
         }
-        R[static_cast<int64_t>(j) * np + i] = static_cast<float>(r);
-        m = fmax(m, fabs(r));
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) ex = max(ex, __shfl_xor_sync(0xffffffffu, ex, o));
+        if ((threadIdx.x & 31) == 0) atomicMax(&ex_max[g], ex);
+    }
+    __syncthreads();
+    int e[G];
+    double scale[G];
+#pragma unroll
+    for (int g = 0; g < G; ++g) {
+        // every term, the +1 included, is below 2^hb; a sum of at most 2^deg_bits terms below 2^62
+        const int hb = max(ex_max[g] - 1022, 0) + 1;
+        e[g] = max(0, 62 - deg_bits - hb);
+        scale[g] = ldexp(eps, -e[g]);
     }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-    if ((threadIdx.x & 31) == 0 && m > 0.0)
-        atomicMax(rmax, static_cast<unsigned long long>(__double_as_longlong(m)));
+    for (int g = 0; g < G; ++g)
+        for (int k = threadIdx.x; k < np; k += blockDim.x) zi[g * np + k] = fixed_of(zi[g * np + k], e[g]);
+    __syncthreads();
+    if (threadIdx.x < G) {  // the eps E[i][j] term, as k = j
+        const int g = threadIdx.x, j = j0 + g;
+        if (j < n) zi[g * np + j] += 1ll << e[g];
+    }
+    __syncthreads();
+    float m = 0.0f;
+    for (int i = threadIdx.x; i < np; i += blockDim.x) {
+        long long sum[G] = {};
+        if (i < n) {
+            const int q1 = ptr[i + 1];
+            for (int q = ptr[i]; q < q1; ++q) {
+                const int c = col[q];
+#pragma unroll
+                for (int g = 0; g < G; ++g) sum[g] += zi[g * np + c];
+            }
+        }
+#pragma unroll
+        for (int g = 0; g < G; ++g) {
+            const int j = j0 + g;
+            if (j >= np) break;
+            float r = 0.0f;
+            if (i < n && j < n)
+                r = static_cast<float>(fma(scale[g], static_cast<double>(sum[g]), -Z[static_cast<int64_t>(j) * np + i]));
+            R[static_cast<int64_t>(j) * np + i] = r;
+            m = fmaxf(m, fabsf(r));
+        }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if ((threadIdx.x & 31) == 0 && m > 0.0f)
+        atomicMax(rmax, static_cast<unsigned long long>(__double_as_longlong(static_cast<double>(m))));
 }
 
 __global__ void f32_to_f64_kernel(const float *__restrict__ a, double *__restrict__ b, int64_t count) {
@@ -352,7 +415,7 @@ struct Launch {
 }  // namespace
 
 dl_status tc_mixed(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &a, dl_stats *st,
-                   const uint8_t *E, double eps, int *launches_io) {
+                   const uint8_t *E, double eps, unsigned long long dmax, int *launches_io) {
     const int32_t n = a.n;
     const int64_t np = round_up(std::max<int64_t>(n, 1), 256);
     const int nb = static_cast<int>(np / BL);
@@ -540,9 +603,43 @@ dl_status tc_mixed(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &
     // ---- refinement ----------------------------------------------------------------------
     const double tol = ctx->cfg.refine_tol > 0 ? ctx->cfg.refine_tol : 1e-13;
     const int max_iters = ctx->cfg.refine_max_iters > 0 ? ctx->cfg.refine_max_iters : 30;
-    const size_t res_smem = sizeof(double) * static_cast<size_t>(np);
-    MCK(cudaFuncSetAttribute(residual_t_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             static_cast<int>(res_smem)));
+    // rows of Z per residual block: as many (up to 3) as shared memory holds
+    const size_t row_bytes = sizeof(long long) * static_cast<size_t>(np);
+    const int rows_per_block = static_cast<int>(std::min<size_t>(3, kResidualSmem / row_bytes));
+    if (rows_per_block < 1) {
+        set_error("mixed path: n = %d exceeds the residual's shared-memory row (%zu bytes)", n, kResidualSmem);
+        return DL_EINVAL;
+    }
+    const size_t res_smem = row_bytes * rows_per_block;
+    int deg_bits = 0;  // 2^deg_bits >= ||E||_inf (the terms of one sum)
+    while ((1ull << deg_bits) < std::max<unsigned long long>(dmax, 1)) ++deg_bits;
+    auto residual = [&](unsigned long long *rmax_p) -> cudaError_t {
+        const unsigned grid = static_cast<unsigned>((np + rows_per_block - 1) / rows_per_block);
+        cudaError_t e;
+        switch (rows_per_block) {
+            case 3:
+                if ((e = cudaFuncSetAttribute(residual_fixed_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              static_cast<int>(res_smem))) != cudaSuccess)
+                    return e;
+                residual_fixed_kernel<3><<<grid, 1024, res_smem, s>>>(csr_ptr, csr_col, n, N, deg_bits, eps, Z64, Z32,
+                                                                     rmax_p);
+                break;
+            case 2:
+                if ((e = cudaFuncSetAttribute(residual_fixed_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              static_cast<int>(res_smem))) != cudaSuccess)
+                    return e;
+                residual_fixed_kernel<2><<<grid, 1024, res_smem, s>>>(csr_ptr, csr_col, n, N, deg_bits, eps, Z64, Z32,
+                                                                     rmax_p);
+                break;
+            default:
+                if ((e = cudaFuncSetAttribute(residual_fixed_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              static_cast<int>(res_smem))) != cudaSuccess)
+                    return e;
+                residual_fixed_kernel<1><<<grid, 1024, res_smem, s>>>(csr_ptr, csr_col, n, N, deg_bits, eps, Z64, Z32,
+                                                                     rmax_p);
+        }
+        return cudaGetLastError();
+    };
     unsigned long long *rmax_d = ws.scal + 20;
     double rmax = 0.0, best = 0.0;
     int it = 0, stall = 0;
@@ -551,9 +648,7 @@ dl_status tc_mixed(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &
     const double floor_ok = 1e-8 * eps;
     for (;;) {
         MCK(cudaMemsetAsync(rmax_d, 0, sizeof(unsigned long long), s));
-        residual_t_kernel<<<static_cast<unsigned>(np), 256, res_smem, s>>>(csr_ptr, csr_col, n, N, eps, Z64, Z32,
-                                                                           rmax_d);
-        MCK(cudaGetLastError());
+        MCK(residual(rmax_d));
         ++launches;
         unsigned long long h = 0;
         MCK(cudaMemcpyAsync(&h, rmax_d, sizeof(h), cudaMemcpyDeviceToHost, s));

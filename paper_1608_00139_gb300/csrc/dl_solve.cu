@@ -771,7 +771,7 @@ dl_status tc_mixed_path(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveA
         return rc;
     dl_stats local{};
     dl_stats *sx = st ? st : &local;
-    if ((rc = tc_mixed(ctx, ws, s, a, sx, E, eps, &launches))) return rc;
+    if ((rc = tc_mixed(ctx, ws, s, a, sx, E, eps, dmax, &launches))) return rc;
     tm.mark(2);
     const auto *X = static_cast<const double *>(ws.get("mx_X64", np * np * 8));
     const double tau = ctx->cfg.guard_tau > 0 ? ctx->cfg.guard_tau : 1e-30;
