@@ -217,6 +217,44 @@ def test_mixed_rtilde_matches_oracle(ctx, n, p, seed):
     assert st["iters"] >= 1
 
 
+def test_mixed_hub_and_chain_dynamic_range(ctx):
+    """A hub with n-1 successors (eps = 1/n) and a long chain: R~ spans hundreds of decades and
+    one row's residual sums n-1 terms (the fixed-point residual's widest sums)."""
+    n = 700
+    e = inputs.er_digraph(n, 0.002, 11)
+    e[3, :] = 1
+    e[3, 3] = 0
+    for k in range(100, 399):
+        e[k, k + 1] = 1
+    bits, st, x = ctx.tc_closure(e, path="mixed", rtilde=True)
+    xr = oracle.tc_rtilde_lu(e, st["eps_used"])
+    assert st["eps_used"] == 1.0 / n
+    assert np.abs(x - xr).max() <= 1e-10 * np.abs(xr).max()
+    assert st["final_resid"] <= 1e-13
+    assert np.array_equal(bits, oracle.tc_model(e))
+
+
+def test_mixed_two_rows_per_residual_block(ctx):
+    """n = 9800: a row of Z takes 78 KB, so the residual stages two rows per block."""
+    n = 9800
+    e = inputs.er_digraph(n, 5e-4, 12)
+    bits, st, x = ctx.tc_closure(e, path="mixed", rtilde=True)
+    assert st["final_resid"] <= 1e-13
+    assert np.array_equal(bits, oracle.tc_model(e))
+    for j in (0, 4321, n - 1):
+        col = oracle.tc_rtilde_col(e, st["eps_used"], j)
+        assert np.abs(x[:, j] - col).max() <= 1e-10 * max(np.abs(col).max(), st["eps_used"])
+
+
+def test_mixed_one_row_per_residual_block(ctx):
+    """n = 15000: one row of Z per residual block; the model against the oracle's."""
+    n = 15000
+    e = inputs.er_digraph(n, 2e-4, 13)
+    bits, st = ctx.tc_closure(e, path="mixed")
+    assert st["final_resid"] <= 1e-13
+    assert np.array_equal(bits, oracle.tc_model(e))
+
+
 def test_user_eps(ctx):
     e = inputs.er_digraph(200, 0.02, 5)
     e0 = oracle.tc_eps(e)
