@@ -384,6 +384,16 @@ __global__ void __launch_bounds__(1024, 1)
         atomicMax(rmax, static_cast<unsigned long long>(__double_as_longlong(static_cast<double>(m))));
 }
 
+// Y = I on every group's rows (groups of gw rows starting at multiples of gw; row r of a group
+// holds its identity entry at column r mod gw), for both group-inverse buffers (zeroed before).
+__global__ void group_identity_kernel(float *YL, float *YU, int np, int gw) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r >= np) return;
+    const int64_t at = static_cast<int64_t>(r) * gw + r % gw;
+    YL[at] = 1.0f;
+    YU[at] = 1.0f;
+}
+
 __global__ void f32_to_f64_kernel(const float *__restrict__ a, double *__restrict__ b, int64_t count) {
     for (int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; t < count;
          t += static_cast<int64_t>(gridDim.x) * blockDim.x)
@@ -429,6 +439,17 @@ dl_status tc_mixed(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &
     auto *Linv = static_cast<float *>(ws.get("mx_Linv", np * BL * 4));
     auto *Uinv = static_cast<float *>(ws.get("mx_Uinv", np * BL * 4));
     auto *UinvT = static_cast<float *>(ws.get("mx_UinvT", np * BL * 4));
+    // group inverses of the solves: a group is kSolveGroup panels (GW columns)
+    const int64_t GW = std::min<int64_t>(np, static_cast<int64_t>(kSolveGroup) * BL);
+    auto *YL = static_cast<float *>(ws.get("mx_YL", np * GW * 4));
+    auto *YU = static_cast<float *>(ws.get("mx_YU", np * GW * 4));
+    auto *GL = static_cast<float *>(ws.get("mx_GL", np * GW * 4));
+    auto *GU = static_cast<float *>(ws.get("mx_GU", np * GW * 4));
+    auto *Tg = static_cast<float *>(ws.get("mx_Tg", np * GW * 4));
+    if (!YL || !YU || !GL || !GU || !Tg) {
+        set_error("mixed path: device allocation failed (group inverses)");
+        return DL_ENOMEM;
+    }
     auto *csr_cnt = static_cast<int *>(ws.get("mx_cnt", (np + 1) * 4));
     auto *csr_ptr = static_cast<int *>(ws.get("mx_ptr", (np + 1) * 4));
     if (!A32 || !Z32 || !Z64 || !X64 || !T || !Linv || !Uinv || !UinvT || !csr_cnt || !csr_ptr) {
@@ -461,7 +482,13 @@ dl_status tc_mixed(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &
 
     // ---- GEMM table (every product is C (=|-=) A B'^T, both operands K-major) --------------
     std::vector<GemmProblem> probs;
-    std::vector<Launch> lu, fwd, bwd;
+    std::vector<Launch> lu, ginv, fwd, bwd;
+    // a solve step: a GEMM launch of fwd/bwd, or (launch < 0) the copy of the group panel Tg
+    // back into Z's columns [gs, gs + w)
+    struct Step {
+        int launch, gs, w;
+    };
+    std::vector<Step> fwd_steps, bwd_steps;
     std::string err;
     double flops_lu = 0, flops_solve = 0;
     auto add = [&](std::vector<Launch> &list, GemmEpi epi, int M, int Nn, int K, const Operand &Aop,
@@ -514,37 +541,66 @@ dl_status tc_mixed(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &
         ok = ok && add(lu, EPI_SUB_F32, rem, rem, BL, at(opA, kb + BL, kb), opT, A32, np, kb + BL, kb + BL, false,
                        &flops_lu);
     }
-    // The N-RHS solves run in groups of kSolveGroup panels: inside a group each panel is
-    // solved with its diagonal inverse and updates the group's later (forward) or earlier
-    // (backward) panels; one update with K = the group's width then carries the whole group to
-    // the columns beyond it, so the trailing part of Z is read and written once per group.
-    for (int g0 = 0; g0 < nb && ok; g0 += kSolveGroup) {
-        const int g1 = std::min(nb, g0 + kSolveGroup), gs = g0 * BL, ge = g1 * BL;
-        for (int k = g0; k < g1 && ok; ++k) {
-            const int kb = k * BL;
-            ok = add(fwd, EPI_STORE_F32, N, BL, BL, at(opZ, 0, kb), at(opL, kb, 0), Z32, np, 0, kb, false,
-                     &flops_solve);
-            if (ok && kb + BL < ge)
-                ok = add(fwd, EPI_SUB_F32, N, ge - kb - BL, BL, at(opZ, 0, kb), at(opA, kb + BL, kb), Z32, np, 0,
-                         kb + BL, false, &flops_solve);
+    // Inverses of the diagonal groups (kSolveGroup panels each), once per factorisation: the
+    // forward machinery on rows Y = I of a group gives Y L_gg^T = I, i.e. Y = L_gg^-T, and the
+    // backward one Y = U_gg^-T; every step is one launch over all groups.  (Transposed after.)
+    const Operand opYL{YL, np, GW, GW, 0, 0}, opYU{YU, np, GW, GW, 0, 0};
+    const Operand opGL{GL, np, GW, GW, 0, 0}, opGU{GU, np, GW, GW, 0, 0};
+    const Operand opTg{Tg, np, GW, GW, 0, 0};
+    const int ng = (nb + kSolveGroup - 1) / kSolveGroup;
+    for (int kl = 0; kl < kSolveGroup && ok; ++kl) {
+        for (int g = 0; g < ng && ok; ++g) {  // Y_k = Y_k L_kk^-T
+            const int g0 = g * kSolveGroup, g1 = std::min(nb, g0 + kSolveGroup), gs = g0 * BL, w = (g1 - g0) * BL;
+            if (g0 + kl < g1)
+                ok = add(ginv, EPI_STORE_F32, w, BL, BL, at(opYL, gs, kl * BL), at(opL, gs + kl * BL, 0), YL, GW, gs,
+                         kl * BL, true, &flops_lu);
         }
-        if (ok && ge < N)
-            ok = add(fwd, EPI_SUB_F32, N, N - ge, ge - gs, at(opZ, 0, gs), at(opA, ge, gs), Z32, np, 0, ge, false,
-                     &flops_solve);
+        for (int g = 0; g < ng && ok; ++g) {  // Y_{>k} -= Y_k L_{>k,k}^T
+            const int g0 = g * kSolveGroup, g1 = std::min(nb, g0 + kSolveGroup), gs = g0 * BL, ge = g1 * BL,
+                      w = ge - gs, kb = gs + kl * BL;
+            if (g0 + kl < g1 && kb + BL < ge)
+                ok = add(ginv, EPI_SUB_F32, w, ge - kb - BL, BL, at(opYL, gs, kl * BL), at(opA, kb + BL, kb), YL, GW,
+                         gs, (kl + 1) * BL, true, &flops_lu);
+        }
     }
-    for (int g1 = nb; g1 > 0 && ok; g1 -= kSolveGroup) {
-        const int g0 = std::max(0, g1 - kSolveGroup), gs = g0 * BL, ge = g1 * BL;
-        for (int k = g1 - 1; k >= g0 && ok; --k) {
-            const int kb = k * BL;
-            ok = add(bwd, EPI_STORE_F32, N, BL, BL, at(opZ, 0, kb), at(opU, kb, 0), Z32, np, 0, kb, false,
-                     &flops_solve);
-            if (ok && kb > gs)
-                ok = add(bwd, EPI_SUB_F32, N, kb - gs, BL, at(opZ, 0, kb), at(opA, gs, kb), Z32, np, 0, gs, false,
-                         &flops_solve);
+    for (int kl = kSolveGroup - 1; kl >= 0 && ok; --kl) {
+        for (int g = 0; g < ng && ok; ++g) {  // Y_k = Y_k U_kk^-T
+            const int g0 = g * kSolveGroup, g1 = std::min(nb, g0 + kSolveGroup), gs = g0 * BL, w = (g1 - g0) * BL;
+            if (g0 + kl < g1)
+                ok = add(ginv, EPI_STORE_F32, w, BL, BL, at(opYU, gs, kl * BL), at(opU, gs + kl * BL, 0), YU, GW, gs,
+                         kl * BL, true, &flops_lu);
         }
-        if (ok && gs > 0)
-            ok = add(bwd, EPI_SUB_F32, N, gs, ge - gs, at(opZ, 0, gs), at(opA, 0, gs), Z32, np, 0, 0, false,
+        for (int g = 0; g < ng && ok; ++g) {  // Y_{<k} -= Y_k U_{<k,k}^T
+            const int g0 = g * kSolveGroup, g1 = std::min(nb, g0 + kSolveGroup), gs = g0 * BL, w = (g1 - g0) * BL,
+                      kb = gs + kl * BL;
+            if (g0 + kl < g1 && kb > gs)
+                ok = add(ginv, EPI_SUB_F32, w, kb - gs, BL, at(opYU, gs, kl * BL), at(opA, gs, kb), YU, GW, gs, 0,
+                         true, &flops_lu);
+        }
+    }
+    // The N-RHS solves by groups: Z_g = Z_g G_g^T (G_g = L_gg^-1 or U_gg^-1, one GEMM with
+    // K = the group's width, into Tg and copied back), then one update with the same K carries
+    // the group to the columns beyond it (forward) or before it (backward).
+    for (int g = 0; g < ng && ok; ++g) {
+        const int g0 = g * kSolveGroup, g1 = std::min(nb, g0 + kSolveGroup), gs = g0 * BL, ge = g1 * BL, w = ge - gs;
+        fwd_steps.push_back(Step{static_cast<int>(fwd.size()), gs, w});
+        ok = add(fwd, EPI_STORE_F32, N, w, w, at(opZ, 0, gs), at(opGL, gs, 0), Tg, GW, 0, 0, false, &flops_solve);
+        fwd_steps.push_back(Step{-1, gs, w});
+        if (ok && ge < N) {
+            fwd_steps.push_back(Step{static_cast<int>(fwd.size()), gs, w});
+            ok = add(fwd, EPI_SUB_F32, N, N - ge, w, at(opTg, 0, 0), at(opA, ge, gs), Z32, np, 0, ge, false,
                      &flops_solve);
+        }
+    }
+    for (int g = ng - 1; g >= 0 && ok; --g) {
+        const int g0 = g * kSolveGroup, g1 = std::min(nb, g0 + kSolveGroup), gs = g0 * BL, ge = g1 * BL, w = ge - gs;
+        bwd_steps.push_back(Step{static_cast<int>(bwd.size()), gs, w});
+        ok = add(bwd, EPI_STORE_F32, N, w, w, at(opZ, 0, gs), at(opGU, gs, 0), Tg, GW, 0, 0, false, &flops_solve);
+        bwd_steps.push_back(Step{-1, gs, w});
+        if (ok && gs > 0) {
+            bwd_steps.push_back(Step{static_cast<int>(bwd.size()), gs, w});
+            ok = add(bwd, EPI_SUB_F32, N, gs, w, at(opTg, 0, 0), at(opA, 0, gs), Z32, np, 0, 0, false, &flops_solve);
+        }
     }
     if (!ok) {
         set_error("mixed path: %s", err.c_str());
@@ -583,13 +639,34 @@ dl_status tc_mixed(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &
             launches += 2;
         }
     }
+    // group inverses: Y = I on each group's rows, the grouped steps, then G = Y^T per group
+    MCK(cudaMemsetAsync(YL, 0, np * GW * 4, s));
+    MCK(cudaMemsetAsync(YU, 0, np * GW * 4, s));
+    group_identity_kernel<<<static_cast<unsigned>((np + 255) / 256), 256, 0, s>>>(YL, YU, N, static_cast<int>(GW));
+    MCK(cudaGetLastError());
+    ++launches;
+    for (const Launch &L : ginv) MCK(run(L));
+    for (int64_t gs = 0; gs < np; gs += GW) {
+        const int w = static_cast<int>(std::min<int64_t>(GW, np - gs));
+        MCK(transpose(YL + gs * GW, GW, w, w, GL + gs * GW, GW, s));
+        MCK(transpose(YU + gs * GW, GW, w, w, GU + gs * GW, GW, s));
+        launches += 2;
+    }
     MCK(cudaEventRecord(ev[5], s));
     auto solve = [&]() -> cudaError_t {
         cudaError_t e;
-        for (const Launch &L : fwd)
-            if ((e = run(L)) != cudaSuccess) return e;
-        for (const Launch &L : bwd)
-            if ((e = run(L)) != cudaSuccess) return e;
+        for (int pass = 0; pass < 2; ++pass) {
+            const std::vector<Step> &steps = pass == 0 ? fwd_steps : bwd_steps;
+            const std::vector<Launch> &list = pass == 0 ? fwd : bwd;
+            for (const Step &st_ : steps) {
+                if (st_.launch >= 0) {
+                    if ((e = run(list[st_.launch])) != cudaSuccess) return e;
+                } else if ((e = cudaMemcpy2DAsync(Z32 + st_.gs, np * 4, Tg, GW * 4, static_cast<size_t>(st_.w) * 4, np,
+                                                  cudaMemcpyDeviceToDevice, s)) != cudaSuccess) {
+                    return e;
+                }
+            }
+        }
         return cudaSuccess;
     };
     MCK(solve());
@@ -679,7 +756,7 @@ dl_status tc_mixed(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &
         st->iters = it;
         st->final_resid = rmax / eps;
         st->gemm_flops = flops_lu + flops_solve * (1 + it);
-        st->gemm_launches = static_cast<int>(lu.size() + (fwd.size() + bwd.size()) * (1 + it));
+        st->gemm_launches = static_cast<int>(lu.size() + ginv.size() + (fwd.size() + bwd.size()) * (1 + it));
         float t1 = 0, t2 = 0, t3 = 0;
         cudaEventElapsedTime(&t1, ev[4], ev[5]);
         cudaEventElapsedTime(&t2, ev[5], ev[6]);
