@@ -12,6 +12,7 @@ Functions (passages they follow are cited in ``oracle.c``):
   tc_rtilde_col(E, eps, j)  column j of R~ by the series of Lemma 1
   sg_model(P, B)         least model of the same-generation program (Sec. 6.2), semi-naive
   tc_eps(E), sg_eps(P)   the paper's default epsilons (Sec. 4, Sec. 6.1, Sec. 6.2)
+  sg_stilde_kron, sg_stilde_series   the real S~ of same generation (sg_real.py, numpy FP64)
 Bit matrices: ceil(n/64) uint64 words per row, bit j%64 of word j//64, LSB first.
 """
 from __future__ import annotations
@@ -22,6 +23,8 @@ import subprocess
 import threading
 
 import numpy as np
+
+from .sg_real import sg_stilde_kron, sg_stilde_series  # noqa: F401  (numpy FP64, no C part)
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "oracle.c")
