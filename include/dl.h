@@ -169,6 +169,28 @@ DL_API dl_status dl_sg_least_model(dl_ctx *ctx, int32_t n, const uint8_t *P, con
                             uint64_t *out_bits, dl_stats *stats);
 
 /*
+ * The real least solution of the same-generation equation (Sec. 6.2; the two-sided class of
+ * Sec. 5.3, a discrete Stein/Sylvester equation):
+ *     S~ = eps (B + P S~ P^T),
+ * whose positive entries are the least model of sg (Theorem 2).  P: n x n 0/1; B: n x n 0/1,
+ * or NULL for the identity.  eps <= 0 selects 1/(1 + ||P||_inf^2) (Sec. 6.2); otherwise
+ * 0 < eps <= that bound is required (it makes eps ||P^T kron P||_inf < 1, the condition of
+ * Sec. 5.3 for a unique solution), else DL_EINVAL.  out_stilde: n x n doubles, row-major
+ * (required).  out_bits (optional, NULL allowed): the model, S~ > 0 made exact by the
+ * boolean iteration (n * ceil(n/64) words).  mem: where P, B and both outputs live.
+ * Paths: DL_PATH_FP64 -- the fixpoint series X <- eps (B + P X P^T) in FP64 until a step
+ * changes nothing beyond 1e-13 eps (exact after depth + 1 steps when P is nilpotent);
+ * DL_PATH_MIXED -- Smith's doubling on the TF32 tensor cores with FP64 refinement;
+ * DL_PATH_AUTO -- the series, then the refinement if 64 steps did not converge.
+ * DL_PATH_BOOL_FP8: DL_EINVAL (no real values).  n is limited to 29000 (a row of S~ in one
+ * block's shared memory); DL_ENOTCONV if the series or the refinement does not converge.
+ * stats: iters = series steps + refinement steps, final_resid = max|eps (B + P S P^T) - S|/eps,
+ * path_used = DL_PATH_FP64 when the series alone sufficed, else DL_PATH_MIXED.
+ */
+DL_API dl_status dl_sg_real(dl_ctx *ctx, int32_t n, const uint8_t *P, const uint8_t *B, dl_mem mem, double eps,
+                     dl_path path, double *out_stilde, uint64_t *out_bits, dl_stats *stats);
+
+/*
  * Relational composition, the denotation of an existential join (Sec. 2,
  * eq. denote:quant):  [[exists y r1(x,y) and r2(y,z)]] = min1(R1 R2).
  * R1, R2: n x n 0/1.  Output: bits of min1(R1 R2).  Runs on the FP8 tensor-core path.

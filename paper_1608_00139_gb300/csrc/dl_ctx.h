@@ -98,6 +98,8 @@ struct SolveArgs {
 // Drivers: run on (ws, stream); return a dl_status and fill stats.
 dl_status solve_tc(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &a, dl_stats *st);
 dl_status solve_sg(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &a, dl_stats *st);
+// The real S~ of same generation into a.out_rtilde (n x n doubles); bits optional.
+dl_status solve_sg_real(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &a, dl_stats *st);
 dl_status solve_compose(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &a,
                         dl_stats *st);
 dl_status solve_tc_batch(dl_ctx *ctx, Workspace &ws, cudaStream_t s, int32_t count,

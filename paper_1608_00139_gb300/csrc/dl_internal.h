@@ -203,4 +203,23 @@ cudaError_t thresh_pack_f64(const double *X, int64_t ldx, int n, int np, double 
 
 int num_sms();
 
+// ---------------------------------------------------------------------------------------
+// Real same-generation solution S~ = eps (B + P S~ P^T) (dl_sgreal.cu)
+// ---------------------------------------------------------------------------------------
+// One FP64 step over the CSR of P (np x np row-major buffers, zero outside n x n; B: n x n
+// bytes or NULL for the identity):  U = X P^T, V = eps (B + P U), D = V - X.  Xn (optional)
+// <- V; R (optional) <- D in FP32; *dmax = max |D| as the bit pattern of a non-negative double
+// (zeroed by the caller).  np * 8 bytes of shared memory per block (np <= 29056).
+cudaError_t sg_real_step(const int *ptr, const int *col, int n, int np, double eps, const uint8_t *B, const double *X,
+                         double *U, double *Xn, float *R, unsigned long long *dmax, cudaStream_t s);
+// A = scale P, NA = -A (FP32, np x np, zero padding).
+cudaError_t sg_scaled_p(const uint8_t *P, int n, int np, float scale, float *A, float *NA, cudaStream_t s);
+// *out = max_i sum_j |A[i][j]| as FP32 bits (zeroed by the caller).
+cudaError_t row_abs_sum_max(const float *A, int np, unsigned *out, cudaStream_t s);
+cudaError_t negate_f32(const float *a, float *b, int64_t count, cudaStream_t s);
+cudaError_t add_f32_to_f64(double *x, const float *d, int64_t count, cudaStream_t s);
+cudaError_t transpose_f32(const float *src, int64_t lds, int rows, int cols, float *dst, int64_t ldd, cudaStream_t s);
+// dst |= src over `words` 64-bit words.
+cudaError_t bits_or(uint64_t *dst, const uint64_t *src, int64_t words, cudaStream_t s);
+
 }  // namespace dl

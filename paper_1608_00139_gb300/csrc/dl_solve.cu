@@ -26,6 +26,7 @@
 #include <cmath>
 #include <cstring>
 #include <string>
+#include <vector>
 
 #include "dl_ctx.h"
 #include "dl_internal.h"
@@ -881,7 +882,8 @@ dl_status solve_tc(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &
 // S |= P X (rows of P gather rows of X); when B is symmetric so is every S_t and S^T = S.
 // Returns with *done = false (and nothing written) if the rows are too wide or the
 // iterations exceed the budget: the doubling below then solves the problem.
-dl_status sg_iteration(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &a, dl_stats *st, bool *done) {
+dl_status sg_iteration(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &a, dl_stats *st, bool *done,
+                       const uint64_t *seed = nullptr) {
     (void)ctx;
     *done = false;
     const int32_t n = a.n;
@@ -920,12 +922,16 @@ dl_status sg_iteration(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveAr
         CK(bits_identity(S, n, static_cast<int>(np), wp, s));
         ++launches;
     }
+    if (seed) {  // S_0 = B | seed (the seed lies inside the least model, so the limit is unchanged)
+        CK(bits_or(S, seed, np * wp, s));
+        ++launches;
+    }
     if ((rc = read_scalars(ws, s))) return rc;
     if ((rc = check_status(ws, s))) return rc;
     const double dmax = static_cast<double>(host_scal(ws)[SC_DMAX]);
     double eps = 0;
     if ((rc = choose_eps(a.eps, 1.0 / (1.0 + dmax * dmax), "Sec. 6.2 (1/(1+||P||^2))", &eps))) return rc;
-    const bool sym = Bm == nullptr || host_scal(ws)[SC_CQ] == 0;
+    const bool sym = seed == nullptr && (Bm == nullptr || host_scal(ws)[SC_CQ] == 0);
     const int64_t nnz = static_cast<int64_t>(host_scal(ws)[SC_NNZ]);
     auto *col = static_cast<int *>(ws.get("g_col", static_cast<size_t>(std::max<int64_t>(nnz, 1)) * 4));
     NEED(col);
@@ -1181,6 +1187,276 @@ dl_status solve_compose(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveA
         st->ms_epilogue = tm.ms(2, 3);
         st->ms_total = tm.ms(0, 3);
         st->gpu_launches = launches;
+    }
+    return DL_OK;
+}
+
+// The real least solution S~ = eps (B + P S~ P^T) of same generation (Sec. 6.2; its positive
+// entries are the model, Theorem 2), in FP64, written to a.out_rtilde (n x n doubles).
+//  * the series X_{t+1} = eps (B + P X_t P^T) from X_0 = 0 (FP64 gathers over the CSR of P;
+//    X_{t+1} - X_t is X_t's residual, so a step whose change is at most tol eps ends it).  It
+//    is exact after depth + 1 steps when P is nilpotent (a forest or a DAG);
+//  * otherwise (DL_PATH_MIXED, or AUTO after 64 steps) refinement from the current X: the
+//    residual in FP64, the correction D = sum_m (eps P)^m R (P^T)^m by Smith's doubling for
+//    the Stein equation X = R + A X A^T with A = sqrt(eps) P on the TF32 tensor cores
+//    (A_0 = A, A_{k+1} = A_k^2, X <- X + A_k X A_k^T; stopped when ||A_K||_inf^2 <= 1e-5, the
+//    tail's relative size), X += D.
+// The optional bits are S~ > 0 made exact by the boolean iteration S <- B | P S P^T started from
+// B and those bits (an entry lost to underflow comes back; none can be spurious, since exact
+// zeros stay exact through non-negative products and through the refinement).
+dl_status solve_sg_real(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &a, dl_stats *st) {
+    if (a.thr != 0.0) {
+        set_error("thr must be 0: the model is S~ > 0 (Theorem 2)");
+        return DL_EINVAL;
+    }
+    if (a.path != DL_PATH_AUTO && a.path != DL_PATH_FP64 && a.path != DL_PATH_MIXED) {
+        set_error("the real S~ runs on DL_PATH_AUTO, DL_PATH_FP64 or DL_PATH_MIXED");
+        return DL_EINVAL;
+    }
+    const int32_t n = a.n;
+    const int64_t np = round_up(std::max<int64_t>(n, 1), 256);
+    const int64_t wp = np / 64;
+    if (np * static_cast<int64_t>(sizeof(double)) > 227 * 1024) {
+        set_error("n = %d: a row of S~ exceeds one block's shared memory", n);
+        return DL_EINVAL;
+    }
+    Timer tm{ws.ev, s};
+    int launches = 0, gemm_launches = 0;
+    tm.mark(0);
+    const uint8_t *P = nullptr, *Bm = nullptr;
+    dl_status rc = stage_input(ws, s, a.E, n, a.mem, "in0", &P);
+    if (rc) return rc;
+    if (a.E2 && (rc = stage_input(ws, s, a.E2, n, a.mem, "in1", &Bm))) return rc;
+    const size_t nn = static_cast<size_t>(np) * np;
+    auto *bits = static_cast<uint64_t *>(ws.get("bits0", np * wp * 8));
+    auto *bitsB = static_cast<uint64_t *>(ws.get("bits1", np * wp * 8));
+    auto *cnt = static_cast<int *>(ws.get("g_cnt", (np + 1) * 4));
+    auto *ptr = static_cast<int *>(ws.get("g_ptr", (np + 1) * 4));
+    auto *colmask = static_cast<uint64_t *>(ws.get("g_colmask", wp * 8));
+    auto *Xd = static_cast<double *>(ws.get("sr_X", nn * 8));
+    auto *Xn = static_cast<double *>(ws.get("sr_Xn", nn * 8));
+    auto *U = static_cast<double *>(ws.get("sr_U", nn * 8));
+    NEED(bits && bitsB && cnt && ptr && colmask && Xd && Xn && U);
+    CK(cudaMemsetAsync(ws.scal, 0, kScalars * sizeof(unsigned long long), s));
+    CK(cudaMemsetAsync(ws.status, 0, sizeof(int), s));
+    CK(cudaMemsetAsync(colmask, 0, wp * 8, s));
+    // P: 0/1 check, ||P||_inf, the CSR; B: 0/1 check
+    CK(csr_pack_checked(P, n, static_cast<int>(np), wp, cnt, ptr, bits, ws.scal + SC_DMAX, ws.scal + SC_NNZ,
+                        ws.scal + SC_COUNT0, ws.status, colmask, s));
+    launches += 2;
+    if (Bm) {
+        CK(pack_bits(Bm, n, static_cast<int>(np), wp, bitsB, ws.status, s));
+        ++launches;
+    }
+    if ((rc = read_scalars(ws, s))) return rc;
+    if ((rc = check_status(ws, s))) return rc;
+    const double dmax = static_cast<double>(host_scal(ws)[SC_DMAX]);
+    double eps = 0;
+    if ((rc = choose_eps(a.eps, 1.0 / (1.0 + dmax * dmax), "Sec. 6.2 (1/(1+||P||^2))", &eps))) return rc;
+    const int64_t nnz = static_cast<int64_t>(host_scal(ws)[SC_NNZ]);
+    auto *col = static_cast<int *>(ws.get("g_col", static_cast<size_t>(std::max<int64_t>(nnz, 1)) * 4));
+    NEED(col);
+    CK(csr_fill_from_bits(bits, n, wp, ptr, col, s));
+    CK(cudaMemsetAsync(Xd, 0, nn * 8, s));
+    ++launches;
+    tm.mark(1);
+
+    const double tol = ctx->cfg.refine_tol > 0 ? ctx->cfg.refine_tol : 1e-13;
+    unsigned long long *slot = ws.scal + 32;  // per-step max |change|, bit patterns of doubles
+    auto as_double = [](unsigned long long b) {
+        double d;
+        std::memcpy(&d, &b, sizeof d);
+        return d;
+    };
+    bool done = false;
+    int steps = 0, refine_steps = 0;
+    double resid = 0.0;
+    if (a.path != DL_PATH_MIXED) {  // the series, four steps per host read
+        constexpr int kGroup = 4;
+        const int budget = a.path == DL_PATH_FP64 ? 100000 : 64;
+        while (!done && steps < budget) {
+            CK(cudaMemsetAsync(slot, 0, kGroup * sizeof(unsigned long long), s));
+            for (int k = 0; k < kGroup; ++k) {
+                CK(sg_real_step(ptr, col, n, static_cast<int>(np), eps, Bm, Xd, U, Xn, nullptr, slot + k, s));
+                std::swap(Xd, Xn);
+                launches += 2;
+            }
+            if ((rc = read_scalars(ws, s))) return rc;
+            for (int k = 0; k < kGroup; ++k) {
+                ++steps;
+                resid = as_double(host_scal(ws)[32 + k]) / eps;
+                if (resid <= tol) {
+                    done = true;  // the iterates after this step are at least as close
+                    break;
+                }
+            }
+        }
+        if (!done && a.path == DL_PATH_FP64) {
+            set_error("the series did not reach max|change|/eps <= %g in %d steps", tol, steps);
+            return DL_ENOTCONV;
+        }
+    }
+    tm.mark(2);
+    if (!done) {  // refinement with Smith's doubling for the corrections
+        constexpr int kMaxK = 40;
+        constexpr int TB = 128;  // GEMM tile
+        auto *Xs = static_cast<float *>(ws.get("sr_Xs", nn * 4));
+        auto *W = static_cast<float *>(ws.get("sr_W", nn * 4));
+        auto *WT = static_cast<float *>(ws.get("sr_WT", nn * 4));
+        auto *AT = static_cast<float *>(ws.get("sr_AT", nn * 4));
+        auto *dprob = static_cast<GemmProblem *>(ws.get("sr_probs", sizeof(GemmProblem) * (3 * kMaxK + 3)));
+        NEED(Xs && W && WT && AT && dprob);
+        std::vector<float *> A, NA;
+        auto mat = [&](const char *base, int k) {
+            return static_cast<float *>(ws.get(std::string(base) + std::to_string(k), nn * 4));
+        };
+        A.push_back(mat("sr_A", 0));
+        NA.push_back(mat("sr_NA", 0));
+        NEED(A[0] && NA[0]);
+        CK(sg_scaled_p(P, n, static_cast<int>(np), static_cast<float>(std::sqrt(eps)), A[0], NA[0], s));
+        ++launches;
+        CK(gemm_prepare(KIND_TF32, true, TB, EPI_STORE_F32));
+        CK(gemm_prepare(KIND_TF32, true, TB, EPI_SUB_F32));
+        int nprob = 0;
+        std::string err;
+        auto op = [&](const float *m) { return Operand{m, np, np, np, 0, 0}; };
+        // one problem C (=|-=) X Y^T of np x np operands, uploaded to slot nprob
+        auto problem = [&](const float *X, const float *Y, float *C, GemmEpi epi, int *slot_out) -> dl_status {
+            GemmProblem p;
+            GemmEpilogue e{};
+            e.c32 = C;
+            e.ld_c32 = np;
+            if (!gemm_make_problem(&p, KIND_TF32, true, TB, static_cast<int>(np), static_cast<int>(np),
+                                   static_cast<int>(np), op(X), op(Y), e, &err)) {
+                set_error("same generation S~: %s", err.c_str());
+                return DL_EDEVICE;
+            }
+            p.tile_start = 0;
+            CK(cudaMemcpyAsync(dprob + nprob, &p, sizeof p, cudaMemcpyHostToDevice, s));
+            *slot_out = nprob++;
+            return DL_OK;
+        };
+        const int tiles = static_cast<int>((np / TB) * (np / TB));
+        auto run = [&](int slot_i, GemmEpi epi) -> dl_status {
+            CK(gemm_launch(KIND_TF32, true, TB, epi, dprob + slot_i, 1, tiles, std::min(tiles, ctx->sms), ws.status,
+                           ctx->budget_ns, s));
+            ++launches;
+            ++gemm_launches;
+            return DL_OK;
+        };
+        // A_{k+1} = A_k^2 until ||A_K||_inf^2 <= 1e-5
+        unsigned *nrm = reinterpret_cast<unsigned *>(ws.scal + 30);
+        int K = 0;
+        for (;;) {
+            CK(cudaMemsetAsync(nrm, 0, sizeof(unsigned), s));
+            CK(row_abs_sum_max(A[K], static_cast<int>(np), nrm, s));
+            ++launches;
+            if ((rc = read_scalars(ws, s))) return rc;
+            unsigned nb_ = 0;
+            std::memcpy(&nb_, host_scal(ws) + 30, sizeof nb_);
+            float nk = 0.f;
+            std::memcpy(&nk, &nb_, sizeof nk);
+            if (nk == 0.0f || static_cast<double>(nk) * nk <= 1e-5) break;
+            if (K + 1 > kMaxK) {
+                set_error("same generation S~: ||(sqrt(eps) P)^(2^k)|| did not fall below 3e-3 in %d squarings", kMaxK);
+                return DL_ENOTCONV;
+            }
+            A.push_back(mat("sr_A", K + 1));
+            NA.push_back(mat("sr_NA", K + 1));
+            NEED(A[K + 1] && NA[K + 1]);
+            CK(transpose_f32(A[K], np, static_cast<int>(np), static_cast<int>(np), AT, np, s));
+            int sq = 0;
+            if ((rc = problem(A[K], AT, A[K + 1], EPI_STORE_F32, &sq))) return rc;
+            if ((rc = run(sq, EPI_STORE_F32))) return rc;
+            CK(negate_f32(A[K + 1], NA[K + 1], static_cast<int64_t>(nn), s));
+            launches += 2;
+            ++K;
+        }
+        // the doubling steps as problems: W = X_k A_k^T, then X_k -= (-A_k) (W^T)^T
+        std::vector<int> p1(K), p2(K);
+        for (int k = 0; k < K; ++k) {
+            if ((rc = problem(Xs, A[k], W, EPI_STORE_F32, &p1[k]))) return rc;
+            if ((rc = problem(NA[k], WT, Xs, EPI_SUB_F32, &p2[k]))) return rc;
+        }
+        double best = 0.0;
+        int stall = 0;
+        const int max_iters = ctx->cfg.refine_max_iters > 0 ? ctx->cfg.refine_max_iters : 30;
+        for (;;) {
+            CK(cudaMemsetAsync(slot, 0, sizeof(unsigned long long), s));
+            CK(sg_real_step(ptr, col, n, static_cast<int>(np), eps, Bm, Xd, U, nullptr, Xs, slot, s));  // Xs = R
+            launches += 2;
+            if ((rc = read_scalars(ws, s))) return rc;
+            resid = as_double(host_scal(ws)[32]) / eps;
+            if (resid <= tol) break;
+            if (refine_steps == 0 || resid < 0.5 * best) {
+                best = resid;
+                stall = 0;
+            } else if (++stall >= 2 && best <= 1e-8) {
+                break;  // at the residual's rounding floor
+            }
+            if (refine_steps >= max_iters) {
+                set_error("same generation S~: refinement stopped at max|R|/eps = %.3g after %d steps", resid,
+                          refine_steps);
+                return DL_ENOTCONV;
+            }
+            for (int k = 0; k < K; ++k) {  // Xs <- sum_m (A Xs A^T)-terms: the correction D
+                if ((rc = run(p1[k], EPI_STORE_F32))) return rc;
+                CK(transpose_f32(W, np, static_cast<int>(np), static_cast<int>(np), WT, np, s));
+                ++launches;
+                if ((rc = run(p2[k], EPI_SUB_F32))) return rc;
+            }
+            CK(add_f32_to_f64(Xd, Xs, static_cast<int64_t>(nn), s));
+            ++launches;
+            ++refine_steps;
+        }
+        steps += refine_steps;
+    }
+    tm.mark(3);
+    CK(cudaMemcpy2DAsync(a.out_rtilde, static_cast<size_t>(n) * 8, Xd, static_cast<size_t>(np) * 8,
+                         static_cast<size_t>(n) * 8, n,
+                         a.mem == DL_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+    tm.mark(4);
+    CK(cudaEventSynchronize(ws.ev[4]));  // read before the boolean step reuses the events
+    const double t_ingest = tm.ms(0, 1), t_series = tm.ms(1, 2), t_refine = tm.ms(2, 3), t_real = tm.ms(0, 4);
+    double t_bits = 0.0;
+    int64_t model_ones = -1;
+    unsigned long long guard = 0;
+    if (a.out_bits) {
+        auto *M = static_cast<uint64_t *>(ws.get("sr_bits", np * wp * 8));
+        NEED(M);
+        CK(cudaMemsetAsync(M, 0, np * wp * 8, s));  // the threshold writes rows < n, words < ceil(n/64)
+        CK(cudaMemsetAsync(ws.scal + SC_GUARD, 0, sizeof(unsigned long long), s));
+        const double tau = ctx->cfg.guard_tau > 0 ? ctx->cfg.guard_tau : 1e-30;
+        CK(thresh_pack_f64(Xd, np, n, static_cast<int>(np), tau, M, wp, ws.scal + SC_GUARD, s));
+        ++launches;
+        if ((rc = read_scalars(ws, s))) return rc;
+        guard = host_scal(ws)[SC_GUARD];
+        dl_stats bs{};
+        bool exact = false;
+        SolveArgs b = a;
+        b.path = DL_PATH_AUTO;
+        b.eps = 0.0;
+        if ((rc = sg_iteration(ctx, ws, s, b, &bs, &exact, M))) return rc;
+        if (!exact && (rc = sg_doubling(ctx, ws, s, b, &bs))) return rc;
+        launches += bs.gpu_launches;
+        model_ones = bs.model_ones;
+        t_bits = bs.ms_total;
+        if (st) st->recheck_sweeps = bs.iters;
+    }
+    if (st) {
+        st->path_used = done ? DL_PATH_FP64 : DL_PATH_MIXED;
+        st->eps_used = eps;
+        st->iters = steps;
+        st->final_resid = resid;
+        st->guard_flagged = static_cast<int64_t>(guard);
+        st->model_ones = model_ones;
+        st->ms_factor = t_ingest;
+        st->ms_solve = t_series;
+        st->ms_refine = t_refine;
+        st->ms_epilogue = t_bits;
+        st->ms_total = t_real + t_bits;
+        st->gpu_launches = launches;
+        st->gemm_launches = gemm_launches;
     }
     return DL_OK;
 }

@@ -24,7 +24,7 @@ PATHS = {"auto": 0, "fp64": 1, "mixed": 2, "bool_fp8": 3, "fp8": 3}
 DL_MEM_HOST, DL_MEM_DEVICE = 0, 1
 
 EXPORTED = ["dl_create", "dl_destroy", "dl_last_error", "dl_set_stream", "dl_tc_closure", "dl_tc_closure_bits",
-            "dl_sg_least_model", "dl_compose", "dl_tc_batch", "dl_submit", "dl_poll", "dl_cancel",
+            "dl_sg_least_model", "dl_sg_real", "dl_compose", "dl_tc_batch", "dl_submit", "dl_poll", "dl_cancel",
             "dl_tc_closure_noalloc", "dl_selftest_wait_timeout"]
 NOALLOC_MAX_N = 2048
 
@@ -93,6 +93,8 @@ def lib() -> ctypes.CDLL:
                                              ctypes.POINTER(Stats)]
             L.dl_sg_least_model.argtypes = [vp, i32, vp, vp, ctypes.c_int, f64, f64, ctypes.c_int,
                                             vp, ctypes.POINTER(Stats)]
+            L.dl_sg_real.argtypes = [vp, i32, vp, vp, ctypes.c_int, f64, ctypes.c_int, vp, vp,
+                                     ctypes.POINTER(Stats)]
             L.dl_compose.argtypes = [vp, i32, vp, vp, ctypes.c_int, vp, ctypes.POINTER(Stats)]
             L.dl_tc_batch.argtypes = [vp, i32, vp, vp, ctypes.c_int, vp, ctypes.POINTER(Stats)]
             L.dl_submit.argtypes = [vp, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_uint64)]
@@ -277,6 +279,27 @@ class Context:
         _check(lib().dl_sg_least_model(self._h, n, p, bptr, mem, float(eps), float(thr),
                                        PATHS[path], bp, ctypes.byref(st)))
         return bits, st.as_dict()
+
+    def sg_real(self, P, B=None, eps: float = 0.0, path: str = "auto", bits: bool = True):
+        """Real S~ = eps (B + P S~ P^T) of same generation (Sec. 6.2); returns (S~, bits or
+        None, stats), S~ as float64 in P's memory kind."""
+        p, n, mem, keep = _square_u8(P)
+        bptr, keepb = None, None
+        if B is not None:
+            bptr, nb, memb, keepb = _square_u8(B)
+            if nb != n or memb != mem:
+                raise ValueError("B must match P in size and memory kind")
+        if mem == DL_MEM_DEVICE:
+            import torch
+            x = torch.empty((n, n), dtype=torch.float64, device=keep.device)
+            xp = x.data_ptr()
+        else:
+            x = np.zeros((n, n), dtype=np.float64)
+            xp = x.ctypes.data
+        out, bp = (_alloc_bits(n, mem, keep) if bits else (None, None))
+        st = Stats()
+        _check(lib().dl_sg_real(self._h, n, p, bptr, mem, float(eps), PATHS[path], xp, bp, ctypes.byref(st)))
+        return x, out, st.as_dict()
 
     def compose(self, R1, R2):
         """Bits of min1(R1 R2), the join of Sec. 2; returns (bits, stats)."""
