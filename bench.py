@@ -175,6 +175,48 @@ def bench_sg(ctx, torch, reps: int = 10) -> dict:
             "device_ms": st["ms_total"]}
 
 
+SG_REAL_N = 4096
+
+
+def bench_sg_real(ctx, torch, reps: int = 5) -> dict:
+    """Real S~ = eps (I + P S~ P^T) of same generation on the N = 4096 forest + DAG (seed 5),
+    device-resident input and outputs: the FP64 series on the GPU (exact after depth + 1 steps
+    on this nilpotent P), plus the certified model bits.  Roofline of one series step (one pass
+    of sg_fused_kernel here, at most two parents per node): a step must read the iterate and
+    write the next one, 2 Np^2 x 8 bytes (the kernel reads X a second time for the change)."""
+    from paper_1608_00139_gb300 import inputs
+    p = torch.from_numpy(inputs.forest_dag(SG_REAL_N, 5)).cuda()
+    torch.cuda.synchronize()
+    ctx.sg_real(p)
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        _, _, st = ctx.sg_real(p)
+    ms = (time.perf_counter() - t0) / reps * 1e3
+    npad = (SG_REAL_N + 255) // 256 * 256
+    step_bytes = 2.0 * npad * npad * 8
+    pk = peaks()
+    gbs = st["iters"] * step_bytes / (st["ms_solve"] * 1e-3) / 1e9 if st["ms_solve"] > 0 else None
+    return {"workload": "SG S~ forest+DAG N=4096 seed 5", "ms": ms, "device_ms": st["ms_total"],
+            "path_used": "fp64 series" if st["path_used"] == 1 else "mixed refinement",
+            "series_steps": st["iters"], "final_resid": st["final_resid"], "ms_series": st["ms_solve"],
+            "ms_model_bits": st["ms_epilogue"],
+            "roofline": {"bound": "hbm", "kernel": "sg_fused_kernel (one series step)",
+                         "achieved": gbs, "peak": pk["hbm"], "unit": "GB/s",
+                         "frac": gbs / pk["hbm"] if gbs else None, "bytes_per_step": step_bytes,
+                         "peak_source": pk["source"]}}
+
+
+def cpu_sg_real() -> dict:
+    """The oracle's S~ (FP64 fixpoint series, sparse P) on the same workload, host cores."""
+    import oracle
+    from paper_1608_00139_gb300 import inputs
+    p = inputs.forest_dag(SG_REAL_N, 5)
+    t0 = time.perf_counter()
+    _, it = oracle.sg_stilde_series(p, return_iters=True)
+    return {"ms": (time.perf_counter() - t0) * 1e3, "kind": "oracle", "steps": it,
+            "sample": "the whole N = 4096 workload"}
+
+
 def bench_batch(ctx, torch, reps: int = 10) -> dict:
     """1024 uneven ER closures (N ~ U{32..2048}, mean degree ~ U[1,8], seeds 1000+k), resident
     back to back in one device buffer; each call writes every model to one device buffer."""
@@ -318,6 +360,9 @@ def run_part(args, device: int) -> None:
                 out[name] = {"ms": stm["ms_total"], "ms_factor": stm["ms_factor"], "ms_solve": stm["ms_solve"],
                              "ms_refine": stm["ms_refine"], "refine_steps": stm["iters"],
                              "final_resid": stm["final_resid"]}
+    elif args.part == "sg_real":
+        with dl.Context(device) as ctx:
+            out = bench_sg_real(ctx, torch)
     else:
         with dl.Context(device) as ctx:
             out = bench_sg(ctx, torch) if args.part == "sg" else bench_batch(ctx, torch, reps=max(1, args.steps))
@@ -340,7 +385,7 @@ def main() -> None:
                     help="skip the same-generation, batch and serving measurements")
     ap.add_argument("--serve-seconds", type=float, default=10.0,
                     help="length of the serving stream (the full workload is 60 s)")
-    ap.add_argument("--part", default="all", choices=["all", "sg", "batch", "serving", "mixed"],
+    ap.add_argument("--part", default="all", choices=["all", "sg", "sg_real", "batch", "serving", "mixed"],
                     help="run one secondary measurement alone and print its JSON (for profiling)")
     args = ap.parse_args()
     rank, world, local = dist_env()
@@ -539,6 +584,7 @@ def main() -> None:
             "clocks": clocks}
     if not args.no_extra and rank == 0:
         line["same_generation"] = bench_sg(ctxs[0], torch)
+        line["sg_real"] = bench_sg_real(ctxs[0], torch)
         line["batch"] = bench_batch(ctxs[0], torch)
         line["serving"] = bench_serving(dl, torch, local, args.serve_seconds)
     if pure:
@@ -550,6 +596,8 @@ def main() -> None:
         line["speedup_vs_fp64"] = fp64["ms"] / (ms_step / len(gs))
     if rank == 0 and world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(gs)
+        if "sg_real" in line:
+            line["sg_real"]["cpu_oracle"] = cpu_sg_real()
     if rank == 0:
         print(json.dumps(line), flush=True)
     for c in ctxs:

@@ -184,7 +184,9 @@ DL_API dl_status dl_sg_least_model(dl_ctx *ctx, int32_t n, const uint8_t *P, con
  * DL_PATH_AUTO -- the series, then the refinement if 64 steps did not converge.
  * DL_PATH_BOOL_FP8: DL_EINVAL (no real values).  n is limited to 29000 (a row of S~ in one
  * block's shared memory); DL_ENOTCONV if the series or the refinement does not converge.
- * stats: iters = series steps + refinement steps, final_resid = max|eps (B + P S P^T) - S|/eps,
+ * stats: iters = series steps + refinement steps, final_resid = max|eps (B + P S P^T) - S|/eps
+ * (after the series: a power-of-two bound on the last step's largest change, 0 if it changed
+ * nothing),
  * path_used = DL_PATH_FP64 when the series alone sufficed, else DL_PATH_MIXED.
  */
 DL_API dl_status dl_sg_real(dl_ctx *ctx, int32_t n, const uint8_t *P, const uint8_t *B, dl_mem mem, double eps,

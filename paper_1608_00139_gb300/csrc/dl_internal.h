@@ -208,10 +208,16 @@ int num_sms();
 // ---------------------------------------------------------------------------------------
 // One FP64 step over the CSR of P (np x np row-major buffers, zero outside n x n; B: n x n
 // bytes or NULL for the identity):  U = X P^T, V = eps (B + P U), D = V - X.  Xn (optional)
-// <- V; R (optional) <- D in FP32; *dmax = max |D| as the bit pattern of a non-negative double
-// (zeroed by the caller).  np * 8 bytes of shared memory per block (np <= 29056).
+// <- V; R (optional) <- D in FP32.  *dmax (zeroed by the caller): with R, max |D| as the bit
+// pattern of a non-negative double; without R (a series step, where V >= X), a bound coded as
+// e + 4096 with max D < 2^e, or 0 when nothing changed (integer operations only).  np * 8 bytes
+// of shared memory per block (np <= 29056).
+// fused: one pass that sums X over (parent of i) x (parent of j) pairs, for P with at most 4
+// parents per node and np <= 16384 (sg_real_fused); U is then unused.  dmax may be NULL (no
+// change is measured and X is not read back).
 cudaError_t sg_real_step(const int *ptr, const int *col, int n, int np, double eps, const uint8_t *B, const double *X,
-                         double *U, double *Xn, float *R, unsigned long long *dmax, cudaStream_t s);
+                         double *U, double *Xn, float *R, unsigned long long *dmax, bool fused, cudaStream_t s);
+bool sg_real_fused(int np, unsigned long long max_parents);
 // A = scale P, NA = -A (FP32, np x np, zero padding).
 cudaError_t sg_scaled_p(const uint8_t *P, int n, int np, float scale, float *A, float *NA, cudaStream_t s);
 // *out = max_i sum_j |A[i][j]| as FP32 bits (zeroed by the caller).

@@ -16,6 +16,19 @@ namespace dl {
 
 namespace {
 
+// Bound on the change of a series step without FP64 arithmetic.  The series is monotone in
+// floating point too (every operation is monotone on non-negative values), so v >= x and
+// k = bits(v) - bits(x) >= 0 counts the doubles between them; then v - x < 2^(bitlength(k) +
+// exponent(v) - 1075).  Returned as that power plus 4096 (0: no change), for an integer max.
+__device__ __forceinline__ unsigned long long change_code(double v, double x) {
+    const long long bv = __double_as_longlong(v), bx = __double_as_longlong(x);
+    long long k = bv - bx;
+    if (k == 0) return 0ull;
+    if (k < 0) k = -k;  // not reached by the series; kept as a bound
+    const int ev = static_cast<int>((bv >> 52) & 0x7FF);
+    return static_cast<unsigned long long>((64 - __clzll(k)) + max(ev, 1) - 1075 + 4096);
+}
+
 // U = X P^T:  U[i][j] = sum_{w : P[j][w] = 1} X[i][w].  One block per row i, the row staged in
 // shared memory; rows and columns >= n are zero.
 __global__ void __launch_bounds__(256) sg_xpt_kernel(const int *__restrict__ ptr, const int *__restrict__ col, int n,
@@ -38,7 +51,8 @@ __global__ void __launch_bounds__(256) sg_xpt_kernel(const int *__restrict__ ptr
 
 // V[i][j] = eps (B[i][j] + sum_{y : P[i][y] = 1} U[y][j])  (B = NULL: the identity), and
 // D = V - X.  Xn (optional) <- V (a series step); R (optional, FP32) <- D (the residual).
-// *dmax = max |D|, reduced on the bit patterns of non-negative doubles (integer operations).
+// With R: *dmax = max |D| as the bit pattern of a non-negative double; without: *dmax = the
+// max of change_code(V, X).
 // Grid: x over columns (256 per block), y over rows.
 __global__ void __launch_bounds__(256) sg_pu_kernel(const int *__restrict__ ptr, const int *__restrict__ col, int n,
                                                     int np, double eps, const uint8_t *__restrict__ B,
@@ -57,10 +71,14 @@ __global__ void __launch_bounds__(256) sg_pu_kernel(const int *__restrict__ ptr,
             v = eps * s;
         }
         const int64_t at = static_cast<int64_t>(i) * np + j;
-        const double d = v - X[at];
+        if (R != nullptr) {  // the residual: the real difference
+            const double d = v - X[at];
+            R[at] = static_cast<float>(d);
+            m = static_cast<unsigned long long>(__double_as_longlong(d)) & 0x7FFFFFFFFFFFFFFFull;  // |d|
+        } else {
+            m = change_code(v, X[at]);
+        }
         if (Xn != nullptr) Xn[at] = v;
-        if (R != nullptr) R[at] = static_cast<float>(d);
-        m = static_cast<unsigned long long>(__double_as_longlong(d)) & 0x7FFFFFFFFFFFFFFFull;  // |d|
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
@@ -68,6 +86,79 @@ __global__ void __launch_bounds__(256) sg_pu_kernel(const int *__restrict__ ptr,
         m = other > m ? other : m;
     }
     if ((threadIdx.x & 31) == 0 && m != 0) atomicMax(dmax, m);
+}
+
+constexpr int kFusedThreads = 1024;
+constexpr int kFusedCols = 16;  // columns per thread: np <= 16384
+
+// The same step in one pass when every node has few parents:
+//   V[i][j] = eps ([B_ij] + sum_{y in P_i} sum_{w in P_j} X[y][w]).
+// One block per row i; the rows y of X (the parents of i) go through shared memory one at a
+// time and each thread keeps the sums of its columns j = t + 1024 c in registers.  A sum starts
+// from its first term (no 0 + x) and B's term is added only where it is 1, so a column with one
+// parent pair costs one FP64 multiply.
+__global__ void __launch_bounds__(kFusedThreads)
+    sg_fused_kernel(const int *__restrict__ ptr, const int *__restrict__ col, int n, int np, double eps,
+                    const uint8_t *__restrict__ B, const double *__restrict__ X, double *__restrict__ Xn,
+                    float *__restrict__ R, unsigned long long *dmax) {
+    extern __shared__ double xs[];
+    const int i = blockIdx.x;
+    double acc[kFusedCols];
+    unsigned started = 0;  // bit c: column c's sum has a term
+#pragma unroll
+    for (int c = 0; c < kFusedCols; ++c) acc[c] = 0.0;
+    const int q0 = i < n ? ptr[i] : 0, q1 = i < n ? ptr[i + 1] : 0;
+    for (int q = q0; q < q1; ++q) {  // parents y of i (block-uniform)
+        const double *xr = X + static_cast<int64_t>(col[q]) * np;
+        __syncthreads();
+        for (int t = threadIdx.x; t < np; t += kFusedThreads) xs[t] = xr[t];
+        __syncthreads();
+#pragma unroll
+        for (int c = 0; c < kFusedCols; ++c) {
+            const int j = threadIdx.x + c * kFusedThreads;
+            if (j >= n) break;
+            int w = ptr[j];
+            const int w1 = ptr[j + 1];
+            if (w < w1 && !((started >> c) & 1)) {  // a first term is assigned, not added to 0
+                acc[c] = xs[col[w]];
+                started |= 1u << c;
+                ++w;
+            }
+            for (; w < w1; ++w) acc[c] += xs[col[w]];
+        }
+    }
+    unsigned long long m = 0;
+#pragma unroll
+    for (int c = 0; c < kFusedCols; ++c) {
+        const int j = threadIdx.x + c * kFusedThreads;
+        if (j >= np) break;
+        double v = 0.0;
+        if (i < n && j < n) {
+            const bool b = B != nullptr ? (B[static_cast<int64_t>(i) * n + j] & 1) != 0 : i == j;
+            double s = acc[c];
+            if (b) s = (started >> c) & 1 ? s + 1.0 : 1.0;
+            v = eps * s;
+        }
+        const int64_t at = static_cast<int64_t>(i) * np + j;
+        if (Xn != nullptr) Xn[at] = v;
+        if (R != nullptr) {  // the residual: the real difference
+            const double d = v - X[at];
+            R[at] = static_cast<float>(d);
+            const unsigned long long ad = static_cast<unsigned long long>(__double_as_longlong(d)) & 0x7FFFFFFFFFFFFFFFull;
+            m = ad > m ? ad : m;
+        } else if (dmax != nullptr) {  // a series step: the integer bound
+            const unsigned long long cc = change_code(v, X[at]);
+            m = cc > m ? cc : m;
+        }
+    }
+    if (dmax != nullptr) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            const unsigned long long other = __shfl_xor_sync(0xffffffffu, m, o);
+            m = other > m ? other : m;
+        }
+        if ((threadIdx.x & 31) == 0 && m != 0) atomicMax(dmax, m);
+    }
 }
 
 // A = s P (FP32, np x np, zero padding) and NA = -A.
@@ -142,9 +233,21 @@ unsigned stream_blocks(int64_t count) {
 
 }  // namespace
 
+bool sg_real_fused(int np, unsigned long long max_parents) {
+    return np <= kFusedThreads * kFusedCols && max_parents <= 4;
+}
+
 cudaError_t sg_real_step(const int *ptr, const int *col, int n, int np, double eps, const uint8_t *B, const double *X,
-                         double *U, double *Xn, float *R, unsigned long long *dmax, cudaStream_t s) {
+                         double *U, double *Xn, float *R, unsigned long long *dmax, bool fused, cudaStream_t s) {
     const size_t smem = sizeof(double) * static_cast<size_t>(np);
+    if (fused) {
+        cudaError_t e = cudaFuncSetAttribute(sg_fused_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             static_cast<int>(smem));
+        if (e != cudaSuccess) return e;
+        sg_fused_kernel<<<static_cast<unsigned>(np), kFusedThreads, smem, s>>>(ptr, col, n, np, eps, B, X, Xn, R,
+                                                                              dmax);
+        return cudaGetLastError();
+    }
     cudaError_t e = cudaFuncSetAttribute(sg_xpt_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(smem));
     if (e != cudaSuccess) return e;

@@ -1262,6 +1262,7 @@ dl_status solve_sg_real(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveA
     tm.mark(1);
 
     const double tol = ctx->cfg.refine_tol > 0 ? ctx->cfg.refine_tol : 1e-13;
+    const bool fused = sg_real_fused(static_cast<int>(np), host_scal(ws)[SC_DMAX]);
     unsigned long long *slot = ws.scal + 32;  // per-step max |change|, bit patterns of doubles
     auto as_double = [](unsigned long long b) {
         double d;
@@ -1277,14 +1278,15 @@ dl_status solve_sg_real(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveA
         while (!done && steps < budget) {
             CK(cudaMemsetAsync(slot, 0, kGroup * sizeof(unsigned long long), s));
             for (int k = 0; k < kGroup; ++k) {
-                CK(sg_real_step(ptr, col, n, static_cast<int>(np), eps, Bm, Xd, U, Xn, nullptr, slot + k, s));
+                CK(sg_real_step(ptr, col, n, static_cast<int>(np), eps, Bm, Xd, U, Xn, nullptr, slot + k, fused, s));
                 std::swap(Xd, Xn);
                 launches += 2;
             }
             if ((rc = read_scalars(ws, s))) return rc;
             for (int k = 0; k < kGroup; ++k) {
                 ++steps;
-                resid = as_double(host_scal(ws)[32 + k]) / eps;
+                const unsigned long long code = host_scal(ws)[32 + k];  // max change < 2^(code - 4096)
+                resid = code == 0 ? 0.0 : std::ldexp(1.0, static_cast<int>(code) - 4096) / eps;
                 if (resid <= tol) {
                     done = true;  // the iterates after this step are at least as close
                     break;
@@ -1383,7 +1385,7 @@ dl_status solve_sg_real(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveA
         const int max_iters = ctx->cfg.refine_max_iters > 0 ? ctx->cfg.refine_max_iters : 30;
         for (;;) {
             CK(cudaMemsetAsync(slot, 0, sizeof(unsigned long long), s));
-            CK(sg_real_step(ptr, col, n, static_cast<int>(np), eps, Bm, Xd, U, nullptr, Xs, slot, s));  // Xs = R
+            CK(sg_real_step(ptr, col, n, static_cast<int>(np), eps, Bm, Xd, U, nullptr, Xs, slot, fused, s));  // Xs = R
             launches += 2;
             if ((rc = read_scalars(ws, s))) return rc;
             resid = as_double(host_scal(ws)[32]) / eps;
