@@ -88,34 +88,35 @@ __global__ void __launch_bounds__(256) sg_pu_kernel(const int *__restrict__ ptr,
     if ((threadIdx.x & 31) == 0 && m != 0) atomicMax(dmax, m);
 }
 
-constexpr int kFusedThreads = 1024;
-constexpr int kFusedCols = 16;  // columns per thread: np <= 16384
+constexpr int kFusedMaxNp = 16384;  // 1024 threads x 16 columns
 
 // The same step in one pass when every node has few parents:
 //   V[i][j] = eps ([B_ij] + sum_{y in P_i} sum_{w in P_j} X[y][w]).
 // One block per row i; the rows y of X (the parents of i) go through shared memory one at a
-// time and each thread keeps the sums of its columns j = t + 1024 c in registers.  A sum starts
+// time and each thread keeps the sums of its columns j = t + THREADS c in registers (512 x 8
+// up to np = 4096, two blocks per SM; else 1024 x 16).  A sum starts
 // from its first term (no 0 + x) and B's term is added only where it is 1, so a column with one
 // parent pair costs one FP64 multiply.
-__global__ void __launch_bounds__(kFusedThreads)
+template <int THREADS, int COLS>
+__global__ void __launch_bounds__(THREADS)
     sg_fused_kernel(const int *__restrict__ ptr, const int *__restrict__ col, int n, int np, double eps,
                     const uint8_t *__restrict__ B, const double *__restrict__ X, double *__restrict__ Xn,
                     float *__restrict__ R, unsigned long long *dmax) {
     extern __shared__ double xs[];
     const int i = blockIdx.x;
-    double acc[kFusedCols];
+    double acc[COLS];
     unsigned started = 0;  // bit c: column c's sum has a term
 #pragma unroll
-    for (int c = 0; c < kFusedCols; ++c) acc[c] = 0.0;
+    for (int c = 0; c < COLS; ++c) acc[c] = 0.0;
     const int q0 = i < n ? ptr[i] : 0, q1 = i < n ? ptr[i + 1] : 0;
     for (int q = q0; q < q1; ++q) {  // parents y of i (block-uniform)
         const double *xr = X + static_cast<int64_t>(col[q]) * np;
         __syncthreads();
-        for (int t = threadIdx.x; t < np; t += kFusedThreads) xs[t] = xr[t];
+        for (int t = threadIdx.x; t < np; t += THREADS) xs[t] = xr[t];
         __syncthreads();
 #pragma unroll
-        for (int c = 0; c < kFusedCols; ++c) {
-            const int j = threadIdx.x + c * kFusedThreads;
+        for (int c = 0; c < COLS; ++c) {
+            const int j = threadIdx.x + c * THREADS;
             if (j >= n) break;
             int w = ptr[j];
             const int w1 = ptr[j + 1];
@@ -129,8 +130,8 @@ __global__ void __launch_bounds__(kFusedThreads)
     }
     unsigned long long m = 0;
 #pragma unroll
-    for (int c = 0; c < kFusedCols; ++c) {
-        const int j = threadIdx.x + c * kFusedThreads;
+    for (int c = 0; c < COLS; ++c) {
+        const int j = threadIdx.x + c * THREADS;
         if (j >= np) break;
         double v = 0.0;
         if (i < n && j < n) {
@@ -234,18 +235,25 @@ unsigned stream_blocks(int64_t count) {
 }  // namespace
 
 bool sg_real_fused(int np, unsigned long long max_parents) {
-    return np <= kFusedThreads * kFusedCols && max_parents <= 4;
+    return np <= kFusedMaxNp && max_parents <= 4;
 }
 
 cudaError_t sg_real_step(const int *ptr, const int *col, int n, int np, double eps, const uint8_t *B, const double *X,
                          double *U, double *Xn, float *R, unsigned long long *dmax, bool fused, cudaStream_t s) {
     const size_t smem = sizeof(double) * static_cast<size_t>(np);
-    if (fused) {
-        cudaError_t e = cudaFuncSetAttribute(sg_fused_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    if (fused && np <= 4096) {
+        cudaError_t e = cudaFuncSetAttribute(sg_fused_kernel<512, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              static_cast<int>(smem));
         if (e != cudaSuccess) return e;
-        sg_fused_kernel<<<static_cast<unsigned>(np), kFusedThreads, smem, s>>>(ptr, col, n, np, eps, B, X, Xn, R,
-                                                                              dmax);
+        sg_fused_kernel<512, 8><<<static_cast<unsigned>(np), 512, smem, s>>>(ptr, col, n, np, eps, B, X, Xn, R, dmax);
+        return cudaGetLastError();
+    }
+    if (fused) {
+        cudaError_t e = cudaFuncSetAttribute(sg_fused_kernel<1024, 16>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             static_cast<int>(smem));
+        if (e != cudaSuccess) return e;
+        sg_fused_kernel<1024, 16><<<static_cast<unsigned>(np), 1024, smem, s>>>(ptr, col, n, np, eps, B, X, Xn, R,
+                                                                               dmax);
         return cudaGetLastError();
     }
     cudaError_t e = cudaFuncSetAttribute(sg_xpt_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
