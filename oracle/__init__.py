@@ -13,6 +13,7 @@ Functions (passages they follow are cited in ``oracle.c``):
   sg_model(P, B)         least model of the same-generation program (Sec. 6.2), semi-naive
   tc_eps(E), sg_eps(P)   the paper's default epsilons (Sec. 4, Sec. 6.1, Sec. 6.2)
   sg_stilde_kron, sg_stilde_series   the real S~ of same generation (sg_real.py, numpy FP64)
+  tail_model, tail_rtilde, tail_eps  one equation of the tail recursive class (tail.py)
 Bit matrices: ceil(n/64) uint64 words per row, bit j%64 of word j//64, LSB first.
 """
 from __future__ import annotations
@@ -25,6 +26,7 @@ import threading
 import numpy as np
 
 from .sg_real import sg_stilde_kron, sg_stilde_series  # noqa: F401  (numpy FP64, no C part)
+from .tail import tail_eps, tail_model, tail_rtilde  # noqa: F401  (numpy FP64, no C part)
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "oracle.c")

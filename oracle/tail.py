@@ -1,0 +1,56 @@
+"""Least solutions of the tail recursive class (Sec. 5.1, eq. matrixeq:trec) for one equation:
+
+    R~ = eps (A + B0 R~),   i.e.  R~ = (I - eps B0)^-1 eps A,
+
+where A stands for the whole non-recursive part A_1 + B_1 R~_{j_1} + ... + B_q R~_{j_q} once the
+lower equations are solved and substituted, and B0 is the coefficient of the recursive
+occurrence.  The model is the least R with R = min1(A + B0 R).  Transitive closure is the case
+A = B0 = E (Sec. 3).
+
+TEST INFRASTRUCTURE ONLY, like the rest of ``oracle/``.  Plain numpy / FP64, no blocking.
+
+  tail_model(B0, A)          the least model by semi-naive evaluation of R = A u B0 R: the new
+                             facts of a round are the B0-predecessors of the previous round's
+                             new facts, minus what is known (the T_P fixpoint of Sec. 2)
+  tail_rtilde(B0, A, eps)    R~ by one dense FP64 solve of (I - eps B0) X = eps A
+  tail_eps(B0)               the default eps = 1 / (1 + ||B0||_inf), inside the uniqueness
+                             condition eps < 1 / ||B0||_inf of Sec. 5.1
+"""
+from __future__ import annotations
+
+import numpy as np
+
+
+def tail_eps(b0: np.ndarray) -> float:
+    b0 = np.asarray(b0)
+    d = float(b0.sum(axis=1).max()) if b0.size else 0.0
+    return 1.0 / (1.0 + d)
+
+
+def tail_model(b0: np.ndarray, a: np.ndarray) -> np.ndarray:
+    """Least R with R = A u B0 R, as a dense 0/1 uint8 matrix."""
+    b0 = np.asarray(b0, dtype=np.uint8) != 0
+    a = np.asarray(a, dtype=np.uint8) != 0
+    if b0.shape != a.shape or b0.ndim != 2 or b0.shape[0] != b0.shape[1]:
+        raise ValueError("B0 and A must be square and of one shape")
+    r = a.copy()
+    delta = a.copy()
+    b0i = b0.astype(np.int64)
+    while delta.any():
+        # (x, z) is derived when x -> y in B0 and (y, z) is a new fact
+        new = (b0i @ delta.astype(np.int64)) > 0
+        delta = new & ~r
+        r |= delta
+    return r.astype(np.uint8)
+
+
+def tail_rtilde(b0: np.ndarray, a: np.ndarray, eps: float | None = None) -> np.ndarray:
+    """R~ = (I - eps B0)^-1 eps A in FP64 (one dense solve)."""
+    b0 = np.asarray(b0, dtype=np.float64)
+    a = np.asarray(a, dtype=np.float64)
+    n = b0.shape[0]
+    if eps is None:
+        eps = tail_eps(b0)
+    if n == 0:
+        return np.zeros((0, 0))
+    return np.linalg.solve(np.eye(n) - eps * b0, eps * a)
