@@ -169,6 +169,27 @@ DL_API dl_status dl_sg_least_model(dl_ctx *ctx, int32_t n, const uint8_t *P, con
                             uint64_t *out_bits, dl_stats *stats);
 
 /*
+ * One equation of the tail recursive class (Sec. 5.1, eq. matrixeq:trec), the generalisation
+ * of transitive closure to clauses r(x,z) <- s_1(x,y_1), ..., s_n(y_{n-1},z) and
+ * r(x,z) <- s_1(x,y_1), ..., s_n(y_{n-1},y), t(y,z):
+ *     R~ = eps (A + B0 R~),   R~ = (I - eps B0)^-1 eps A,
+ * with the equation's non-recursive part A = A_1 + B_1 R_{j_1} + ... + B_q R_{j_q} already
+ * formed from the lower equations (their models combined with dl_compose: the model depends
+ * only on which entries are positive).  B0, A: n x n 0/1.  out_bits (required): the model, the
+ * least R with R = min1(A + B0 R), i.e. min1((I + B0^+) A) with B0^+ the transitive closure.
+ * eps <= 0 selects 1/(1 + ||B0||_inf) (inside the paper's uniqueness condition eps < 1/||B0||);
+ * otherwise 0 < eps <= that value, else DL_EINVAL.  thr must be 0.  Paths: DL_PATH_AUTO and
+ * DL_PATH_BOOL_FP8 give the model (the closure of B0 by that path, then one FP8 boolean
+ * product); DL_PATH_FP64 and DL_PATH_MIXED also give R~ in out_rtilde (n x n doubles, optional)
+ * by the closure's real paths with the right-hand side eps A, and report in rows_rechecked the
+ * model entries that X > 0 missed (underflow; X > 0 never holds outside the model).
+ * A = B0 = E is the closure program (dl_tc_closure).
+ */
+DL_API dl_status dl_tail_recursive(dl_ctx *ctx, int32_t n, const uint8_t *B0, const uint8_t *A, dl_mem mem,
+                            double eps, double thr, dl_path path, uint64_t *out_bits, double *out_rtilde,
+                            dl_stats *stats);
+
+/*
  * The real least solution of the same-generation equation (Sec. 6.2; the two-sided class of
  * Sec. 5.3, a discrete Stein/Sylvester equation):
  *     S~ = eps (B + P S~ P^T),

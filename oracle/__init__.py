@@ -26,7 +26,7 @@ import threading
 import numpy as np
 
 from .sg_real import sg_stilde_kron, sg_stilde_series  # noqa: F401  (numpy FP64, no C part)
-from .tail import tail_eps, tail_model, tail_rtilde  # noqa: F401  (numpy FP64, no C part)
+from .tail import tail_eps, tail_model, tail_model_rows, tail_rtilde  # noqa: F401  (numpy FP64)
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "oracle.c")

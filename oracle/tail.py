@@ -12,6 +12,9 @@ TEST INFRASTRUCTURE ONLY, like the rest of ``oracle/``.  Plain numpy / FP64, no 
   tail_model(B0, A)          the least model by semi-naive evaluation of R = A u B0 R: the new
                              facts of a round are the B0-predecessors of the previous round's
                              new facts, minus what is known (the T_P fixpoint of Sec. 2)
+  tail_model_rows(B0, A, rows)  the model's rows by definition, for sampling at large N: row x is
+                             the union of A's rows over the nodes reachable from x in zero or more
+                             B0 steps (breadth-first search)
   tail_rtilde(B0, A, eps)    R~ by one dense FP64 solve of (I - eps B0) X = eps A
   tail_eps(B0)               the default eps = 1 / (1 + ||B0||_inf), inside the uniqueness
                              condition eps < 1 / ||B0||_inf of Sec. 5.1
@@ -35,13 +38,36 @@ def tail_model(b0: np.ndarray, a: np.ndarray) -> np.ndarray:
         raise ValueError("B0 and A must be square and of one shape")
     r = a.copy()
     delta = a.copy()
-    b0i = b0.astype(np.int64)
+    b0f = b0.astype(np.float64)  # counts of 0/1 products, exact in FP64
     while delta.any():
         # (x, z) is derived when x -> y in B0 and (y, z) is a new fact
-        new = (b0i @ delta.astype(np.int64)) > 0
+        new = (b0f @ delta.astype(np.float64)) > 0
         delta = new & ~r
         r |= delta
     return r.astype(np.uint8)
+
+
+def tail_model_rows(b0: np.ndarray, a: np.ndarray, rows) -> np.ndarray:
+    """Rows of the least model (dense 0/1, len(rows) x n), each from a breadth-first search."""
+    b0 = np.asarray(b0, dtype=np.uint8)
+    a = np.asarray(a, dtype=np.uint8)
+    n = b0.shape[0]
+    succ = [np.nonzero(b0[y])[0] for y in range(n)]
+    out = np.zeros((len(rows), n), dtype=np.uint8)
+    for t, x in enumerate(rows):
+        seen = np.zeros(n, dtype=bool)
+        seen[x] = True
+        frontier = [x]
+        while frontier:
+            nxt = []
+            for y in frontier:
+                for z in succ[y]:
+                    if not seen[z]:
+                        seen[z] = True
+                        nxt.append(z)
+            frontier = nxt
+        out[t] = (a[seen].max(axis=0) if seen.any() else 0)
+    return out
 
 
 def tail_rtilde(b0: np.ndarray, a: np.ndarray, eps: float | None = None) -> np.ndarray:

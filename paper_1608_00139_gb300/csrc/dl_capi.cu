@@ -261,6 +261,35 @@ dl_status dl_sg_least_model(dl_ctx *ctx, int32_t n, const uint8_t *P, const uint
     });
 }
 
+dl_status dl_tail_recursive(dl_ctx *ctx, int32_t n, const uint8_t *B0, const uint8_t *A, dl_mem mem, double eps,
+                            double thr, dl_path path, uint64_t *out_bits, double *out_rtilde, dl_stats *stats) {
+    clear_error();
+    GUARD_CTX(ctx);
+    if (stats) std::memset(stats, 0, sizeof(*stats));
+    if (n < 0 || !valid_mem(mem)) {
+        set_error("bad n (%d) or memory kind", n);
+        return DL_EINVAL;
+    }
+    if (n == 0) return DL_OK;
+    if (!B0 || !A || !out_bits) {
+        set_error("B0, A and out_bits must not be NULL");
+        return DL_EINVAL;
+    }
+    SolveArgs a;
+    a.n = n;
+    a.E = B0;
+    a.E2 = A;
+    a.mem = mem;
+    a.eps = eps;
+    a.thr = thr;
+    a.path = path;
+    a.out_bits = out_bits;
+    a.out_rtilde = out_rtilde;
+    return run_sync(ctx, stats, [&](Workspace &ws, cudaStream_t s, dl_stats *st) {
+        return solve_tail(ctx, ws, s, a, st);
+    });
+}
+
 dl_status dl_sg_real(dl_ctx *ctx, int32_t n, const uint8_t *P, const uint8_t *B, dl_mem mem, double eps,
                      dl_path path, double *out_stilde, uint64_t *out_bits, dl_stats *stats) {
     clear_error();

@@ -86,6 +86,9 @@ struct SolveArgs {
     const uint8_t *E = nullptr;   // closure: E; same generation: P; compose: R1
     const uint64_t *E_bits = nullptr;  // closure: E bit-packed (n rows of ceil(n/64) words) instead
     bool e_device = false;        // E is on the device whatever mem says (unpacked from E_bits)
+    const uint8_t *rhs = nullptr;  // tail recursive class: the right-hand side A of
+                                   // X = eps (A + E X), a device pointer (NULL: A = E)
+    bool skip_recheck = false;     // real paths: leave X > 0 in the bits unchecked, count its ones
     const uint8_t *E2 = nullptr;  // same generation: B (may be null); compose: R2
     dl_mem mem = DL_MEM_HOST;
     double eps = 0.0;
@@ -98,6 +101,9 @@ struct SolveArgs {
 // Drivers: run on (ws, stream); return a dl_status and fill stats.
 dl_status solve_tc(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &a, dl_stats *st);
 dl_status solve_sg(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &a, dl_stats *st);
+// One equation of the tail recursive class: E = B0 (recursive coefficient), E2 = A (the
+// non-recursive part); bits of the model, R~ into a.out_rtilde on the real paths.
+dl_status solve_tail(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &a, dl_stats *st);
 // The real S~ of same generation into a.out_rtilde (n x n doubles); bits optional.
 dl_status solve_sg_real(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &a, dl_stats *st);
 dl_status solve_compose(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &a,

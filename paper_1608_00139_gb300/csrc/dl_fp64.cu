@@ -28,7 +28,7 @@ namespace {
 
 constexpr int B = 64;  // block size of the blocked elimination
 
-__global__ void build_kernel(const uint8_t *__restrict__ E, int n, int np, double eps,
+__global__ void build_kernel(const uint8_t *__restrict__ E, const uint8_t *__restrict__ A, int n, int np, double eps,
                              double *__restrict__ G, int64_t ldg) {
     const int64_t row = blockIdx.y;
     for (int64_t c = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; c < 2 * np;
@@ -39,7 +39,7 @@ __global__ void build_kernel(const uint8_t *__restrict__ E, int n, int np, doubl
             v = (c == row ? 1.0 : 0.0) - e;
         } else {
             const int64_t cc = c - np;
-            v = (row < n && cc < n && E[row * n + cc]) ? eps : 0.0;
+            v = (row < n && cc < n && A[row * n + cc]) ? eps : 0.0;
         }
         G[row * ldg + c] = v;
     }
@@ -203,11 +203,11 @@ __global__ void thresh_pack_kernel(const double *__restrict__ X, int64_t ldx, in
 
 }  // namespace
 
-cudaError_t fp64_build(const uint8_t *E, int n, int np, double eps, double *G, int64_t ldg,
+cudaError_t fp64_build(const uint8_t *E, const uint8_t *A, int n, int np, double eps, double *G, int64_t ldg,
                        cudaStream_t s) {
     dim3 grid(static_cast<unsigned>((2 * np + 255) / 256 < 64 ? (2 * np + 255) / 256 : 64),
               static_cast<unsigned>(np));
-    build_kernel<<<grid, 256, 0, s>>>(E, n, np, eps, G, ldg);
+    build_kernel<<<grid, 256, 0, s>>>(E, A, n, np, eps, G, ldg);
     return cudaGetLastError();
 }
 

@@ -194,7 +194,8 @@ cudaError_t exclusive_scan_large(const int *cnt, int n, int *out, int *scratch, 
 // ---------------------------------------------------------------------------------------
 // FP64 path (dl_fp64.cu)
 // ---------------------------------------------------------------------------------------
-cudaError_t fp64_build(const uint8_t *E, int n, int np, double eps, double *G, int64_t ldg,
+// G = [I - eps E | eps A] (np x 2np doubles, zero/identity padding; A = E for the closure).
+cudaError_t fp64_build(const uint8_t *E, const uint8_t *A, int n, int np, double eps, double *G, int64_t ldg,
                        cudaStream_t s);
 cudaError_t fp64_solve(double *G, int64_t ldg, int np, int *launches, cudaStream_t s);
 // threshold X > 0 into bits, count guard-band entries (|X| <= tau or X < 0)

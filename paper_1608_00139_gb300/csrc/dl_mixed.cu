@@ -306,7 +306,8 @@ __device__ __forceinline__ long long fixed_of(long long bits, int e) {
 }
 
 // Residual of the transposed system for G rows j of Z per block (the rows share each read of
-// the CSR):  R^T[j][i] = eps * sum_{k in succ(i)} (Z[j][k] + [k = j]) - Z[j][i],  stored as FP32
+// the CSR):  R^T[j][i] = eps * sum_{k in succ(i)} (Z[j][k] + [k = j]) - Z[j][i]  (right-hand side
+// eps E; with At, the bytes of A^T, the term [k = j] becomes A[i][j]: right-hand side eps A),  stored as FP32
 // (right-hand side of the correction solve); max |R| -> *rmax.  The sums are exact in 64-bit
 // fixed point: row j sits in shared memory as round((Z[j][k] + [k = j]) 2^e_j), e_j chosen from
 // the row's largest exponent and 2^deg_bits >= ||E||_inf so that no sum reaches 2^62.  Each
@@ -315,7 +316,8 @@ __device__ __forceinline__ long long fixed_of(long long bits, int e) {
 template <int G>
 __global__ void __launch_bounds__(1024, 1)
     residual_fixed_kernel(const int *__restrict__ ptr, const int *__restrict__ col, int n, int np, int deg_bits,
-                          double eps, const double *__restrict__ Z, float *__restrict__ R, unsigned long long *rmax) {
+                          double eps, const double *__restrict__ Z, float *__restrict__ R, unsigned long long *rmax,
+                          const uint8_t *__restrict__ At) {
     extern __shared__ long long zi[];  // G rows of np entries
     __shared__ int ex_max[G];
     const int j0 = blockIdx.x * G;
@@ -351,7 +353,7 @@ __global__ void __launch_bounds__(1024, 1)
     for (int g = 0; g < G; ++g)
         for (int k = threadIdx.x; k < np; k += blockDim.x) zi[g * np + k] = fixed_of(zi[g * np + k], e[g]);
     __syncthreads();
-    if (threadIdx.x < G) {  // the eps E[i][j] term, as k = j
+    if (threadIdx.x < G && At == nullptr) {  // the eps E[i][j] term, as k = j
         const int g = threadIdx.x, j = j0 + g;
         if (j < n) zi[g * np + j] += 1ll << e[g];
     }
@@ -365,6 +367,13 @@ __global__ void __launch_bounds__(1024, 1)
                 const int c = col[q];
 #pragma unroll
                 for (int g = 0; g < G; ++g) sum[g] += zi[g * np + c];
+            }
+            if (At != nullptr) {  // a general right-hand side: the eps A[i][j] term from A^T's row j
+#pragma unroll
+                for (int g = 0; g < G; ++g) {
+                    const int j = j0 + g;
+                    if (j < n && At[static_cast<int64_t>(j) * n + i]) sum[g] += 1ll << e[g];
+                }
             }
         }
 #pragma unroll
@@ -463,9 +472,20 @@ dl_status tc_mixed(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &
         build_a_kernel<<<grid, 256, 0, s>>>(E, n, N, static_cast<float>(eps), A32);
         MCK(cudaGetLastError());
         dim3 tgrid(static_cast<unsigned>(np / TT), static_cast<unsigned>(np / TT));
-        build_zt_kernel<<<tgrid, dim3(TT, 8), 0, s>>>(E, n, N, static_cast<float>(eps), Z32);
+        build_zt_kernel<<<tgrid, dim3(TT, 8), 0, s>>>(a.rhs ? a.rhs : E, n, N, static_cast<float>(eps), Z32);
         MCK(cudaGetLastError());
         launches += 2;
+    }
+    // a general right-hand side A: its transpose (bytes) for the residual's A[i][j] terms
+    uint8_t *At = nullptr;
+    if (a.rhs) {
+        At = static_cast<uint8_t *>(ws.get("mx_At", std::max<size_t>(static_cast<size_t>(n) * n, 16)));
+        if (!At) {
+            set_error("mixed path: device allocation failed (A^T)");
+            return DL_ENOMEM;
+        }
+        MCK(transpose(a.rhs, n, n, n, At, n, s));
+        ++launches;
     }
     // CSR of E for the residual
     MCK(csr_build(E, n, csr_cnt, csr_ptr, s));
@@ -699,21 +719,21 @@ dl_status tc_mixed(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &
                                               static_cast<int>(res_smem))) != cudaSuccess)
                     return e;
                 residual_fixed_kernel<3><<<grid, 1024, res_smem, s>>>(csr_ptr, csr_col, n, N, deg_bits, eps, Z64, Z32,
-                                                                     rmax_p);
+                                                                     rmax_p, At);
                 break;
             case 2:
                 if ((e = cudaFuncSetAttribute(residual_fixed_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                               static_cast<int>(res_smem))) != cudaSuccess)
                     return e;
                 residual_fixed_kernel<2><<<grid, 1024, res_smem, s>>>(csr_ptr, csr_col, n, N, deg_bits, eps, Z64, Z32,
-                                                                     rmax_p);
+                                                                     rmax_p, At);
                 break;
             default:
                 if ((e = cudaFuncSetAttribute(residual_fixed_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                               static_cast<int>(res_smem))) != cudaSuccess)
                     return e;
                 residual_fixed_kernel<1><<<grid, 1024, res_smem, s>>>(csr_ptr, csr_col, n, N, deg_bits, eps, Z64, Z32,
-                                                                     rmax_p);
+                                                                     rmax_p, At);
         }
         return cudaGetLastError();
     };

@@ -669,6 +669,35 @@ dl_status tc_auto(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &a
     return DL_OK;
 }
 
+// After X > 0 went into mbits: the exact recheck (in-place sweeps until the bits satisfy
+// M = min1(E + E M)), or with a.skip_recheck only the count of ones (SC_ONES).
+dl_status recheck_bits(Workspace &ws, cudaStream_t s, const SolveArgs &a, const uint8_t *E, int32_t n, int64_t wp,
+                       uint64_t *mbits, int *sweeps, unsigned long long *corrected, int *launches) {
+    dl_status rc;
+    *sweeps = 0;
+    *corrected = 0;
+    if (a.skip_recheck) {
+        CK(cudaMemsetAsync(ws.scal + SC_ONES, 0, sizeof(unsigned long long), s));
+        CK(bits_count(mbits, n, wp, ws.scal + SC_ONES, s));
+        ++*launches;
+        return read_scalars(ws, s);
+    }
+    for (;;) {
+        CK(cudaMemsetAsync(ws.scal + SC_VIOL, 0, 2 * sizeof(unsigned long long), s));
+        CK(bits_sweep(E, n, n, mbits, mbits, wp, 1, 0, ws.scal + SC_VIOL, ws.scal + SC_ONES, s));
+        ++*launches;
+        ++*sweeps;
+        if ((rc = read_scalars(ws, s))) return rc;
+        const unsigned long long v = host_scal(ws)[SC_VIOL];
+        if (v == 0) return DL_OK;
+        *corrected += v;
+        if (*sweeps > n + 1) {
+            set_error("recheck did not converge");
+            return DL_ENOTCONV;
+        }
+    }
+}
+
 dl_status tc_fp64(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &a, dl_stats *st) {
     const int32_t n = a.n;
     const int64_t np = round_up(std::max<int64_t>(n, 1), 64);
@@ -695,7 +724,7 @@ dl_status tc_fp64(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &a
     double eps = 0;
     if ((rc = choose_eps(a.eps, 1.0 / (1.0 + static_cast<double>(dmax)), "Lemma 1 (1/(1+||E||))", &eps)))
         return rc;
-    CK(fp64_build(E, n, static_cast<int>(np), eps, G, ldg, s));
+    CK(fp64_build(E, a.rhs ? a.rhs : E, n, static_cast<int>(np), eps, G, ldg, s));
     ++launches;
     tm.mark(1);
     CK(fp64_solve(G, ldg, static_cast<int>(np), &launches, s));
@@ -707,21 +736,8 @@ dl_status tc_fp64(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &a
     // recheck: in-place sweeps until the model satisfies R2 = min1(E + E R2)
     int sweeps = 0;
     unsigned long long corrected = 0;
-    for (;;) {
-        CK(cudaMemsetAsync(ws.scal + SC_VIOL, 0, 2 * sizeof(unsigned long long), s));
-        CK(bits_sweep(E, n, n, mbits, mbits, wp, 1, 0, ws.scal + SC_VIOL, ws.scal + SC_ONES, s));
-        ++launches;
-        ++sweeps;
-        if ((rc = read_scalars(ws, s))) return rc;
-        const unsigned long long v = host_scal(ws)[SC_VIOL];
-        if (v == 0) break;
-        corrected += v;
-        if (sweeps > n + 1) {
-            set_error("recheck did not converge");
-            return DL_ENOTCONV;
-        }
-    }
-    if ((rc = write_bits(s, mbits, wp, a.out_bits, n, a.mem))) return rc;
+    if ((rc = recheck_bits(ws, s, a, E, n, wp, mbits, &sweeps, &corrected, &launches))) return rc;
+    if (a.out_bits && (rc = write_bits(s, mbits, wp, a.out_bits, n, a.mem))) return rc;
     if (a.out_rtilde) {
         CK(cudaMemcpy2DAsync(a.out_rtilde, static_cast<size_t>(n) * 8, X, ldg * 8,
                              static_cast<size_t>(n) * 8, n,
@@ -780,21 +796,8 @@ dl_status tc_mixed_path(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveA
     ++launches;
     int sweeps = 0;
     unsigned long long corrected = 0;
-    for (;;) {
-        CK(cudaMemsetAsync(ws.scal + SC_VIOL, 0, 2 * sizeof(unsigned long long), s));
-        CK(bits_sweep(E, n, n, mbits, mbits, wp, 1, 0, ws.scal + SC_VIOL, ws.scal + SC_ONES, s));
-        ++launches;
-        ++sweeps;
-        if ((rc = read_scalars(ws, s))) return rc;
-        const unsigned long long v = host_scal(ws)[SC_VIOL];
-        if (v == 0) break;
-        corrected += v;
-        if (sweeps > n + 1) {
-            set_error("recheck did not converge");
-            return DL_ENOTCONV;
-        }
-    }
-    if ((rc = write_bits(s, mbits, wp, a.out_bits, n, a.mem))) return rc;
+    if ((rc = recheck_bits(ws, s, a, E, n, wp, mbits, &sweeps, &corrected, &launches))) return rc;
+    if (a.out_bits && (rc = write_bits(s, mbits, wp, a.out_bits, n, a.mem))) return rc;
     if (a.out_rtilde) {
         CK(cudaMemcpy2DAsync(a.out_rtilde, static_cast<size_t>(n) * 8, X, np * 8, static_cast<size_t>(n) * 8, n,
                              a.mem == DL_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
@@ -1143,9 +1146,9 @@ dl_status solve_compose(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveA
     int launches = 0;
     tm.mark(0);
     const uint8_t *R1 = nullptr, *R2 = nullptr;
-    dl_status rc = stage_input(ws, s, a.E, n, a.mem, "in0", &R1);
+    dl_status rc = stage_input(ws, s, a.E, n, in_mem(a), "in0", &R1);
     if (rc) return rc;
-    if ((rc = stage_input(ws, s, a.E2, n, a.mem, "in1", &R2))) return rc;
+    if ((rc = stage_input(ws, s, a.E2, n, in_mem(a), "in1", &R2))) return rc;
     auto *A8 = static_cast<uint8_t *>(ws.get("c0", np * np));
     auto *B8 = static_cast<uint8_t *>(ws.get("c1", np * np));
     auto *bits = static_cast<uint64_t *>(ws.get("bits0", np * wp * 8));
@@ -1459,6 +1462,91 @@ dl_status solve_sg_real(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveA
         st->ms_total = t_real + t_bits;
         st->gpu_launches = launches;
         st->gemm_launches = gemm_launches;
+    }
+    return DL_OK;
+}
+
+// One equation of the tail recursive class (Sec. 5.1, eq. matrixeq:trec), its non-recursive
+// part A already formed from the lower equations' solutions:
+//     R~ = eps (A + B0 R~),  R~ = (I - eps B0)^-1 eps A,
+// and its model, the least R with R = min1(A + B0 R) = min1((I + B0^+) A), B0^+ the transitive
+// closure of B0 (a row of R is A's rows at every node reachable in zero or more B0 steps).
+//  * the model: the closure of B0 (AUTO, or the squarings-only path), the identity added, one
+//    boolean product with A on the FP8 tensor cores;
+//  * R~ (DL_PATH_FP64 / DL_PATH_MIXED): the closure's real paths with the right-hand side eps A.
+//    Exact zeros stay exact (an M-matrix and a non-negative right-hand side), so X > 0 lies
+//    inside the model; the model's entries missing from it (underflow) are rows_rechecked.
+dl_status solve_tail(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &a, dl_stats *st) {
+    if (a.thr != 0.0) {
+        set_error("thr must be 0: the model is R~ > 0");
+        return DL_EINVAL;
+    }
+    const bool real = a.path == DL_PATH_FP64 || a.path == DL_PATH_MIXED;
+    if (!real && a.path != DL_PATH_AUTO && a.path != DL_PATH_BOOL_FP8) {
+        set_error("unknown path %d", static_cast<int>(a.path));
+        return DL_EINVAL;
+    }
+    if (a.out_rtilde && !real) {
+        set_error("the boolean paths compute no real-valued R~; use DL_PATH_FP64 or DL_PATH_MIXED");
+        return DL_EINVAL;
+    }
+    const int32_t n = a.n;
+    const int64_t w = (n + 63) / 64;
+    const uint8_t *B0 = nullptr, *A = nullptr;
+    dl_status rc = stage_input(ws, s, a.E, n, a.mem, "tr_b0", &B0);
+    if (rc) return rc;
+    if ((rc = stage_input(ws, s, a.E2, n, a.mem, "tr_a", &A))) return rc;
+    dl_stats sr{}, sc{}, sm{};
+    int64_t thresh_ones = -1;
+    if (real) {  // R~ with the right-hand side eps A; the model comes from the boolean route
+        SolveArgs r = a;
+        r.E = B0;
+        r.E2 = nullptr;
+        r.e_device = true;
+        r.rhs = A;
+        r.out_bits = nullptr;
+        r.skip_recheck = true;
+        if ((rc = solve_tc(ctx, ws, s, r, &sr))) return rc;
+        thresh_ones = sr.model_ones;
+    }
+    auto *cl = static_cast<uint64_t *>(ws.get("tr_cl", static_cast<size_t>(n) * w * 8));
+    auto *clb = static_cast<uint8_t *>(ws.get("tr_clb", std::max<size_t>(static_cast<size_t>(n) * n, 16)));
+    NEED(cl && clb);
+    SolveArgs c;
+    c.n = n;
+    c.E = B0;
+    c.mem = DL_MEM_DEVICE;
+    c.eps = a.eps;
+    c.path = a.path == DL_PATH_BOOL_FP8 ? DL_PATH_BOOL_FP8 : DL_PATH_AUTO;
+    c.out_bits = cl;
+    if ((rc = solve_tc(ctx, ws, s, c, &sc))) return rc;  // B0^+ (and eps checked against ||B0||)
+    CK(unpack_bits_u8(cl, n, clb, ws.status, s));
+    CK(cudaMemset2DAsync(clb, static_cast<size_t>(n) + 1, 1, 1, n, s));  // + I: the diagonal bytes
+    SolveArgs m;
+    m.n = n;
+    m.E = clb;
+    m.E2 = A;
+    m.e_device = true;
+    m.mem = a.mem;
+    m.out_bits = a.out_bits;
+    if ((rc = solve_compose(ctx, ws, s, m, &sm))) return rc;  // min1((I + B0^+) A)
+    if (st) {
+        st->path_used = a.path;
+        st->eps_used = real ? sr.eps_used : sc.eps_used;
+        st->iters = real ? sr.iters : sc.iters;
+        st->final_resid = real ? sr.final_resid : -1.0;
+        st->guard_flagged = sr.guard_flagged;
+        st->model_ones = sm.model_ones;
+        st->rows_rechecked = thresh_ones >= 0 ? sm.model_ones - thresh_ones : 0;
+        st->ms_factor = sr.ms_factor;
+        st->ms_solve = sr.ms_solve;
+        st->ms_refine = sr.ms_refine;
+        st->ms_epilogue = sc.ms_total + sm.ms_total;
+        st->ms_total = sr.ms_total + sc.ms_total + sm.ms_total;
+        st->gpu_launches = sr.gpu_launches + sc.gpu_launches + sm.gpu_launches + 1;
+        st->gemm_launches = sr.gemm_launches + sc.gemm_launches + sm.gemm_launches;
+        st->gemm_flops = sr.gemm_flops + sc.gemm_flops + sm.gemm_flops;
+        st->ms_gemm = sr.ms_gemm + sc.ms_gemm + sm.ms_gemm;
     }
     return DL_OK;
 }

@@ -24,7 +24,7 @@ PATHS = {"auto": 0, "fp64": 1, "mixed": 2, "bool_fp8": 3, "fp8": 3}
 DL_MEM_HOST, DL_MEM_DEVICE = 0, 1
 
 EXPORTED = ["dl_create", "dl_destroy", "dl_last_error", "dl_set_stream", "dl_tc_closure", "dl_tc_closure_bits",
-            "dl_sg_least_model", "dl_sg_real", "dl_compose", "dl_tc_batch", "dl_submit", "dl_poll", "dl_cancel",
+            "dl_sg_least_model", "dl_sg_real", "dl_tail_recursive", "dl_compose", "dl_tc_batch", "dl_submit", "dl_poll", "dl_cancel",
             "dl_tc_closure_noalloc", "dl_selftest_wait_timeout"]
 NOALLOC_MAX_N = 2048
 
@@ -93,6 +93,8 @@ def lib() -> ctypes.CDLL:
                                              ctypes.POINTER(Stats)]
             L.dl_sg_least_model.argtypes = [vp, i32, vp, vp, ctypes.c_int, f64, f64, ctypes.c_int,
                                             vp, ctypes.POINTER(Stats)]
+            L.dl_tail_recursive.argtypes = [vp, i32, vp, vp, ctypes.c_int, f64, f64, ctypes.c_int, vp, vp,
+                                            ctypes.POINTER(Stats)]
             L.dl_sg_real.argtypes = [vp, i32, vp, vp, ctypes.c_int, f64, ctypes.c_int, vp, vp,
                                      ctypes.POINTER(Stats)]
             L.dl_compose.argtypes = [vp, i32, vp, vp, ctypes.c_int, vp, ctypes.POINTER(Stats)]
@@ -279,6 +281,28 @@ class Context:
         _check(lib().dl_sg_least_model(self._h, n, p, bptr, mem, float(eps), float(thr),
                                        PATHS[path], bp, ctypes.byref(st)))
         return bits, st.as_dict()
+
+    def tail_recursive(self, B0, A, eps: float = 0.0, path: str = "auto", rtilde: bool = False):
+        """One equation of the tail recursive class, R~ = eps (A + B0 R~) (Sec. 5.1); returns
+        (bits of the model, stats[, R~])."""
+        pb, n, mem, keep = _square_u8(B0)
+        pa, na, mema, keepa = _square_u8(A)
+        if na != n or mema != mem:
+            raise ValueError("A must match B0 in size and memory kind")
+        bits, bp = _alloc_bits(n, mem, keep)
+        rt, rp = None, None
+        if rtilde:
+            if mem == DL_MEM_DEVICE:
+                import torch
+                rt = torch.empty((n, n), dtype=torch.float64, device=keep.device)
+                rp = rt.data_ptr()
+            else:
+                rt = np.zeros((n, n), dtype=np.float64)
+                rp = rt.ctypes.data
+        st = Stats()
+        _check(lib().dl_tail_recursive(self._h, n, pb, pa, mem, float(eps), 0.0, PATHS[path], bp, rp,
+                                       ctypes.byref(st)))
+        return (bits, st.as_dict(), rt) if rtilde else (bits, st.as_dict())
 
     def sg_real(self, P, B=None, eps: float = 0.0, path: str = "auto", bits: bool = True):
         """Real S~ = eps (B + P S~ P^T) of same generation (Sec. 6.2); returns (S~, bits or

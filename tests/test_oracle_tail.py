@@ -66,3 +66,13 @@ def test_rtilde_solves_the_equation():
     x = oracle.tail_rtilde(b0, a, eps)
     r = x - eps * (a + b0.astype(np.float64) @ x)
     assert np.abs(r).max() <= 1e-15 * max(1.0, np.abs(x).max())
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_sampled_rows_match_the_whole_model(seed):
+    n = 300
+    b0 = rand01(n, 0.006, 40 + seed)
+    a = rand01(n, 0.004, 50 + seed)
+    m = oracle.tail_model(b0, a)
+    rows = [0, 17, 150, n - 1]
+    assert np.array_equal(oracle.tail_model_rows(b0, a, rows), m[rows])
