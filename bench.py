@@ -206,6 +206,28 @@ def bench_sg_real(ctx, torch, reps: int = 5) -> dict:
                          "peak_source": pk["source"]}}
 
 
+def bench_tail(ctx, torch, reps: int = 5) -> dict:
+    """One equation of the tail recursive class, R~ = eps (A + B0 R~), at N = 8192: B0 the ER
+    graph with p = 1e-3 (seed 3), A the one with p = 1e-4 (seed 2), device-resident.  The model
+    (closure of B0 by AUTO, then one FP8 product) and R~ on the mixed path."""
+    from paper_1608_00139_gb300 import inputs
+    b0 = torch.from_numpy(inputs.er_digraph(N, 1e-3, 3)).cuda()
+    a = torch.from_numpy(inputs.er_digraph(N, 1e-4, 2)).cuda()
+    torch.cuda.synchronize()
+    out = {"workload": "tail recursive R~ = eps (A + B0 R~), N=8192, B0 ER p=1e-3 seed 3, A ER p=1e-4 seed 2"}
+    for path, reps_p in (("auto", reps), ("mixed", 2)):
+        ctx.tail_recursive(b0, a, path=path)
+        t0 = time.perf_counter()
+        for _ in range(reps_p):
+            _, st = ctx.tail_recursive(b0, a, path=path)
+        out[path] = {"ms": (time.perf_counter() - t0) / reps_p * 1e3, "device_ms": st["ms_total"],
+                     "model_ones": st["model_ones"], "gemm_launches": st["gemm_launches"]}
+        if path == "mixed":
+            out[path].update({"refine_steps": st["iters"], "final_resid": st["final_resid"],
+                              "rows_rechecked": st["rows_rechecked"]})
+    return out
+
+
 def cpu_sg_real() -> dict:
     """The oracle's S~ (FP64 fixpoint series, sparse P) on the same workload, host cores."""
     import oracle
@@ -363,6 +385,9 @@ def run_part(args, device: int) -> None:
     elif args.part == "sg_real":
         with dl.Context(device) as ctx:
             out = bench_sg_real(ctx, torch)
+    elif args.part == "tail":
+        with dl.Context(device) as ctx:
+            out = bench_tail(ctx, torch)
     else:
         with dl.Context(device) as ctx:
             out = bench_sg(ctx, torch) if args.part == "sg" else bench_batch(ctx, torch, reps=max(1, args.steps))
@@ -385,7 +410,7 @@ def main() -> None:
                     help="skip the same-generation, batch and serving measurements")
     ap.add_argument("--serve-seconds", type=float, default=10.0,
                     help="length of the serving stream (the full workload is 60 s)")
-    ap.add_argument("--part", default="all", choices=["all", "sg", "sg_real", "batch", "serving", "mixed"],
+    ap.add_argument("--part", default="all", choices=["all", "sg", "sg_real", "tail", "batch", "serving", "mixed"],
                     help="run one secondary measurement alone and print its JSON (for profiling)")
     args = ap.parse_args()
     rank, world, local = dist_env()
@@ -585,6 +610,7 @@ def main() -> None:
     if not args.no_extra and rank == 0:
         line["same_generation"] = bench_sg(ctxs[0], torch)
         line["sg_real"] = bench_sg_real(ctxs[0], torch)
+        line["tail_recursive"] = bench_tail(ctxs[0], torch)
         line["batch"] = bench_batch(ctxs[0], torch)
         line["serving"] = bench_serving(dl, torch, local, args.serve_seconds)
     if pure:

@@ -731,6 +731,7 @@ dl_status tc_fp64(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &a
     tm.mark(2);
     const double *X = G + np;
     const double tau = ctx->cfg.guard_tau > 0 ? ctx->cfg.guard_tau : 1e-30;
+    CK(cudaMemsetAsync(mbits, 0, npb * wp * 8, s));  // the threshold writes rows < n, words < ceil(n/64)
     CK(thresh_pack_f64(X, ldg, n, static_cast<int>(np), tau, mbits, wp, ws.scal + SC_GUARD, s));
     ++launches;
     // recheck: in-place sweeps until the model satisfies R2 = min1(E + E R2)
@@ -792,6 +793,7 @@ dl_status tc_mixed_path(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveA
     tm.mark(2);
     const auto *X = static_cast<const double *>(ws.get("mx_X64", np * np * 8));
     const double tau = ctx->cfg.guard_tau > 0 ? ctx->cfg.guard_tau : 1e-30;
+    CK(cudaMemsetAsync(mbits, 0, np * wp * 8, s));  // the threshold writes rows < n, words < ceil(n/64)
     CK(thresh_pack_f64(X, np, n, static_cast<int>(np), tau, mbits, wp, ws.scal + SC_GUARD, s));
     ++launches;
     int sweeps = 0;
