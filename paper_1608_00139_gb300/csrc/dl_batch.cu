@@ -86,27 +86,47 @@ __global__ void batch_map_kernel(const BatchInst *__restrict__ inst, int *pinst)
     for (int r = threadIdx.x; r < I.np; r += blockDim.x) pinst[I.prow0 + r] = blockIdx.x;
 }
 
-// Bits of row r of I + E_k into M (one warp per padded row), the row's successor count and
-// the 0/1 check.
+// Bits of row r of I + E_k into M, the row's successor count and the 0/1 check.  A warp takes
+// kPackRows consecutive padded rows and looks the instance up again only where the rows cross
+// into the next one (rows are short: per-row lookups would put two dependent loads before
+// every row's own).
+constexpr int kPackRows = 4;
+
 __global__ void __launch_bounds__(256, 4)
     batch_pack_kernel(const BatchInst *__restrict__ inst, const int *__restrict__ pinst, int total_prows,
                       int *cnt, int *status) {
     const int lane = threadIdx.x & 31;
-    const int g = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    if (g >= total_prows) return;
-    const BatchInst I = inst[pinst[g]];
-    const int r = g - I.prow0;
-    uint64_t *row = I.rbits + static_cast<int64_t>(r) * I.wp;
-    if (r >= I.n) {  // padding: identity only
-        for (int w = lane; w < I.wp; w += 32) row[w] = w == (r >> 6) ? 1ull << (r & 63) : 0ull;
-        return;
-    }
-    int c = 0;
-    bool bad = false;
-    pack_row_bits(I.E + static_cast<int64_t>(r) * I.n, I.n, r, I.wp, row, lane, c, bad);
-    if (lane == 0) {
-        cnt[I.row0 + r] = c;
-        if (bad) atomicOr(status, ST_BAD_INPUT);
+    const int g0 = (blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * kPackRows;
+    if (g0 >= total_prows) return;
+    const int g1 = min(g0 + kPackRows, total_prows);
+    int k = pinst[g0];
+    const uint8_t *E = inst[k].E;
+    uint64_t *rbits = inst[k].rbits;
+    int n = inst[k].n, np = inst[k].np, wp = inst[k].wp, prow0 = inst[k].prow0, row0 = inst[k].row0;
+    for (int g = g0; g < g1; ++g) {
+        if (g - prow0 >= np) {  // the next instance
+            k = pinst[g];
+            E = inst[k].E;
+            rbits = inst[k].rbits;
+            n = inst[k].n;
+            np = inst[k].np;
+            wp = inst[k].wp;
+            prow0 = inst[k].prow0;
+            row0 = inst[k].row0;
+        }
+        const int r = g - prow0;
+        uint64_t *row = rbits + static_cast<int64_t>(r) * wp;
+        if (r >= n) {  // padding: identity only
+            for (int w = lane; w < wp; w += 32) row[w] = w == (r >> 6) ? 1ull << (r & 63) : 0ull;
+            continue;
+        }
+        int c = 0;
+        bool bad = false;
+        pack_row_bits(E + static_cast<int64_t>(r) * n, n, r, wp, row, lane, c, bad);
+        if (lane == 0) {
+            cnt[row0 + r] = c;
+            if (bad) atomicOr(status, ST_BAD_INPUT);
+        }
     }
 }
 
@@ -618,8 +638,8 @@ dl_status solve_tc_batch(dl_ctx *ctx, Workspace &ws, cudaStream_t s, int32_t cou
     //    call: the contents, hence the number of facts, may differ between calls)
     BCK(cudaMemsetAsync(ws.status, 0, sizeof(int), s));
     batch_map_kernel<<<L, 256, 0, s>>>(dinst, pinst);
-    const unsigned prow_blocks = static_cast<unsigned>((total_prows + 7) / 8);
-    batch_pack_kernel<<<prow_blocks, 256, 0, s>>>(dinst, pinst, static_cast<int>(total_prows), gcnt, ws.status);
+    const unsigned pack_blocks = static_cast<unsigned>((total_prows + 8 * kPackRows - 1) / (8 * kPackRows));
+    batch_pack_kernel<<<pack_blocks, 256, 0, s>>>(dinst, pinst, static_cast<int>(total_prows), gcnt, ws.status);
     BCK(cudaGetLastError());
     BCK(exclusive_scan_large(gcnt, static_cast<int>(total_rows), gptr, scratch, s));
     const int pre_launches = 2 + (total_rows > 64 * 1024 ? 3 : 1);
