@@ -228,6 +228,21 @@ def bench_tail(ctx, torch, reps: int = 5) -> dict:
     return out
 
 
+def cpu_tail() -> dict:
+    """The oracle on the tail recursive workload: rows of the model by breadth-first search (the
+    whole-model oracle needs dense products at N = 8192), a bounded sample scaled to N rows."""
+    import oracle
+    from paper_1608_00139_gb300 import inputs
+    b0 = inputs.er_digraph(N, 1e-3, 3)
+    a = inputs.er_digraph(N, 1e-4, 2)
+    rows = list(range(0, N, N // 64))
+    t0 = time.perf_counter()
+    oracle.tail_model_rows(b0, a, rows)
+    ms = (time.perf_counter() - t0) * 1e3
+    return {"ms_per_row": ms / len(rows), "ms_full_estimate": ms / len(rows) * N, "kind": "oracle",
+            "cores": 1, "sample": f"{len(rows)} of {N} rows by breadth-first search, scaled to {N} rows"}
+
+
 def cpu_sg_real() -> dict:
     """The oracle's S~ (FP64 fixpoint series, sparse P) on the same workload, host cores."""
     import oracle
@@ -624,6 +639,8 @@ def main() -> None:
         line["cpu_baseline"] = cpu_baseline(gs)
         if "sg_real" in line:
             line["sg_real"]["cpu_oracle"] = cpu_sg_real()
+        if "tail_recursive" in line:
+            line["tail_recursive"]["cpu_oracle"] = cpu_tail()
     if rank == 0:
         print(json.dumps(line), flush=True)
     for c in ctxs:
