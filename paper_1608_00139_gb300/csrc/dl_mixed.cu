@@ -363,7 +363,14 @@ __global__ void __launch_bounds__(1024, 1)
         long long sum[G] = {};
         if (i < n) {
             const int q1 = ptr[i + 1];
-            for (int q = ptr[i]; q < q1; ++q) {
+            int q = ptr[i];
+            for (; q + 4 <= q1; q += 4) {  // four successor indices in flight
+                const int c0 = col[q], c1 = col[q + 1], c2 = col[q + 2], c3 = col[q + 3];
+#pragma unroll
+                for (int g = 0; g < G; ++g)
+                    sum[g] += (zi[g * np + c0] + zi[g * np + c1]) + (zi[g * np + c2] + zi[g * np + c3]);
+            }
+            for (; q < q1; ++q) {
                 const int c = col[q];
 #pragma unroll
                 for (int g = 0; g < G; ++g) sum[g] += zi[g * np + c];
