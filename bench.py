@@ -196,7 +196,15 @@ def bench_sg_real(ctx, torch, reps: int = 5) -> dict:
     step_bytes = 2.0 * npad * npad * 8
     pk = peaks()
     gbs = st["iters"] * step_bytes / (st["ms_solve"] * 1e-3) / 1e9 if st["ms_solve"] > 0 else None
+    # the same S~ by Smith's doubling on the TF32 tensor cores with FP64 refinement
+    ctx.sg_real(p, path="mixed", bits=False)
+    t0 = time.perf_counter()
+    _, _, sm = ctx.sg_real(p, path="mixed", bits=False)
+    mixed = {"ms": (time.perf_counter() - t0) * 1e3, "refine_steps": sm["iters"], "final_resid": sm["final_resid"],
+             "gemm_launches": sm["gemm_launches"],
+             "gemm_tflops": sm["gemm_flops"] / (sm["ms_gemm"] * 1e-3) / 1e12 if sm["ms_gemm"] else None}
     return {"workload": "SG S~ forest+DAG N=4096 seed 5", "ms": ms, "device_ms": st["ms_total"],
+            "mixed_path": mixed,
             "path_used": "fp64 series" if st["path_used"] == 1 else "mixed refinement",
             "series_steps": st["iters"], "final_resid": st["final_resid"], "ms_series": st["ms_solve"],
             "ms_model_bits": st["ms_epilogue"],
