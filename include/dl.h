@@ -72,8 +72,9 @@ typedef struct {
     void *stream;              /* cudaStream_t to run on; NULL = the context's own stream */
     size_t hbm_budget_bytes;   /* serving admission budget; 0 = 90% of free device memory */
     int32_t max_slots;         /* serving: requests in flight at once; 0 = 4 */
-    double refine_tol;         /* mixed path: stop when max|R| <= tol * max|eps E|; 0 = 1e-13 */
-    int32_t refine_max_iters;  /* mixed path: refinement step limit; 0 = 30 */
+    double refine_tol;         /* refinement of the real paths (closure, tail class, S~) and the
+                                  S~ series: stop when max|R| <= tol * eps; 0 = 1e-13 */
+    int32_t refine_max_iters;  /* refinement step limit of those paths; 0 = 30 */
     double guard_tau;          /* entries with |R~| <= tau are flagged for recheck; 0 = 1e-30 */
     double wait_timeout_s;     /* limit of every device-side wait; 0 = 2 s */
 } dl_config;
@@ -200,8 +201,9 @@ DL_API dl_status dl_tail_recursive(dl_ctx *ctx, int32_t n, const uint8_t *B0, co
  * (required).  out_bits (optional, NULL allowed): the model, S~ > 0 made exact by the
  * boolean iteration (n * ceil(n/64) words).  mem: where P, B and both outputs live.
  * Paths: DL_PATH_FP64 -- the fixpoint series X <- eps (B + P X P^T) in FP64 until a step
- * changes nothing beyond 1e-13 eps (exact after depth + 1 steps when P is nilpotent);
- * DL_PATH_MIXED -- Smith's doubling on the TF32 tensor cores with FP64 refinement;
+ * changes nothing beyond refine_tol * eps (exact after depth + 1 steps when P is nilpotent);
+ * DL_PATH_MIXED -- Smith's doubling on the TF32 tensor cores with FP64 refinement (device
+ * workspace about (2K + 4) np^2 FP32 matrices, K the doubling steps, np = n rounded up to 256);
  * DL_PATH_AUTO -- the series, then the refinement if 64 steps did not converge.
  * DL_PATH_BOOL_FP8: DL_EINVAL (no real values).  n is limited to 29000 (a row of S~ in one
  * block's shared memory); DL_ENOTCONV if the series or the refinement does not converge.
