@@ -73,3 +73,49 @@ def test_config_er8192_mixed(ctx, big_graphs, big_models, p):
     for j in (0, 4095, 8191):
         col = oracle.tc_rtilde_col(e, eps, j)
         assert np.abs(x[:, j] - col).max() <= 1e-10 * scale
+
+
+def test_config_er8192_six_closures_in_flight(big_graphs, big_models):
+    """The headline step's launch configuration: six contexts (two per graph), each on its own
+    CUDA stream and host thread, solving their graph back to back with device-resident inputs
+    and preallocated device outputs, then through pinned host buffers and bit-packed host
+    input; every model bit-exact against the oracle."""
+    from concurrent.futures import ThreadPoolExecutor
+
+    import torch
+
+    from paper_1608_00139_gb300 import dl
+
+    ps = [p for p, _ in BIG]
+    model_of = [i % 3 for i in range(6)]
+    dev = {p: torch.from_numpy(big_graphs[p]).cuda() for p in ps}
+    host = {p: torch.from_numpy(big_graphs[p]).pin_memory().numpy() for p in ps}
+    packed = {p: oracle.pack(big_graphs[p]) for p in ps}
+    words = (8192 + 63) // 64
+    outs = [torch.empty((8192, words), dtype=torch.int64, device="cuda") for _ in range(6)]
+    host_outs = [np.zeros((8192, words), dtype=np.uint64) for _ in range(6)]
+    torch.cuda.synchronize()
+    streams = [torch.cuda.Stream() for _ in range(6)]
+    ctxs = [dl.Context(0, stream=st) for st in streams]
+    try:
+        def run(i):
+            p = ps[model_of[i]]
+            got = []
+            for _ in range(4):
+                ctxs[i].tc_closure(dev[p], out=outs[i])
+                got.append(outs[i].cpu().numpy().view(np.uint64).copy())
+            ctxs[i].tc_closure(host[p], out=host_outs[i])
+            got.append(host_outs[i].copy())
+            bits, _ = ctxs[i].tc_closure_bits(packed[p], 8192)
+            got.append(bits)
+            return got
+
+        with ThreadPoolExecutor(max_workers=6) as pool:
+            results = list(pool.map(run, range(6)))
+        for i, got in enumerate(results):
+            want = big_models[ps[model_of[i]]]
+            for k, g in enumerate(got):
+                assert np.array_equal(g, want), (i, k)
+    finally:
+        for c in ctxs:
+            c.close()
