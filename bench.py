@@ -32,7 +32,7 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 N = 8192
-INFLIGHT = 2  # contexts per model in the headline step (closures in flight = 3 x INFLIGHT)
+INFLIGHT = 3  # contexts per model in the headline step (closures in flight = 3 x INFLIGHT)
 PS = (1e-4, 1e-3, 1e-2)
 SEEDS = (2, 3, 4)
 METRIC = "TC least-model TFLOP/s-equiv (N=8192) vs plain FP64 path; served p50/p99 latency"
