@@ -112,3 +112,22 @@ def test_arguments(ctx):
     assert rel_err(x, oracle.sg_stilde_series(p, None, oracle.sg_eps(p) / 2)) <= 1e-10
     x0, _, _ = ctx.sg_real(np.zeros((0, 0), dtype=np.uint8))
     assert x0.shape == (0, 0)
+
+
+@pytest.mark.parametrize("path", ["auto", "fp64", "mixed"])
+def test_slowly_converging_series(ctx, path):
+    """A circulant P with four successors per node: eps ||P kron P|| = 16/17, so the series needs
+    about 480 steps; AUTO leaves it after 64 for the refinement, FP64 runs it to the end."""
+    n = 300
+    p = np.zeros((n, n), dtype=np.uint8)
+    for k in range(1, 5):
+        p[np.arange(n), (np.arange(n) + k) % n] = 1
+    x, bits, st = ctx.sg_real(p, path=path)
+    ref = oracle.sg_stilde_series(p)
+    assert rel_err(x, ref) <= 1e-10
+    assert st["final_resid"] <= 1e-13
+    assert np.array_equal(bits, oracle.sg_model(p))
+    if path == "auto":
+        assert st["path_used"] == dl.PATHS["mixed"] and st["iters"] > 64
+    if path == "fp64":
+        assert st["iters"] > 64
