@@ -43,6 +43,7 @@ struct Workspace {
     BatchPlan *batch_plan = nullptr;
     bool last_heavy = false;  // the last closure on this workspace had rows of > 256 successors
     bool last_rows_closed = false;  // ... was closed by the Iteration on single rows alone
+    bool last_dense = false;        // ... had more than two facts per row (no single-row Iteration)
 
     cudaError_t init();
     void release();

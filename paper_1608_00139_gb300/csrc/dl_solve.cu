@@ -474,7 +474,9 @@ dl_status tc_auto(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &a
         const int64_t cap = static_cast<int64_t>(ws.capacity("g_col") / sizeof(int));
         CK(csr_fill_from_bits_guarded(rbits, n, wp, ptr, col, cap, ws.scal + SC_DMAX, 256, gate, s));
         ++launches;
-        iterated = row_iteration_fits(wp);
+        // the Iteration on single rows (it checks sparsity on the device; not launched when the
+        // last closure here was too dense for it)
+        iterated = row_iteration_fits(wp) && !ws.last_dense;
         if (iterated) {
             CK(row_iteration(ptr, col, n, wp, rbits, ws.scal + SC_OPEN, s, gate));
             ++launches;
@@ -496,6 +498,7 @@ dl_status tc_auto(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &a
     if ((rc = choose_eps(a.eps, 1.0 / (1.0 + static_cast<double>(dmax)), "Lemma 1 (1/(1+||E||))", &eps)))
         return rc;
     const int64_t nnz = static_cast<int64_t>(host_scal(ws)[SC_NNZ]);
+    ws.last_dense = nnz > 2 * static_cast<int64_t>(n);
     // bytes a sweep reads at least: the CSR of E and every row of the bit matrix once
     const double sweep_min_bytes = 4.0 * (static_cast<double>(nnz) + n + 1) + static_cast<double>(n) * wp * 8.0;
     if (spec && *reinterpret_cast<const int *>(host_scal(ws) + SC_GATE) != 0) spec = false;  // nothing ran
