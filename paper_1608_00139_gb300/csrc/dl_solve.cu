@@ -438,10 +438,12 @@ dl_status tc_auto(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &a
     const double t_sw_min = 2.0 * bit_bytes / sweep_rate + 5e-6;  // a sweep with no facts
     // the speculative group never exceeds the sweeps a squaring is worth with no facts at all,
     // and is empty when the last closure here was settled by the single-row Iteration alone
-    const int spec_group =
+    // (and no longer than the sweeps that settled the last closure here, when it settled in them)
+    int spec_group =
         ws.last_rows_closed
             ? 0
             : static_cast<int>(std::max(4.0, std::min<double>(kFirstGroup, std::floor(t_sq / t_sw_min))));
+    if (ws.last_spec_sweeps > 0) spec_group = std::min(spec_group, ws.last_spec_sweeps);
     // the model E M, checking M = min1(I + E M) on the way (straight into a device output whose
     // rows have the same stride)
     const bool direct = a.mem == DL_MEM_DEVICE && (n + 63) / 64 == wp;
@@ -503,6 +505,7 @@ dl_status tc_auto(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &a
     const double sweep_min_bytes = 4.0 * (static_cast<double>(nnz) + n + 1) + static_cast<double>(n) * wp * 8.0;
     if (spec && *reinterpret_cast<const int *>(host_scal(ws) + SC_GATE) != 0) spec = false;  // nothing ran
     ws.last_rows_closed = false;
+    ws.last_spec_sweeps = 0;
     if (spec) {
         if (iterated && host_scal(ws)[SC_OPEN] == 0) {
             converged = true;  // every row closed by the single-row Iteration (the sweeps skipped)
@@ -513,6 +516,7 @@ dl_status tc_auto(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &a
                 if (host_scal(ws)[32 + k] == 0) {
                     converged = true;
                     spec_sweeps = k + 1;
+                    ws.last_spec_sweeps = spec_sweeps;
                     break;
                 }
         }
