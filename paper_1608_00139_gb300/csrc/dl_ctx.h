@@ -44,7 +44,8 @@ struct Workspace {
     bool last_heavy = false;  // the last closure on this workspace had rows of > 256 successors
     bool last_rows_closed = false;  // ... was closed by the Iteration on single rows alone
     bool last_dense = false;        // ... had more than two facts per row (no single-row Iteration)
-    int last_spec_sweeps = 0;       // ... settled in its speculative sweeps after this many (0: no)
+    int last_spec_sweeps = 0;       // ... settled in its speculative phase after this many
+                                    // working sweeps, plus one (0: it did not)
 
     cudaError_t init();
     void release();

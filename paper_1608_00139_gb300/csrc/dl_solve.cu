@@ -443,7 +443,7 @@ dl_status tc_auto(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &a
         ws.last_rows_closed
             ? 0
             : static_cast<int>(std::max(4.0, std::min<double>(kFirstGroup, std::floor(t_sq / t_sw_min))));
-    if (ws.last_spec_sweeps > 0) spec_group = std::min(spec_group, ws.last_spec_sweeps);
+    if (ws.last_spec_sweeps > 0) spec_group = std::min(spec_group, ws.last_spec_sweeps - 1);
     // the model E M, checking M = min1(I + E M) on the way (straight into a device output whose
     // rows have the same stride)
     const bool direct = a.mem == DL_MEM_DEVICE && (n + 63) / 64 == wp;
@@ -510,15 +510,22 @@ dl_status tc_auto(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &a
         if (iterated && host_scal(ws)[SC_OPEN] == 0) {
             converged = true;  // every row closed by the single-row Iteration (the sweeps skipped)
             ws.last_rows_closed = true;
-        } else if (spec_group > 0) {
+        } else {
+            // settled when a sweep changed nothing, or when the emitted certificate holds: the
+            // sweeps only add facts of C*, and an M inside C* with M = min1(I + E M) is C*
+            int working = -1;  // sweeps that were needed
             spec_sweeps = spec_group;
             for (int k = 0; k < spec_group; ++k)
                 if (host_scal(ws)[32 + k] == 0) {
-                    converged = true;
+                    working = k;
                     spec_sweeps = k + 1;
-                    ws.last_spec_sweeps = spec_sweeps;
                     break;
                 }
+            if (working < 0 && host_scal(ws)[SC_VIOL] == 0) working = spec_group;
+            if (working >= 0) {
+                converged = true;
+                ws.last_spec_sweeps = working + 1;
+            }
         }
         sc.account(spec_sweeps + 1, sweep_min_bytes);
         emitted = converged;
