@@ -203,20 +203,6 @@ __device__ __forceinline__ uint32_t byte_bad(uint32_t x) {
     return byte_lsbs(((t + 0x7F7F7F7Fu) | t) >> 7);
 }
 
-// The chunks of a row's first segment as pack_row_bits reads them (lane L: the 64 bytes that
-// start 64 L bytes after the aligned address below a; bytes past the row read as zero), so a
-// caller can load the next row's segment while it packs this one.
-__device__ __forceinline__ void pack_row_seg0(const uint8_t *a, int n, int lane, uint4 (&x)[4]) {
-    const int off = static_cast<int>(reinterpret_cast<uintptr_t>(a) & 15);
-    const uint8_t *base = a - off;
-    const int lim = off + n;
-#pragma unroll
-    for (int j = 0; j < 4; ++j) {
-        const int v0 = 64 * lane + 16 * j;
-        x[j] = v0 < lim ? *reinterpret_cast<const uint4 *>(base + v0) : make_uint4(0u, 0u, 0u, 0u);
-    }
-}
-
 // One warp packs row r of a 0/1 byte matrix (the n bytes at a, any alignment) into wp 64-bit
 // words at `row`, plus the identity bit r.  The row is read as aligned 16-byte chunks: lane
 // L of segment s holds the 64 bytes that start 64 (32 s + L) bytes after the aligned address
@@ -224,10 +210,10 @@ __device__ __forceinline__ void pack_row_seg0(const uint8_t *a, int n, int lane,
 // Bytes outside the row are masked off (they are never counted or checked).  Every lane
 // returns the row's count of ones (without the identity) and whether a byte was not 0/1.
 // With colmask (shared memory, wp words) the row's facts are also ORed into it; without
-// identity the bit r is not added.  seg0: the first segment, already loaded by pack_row_seg0.
+// identity the bit r is not added.
 __device__ __forceinline__ void pack_row_bits(const uint8_t *a, int n, int r, int wp, uint64_t *row, int lane,
                                               int &count, bool &bad_byte, uint64_t *colmask = nullptr,
-                                              bool identity = true, const uint4 *seg0 = nullptr) {
+                                              bool identity = true) {
     const int idw = identity ? r >> 6 : -1;
     const uint64_t idb = 1ull << (r & 63);
     const int off = static_cast<int>(reinterpret_cast<uintptr_t>(a) & 15);
@@ -247,12 +233,7 @@ __device__ __forceinline__ void pack_row_bits(const uint8_t *a, int n, int r, in
             x[j] = v0 < lim ? *reinterpret_cast<const uint4 *>(base + v0) : make_uint4(0u, 0u, 0u, 0u);
         }
     };
-    if (seg0 != nullptr) {
-#pragma unroll
-        for (int j = 0; j < 4; ++j) cur[j] = seg0[j];
-    } else {
-        load(0, cur);
-    }
+    load(0, cur);
     for (int sg = 0; sg < nseg; ++sg) {
         const int u = 32 * sg + lane;
         uint4 nx[4] = {};
