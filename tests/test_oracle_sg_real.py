@@ -95,3 +95,28 @@ def test_user_eps_below_the_default():
     xk = oracle.sg_stilde_kron(p, None, e)
     xs = oracle.sg_stilde_series(p, None, e)
     assert np.abs(xk - xs).max() <= 1e-15
+
+
+def _tree(depth):
+    n = 2 ** (depth + 1) - 1
+    p = np.zeros((n, n), dtype=np.uint8)
+    for c in range(1, n):
+        p[c, (c - 1) // 2] = 1
+    return p
+
+
+def test_tree_pin_catches_a_transposed_sandwich():
+    """P^T X P in place of P X P^T (a plausible slip) must break the tree's closed form."""
+    p = _tree(3)
+    right = oracle.sg_stilde_series(p)
+    wrong = oracle.sg_stilde_series(np.ascontiguousarray(p.T))
+    assert np.abs(right - wrong).max() > 0.1
+
+
+def test_tree_pin_catches_the_wrong_kronecker_order():
+    """(P kron P^T) in place of (P kron P) for vec(P X P^T) must disagree with the series."""
+    p = _tree(3).astype(np.float64)
+    n = p.shape[0]
+    eps = oracle.sg_eps(p)
+    wrong = np.linalg.solve(np.eye(n * n) - eps * np.kron(p, p.T), eps * np.eye(n).reshape(-1)).reshape(n, n)
+    assert np.abs(wrong - oracle.sg_stilde_kron(p)).max() > 0.1

@@ -76,3 +76,23 @@ def test_sampled_rows_match_the_whole_model(seed):
     m = oracle.tail_model(b0, a)
     rows = [0, 17, 150, n - 1]
     assert np.array_equal(oracle.tail_model_rows(b0, a, rows), m[rows])
+
+
+def test_brute_force_catches_transposed_or_right_multiplied_b0():
+    """B0^T (predecessors) or R B0 in place of B0 R (plausible slips) must fail the pin."""
+    n = 14
+    b0 = rand01(n, 0.15, 70)
+    a = rand01(n, 0.1, 71)
+    reach = np.eye(n, dtype=bool)
+    for _ in range(n):
+        reach = reach | ((reach.astype(int) @ b0.astype(int)) > 0)
+    want = ((reach.astype(int) @ a.astype(int)) > 0).astype(np.uint8)
+    assert not np.array_equal(oracle.tail_model(np.ascontiguousarray(b0.T), a), want)
+    # R = A u R B0, the least solution computed by the same fixpoint with the product flipped
+    r = a.astype(bool)
+    while True:
+        nxt = r | ((r.astype(int) @ b0.astype(int)) > 0)
+        if np.array_equal(nxt, r):
+            break
+        r = nxt
+    assert not np.array_equal(r.astype(np.uint8), want)
