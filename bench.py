@@ -2,7 +2,7 @@
 
 Workload (a step): the least models of r2 <- r1; r2 <- r1, r2 (Sec. 3) for three seeded
 Erdos-Renyi digraphs with N = 8192 and p = 1e-4, 1e-3, 1e-2 (seeds 2, 3, 4; i != j), the
-paper's ER workload shape (Sec. 6.1).  Metric: TFLOP/s-equivalent = (8/3) N^3 per model
+paper's ER workload shape (Sec. 7.1).  Metric: TFLOP/s-equivalent = (8/3) N^3 per model
 (the cost of the dense direct solve of Proposition 1) / wall time, whole job.
 
   python bench.py [--gpus N --steps K --warmup W] [--impl reference]
@@ -90,6 +90,14 @@ def graph_seeds(rank: int):
 def graphs(rank: int):
     from paper_1608_00139_gb300 import inputs
     return [inputs.er_digraph(N, p, s) for p, s in graph_seeds(rank)]
+
+
+FRESH_K = 4  # graphs per p in the fresh-input leg (the headline's and three more seeds)
+
+
+def fresh_seeds(rank: int):
+    """Seeds of the fresh-input leg: for each p, the headline's seed and FRESH_K - 1 others."""
+    return [[s + 10007 * r for r in range(FRESH_K)] for _, s in graph_seeds(rank)]
 
 
 def max_over_ranks(values, world: int, device: str):
@@ -430,6 +438,8 @@ def main() -> None:
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
     ap.add_argument("--no-compare", action="store_true",
                     help="skip the squarings-only FP8 comparison run")
+    ap.add_argument("--no-fresh", action="store_true",
+                    help="skip the leg that rotates seeded graphs across solves")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the same-generation, batch and serving measurements")
     ap.add_argument("--serve-seconds", type=float, default=10.0,
@@ -486,7 +496,21 @@ def main() -> None:
     def outs_for(inputs):
         return dev_out if inputs is dev else host_out
 
+    # fresh-input leg: FRESH_K seeded graphs per p, each context moving to another graph of its
+    # p on every solve, so no closure starts from a workspace that just solved the same input
+    fresh = None
+    fresh_count = [0] * nctx
+    if not args.no_fresh:
+        from paper_1608_00139_gb300 import inputs as gen
+        with ThreadPoolExecutor(max_workers=8) as ex:
+            fresh = [list(ex.map(lambda sd, p=p: torch.from_numpy(gen.er_digraph(N, p, sd)).cuda(), seeds))
+                     for p, seeds in zip(PS, fresh_seeds(rank))]
+
     def solve(i, inputs, path):
+        if inputs is fresh:
+            m, c = model_of[i], fresh_count[i]
+            fresh_count[i] += 1
+            return ctxs[i].tc_closure(fresh[m][(i // len(gs) + c) % FRESH_K], path=path, out=dev_out[i])
         if inputs is host_bits:
             return ctxs[i].tc_closure_bits(inputs[model_of[i]], N, path=path, out=host_out[i])
         return ctxs[i].tc_closure(inputs[model_of[i]], path=path, out=outs_for(inputs)[i])
@@ -533,11 +557,19 @@ def main() -> None:
         step(host_bits)
         e2e_bits_ms, _ = timed(host_bits, args.path, e2e_steps)
         e2e_bits_s = e2e_bits_ms * 1e-3 / e2e_steps
+        # device-resident again, but every solve on a graph its context did not just solve
+        fresh_ms_step, fresh_stats = None, []
+        if fresh is not None:
+            step(fresh)
+            fresh_steps = max(1, min(args.steps, 400))
+            fresh_ms, fresh_stats = timed(fresh, args.path, fresh_steps)
+            fresh_ms_step = fresh_ms / fresh_steps
     clocks = clk.summary()
     launches = sum(st["gpu_launches"] for st in stats)
     gemm_ms = sum(st["ms_gemm"] for st in stats)
     gemm_flops = sum(st["gemm_flops"] for st in stats)
     gemm_n = sum(st["gemm_launches"] for st in stats)
+    headline_gemms = gemm_n
     squarings = [st["iters"] for st in stats]
     ms_step = ms_total / args.steps
     ms_step, e2e_s, e2e_bits_s = max_over_ranks([ms_step, e2e_s, e2e_bits_s], world, "cuda")
@@ -615,7 +647,9 @@ def main() -> None:
         dominant = roofline_sweep
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "e4m3 (0/1, FP32 accumulate)",
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": ("bits (boolean OR, Iteration sweeps)" if headline_gemms == 0 else
+                      "bits (boolean OR) + e4m3 (0/1, FP32 accumulate) squarings"),
             "data": "synthetic (seeded Erdos-Renyi, i != j)",
             "config": {"workload": "TC ER N=8192 x p in {1e-4,1e-3,1e-2}, seeds 2/3/4 (+1000*rank)",
                        "path": args.path, "l2": "inputs 3 x 64 MiB > L2, cycled each step",
@@ -631,6 +665,15 @@ def main() -> None:
             "gpu_launches": launches, "roofline": dominant, "roofline_gemm": roofline,
             "roofline_sweep": roofline_sweep,
             "clocks": clocks}
+    if fresh_ms_step is not None:
+        fresh_ms_step = max_over_ranks([fresh_ms_step], world, "cuda")[0]
+        line["fresh_inputs"] = {
+            "value": units * flops_equiv(N) / (fresh_ms_step * 1e-3) / 1e12, "unit": UNIT,
+            "ms_per_step": fresh_ms_step, "steps": max(1, min(args.steps, 400)),
+            "inputs": f"{FRESH_K} seeded graphs per p (seeds {fresh_seeds(rank)}), device-resident; "
+                      "each context solves a different graph than its previous solve",
+            "gemm_launches": sum(st["gemm_launches"] for st in fresh_stats),
+            "squarings_per_model": sorted(set(st["iters"] for st in fresh_stats))}
     if not args.no_extra and rank == 0:
         line["same_generation"] = bench_sg(ctxs[0], torch)
         line["sg_real"] = bench_sg_real(ctxs[0], torch)

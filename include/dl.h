@@ -60,7 +60,7 @@ typedef enum {
 /* Which numerical route computes the model (all give the same, exact model). */
 typedef enum {
     DL_PATH_AUTO = 0,      /* FP8 tensor-core squarings and bit sweeps (the Iteration step,
-                              Sec. 6.1), whichever is cheaper for the graph */
+                              Sec. 7.1), whichever is cheaper for the graph */
     DL_PATH_FP64 = 1,      /* plain FP64 inverse of I - eps E (Prop. 1), threshold > 0 */
     DL_PATH_MIXED = 2,     /* TF32 tensor-core LU + FP64 iterative refinement + guard */
     DL_PATH_BOOL_FP8 = 3   /* boolean repeated squaring on FP8 e4m3 tensor cores */
@@ -128,7 +128,7 @@ DL_API dl_status dl_set_stream(dl_ctx *ctx, void *stream);
  * E: the n x n 0/1 matrix of r1.  Output: the least model of r2, i.e. the least solution
  * of R2 = min1(E + E R2) (eq. matrixeq:trcl), as bits (n * ceil(n/64) words).
  *
- * eps <= 0 selects eps = 1/(1 + ||E||_inf) (Sec. 4 after Prop. 1; Sec. 6.1); otherwise
+ * eps <= 0 selects eps = 1/(1 + ||E||_inf) (Sec. 4 after Prop. 1; Sec. 7.1); otherwise
  * 0 < eps <= 1/(1 + ||E||_inf) is required (Lemma 1), else DL_EINVAL.  The model does not
  * depend on eps (Theorem 1).
  * thr must be 0 (the threshold "> 0" of Theorem 1); other values return DL_EINVAL.
@@ -157,11 +157,11 @@ DL_API dl_status dl_tc_closure_bits(dl_ctx *ctx, int32_t n, const uint64_t *E_bi
                              dl_stats *stats);
 
 /*
- * Same generation, the right-hand program of Sec. 6.2 (Fig. "Tested programs"):
+ * Same generation, the right-hand program of Sec. 7.2 (Fig. "Tested programs"):
  *     sg(x,w) <- b(x,w).     sg(x,w) <- p(x,y), sg(y,z), p(w,z).
- * i.e. the least solution of S = min1(B + P S P^T) (two-sided class, Sec. 5.3;
- * Sec. 6.2 with B = I).  P: n x n 0/1; B: n x n 0/1, or NULL for the identity
- * (the paper's diag facts).  eps <= 0 selects 1/(1 + ||P||_inf^2) (Sec. 6.2; reported
+ * i.e. the least solution of S = min1(B + P S P^T) (two-sided class, Sec. 6.3;
+ * Sec. 7.2 with B = I).  P: n x n 0/1; B: n x n 0/1, or NULL for the identity
+ * (the paper's diag facts).  eps <= 0 selects 1/(1 + ||P||_inf^2) (Sec. 7.2; reported
  * only, the model does not depend on it); thr must be 0.  Only DL_PATH_BOOL_FP8 and
  * DL_PATH_AUTO exist (others: DL_ENOTIMPL).  Output: bits of S.
  */
@@ -170,7 +170,7 @@ DL_API dl_status dl_sg_least_model(dl_ctx *ctx, int32_t n, const uint8_t *P, con
                             uint64_t *out_bits, dl_stats *stats);
 
 /*
- * One equation of the tail recursive class (Sec. 5.1, eq. matrixeq:trec), the generalisation
+ * One equation of the tail recursive class (Sec. 6.1, eq. matrixeq:trec), the generalisation
  * of transitive closure to clauses r(x,z) <- s_1(x,y_1), ..., s_n(y_{n-1},z) and
  * r(x,z) <- s_1(x,y_1), ..., s_n(y_{n-1},y), t(y,z):
  *     R~ = eps (A + B0 R~),   R~ = (I - eps B0)^-1 eps A,
@@ -191,13 +191,13 @@ DL_API dl_status dl_tail_recursive(dl_ctx *ctx, int32_t n, const uint8_t *B0, co
                             dl_stats *stats);
 
 /*
- * The real least solution of the same-generation equation (Sec. 6.2; the two-sided class of
- * Sec. 5.3, a discrete Stein/Sylvester equation):
+ * The real least solution of the same-generation equation (Sec. 7.2; the two-sided class of
+ * Sec. 6.3, a discrete Stein/Sylvester equation):
  *     S~ = eps (B + P S~ P^T),
  * whose positive entries are the least model of sg (Theorem 2).  P: n x n 0/1; B: n x n 0/1,
- * or NULL for the identity.  eps <= 0 selects 1/(1 + ||P||_inf^2) (Sec. 6.2); otherwise
+ * or NULL for the identity.  eps <= 0 selects 1/(1 + ||P||_inf^2) (Sec. 7.2); otherwise
  * 0 < eps <= that bound is required (it makes eps ||P^T kron P||_inf < 1, the condition of
- * Sec. 5.3 for a unique solution), else DL_EINVAL.  out_stilde: n x n doubles, row-major
+ * Sec. 6.3 for a unique solution), else DL_EINVAL.  out_stilde: n x n doubles, row-major
  * (required).  out_bits (optional, NULL allowed): the model, S~ > 0 made exact by the
  * boolean iteration (n * ceil(n/64) words).  mem: where P, B and both outputs live.
  * Paths: DL_PATH_FP64 -- the fixpoint series X <- eps (B + P X P^T) in FP64 until a step
@@ -224,11 +224,18 @@ DL_API dl_status dl_compose(dl_ctx *ctx, int32_t n, const uint8_t *R1, const uin
                      dl_mem mem, uint64_t *out_bits, dl_stats *stats);
 
 /*
- * Batch of independent transitive-closure problems of uneven size (each as
- * dl_tc_closure with eps <= 0, thr = 0, DL_PATH_BOOL_FP8).  ns[k], Es[k], out_bits[k]
- * describe problem k; all live in `mem`.  Every squaring round of all unfinished
- * problems runs as one persistent grouped launch, replayed from a captured CUDA graph.
- * stats (optional, one for the whole batch): iters = squaring rounds.
+ * Batch of independent transitive-closure problems of uneven size, each with the model
+ * dl_tc_closure gives (eps <= 0, thr = 0; the program of Sec. 3).  ns[k], Es[k], out_bits[k]
+ * describe problem k; all live in `mem`.  Every problem follows the DL_PATH_AUTO scheme:
+ * one packing pass over all inputs builds one CSR over all problems' rows (one host read
+ * sizes it), then a captured CUDA graph runs problems of at most 1024 padded rows to their
+ * fixpoint in shared memory (one CTA each), batched in-place Iteration sweeps (Sec. 7.1) over
+ * the rows of every problem still changing, and rounds of one persistent grouped FP8
+ * tensor-core squaring launch over exactly the problems still active, each followed by more
+ * sweeps; a problem leaves the active lists when a sweep changes nothing, and its model and
+ * certificate are written then.  A second captured graph with further rounds runs only if a
+ * problem is still active after the first.  Every decision is taken on the device.
+ * stats (optional, one for the whole batch): iters = squaring rounds launched.
  */
 DL_API dl_status dl_tc_batch(dl_ctx *ctx, int32_t count, const int32_t *ns, const uint8_t *const *Es,
                       dl_mem mem, uint64_t *const *out_bits, dl_stats *stats);
@@ -286,14 +293,21 @@ DL_API dl_status dl_selftest_wait_timeout(dl_ctx *ctx, double seconds);
  * E (n*n bytes, 0/1) and out_bits (n * ceil(n/64) words) are device pointers on the current
  * device; stream is a cudaStream_t (NULL = the legacy default stream); *squarings (may be
  * NULL) receives the number of tensor-core squarings.  n > DL_NOALLOC_MAX_N returns
- * DL_EINVAL.  The call returns after its work on `stream` has finished.
+ * DL_EINVAL.  The call is synchronous: it returns after its work on `stream` has finished,
+ * and it must not be called while `stream` (or the legacy stream, under global capture mode)
+ * is being captured into a CUDA graph.  A device-side wait that expires returns DL_ETIMEOUT.
  *
- * Its scratch is one fixed array (about 9 MiB) compiled into the library; every GPU that
- * loads the library keeps it until the process exits.  The first call on each device looks
- * up the array's device address (cudaGetSymbolAddress) with that device current: make that
- * first call before any stream capture.  All calls on a device share the array and it keeps
- * the previous call's contents (each call clears what it needs zeroed); calls whose work
- * overlaps on the GPU race on it and must be serialised by the caller.
+ * Its scratch is one fixed array (about 9 MiB) compiled into the library; every call looks up
+ * its device address (cudaGetSymbolAddress) with the current device.  CUDA loads device code
+ * lazily by default, so the array and the kernels this call launches are placed on a device
+ * (a driver allocation) the first time they are needed there.  A caller that must allocate
+ * nothing later makes one call with n = 0 on each device first (E and out_bits may be NULL):
+ * it places the array and loads those kernels and writes nothing; with
+ * CUDA_MODULE_LOADING=EAGER the driver does this when the library is loaded, and the array is
+ * then held by every GPU that loads the library until the process exits.  All calls on a
+ * device share the array and it keeps the previous call's contents (each call clears what it
+ * needs zeroed); calls whose work overlaps on the GPU race on it and must be serialised by the
+ * caller.
  */
 DL_API dl_status dl_tc_closure_noalloc(int32_t n, const uint8_t *E, uint64_t *out_bits,
                                        void *stream, int32_t *squarings);

@@ -7,11 +7,11 @@ only compiles it with gcc and marshals numpy arrays.
 
 Functions (passages they follow are cited in ``oracle.c``):
   tc_model(E)            least model of the transitive-closure program, semi-naive (Sec. 2-3)
-  tc_naive(E)            the paper's "Iteration" method (Sec. 6.1, eq. series:trcl)
+  tc_naive(E)            the paper's "Iteration" method (Sec. 7.1, eq. series:trcl)
   tc_rtilde_lu(E, eps)   R~ = (I - eps E)^-1 eps E by FP64 LU (Proposition 1)
   tc_rtilde_col(E, eps, j)  column j of R~ by the series of Lemma 1
-  sg_model(P, B)         least model of the same-generation program (Sec. 6.2), semi-naive
-  tc_eps(E), sg_eps(P)   the paper's default epsilons (Sec. 4, Sec. 6.1, Sec. 6.2)
+  sg_model(P, B)         least model of the same-generation program (Sec. 7.2), semi-naive
+  tc_eps(E), sg_eps(P)   the paper's default epsilons (Sec. 4, Sec. 7.1, Sec. 7.2)
   sg_stilde_kron, sg_stilde_series   the real S~ of same generation (sg_real.py, numpy FP64)
   tail_model, tail_rtilde, tail_eps  one equation of the tail recursive class (tail.py)
 Bit matrices: ceil(n/64) uint64 words per row, bit j%64 of word j//64, LSB first.

@@ -8,14 +8,14 @@
  *
  * What it computes (each function cites the passage it follows):
  *   - the least Herbrand model of the transitive-closure program (Sec. 3, eq. prog:trcl)
- *     and of the same-generation program (Sec. 6.2, Fig. "Tested programs", right), by
+ *     and of the same-generation program (Sec. 7.2, Fig. "Tested programs", right), by
  *     symbolic semi-naive bottom-up evaluation of the T_DB fixpoint (Sec. 2) on bitsets;
  *   - the real solution R~ = (I - eps E)^-1 eps E of the linearised equation
  *     (Sec. 4, eq. matrixeq:trcl:epsilon; Proposition 1) by an FP64 LU factorisation and
  *     two triangular solves with N right-hand sides;
  *   - one column of R~ by the monotone series of Lemma 1 (eq. series:trcl:epsilon),
  *     for sampled checks at sizes where the full LU is too slow;
- *   - the paper's "Iteration" method (Sec. 6.1, eq. series:trcl) on 0/1 matrices.
+ *   - the paper's "Iteration" method (Sec. 7.1, eq. series:trcl) on 0/1 matrices.
  *
  * Layouts: matrices are dense row-major, n*n entries; E[i*n+j] = 1 iff r1(e_i, e_j)
  * (Sec. 2 adjacency encoding).  Bit matrices hold ceil(n/64) uint64 words per row, bit
@@ -57,13 +57,13 @@ int64_t oracle_max_row_sum(int32_t n, const uint8_t *a)
 }
 
 /* eps = 1 / (1 + ||E||_inf): the largest value Lemma 1 allows, the one the paper uses
- * (Sec. 4 after Proposition 1; Sec. 6.1 "Matrix"). */
+ * (Sec. 4 after Proposition 1; Sec. 7.1 "Matrix"). */
 double oracle_tc_eps(int32_t n, const uint8_t *e)
 {
     return 1.0 / (1.0 + (double)oracle_max_row_sum(n, e));
 }
 
-/* eps = 1 / (1 + ||P||_inf^2) for the same-generation equation (Sec. 6.2). */
+/* eps = 1 / (1 + ||P||_inf^2) for the same-generation equation (Sec. 7.2). */
 double oracle_sg_eps(int32_t n, const uint8_t *p)
 {
     double d = (double)oracle_max_row_sum(n, p);
@@ -148,7 +148,7 @@ int oracle_tc_seminaive(int32_t n, const uint8_t *e, uint64_t *r, int32_t *iters
 }
 
 /*
- * The paper's "Iteration" method (Sec. 6.1; eq. series:trcl): R^(0) = 0,
+ * The paper's "Iteration" method (Sec. 7.1; eq. series:trcl): R^(0) = 0,
  * R^(k+1) = min1(R1 + R1 R^(k)) on 0/1 matrices, until R^(k+1) = R^(k).
  * R: n*n bytes (output, 0/1).  Cost O(n^3) per step; for small n only.
  */
@@ -282,7 +282,7 @@ int oracle_tc_rtilde_series_col(int32_t n, const uint8_t *e, double eps, int32_t
 }
 
 /*
- * Least model of the same-generation program (Sec. 6.2, Fig. "Tested programs", right):
+ * Least model of the same-generation program (Sec. 7.2, Fig. "Tested programs", right):
  *   sg(x,w) <- b(x,w);   sg(x,w) <- p(x,y), sg(y,z), p(w,z)
  * i.e. the least S with S = min1(B + P S P^T) (eq. matrixeq:two-sided:3 with B = I).
  * Semi-naive evaluation of the T_DB fixpoint (Sec. 2):

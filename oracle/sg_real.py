@@ -1,13 +1,13 @@
-"""Real-valued least solution S~ of the same-generation matrix equation (Sec. 6.2):
+"""Real-valued least solution S~ of the same-generation matrix equation (Sec. 7.2):
 
     S~ = eps (B + P S~ P^T),   eps = 1 / (1 + ||P||_inf^2)   (B = I: the diag facts)
 
-whose positive entries are the least model of sg (Sec. 6.2; the two-sided class of Sec. 5.3).
+whose positive entries are the least model of sg (Sec. 7.2; the two-sided class of Sec. 6.3).
 
 TEST INFRASTRUCTURE ONLY, like the rest of ``oracle/``: imported by ``tests/`` and by the
 CPU-baseline leg of ``bench.py``, never by the package.  Plain FP64 numpy/scipy, no blocking.
 
-  sg_stilde_kron(P, B, eps)    the vectorised equation of Sec. 5.3 (eq. veceq:two-sided:1) with
+  sg_stilde_kron(P, B, eps)    the vectorised equation of Sec. 6.3 (eq. veceq:two-sided:1) with
                                R_1 = P, R_3 = P^T:  (I - eps (P kron P)) vec S~ = eps vec B, solved
                                as one dense linear system.  O(N^6): tiny N only.
   sg_stilde_series(P, B, eps)  the fixpoint iteration X <- eps (B + P X P^T) from X = 0, the least
@@ -29,12 +29,12 @@ def _inputs(p, b, eps):
         raise ValueError("B must have the shape of P")
     if eps is None:
         d = p.sum(axis=1).max() if n else 0.0
-        eps = 1.0 / (1.0 + d * d)  # Sec. 6.2
+        eps = 1.0 / (1.0 + d * d)  # Sec. 7.2
     return p, bm, float(eps)
 
 
 def sg_stilde_kron(p: np.ndarray, b: np.ndarray | None = None, eps: float | None = None) -> np.ndarray:
-    """S~ from the Kronecker form of Sec. 5.3: vec(P X P^T) = (P kron P) vec X for row-major vec."""
+    """S~ from the Kronecker form of Sec. 6.3: vec(P X P^T) = (P kron P) vec X for row-major vec."""
     p, bm, eps = _inputs(p, b, eps)
     n = p.shape[0]
     if n > 40:

@@ -1,4 +1,4 @@
-"""Least solutions of the tail recursive class (Sec. 5.1, eq. matrixeq:trec) for one equation:
+"""Least solutions of the tail recursive class (Sec. 6.1, eq. matrixeq:trec) for one equation:
 
     R~ = eps (A + B0 R~),   i.e.  R~ = (I - eps B0)^-1 eps A,
 
@@ -17,7 +17,7 @@ TEST INFRASTRUCTURE ONLY, like the rest of ``oracle/``.  Plain numpy / FP64, no 
                              B0 steps (breadth-first search)
   tail_rtilde(B0, A, eps)    R~ by one dense FP64 solve of (I - eps B0) X = eps A
   tail_eps(B0)               the default eps = 1 / (1 + ||B0||_inf), inside the uniqueness
-                             condition eps < 1 / ||B0||_inf of Sec. 5.1
+                             condition eps < 1 / ||B0||_inf of Sec. 6.1
 """
 from __future__ import annotations
 

@@ -566,6 +566,13 @@ cudaError_t ingest_u8_to_e4m3(const uint8_t *src, int n, int np, uint8_t *dst, i
     return cudaGetLastError();
 }
 
+cudaError_t load_ingest_and_sweep() {
+    cudaFuncAttributes fa;
+    cudaError_t e = cudaFuncGetAttributes(&fa, ingest_kernel);
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, sweep_kernel);
+    return e;
+}
+
 cudaError_t bits_sweep(const uint8_t *E, int64_t lde, int n, const uint64_t *M, uint64_t *out,
                        int64_t wp, int mode, int stop_early, unsigned long long *violations,
                        unsigned long long *ones, cudaStream_t s) {

@@ -96,6 +96,8 @@ cudaError_t gemm_prepare(GemmKind kind, bool b_kmajor, int bn, GemmEpi epi);
 cudaError_t ingest_u8_to_e4m3(const uint8_t *src, int n, int np, uint8_t *dst, int add_identity,
                               unsigned long long *dmax, unsigned long long *nnz,
                               unsigned long long *count, int *status, cudaStream_t s);
+// Load (under CUDA's lazy module loading) the kernels behind ingest_u8_to_e4m3 and bits_sweep.
+cudaError_t load_ingest_and_sweep();
 // One sweep of the certificate / recheck kernel on bits (64-bit words, wp words per row):
 //   mode 0 (reflexive check):  out_i = OR_{k in succ(i)} M_k;  violation iff (out_i | e_i) != M_i
 //   mode 1 (closure sweep):    out_i = M_i | E_i | OR_{k in succ(i)} M_k (in place allowed);

@@ -16,15 +16,27 @@
 //     clears or fully rewrites what it reads, so results never depend on an earlier call;
 //   - two calls whose work overlaps on the GPU (different streams or host threads) race on
 //     it and give wrong results: serialise them.
-// The host cannot use the array's name as a device address.  The first call on each device
-// (with that device current) asks the runtime for the address with cudaGetSymbolAddress and
-// remembers it; make that first call before any stream capture begins.
+// The host cannot use the array's name as a device address.  Every call asks the runtime for
+// the address with cudaGetSymbolAddress (with the caller's device current); nothing is cached,
+// so a context that was destroyed and re-created (cudaDeviceReset) never leaves a stale
+// pointer behind.
+//
+// Module loading: CUDA loads a library's device code lazily by default (CUDA_MODULE_LOADING
+// unset or LAZY), so the array and the kernels this entry point launches are placed on a device
+// the first time they are needed there, and that first placement is a driver allocation.  A
+// caller that reserves the device's memory for its own pool makes one call with n = 0 on each
+// device first (before the reservation): it looks up the array and loads every kernel the entry
+// point uses, and allocates nothing afterwards.  With CUDA_MODULE_LOADING=EAGER the driver does
+// all of that when the library is loaded.
+//
+// The call is synchronous (it waits on its stream and copies small counters to pageable host
+// memory), so it cannot be made while `stream`, or the legacy stream under global capture mode,
+// is being captured into a CUDA graph.
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <cmath>
 #include <cstring>
-#include <mutex>
 #include <string>
 
 #include "../../include/dl.h"
@@ -54,29 +66,16 @@ static_assert(2 * sizeof(GemmProblem) <= kTableBytes, "GEMM table does not fit")
 // The scratch array itself (one copy per device that loads the library).
 static __device__ __align__(256) uint8_t g_noalloc_scratch[kNoallocBytes];
 
-// Device address of g_noalloc_scratch, looked up once per device.
-std::mutex g_mu;
-void *g_addr[64] = {};
-
+// Device address of g_noalloc_scratch on the current device (looked up on every call).
 dl_status scratch_address(uint8_t **out) {
-    int dev = 0;
-    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+    void *p = nullptr;
+    const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess || !p) {
         cudaGetLastError();
-        set_error("dl_tc_closure_noalloc: no current CUDA device");
+        set_error("dl_tc_closure_noalloc: cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
         return DL_EDEVICE;
     }
-    std::lock_guard<std::mutex> lk(g_mu);
-    if (!g_addr[dev]) {
-        void *p = nullptr;
-        const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-        if (e != cudaSuccess || !p) {
-            cudaGetLastError();
-            set_error("dl_tc_closure_noalloc: cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
-            return DL_EDEVICE;
-        }
-        g_addr[dev] = p;
-    }
-    *out = static_cast<uint8_t *>(g_addr[dev]);
+    *out = static_cast<uint8_t *>(p);
     return DL_OK;
 }
 
@@ -89,9 +88,18 @@ dl_status scratch_address(uint8_t **out) {
         }                                                                                      \
     } while (0)
 
-dl_status read_back(cudaStream_t s, const unsigned long long *dev, unsigned long long *host, int count) {
+// Counters and the status word to the host.  A device-side wait that expired (any status bit
+// but ST_BAD_INPUT) ends the call at once with DL_ETIMEOUT, so a partial result is never
+// mistaken for a non-converged or uncertified closure.
+dl_status read_back(cudaStream_t s, const unsigned long long *dev, unsigned long long *host, int count,
+                    const int *status, int *status_host) {
     NA_CK(cudaMemcpyAsync(host, dev, sizeof(unsigned long long) * count, cudaMemcpyDeviceToHost, s));
+    NA_CK(cudaMemcpyAsync(status_host, status, sizeof(int), cudaMemcpyDeviceToHost, s));
     NA_CK(cudaStreamSynchronize(s));
+    if (*status_host & ~ST_BAD_INPUT) {
+        set_error("dl_tc_closure_noalloc: a device-side wait expired (status 0x%x)", *status_host);
+        return DL_ETIMEOUT;
+    }
     return DL_OK;
 }
 
@@ -108,7 +116,14 @@ extern "C" DL_API dl_status dl_tc_closure_noalloc(int32_t n, const uint8_t *E, u
                   n, static_cast<int>(kMaxN));
         return DL_EINVAL;
     }
-    if (n == 0) return DL_OK;
+    if (n == 0) {  // warm-up: place the array and load every kernel below; writes nothing
+        uint8_t *base = nullptr;
+        const dl_status rc = scratch_address(&base);
+        if (rc) return rc;
+        NA_CK(gemm_prepare(KIND_F8, false, 256, EPI_BOOL));
+        NA_CK(load_ingest_and_sweep());
+        return DL_OK;
+    }
     if (!E || !out_bits) {
         set_error("dl_tc_closure_noalloc: E and out_bits must be device pointers, not NULL");
         return DL_EINVAL;
@@ -134,10 +149,8 @@ extern "C" DL_API dl_status dl_tc_closure_noalloc(int32_t n, const uint8_t *E, u
     NA_CK(cudaMemsetAsync(status, 0, sizeof(int), s));
     NA_CK(ingest_u8_to_e4m3(E, n, static_cast<int>(np), C0, 1, scal + 0, scal + 1, scal + 2, status, s));
     unsigned long long h[8] = {};
-    if ((rc = read_back(s, scal, h, 8))) return rc;
     int hst = 0;
-    NA_CK(cudaMemcpyAsync(&hst, status, sizeof(int), cudaMemcpyDeviceToHost, s));
-    NA_CK(cudaStreamSynchronize(s));
+    if ((rc = read_back(s, scal, h, 8, status, &hst))) return rc;
     if (hst & ST_BAD_INPUT) {
         set_error("dl_tc_closure_noalloc: E holds a byte that is neither 0 nor 1");
         return DL_EINVAL;
@@ -178,12 +191,12 @@ extern "C" DL_API dl_status dl_tc_closure_noalloc(int32_t n, const uint8_t *E, u
         NA_CK(cudaMemsetAsync(scal + 3, 0, sizeof(unsigned long long), s));
         NA_CK(gemm_launch(KIND_F8, false, 256, EPI_BOOL, table + (t & 1), 1, tiles, grid, status, budget, s));
         ++t;
-        if ((rc = read_back(s, scal, h, 8))) return rc;
+        if ((rc = read_back(s, scal, h, 8, status, &hst))) return rc;
         if (h[3] == prev) break;
         prev = h[3];
         NA_CK(cudaMemsetAsync(scal + 4, 0, 2 * sizeof(unsigned long long), s));
         NA_CK(bits_sweep(E, n, n, rbits, mbits, wp, 0, 1, scal + 4, scal + 5, s));
-        if ((rc = read_back(s, scal, h, 8))) return rc;
+        if ((rc = read_back(s, scal, h, 8, status, &hst))) return rc;
         if (h[4] == 0) {
             have_model = true;
             break;
@@ -192,7 +205,7 @@ extern "C" DL_API dl_status dl_tc_closure_noalloc(int32_t n, const uint8_t *E, u
     if (!have_model) {
         NA_CK(cudaMemsetAsync(scal + 4, 0, 2 * sizeof(unsigned long long), s));
         NA_CK(bits_sweep(E, n, n, rbits, mbits, wp, 0, 0, scal + 4, scal + 5, s));
-        if ((rc = read_back(s, scal, h, 8))) return rc;
+        if ((rc = read_back(s, scal, h, 8, status, &hst))) return rc;
         if (h[4] != 0) {
             set_error("dl_tc_closure_noalloc: converged closure failed its certificate");
             return DL_EDEVICE;
@@ -200,12 +213,7 @@ extern "C" DL_API dl_status dl_tc_closure_noalloc(int32_t n, const uint8_t *E, u
     }
     const int64_t w = (n + 63) / 64;
     NA_CK(cudaMemcpy2DAsync(out_bits, w * 8, mbits, wp * 8, w * 8, n, cudaMemcpyDeviceToDevice, s));
-    NA_CK(cudaMemcpyAsync(&hst, status, sizeof(int), cudaMemcpyDeviceToHost, s));
     NA_CK(cudaStreamSynchronize(s));
-    if (hst) {
-        set_error("dl_tc_closure_noalloc: a device-side wait expired (status 0x%x)", hst);
-        return DL_ETIMEOUT;
-    }
     if (squarings) *squarings = t;
     return DL_OK;
 }

@@ -1,5 +1,5 @@
 // dl_sgreal.cu -- kernels of the real least solution S~ of the same-generation equation
-// (Sec. 6.2; the two-sided class of Sec. 5.3):
+// (Sec. 7.2; the two-sided class of Sec. 6.3):
 //     S~ = eps (B + P S~ P^T),   eps = 1 / (1 + ||P||_inf^2).
 // One step of the fixpoint series X <- eps (B + P X P^T) is two gather passes over the CSR of P
 // in FP64 (U = X P^T, then eps (B + P U)); the same passes give the residual

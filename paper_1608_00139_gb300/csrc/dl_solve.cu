@@ -14,7 +14,7 @@
 // satisfies R2 = min1(E + E R2) and adds any fact the rounding lost (e.g. an underflowed
 // eps^d, Lemma 2 footnote); the number of corrected rows is reported.
 //
-// Same generation (Sec. 6.2): the least S = min1(B + P S P^T) by doubling on boolean
+// Same generation (Sec. 7.2): the least S = min1(B + P S P^T) by doubling on boolean
 // matrices: S_1 = B, Q_1 = P, S_{2m} = min1(S_m + Q_m S_m Q_m^T), Q_{2m} = min1(Q_m Q_m).
 // S_m collects the facts derivable through at most m-1 nested applications of the
 // recursive clause; when a step adds nothing (S_{2m} = S_m) or Q becomes 0, S is the
@@ -390,7 +390,7 @@ dl_status tc_bool(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &a
 
 // DL_PATH_AUTO: tensor-core squarings and boolean sweeps, whichever is cheaper.
 // A sweep (in place, M <- M | E | E M on bits) is one step of the paper's Iteration method
-// (Sec. 6.1, eq. series:trcl) and adds at least one hop to every path; a squaring doubles
+// (Sec. 7.1, eq. series:trcl) and adds at least one hop to every path; a squaring doubles
 // the hop count but costs a dense 2 Np^3 product.  Sparse graphs are finished by sweeps
 // alone; dense ones square first and let a few cheap sweeps (rows saturate quickly) finish.
 // A sweep that changes nothing proves M = min1(I + E M), i.e. M is the reflexive closure;
@@ -950,7 +950,7 @@ dl_status sg_iteration(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveAr
     if ((rc = check_status(ws, s))) return rc;
     const double dmax = static_cast<double>(host_scal(ws)[SC_DMAX]);
     double eps = 0;
-    if ((rc = choose_eps(a.eps, 1.0 / (1.0 + dmax * dmax), "Sec. 6.2 (1/(1+||P||^2))", &eps))) return rc;
+    if ((rc = choose_eps(a.eps, 1.0 / (1.0 + dmax * dmax), "Sec. 7.2 (1/(1+||P||^2))", &eps))) return rc;
     const bool sym = seed == nullptr && (Bm == nullptr || host_scal(ws)[SC_CQ] == 0);
     const int64_t nnz = static_cast<int64_t>(host_scal(ws)[SC_NNZ]);
     auto *col = static_cast<int *>(ws.get("g_col", static_cast<size_t>(std::max<int64_t>(nnz, 1)) * 4));
@@ -1076,7 +1076,7 @@ dl_status sg_doubling(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArg
     if ((rc = check_status(ws, s))) return rc;
     const double dmax = static_cast<double>(host_scal(ws)[SC_DMAX]);
     double eps = 0;
-    if ((rc = choose_eps(a.eps, 1.0 / (1.0 + dmax * dmax), "Sec. 6.2 (1/(1+||P||^2))", &eps))) return rc;
+    if ((rc = choose_eps(a.eps, 1.0 / (1.0 + dmax * dmax), "Sec. 7.2 (1/(1+||P||^2))", &eps))) return rc;
     unsigned long long s_count = host_scal(ws)[SC_COUNT2];
     if (!Bm) s_count = static_cast<unsigned long long>(np);  // identity over padded size
     const unsigned long long q_count0 = host_scal(ws)[SC_COUNT0];
@@ -1211,7 +1211,7 @@ dl_status solve_compose(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveA
     return DL_OK;
 }
 
-// The real least solution S~ = eps (B + P S~ P^T) of same generation (Sec. 6.2; its positive
+// The real least solution S~ = eps (B + P S~ P^T) of same generation (Sec. 7.2; its positive
 // entries are the model, Theorem 2), in FP64, written to a.out_rtilde (n x n doubles).
 //  * the series X_{t+1} = eps (B + P X_t P^T) from X_0 = 0 (FP64 gathers over the CSR of P;
 //    X_{t+1} - X_t is X_t's residual, so a step whose change is at most tol eps ends it).  It
@@ -1272,7 +1272,7 @@ dl_status solve_sg_real(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveA
     if ((rc = check_status(ws, s))) return rc;
     const double dmax = static_cast<double>(host_scal(ws)[SC_DMAX]);
     double eps = 0;
-    if ((rc = choose_eps(a.eps, 1.0 / (1.0 + dmax * dmax), "Sec. 6.2 (1/(1+||P||^2))", &eps))) return rc;
+    if ((rc = choose_eps(a.eps, 1.0 / (1.0 + dmax * dmax), "Sec. 7.2 (1/(1+||P||^2))", &eps))) return rc;
     const int64_t nnz = static_cast<int64_t>(host_scal(ws)[SC_NNZ]);
     auto *col = static_cast<int *>(ws.get("g_col", static_cast<size_t>(std::max<int64_t>(nnz, 1)) * 4));
     NEED(col);
@@ -1489,7 +1489,7 @@ dl_status solve_sg_real(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveA
     return DL_OK;
 }
 
-// One equation of the tail recursive class (Sec. 5.1, eq. matrixeq:trec), its non-recursive
+// One equation of the tail recursive class (Sec. 6.1, eq. matrixeq:trec), its non-recursive
 // part A already formed from the lower equations' solutions:
 //     R~ = eps (A + B0 R~),  R~ = (I - eps B0)^-1 eps A,
 // and its model, the least R with R = min1(A + B0 R) = min1((I + B0^+) A), B0^+ the transitive

@@ -283,7 +283,7 @@ class Context:
         return bits, st.as_dict()
 
     def tail_recursive(self, B0, A, eps: float = 0.0, path: str = "auto", rtilde: bool = False):
-        """One equation of the tail recursive class, R~ = eps (A + B0 R~) (Sec. 5.1); returns
+        """One equation of the tail recursive class, R~ = eps (A + B0 R~) (Sec. 6.1); returns
         (bits of the model, stats[, R~])."""
         pb, n, mem, keep = _square_u8(B0)
         pa, na, mema, keepa = _square_u8(A)
@@ -305,7 +305,7 @@ class Context:
         return (bits, st.as_dict(), rt) if rtilde else (bits, st.as_dict())
 
     def sg_real(self, P, B=None, eps: float = 0.0, path: str = "auto", bits: bool = True):
-        """Real S~ = eps (B + P S~ P^T) of same generation (Sec. 6.2); returns (S~, bits or
+        """Real S~ = eps (B + P S~ P^T) of same generation (Sec. 7.2); returns (S~, bits or
         None, stats), S~ as float64 in P's memory kind."""
         p, n, mem, keep = _square_u8(P)
         bptr, keepb = None, None

@@ -10,15 +10,15 @@ function; a uniform in [0, 1) is (draw >> 11) * 2**-53.  Every draw is a pure fu
 (key, counter), so matrices can be generated in row chunks, in any order, with the same
 result on x86 and Arm.
 
-Workloads (the paper's experiments, Sec. 6):
-  * er_digraph      Erdos-Renyi digraph, each ordered pair an edge w.p. p (Sec. 6.1 uses
+Workloads (the paper's experiments, Sec. 7):
+  * er_digraph      Erdos-Renyi digraph, each ordered pair an edge w.p. p (Sec. 7.1 uses
                     this generator with self-loops allowed; here ``self_loops`` is a flag
                     and off by default, i != j).
   * forest_dag      parent relation of a random forest plus a few extra DAG edges, for
-                    the same-generation program (Sec. 6.2, Fig. "Tested programs").
+                    the same-generation program (Sec. 7.2, Fig. "Tested programs").
                     Row i holds a 1 at column parent(i): P[i][parent(i)] = 1.
   * pa_dag          directed preferential attachment DAG with Zipf out-degrees, the
-                    stand-in for real networks (Sec. 6.1, Table 1) in the serving mix.
+                    stand-in for real networks (Sec. 7.1, Table 1) in the serving mix.
   * batch_specs     the sizes and degrees of an uneven batch of closure problems.
   * poisson_stream  arrival times and kinds of a mixed query stream.
 """
@@ -82,7 +82,7 @@ def er_digraph(n: int, p: float, seed: int, self_loops: bool = False,
     """Erdos-Renyi digraph as a dense row-major uint8 0/1 matrix, E[i, j] = 1 iff i -> j.
 
     Pair (i, j) is an edge iff uniform number i*n + j of the ER stream is below p.  With
-    ``self_loops`` false the diagonal is cleared (the generator of Sec. 6.1 draws every
+    ``self_loops`` false the diagonal is cleared (the generator of Sec. 7.1 draws every
     pair; the benchmark workloads take i != j).
     """
     n = int(n)

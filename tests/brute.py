@@ -1,7 +1,7 @@
 """Brute-force references used only to pin the oracle (tiny inputs, pure Python/numpy).
 
 Each is a textbook algorithm that shares nothing with the oracle's semi-naive evaluator or
-its LU solve: breadth-first search, Warshall's algorithm (Sec. 6.1 uses it as a third
+its LU solve: breadth-first search, Warshall's algorithm (Sec. 7.1 uses it as a third
 method), and naive fixpoint iteration of the same-generation equation.
 """
 from collections import deque

@@ -1,4 +1,4 @@
-"""GPU parity of the real same-generation solution S~ = eps (B + P S~ P^T) (Sec. 6.2): the
+"""GPU parity of the real same-generation solution S~ = eps (B + P S~ P^T) (Sec. 7.2): the
 FP64 series, the TF32 doubling with FP64 refinement and AUTO against the oracle's Kronecker
 solve (tiny N) and fixpoint series; the model bits against the semi-naive oracle."""
 import numpy as np

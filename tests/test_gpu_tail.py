@@ -1,4 +1,4 @@
-"""GPU parity of one equation of the tail recursive class, R~ = eps (A + B0 R~) (Sec. 5.1):
+"""GPU parity of one equation of the tail recursive class, R~ = eps (A + B0 R~) (Sec. 6.1):
 the model on every path against the oracle (semi-naive; sampled rows by breadth-first search
 at N = 8192), R~ on the real paths against the oracle's FP64 solve, the closure as the case
 A = B0 = E, and the underflow repair."""

@@ -1,8 +1,8 @@
 """Pins of the CPU oracle for same-generation (no GPU).
 
-The semi-naive least model of S = min1(B + P S P^T) (Sec. 6.2) is checked against naive
+The semi-naive least model of S = min1(B + P S P^T) (Sec. 7.2) is checked against naive
 fixpoint iteration, against the real solution of the Kronecker (vectorised) linear system
-of the two-sided class (Sec. 5.3, eq. veceq:two-sided:1) thresholded at 0 (Theorem 2),
+of the two-sided class (Sec. 6.3, eq. veceq:two-sided:1) thresholded at 0 (Theorem 2),
 and against closed forms on chains and complete trees.
 """
 import numpy as np
@@ -63,7 +63,7 @@ def test_general_base_relation_vs_naive():
 
 @pytest.mark.parametrize("n,pe,seed", [(4, 0.3, 1), (7, 0.2, 2), (9, 0.15, 3), (12, 0.1, 4)])
 def test_kronecker_real_solution_thresholded(n, pe, seed):
-    """vec S~ = eps vec B + eps (P (x) P) vec S~ with eps = 1/(1+||P||^2) (Sec. 6.2).
+    """vec S~ = eps vec B + eps (P (x) P) vec S~ with eps = 1/(1+||P||^2) (Sec. 7.2).
 
     Solved densely (n^2 unknowns); Theorem 2: S~ > 0 is the least model, 0 <= S~ <= 1.
     """

@@ -1,5 +1,5 @@
-"""Pins for the oracle's real same-generation solution S~ = eps (B + P S~ P^T) (Sec. 6.2, the
-two-sided class of Sec. 5.3): the Kronecker solve and the fixpoint series against each other,
+"""Pins for the oracle's real same-generation solution S~ = eps (B + P S~ P^T) (Sec. 7.2, the
+two-sided class of Sec. 6.3): the Kronecker solve and the fixpoint series against each other,
 closed forms on chains, trees and P = 0, the least model, and the equation's residual."""
 import numpy as np
 import pytest

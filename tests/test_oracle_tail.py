@@ -1,4 +1,4 @@
-"""Pins for the oracle's tail recursive class R~ = eps (A + B0 R~) (Sec. 5.1): the closure case
+"""Pins for the oracle's tail recursive class R~ = eps (A + B0 R~) (Sec. 6.1): the closure case
 A = B0 = E against the C oracle's semi-naive model and LU, B0 = 0, a chain in closed form,
 brute-force reachability on small graphs, and the equation's residual."""
 import numpy as np
