@@ -40,6 +40,10 @@ struct Workspace {
     cudaEvent_t gev[kGemmEvents] = {};
     cudaEvent_t sev[kGemmEvents] = {};       // start/stop pairs of timed sweep groups
     bool ready = false;
+    // mixed path: the LU's critical chain (greatest priority) and its bulk updates (least
+    // priority), and events ordering them; created on first use
+    cudaStream_t mx_stream[2] = {};
+    cudaEvent_t mx_ev[4] = {};
     BatchPlan *batch_plan = nullptr;
     bool last_heavy = false;  // the last closure on this workspace had rows of > 256 successors
     bool last_rows_closed = false;  // ... was closed by the Iteration on single rows alone

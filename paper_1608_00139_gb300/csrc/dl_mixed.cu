@@ -1,28 +1,32 @@
 // dl_mixed.cu -- R~ = (I - eps E)^-1 eps E (Proposition 1) on the TF32 tensor cores, with FP64
 // iterative refinement (DL_PATH_MIXED).
 //
-//   1. A = I - eps E in FP32 (padded with the identity).  The right-hand side is kept
-//      transposed: Z = X^T, starting from Z = (eps E)^T, so that every product below is a
-//      "TN" GEMM whose operands are both stored with K contiguous (the form the TF32 tensor
-//      cores run here).
-//   2. Blocked right-looking LU of A without pivoting (A is strictly diagonally dominant by
-//      rows, proof of Proposition 1), block b = 128.  Per block k:
-//        diag_lu_inv:  L11 U11 = A11 on the CUDA cores (FP32) and the explicit inverses
-//                      L11^-1, U11^-1 (and U11^-T);
-//        T = A12^T (transpose of the 128-wide row panel);
-//        one grouped tcgen05 launch:  T = T L11^-T (= U12^T)  and  L21 = A21 U11^-1;
-//        A12 = T^T (U12 kept row-major for the backward substitution);
-//        one tcgen05 launch:  A22 -= L21 U12  (B operand U12^T = T).
-//   3. Z = (eps E)^T U^-T L^-T, i.e. X = U^-1 L^-1 eps E, by block forward and backward
-//      substitution on the columns of Z:  Z_k = Z_k L_kk^-T,  Z_{>k} -= Z_k L_{>k,k}^T,
-//      then Z_k = Z_k U_kk^-T,  Z_{<k} -= Z_k U_{<k,k}^T  (L and U blocks read as stored).
-//   4. Refinement in FP64 on Z: R^T = (eps E - A X)^T, i.e.
-//      R^T[j][i] = eps * sum_{k : E[i][k]} (Z[j][k] + [k = j]) - Z[j][i]
-//      (E is 0/1, so E X is a sum of rows of X: FP64 additions only); D^T = R^T U^-T L^-T on
-//      the tensor cores; Z += D^T; until max|R| <= tol * eps.  Each step contracts the error
-//      by about kappa(A) u_tf32, kappa_inf(A) <= (1 + eps ||E||) / eps <= 2 (1 + ||E||).
+//   1. A = I - eps E in FP32 (padded with the identity).
+//   2. Block LU of A without pivoting, blocks of b = 128 (A is strictly diagonally dominant by
+//      rows, proof of Proposition 1, so every Schur complement is too and block elimination is
+//      stable):  A = L U with L unit block lower (L_ik = A_ik S_kk^-1) and U block upper
+//      (U_kj = A_kj after the eliminations before k, diagonal blocks S_kk).  Per block k:
+//        diag:  S_kk^-1 by Gauss-Jordan on the CUDA cores (FP32, one CTA);
+//        L21 = A21 S_kk^-1 (in place), T = A12^T;
+//        look-ahead: the next block column and block row, A -= L21 U12 there;
+//        bulk:  the rest of the trailing matrix, A22 -= L21 U12.
+//      The look-ahead and the chain that needs it (the next diagonal block, its L21 and T) run
+//      on a stream of the greatest priority, the bulk update on a stream of the least priority
+//      and on all SMs but kReserve, so the chain of 128 x 128 steps proceeds while the bulk
+//      update of the previous block streams through HBM.
+//   3. W = A^-1 in FP32: the block solves applied to the identity (kept transposed, Z = I A^-T,
+//      by groups of 8 blocks with precomputed inverses of the groups' diagonal parts, so that
+//      every product is a tensor-core GEMM with K = 1024), then W = Z^T.
+//   4. Refinement in FP64 on Z = X^T, from Z = 0:  R^T = (eps E - A X)^T, i.e.
+//        R^T[j][i] = eps * sum_{k : E[i][k]} (Z[j][k] + [k = j]) - Z[j][i]
+//      (E is 0/1: E X is a sum of rows of X, summed exactly in 64-bit fixed point);
+//      D^T = R^T W^T, one TF32 GEMM of n x n x n; Z += D^T; until max|R| <= tol * eps.  The first
+//      step (Z = 0, R^T = (eps E)^T) is the solve itself; each later one contracts the error by
+//      about ||I - W A||, a few TF32 units times kappa(A), kappa_inf(A) <= 2 (1 + ||E||_inf).
 //   5. X = Z^T; model X > 0 (Theorem 1); entries in the guard band are counted and the exact
 //      boolean recheck of R2 = min1(E + E R2) confirms the model or adds lost facts.
+// Every product is a "TN" GEMM (both operands stored with K contiguous), the form the TF32
+// tensor cores run here; that is why the right-hand side is kept transposed.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -38,8 +42,11 @@ namespace dl {
 
 namespace {
 
-constexpr int BL = 128;  // LU block size = GEMM tile
-constexpr int TT = 32;   // transpose tile
+constexpr int BL = 128;        // LU block size = GEMM tile
+constexpr int TT = 32;         // transpose tile
+constexpr int kSolveGroup = 8;  // blocks per group of the solves (1024 columns)
+constexpr int kReserve = 16;   // SMs the bulk LU update leaves to the critical chain
+constexpr size_t kResidualSmem = 227 * 1024;  // dynamic shared memory of one residual block
 
 __global__ void build_a_kernel(const uint8_t *__restrict__ E, int n, int np, float eps, float *__restrict__ A) {
     const int64_t row = blockIdx.y;
@@ -47,21 +54,6 @@ __global__ void build_a_kernel(const uint8_t *__restrict__ E, int n, int np, flo
          c += static_cast<int64_t>(gridDim.x) * blockDim.x) {
         const float e = (row < n && c < n && E[row * n + c]) ? eps : 0.0f;
         A[row * np + c] = (c == row ? 1.0f : 0.0f) - e;
-    }
-}
-
-// Z = (eps E)^T, np x np (zero padding); 32 x 32 tiles through shared memory.
-__global__ void build_zt_kernel(const uint8_t *__restrict__ E, int n, int np, float eps, float *__restrict__ Z) {
-    __shared__ float tile[TT][TT + 1];
-    const int c0 = blockIdx.x * TT, r0 = blockIdx.y * TT;
-    for (int y = threadIdx.y; y < TT; y += blockDim.y) {
-        const int r = r0 + y, c = c0 + threadIdx.x;
-        tile[y][threadIdx.x] = (r < n && c < n && E[static_cast<int64_t>(r) * n + c]) ? eps : 0.0f;
-    }
-    __syncthreads();
-    for (int y = threadIdx.y; y < TT; y += blockDim.y) {
-        const int r = c0 + y, c = r0 + threadIdx.x;  // Z[r][c] = eps E[c][r]
-        if (r < np && c < np) Z[static_cast<int64_t>(r) * np + c] = tile[threadIdx.x][y];
     }
 }
 
@@ -89,206 +81,94 @@ cudaError_t transpose(const T *src, int64_t lds, int rows, int cols, T *dst, int
     return cudaGetLastError();
 }
 
-// Unpivoted LU of the BL x BL block at A (row stride lda) with the inverses of its factors,
-// FP32, blocked by 32 in shared memory: one CTA of 1024 threads holds the block, L^-1 and
-// U^-1 (three BL x (BL + 4) float arrays).
-//  1. right-looking LU by 32-column panels: warp 0 factors the panel's 32 x 32 diagonal block
-//     (lane = row; the pivot row, final once the earlier steps are done, is read back from
-//     shared memory), warps 1-3 form L21 = A21 U11^-1 (lane = row) and warps 4-6 form
-//     U12 = L11^-1 A12 (lane = column) by substitution, then all warps update A22 -= L21 U12
-//     in strips of 8 rows x 32 columns;
-//  2. the inverses of the 32 x 32 diagonal blocks of L and U by substitution (a warp each),
-//     then the blocks off the diagonal at distance d = 1, 2, 3 from it, each from blocks
-//     nearer the diagonal:  X_ij = -X_ii sum_{k=j..i-1} L_ik X_kj  (X = L^-1, i > j) and
-//     Y_ij = -Y_ii sum_{k=i+1..j} U_ik Y_kj  (Y = U^-1, i < j).
-// Writes L^-1 (unit lower), U^-1 and U^-T, BL x BL each; a zero pivot sets ST_BAD_INPUT.
-constexpr int kDiagThreads = 1024;
-constexpr int kDiagLd = BL + 4;  // padded shared-memory row (keeps float4 alignment)
-constexpr size_t kDiagSmem = 3ull * BL * kDiagLd * sizeof(float) + 16;
-constexpr int kSolveGroup = 8;  // panels per group of the N-RHS solves
-constexpr size_t kResidualSmem = 227 * 1024;  // dynamic shared memory of one residual block
+// S^-1 of the BL x BL block at A (row stride lda) by in-place Gauss-Jordan elimination without
+// pivoting, FP32, one CTA of 256 threads.  Thread t holds an 8 x 8 tile of the block in
+// registers: rows r0 .. r0 + 7 (r0 = 16 warp + 8 (lane / 16)), columns c0 .. c0 + 7
+// (c0 = 8 (lane mod 16)).  Step k (p = 1 / S_kk, r = row k, c = column k before the step):
+//     S_ij -= c_i r_j p (i, j != k),   S_kj = r_j p,   S_ik = -c_i p,   S_kk = p.
+// The owners of row k and of column k publish them through shared memory (two buffers, so one
+// barrier per step suffices: a buffer is rewritten two steps later, after every thread has
+// passed the barrier between).  A is strictly diagonally dominant by rows and so is every
+// Schur complement, hence every pivot is positive; a pivot that is not sets ST_BAD_INPUT.
+// Writes S^-1 and S^-T (BL x BL, row-major).
+constexpr int kDiagThreads = 256;
 
-// acc[r] += sum_{k < 32} A[r][k] B[k][lane] for an 8 x 32 strip A and a 32 x 32 block B, both in
-// shared memory with row stride kDiagLd (A's rows read as broadcast float4s).
-__device__ __forceinline__ void strip_product(const float *A, const float *B, int lane, float (&acc)[8]) {
+__global__ void __launch_bounds__(kDiagThreads) diag_inv_kernel(const float *__restrict__ A, int64_t lda,
+                                                                float *__restrict__ Sinv, float *__restrict__ SinvT,
+                                                                int *status) {
+    static_assert(BL == 128 && kDiagThreads == 256, "8 x 8 tiles of a 128 x 128 block");
+    __shared__ __align__(16) float rowbuf[2][BL];
+    __shared__ __align__(16) float colbuf[2][BL];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int r0 = 16 * warp + 8 * (lane >> 4);
+    const int c0 = 8 * (lane & 15);
+    float a[8][8];
 #pragma unroll
-    for (int k = 0; k < 32; k += 4) {
-        const float b0 = B[(k + 0) * kDiagLd + lane], b1 = B[(k + 1) * kDiagLd + lane];
-        const float b2 = B[(k + 2) * kDiagLd + lane], b3 = B[(k + 3) * kDiagLd + lane];
-#pragma unroll
-        for (int r = 0; r < 8; ++r) {
-            const float4 a = *reinterpret_cast<const float4 *>(A + r * kDiagLd + k);
-            acc[r] = fmaf(a.x, b0, acc[r]);
-            acc[r] = fmaf(a.y, b1, acc[r]);
-            acc[r] = fmaf(a.z, b2, acc[r]);
-            acc[r] = fmaf(a.w, b3, acc[r]);
-        }
+    for (int i = 0; i < 8; ++i) {
+        const float4 x = *reinterpret_cast<const float4 *>(A + (r0 + i) * lda + c0);
+        const float4 y = *reinterpret_cast<const float4 *>(A + (r0 + i) * lda + c0 + 4);
+        a[i][0] = x.x, a[i][1] = x.y, a[i][2] = x.z, a[i][3] = x.w;
+        a[i][4] = y.x, a[i][5] = y.y, a[i][6] = y.z, a[i][7] = y.w;
     }
-}
-
-__device__ __forceinline__ void load_row32(const float *p, float (&r)[32]) {
+    bool bad = false;
+#pragma unroll 1
+    for (int kb = 0; kb < BL; kb += 8) {
+        const bool row_owner = r0 == kb;  // rows kb .. kb + 7 are this thread's
+        const bool col_owner = c0 == kb;  // columns kb .. kb + 7 are this thread's
 #pragma unroll
-    for (int c = 0; c < 32; c += 4) {
-        const float4 v = *reinterpret_cast<const float4 *>(p + c);
-        r[c] = v.x;
-        r[c + 1] = v.y;
-        r[c + 2] = v.z;
-        r[c + 3] = v.w;
-    }
-}
-
-__device__ __forceinline__ void store_row32(float *p, const float (&r)[32]) {
+        for (int kk = 0; kk < 8; ++kk) {
+            const int k = kb + kk, buf = k & 1;
+            if (row_owner) {
+                *reinterpret_cast<float4 *>(&rowbuf[buf][c0]) = make_float4(a[kk][0], a[kk][1], a[kk][2], a[kk][3]);
+                *reinterpret_cast<float4 *>(&rowbuf[buf][c0 + 4]) = make_float4(a[kk][4], a[kk][5], a[kk][6], a[kk][7]);
+            }
+            if (col_owner) {
+                *reinterpret_cast<float4 *>(&colbuf[buf][r0]) = make_float4(a[0][kk], a[1][kk], a[2][kk], a[3][kk]);
+                *reinterpret_cast<float4 *>(&colbuf[buf][r0 + 4]) = make_float4(a[4][kk], a[5][kk], a[6][kk], a[7][kk]);
+            }
+            __syncthreads();
+            const float piv = rowbuf[buf][k];
+            const float p = 1.0f / piv;
+            bad |= !(piv > 0.0f) || !isfinite(p);
+            float c[8], rp[8];
+            {
+                const float4 c_lo = *reinterpret_cast<const float4 *>(&colbuf[buf][r0]);
+                const float4 c_hi = *reinterpret_cast<const float4 *>(&colbuf[buf][r0 + 4]);
+                const float4 r_lo = *reinterpret_cast<const float4 *>(&rowbuf[buf][c0]);
+                const float4 r_hi = *reinterpret_cast<const float4 *>(&rowbuf[buf][c0 + 4]);
+                c[0] = c_lo.x, c[1] = c_lo.y, c[2] = c_lo.z, c[3] = c_lo.w;
+                c[4] = c_hi.x, c[5] = c_hi.y, c[6] = c_hi.z, c[7] = c_hi.w;
+                rp[0] = r_lo.x * p, rp[1] = r_lo.y * p, rp[2] = r_lo.z * p, rp[3] = r_lo.w * p;
+                rp[4] = r_hi.x * p, rp[5] = r_hi.y * p, rp[6] = r_hi.z * p, rp[7] = r_hi.w * p;
+            }
 #pragma unroll
-    for (int c = 0; c < 32; c += 4) *reinterpret_cast<float4 *>(p + c) = make_float4(r[c], r[c + 1], r[c + 2], r[c + 3]);
-}
-
-__global__ void __launch_bounds__(kDiagThreads) diag_lu_inv_kernel(const float *A, int64_t lda, float *Linv,
-                                                                   float *Uinv, float *UinvT, int *status) {
-    static_assert(BL == 128, "four 32-column panels");
-    extern __shared__ float4 diag_smem[];
-    float *S = reinterpret_cast<float *>(diag_smem);  // the block; then L (strictly lower) and U in place
-    float *XL = S + BL * kDiagLd;                      // L^-1
-    float *XU = XL + BL * kDiagLd;                     // U^-1
-    int *bad = reinterpret_cast<int *>(XU + BL * kDiagLd);
-    const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
-    if (t == 0) *bad = 0;
-    for (int e = t; e < BL * BL / 4; e += kDiagThreads) {
-        const int r = e >> 5, c = (e & 31) * 4;
-        *reinterpret_cast<float4 *>(S + r * kDiagLd + c) = *reinterpret_cast<const float4 *>(A + r * lda + c);
-    }
-    __syncthreads();
-
-    // ---- 1. LU by 32-column panels ----
-    for (int o = 0; o < BL; o += 32) {
-        const int rem = BL - o - 32;  // rows (and columns) after the panel
-        if (warp == 0) {
-            float *rowp = S + (o + lane) * kDiagLd + o;
-            float r[32];
-            load_row32(rowp, r);
+            for (int i = 0; i < 8; ++i) {
 #pragma unroll
-            for (int j = 0; j < 32; ++j) {
-                if (lane == j) store_row32(rowp, r);  // row j is final after steps 0 .. j-1
-                __syncwarp();
-                const float *pj = S + (o + j) * kDiagLd + o;
-                if (lane > j) {
-                    const float l = r[j] / pj[j];
-                    r[j] = l;
-#pragma unroll
-                    for (int c = j + 1; c < 32; ++c) r[c] = fmaf(-l, pj[c], r[c]);
+                for (int j = 0; j < 8; ++j) {
+                    const float upd = fmaf(-c[i], rp[j], a[i][j]);
+                    if (i == kk && j == kk) {
+                        a[i][j] = row_owner && col_owner ? p : row_owner ? rp[j] : col_owner ? -c[i] * p : upd;
+                    } else if (i == kk) {
+                        a[i][j] = row_owner ? rp[j] : upd;
+                    } else if (j == kk) {
+                        a[i][j] = col_owner ? -c[i] * p : upd;
+                    } else {
+                        a[i][j] = upd;
+                    }
                 }
             }
-            store_row32(rowp, r);
-            const float d = S[(o + lane) * kDiagLd + o + lane];  // U_ii (this lane's row, stored above)
-            if (!(fabsf(d) > 0.0f) || !isfinite(d)) atomicOr(bad, 1);
         }
-        __syncthreads();
-        if (*bad) {  // uniform: every thread reads the flag after the barrier
-            if (t == 0) atomicOr(status, ST_BAD_INPUT);
-            return;
-        }
-        if (rem == 0) break;
-        if (warp >= 1 && warp <= 3 && 32 * (warp - 1) < rem) {  // L21 = A21 U11^-1, lane = row
-            float *rowp = S + (o + 32 + 32 * (warp - 1) + lane) * kDiagLd + o;
-            float r[32];
-            load_row32(rowp, r);
-#pragma unroll
-            for (int j = 0; j < 32; ++j) {
-                const float *uj = S + (o + j) * kDiagLd + o;
-                r[j] = r[j] / uj[j];
-#pragma unroll
-                for (int c = j + 1; c < 32; ++c) r[c] = fmaf(-r[j], uj[c], r[c]);
-            }
-            store_row32(rowp, r);
-        } else if (warp >= 4 && warp <= 6 && 32 * (warp - 4) < rem) {  // U12 = L11^-1 A12, lane = column
-            const int c = o + 32 + 32 * (warp - 4) + lane;
-            float x[32];
-#pragma unroll
-            for (int i = 0; i < 32; ++i) x[i] = S[(o + i) * kDiagLd + c];
-#pragma unroll
-            for (int j = 0; j < 32; ++j) {
-#pragma unroll
-                for (int i = j + 1; i < 32; ++i) x[i] = fmaf(-S[(o + i) * kDiagLd + o + j], x[j], x[i]);
-            }
-#pragma unroll
-            for (int i = 0; i < 32; ++i) S[(o + i) * kDiagLd + c] = x[i];
-        }
-        __syncthreads();
-        const int nbk = rem / 32, tasks = nbk * nbk * 4;  // A22 -= L21 U12: 4 strips per 32 x 32 block
-        for (int task = warp; task < tasks; task += 32) {
-            const int blk = task >> 2, strip = task & 3;
-            const int row0 = o + 32 + 32 * (blk / nbk) + 8 * strip, col0 = o + 32 + 32 * (blk % nbk);
-            float acc[8] = {};
-            strip_product(S + row0 * kDiagLd + o, S + o * kDiagLd + col0, lane, acc);
-#pragma unroll
-            for (int r = 0; r < 8; ++r) S[(row0 + r) * kDiagLd + col0 + lane] -= acc[r];
-        }
-        __syncthreads();
     }
-
-    // ---- 2a. inverses of the diagonal blocks (lane = column) ----
-    if (warp < 4) {  // L_pp^-1, unit lower: forward substitution on e_lane
-        const int o = 32 * warp;
-        float x[32];
+    if (bad) atomicOr(status, ST_BAD_INPUT);
 #pragma unroll
-        for (int i = 0; i < 32; ++i) x[i] = i == lane ? 1.0f : 0.0f;
-#pragma unroll
-        for (int k = 0; k < 32; ++k) {
-#pragma unroll
-            for (int i = k + 1; i < 32; ++i) x[i] = fmaf(-S[(o + i) * kDiagLd + o + k], x[k], x[i]);
-        }
-#pragma unroll
-        for (int i = 0; i < 32; ++i) XL[(o + i) * kDiagLd + o + lane] = x[i];
-    } else if (warp < 8) {  // U_pp^-1 by rows: row lane of U^-1 solves U^T z = e_lane (forward)
-        const int o = 32 * (warp - 4);
-        float z[32];
-#pragma unroll
-        for (int i = 0; i < 32; ++i) z[i] = i == lane ? 1.0f : 0.0f;
-#pragma unroll
-        for (int k = 0; k < 32; ++k) {
-            const float *uk = S + (o + k) * kDiagLd + o;  // row k of U
-            z[k] = z[k] / uk[k];
-#pragma unroll
-            for (int i = k + 1; i < 32; ++i) z[i] = fmaf(-uk[i], z[k], z[i]);
-        }
-        store_row32(XU + (o + lane) * kDiagLd + o, z);
+    for (int i = 0; i < 8; ++i) {
+        *reinterpret_cast<float4 *>(Sinv + (r0 + i) * BL + c0) = make_float4(a[i][0], a[i][1], a[i][2], a[i][3]);
+        *reinterpret_cast<float4 *>(Sinv + (r0 + i) * BL + c0 + 4) = make_float4(a[i][4], a[i][5], a[i][6], a[i][7]);
     }
-    __syncthreads();
-
-    // ---- 2b. blocks off the diagonal, by distance d: warp -> (side, j, strip) ----
-    for (int d = 1; d < 4; ++d) {
-        const int nblk = 4 - d, tasks = 2 * nblk * 4;  // at most 24 <= 32 warps
-        const bool has = warp < tasks;
-        const int task = has ? warp : 0;  // idle warps take task 0's indices and access nothing
-        const int side = task / (nblk * 4), j = (task % (nblk * 4)) >> 2, strip = task & 3;
-        // L side: block (j + d, j) of X;  U side: block (j, j + d) of Y
-        const int bi = side == 0 ? j + d : j, bj = side == 0 ? j : j + d;
-        float *X = side == 0 ? XL : XU;
-        float *dst = X + (32 * bi + 8 * strip) * kDiagLd + 32 * bj;
-        if (has) {  // T = sum_k L_{bi,k} X_{k,bj} (k = bj .. bi-1), or U_{bi,k} Y_{k,bj} (k = bi+1 .. bj)
-            float acc[8] = {};
-            const int k0 = side == 0 ? bj : bi + 1, k1 = side == 0 ? bi - 1 : bj;
-            for (int k = k0; k <= k1; ++k)
-                strip_product(S + (32 * bi + 8 * strip) * kDiagLd + 32 * k, X + 32 * k * kDiagLd + 32 * bj, lane, acc);
 #pragma unroll
-            for (int r = 0; r < 8; ++r) dst[r * kDiagLd + lane] = acc[r];
-        }
-        __syncthreads();
-        float acc[8] = {};
-        if (has)  // -X_{bi,bi} T (the whole T block is read: products first, stores after a barrier)
-            strip_product(X + (32 * bi + 8 * strip) * kDiagLd + 32 * bi, X + 32 * bi * kDiagLd + 32 * bj, lane, acc);
-        __syncthreads();
-        if (has) {
-#pragma unroll
-            for (int r = 0; r < 8; ++r) dst[r * kDiagLd + lane] = -acc[r];
-        }
-        __syncthreads();
-    }
-
-    for (int e = t; e < BL * BL; e += kDiagThreads) {
-        const int r = e >> 7, c = e & (BL - 1);
-        Linv[e] = c < r ? XL[r * kDiagLd + c] : (c == r ? 1.0f : 0.0f);
-        Uinv[e] = c >= r ? XU[r * kDiagLd + c] : 0.0f;
-        UinvT[e] = r >= c ? XU[c * kDiagLd + r] : 0.0f;  // U^-T[r][c] = U^-1[c][r]
+    for (int j = 0; j < 8; ++j) {
+        *reinterpret_cast<float4 *>(SinvT + (c0 + j) * BL + r0) = make_float4(a[0][j], a[1][j], a[2][j], a[3][j]);
+        *reinterpret_cast<float4 *>(SinvT + (c0 + j) * BL + r0 + 4) = make_float4(a[4][j], a[5][j], a[6][j], a[7][j]);
     }
 }
 
@@ -410,10 +290,10 @@ __global__ void group_identity_kernel(float *YL, float *YU, int np, int gw) {
     YU[at] = 1.0f;
 }
 
-__global__ void f32_to_f64_kernel(const float *__restrict__ a, double *__restrict__ b, int64_t count) {
-    for (int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; t < count;
-         t += static_cast<int64_t>(gridDim.x) * blockDim.x)
-        b[t] = static_cast<double>(a[t]);
+// Z = I (np x np, zeroed before).
+__global__ void identity_kernel(float *Z, int np) {
+    const int r = blockIdx.x * blockDim.x + threadIdx.x;
+    if (r < np) Z[static_cast<int64_t>(r) * np + r] = 1.0f;
 }
 
 __global__ void add_f32_kernel(double *__restrict__ x, const float *__restrict__ d, int64_t count) {
@@ -436,7 +316,55 @@ int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 struct Launch {
     int first, count, tiles;  // problems [first, first + count) of the table
     GemmEpi epi;
+    int bn;
 };
+
+// The GEMM table of one mixed solve (every product is C (=|-=) A B'^T, both operands K-major).
+struct Table {
+    std::vector<GemmProblem> probs;
+    std::string err;
+    // Append one problem to `list`: grouped into the list's last launch when asked and the
+    // kinds match, else as a launch of its own.
+    bool add(std::vector<Launch> &list, GemmEpi epi, int bn, int M, int N, int K, const Operand &A,
+             const Operand &B, float *C, int64_t ldc, int r0, int c0, bool group_with_prev, double *fl) {
+        GemmProblem p;
+        GemmEpilogue e{};
+        e.c32 = C;
+        e.ld_c32 = ldc;
+        e.out_row0 = r0;
+        e.out_col0 = c0;
+        if (!gemm_make_problem(&p, KIND_TF32, true, bn, M, N, K, A, B, e, &err)) return false;
+        const int t = p.tiles_m * p.tiles_n;
+        if (group_with_prev && !list.empty() && list.back().epi == epi && list.back().bn == bn &&
+            list.back().first + list.back().count == static_cast<int>(probs.size())) {
+            p.tile_start = list.back().tiles;
+            list.back().count += 1;
+            list.back().tiles += t;
+        } else {
+            p.tile_start = 0;
+            list.push_back(Launch{static_cast<int>(probs.size()), 1, t, epi, bn});
+        }
+        probs.push_back(p);
+        *fl += 2.0 * M * N * K;
+        return true;
+    }
+};
+
+Operand at(Operand o, int r, int c) {
+    o.row0 = r;
+    o.col0 = c;
+    return o;
+}
+
+dl_status mixed_streams(Workspace &ws) {
+    if (ws.mx_stream[0]) return DL_OK;
+    int least = 0, greatest = 0;
+    MCK(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+    MCK(cudaStreamCreateWithPriority(&ws.mx_stream[0], cudaStreamNonBlocking, greatest));
+    MCK(cudaStreamCreateWithPriority(&ws.mx_stream[1], cudaStreamNonBlocking, least));
+    for (auto &e : ws.mx_ev) MCK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    return DL_OK;
+}
 
 }  // namespace
 
@@ -447,41 +375,39 @@ dl_status tc_mixed(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &
     const int nb = static_cast<int>(np / BL);
     const int N = static_cast<int>(np);
     int launches = 0;
+    dl_status rc = mixed_streams(ws);
+    if (rc) return rc;
+    cudaStream_t P = ws.mx_stream[0], U = ws.mx_stream[1];
     auto *A32 = static_cast<float *>(ws.get("mx_A", np * np * 4));
-    auto *Z32 = static_cast<float *>(ws.get("mx_Z", np * np * 4));
+    auto *W32 = static_cast<float *>(ws.get("mx_W", np * np * 4));   // Z = A^-T, then R
+    auto *Wt = static_cast<float *>(ws.get("mx_Wt", np * np * 4));   // W = A^-1
+    auto *D32 = static_cast<float *>(ws.get("mx_D", np * np * 4));
     auto *Z64 = static_cast<double *>(ws.get("mx_Z64", np * np * 8));
     auto *X64 = static_cast<double *>(ws.get("mx_X64", np * np * 8));
-    auto *T = static_cast<float *>(ws.get("mx_T", np * BL * 4));
-    auto *Linv = static_cast<float *>(ws.get("mx_Linv", np * BL * 4));
-    auto *Uinv = static_cast<float *>(ws.get("mx_Uinv", np * BL * 4));
-    auto *UinvT = static_cast<float *>(ws.get("mx_UinvT", np * BL * 4));
-    // group inverses of the solves: a group is kSolveGroup panels (GW columns)
+    auto *T2 = static_cast<float *>(ws.get("mx_T", 2 * np * BL * 4));  // two transposed row panels
+    auto *Sinv = static_cast<float *>(ws.get("mx_Sinv", np * BL * 4));
+    auto *SinvT = static_cast<float *>(ws.get("mx_SinvT", np * BL * 4));
     const int64_t GW = std::min<int64_t>(np, static_cast<int64_t>(kSolveGroup) * BL);
     auto *YL = static_cast<float *>(ws.get("mx_YL", np * GW * 4));
     auto *YU = static_cast<float *>(ws.get("mx_YU", np * GW * 4));
     auto *GL = static_cast<float *>(ws.get("mx_GL", np * GW * 4));
     auto *GU = static_cast<float *>(ws.get("mx_GU", np * GW * 4));
     auto *Tg = static_cast<float *>(ws.get("mx_Tg", np * GW * 4));
-    if (!YL || !YU || !GL || !GU || !Tg) {
-        set_error("mixed path: device allocation failed (group inverses)");
-        return DL_ENOMEM;
-    }
     auto *csr_cnt = static_cast<int *>(ws.get("mx_cnt", (np + 1) * 4));
     auto *csr_ptr = static_cast<int *>(ws.get("mx_ptr", (np + 1) * 4));
-    if (!A32 || !Z32 || !Z64 || !X64 || !T || !Linv || !Uinv || !UinvT || !csr_cnt || !csr_ptr) {
+    if (!A32 || !W32 || !Wt || !D32 || !Z64 || !X64 || !T2 || !Sinv || !SinvT || !YL || !YU || !GL || !GU || !Tg ||
+        !csr_cnt || !csr_ptr) {
         set_error("mixed path: device allocation failed");
         return DL_ENOMEM;
     }
+    float *R32 = W32;  // the residual reuses Z's buffer once W = Z^T is formed
     cudaEvent_t *ev = ws.ev;
     MCK(cudaEventRecord(ev[4], s));
     {
         dim3 grid(static_cast<unsigned>(std::min<int64_t>((np + 255) / 256, 64)), static_cast<unsigned>(np));
         build_a_kernel<<<grid, 256, 0, s>>>(E, n, N, static_cast<float>(eps), A32);
         MCK(cudaGetLastError());
-        dim3 tgrid(static_cast<unsigned>(np / TT), static_cast<unsigned>(np / TT));
-        build_zt_kernel<<<tgrid, dim3(TT, 8), 0, s>>>(a.rhs ? a.rhs : E, n, N, static_cast<float>(eps), Z32);
-        MCK(cudaGetLastError());
-        launches += 2;
+        ++launches;
     }
     // a general right-hand side A: its transpose (bytes) for the residual's A[i][j] terms
     uint8_t *At = nullptr;
@@ -507,172 +433,176 @@ dl_status tc_mixed(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &
     MCK(csr_fill(E, n, csr_ptr, csr_col, s));
     launches += 3;
 
-    // ---- GEMM table (every product is C (=|-=) A B'^T, both operands K-major) --------------
-    std::vector<GemmProblem> probs;
-    std::vector<Launch> lu, ginv, fwd, bwd;
-    // a solve step: a GEMM launch of fwd/bwd, or (launch < 0) the copy of the group panel Tg
-    // back into Z's columns [gs, gs + w)
-    struct Step {
-        int launch, gs, w;
-    };
-    std::vector<Step> fwd_steps, bwd_steps;
-    std::string err;
-    double flops_lu = 0, flops_solve = 0;
-    auto add = [&](std::vector<Launch> &list, GemmEpi epi, int M, int Nn, int K, const Operand &Aop,
-                   const Operand &Bop, float *C, int64_t ldc, int r0, int c0, bool group_with_prev,
-                   double *fl) -> bool {
-        GemmProblem p;
-        GemmEpilogue e{};
-        e.c32 = C;
-        e.ld_c32 = ldc;
-        e.out_row0 = r0;
-        e.out_col0 = c0;
-        if (!gemm_make_problem(&p, KIND_TF32, true, BL, M, Nn, K, Aop, Bop, e, &err)) return false;
-        const int t = p.tiles_m * p.tiles_n;
-        if (group_with_prev && !list.empty() && list.back().epi == epi &&
-            list.back().first + list.back().count == static_cast<int>(probs.size())) {
-            p.tile_start = list.back().tiles;
-            list.back().count += 1;
-            list.back().tiles += t;
-        } else {
-            p.tile_start = 0;
-            list.push_back(Launch{static_cast<int>(probs.size()), 1, t, epi});
-        }
-        probs.push_back(p);
-        *fl += 2.0 * M * Nn * K;
-        return true;
-    };
-    auto at = [](Operand o, int r, int c) {
-        o.row0 = r;
-        o.col0 = c;
-        return o;
-    };
+    // ---- GEMM table ---------------------------------------------------------------------
+    Table tb;
+    std::vector<Launch> l21, ahead, bulk, ginv, wfwd, wbwd, refine;
+    double flops_lu = 0, flops_w = 0, flops_ref = 0;
     const Operand opA{A32, np, np, np, 0, 0};
-    const Operand opZ{Z32, np, np, np, 0, 0};
-    const Operand opT{T, np, BL, BL, 0, 0};
-    const Operand opL{Linv, np, BL, BL, 0, 0};
-    const Operand opU{Uinv, np, BL, BL, 0, 0};
-    const Operand opUT{UinvT, np, BL, BL, 0, 0};
+    const Operand opS{Sinv, np, BL, BL, 0, 0}, opST{SinvT, np, BL, BL, 0, 0};
     bool ok = true;
-    std::vector<int> lu_panel(nb, -1), lu_trail(nb, -1);
+    std::vector<int> has_bulk(nb, -1), has_ahead(nb, -1), has_l21(nb, -1);
     for (int k = 0; k < nb && ok; ++k) {
         const int kb = k * BL, rem = N - kb - BL;
         if (rem <= 0) break;
-        lu_panel[k] = static_cast<int>(lu.size());
-        // U12^T = A12^T L11^-T (in T), L21 = A21 U11^-1 (in place)
-        ok = add(lu, EPI_STORE_F32, rem, BL, BL, opT, at(opL, kb, 0), T, BL, 0, 0, false, &flops_lu) &&
-             add(lu, EPI_STORE_F32, rem, BL, BL, at(opA, kb + BL, kb), at(opUT, kb, 0), A32, np, kb + BL, kb, true,
-                 &flops_lu);
-        lu_trail[k] = static_cast<int>(lu.size());
-        // A22 -= L21 U12
-        ok = ok && add(lu, EPI_SUB_F32, rem, rem, BL, at(opA, kb + BL, kb), opT, A32, np, kb + BL, kb + BL, false,
-                       &flops_lu);
+        const Operand opT{T2 + static_cast<int64_t>(k & 1) * np * BL, np, BL, BL, 0, 0};  // T = A12^T
+        // L21 = A21 S^-1 (in place: each output tile reads only its own rows of A21)
+        has_l21[k] = static_cast<int>(l21.size());
+        ok = tb.add(l21, EPI_STORE_F32, BL, rem, BL, BL, at(opA, kb + BL, kb), at(opST, kb, 0), A32, np, kb + BL, kb,
+                    false, &flops_lu);
+        // look-ahead: block column k+1 (all rows below) and block row k+1 (columns beyond it)
+        has_ahead[k] = static_cast<int>(ahead.size());
+        ok = ok && tb.add(ahead, EPI_SUB_F32, BL, rem, BL, BL, at(opA, kb + BL, kb), opT, A32, np, kb + BL, kb + BL,
+                          false, &flops_lu);
+        if (ok && rem > BL) {
+            ok = tb.add(ahead, EPI_SUB_F32, BL, BL, rem - BL, BL, at(opA, kb + BL, kb), at(opT, BL, 0), A32, np,
+                        kb + BL, kb + 2 * BL, true, &flops_lu);
+            has_bulk[k] = static_cast<int>(bulk.size());
+            ok = ok && tb.add(bulk, EPI_SUB_F32, 256, rem - BL, rem - BL, BL, at(opA, kb + 2 * BL, kb),
+                              at(opT, BL, 0), A32, np, kb + 2 * BL, kb + 2 * BL, false, &flops_lu);
+        }
     }
-    // Inverses of the diagonal groups (kSolveGroup panels each), once per factorisation: the
-    // forward machinery on rows Y = I of a group gives Y L_gg^T = I, i.e. Y = L_gg^-T, and the
-    // backward one Y = U_gg^-T; every step is one launch over all groups.  (Transposed after.)
+    // Inverses of the diagonal groups (kSolveGroup blocks each), once per factorisation.
+    // L_gg is unit block lower: Y = I, Y_{>k} -= Y_k L_{>k,k}^T for k in order gives Y = L_gg^-T.
+    // U_gg is block upper with diagonal blocks S_kk: Y = I, then for k descending
+    // Y_k = Y_k S_kk^-T, Y_{<k} -= Y_k U_{<k,k}^T gives Y = U_gg^-T.  Every step is one launch over
+    // all groups; transposed afterwards (GL = L_gg^-1, GU = U_gg^-1).
     const Operand opYL{YL, np, GW, GW, 0, 0}, opYU{YU, np, GW, GW, 0, 0};
     const Operand opGL{GL, np, GW, GW, 0, 0}, opGU{GU, np, GW, GW, 0, 0};
     const Operand opTg{Tg, np, GW, GW, 0, 0};
     const int ng = (nb + kSolveGroup - 1) / kSolveGroup;
     for (int kl = 0; kl < kSolveGroup && ok; ++kl) {
-        for (int g = 0; g < ng && ok; ++g) {  // Y_k = Y_k L_kk^-T
-            const int g0 = g * kSolveGroup, g1 = std::min(nb, g0 + kSolveGroup), gs = g0 * BL, w = (g1 - g0) * BL;
-            if (g0 + kl < g1)
-                ok = add(ginv, EPI_STORE_F32, w, BL, BL, at(opYL, gs, kl * BL), at(opL, gs + kl * BL, 0), YL, GW, gs,
-                         kl * BL, true, &flops_lu);
-        }
-        for (int g = 0; g < ng && ok; ++g) {  // Y_{>k} -= Y_k L_{>k,k}^T
+        bool first = true;  // step kl needs step kl - 1: a launch of its own
+        for (int g = 0; g < ng && ok; ++g) {
             const int g0 = g * kSolveGroup, g1 = std::min(nb, g0 + kSolveGroup), gs = g0 * BL, ge = g1 * BL,
                       w = ge - gs, kb = gs + kl * BL;
-            if (g0 + kl < g1 && kb + BL < ge)
-                ok = add(ginv, EPI_SUB_F32, w, ge - kb - BL, BL, at(opYL, gs, kl * BL), at(opA, kb + BL, kb), YL, GW,
-                         gs, (kl + 1) * BL, true, &flops_lu);
+            if (g0 + kl < g1 && kb + BL < ge) {
+                ok = tb.add(ginv, EPI_SUB_F32, BL, w, ge - kb - BL, BL, at(opYL, gs, kl * BL), at(opA, kb + BL, kb), YL,
+                            GW, gs, (kl + 1) * BL, !first, &flops_lu);
+                first = false;
+            }
         }
     }
     for (int kl = kSolveGroup - 1; kl >= 0 && ok; --kl) {
-        for (int g = 0; g < ng && ok; ++g) {  // Y_k = Y_k U_kk^-T
+        bool first = true;
+        for (int g = 0; g < ng && ok; ++g) {  // Y_k = Y_k S_kk^-T (in place: N = BL)
             const int g0 = g * kSolveGroup, g1 = std::min(nb, g0 + kSolveGroup), gs = g0 * BL, w = (g1 - g0) * BL;
-            if (g0 + kl < g1)
-                ok = add(ginv, EPI_STORE_F32, w, BL, BL, at(opYU, gs, kl * BL), at(opU, gs + kl * BL, 0), YU, GW, gs,
-                         kl * BL, true, &flops_lu);
+            if (g0 + kl < g1) {
+                ok = tb.add(ginv, EPI_STORE_F32, BL, w, BL, BL, at(opYU, gs, kl * BL), at(opS, gs + kl * BL, 0), YU,
+                            GW, gs, kl * BL, !first, &flops_lu);
+                first = false;
+            }
         }
+        first = true;
         for (int g = 0; g < ng && ok; ++g) {  // Y_{<k} -= Y_k U_{<k,k}^T
             const int g0 = g * kSolveGroup, g1 = std::min(nb, g0 + kSolveGroup), gs = g0 * BL, w = (g1 - g0) * BL,
                       kb = gs + kl * BL;
-            if (g0 + kl < g1 && kb > gs)
-                ok = add(ginv, EPI_SUB_F32, w, kb - gs, BL, at(opYU, gs, kl * BL), at(opA, gs, kb), YU, GW, gs, 0,
-                         true, &flops_lu);
+            if (g0 + kl < g1 && kb > gs) {
+                ok = tb.add(ginv, EPI_SUB_F32, BL, w, kb - gs, BL, at(opYU, gs, kl * BL), at(opA, gs, kb), YU, GW, gs, 0,
+                            !first, &flops_lu);
+                first = false;
+            }
         }
     }
-    // The N-RHS solves by groups: Z_g = Z_g G_g^T (G_g = L_gg^-1 or U_gg^-1, one GEMM with
-    // K = the group's width, into Tg and copied back), then one update with the same K carries
-    // the group to the columns beyond it (forward) or before it (backward).
+    // W: the solves on Z = I.  Forward by groups, Z_g = Z_g L_gg^-T (into Tg, copied back) and
+    // Z_{>g} -= Z_g L_{>g,g}^T; Z = L^-T is block upper triangular, so the forward steps of group g
+    // touch rows [0, ge) only.  Backward by groups, Z_g = Z_g U_gg^-T, Z_{<g} -= Z_g U_{<g,g}^T.
+    struct Step {
+        int launch, gs, w, rows;  // launch < 0: copy Tg back into Z's columns [gs, gs + w), rows rows
+    };
+    std::vector<Step> fwd_steps, bwd_steps;
+    const Operand opZ{W32, np, np, np, 0, 0};
     for (int g = 0; g < ng && ok; ++g) {
         const int g0 = g * kSolveGroup, g1 = std::min(nb, g0 + kSolveGroup), gs = g0 * BL, ge = g1 * BL, w = ge - gs;
-        fwd_steps.push_back(Step{static_cast<int>(fwd.size()), gs, w});
-        ok = add(fwd, EPI_STORE_F32, N, w, w, at(opZ, 0, gs), at(opGL, gs, 0), Tg, GW, 0, 0, false, &flops_solve);
-        fwd_steps.push_back(Step{-1, gs, w});
+        fwd_steps.push_back(Step{static_cast<int>(wfwd.size()), gs, w, ge});
+        ok = tb.add(wfwd, EPI_STORE_F32, 256, ge, w, w, at(opZ, 0, gs), at(opGL, gs, 0), Tg, GW, 0, 0, false, &flops_w);
+        fwd_steps.push_back(Step{-1, gs, w, ge});
         if (ok && ge < N) {
-            fwd_steps.push_back(Step{static_cast<int>(fwd.size()), gs, w});
-            ok = add(fwd, EPI_SUB_F32, N, N - ge, w, at(opTg, 0, 0), at(opA, ge, gs), Z32, np, 0, ge, false,
-                     &flops_solve);
+            fwd_steps.push_back(Step{static_cast<int>(wfwd.size()), gs, w, ge});
+            ok = tb.add(wfwd, EPI_SUB_F32, 256, ge, N - ge, w, at(opTg, 0, 0), at(opA, ge, gs), W32, np, 0, ge, false,
+                        &flops_w);
         }
     }
     for (int g = ng - 1; g >= 0 && ok; --g) {
         const int g0 = g * kSolveGroup, g1 = std::min(nb, g0 + kSolveGroup), gs = g0 * BL, ge = g1 * BL, w = ge - gs;
-        bwd_steps.push_back(Step{static_cast<int>(bwd.size()), gs, w});
-        ok = add(bwd, EPI_STORE_F32, N, w, w, at(opZ, 0, gs), at(opGU, gs, 0), Tg, GW, 0, 0, false, &flops_solve);
-        bwd_steps.push_back(Step{-1, gs, w});
+        bwd_steps.push_back(Step{static_cast<int>(wbwd.size()), gs, w, N});
+        ok = tb.add(wbwd, EPI_STORE_F32, 256, N, w, w, at(opZ, 0, gs), at(opGU, gs, 0), Tg, GW, 0, 0, false, &flops_w);
+        bwd_steps.push_back(Step{-1, gs, w, N});
         if (ok && gs > 0) {
-            bwd_steps.push_back(Step{static_cast<int>(bwd.size()), gs, w});
-            ok = add(bwd, EPI_SUB_F32, N, gs, w, at(opTg, 0, 0), at(opA, 0, gs), Z32, np, 0, 0, false, &flops_solve);
+            bwd_steps.push_back(Step{static_cast<int>(wbwd.size()), gs, w, N});
+            ok = tb.add(wbwd, EPI_SUB_F32, 256, N, gs, w, at(opTg, 0, 0), at(opA, 0, gs), W32, np, 0, 0, false,
+                        &flops_w);
         }
     }
+    // refinement product D^T = R^T W^T (B operand W = A^-1, row-major)
+    ok = ok && tb.add(refine, EPI_STORE_F32, 256, N, N, N, Operand{R32, np, np, np, 0, 0},
+                      Operand{Wt, np, np, np, 0, 0}, D32, np, 0, 0, false, &flops_ref);
     if (!ok) {
-        set_error("mixed path: %s", err.c_str());
+        set_error("mixed path: %s", tb.err.c_str());
         return DL_EDEVICE;
     }
-    auto *dprob = static_cast<GemmProblem *>(ws.get("mx_probs", sizeof(GemmProblem) * probs.size()));
+    auto *dprob = static_cast<GemmProblem *>(ws.get("mx_probs", sizeof(GemmProblem) * tb.probs.size()));
     if (!dprob) {
         set_error("mixed path: device allocation failed (table)");
         return DL_ENOMEM;
     }
-    MCK(cudaMemcpyAsync(dprob, probs.data(), sizeof(GemmProblem) * probs.size(), cudaMemcpyHostToDevice, s));
-    MCK(gemm_prepare(KIND_TF32, true, BL, EPI_STORE_F32));
-    MCK(gemm_prepare(KIND_TF32, true, BL, EPI_SUB_F32));
-
-    auto run = [&](const Launch &L) -> cudaError_t {
+    MCK(cudaMemcpyAsync(dprob, tb.probs.data(), sizeof(GemmProblem) * tb.probs.size(), cudaMemcpyHostToDevice, s));
+    for (int bn : {128, 256}) {
+        MCK(gemm_prepare(KIND_TF32, true, bn, EPI_STORE_F32));
+        MCK(gemm_prepare(KIND_TF32, true, bn, EPI_SUB_F32));
+    }
+    auto run = [&](const Launch &L, int max_grid, cudaStream_t on) -> cudaError_t {
         ++launches;
-        return gemm_launch(KIND_TF32, true, BL, L.epi, dprob + L.first, L.count, L.tiles,
-                           std::min(L.tiles, ctx->sms), ws.status, ctx->budget_ns, s);
+        return gemm_launch(KIND_TF32, true, L.bn, L.epi, dprob + L.first, L.count, L.tiles,
+                           std::min(L.tiles, max_grid), ws.status, ctx->budget_ns, on);
     };
+    const int sms = ctx->sms;
 
-    // ---- LU ----------------------------------------------------------------------------
-    MCK(cudaFuncSetAttribute(diag_lu_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             static_cast<int>(kDiagSmem)));
+    // ---- LU with look-ahead --------------------------------------------------------------
+    MCK(cudaEventRecord(ws.mx_ev[0], s));  // the table and A are ready on s
+    MCK(cudaStreamWaitEvent(P, ws.mx_ev[0], 0));
+    MCK(cudaStreamWaitEvent(U, ws.mx_ev[0], 0));
+    cudaEvent_t evT[2] = {ws.mx_ev[0], ws.mx_ev[1]}, evB[2] = {ws.mx_ev[2], ws.mx_ev[3]};
+    bool bulk_pending = false;  // the bulk update of the previous block is queued on U
     for (int k = 0; k < nb; ++k) {
         const int64_t kb = static_cast<int64_t>(k) * BL;
-        diag_lu_inv_kernel<<<1, kDiagThreads, kDiagSmem, s>>>(A32 + kb * np + kb, np, Linv + kb * BL, Uinv + kb * BL,
-                                                      UinvT + kb * BL, ws.status);
+        const int rem = N - static_cast<int>(kb) - BL;
+        diag_inv_kernel<<<1, kDiagThreads, 0, P>>>(A32 + kb * np + kb, np, Sinv + kb * BL, SinvT + kb * BL, ws.status);
         MCK(cudaGetLastError());
         ++launches;
-        if (lu_panel[k] >= 0) {
-            const int rem = N - static_cast<int>(kb) - BL;
-            MCK(transpose(A32 + kb * np + kb + BL, np, BL, rem, T, BL, s));  // T = A12^T
-            MCK(run(lu[lu_panel[k]]));                                        // T = U12^T, L21
-            MCK(transpose(T, BL, rem, BL, A32 + kb * np + kb + BL, np, s));  // A12 = U12
-            MCK(run(lu[lu_trail[k]]));                                        // A22 -= L21 U12
-            launches += 2;
+        if (rem <= 0) break;
+        // L21 runs beside the bulk update of block k - 1, which leaves it kReserve SMs
+        const bool beside_bulk = k > 0 && has_bulk[k - 1] >= 0;
+        MCK(run(l21[has_l21[k]], beside_bulk ? kReserve : sms, P));
+        float *Tk = T2 + static_cast<int64_t>(k & 1) * np * BL;
+        MCK(transpose(A32 + kb * np + kb + BL, np, BL, rem, Tk, BL, P));  // T = A12^T
+        ++launches;
+        MCK(cudaEventRecord(evT[k & 1], P));
+        if (bulk_pending) MCK(cudaStreamWaitEvent(P, evB[(k - 1) & 1], 0));
+        // the look-ahead launch (one or two problems)
+        {
+            Launch L = ahead[has_ahead[k]];
+            MCK(run(L, sms, P));
+        }
+        bulk_pending = false;
+        if (has_bulk[k] >= 0) {
+            MCK(cudaStreamWaitEvent(U, evT[k & 1], 0));
+            MCK(run(bulk[has_bulk[k]], std::max(1, sms - kReserve), U));
+            MCK(cudaEventRecord(evB[k & 1], U));
+            bulk_pending = true;
         }
     }
+    MCK(cudaEventRecord(ws.mx_ev[0], U));  // (evT[0] is no longer needed)
+    MCK(cudaStreamWaitEvent(P, ws.mx_ev[0], 0));
+    MCK(cudaEventRecord(ws.mx_ev[1], P));
+    MCK(cudaStreamWaitEvent(s, ws.mx_ev[1], 0));
+
     // group inverses: Y = I on each group's rows, the grouped steps, then G = Y^T per group
     MCK(cudaMemsetAsync(YL, 0, np * GW * 4, s));
     MCK(cudaMemsetAsync(YU, 0, np * GW * 4, s));
     group_identity_kernel<<<static_cast<unsigned>((np + 255) / 256), 256, 0, s>>>(YL, YU, N, static_cast<int>(GW));
     MCK(cudaGetLastError());
     ++launches;
-    for (const Launch &L : ginv) MCK(run(L));
+    for (const Launch &L : ginv) MCK(run(L, sms, s));
     for (int64_t gs = 0; gs < np; gs += GW) {
         const int w = static_cast<int>(std::min<int64_t>(GW, np - gs));
         MCK(transpose(YL + gs * GW, GW, w, w, GL + gs * GW, GW, s));
@@ -680,31 +610,29 @@ dl_status tc_mixed(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &
         launches += 2;
     }
     MCK(cudaEventRecord(ev[5], s));
-    auto solve = [&]() -> cudaError_t {
-        cudaError_t e;
-        for (int pass = 0; pass < 2; ++pass) {
-            const std::vector<Step> &steps = pass == 0 ? fwd_steps : bwd_steps;
-            const std::vector<Launch> &list = pass == 0 ? fwd : bwd;
-            for (const Step &st_ : steps) {
-                if (st_.launch >= 0) {
-                    if ((e = run(list[st_.launch])) != cudaSuccess) return e;
-                } else if ((e = cudaMemcpy2DAsync(Z32 + st_.gs, np * 4, Tg, GW * 4, static_cast<size_t>(st_.w) * 4, np,
-                                                  cudaMemcpyDeviceToDevice, s)) != cudaSuccess) {
-                    return e;
-                }
+
+    // ---- W = A^-1 ------------------------------------------------------------------------
+    MCK(cudaMemsetAsync(W32, 0, np * np * 4, s));
+    identity_kernel<<<static_cast<unsigned>((np + 255) / 256), 256, 0, s>>>(W32, N);
+    MCK(cudaGetLastError());
+    ++launches;
+    for (int pass = 0; pass < 2; ++pass) {
+        const std::vector<Step> &steps = pass == 0 ? fwd_steps : bwd_steps;
+        const std::vector<Launch> &list = pass == 0 ? wfwd : wbwd;
+        for (const Step &sp : steps) {
+            if (sp.launch >= 0) {
+                MCK(run(list[sp.launch], sms, s));
+            } else {
+                MCK(cudaMemcpy2DAsync(W32 + sp.gs, np * 4, Tg, GW * 4, static_cast<size_t>(sp.w) * 4, sp.rows,
+                                      cudaMemcpyDeviceToDevice, s));
             }
         }
-        return cudaSuccess;
-    };
-    MCK(solve());
-    const int64_t cnt = np * np;
-    const unsigned eblocks = static_cast<unsigned>(std::min<int64_t>((cnt + 255) / 256, 8 * 1024));
-    f32_to_f64_kernel<<<eblocks, 256, 0, s>>>(Z32, Z64, cnt);
-    MCK(cudaGetLastError());
+    }
+    MCK(transpose(W32, np, N, N, Wt, np, s));  // W = (A^-T)^T
     ++launches;
     MCK(cudaEventRecord(ev[6], s));
 
-    // ---- refinement ----------------------------------------------------------------------
+    // ---- refinement from Z = 0 -------------------------------------------------------------
     const double tol = ctx->cfg.refine_tol > 0 ? ctx->cfg.refine_tol : 1e-13;
     const int max_iters = ctx->cfg.refine_max_iters > 0 ? ctx->cfg.refine_max_iters : 30;
     // rows of Z per residual block: as many (up to 3) as shared memory holds
@@ -725,31 +653,34 @@ dl_status tc_mixed(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &
                 if ((e = cudaFuncSetAttribute(residual_fixed_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                               static_cast<int>(res_smem))) != cudaSuccess)
                     return e;
-                residual_fixed_kernel<3><<<grid, 1024, res_smem, s>>>(csr_ptr, csr_col, n, N, deg_bits, eps, Z64, Z32,
+                residual_fixed_kernel<3><<<grid, 1024, res_smem, s>>>(csr_ptr, csr_col, n, N, deg_bits, eps, Z64, R32,
                                                                      rmax_p, At);
                 break;
             case 2:
                 if ((e = cudaFuncSetAttribute(residual_fixed_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                               static_cast<int>(res_smem))) != cudaSuccess)
                     return e;
-                residual_fixed_kernel<2><<<grid, 1024, res_smem, s>>>(csr_ptr, csr_col, n, N, deg_bits, eps, Z64, Z32,
+                residual_fixed_kernel<2><<<grid, 1024, res_smem, s>>>(csr_ptr, csr_col, n, N, deg_bits, eps, Z64, R32,
                                                                      rmax_p, At);
                 break;
             default:
                 if ((e = cudaFuncSetAttribute(residual_fixed_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                               static_cast<int>(res_smem))) != cudaSuccess)
                     return e;
-                residual_fixed_kernel<1><<<grid, 1024, res_smem, s>>>(csr_ptr, csr_col, n, N, deg_bits, eps, Z64, Z32,
+                residual_fixed_kernel<1><<<grid, 1024, res_smem, s>>>(csr_ptr, csr_col, n, N, deg_bits, eps, Z64, R32,
                                                                      rmax_p, At);
         }
         return cudaGetLastError();
     };
+    const int64_t cnt = np * np;
+    const unsigned eblocks = static_cast<unsigned>(std::min<int64_t>((cnt + 255) / 256, 8 * 1024));
     unsigned long long *rmax_d = ws.scal + 20;
     double rmax = 0.0, best = 0.0;
-    int it = 0, stall = 0;
+    int products = 0, stall = 0;
     // The FP64 residual has a rounding floor of about (row length) * u * max|X|; refinement
     // stops at tol, or when it no longer halves the residual once that is below 1e-8 * eps.
     const double floor_ok = 1e-8 * eps;
+    MCK(cudaMemsetAsync(Z64, 0, np * np * 8, s));
     for (;;) {
         MCK(cudaMemsetAsync(rmax_d, 0, sizeof(unsigned long long), s));
         MCK(residual(rmax_d));
@@ -759,31 +690,34 @@ dl_status tc_mixed(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &
         MCK(cudaStreamSynchronize(s));
         std::memcpy(&rmax, &h, sizeof(rmax));
         if (rmax <= tol * eps) break;
-        if (it == 0 || rmax < 0.5 * best) {
-            best = rmax;
-            stall = 0;
-        } else if (++stall >= 2 && best <= floor_ok) {
-            break;
+        if (products >= 1) {  // after the solve: refinement steps must keep halving the residual
+            if (products == 1 || rmax < 0.5 * best) {
+                best = rmax;
+                stall = 0;
+            } else if (++stall >= 2 && best <= floor_ok) {
+                break;
+            }
         }
-        if (it >= max_iters) {
-            set_error("mixed path: refinement stopped at max|R|/eps = %.3g after %d steps", rmax / eps, it);
+        if (products > max_iters) {
+            set_error("mixed path: refinement stopped at max|R|/eps = %.3g after %d steps", rmax / eps, products - 1);
             return DL_ENOTCONV;
         }
-        MCK(solve());
-        add_f32_kernel<<<eblocks, 256, 0, s>>>(Z64, Z32, cnt);
+        MCK(run(refine[0], sms, s));  // D^T = R^T W^T
+        add_f32_kernel<<<eblocks, 256, 0, s>>>(Z64, D32, cnt);
         MCK(cudaGetLastError());
         ++launches;
-        ++it;
+        ++products;
     }
     MCK(transpose(Z64, np, N, N, X64, np, s));  // X = Z^T
     ++launches;
     MCK(cudaEventRecord(ev[7], s));
     MCK(cudaEventSynchronize(ev[7]));
     if (st) {
-        st->iters = it;
+        st->iters = std::max(products - 1, 0);  // refinement steps after the first product (the solve)
         st->final_resid = rmax / eps;
-        st->gemm_flops = flops_lu + flops_solve * (1 + it);
-        st->gemm_launches = static_cast<int>(lu.size() + ginv.size() + (fwd.size() + bwd.size()) * (1 + it));
+        st->gemm_flops = flops_lu + flops_w + flops_ref * products;
+        st->gemm_launches = static_cast<int>(l21.size() + ahead.size() + bulk.size() + ginv.size() + wfwd.size() +
+                                             wbwd.size()) + products;
         float t1 = 0, t2 = 0, t3 = 0;
         cudaEventElapsedTime(&t1, ev[4], ev[5]);
         cudaEventElapsedTime(&t2, ev[5], ev[6]);

@@ -1614,6 +1614,12 @@ void Workspace::release() {
         if (x) cudaEventDestroy(x);
     for (auto &x : sev)
         if (x) cudaEventDestroy(x);
+    for (auto &x : mx_ev)
+        if (x) cudaEventDestroy(x);
+    for (auto &x : mx_stream)
+        if (x) cudaStreamDestroy(x);
+    for (auto &x : mx_ev) x = nullptr;
+    for (auto &x : mx_stream) x = nullptr;
     host_pinned = nullptr;
     status = nullptr;
     scal = nullptr;

@@ -16,9 +16,14 @@
 //   warp 1      allocates 2*BN TMEM columns (two FP32 accumulators of 128 lanes x BN) and one
 //               elected thread issues tcgen05.mma; tcgen05.commit releases smem stages and
 //               signals a finished accumulator.
-//   warps 2..5  epilogue: tcgen05.ld 32 lanes x 32 columns, fused min1/OR/bit-pack/popcount
+//   warps 2..9  epilogue: tcgen05.ld 32 lanes x 32 columns, fused min1/OR/bit-pack/popcount
 //               (boolean) or read-modify-write of C (TF32 update), then release the
-//               accumulator so the next tile's MMAs overlap this epilogue.
+//               accumulator so the next tile's MMAs overlap this epilogue.  A warp may only
+//               read the TMEM lane quarter (warp % 4), so two warps share each quarter and take
+//               alternate 32-column chunks; the subtracting epilogue loads its first chunk of C
+//               before the accumulator is ready and the next chunk while it finishes the current
+//               one (a K = 128 update moves 8 bytes of C per 256 flops: it needs that many bytes
+//               in flight to run at HBM rate).
 // Problems come from a device-memory table so that one launch can cover many independent
 // problems (a grouped GEMM for the uneven batch).
 #include <cuda.h>
@@ -36,7 +41,8 @@ namespace dl {
 namespace {
 
 constexpr int BM = 128;
-constexpr int kThreads = 192;
+constexpr int kEpiWarps = 8;
+constexpr int kThreads = 64 + 32 * kEpiWarps;
 
 template <int KIND, int BN>
 struct Cfg {
@@ -163,20 +169,26 @@ __device__ __forceinline__ void epi_store_chunk(const GemmEpilogue &e, int row, 
                            __uint_as_float(v[4 * q + 2]), __uint_as_float(v[4 * q + 3]));
 }
 
-__device__ __forceinline__ void epi_sub_chunk(const GemmEpilogue &e, int row, int col,
-                                              const uint32_t (&v)[32]) {
+__device__ __forceinline__ float4 *c_chunk(const GemmEpilogue &e, int row, int col) {
     const int64_t r = static_cast<int64_t>(e.out_row0) + row;
     const int64_t c = static_cast<int64_t>(e.out_col0) + col;
-    float4 *p = reinterpret_cast<float4 *>(e.c32 + r * e.ld_c32 + c);
+    return reinterpret_cast<float4 *>(e.c32 + r * e.ld_c32 + c);
+}
+
+__device__ __forceinline__ void load_c_chunk(const GemmEpilogue &e, int row, int col, float4 (&x)[8]) {
+    const float4 *p = c_chunk(e, row, col);
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
-        float4 x = p[q];
-        x.x -= __uint_as_float(v[4 * q + 0]);
-        x.y -= __uint_as_float(v[4 * q + 1]);
-        x.z -= __uint_as_float(v[4 * q + 2]);
-        x.w -= __uint_as_float(v[4 * q + 3]);
-        p[q] = x;
-    }
+    for (int q = 0; q < 8; ++q) x[q] = p[q];
+}
+
+// C -= acc on one chunk whose old values x were loaded earlier.
+__device__ __forceinline__ void epi_sub_chunk(const GemmEpilogue &e, int row, int col, const float4 (&x)[8],
+                                              const uint32_t (&v)[32]) {
+    float4 *p = c_chunk(e, row, col);
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+        p[q] = make_float4(x[q].x - __uint_as_float(v[4 * q + 0]), x[q].y - __uint_as_float(v[4 * q + 1]),
+                           x[q].z - __uint_as_float(v[4 * q + 2]), x[q].w - __uint_as_float(v[4 * q + 3]));
 }
 
 template <int KIND, int BN, bool B_KMAJOR, int EPI>
@@ -213,7 +225,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         }
         for (int a = 0; a < 2; ++a) {
             mbar_init(&accf[a], 1);
-            mbar_init(&acce[a], 128);
+            mbar_init(&acce[a], 32 * kEpiWarps);
         }
         mbar_init(drain, 1);
         fence_barrier_init();
@@ -331,9 +343,11 @@ __global__ void __launch_bounds__(kThreads, 1)
             mbar_wait_bounded(drain, 0u, budget_ns, status, ST_TIMEOUT_DRAIN);
         }
     } else {
-        // ------------------------------ epilogue (warps 2..5) ---------------------------
-        const int quarter = warp & 3;  // TMEM lanes this warp may access
+        // ------------------------------ epilogue (warps 2..9) ---------------------------
+        const int quarter = warp & 3;       // TMEM lanes this warp may access
+        const int half = (warp - 2) >> 2;   // this warp's chunks: half, half + 2, ...
         const int r_in_tile = quarter * 32 + lane;
+        constexpr int kChunks = BN / 32;
         int acc = 0;
         uint32_t acc_ph = 0;
         for (int tile = blockIdx.x; tile < total_tiles; tile += gridDim.x) {
@@ -341,17 +355,25 @@ __global__ void __launch_bounds__(kThreads, 1)
             const GemmProblem *P = resolve_tile(probs, nprob, sched, tile, &local);
             if (P == nullptr) continue;
             const int mb = local % P->tiles_m, nb = local / P->tiles_m;
+            const int row = mb * BM + r_in_tile;
+            const bool row_ok = row < P->M;
+            // the first chunk of C is on its way while the MMAs finish
+            float4 cur[8], nxt[8];
+            bool have = row_ok && nb * BN + half * 32 < P->N;
+            if (EPI == EPI_SUB_F32 && have) load_c_chunk(P->epi, row, nb * BN + half * 32, cur);
             if (!mbar_wait_bounded(&accf[acc], acc_ph, budget_ns, status, ST_TIMEOUT_ACC_FULL))
                 break;
             tc_fence_after();
-            const int row = mb * BM + r_in_tile;
-            const bool row_ok = row < P->M;
             const bool live = tile_live<BN>(P, mb, nb, P->K / C::BK);  // warp-uniform
             const uint32_t tbase = tmem_base + (static_cast<uint32_t>(quarter * 32) << 16) +
                                    static_cast<uint32_t>(acc * BN);
             uint32_t cnt = 0;
 #pragma unroll 1
-            for (int c = 0; c < BN / 32; ++c) {
+            for (int c = half; c < kChunks; c += 2) {
+                const int col = nb * BN + c * 32;
+                const int cn = c + 2;
+                const bool have_n = cn < kChunks && row_ok && nb * BN + cn * 32 < P->N;
+                if (EPI == EPI_SUB_F32 && have_n) load_c_chunk(P->epi, row, nb * BN + cn * 32, nxt);
                 uint32_t v[32];
                 if (live) {
                     tmem_ld_32x32b_x32(tbase + c * 32, v);
@@ -360,11 +382,10 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
                     for (int j = 0; j < 32; ++j) v[j] = 0u;
                 }
-                const int col = nb * BN + c * 32;
                 uint32_t word = 0;
-                if (row_ok && col < P->N) {
+                if (have) {
                     if (EPI == EPI_BOOL) word = epi_bool_chunk(P->epi, row, col, v, cnt);
-                    else if (EPI == EPI_SUB_F32) epi_sub_chunk(P->epi, row, col, v);
+                    else if (EPI == EPI_SUB_F32) epi_sub_chunk(P->epi, row, col, cur, v);
                     else epi_store_chunk(P->epi, row, col, v);
                 }
                 if (EPI == EPI_BOOL && P->epi.occ_out != nullptr) {
@@ -372,6 +393,11 @@ __global__ void __launch_bounds__(kThreads, 1)
                         P->epi.occ_out[((P->epi.out_row0 + mb * BM + quarter * 32) >> 7) * P->epi.occ_ld +
                                        ((P->epi.out_col0 + col) >> 7)] = 1;
                 }
+                if (EPI == EPI_SUB_F32) {
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) cur[q] = nxt[q];
+                }
+                have = have_n;
             }
             tc_fence_before();
             mbar_arrive(&acce[acc]);
@@ -472,10 +498,13 @@ cudaError_t gemm_prepare(GemmKind kind, bool b_kmajor, int bn, GemmEpi epi) {
         if (bn == 128) return b_kmajor ? prepare_t<KIND_F8, 128, true, EPI_BOOL>() : prepare_t<KIND_F8, 128, false, EPI_BOOL>();
     }
     // TF32 runs with K-major operands only (both operands row-major with K contiguous)
-    if (kind == KIND_TF32 && epi == EPI_SUB_F32 && bn == 128 && b_kmajor)
-        return prepare_t<KIND_TF32, 128, true, EPI_SUB_F32>();
-    if (kind == KIND_TF32 && epi == EPI_STORE_F32 && bn == 128 && b_kmajor)
-        return prepare_t<KIND_TF32, 128, true, EPI_STORE_F32>();
+    if (kind == KIND_TF32 && b_kmajor && (bn == 128 || bn == 256)) {
+        if (epi == EPI_SUB_F32)
+            return bn == 256 ? prepare_t<KIND_TF32, 256, true, EPI_SUB_F32>() : prepare_t<KIND_TF32, 128, true, EPI_SUB_F32>();
+        if (epi == EPI_STORE_F32)
+            return bn == 256 ? prepare_t<KIND_TF32, 256, true, EPI_STORE_F32>()
+                             : prepare_t<KIND_TF32, 128, true, EPI_STORE_F32>();
+    }
     return cudaErrorInvalidValue;
 }
 
@@ -527,10 +556,13 @@ cudaError_t gemm_launch(GemmKind kind, bool b_kmajor, int bn, GemmEpi epi, const
         if (bn == 128)
             return b_kmajor ? DL_GEMM_T(KIND_F8, 128, true, EPI_BOOL) : DL_GEMM_T(KIND_F8, 128, false, EPI_BOOL);
     }
-    if (kind == KIND_TF32 && epi == EPI_SUB_F32 && bn == 128 && b_kmajor)
-        return DL_GEMM_T(KIND_TF32, 128, true, EPI_SUB_F32);
-    if (kind == KIND_TF32 && epi == EPI_STORE_F32 && bn == 128 && b_kmajor)
-        return DL_GEMM_T(KIND_TF32, 128, true, EPI_STORE_F32);
+    if (kind == KIND_TF32 && b_kmajor && (bn == 128 || bn == 256)) {
+        if (epi == EPI_SUB_F32)
+            return bn == 256 ? DL_GEMM_T(KIND_TF32, 256, true, EPI_SUB_F32) : DL_GEMM_T(KIND_TF32, 128, true, EPI_SUB_F32);
+        if (epi == EPI_STORE_F32)
+            return bn == 256 ? DL_GEMM_T(KIND_TF32, 256, true, EPI_STORE_F32)
+                             : DL_GEMM_T(KIND_TF32, 128, true, EPI_STORE_F32);
+    }
 #undef DL_GEMM_T
     return cudaErrorInvalidValue;
 }
