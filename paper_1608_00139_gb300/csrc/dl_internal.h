@@ -84,6 +84,10 @@ cudaError_t gemm_launch(GemmKind kind, bool b_kmajor, int bn, GemmEpi epi,
                         int *d_status, uint64_t budget_ns, cudaStream_t stream,
                         const int *d_sched = nullptr);
 int gemm_tile_m();
+// A 2-D tensor map (no swizzle) of a row-major matrix (rows x cols elements, ld elements per
+// row) with a box of box_y rows x box_x elements, for TMA loads outside the GEMM.
+bool tensor_map_2d(CUtensorMap *m, CUtensorMapDataType dt, int elem, const void *base, int64_t cols, int64_t rows,
+                   int64_t ld, uint32_t box_x, uint32_t box_y, std::string *err);
 // Set the kernel's shared-memory attribute ahead of time (e.g. before a stream capture).
 cudaError_t gemm_prepare(GemmKind kind, bool b_kmajor, int bn, GemmEpi epi);
 

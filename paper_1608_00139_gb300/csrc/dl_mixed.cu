@@ -37,6 +37,7 @@
 
 #include "dl_ctx.h"
 #include "dl_internal.h"
+#include "dl_ptx.cuh"
 
 namespace dl {
 
@@ -45,8 +46,7 @@ namespace {
 constexpr int BL = 128;        // LU block size = GEMM tile
 constexpr int TT = 32;         // transpose tile
 constexpr int kSolveGroup = 8;  // blocks per group of the solves (1024 columns)
-constexpr int kReserve = 16;   // SMs the bulk LU update leaves to the critical chain
-constexpr size_t kResidualSmem = 227 * 1024;  // dynamic shared memory of one residual block
+constexpr int kReserve = 32;   // SMs the bulk LU update leaves to the critical chain
 
 __global__ void build_a_kernel(const uint8_t *__restrict__ E, int n, int np, float eps, float *__restrict__ A) {
     const int64_t row = blockIdx.y;
@@ -128,7 +128,7 @@ __global__ void __launch_bounds__(kDiagThreads) diag_inv_kernel(const float *__r
             }
             __syncthreads();
             const float piv = rowbuf[buf][k];
-            const float p = 1.0f / piv;
+            const float p = __fdividef(1.0f, piv);  // within 2 ulp: S^-1 only preconditions the refinement
             bad |= !(piv > 0.0f) || !isfinite(p);
             float c[8], rp[8];
             {
@@ -185,62 +185,82 @@ __device__ __forceinline__ long long fixed_of(long long bits, int e) {
     return bits < 0 ? -v : v;
 }
 
-// Residual of the transposed system for G rows j of Z per block (the rows share each read of
-// the CSR):  R^T[j][i] = eps * sum_{k in succ(i)} (Z[j][k] + [k = j]) - Z[j][i]  (right-hand side
-// eps E; with At, the bytes of A^T, the term [k = j] becomes A[i][j]: right-hand side eps A),  stored as FP32
-// (right-hand side of the correction solve); max |R| -> *rmax.  The sums are exact in 64-bit
-// fixed point: row j sits in shared memory as round((Z[j][k] + [k = j]) 2^e_j), e_j chosen from
-// the row's largest exponent and 2^deg_bits >= ||E||_inf so that no sum reaches 2^62.  Each
-// term is rounded once (at most 2^-(e_j + 1), below one FP64 ulp of the row's largest entry);
-// the scaling by eps 2^-e_j and the subtraction are one FP64 fma.
+// Scale of row j of Z in the residual: every term of a sum (the +1 or A[i][j] included) stays
+// below 2^hb, hb from the row's largest exponent field, and a sum of at most 2^deg_bits terms
+// below 2^62.
+__device__ __forceinline__ int row_scale(int ex_max, int deg_bits) {
+    const int hb = max(ex_max - 1022, 0) + 1;
+    return max(0, 62 - deg_bits - hb);
+}
+
+// floor(s * eps_q / 2^62) for |s| < 2^62, 0 <= eps_q <= 2^62: eps s in fixed point, with
+// eps_q = round(eps 2^62) (a 128-bit product, integer units only).
+__device__ __forceinline__ long long mul_eps(long long s, long long eps_q) {
+    const unsigned long long lo = static_cast<unsigned long long>(s) * static_cast<unsigned long long>(eps_q);
+    const long long hi = __mul64hi(s, eps_q);
+    return static_cast<long long>((static_cast<unsigned long long>(hi) << 2) | (lo >> 62));
+}
+
+// r (|r| < 2^62) as a float, within one rounding of the nearest: two exact 32-bit conversions
+// of its halves combined by one fma.
+__device__ __forceinline__ float float_of(long long r) {
+    const float hi = static_cast<float>(static_cast<int>(r >> 31));
+    const float lo = static_cast<float>(static_cast<unsigned>(r & 0x7FFFFFFFll));
+    return fmaf(hi, 2147483648.0f, lo);
+}
+
+// Residual of the transposed system:
+//     R^T[j][i] = eps * sum_{k in succ(i)} (Z[j][k] + [k = j]) - Z[j][i]
+// (right-hand side eps E; with rhs, a general right-hand side eps A, the [k = j] term becomes
+// A[i][j]), as FP32 (right-hand side of the next correction), and max |R| into *rmax (bits of a
+// non-negative float).  The sums are exact in 64-bit fixed point: Zf[j][k] = round(Z[j][k] 2^e_j)
+// (plus 2^e_j at k = j for the closure's right-hand side), written by add_fix_kernel with e_j
+// chosen so that no sum reaches 2^62; eps times a sum is an exact 128-bit product with
+// eps_q = round(eps 2^62), floored; the result is rounded once to FP32.  Every error is below
+// 2^-(62 - deg_bits) of the row's largest entry, under one FP64 ulp of it, and no FP64 unit is
+// used.  Two kernels compute it, by the density of E:
+
+// R^T[j][i] from the fixed-point sum and Zf[j][i] (the result's last step).
+__device__ __forceinline__ float residual_entry(long long sum, long long z, int i, int j, int n, int e,
+                                                long long eps_q, float inv, const uint8_t *rhs) {
+    if (rhs != nullptr) {
+        if (rhs[static_cast<int64_t>(i) * n + j]) sum += 1ll << e;
+    } else if (i == j) {
+        z -= 1ll << e;  // Zf carries the [k = j] term
+    }
+    return float_of(mul_eps(sum, eps_q) - z) * inv;
+}
+
+// (1) Sparse E: G rows j of Zf per block in shared memory, a thread per row i walking its
+// successors (few gathers per row; Zf is read once).
 template <int G>
 __global__ void __launch_bounds__(1024, 1)
-    residual_fixed_kernel(const int *__restrict__ ptr, const int *__restrict__ col, int n, int np, int deg_bits,
-                          double eps, const double *__restrict__ Z, float *__restrict__ R, unsigned long long *rmax,
-                          const uint8_t *__restrict__ At) {
-    extern __shared__ long long zi[];  // G rows of np entries
-    __shared__ int ex_max[G];
+    residual_rows_kernel(const int *__restrict__ ptr, const int *__restrict__ col, int n, int np, long long eps_q,
+                         const int *__restrict__ escale, const long long *__restrict__ Zf, float *__restrict__ R,
+                         unsigned *rmax, const uint8_t *__restrict__ rhs) {
+    extern __shared__ long long zi[];  // G rows of np
     const int j0 = blockIdx.x * G;
-    if (threadIdx.x < G) ex_max[threadIdx.x] = 0;
-    __syncthreads();
 #pragma unroll
-    for (int g = 0; g < G; ++g) {  // stage the raw bits and find the largest exponent
-        const int j = j0 + g;
-        int ex = 0;
-        if (j < np) {
-            const long long *zb = reinterpret_cast<const long long *>(Z + static_cast<int64_t>(j) * np);
-            for (int k = threadIdx.x; k < np; k += blockDim.x) {
-                const long long b = zb[k];
-                zi[g * np + k] = b;
-                ex = max(ex, static_cast<int>((b >> 52) & 0x7FF));
-            }
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) ex = max(ex, __shfl_xor_sync(0xffffffffu, ex, o));
-        if ((threadIdx.x & 31) == 0) atomicMax(&ex_max[g], ex);
+    for (int g = 0; g < G; ++g) {
+        const longlong2 *src = reinterpret_cast<const longlong2 *>(Zf + static_cast<int64_t>(j0 + g) * np);
+        longlong2 *dst = reinterpret_cast<longlong2 *>(zi + g * np);
+        const bool live = j0 + g < np;
+#pragma unroll 4
+        for (int t = threadIdx.x; t < np / 2; t += blockDim.x) dst[t] = live ? src[t] : make_longlong2(0, 0);
     }
     __syncthreads();
     int e[G];
-    double scale[G];
+    float inv[G];
 #pragma unroll
     for (int g = 0; g < G; ++g) {
-        // every term, the +1 included, is below 2^hb; a sum of at most 2^deg_bits terms below 2^62
-        const int hb = max(ex_max[g] - 1022, 0) + 1;
-        e[g] = max(0, 62 - deg_bits - hb);
-        scale[g] = ldexp(eps, -e[g]);
+        e[g] = j0 + g < np ? escale[j0 + g] : 0;
+        inv[g] = __int_as_float((127 - e[g]) << 23);  // 2^-e (0 <= e <= 62)
     }
-#pragma unroll
-    for (int g = 0; g < G; ++g)
-        for (int k = threadIdx.x; k < np; k += blockDim.x) zi[g * np + k] = fixed_of(zi[g * np + k], e[g]);
-    __syncthreads();
-    if (threadIdx.x < G && At == nullptr) {  // the eps E[i][j] term, as k = j
-        const int g = threadIdx.x, j = j0 + g;
-        if (j < n) zi[g * np + j] += 1ll << e[g];
-    }
-    __syncthreads();
     float m = 0.0f;
     for (int i = threadIdx.x; i < np; i += blockDim.x) {
-        long long sum[G] = {};
+        long long sum[G];
+#pragma unroll
+        for (int g = 0; g < G; ++g) sum[g] = 0;
         if (i < n) {
             const int q1 = ptr[i + 1];
             int q = ptr[i];
@@ -255,29 +275,258 @@ __global__ void __launch_bounds__(1024, 1)
 #pragma unroll
                 for (int g = 0; g < G; ++g) sum[g] += zi[g * np + c];
             }
-            if (At != nullptr) {  // a general right-hand side: the eps A[i][j] term from A^T's row j
-#pragma unroll
-                for (int g = 0; g < G; ++g) {
-                    const int j = j0 + g;
-                    if (j < n && At[static_cast<int64_t>(j) * n + i]) sum[g] += 1ll << e[g];
-                }
-            }
         }
 #pragma unroll
         for (int g = 0; g < G; ++g) {
             const int j = j0 + g;
             if (j >= np) break;
             float r = 0.0f;
-            if (i < n && j < n)
-                r = static_cast<float>(fma(scale[g], static_cast<double>(sum[g]), -Z[static_cast<int64_t>(j) * np + i]));
+            if (i < n && j < n) r = residual_entry(sum[g], zi[g * np + i], i, j, n, e[g], eps_q, inv[g], rhs);
             R[static_cast<int64_t>(j) * np + i] = r;
             m = fmaxf(m, fabsf(r));
         }
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-    if ((threadIdx.x & 31) == 0 && m > 0.0f)
-        atomicMax(rmax, static_cast<unsigned long long>(__double_as_longlong(static_cast<double>(m))));
+    if ((threadIdx.x & 31) == 0 && m > 0.0f) atomicMax(rmax, __float_as_uint(m));
+}
+
+// (2) Denser E: a block is kRJ = 32 rows j (one per lane) by kRI = 512 rows i (kIW = 32 per warp
+// of kRWarps = 16).  It reads the fixed-point Z transposed, ZfT[k][j] = Zf[j][k], so that the
+// band of kBand columns k of its 32 rows j is a kBand x 32 tile of 256-byte rows: TMA copies it
+// into shared memory (two buffers, the next band's copy in flight during this band's gathers), and
+// the 32 lanes reading one k read 256 contiguous bytes (no bank conflict).  The edges come
+// bucketed by (i-tile, band) with band-local columns (bucket_*_kernel): a warp copies its rows'
+// edges of the band into a shared buffer with coalesced loads, then row by row every lane adds
+// its row's entry at each edge's column.  Bands without edges in the i-tile are skipped.  Every
+// index read serves 32 rows of Z.  The copies complete on mbarriers whose waits are bounded: on
+// expiry the kernel records ST_TIMEOUT_FULL, waits (bounded) for its copies still in flight and
+// returns.
+constexpr int kRJ = 32, kIW = 32, kRWarps = 16, kRI = kRWarps * kIW, kBand = 384, kBox = 128;
+constexpr int kEdgeBuf = 256;  // band-local columns per warp buffered at once
+constexpr size_t kBandBytes = sizeof(long long) * kBand * kRJ;
+constexpr size_t kResidualSmem = 2 * kBandBytes + sizeof(uint16_t) * kRWarps * kEdgeBuf + 64;
+
+// Bucketed edges: segment (t, b) holds the edges (i, k) with i in i-tile t (kRI rows) and k in
+// band b (kBand columns), ordered by (i, k); off[(t * nbd + b) * kRI + il] is the first edge of
+// row t kRI + il in it (flat exclusive scan of the counts, so the next entry is the row's end).
+// cnt: one count per (segment, row), zeroed by the caller; a warp per row.
+__global__ void bucket_count_kernel(const int *__restrict__ ptr, const int *__restrict__ col, int n, int nbd,
+                                    int *__restrict__ cnt) {
+    const int lane = threadIdx.x & 31;
+    const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (i >= n) return;
+    const int t = i / kRI, il = i - t * kRI;
+    for (int q = ptr[i] + lane; q < ptr[i + 1]; q += 32)
+        atomicAdd(&cnt[(t * nbd + col[q] / kBand) * kRI + il], 1);
+}
+
+__global__ void bucket_fill_kernel(const int *__restrict__ ptr, const int *__restrict__ col, int n, int nbd,
+                                   const int *__restrict__ off, uint16_t *__restrict__ edges) {
+    const int lane = threadIdx.x & 31;
+    const int i = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (i >= n) return;
+    const int t = i / kRI, il = i - t * kRI;
+    const int q0 = ptr[i], q1 = ptr[i + 1];
+    for (int q = q0 + lane; q < q1; q += 32) {
+        const int k = col[q], b = k / kBand;
+        int lo = q0, hi = q;  // first successor of row i in band b (columns sorted)
+        while (lo < hi) {
+            const int mid = (lo + hi) >> 1;
+            if (col[mid] < b * kBand) lo = mid + 1;
+            else hi = mid;
+        }
+        edges[off[(t * nbd + b) * kRI + il] + (q - lo)] = static_cast<uint16_t>(k - b * kBand);
+    }
+}
+
+// ZfT[k][j] = round(Z[j][k] 2^e_j), plus 2^e_j at k = j < n when add_identity; 32 x 32 tiles.
+__global__ void fix_transpose_kernel(const double *__restrict__ Z, const int *__restrict__ escale, int n, int np,
+                                     int add_identity, long long *__restrict__ ZfT) {
+    __shared__ long long tile[TT][TT + 1];
+    const int k0 = blockIdx.x * TT, j0 = blockIdx.y * TT;
+    for (int y = threadIdx.y; y < TT; y += blockDim.y) {
+        const int j = j0 + y, k = k0 + threadIdx.x;
+        const int e = escale[j];
+        long long v = fixed_of(__double_as_longlong(Z[static_cast<int64_t>(j) * np + k]), e);
+        if (add_identity && k == j && j < n) v += 1ll << e;
+        tile[y][threadIdx.x] = v;
+    }
+    __syncthreads();
+    for (int y = threadIdx.y; y < TT; y += blockDim.y)
+        ZfT[static_cast<int64_t>(k0 + y) * np + j0 + threadIdx.x] = tile[threadIdx.x][y];
+}
+
+__global__ void __launch_bounds__(32 * kRWarps, 1)
+    residual_band_kernel(const __grid_constant__ CUtensorMap zmap, int n, int np, int nbd, const int *__restrict__ off,
+                         const uint16_t *__restrict__ edges, long long eps_q, const int *__restrict__ escale,
+                         const long long *__restrict__ ZfT, float *__restrict__ R, unsigned *rmax,
+                         const uint8_t *__restrict__ rhs, int *status, uint64_t budget_ns) {
+    extern __shared__ __align__(1024) uint8_t rsmem[];
+    uint16_t *ebuf = reinterpret_cast<uint16_t *>(rsmem + 2 * kBandBytes) + (threadIdx.x >> 5) * kEdgeBuf;
+    uint64_t *full = reinterpret_cast<uint64_t *>(rsmem + 2 * kBandBytes + sizeof(uint16_t) * kRWarps * kEdgeBuf);
+    __shared__ int abort_s;
+    const unsigned fullmask = 0xffffffffu;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int ni = (np + kRI - 1) / kRI;
+    const int it = blockIdx.x % ni, jt = blockIdx.x / ni;  // the i-tiles of one j-tile are adjacent
+    const int j0 = jt * kRJ, i0 = it * kRI + warp * kIW;   // i0 < np or the warp only helps
+    const int j = j0 + lane;
+    const int e = escale[j];
+    const int *seg = off + it * nbd * kRI;  // segment b's row starts at seg + b kRI
+    if (threadIdx.x == 0) {
+        mbar_init(&full[0], 1);
+        mbar_init(&full[1], 1);
+        fence_barrier_init();
+        abort_s = 0;
+    }
+    __syncthreads();
+    // the bands with edges in this i-tile, in order: b is live iff seg[b kRI] != seg[(b + 1) kRI]
+    auto next_live = [&](int b) {
+        while (b < nbd && seg[b * kRI] == seg[(b + 1) * kRI]) ++b;
+        return b;
+    };
+    auto slab = [&](int buf) { return reinterpret_cast<long long *>(rsmem + buf * kBandBytes); };
+    auto issue = [&](int b, int buf) {  // one thread: the band's kBand x 32 tile of ZfT
+        mbar_arrive_expect_tx(&full[buf], static_cast<uint32_t>(kBandBytes));
+        for (int c = 0; c < kBand / kBox; ++c)
+            tma_load_2d(&zmap, slab(buf) + c * kBox * kRJ, &full[buf], j0, b * kBand + c * kBox);
+    };
+    long long acc[kIW];
+#pragma unroll
+    for (int q = 0; q < kIW; ++q) acc[q] = 0;
+    int b = next_live(0), use = 0;
+    uint32_t phases = 0u;    // bit u: parity of buffer u's next completion
+    uint32_t inflight = 0u;  // bit u: thread 0 issued a copy into buffer u that nobody has waited on
+    if (b < nbd && threadIdx.x == 0) {
+        issue(b, 0);
+        inflight = 1u;
+    }
+    while (b < nbd) {
+        const int bn = next_live(b + 1);
+        if (bn < nbd && threadIdx.x == 0) {  // the other buffer was freed by the previous barrier
+            issue(bn, use ^ 1);
+            inflight |= 1u << (use ^ 1);
+        }
+        const bool ok = mbar_wait_bounded(&full[use], (phases >> use) & 1u, budget_ns, status, ST_TIMEOUT_FULL);
+        if (ok) {
+            phases ^= 1u << use;
+            inflight &= ~(1u << use);
+        } else {
+            atomicOr(&abort_s, 1);
+        }
+        if (__syncthreads_or(abort_s)) {  // every thread leaves together; thread 0 drains its copies
+            if (threadIdx.x == 0)
+                for (int u = 0; u < 2; ++u)
+                    if ((inflight >> u) & 1u)
+                        mbar_wait_bounded(&full[u], (phases >> u) & 1u, budget_ns, status, ST_TIMEOUT_DRAIN);
+            return;
+        }
+        const long long *sl = slab(use);
+        const int *so = seg + b * kRI;
+        const int rs = so[min(warp * kIW + lane, kRI)];      // lane l: start of row il = l
+        const int re = so[min(warp * kIW + lane + 1, kRI)];  // ... and its end
+        const int ws = __shfl_sync(fullmask, rs, 0), we = __shfl_sync(fullmask, re, kIW - 1);
+        for (int w0 = ws; w0 < we; w0 += kEdgeBuf) {
+            const int wl = min(kEdgeBuf, we - w0);
+            __syncwarp();
+            for (int p = lane; p < wl; p += 32) ebuf[p] = edges[w0 + p];
+            __syncwarp();
+#pragma unroll
+            for (int il = 0; il < kIW; ++il) {
+                const int lo = max(__shfl_sync(fullmask, rs, il), w0) - w0;
+                const int hi = min(__shfl_sync(fullmask, re, il), w0 + wl) - w0;
+                long long a = acc[il];
+                for (int p = lo; p < hi; ++p) a += sl[ebuf[p] * kRJ + lane];
+                acc[il] = a;
+            }
+        }
+        __syncthreads();  // this buffer's gathers are done: it may be refilled
+        b = bn;
+        use ^= 1;
+    }
+    if (i0 >= np) return;
+    // R^T[j][i0 .. i0 + kIW - 1]: lane j writes kIW consecutive entries of its row
+    float m = 0.0f;
+    const float inv = __int_as_float((127 - e) << 23);  // 2^-e (0 <= e <= 62)
+    float *rrow = R + static_cast<int64_t>(j) * np + i0;
+#pragma unroll
+    for (int il = 0; il < kIW; il += 4) {
+        float v4[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int i = i0 + il + u;
+            const long long z = ZfT[static_cast<int64_t>(i) * np + j];
+            v4[u] = i < n && j < n ? residual_entry(acc[il + u], z, i, j, n, e, eps_q, inv, rhs) : 0.0f;
+            m = fmaxf(m, fabsf(v4[u]));
+        }
+        *reinterpret_cast<float4 *>(rrow + il) = make_float4(v4[0], v4[1], v4[2], v4[3]);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(fullmask, m, o));
+    if (lane == 0 && m > 0.0f) atomicMax(rmax, __float_as_uint(m));
+}
+
+// Z += D for row j (one block per row, the new row kept in shared memory), then the row's scale
+// e_j = row_scale(largest exponent field, deg_bits) into escale[j] and the fixed-point row
+// Zf[j][k] = round(Z[j][k] 2^e_j), plus 2^e_j at k = j < n when add_identity (the closure's
+// [k = j] term of the residual).
+__global__ void __launch_bounds__(256) add_fix_kernel(double *__restrict__ Z, const float *__restrict__ D, int n,
+                                                      int np, int deg_bits, int add_identity, int *__restrict__ escale,
+                                                      long long *__restrict__ Zf) {
+    // (Zf == nullptr: only Z and escale; fix_transpose_kernel then writes the transposed copy)
+    extern __shared__ double zrow_s[];
+    __shared__ int wmax[8];
+    const int j = blockIdx.x;
+    const int64_t base = static_cast<int64_t>(j) * np;
+    int ex = 0;
+    for (int k = threadIdx.x * 4; k < np; k += blockDim.x * 4) {
+        const float4 d = *reinterpret_cast<const float4 *>(D + base + k);
+        double2 z0 = *reinterpret_cast<const double2 *>(Z + base + k);
+        double2 z1 = *reinterpret_cast<const double2 *>(Z + base + k + 2);
+        z0.x += static_cast<double>(d.x);
+        z0.y += static_cast<double>(d.y);
+        z1.x += static_cast<double>(d.z);
+        z1.y += static_cast<double>(d.w);
+        *reinterpret_cast<double2 *>(Z + base + k) = z0;
+        *reinterpret_cast<double2 *>(Z + base + k + 2) = z1;
+        *reinterpret_cast<double2 *>(zrow_s + k) = z0;
+        *reinterpret_cast<double2 *>(zrow_s + k + 2) = z1;
+        ex = max(ex, max(max(static_cast<int>((__double_as_longlong(z0.x) >> 52) & 0x7FF),
+                             static_cast<int>((__double_as_longlong(z0.y) >> 52) & 0x7FF)),
+                         max(static_cast<int>((__double_as_longlong(z1.x) >> 52) & 0x7FF),
+                             static_cast<int>((__double_as_longlong(z1.y) >> 52) & 0x7FF))));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) ex = max(ex, __shfl_xor_sync(0xffffffffu, ex, o));
+    if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = ex;
+    __syncthreads();
+    int m = 0;
+#pragma unroll
+    for (int w = 0; w < 8; ++w) m = max(m, wmax[w]);
+    const int e = row_scale(m, deg_bits);
+    if (threadIdx.x == 0) escale[j] = e;
+    if (Zf == nullptr) return;
+    for (int k = threadIdx.x; k < np; k += blockDim.x) {
+        long long v = fixed_of(__double_as_longlong(zrow_s[k]), e);
+        if (add_identity && k == j && j < n) v += 1ll << e;
+        Zf[base + k] = v;
+    }
+}
+
+// R^T = (eps A)^T (np x np, zero padding): the residual of Z = 0, the first right-hand side.
+__global__ void build_rt_kernel(const uint8_t *__restrict__ A, int n, int np, float eps, float *__restrict__ R) {
+    __shared__ float tile[TT][TT + 1];
+    const int c0 = blockIdx.x * TT, r0 = blockIdx.y * TT;
+    for (int y = threadIdx.y; y < TT; y += blockDim.y) {
+        const int r = r0 + y, c = c0 + threadIdx.x;
+        tile[y][threadIdx.x] = (r < n && c < n && A[static_cast<int64_t>(r) * n + c]) ? eps : 0.0f;
+    }
+    __syncthreads();
+    for (int y = threadIdx.y; y < TT; y += blockDim.y) {
+        const int r = c0 + y, c = r0 + threadIdx.x;  // R[r][c] = eps A[c][r]
+        if (r < np && c < np) R[static_cast<int64_t>(r) * np + c] = tile[threadIdx.x][y];
+    }
 }
 
 // Y = I on every group's rows (groups of gw rows starting at multiples of gw; row r of a group
@@ -294,12 +543,6 @@ __global__ void group_identity_kernel(float *YL, float *YU, int np, int gw) {
 __global__ void identity_kernel(float *Z, int np) {
     const int r = blockIdx.x * blockDim.x + threadIdx.x;
     if (r < np) Z[static_cast<int64_t>(r) * np + r] = 1.0f;
-}
-
-__global__ void add_f32_kernel(double *__restrict__ x, const float *__restrict__ d, int64_t count) {
-    for (int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; t < count;
-         t += static_cast<int64_t>(gridDim.x) * blockDim.x)
-        x[t] += static_cast<double>(d[t]);
 }
 
 int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
@@ -407,17 +650,6 @@ dl_status tc_mixed(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &
         dim3 grid(static_cast<unsigned>(std::min<int64_t>((np + 255) / 256, 64)), static_cast<unsigned>(np));
         build_a_kernel<<<grid, 256, 0, s>>>(E, n, N, static_cast<float>(eps), A32);
         MCK(cudaGetLastError());
-        ++launches;
-    }
-    // a general right-hand side A: its transpose (bytes) for the residual's A[i][j] terms
-    uint8_t *At = nullptr;
-    if (a.rhs) {
-        At = static_cast<uint8_t *>(ws.get("mx_At", std::max<size_t>(static_cast<size_t>(n) * n, 16)));
-        if (!At) {
-            set_error("mixed path: device allocation failed (A^T)");
-            return DL_ENOMEM;
-        }
-        MCK(transpose(a.rhs, n, n, n, At, n, s));
         ++launches;
     }
     // CSR of E for the residual
@@ -635,78 +867,116 @@ dl_status tc_mixed(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &
     // ---- refinement from Z = 0 -------------------------------------------------------------
     const double tol = ctx->cfg.refine_tol > 0 ? ctx->cfg.refine_tol : 1e-13;
     const int max_iters = ctx->cfg.refine_max_iters > 0 ? ctx->cfg.refine_max_iters : 30;
-    // rows of Z per residual block: as many (up to 3) as shared memory holds
-    const size_t row_bytes = sizeof(long long) * static_cast<size_t>(np);
-    const int rows_per_block = static_cast<int>(std::min<size_t>(3, kResidualSmem / row_bytes));
-    if (rows_per_block < 1) {
-        set_error("mixed path: n = %d exceeds the residual's shared-memory row (%zu bytes)", n, kResidualSmem);
+    int deg_bits = 0;  // 2^deg_bits >= ||E||_inf + 1 (the terms of one sum, the +1 or A[i][j] included)
+    while ((1ull << deg_bits) < std::max<unsigned long long>(dmax, 1) + 1) ++deg_bits;
+    const long long eps_q = std::llround(std::ldexp(eps, 62));
+    auto *escale = static_cast<int *>(ws.get("mx_escale", np * 4));
+    auto *Zf = static_cast<long long *>(ws.get("mx_Zf", np * np * 8));
+    if (!escale || !Zf) {
+        set_error("mixed path: device allocation failed (row scales)");
+        return DL_ENOMEM;
+    }
+    const size_t row_smem = static_cast<size_t>(np) * sizeof(double);
+    if (row_smem > 227 * 1024) {
+        set_error("mixed path: n = %d exceeds the refinement's shared-memory row (%zu bytes)", n, row_smem);
         return DL_EINVAL;
     }
-    const size_t res_smem = row_bytes * rows_per_block;
-    int deg_bits = 0;  // 2^deg_bits >= ||E||_inf (the terms of one sum)
-    while ((1ull << deg_bits) < std::max<unsigned long long>(dmax, 1)) ++deg_bits;
-    auto residual = [&](unsigned long long *rmax_p) -> cudaError_t {
-        const unsigned grid = static_cast<unsigned>((np + rows_per_block - 1) / rows_per_block);
-        cudaError_t e;
-        switch (rows_per_block) {
-            case 3:
-                if ((e = cudaFuncSetAttribute(residual_fixed_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                              static_cast<int>(res_smem))) != cudaSuccess)
-                    return e;
-                residual_fixed_kernel<3><<<grid, 1024, res_smem, s>>>(csr_ptr, csr_col, n, N, deg_bits, eps, Z64, R32,
-                                                                     rmax_p, At);
-                break;
-            case 2:
-                if ((e = cudaFuncSetAttribute(residual_fixed_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                              static_cast<int>(res_smem))) != cudaSuccess)
-                    return e;
-                residual_fixed_kernel<2><<<grid, 1024, res_smem, s>>>(csr_ptr, csr_col, n, N, deg_bits, eps, Z64, R32,
-                                                                     rmax_p, At);
-                break;
-            default:
-                if ((e = cudaFuncSetAttribute(residual_fixed_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                              static_cast<int>(res_smem))) != cudaSuccess)
-                    return e;
-                residual_fixed_kernel<1><<<grid, 1024, res_smem, s>>>(csr_ptr, csr_col, n, N, deg_bits, eps, Z64, R32,
-                                                                     rmax_p, At);
+    MCK(cudaFuncSetAttribute(add_fix_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(row_smem)));
+    // the residual kernel by density: rows of Zf per block for sparse E, bucketed bands otherwise
+    const bool banded = static_cast<int64_t>(nnz) >= 32ll * n;
+    const int rows_per_block = static_cast<int>(std::min<size_t>(3, (227 * 1024) / row_smem));
+    const int nbd = (n + kBand - 1) / kBand, ni = static_cast<int>((np + kRI - 1) / kRI);
+    int *boff = nullptr;
+    uint16_t *bedges = nullptr;
+    CUtensorMap zmap{};  // ZfT (banded residual)
+    if (banded) {
+        const int64_t cells = static_cast<int64_t>(ni) * nbd * kRI;
+        auto *bcnt = static_cast<int *>(ws.get("mx_bcnt", (cells + 1) * 4));
+        boff = static_cast<int *>(ws.get("mx_boff", (cells + 1) * 4));
+        auto *bscr = static_cast<int *>(ws.get("mx_bscr", (2 * (cells / 1024 + 2)) * 4));
+        bedges = static_cast<uint16_t *>(ws.get("mx_bedges", std::max<size_t>(static_cast<size_t>(nnz), 8) * 2));
+        if (!bcnt || !boff || !bscr || !bedges) {
+            set_error("mixed path: device allocation failed (residual buckets)");
+            return DL_ENOMEM;
         }
+        MCK(cudaMemsetAsync(bcnt, 0, (cells + 1) * 4, s));
+        bucket_count_kernel<<<static_cast<unsigned>((n + 7) / 8), 256, 0, s>>>(csr_ptr, csr_col, n, nbd, bcnt);
+        MCK(cudaGetLastError());
+        MCK(exclusive_scan_large(bcnt, static_cast<int>(cells), boff, bscr, s));
+        bucket_fill_kernel<<<static_cast<unsigned>((n + 7) / 8), 256, 0, s>>>(csr_ptr, csr_col, n, nbd, boff, bedges);
+        MCK(cudaGetLastError());
+        launches += 3;
+        MCK(cudaFuncSetAttribute(residual_band_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 static_cast<int>(kResidualSmem)));
+        std::string err;
+        if (!tensor_map_2d(&zmap, CU_TENSOR_MAP_DATA_TYPE_INT64, 8, Zf, np, np, np, kRJ, kBox, &err)) {
+            set_error("mixed path: %s (residual)", err.c_str());
+            return DL_EDEVICE;
+        }
+    } else {
+        const int smem = static_cast<int>(row_smem * rows_per_block);
+        MCK(cudaFuncSetAttribute(residual_rows_kernel<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        MCK(cudaFuncSetAttribute(residual_rows_kernel<2>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+        MCK(cudaFuncSetAttribute(residual_rows_kernel<3>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem));
+    }
+    auto residual = [&](unsigned *rmax_p) -> cudaError_t {
+        if (banded) {
+            dim3 tgrid(static_cast<unsigned>(np / TT), static_cast<unsigned>(np / TT));
+            fix_transpose_kernel<<<tgrid, dim3(TT, 8), 0, s>>>(Z64, escale, n, N, a.rhs ? 0 : 1, Zf);
+            residual_band_kernel<<<static_cast<unsigned>((np / kRJ) * ni), 32 * kRWarps, kResidualSmem, s>>>(
+                zmap, n, N, nbd, boff, bedges, eps_q, escale, Zf, R32, rmax_p, a.rhs, ws.status, ctx->budget_ns);
+            return cudaGetLastError();
+        }
+        const unsigned grid = static_cast<unsigned>((np + rows_per_block - 1) / rows_per_block);
+        const size_t smem = row_smem * rows_per_block;
+        if (rows_per_block == 3)
+            residual_rows_kernel<3><<<grid, 1024, smem, s>>>(csr_ptr, csr_col, n, N, eps_q, escale, Zf, R32, rmax_p, a.rhs);
+        else if (rows_per_block == 2)
+            residual_rows_kernel<2><<<grid, 1024, smem, s>>>(csr_ptr, csr_col, n, N, eps_q, escale, Zf, R32, rmax_p, a.rhs);
+        else
+            residual_rows_kernel<1><<<grid, 1024, smem, s>>>(csr_ptr, csr_col, n, N, eps_q, escale, Zf, R32, rmax_p, a.rhs);
         return cudaGetLastError();
     };
-    const int64_t cnt = np * np;
-    const unsigned eblocks = static_cast<unsigned>(std::min<int64_t>((cnt + 255) / 256, 8 * 1024));
-    unsigned long long *rmax_d = ws.scal + 20;
+    unsigned *rmax_d = reinterpret_cast<unsigned *>(ws.scal + 20);
     double rmax = 0.0, best = 0.0;
     int products = 0, stall = 0;
-    // The FP64 residual has a rounding floor of about (row length) * u * max|X|; refinement
-    // stops at tol, or when it no longer halves the residual once that is below 1e-8 * eps.
+    // The residual has a rounding floor of about (row length) * 2^-53 * max|X|; refinement stops
+    // at tol, or when it no longer halves the residual once that is below 1e-8 * eps.
     const double floor_ok = 1e-8 * eps;
     MCK(cudaMemsetAsync(Z64, 0, np * np * 8, s));
+    {
+        dim3 tgrid(static_cast<unsigned>(np / TT), static_cast<unsigned>(np / TT));
+        build_rt_kernel<<<tgrid, dim3(TT, 8), 0, s>>>(a.rhs ? a.rhs : E, n, N, static_cast<float>(eps), R32);
+        MCK(cudaGetLastError());
+        ++launches;
+    }
     for (;;) {
-        MCK(cudaMemsetAsync(rmax_d, 0, sizeof(unsigned long long), s));
+        MCK(run(refine[0], sms, s));  // D^T = R^T W^T
+        add_fix_kernel<<<static_cast<unsigned>(np), 256, row_smem, s>>>(Z64, D32, n, N, deg_bits, a.rhs ? 0 : 1,
+                                                                      escale, banded ? nullptr : Zf);
+        MCK(cudaGetLastError());
+        ++launches;
+        ++products;
+        MCK(cudaMemsetAsync(rmax_d, 0, sizeof(unsigned), s));
         MCK(residual(rmax_d));
         ++launches;
-        unsigned long long h = 0;
+        unsigned h = 0;
         MCK(cudaMemcpyAsync(&h, rmax_d, sizeof(h), cudaMemcpyDeviceToHost, s));
         MCK(cudaStreamSynchronize(s));
-        std::memcpy(&rmax, &h, sizeof(rmax));
+        float hf = 0.0f;
+        std::memcpy(&hf, &h, sizeof(hf));
+        rmax = hf;
         if (rmax <= tol * eps) break;
-        if (products >= 1) {  // after the solve: refinement steps must keep halving the residual
-            if (products == 1 || rmax < 0.5 * best) {
-                best = rmax;
-                stall = 0;
-            } else if (++stall >= 2 && best <= floor_ok) {
-                break;
-            }
+        if (products == 1 || rmax < 0.5 * best) {  // refinement steps must keep halving the residual
+            best = rmax;
+            stall = 0;
+        } else if (++stall >= 2 && best <= floor_ok) {
+            break;
         }
         if (products > max_iters) {
             set_error("mixed path: refinement stopped at max|R|/eps = %.3g after %d steps", rmax / eps, products - 1);
             return DL_ENOTCONV;
         }
-        MCK(run(refine[0], sms, s));  // D^T = R^T W^T
-        add_f32_kernel<<<eblocks, 256, 0, s>>>(Z64, D32, cnt);
-        MCK(cudaGetLastError());
-        ++launches;
-        ++products;
     }
     MCK(transpose(Z64, np, N, N, X64, np, s));  // X = Z^T
     ++launches;

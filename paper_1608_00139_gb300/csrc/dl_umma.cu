@@ -20,10 +20,9 @@
 //               (boolean) or read-modify-write of C (TF32 update), then release the
 //               accumulator so the next tile's MMAs overlap this epilogue.  A warp may only
 //               read the TMEM lane quarter (warp % 4), so two warps share each quarter and take
-//               alternate 32-column chunks; the subtracting epilogue loads its first chunk of C
-//               before the accumulator is ready and the next chunk while it finishes the current
-//               one (a K = 128 update moves 8 bytes of C per 256 flops: it needs that many bytes
-//               in flight to run at HBM rate).
+//               alternate 32-column chunks; the subtracting epilogue loads all of its chunks of
+//               C before the accumulator is ready (a K = 128 update moves 8 bytes of C per 256
+//               flops: it needs that many bytes in flight to run at HBM rate).
 // Problems come from a device-memory table so that one launch can cover many independent
 // problems (a grouped GEMM for the uneven batch).
 #include <cuda.h>
@@ -357,10 +356,17 @@ __global__ void __launch_bounds__(kThreads, 1)
             const int mb = local % P->tiles_m, nb = local / P->tiles_m;
             const int row = mb * BM + r_in_tile;
             const bool row_ok = row < P->M;
-            // the first chunk of C is on its way while the MMAs finish
-            float4 cur[8], nxt[8];
-            bool have = row_ok && nb * BN + half * 32 < P->N;
-            if (EPI == EPI_SUB_F32 && have) load_c_chunk(P->epi, row, nb * BN + half * 32, cur);
+            // the subtracting epilogue loads all of its chunks of C while the MMAs finish (a
+            // K = 128 update is bound by these bytes: one memory latency per tile, not per chunk)
+            constexpr int kMine = kChunks / 2;  // chunks of this warp: half, half + 2, ...
+            float4 cbuf[EPI == EPI_SUB_F32 ? kMine : 1][8];
+            if (EPI == EPI_SUB_F32) {
+#pragma unroll
+                for (int u = 0; u < kMine; ++u) {
+                    const int col = nb * BN + (half + 2 * u) * 32;
+                    if (row_ok && col < P->N) load_c_chunk(P->epi, row, col, cbuf[u]);
+                }
+            }
             if (!mbar_wait_bounded(&accf[acc], acc_ph, budget_ns, status, ST_TIMEOUT_ACC_FULL))
                 break;
             tc_fence_after();
@@ -368,12 +374,10 @@ __global__ void __launch_bounds__(kThreads, 1)
             const uint32_t tbase = tmem_base + (static_cast<uint32_t>(quarter * 32) << 16) +
                                    static_cast<uint32_t>(acc * BN);
             uint32_t cnt = 0;
-#pragma unroll 1
-            for (int c = half; c < kChunks; c += 2) {
+#pragma unroll
+            for (int u = 0; u < kMine; ++u) {
+                const int c = half + 2 * u;
                 const int col = nb * BN + c * 32;
-                const int cn = c + 2;
-                const bool have_n = cn < kChunks && row_ok && nb * BN + cn * 32 < P->N;
-                if (EPI == EPI_SUB_F32 && have_n) load_c_chunk(P->epi, row, nb * BN + cn * 32, nxt);
                 uint32_t v[32];
                 if (live) {
                     tmem_ld_32x32b_x32(tbase + c * 32, v);
@@ -383,9 +387,9 @@ __global__ void __launch_bounds__(kThreads, 1)
                     for (int j = 0; j < 32; ++j) v[j] = 0u;
                 }
                 uint32_t word = 0;
-                if (have) {
+                if (row_ok && col < P->N) {
                     if (EPI == EPI_BOOL) word = epi_bool_chunk(P->epi, row, col, v, cnt);
-                    else if (EPI == EPI_SUB_F32) epi_sub_chunk(P->epi, row, col, cur, v);
+                    else if (EPI == EPI_SUB_F32) epi_sub_chunk(P->epi, row, col, cbuf[EPI == EPI_SUB_F32 ? u : 0], v);
                     else epi_store_chunk(P->epi, row, col, v);
                 }
                 if (EPI == EPI_BOOL && P->epi.occ_out != nullptr) {
@@ -393,11 +397,6 @@ __global__ void __launch_bounds__(kThreads, 1)
                         P->epi.occ_out[((P->epi.out_row0 + mb * BM + quarter * 32) >> 7) * P->epi.occ_ld +
                                        ((P->epi.out_col0 + col) >> 7)] = 1;
                 }
-                if (EPI == EPI_SUB_F32) {
-#pragma unroll
-                    for (int q = 0; q < 8; ++q) cur[q] = nxt[q];
-                }
-                have = have_n;
             }
             tc_fence_before();
             mbar_arrive(&acce[acc]);
@@ -489,6 +488,27 @@ cudaError_t launch_t(const GemmProblem *d_probs, int nprob, int total_tiles, con
 }
 
 }  // namespace
+
+bool tensor_map_2d(CUtensorMap *m, CUtensorMapDataType dt, int elem, const void *base, int64_t cols, int64_t rows,
+                   int64_t ld, uint32_t box_x, uint32_t box_y, std::string *err) {
+    EncodeTiledFn fn = encode_fn();
+    if (!fn) {
+        if (err) *err = "cuTensorMapEncodeTiled is not available from the driver";
+        return false;
+    }
+    cuuint64_t dims[2] = {static_cast<cuuint64_t>(cols), static_cast<cuuint64_t>(rows)};
+    cuuint64_t strides[1] = {static_cast<cuuint64_t>(ld) * elem};
+    cuuint32_t box[2] = {box_x, box_y};
+    cuuint32_t estr[2] = {1, 1};
+    const CUresult r = fn(m, dt, 2, const_cast<void *>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                          CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) {
+        if (err) *err = "cuTensorMapEncodeTiled failed";
+        return false;
+    }
+    return true;
+}
 
 int gemm_tile_m() { return BM; }
 
