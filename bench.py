@@ -414,6 +414,17 @@ def run_part(args, device: int) -> None:
                 out[name] = {"ms": stm["ms_total"], "ms_factor": stm["ms_factor"], "ms_solve": stm["ms_solve"],
                              "ms_refine": stm["ms_refine"], "refine_steps": stm["iters"],
                              "final_resid": stm["final_resid"]}
+    elif args.part == "bool":
+        # the squarings-only FP8 path on the three graphs (the FP8 GEMM's profiling workload)
+        out = {}
+        with dl.Context(device) as ctx:
+            gs = [torch.from_numpy(e).cuda() for e in graphs(0)]
+            for x in gs:
+                ctx.tc_closure(x, path="bool_fp8")  # warm
+            for name, x in zip(("p=1e-4", "p=1e-3", "p=1e-2"), gs):
+                _, stb = ctx.tc_closure(x, path="bool_fp8")
+                out[name] = {"ms": stb["ms_total"], "squarings": stb["iters"], "ms_gemm": stb["ms_gemm"],
+                             "gemm_tflops": stb["gemm_flops"] / (stb["ms_gemm"] * 1e-3) / 1e12}
     elif args.part == "sg_real":
         with dl.Context(device) as ctx:
             out = bench_sg_real(ctx, torch)
@@ -444,7 +455,7 @@ def main() -> None:
                     help="skip the same-generation, batch and serving measurements")
     ap.add_argument("--serve-seconds", type=float, default=10.0,
                     help="length of the serving stream (the full workload is 60 s)")
-    ap.add_argument("--part", default="all", choices=["all", "sg", "sg_real", "tail", "batch", "serving", "mixed"],
+    ap.add_argument("--part", default="all", choices=["all", "sg", "sg_real", "tail", "batch", "serving", "mixed", "bool"],
                     help="run one secondary measurement alone and print its JSON (for profiling)")
     args = ap.parse_args()
     rank, world, local = dist_env()

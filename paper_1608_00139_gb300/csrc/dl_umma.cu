@@ -104,6 +104,21 @@ __device__ __forceinline__ const GemmProblem *resolve_tile(const GemmProblem *pr
     return probs + sched[2 + lo];
 }
 
+// Output tile (mb, nb) of a problem's local tile index: groups of kGroupM row blocks, each
+// swept column by column, so that the tiles a wave of CTAs works on (consecutive indices) share
+// a few row blocks of A and a few column blocks of B that stay in L2 (walking all row blocks of a
+// column first re-reads all of A from DRAM for every wave once A outgrows L2).
+constexpr int kGroupM = 16;
+__device__ __forceinline__ void tile_coords(const GemmProblem *P, int local, int &mb, int &nb) {
+    const int per_group = kGroupM * P->tiles_n;
+    const int g = local / per_group;
+    const int first = g * kGroupM;
+    const int rows = min(kGroupM, P->tiles_m - first);
+    const int r = local - g * per_group;
+    mb = first + r % rows;
+    nb = r / rows;
+}
+
 // Does k-block kb of output tile (mb, nb) contribute?  (always, without occupancy maps)
 template <int BN>
 __device__ __forceinline__ bool kblock_live(const GemmProblem *P, int mb, int nb, int kb) {
@@ -249,7 +264,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                 int local = 0;
                 const GemmProblem *P = resolve_tile(probs, nprob, sched, tile, &local);
                 if (P == nullptr) continue;
-                const int mb = local % P->tiles_m, nb = local / P->tiles_m;
+                int mb, nb;
+                tile_coords(P, local, mb, nb);
                 const int nkb = P->K / C::BK;
                 for (int kb = 0; kb < nkb; ++kb) {
                     if (!kblock_live<BN>(P, mb, nb, kb)) continue;
@@ -296,7 +312,8 @@ __global__ void __launch_bounds__(kThreads, 1)
                 int local = 0;
                 const GemmProblem *P = resolve_tile(probs, nprob, sched, tile, &local);
                 if (P == nullptr) continue;
-                const int mb = local % P->tiles_m, nb = local / P->tiles_m;
+                int mb, nb;
+                tile_coords(P, local, mb, nb);
                 const int nkb = P->K / C::BK;
                 if (!mbar_wait_bounded(&acce[acc], acc_ph ^ 1u, budget_ns, status,
                                        ST_TIMEOUT_ACC_EMPTY)) {
@@ -353,7 +370,8 @@ __global__ void __launch_bounds__(kThreads, 1)
             int local = 0;
             const GemmProblem *P = resolve_tile(probs, nprob, sched, tile, &local);
             if (P == nullptr) continue;
-            const int mb = local % P->tiles_m, nb = local / P->tiles_m;
+            int mb, nb;
+                tile_coords(P, local, mb, nb);
             const int row = mb * BM + r_in_tile;
             const bool row_ok = row < P->M;
             // the subtracting epilogue loads all of its chunks of C while the MMAs finish (a
