@@ -42,9 +42,9 @@ UNIT = "TFLOP/s-equiv"
 # DRAM bytes per launch from the ncu captures summarised under profiles/; each is only valid
 # for the kernel source it was taken on (sha256 prefixes).
 TRAFFIC = {
-    "gemm": {"sources": {"dl_umma.cu": "a0ca42a48c46c344", "dl_ptx.cuh": "b4fd45714c88d2fc"},
-             "bytes_per_launch": 444.5e6},   # ncu: DRAM read + write of one N = 8192 squaring
-    "sweep": {"sources": {"dl_bool.cu": "bd4d428fec85b53d"},
+    "gemm": {"sources": {"dl_umma.cu": "f47fffb50b28217c", "dl_ptx.cuh": "b4fd45714c88d2fc"},
+             "bytes_per_launch": 177.5e6},   # ncu: DRAM read + write of one dense N = 8192 squaring
+    "sweep": {"sources": {"dl_bool.cu": "4e1ad3c162a9b14b"},
               "bytes_per_launch": 8.70e6},    # ncu: one working sweep, p = 1e-3, cold L2
 }
 
