@@ -14,6 +14,8 @@ Functions (passages they follow are cited in ``oracle.c``):
   tc_eps(E), sg_eps(P)   the paper's default epsilons (Sec. 4, Sec. 7.1, Sec. 7.2)
   sg_stilde_kron, sg_stilde_series   the real S~ of same generation (sg_real.py, numpy FP64)
   tail_model, tail_rtilde, tail_eps  one equation of the tail recursive class (tail.py)
+  trans_model, trans_naive, trans_rtilde_kron, trans_rtilde_series, trans_eps
+                         the transposed class, program prog:2 of Sec. 6.2 (transposed.py)
 Bit matrices: ceil(n/64) uint64 words per row, bit j%64 of word j//64, LSB first.
 """
 from __future__ import annotations
@@ -27,6 +29,8 @@ import numpy as np
 
 from .sg_real import sg_stilde_kron, sg_stilde_series  # noqa: F401  (numpy FP64, no C part)
 from .tail import tail_eps, tail_model, tail_model_rows, tail_rtilde  # noqa: F401  (numpy FP64)
+from .transposed import (trans_eps, trans_model, trans_naive, trans_rtilde_kron,  # noqa: F401
+                         trans_rtilde_series)
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "oracle.c")
