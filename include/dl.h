@@ -216,6 +216,29 @@ DL_API dl_status dl_sg_real(dl_ctx *ctx, int32_t n, const uint8_t *P, const uint
                      dl_path path, double *out_stilde, uint64_t *out_bits, dl_stats *stats);
 
 /*
+ * The transposed class (Sec. 6.2), its program prog:2:
+ *     r2(x,z) <- r1(x,z).     r2(x,z) <- r1(x,y), r2(z,y).
+ * The recursive atom's arguments are interchanged, so the completion is R2 = min1(R1 + R1 R2^T)
+ * and its linearisation R~2 = eps (R1 + R1 R~2^T) (eq. matrixeq:trans:1), with
+ * 0 < eps <= 1/(1 + ||R1||_inf) (eps <= 0 selects that bound; a larger eps returns DL_EINVAL).
+ * R1: n x n 0/1.  out_bits (required): the least model of r2.  The model is computed through
+ * the paper's reduction to a two-sided equation (eq. matrixeq:trans:2):
+ * R2 = min1(B + R1 R2 R1^T) with B = min1(R1 + R1 R1^T) (one FP8 tensor-core product), solved as
+ * dl_sg_least_model does (boolean doubling or the Iteration on bits).
+ * out_rtilde (optional, n x n doubles): the real least solution R~2, by the increasing series
+ * X_{t+1} = eps (R1 + R1 X_t^T) from 0 in FP64 until a step changes no entry by more than
+ * refine_tol * eps (DL_ENOTCONV after 100000 steps); stats->guard_flagged counts the 64-bit bit
+ * words where R~2 > 0 differs from the model (nonzero only under FP64 underflow).
+ * Paths: DL_PATH_AUTO (model; R~2 if out_rtilde is not NULL), DL_PATH_FP64 (model and the series,
+ * out_rtilde optional), DL_PATH_BOOL_FP8 (model only: a non-NULL out_rtilde returns DL_EINVAL);
+ * DL_PATH_MIXED returns DL_ENOTIMPL.  thr must be 0.
+ * stats: eps_used, iters (series steps, or the model's steps), final_resid (a power-of-two bound
+ * on the last step's largest change / eps), model_ones.
+ */
+DL_API dl_status dl_transposed(dl_ctx *ctx, int32_t n, const uint8_t *R1, dl_mem mem, double eps, double thr,
+                               dl_path path, uint64_t *out_bits, double *out_rtilde, dl_stats *stats);
+
+/*
  * Relational composition, the denotation of an existential join (Sec. 2,
  * eq. denote:quant):  [[exists y r1(x,y) and r2(y,z)]] = min1(R1 R2).
  * R1, R2: n x n 0/1.  Output: bits of min1(R1 R2).  Runs on the FP8 tensor-core path.

@@ -290,6 +290,34 @@ dl_status dl_tail_recursive(dl_ctx *ctx, int32_t n, const uint8_t *B0, const uin
     });
 }
 
+dl_status dl_transposed(dl_ctx *ctx, int32_t n, const uint8_t *R1, dl_mem mem, double eps, double thr, dl_path path,
+                        uint64_t *out_bits, double *out_rtilde, dl_stats *stats) {
+    clear_error();
+    GUARD_CTX(ctx);
+    if (stats) std::memset(stats, 0, sizeof(*stats));
+    if (n < 0 || !valid_mem(mem)) {
+        set_error("bad n (%d) or memory kind", n);
+        return DL_EINVAL;
+    }
+    if (n == 0) return DL_OK;
+    if (!R1 || !out_bits) {
+        set_error("R1 and out_bits must not be NULL");
+        return DL_EINVAL;
+    }
+    SolveArgs a;
+    a.n = n;
+    a.E = R1;
+    a.mem = mem;
+    a.eps = eps;
+    a.thr = thr;
+    a.path = path;
+    a.out_bits = out_bits;
+    a.out_rtilde = out_rtilde;
+    return run_sync(ctx, stats, [&](Workspace &ws, cudaStream_t s, dl_stats *st) {
+        return solve_transposed(ctx, ws, s, a, st);
+    });
+}
+
 dl_status dl_sg_real(dl_ctx *ctx, int32_t n, const uint8_t *P, const uint8_t *B, dl_mem mem, double eps,
                      dl_path path, double *out_stilde, uint64_t *out_bits, dl_stats *stats) {
     clear_error();

@@ -111,6 +111,8 @@ dl_status solve_sg(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &
 // One equation of the tail recursive class: E = B0 (recursive coefficient), E2 = A (the
 // non-recursive part); bits of the model, R~ into a.out_rtilde on the real paths.
 dl_status solve_tail(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &a, dl_stats *st);
+// The transposed class (program prog:2): E = R1; bits of the model, R~ into a.out_rtilde.
+dl_status solve_transposed(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &a, dl_stats *st);
 // The real S~ of same generation into a.out_rtilde (n x n doubles); bits optional.
 dl_status solve_sg_real(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &a, dl_stats *st);
 dl_status solve_compose(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &a,

@@ -232,6 +232,12 @@ cudaError_t row_abs_sum_max(const float *A, int np, unsigned *out, cudaStream_t 
 cudaError_t negate_f32(const float *a, float *b, int64_t count, cudaStream_t s);
 cudaError_t add_f32_to_f64(double *x, const float *d, int64_t count, cudaStream_t s);
 cudaError_t transpose_f32(const float *src, int64_t lds, int rows, int cols, float *dst, int64_t ldd, cudaStream_t s);
+// One step of the transposed class's series (Sec. 6.2, eq. matrixeq:trans:1) over the CSR of R1:
+// U = X^T, then Xn = eps (R1 + R1 U), i.e. Xn[i][j] = eps (R1[i][j] + sum_{y in succ(i)} X[j][y])
+// (R1: n x n bytes; X, U, Xn: np x np, zero outside n x n); *dmax (zeroed by the caller) as
+// for the same-generation series (a power-of-two bound on the step's largest change).
+cudaError_t trans_real_step(const int *ptr, const int *col, int n, int np, double eps, const uint8_t *R1,
+                            const double *X, double *U, double *Xn, unsigned long long *dmax, cudaStream_t s);
 // dst |= src over `words` 64-bit words.
 cudaError_t bits_or(uint64_t *dst, const uint64_t *src, int64_t words, cudaStream_t s);
 

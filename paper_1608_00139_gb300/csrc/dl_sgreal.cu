@@ -213,9 +213,10 @@ __global__ void bits_or_kernel(uint64_t *__restrict__ dst, const uint64_t *__res
 constexpr int kTT = 32;
 
 // dst[c][r] = src[r][c] for an rows x cols block (32 x 32 tiles through shared memory).
-__global__ void transpose_f32_kernel(const float *__restrict__ src, int64_t lds, int rows, int cols,
-                                     float *__restrict__ dst, int64_t ldd) {
-    __shared__ float tile[kTT][kTT + 1];
+template <class T>
+__global__ void transpose_tile_kernel(const T *__restrict__ src, int64_t lds, int rows, int cols, T *__restrict__ dst,
+                                      int64_t ldd) {
+    __shared__ T tile[kTT][kTT + 1];
     const int c0 = blockIdx.x * kTT, r0 = blockIdx.y * kTT;
     for (int y = threadIdx.y; y < kTT; y += blockDim.y) {
         const int r = r0 + y, c = c0 + threadIdx.x;
@@ -292,7 +293,16 @@ cudaError_t bits_or(uint64_t *dst, const uint64_t *src, int64_t words, cudaStrea
 
 cudaError_t transpose_f32(const float *src, int64_t lds, int rows, int cols, float *dst, int64_t ldd, cudaStream_t s) {
     dim3 grid(static_cast<unsigned>((cols + kTT - 1) / kTT), static_cast<unsigned>((rows + kTT - 1) / kTT));
-    transpose_f32_kernel<<<grid, dim3(kTT, 8), 0, s>>>(src, lds, rows, cols, dst, ldd);
+    transpose_tile_kernel<float><<<grid, dim3(kTT, 8), 0, s>>>(src, lds, rows, cols, dst, ldd);
+    return cudaGetLastError();
+}
+
+cudaError_t trans_real_step(const int *ptr, const int *col, int n, int np, double eps, const uint8_t *R1,
+                            const double *X, double *U, double *Xn, unsigned long long *dmax, cudaStream_t s) {
+    dim3 tgrid(static_cast<unsigned>((np + kTT - 1) / kTT), static_cast<unsigned>((np + kTT - 1) / kTT));
+    transpose_tile_kernel<double><<<tgrid, dim3(kTT, 8), 0, s>>>(X, np, np, np, U, np);  // U = X^T
+    dim3 grid(static_cast<unsigned>((np + 255) / 256), static_cast<unsigned>(np));
+    sg_pu_kernel<<<grid, 256, 0, s>>>(ptr, col, n, np, eps, R1, U, X, Xn, nullptr, dmax);
     return cudaGetLastError();
 }
 

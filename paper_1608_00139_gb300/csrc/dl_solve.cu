@@ -1582,6 +1582,195 @@ size_t footprint_bytes(int kind, int32_t n) {
 
 // ---- workspace ------------------------------------------------------------------------
 
+namespace {
+
+// The 0/1 bytes (n x n, row stride n) of an e4m3 0/1 matrix (row stride ldc).
+__global__ void e4m3_to_u8_kernel(const uint8_t *__restrict__ C, int64_t ldc, int n, uint8_t *__restrict__ B) {
+    const int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+    if (t >= static_cast<int64_t>(n) * n) return;
+    const int64_t i = t / n, j = t - i * n;
+    B[t] = C[i * ldc + j] != 0 ? 1 : 0;
+}
+
+}  // namespace
+
+// The transposed class (Sec. 6.2), program prog:2:
+//     r2(x,z) <- r1(x,z).      r2(x,z) <- r1(x,y), r2(z,y).
+// Its completion R2 = min1(R1 + R1 R2^T) substituted into itself gives the two-sided equation
+// R2 = min1(B + R1 R2 R1^T), B = min1(R1 + R1 R1^T) (eq. matrixeq:trans:2).  Both have the same
+// least solution: the iterates of the two-step operator from 0 are every other iterate of the
+// one-step operator, which increase to its least fixpoint.  So the model is one FP8 product
+// (C = R1 R1^T with R1 added in the epilogue) and the same-generation solver with P = R1 and B.
+// The real R~2 = eps (R1 + R1 R~2^T) (eq. matrixeq:trans:1; DL_PATH_FP64, or DL_PATH_AUTO when
+// asked for): the increasing series X_{t+1} = eps (R1 + R1 X_t^T) from X_0 = 0 in FP64, four steps
+// per host read, until a step changes no entry by more than tol eps; its positive entries are
+// compared with the model (guard_flagged counts the bit words where they differ: only underflow
+// can make them).
+dl_status solve_transposed(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &a, dl_stats *st) {
+    if (a.thr != 0.0) {
+        set_error("thr must be 0: the model is R~ > 0 (Theorem 2)");
+        return DL_EINVAL;
+    }
+    if (a.path == DL_PATH_MIXED) {
+        set_error("the transposed class has no mixed-precision path; use DL_PATH_FP64 or DL_PATH_AUTO");
+        return DL_ENOTIMPL;
+    }
+    if (a.path != DL_PATH_AUTO && a.path != DL_PATH_BOOL_FP8 && a.path != DL_PATH_FP64) {
+        set_error("unknown path %d", static_cast<int>(a.path));
+        return DL_EINVAL;
+    }
+    if (a.path == DL_PATH_BOOL_FP8 && a.out_rtilde) {
+        set_error("DL_PATH_BOOL_FP8 computes no real-valued R~; use DL_PATH_FP64 or DL_PATH_AUTO");
+        return DL_EINVAL;
+    }
+    const int32_t n = a.n;
+    const int64_t np = round_up(std::max<int64_t>(n, 1), 256);
+    const int64_t wp = np / 64, w = (n + 63) / 64;
+    Timer tm{ws.ev + 4, s};  // events 0-3 belong to the same-generation solver it calls
+    int launches = 0;
+    tm.mark(0);
+    const uint8_t *R1 = nullptr;
+    dl_status rc = stage_input(ws, s, a.E, n, a.mem, "tr_in0", &R1);
+    if (rc) return rc;
+    auto *R8 = static_cast<uint8_t *>(ws.get("tr_e8", np * np));
+    auto *B8 = static_cast<uint8_t *>(ws.get("tr_b8", np * np));
+    auto *Bu = static_cast<uint8_t *>(ws.get("tr_bu8", std::max<size_t>(static_cast<size_t>(n) * n, 16)));
+    auto *Mw = static_cast<uint64_t *>(ws.get("tr_bits", std::max<size_t>(static_cast<size_t>(n) * w * 8, 16)));
+    NEED(R8 && B8 && Bu && Mw);
+    CK(cudaMemsetAsync(ws.scal, 0, kScalars * sizeof(unsigned long long), s));
+    CK(cudaMemsetAsync(ws.status, 0, sizeof(int), s));
+    if ((rc = ingest(ctx, ws, s, R1, n, np, R8, 0, SC_DMAX, SC_NNZ, SC_COUNT0, &launches))) return rc;
+    if ((rc = read_scalars(ws, s))) return rc;
+    if ((rc = check_status(ws, s))) return rc;
+    const unsigned long long dmax = host_scal(ws)[SC_DMAX];
+    double eps = 0;
+    if ((rc = choose_eps(a.eps, 1.0 / (1.0 + static_cast<double>(dmax)), "Sec. 6.2 (1/(1+||R1||_inf))", &eps)))
+        return rc;
+    // B = min1(R1 + R1 R1^T): C[i][j] = sum_k R1[i][k] R1[j][k] (B operand K-major = R1 itself)
+    GemmProblem pr;
+    std::string err;
+    const int bn = bool_bn(np);
+    if (!gemm_make_problem(&pr, KIND_F8, true, bn, static_cast<int>(np), static_cast<int>(np), static_cast<int>(np),
+                           square_op(R8, np), square_op(R8, np), bool_epi(B8, np, nullptr, wp, nullptr, R8), &err)) {
+        set_error("%s", err.c_str());
+        return DL_EDEVICE;
+    }
+    GemmProblem *d = nullptr;
+    if ((rc = upload_problems(ws, s, &pr, 1, &d))) return rc;
+    const int tiles = pr.tiles_m * pr.tiles_n;
+    GemmClock gc{ws, s};
+    gc.start();
+    CK(gemm_launch(KIND_F8, true, bn, EPI_BOOL, d, 1, tiles, std::min(tiles, ctx->sms), ws.status, ctx->budget_ns, s));
+    gc.stop(2.0 * np * np * np);
+    const int64_t nn = static_cast<int64_t>(n) * n;
+    e4m3_to_u8_kernel<<<static_cast<unsigned>((nn + 255) / 256), 256, 0, s>>>(B8, np, n, Bu);
+    CK(cudaGetLastError());
+    launches += 2;
+    if ((rc = read_scalars(ws, s))) return rc;  // (the GEMM table's staging is free again)
+    if ((rc = check_status(ws, s))) return rc;
+    const double b_gemm_ms = gc.ms(), b_gemm_flops = gc.timed_flops;  // (its events are reused below)
+    tm.mark(1);
+    SolveArgs b = a;
+    b.E = R1;
+    b.E2 = Bu;
+    b.mem = DL_MEM_DEVICE;
+    b.e_device = false;
+    b.eps = 0.0;
+    b.path = a.path == DL_PATH_BOOL_FP8 ? DL_PATH_BOOL_FP8 : DL_PATH_AUTO;
+    b.out_bits = Mw;
+    b.out_rtilde = nullptr;
+    dl_stats sgst{};
+    if ((rc = solve_sg(ctx, ws, s, b, &sgst))) return rc;
+    launches += sgst.gpu_launches;
+    CK(cudaMemcpyAsync(a.out_bits, Mw, static_cast<size_t>(n) * w * 8,
+                       a.mem == DL_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+    tm.mark(2);
+    int steps = 0;
+    double resid = 0.0;
+    unsigned long long differ = 0;
+    const bool real = a.out_rtilde != nullptr || a.path == DL_PATH_FP64;
+    if (real) {
+        const size_t nq = static_cast<size_t>(np) * np;
+        auto *cnt = static_cast<int *>(ws.get("tr_cnt", (np + 1) * 4));
+        auto *ptr = static_cast<int *>(ws.get("tr_ptr", (np + 1) * 4));
+        auto *X = static_cast<double *>(ws.get("tr_X", nq * 8));
+        auto *Xn = static_cast<double *>(ws.get("tr_Xn", nq * 8));
+        auto *U = static_cast<double *>(ws.get("tr_U", nq * 8));
+        NEED(cnt && ptr && X && Xn && U);
+        CK(csr_build(R1, n, cnt, ptr, s));
+        int nnz = 0;
+        CK(cudaMemcpyAsync(&nnz, ptr + n, sizeof(int), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        auto *col = static_cast<int *>(ws.get("tr_col", static_cast<size_t>(std::max(nnz, 1)) * 4));
+        NEED(col);
+        CK(csr_fill(R1, n, ptr, col, s));
+        CK(cudaMemsetAsync(X, 0, nq * 8, s));
+        launches += 3;
+        const double tol = ctx->cfg.refine_tol > 0 ? ctx->cfg.refine_tol : 1e-13;
+        unsigned long long *slot = ws.scal + 32;
+        constexpr int kGroup = 4, kBudget = 100000;
+        bool done = false;
+        while (!done && steps < kBudget) {
+            CK(cudaMemsetAsync(slot, 0, kGroup * sizeof(unsigned long long), s));
+            for (int k = 0; k < kGroup; ++k) {
+                CK(trans_real_step(ptr, col, n, static_cast<int>(np), eps, R1, X, U, Xn, slot + k, s));
+                std::swap(X, Xn);
+                launches += 2;
+            }
+            if ((rc = read_scalars(ws, s))) return rc;
+            for (int k = 0; k < kGroup; ++k) {
+                ++steps;
+                const unsigned long long code = host_scal(ws)[32 + k];  // max change < 2^(code - 4096)
+                resid = code == 0 ? 0.0 : std::ldexp(1.0, static_cast<int>(code) - 4096) / eps;
+                if (resid <= tol) {
+                    done = true;  // the iterates after this step are at least as close
+                    break;
+                }
+            }
+        }
+        if (!done) {
+            set_error("transposed class: the series did not reach max|change|/eps <= %g in %d steps", tol, steps);
+            return DL_ENOTCONV;
+        }
+        if (a.out_rtilde)
+            CK(cudaMemcpy2DAsync(a.out_rtilde, static_cast<size_t>(n) * 8, X, static_cast<size_t>(np) * 8,
+                                 static_cast<size_t>(n) * 8, n,
+                                 a.mem == DL_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+        // X > 0 against the model, word by word (np x wp layouts, rows < n)
+        auto *T = static_cast<uint64_t *>(ws.get("tr_tbits", np * wp * 8));
+        auto *Mp = static_cast<uint64_t *>(ws.get("tr_mbits", np * wp * 8));
+        NEED(T && Mp);
+        CK(cudaMemsetAsync(T, 0, np * wp * 8, s));
+        CK(cudaMemsetAsync(Mp, 0, np * wp * 8, s));
+        CK(cudaMemcpy2DAsync(Mp, wp * 8, Mw, w * 8, w * 8, n, cudaMemcpyDeviceToDevice, s));
+        CK(cudaMemsetAsync(ws.scal + SC_GUARD, 0, 2 * sizeof(unsigned long long), s));
+        CK(thresh_pack_f64(X, np, n, static_cast<int>(np), 0.0, T, wp, ws.scal + SC_GUARD, s));
+        CK(bits_diff(T, Mp, np * wp, ws.scal + SC_GUARD + 1, s));
+        launches += 2;
+        if ((rc = read_scalars(ws, s))) return rc;
+        differ = host_scal(ws)[SC_GUARD + 1];
+    }
+    tm.mark(3);
+    if ((rc = check_status(ws, s))) return rc;
+    if (st) {
+        st->path_used = real ? DL_PATH_FP64 : sgst.path_used;
+        st->eps_used = eps;
+        st->iters = real ? steps : sgst.iters;
+        st->final_resid = resid;
+        st->guard_flagged = static_cast<int64_t>(differ);
+        st->model_ones = sgst.model_ones;
+        st->ms_factor = tm.ms(0, 1);
+        st->ms_solve = tm.ms(1, 2);
+        st->ms_refine = tm.ms(2, 3);
+        st->ms_total = tm.ms(0, 3);
+        st->gpu_launches = launches;
+        st->gemm_launches = 1 + sgst.gemm_launches;
+        st->ms_gemm = b_gemm_ms + sgst.ms_gemm;
+        st->gemm_flops = b_gemm_flops + sgst.gemm_flops;
+    }
+    return DL_OK;
+}
+
 cudaError_t Workspace::init() {
     if (ready) return cudaSuccess;
     cudaError_t e;

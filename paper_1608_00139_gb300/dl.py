@@ -24,7 +24,7 @@ PATHS = {"auto": 0, "fp64": 1, "mixed": 2, "bool_fp8": 3, "fp8": 3}
 DL_MEM_HOST, DL_MEM_DEVICE = 0, 1
 
 EXPORTED = ["dl_create", "dl_destroy", "dl_last_error", "dl_set_stream", "dl_tc_closure", "dl_tc_closure_bits",
-            "dl_sg_least_model", "dl_sg_real", "dl_tail_recursive", "dl_compose", "dl_tc_batch", "dl_submit", "dl_poll", "dl_cancel",
+            "dl_sg_least_model", "dl_sg_real", "dl_tail_recursive", "dl_transposed", "dl_compose", "dl_tc_batch", "dl_submit", "dl_poll", "dl_cancel",
             "dl_tc_closure_noalloc", "dl_selftest_wait_timeout"]
 NOALLOC_MAX_N = 2048
 
@@ -97,6 +97,8 @@ def lib() -> ctypes.CDLL:
                                             ctypes.POINTER(Stats)]
             L.dl_sg_real.argtypes = [vp, i32, vp, vp, ctypes.c_int, f64, ctypes.c_int, vp, vp,
                                      ctypes.POINTER(Stats)]
+            L.dl_transposed.argtypes = [vp, i32, vp, ctypes.c_int, f64, f64, ctypes.c_int, vp, vp,
+                                        ctypes.POINTER(Stats)]
             L.dl_compose.argtypes = [vp, i32, vp, vp, ctypes.c_int, vp, ctypes.POINTER(Stats)]
             L.dl_tc_batch.argtypes = [vp, i32, vp, vp, ctypes.c_int, vp, ctypes.POINTER(Stats)]
             L.dl_submit.argtypes = [vp, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_uint64)]
@@ -302,6 +304,24 @@ class Context:
         st = Stats()
         _check(lib().dl_tail_recursive(self._h, n, pb, pa, mem, float(eps), 0.0, PATHS[path], bp, rp,
                                        ctypes.byref(st)))
+        return (bits, st.as_dict(), rt) if rtilde else (bits, st.as_dict())
+
+    def transposed(self, R1, eps: float = 0.0, path: str = "auto", rtilde: bool = False):
+        """The transposed class, r2(x,z) <- r1(x,z); r2(x,z) <- r1(x,y), r2(z,y) (Sec. 6.2);
+        returns (bits of the model, stats[, R~2 as float64 in R1's memory kind])."""
+        p, n, mem, keep = _square_u8(R1)
+        bits, bp = _alloc_bits(n, mem, keep)
+        rt, rp = None, None
+        if rtilde:
+            if mem == DL_MEM_DEVICE:
+                import torch
+                rt = torch.empty((n, n), dtype=torch.float64, device=keep.device)
+                rp = rt.data_ptr()
+            else:
+                rt = np.zeros((n, n), dtype=np.float64)
+                rp = rt.ctypes.data
+        st = Stats()
+        _check(lib().dl_transposed(self._h, n, p, mem, float(eps), 0.0, PATHS[path], bp, rp, ctypes.byref(st)))
         return (bits, st.as_dict(), rt) if rtilde else (bits, st.as_dict())
 
     def sg_real(self, P, B=None, eps: float = 0.0, path: str = "auto", bits: bool = True):
