@@ -244,6 +244,52 @@ def bench_tail(ctx, torch, reps: int = 5) -> dict:
     return out
 
 
+TRANS_N = 4096
+
+
+def bench_trans(ctx, torch, reps: int = 5) -> dict:
+    """The transposed class, r2(x,z) <- r1(x,z); r2(x,z) <- r1(x,y), r2(z,y) (Sec. 6.2), on the
+    ER graph N = 4096, p = 1e-3 (seed 8), device-resident: the model (two-sided reduction) and
+    the real R~2 by the FP64 series."""
+    from paper_1608_00139_gb300 import inputs
+    r1 = torch.from_numpy(inputs.er_digraph(TRANS_N, 1e-3, 8)).cuda()
+    torch.cuda.synchronize()
+    out = {"workload": f"transposed class prog:2, ER N={TRANS_N} p=1e-3 seed 8"}
+    ctx.transposed(r1)
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        _, st = ctx.transposed(r1)
+    out["model"] = {"ms": (time.perf_counter() - t0) / reps * 1e3, "device_ms": st["ms_total"],
+                    "model_ones": st["model_ones"], "gemm_launches": st["gemm_launches"]}
+    ctx.transposed(r1, rtilde=True)
+    t0 = time.perf_counter()
+    _, st, _ = ctx.transposed(r1, rtilde=True)
+    npad = (TRANS_N + 255) // 256 * 256
+    step_bytes = 3.0 * npad * npad * 8  # a step reads X, writes X^T, writes the next X
+    gbs = st["iters"] * step_bytes / (st["ms_refine"] * 1e-3) / 1e9 if st["ms_refine"] > 0 else None
+    pk = peaks()
+    out["rtilde"] = {"ms": (time.perf_counter() - t0) * 1e3, "series_steps": st["iters"],
+                     "final_resid": st["final_resid"], "ms_series": st["ms_refine"],
+                     "roofline": {"bound": "hbm", "kernel": "one series step (transpose + gather pass)",
+                                  "achieved": gbs, "peak": pk["hbm"], "unit": "GB/s",
+                                  "frac": gbs / pk["hbm"] if gbs else None, "bytes_per_step": step_bytes}}
+    return out
+
+
+def cpu_trans() -> dict:
+    """The oracle on the transposed workload: semi-naive model and the FP64 series (numpy/scipy)."""
+    from oracle import transposed as tr
+    from paper_1608_00139_gb300 import inputs
+    r1 = inputs.er_digraph(TRANS_N, 1e-3, 8)
+    t0 = time.perf_counter()
+    tr.trans_model(r1)
+    t1 = time.perf_counter()
+    tr.trans_rtilde_series(r1, tol=1e-13 * tr.trans_eps(r1))
+    t2 = time.perf_counter()
+    return {"model_ms": (t1 - t0) * 1e3, "rtilde_ms": (t2 - t1) * 1e3, "kind": "oracle", "cores": 1,
+            "sample": "the whole N = 4096 workload"}
+
+
 def cpu_tail() -> dict:
     """The oracle on the tail recursive workload: rows of the model by breadth-first search (the
     whole-model oracle needs dense products at N = 8192), a bounded sample scaled to N rows."""
@@ -431,6 +477,9 @@ def run_part(args, device: int) -> None:
     elif args.part == "tail":
         with dl.Context(device) as ctx:
             out = bench_tail(ctx, torch)
+    elif args.part == "trans":
+        with dl.Context(device) as ctx:
+            out = bench_trans(ctx, torch)
     else:
         with dl.Context(device) as ctx:
             out = bench_sg(ctx, torch) if args.part == "sg" else bench_batch(ctx, torch, reps=max(1, args.steps))
@@ -455,7 +504,7 @@ def main() -> None:
                     help="skip the same-generation, batch and serving measurements")
     ap.add_argument("--serve-seconds", type=float, default=10.0,
                     help="length of the serving stream (the full workload is 60 s)")
-    ap.add_argument("--part", default="all", choices=["all", "sg", "sg_real", "tail", "batch", "serving", "mixed", "bool"],
+    ap.add_argument("--part", default="all", choices=["all", "sg", "sg_real", "tail", "trans", "batch", "serving", "mixed", "bool"],
                     help="run one secondary measurement alone and print its JSON (for profiling)")
     args = ap.parse_args()
     rank, world, local = dist_env()
@@ -689,6 +738,7 @@ def main() -> None:
         line["same_generation"] = bench_sg(ctxs[0], torch)
         line["sg_real"] = bench_sg_real(ctxs[0], torch)
         line["tail_recursive"] = bench_tail(ctxs[0], torch)
+        line["transposed"] = bench_trans(ctxs[0], torch)
         line["batch"] = bench_batch(ctxs[0], torch)
         line["serving"] = bench_serving(dl, torch, local, args.serve_seconds)
     if pure:
@@ -704,6 +754,8 @@ def main() -> None:
             line["sg_real"]["cpu_oracle"] = cpu_sg_real()
         if "tail_recursive" in line:
             line["tail_recursive"]["cpu_oracle"] = cpu_tail()
+        if "transposed" in line:
+            line["transposed"]["cpu_oracle"] = cpu_trans()
     if rank == 0:
         print(json.dumps(line), flush=True)
     for c in ctxs:

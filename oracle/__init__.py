@@ -16,6 +16,12 @@ Functions (passages they follow are cited in ``oracle.c``):
   tail_model, tail_rtilde, tail_eps  one equation of the tail recursive class (tail.py)
   trans_model, trans_naive, trans_rtilde_kron, trans_rtilde_series, trans_eps
                          the transposed class, program prog:2 of Sec. 6.2 (transposed.py)
+  tail_rtilde_real, tail_system, tail_system_stacked, tail_eps_terms
+                         tail recursive equations with real lower solutions and layered systems
+                         of them (tail.py)
+  program.parse, program.least_model, program.naive_model
+                         least models of Datalog programs over binary predicates by symbolic
+                         semi-naive evaluation, with stratified negation (program.py)
 Bit matrices: ceil(n/64) uint64 words per row, bit j%64 of word j//64, LSB first.
 """
 from __future__ import annotations

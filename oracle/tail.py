@@ -80,3 +80,78 @@ def tail_rtilde(b0: np.ndarray, a: np.ndarray, eps: float | None = None) -> np.n
     if n == 0:
         return np.zeros((0, 0))
     return np.linalg.solve(np.eye(n) - eps * b0, eps * a)
+
+
+# ---- equations with real lower solutions, and layered systems (Sec. 6.1) --------------------
+#
+#   R~_h = eps_h (A1_h + B0_h R~_h + sum_q B_q R~_{j_q}),   j_q < h,
+#
+# solved in order h = 0, 1, ... with the lower R~_{j_q} substituted (the elimination the paper
+# describes after eq. matrixeq:trec).  Its model is the least R_h with
+# R_h = min1(A1_h + B0_h R_h + sum_q B_q R_{j_q}).
+
+def tail_eps_terms(b0: np.ndarray | None, bs) -> float:
+    """The default eps_h = 1 / (1 + max_i (rowsum(B0)_i + sum_q rowsum(B_q)_i)): then
+    eps_h F_h[1, ..., 1] <= 1 entrywise (the condition of Theorem 2), and eps_h < 1 / ||B0||_inf
+    (the uniqueness condition of Sec. 6.1)."""
+    mats = ([] if b0 is None else [np.asarray(b0)]) + [np.asarray(b) for b in bs]
+    if not mats:
+        return 1.0
+    d = sum(m.astype(np.float64).sum(axis=1) for m in mats)
+    return 1.0 / (1.0 + float(d.max()))
+
+
+def tail_rtilde_real(b0, a1, terms, eps: float | None = None) -> np.ndarray:
+    """R~ = (I - eps B0)^-1 eps (A1 + sum_q B_q R_q) in FP64; terms = [(B_q, R_q)] with R_q real
+    (n x n); B0 or A1 may be None (zero)."""
+    n = (b0 if b0 is not None else a1 if a1 is not None else terms[0][0]).shape[0]
+    if eps is None:
+        eps = tail_eps_terms(b0, [b for b, _ in terms])
+    f = np.zeros((n, n)) if a1 is None else np.asarray(a1, dtype=np.float64).copy()
+    for b, r in terms:
+        f += np.asarray(b, dtype=np.float64) @ np.asarray(r, dtype=np.float64)
+    a = np.eye(n) - (0.0 if b0 is None else eps * np.asarray(b0, dtype=np.float64))
+    return np.linalg.solve(a, eps * f)
+
+
+def _eq_parts(eq, n):
+    z = np.zeros((n, n), dtype=np.uint8)
+    a1 = z if eq.get("A1") is None else np.asarray(eq["A1"], dtype=np.uint8)
+    b0 = z if eq.get("B0") is None else np.asarray(eq["B0"], dtype=np.uint8)
+    return a1, b0, list(eq.get("terms", []))
+
+
+def tail_system(eqs, n: int):
+    """In-order solution of a layered system: eqs[h] = {"A1", "B0", "terms": [(B, j)], "eps"}
+    with every j < h.  Returns (models (dense 0/1), R~ (FP64), eps per equation)."""
+    models, xs, epss = [], [], []
+    for h, eq in enumerate(eqs):
+        a1, b0, terms = _eq_parts(eq, n)
+        if any(j >= h for _, j in terms):
+            raise ValueError("a term refers to an equation that is not below")
+        eps = eq.get("eps") or tail_eps_terms(b0, [b for b, _ in terms])
+        a = a1.astype(np.int64)
+        for b, j in terms:
+            a = a + np.asarray(b, dtype=np.int64) @ models[j].astype(np.int64)
+        models.append(tail_model(b0, np.minimum(a, 1).astype(np.uint8)))
+        xs.append(tail_rtilde_real(b0, a1, [(b, xs[j]) for b, j in terms], eps))
+        epss.append(eps)
+    return models, xs, epss
+
+
+def tail_system_stacked(eqs, n: int, epss) -> list:
+    """The same R~ from one dense solve of the whole system: unknowns stacked (m n x n), block
+    (h, h) = I - eps_h B0_h, block (h, j) = -eps_h (sum of the B_q with j_q = j), right-hand side
+    block h = eps_h A1_h."""
+    m = len(eqs)
+    big = np.eye(m * n)
+    rhs = np.zeros((m * n, n))
+    for h, eq in enumerate(eqs):
+        a1, b0, terms = _eq_parts(eq, n)
+        e = epss[h]
+        big[h * n:(h + 1) * n, h * n:(h + 1) * n] -= e * b0.astype(np.float64)
+        for b, j in terms:
+            big[h * n:(h + 1) * n, j * n:(j + 1) * n] -= e * np.asarray(b, dtype=np.float64)
+        rhs[h * n:(h + 1) * n] = e * a1.astype(np.float64)
+    x = np.linalg.solve(big, rhs)
+    return [x[h * n:(h + 1) * n] for h in range(m)]
