@@ -191,6 +191,54 @@ DL_API dl_status dl_tail_recursive(dl_ctx *ctx, int32_t n, const uint8_t *B0, co
                             dl_stats *stats);
 
 /*
+ * One equation of the tail recursive class with the real solutions of the lower equations it
+ * refers to (Sec. 6.1, eq. matrixeq:trec):
+ *     R~ = eps (A1 + B0 R~ + B_1 R~_{j_1} + ... + B_q R~_{j_q}),
+ *     R~ = (I - eps B0)^-1 eps F,   F = A1 + sum_k B_k R~_{j_k}.
+ * B0, A1: n x n 0/1 or NULL (zero).  B[k] (n x n 0/1) and R[k] (n x n doubles, row-major: the
+ * real solution of lower equation j_k) for k < nterms.  All inputs and outputs live in `mem`.
+ * eps <= 0 selects 1/(1 + max_i (rowsum(B0)_i + sum_k rowsum(B_k)_i)), which makes
+ * eps F[1,...,1] <= 1 (the condition of Theorem 2, with every R~_{j_k} <= 1) and eps < 1/||B0||
+ * (the uniqueness condition of Sec. 6.1); a larger eps returns DL_EINVAL.
+ * out_bits (required): the model, the least R with R = min1(A' + B0 R) where A' = [F > 0] is what
+ * the lower models contribute (R~_{j_k} > 0 exactly on the lower models, Theorem 2; real values
+ * that underflowed to 0 in the caller's R[k] would drop facts here: dl_tail_system forms A' from the
+ * lower models instead).  out_rtilde (optional, n x n doubles): R~, by the closure's real
+ * paths with the real right-hand side F: DL_PATH_FP64 (blocked LU in FP64) or DL_PATH_MIXED (TF32
+ * LU, FP64 refinement; DL_PATH_AUTO takes it when out_rtilde is not NULL).  DL_PATH_BOOL_FP8: the
+ * model only.  stats->rows_rechecked: model entries that R~ > 0 missed (underflow).
+ */
+DL_API dl_status dl_tail_recursive_real(dl_ctx *ctx, int32_t n, const uint8_t *B0, const uint8_t *A1, int32_t nterms,
+                                        const uint8_t *const *B, const double *const *R, dl_mem mem, double eps,
+                                        dl_path path, uint64_t *out_bits, double *out_rtilde, dl_stats *stats);
+
+/* One equation of a layered tail recursive system (dl_tail_system). */
+typedef struct {
+    const uint8_t *A1;          /* n x n 0/1, or NULL */
+    const uint8_t *B0;          /* n x n 0/1 coefficient of the equation's own R~, or NULL */
+    int32_t nterms;             /* terms B_k R~_{j_k} of lower equations */
+    const uint8_t *const *B;    /* nterms n x n 0/1 matrices */
+    const int32_t *j;           /* nterms indices of lower equations: 0 <= j[k] < this equation's index */
+    double eps;                 /* <= 0: the default of dl_tail_recursive_real */
+} dl_tail_eq;
+
+/*
+ * A system of m tail recursive equations over the same n constants, solved in order
+ * (Sec. 6.1: a solution is substituted into the equations above it, M solves in all):
+ *     R~_h = eps_h (A1_h + B0_h R~_h + sum_k B_{h,k} R~_{j_{h,k}}),   j_{h,k} < h.
+ * Equation h is what the clauses of one predicate r_h give when every predicate its clauses
+ * read is defined in a lower layer or is r_h itself in the rightmost position.
+ * out_bits[h] (required, n * ceil(n/64) words each): the model of equation h, always from the
+ * lower models: A1_h + sum_k B_{h,k} R_{j_{h,k}} by FP8 products, then the equation's boolean
+ * route (exact whatever the precision of R~).  out_rtilde (NULL, or m pointers each NULL or n x n
+ * doubles): R~_h, on DL_PATH_FP64 or DL_PATH_MIXED; those paths keep every R~_h on the device for
+ * the equations above it.  DL_PATH_AUTO / DL_PATH_BOOL_FP8 give the models only.  All matrices live in `mem`.  stats: sums over the equations (eps_used: the last
+ * one's).
+ */
+DL_API dl_status dl_tail_system(dl_ctx *ctx, int32_t n, int32_t m, const dl_tail_eq *eqs, dl_mem mem, dl_path path,
+                                uint64_t *const *out_bits, double *const *out_rtilde, dl_stats *stats);
+
+/*
  * The real least solution of the same-generation equation (Sec. 7.2; the two-sided class of
  * Sec. 6.3, a discrete Stein/Sylvester equation):
  *     S~ = eps (B + P S~ P^T),

@@ -290,6 +290,82 @@ dl_status dl_tail_recursive(dl_ctx *ctx, int32_t n, const uint8_t *B0, const uin
     });
 }
 
+dl_status dl_tail_recursive_real(dl_ctx *ctx, int32_t n, const uint8_t *B0, const uint8_t *A1, int32_t nterms,
+                                 const uint8_t *const *B, const double *const *R, dl_mem mem, double eps, dl_path path,
+                                 uint64_t *out_bits, double *out_rtilde, dl_stats *stats) {
+    clear_error();
+    GUARD_CTX(ctx);
+    if (stats) std::memset(stats, 0, sizeof(*stats));
+    if (n < 0 || nterms < 0 || !valid_mem(mem)) {
+        set_error("bad n (%d), nterms (%d) or memory kind", n, nterms);
+        return DL_EINVAL;
+    }
+    if (n == 0) return DL_OK;
+    if (!out_bits || (nterms > 0 && (!B || !R))) {
+        set_error("out_bits, and B and R when nterms > 0, must not be NULL");
+        return DL_EINVAL;
+    }
+    for (int32_t k = 0; k < nterms; ++k)
+        if (!B[k] || !R[k]) {
+            set_error("B[%d] and R[%d] must not be NULL", k, k);
+            return DL_EINVAL;
+        }
+    return run_sync(ctx, stats, [&](Workspace &ws, cudaStream_t s, dl_stats *st) -> dl_status {
+        const size_t nn = static_cast<size_t>(n) * n;
+        auto stage = [&](const void *src, size_t bytes, const std::string &name, const void **out) -> dl_status {
+            if (!src || mem == DL_MEM_DEVICE) {
+                *out = src;
+                return DL_OK;
+            }
+            void *d = ws.get(name, std::max<size_t>(bytes, 16));
+            if (!d) {
+                set_error("device allocation failed (%s)", name.c_str());
+                return DL_ENOMEM;
+            }
+            if (cudaMemcpyAsync(d, src, bytes, cudaMemcpyHostToDevice, s) != cudaSuccess) {
+                set_error("copy of %s to the device failed", name.c_str());
+                return DL_EDEVICE;
+            }
+            *out = d;
+            return DL_OK;
+        };
+        const void *b0 = nullptr, *a1 = nullptr;
+        dl_status rc;
+        if ((rc = stage(B0, nn, "tq_b0", &b0)) || (rc = stage(A1, nn, "tq_a1", &a1))) return rc;
+        std::vector<const uint8_t *> bq(static_cast<size_t>(nterms));
+        std::vector<const double *> rq(static_cast<size_t>(nterms));
+        for (int32_t k = 0; k < nterms; ++k) {
+            const void *bd = nullptr, *rd = nullptr;
+            if ((rc = stage(B[k], nn, "tq_term_b" + std::to_string(k), &bd)) ||
+                (rc = stage(R[k], nn * 8, "tq_term_r" + std::to_string(k), &rd)))
+                return rc;
+            bq[k] = static_cast<const uint8_t *>(bd);
+            rq[k] = static_cast<const double *>(rd);
+        }
+        return solve_tail_real(ctx, ws, s, n, static_cast<const uint8_t *>(b0), static_cast<const uint8_t *>(a1),
+                               nterms, bq.data(), rq.data(), eps, path, mem, out_bits, out_rtilde, st);
+    });
+}
+
+dl_status dl_tail_system(dl_ctx *ctx, int32_t n, int32_t m, const dl_tail_eq *eqs, dl_mem mem, dl_path path,
+                         uint64_t *const *out_bits, double *const *out_rtilde, dl_stats *stats) {
+    clear_error();
+    GUARD_CTX(ctx);
+    if (stats) std::memset(stats, 0, sizeof(*stats));
+    if (n < 0 || m < 0 || !valid_mem(mem)) {
+        set_error("bad n (%d), m (%d) or memory kind", n, m);
+        return DL_EINVAL;
+    }
+    if (n == 0 || m == 0) return DL_OK;
+    if (!eqs || !out_bits) {
+        set_error("eqs and out_bits must not be NULL");
+        return DL_EINVAL;
+    }
+    return run_sync(ctx, stats, [&](Workspace &ws, cudaStream_t s, dl_stats *st) {
+        return solve_tail_system(ctx, ws, s, n, m, eqs, mem, path, out_bits, out_rtilde, st);
+    });
+}
+
 dl_status dl_transposed(dl_ctx *ctx, int32_t n, const uint8_t *R1, dl_mem mem, double eps, double thr, dl_path path,
                         uint64_t *out_bits, double *out_rtilde, dl_stats *stats) {
     clear_error();

@@ -95,6 +95,9 @@ struct SolveArgs {
     bool e_device = false;        // E is on the device whatever mem says (unpacked from E_bits)
     const uint8_t *rhs = nullptr;  // tail recursive class: the right-hand side A of
                                    // X = eps (A + E X), a device pointer (NULL: A = E)
+    const double *rhs_real = nullptr;  // a real right-hand side F of X = eps (F + E X) instead
+                                       // (device, n x n FP64, row stride n; FP64 / mixed paths)
+    double rhs_bound = 1.0;        // a bound on |F| (the mixed residual's fixed-point scale)
     bool skip_recheck = false;     // real paths: leave X > 0 in the bits unchecked, count its ones
     const uint8_t *E2 = nullptr;  // same generation: B (may be null); compose: R2
     dl_mem mem = DL_MEM_HOST;
@@ -111,6 +114,14 @@ dl_status solve_sg(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &
 // One equation of the tail recursive class: E = B0 (recursive coefficient), E2 = A (the
 // non-recursive part); bits of the model, R~ into a.out_rtilde on the real paths.
 dl_status solve_tail(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &a, dl_stats *st);
+// One tail recursive equation with real lower solutions, and a layered system of them.
+dl_status solve_tail_real(dl_ctx *ctx, Workspace &ws, cudaStream_t s, int32_t n, const uint8_t *B0,
+                          const uint8_t *A1, int32_t nterms, const uint8_t *const *Bq, const double *const *Rq,
+                          double eps_user, dl_path path, dl_mem mem, uint64_t *out_bits, double *out_rtilde,
+                          dl_stats *st);
+dl_status solve_tail_system(dl_ctx *ctx, Workspace &ws, cudaStream_t s, int32_t n, int32_t m, const dl_tail_eq *eqs,
+                            dl_mem mem, dl_path path, uint64_t *const *out_bits, double *const *out_rtilde,
+                            dl_stats *st);
 // The transposed class (program prog:2): E = R1; bits of the model, R~ into a.out_rtilde.
 dl_status solve_transposed(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &a, dl_stats *st);
 // The real S~ of same generation into a.out_rtilde (n x n doubles); bits optional.

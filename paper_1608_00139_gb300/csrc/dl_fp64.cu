@@ -45,6 +45,24 @@ __global__ void build_kernel(const uint8_t *__restrict__ E, const uint8_t *__res
     }
 }
 
+// G = [I - eps E | eps F] with a real right-hand side F (n x n FP64, row stride n).
+__global__ void build_real_kernel(const uint8_t *__restrict__ E, const double *__restrict__ F, int n, int np,
+                                  double eps, double *__restrict__ G, int64_t ldg) {
+    const int64_t row = blockIdx.y;
+    for (int64_t c = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; c < 2 * np;
+         c += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        double v;
+        if (c < np) {
+            const double e = (row < n && c < n && E[row * n + c]) ? eps : 0.0;
+            v = (c == row ? 1.0 : 0.0) - e;
+        } else {
+            const int64_t cc = c - np;
+            v = (row < n && cc < n) ? eps * F[row * n + cc] : 0.0;
+        }
+        G[row * ldg + c] = v;
+    }
+}
+
 // Unpivoted LU of the b x b block at g (row stride ldg), in place: unit L below, U on/above.
 __global__ void __launch_bounds__(256) diag_lu_kernel(double *g, int64_t ldg) {
     __shared__ double s[B][B + 1];
@@ -208,6 +226,14 @@ cudaError_t fp64_build(const uint8_t *E, const uint8_t *A, int n, int np, double
     dim3 grid(static_cast<unsigned>((2 * np + 255) / 256 < 64 ? (2 * np + 255) / 256 : 64),
               static_cast<unsigned>(np));
     build_kernel<<<grid, 256, 0, s>>>(E, A, n, np, eps, G, ldg);
+    return cudaGetLastError();
+}
+
+cudaError_t fp64_build_real(const uint8_t *E, const double *F, int n, int np, double eps, double *G, int64_t ldg,
+                            cudaStream_t s) {
+    dim3 grid(static_cast<unsigned>((2 * np + 255) / 256 < 64 ? (2 * np + 255) / 256 : 64),
+              static_cast<unsigned>(np));
+    build_real_kernel<<<grid, 256, 0, s>>>(E, F, n, np, eps, G, ldg);
     return cudaGetLastError();
 }
 

@@ -203,6 +203,9 @@ cudaError_t exclusive_scan_large(const int *cnt, int n, int *out, int *scratch, 
 // G = [I - eps E | eps A] (np x 2np doubles, zero/identity padding; A = E for the closure).
 cudaError_t fp64_build(const uint8_t *E, const uint8_t *A, int n, int np, double eps, double *G, int64_t ldg,
                        cudaStream_t s);
+// The same with a real right-hand side: G = [I - eps E | eps F], F n x n FP64 (row stride n).
+cudaError_t fp64_build_real(const uint8_t *E, const double *F, int n, int np, double eps, double *G, int64_t ldg,
+                            cudaStream_t s);
 cudaError_t fp64_solve(double *G, int64_t ldg, int np, int *launches, cudaStream_t s);
 // threshold X > 0 into bits, count guard-band entries (|X| <= tau or X < 0)
 cudaError_t thresh_pack_f64(const double *X, int64_t ldx, int n, int np, double tau, uint64_t *bits,

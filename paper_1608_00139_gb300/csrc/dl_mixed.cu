@@ -188,8 +188,8 @@ __device__ __forceinline__ long long fixed_of(long long bits, int e) {
 // Scale of row j of Z in the residual: every term of a sum (the +1 or A[i][j] included) stays
 // below 2^hb, hb from the row's largest exponent field, and a sum of at most 2^deg_bits terms
 // below 2^62.
-__device__ __forceinline__ int row_scale(int ex_max, int deg_bits) {
-    const int hb = max(ex_max - 1022, 0) + 1;
+__device__ __forceinline__ int row_scale(int ex_max, int deg_bits, int min_hb = 1) {
+    const int hb = max(max(ex_max - 1022, 0) + 1, min_hb);
     return max(0, 62 - deg_bits - hb);
 }
 
@@ -222,8 +222,10 @@ __device__ __forceinline__ float float_of(long long r) {
 
 // R^T[j][i] from the fixed-point sum and Zf[j][i] (the result's last step).
 __device__ __forceinline__ float residual_entry(long long sum, long long z, int i, int j, int n, int e,
-                                                long long eps_q, float inv, const uint8_t *rhs) {
-    if (rhs != nullptr) {
+                                                long long eps_q, float inv, const uint8_t *rhs, const double *rhsr) {
+    if (rhsr != nullptr) {
+        sum += fixed_of(__double_as_longlong(rhsr[static_cast<int64_t>(i) * n + j]), e);
+    } else if (rhs != nullptr) {
         if (rhs[static_cast<int64_t>(i) * n + j]) sum += 1ll << e;
     } else if (i == j) {
         z -= 1ll << e;  // Zf carries the [k = j] term
@@ -237,7 +239,7 @@ template <int G>
 __global__ void __launch_bounds__(1024, 1)
     residual_rows_kernel(const int *__restrict__ ptr, const int *__restrict__ col, int n, int np, long long eps_q,
                          const int *__restrict__ escale, const long long *__restrict__ Zf, float *__restrict__ R,
-                         unsigned *rmax, const uint8_t *__restrict__ rhs) {
+                         unsigned *rmax, const uint8_t *__restrict__ rhs, const double *__restrict__ rhsr) {
     extern __shared__ long long zi[];  // G rows of np
     const int j0 = blockIdx.x * G;
 #pragma unroll
@@ -281,7 +283,7 @@ __global__ void __launch_bounds__(1024, 1)
             const int j = j0 + g;
             if (j >= np) break;
             float r = 0.0f;
-            if (i < n && j < n) r = residual_entry(sum[g], zi[g * np + i], i, j, n, e[g], eps_q, inv[g], rhs);
+            if (i < n && j < n) r = residual_entry(sum[g], zi[g * np + i], i, j, n, e[g], eps_q, inv[g], rhs, rhsr);
             R[static_cast<int64_t>(j) * np + i] = r;
             m = fmaxf(m, fabsf(r));
         }
@@ -361,7 +363,8 @@ __global__ void __launch_bounds__(32 * kRWarps, 1)
     residual_band_kernel(const __grid_constant__ CUtensorMap zmap, int n, int np, int nbd, const int *__restrict__ off,
                          const uint16_t *__restrict__ edges, long long eps_q, const int *__restrict__ escale,
                          const long long *__restrict__ ZfT, float *__restrict__ R, unsigned *rmax,
-                         const uint8_t *__restrict__ rhs, int *status, uint64_t budget_ns) {
+                         const uint8_t *__restrict__ rhs, const double *__restrict__ rhsr, int *status,
+                         uint64_t budget_ns) {
     extern __shared__ __align__(1024) uint8_t rsmem[];
     uint16_t *ebuf = reinterpret_cast<uint16_t *>(rsmem + 2 * kBandBytes) + (threadIdx.x >> 5) * kEdgeBuf;
     uint64_t *full = reinterpret_cast<uint64_t *>(rsmem + 2 * kBandBytes + sizeof(uint16_t) * kRWarps * kEdgeBuf);
@@ -457,7 +460,7 @@ __global__ void __launch_bounds__(32 * kRWarps, 1)
         for (int u = 0; u < 4; ++u) {
             const int i = i0 + il + u;
             const long long z = ZfT[static_cast<int64_t>(i) * np + j];
-            v4[u] = i < n && j < n ? residual_entry(acc[il + u], z, i, j, n, e, eps_q, inv, rhs) : 0.0f;
+            v4[u] = i < n && j < n ? residual_entry(acc[il + u], z, i, j, n, e, eps_q, inv, rhs, rhsr) : 0.0f;
             m = fmaxf(m, fabsf(v4[u]));
         }
         *reinterpret_cast<float4 *>(rrow + il) = make_float4(v4[0], v4[1], v4[2], v4[3]);
@@ -468,12 +471,13 @@ __global__ void __launch_bounds__(32 * kRWarps, 1)
 }
 
 // Z += D for row j (one block per row, the new row kept in shared memory), then the row's scale
-// e_j = row_scale(largest exponent field, deg_bits) into escale[j] and the fixed-point row
+// e_j = row_scale(largest exponent field, deg_bits, min_hb) into escale[j] (min_hb: a real right-
+// hand side's terms are below 2^min_hb too) and the fixed-point row
 // Zf[j][k] = round(Z[j][k] 2^e_j), plus 2^e_j at k = j < n when add_identity (the closure's
 // [k = j] term of the residual).
 __global__ void __launch_bounds__(256) add_fix_kernel(double *__restrict__ Z, const float *__restrict__ D, int n,
-                                                      int np, int deg_bits, int add_identity, int *__restrict__ escale,
-                                                      long long *__restrict__ Zf) {
+                                                      int np, int deg_bits, int min_hb, int add_identity,
+                                                      int *__restrict__ escale, long long *__restrict__ Zf) {
     // (Zf == nullptr: only Z and escale; fix_transpose_kernel then writes the transposed copy)
     extern __shared__ double zrow_s[];
     __shared__ int wmax[8];
@@ -504,13 +508,28 @@ __global__ void __launch_bounds__(256) add_fix_kernel(double *__restrict__ Z, co
     int m = 0;
 #pragma unroll
     for (int w = 0; w < 8; ++w) m = max(m, wmax[w]);
-    const int e = row_scale(m, deg_bits);
+    const int e = row_scale(m, deg_bits, min_hb);
     if (threadIdx.x == 0) escale[j] = e;
     if (Zf == nullptr) return;
     for (int k = threadIdx.x; k < np; k += blockDim.x) {
         long long v = fixed_of(__double_as_longlong(zrow_s[k]), e);
         if (add_identity && k == j && j < n) v += 1ll << e;
         Zf[base + k] = v;
+    }
+}
+
+// R^T = (eps F)^T for a real F (n x n FP64), FP32, zero padding.
+__global__ void build_rt_real_kernel(const double *__restrict__ F, int n, int np, double eps, float *__restrict__ R) {
+    __shared__ float tile[TT][TT + 1];
+    const int c0 = blockIdx.x * TT, r0 = blockIdx.y * TT;
+    for (int y = threadIdx.y; y < TT; y += blockDim.y) {
+        const int r = r0 + y, c = c0 + threadIdx.x;
+        tile[y][threadIdx.x] = (r < n && c < n) ? static_cast<float>(eps * F[static_cast<int64_t>(r) * n + c]) : 0.0f;
+    }
+    __syncthreads();
+    for (int y = threadIdx.y; y < TT; y += blockDim.y) {
+        const int r = c0 + y, c = r0 + threadIdx.x;
+        if (r < np && c < np) R[static_cast<int64_t>(r) * np + c] = tile[threadIdx.x][y];
     }
 }
 
@@ -869,6 +888,13 @@ dl_status tc_mixed(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &
     const int max_iters = ctx->cfg.refine_max_iters > 0 ? ctx->cfg.refine_max_iters : 30;
     int deg_bits = 0;  // 2^deg_bits >= ||E||_inf + 1 (the terms of one sum, the +1 or A[i][j] included)
     while ((1ull << deg_bits) < std::max<unsigned long long>(dmax, 1) + 1) ++deg_bits;
+    const bool general_rhs = a.rhs != nullptr || a.rhs_real != nullptr;
+    int min_hb = 1;  // a real right-hand side's terms are below 2^min_hb as well
+    if (a.rhs_real) {
+        int ex = 0;
+        std::frexp(std::max(a.rhs_bound, 1.0), &ex);  // rhs_bound < 2^ex
+        min_hb = std::max(1, ex);
+    }
     const long long eps_q = std::llround(std::ldexp(eps, 62));
     auto *escale = static_cast<int *>(ws.get("mx_escale", np * 4));
     auto *Zf = static_cast<long long *>(ws.get("mx_Zf", np * np * 8));
@@ -922,19 +948,23 @@ dl_status tc_mixed(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &
     auto residual = [&](unsigned *rmax_p) -> cudaError_t {
         if (banded) {
             dim3 tgrid(static_cast<unsigned>(np / TT), static_cast<unsigned>(np / TT));
-            fix_transpose_kernel<<<tgrid, dim3(TT, 8), 0, s>>>(Z64, escale, n, N, a.rhs ? 0 : 1, Zf);
+            fix_transpose_kernel<<<tgrid, dim3(TT, 8), 0, s>>>(Z64, escale, n, N, general_rhs ? 0 : 1, Zf);
             residual_band_kernel<<<static_cast<unsigned>((np / kRJ) * ni), 32 * kRWarps, kResidualSmem, s>>>(
-                zmap, n, N, nbd, boff, bedges, eps_q, escale, Zf, R32, rmax_p, a.rhs, ws.status, ctx->budget_ns);
+                zmap, n, N, nbd, boff, bedges, eps_q, escale, Zf, R32, rmax_p, a.rhs, a.rhs_real, ws.status,
+                ctx->budget_ns);
             return cudaGetLastError();
         }
         const unsigned grid = static_cast<unsigned>((np + rows_per_block - 1) / rows_per_block);
         const size_t smem = row_smem * rows_per_block;
         if (rows_per_block == 3)
-            residual_rows_kernel<3><<<grid, 1024, smem, s>>>(csr_ptr, csr_col, n, N, eps_q, escale, Zf, R32, rmax_p, a.rhs);
+            residual_rows_kernel<3><<<grid, 1024, smem, s>>>(csr_ptr, csr_col, n, N, eps_q, escale, Zf, R32, rmax_p, a.rhs,
+                                                             a.rhs_real);
         else if (rows_per_block == 2)
-            residual_rows_kernel<2><<<grid, 1024, smem, s>>>(csr_ptr, csr_col, n, N, eps_q, escale, Zf, R32, rmax_p, a.rhs);
+            residual_rows_kernel<2><<<grid, 1024, smem, s>>>(csr_ptr, csr_col, n, N, eps_q, escale, Zf, R32, rmax_p, a.rhs,
+                                                             a.rhs_real);
         else
-            residual_rows_kernel<1><<<grid, 1024, smem, s>>>(csr_ptr, csr_col, n, N, eps_q, escale, Zf, R32, rmax_p, a.rhs);
+            residual_rows_kernel<1><<<grid, 1024, smem, s>>>(csr_ptr, csr_col, n, N, eps_q, escale, Zf, R32, rmax_p, a.rhs,
+                                                             a.rhs_real);
         return cudaGetLastError();
     };
     unsigned *rmax_d = reinterpret_cast<unsigned *>(ws.scal + 20);
@@ -946,14 +976,18 @@ dl_status tc_mixed(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &
     MCK(cudaMemsetAsync(Z64, 0, np * np * 8, s));
     {
         dim3 tgrid(static_cast<unsigned>(np / TT), static_cast<unsigned>(np / TT));
-        build_rt_kernel<<<tgrid, dim3(TT, 8), 0, s>>>(a.rhs ? a.rhs : E, n, N, static_cast<float>(eps), R32);
+        if (a.rhs_real)
+            build_rt_real_kernel<<<tgrid, dim3(TT, 8), 0, s>>>(a.rhs_real, n, N, eps, R32);
+        else
+            build_rt_kernel<<<tgrid, dim3(TT, 8), 0, s>>>(a.rhs ? a.rhs : E, n, N, static_cast<float>(eps), R32);
         MCK(cudaGetLastError());
         ++launches;
     }
     for (;;) {
         MCK(run(refine[0], sms, s));  // D^T = R^T W^T
-        add_fix_kernel<<<static_cast<unsigned>(np), 256, row_smem, s>>>(Z64, D32, n, N, deg_bits, a.rhs ? 0 : 1,
-                                                                      escale, banded ? nullptr : Zf);
+        add_fix_kernel<<<static_cast<unsigned>(np), 256, row_smem, s>>>(Z64, D32, n, N, deg_bits, min_hb,
+                                                                      general_rhs ? 0 : 1, escale,
+                                                                      banded ? nullptr : Zf);
         MCK(cudaGetLastError());
         ++launches;
         ++products;

@@ -739,7 +739,10 @@ dl_status tc_fp64(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &a
     double eps = 0;
     if ((rc = choose_eps(a.eps, 1.0 / (1.0 + static_cast<double>(dmax)), "Lemma 1 (1/(1+||E||))", &eps)))
         return rc;
-    CK(fp64_build(E, a.rhs ? a.rhs : E, n, static_cast<int>(np), eps, G, ldg, s));
+    if (a.rhs_real)
+        CK(fp64_build_real(E, a.rhs_real, n, static_cast<int>(np), eps, G, ldg, s));
+    else
+        CK(fp64_build(E, a.rhs ? a.rhs : E, n, static_cast<int>(np), eps, G, ldg, s));
     ++launches;
     tm.mark(1);
     CK(fp64_solve(G, ldg, static_cast<int>(np), &launches, s));
@@ -1570,6 +1573,336 @@ dl_status solve_tail(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs
         st->gemm_launches = sr.gemm_launches + sc.gemm_launches + sm.gemm_launches;
         st->gemm_flops = sr.gemm_flops + sc.gemm_flops + sm.gemm_flops;
         st->ms_gemm = sr.ms_gemm + sc.ms_gemm + sm.ms_gemm;
+    }
+    return DL_OK;
+}
+
+namespace {
+
+// F = A1 (0/1 bytes) or 0, n x n FP64.
+__global__ void rhs_init_kernel(const uint8_t *__restrict__ A1, int n, double *__restrict__ F) {
+    const int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x;
+    if (t < static_cast<int64_t>(n) * n) F[t] = A1 != nullptr && A1[t] ? 1.0 : 0.0;
+}
+
+// F += B R over the CSR of B:  F[i][j] += sum_{y in succ(i)} R[y][j]  (R n x n, row stride n).
+__global__ void rhs_gather_kernel(const int *__restrict__ ptr, const int *__restrict__ col, int n,
+                                  const double *__restrict__ R, double *__restrict__ F) {
+    const int i = blockIdx.y, j = blockIdx.x * blockDim.x + threadIdx.x;
+    if (j >= n) return;
+    double acc = 0.0;
+    const int q1 = ptr[i + 1];
+    for (int q = ptr[i]; q < q1; ++q) acc += R[static_cast<int64_t>(col[q]) * n + j];
+    F[static_cast<int64_t>(i) * n + j] += acc;
+}
+
+// out = [F > 0] (bytes) and *amax = max |F| (bits of a non-negative double).
+__global__ void positive_bytes_kernel(const double *__restrict__ F, int64_t count, uint8_t *__restrict__ out,
+                                      unsigned long long *amax) {
+    unsigned long long m = 0;
+    for (int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; t < count;
+         t += static_cast<int64_t>(gridDim.x) * blockDim.x) {
+        const double v = F[t];
+        out[t] = v > 0.0 ? 1 : 0;
+        const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(v)) & 0x7FFFFFFFFFFFFFFFull;
+        m = b > m ? b : m;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        const unsigned long long other = __shfl_xor_sync(0xffffffffu, m, o);
+        m = other > m ? other : m;
+    }
+    if ((threadIdx.x & 31) == 0 && m) atomicMax(amax, m);
+}
+
+// dst |= src (bytes).
+__global__ void or_bytes_kernel(uint8_t *__restrict__ dst, const uint8_t *__restrict__ src, int64_t count) {
+    for (int64_t t = blockIdx.x * static_cast<int64_t>(blockDim.x) + threadIdx.x; t < count;
+         t += static_cast<int64_t>(gridDim.x) * blockDim.x)
+        dst[t] |= src[t];
+}
+
+unsigned stream_grid(int64_t count) { return static_cast<unsigned>(std::min<int64_t>((count + 255) / 256, 16384)); }
+
+}  // namespace
+
+// One equation of the tail recursive class with the lower equations' real solutions
+// (Sec. 6.1, eq. matrixeq:trec):
+//     R~ = eps (A1 + B0 R~ + sum_q B_q R_q),   R~ = (I - eps B0)^-1 eps F,   F = A1 + sum_q B_q R_q,
+// All pointers are device pointers (B0 / A1 may be null: zero); out_bits / out_rtilde in `mem`.
+//  * F in FP64 by gathers over the CSR of each B_q;
+//  * eps: default 1 / (1 + max_i (rowsum(B0)_i + sum_q rowsum(B_q)_i)), which makes
+//    eps F[1, ..., 1] <= 1 when the R_q are at most 1 (Theorem 2) and keeps eps < 1 / ||B0||;
+//  * the model: the least R with R = min1(A' + B0 R), A' = [F > 0] (the support of F is what the
+//    lower models contribute, by the positivity of Lemma 5's kind), by solve_tail's boolean route;
+//  * R~ (DL_PATH_FP64 / DL_PATH_MIXED, or AUTO with out_rtilde: mixed): the closure's real paths
+//    with the real right-hand side F.
+dl_status solve_tail_real(dl_ctx *ctx, Workspace &ws, cudaStream_t s, int32_t n, const uint8_t *B0,
+                          const uint8_t *A1, int32_t nterms, const uint8_t *const *Bq, const double *const *Rq,
+                          double eps_user, dl_path path, dl_mem mem, uint64_t *out_bits, double *out_rtilde,
+                          dl_stats *st) {
+    if (path != DL_PATH_AUTO && path != DL_PATH_BOOL_FP8 && path != DL_PATH_FP64 && path != DL_PATH_MIXED) {
+        set_error("unknown path %d", static_cast<int>(path));
+        return DL_EINVAL;
+    }
+    if (out_rtilde && path == DL_PATH_BOOL_FP8) {
+        set_error("DL_PATH_BOOL_FP8 computes no real-valued R~; use DL_PATH_FP64 or DL_PATH_MIXED");
+        return DL_EINVAL;
+    }
+    const int64_t nn = static_cast<int64_t>(n) * n, w = (n + 63) / 64;
+    auto *F = static_cast<double *>(ws.get("tt_F", std::max<int64_t>(nn, 2) * 8));
+    auto *Ab = static_cast<uint8_t *>(ws.get("tt_Ab", std::max<int64_t>(nn, 16)));
+    auto *cnt = static_cast<int *>(ws.get("tt_cnt", (static_cast<size_t>(n) + 1) * 4));
+    auto *ptr = static_cast<int *>(ws.get("tt_ptr", (static_cast<size_t>(n) + 1) * 4));
+    auto *bits = static_cast<uint64_t *>(ws.get("tt_bits", std::max<int64_t>(n * w, 2) * 8));
+    NEED(F && Ab && cnt && ptr && bits);
+    const uint8_t *b0 = B0;
+    if (!b0) {  // no recursive occurrence: B0 = 0
+        auto *z = static_cast<uint8_t *>(ws.get("tt_zero", std::max<int64_t>(nn, 16)));
+        NEED(z);
+        CK(cudaMemsetAsync(z, 0, std::max<int64_t>(nn, 16), s));
+        b0 = z;
+    }
+    CK(cudaMemsetAsync(ws.status, 0, sizeof(int), s));
+    // row degrees of B0 and of every B_q (the default eps), and F
+    std::vector<int> deg(static_cast<size_t>(n), 0), h(static_cast<size_t>(n) + 1);
+    auto add_degrees = [&](const uint8_t *M) -> dl_status {
+        CK(csr_build(M, n, cnt, ptr, s));
+        CK(cudaMemcpyAsync(h.data(), cnt, static_cast<size_t>(n) * 4, cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        for (int32_t i = 0; i < n; ++i) deg[i] += h[i];
+        return DL_OK;
+    };
+    dl_status rc;
+    if ((rc = add_degrees(b0))) return rc;
+    rhs_init_kernel<<<static_cast<unsigned>((nn + 255) / 256), 256, 0, s>>>(A1, n, F);
+    CK(cudaGetLastError());
+    int launches = 3;
+    for (int32_t q = 0; q < nterms; ++q) {
+        if ((rc = add_degrees(Bq[q]))) return rc;
+        int nnz = 0;
+        CK(cudaMemcpyAsync(&nnz, ptr + n, sizeof(int), cudaMemcpyDeviceToHost, s));
+        CK(cudaStreamSynchronize(s));
+        auto *col = static_cast<int *>(ws.get("tt_col", static_cast<size_t>(std::max(nnz, 1)) * 4));
+        NEED(col);
+        CK(csr_fill(Bq[q], n, ptr, col, s));
+        dim3 grid(static_cast<unsigned>((n + 255) / 256), static_cast<unsigned>(n));
+        rhs_gather_kernel<<<grid, 256, 0, s>>>(ptr, col, n, Rq[q], F);
+        CK(cudaGetLastError());
+        launches += 4;
+    }
+    const int dmax = *std::max_element(deg.begin(), deg.end());
+    double eps = 0;
+    if ((rc = choose_eps(eps_user, 1.0 / (1.0 + dmax), "Theorem 2 (eps F[1] <= 1)", &eps))) return rc;
+    CK(cudaMemsetAsync(ws.scal + SC_GUARD, 0, sizeof(unsigned long long), s));
+    positive_bytes_kernel<<<stream_grid(nn), 256, 0, s>>>(F, nn, Ab, ws.scal + SC_GUARD);
+    CK(cudaGetLastError());
+    ++launches;
+    if ((rc = read_scalars(ws, s))) return rc;
+    if ((rc = check_status(ws, s))) return rc;
+    double fmax = 0.0;
+    {
+        const unsigned long long b = host_scal(ws)[SC_GUARD];
+        std::memcpy(&fmax, &b, sizeof fmax);
+    }
+    // the model (unless the caller forms it from exact lower models: out_bits == nullptr)
+    dl_stats sm{};
+    if (out_bits) {
+    SolveArgs m;
+    m.n = n;
+    m.E = b0;
+    m.E2 = Ab;
+    m.mem = DL_MEM_DEVICE;
+    m.eps = eps;
+    m.path = path == DL_PATH_BOOL_FP8 ? DL_PATH_BOOL_FP8 : DL_PATH_AUTO;
+    m.out_bits = bits;
+    if ((rc = solve_tail(ctx, ws, s, m, &sm))) return rc;
+    CK(cudaMemcpyAsync(out_bits, bits, static_cast<size_t>(n) * w * 8,
+                       mem == DL_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+    }
+    // R~
+    dl_stats sr{};
+    const bool real = path == DL_PATH_FP64 || path == DL_PATH_MIXED || out_rtilde != nullptr;
+    if (real) {
+        SolveArgs r;
+        r.n = n;
+        r.E = b0;
+        r.e_device = true;
+        r.rhs_real = F;
+        r.rhs_bound = fmax;
+        r.skip_recheck = true;
+        r.mem = mem;
+        r.eps = eps;
+        r.path = path == DL_PATH_FP64 ? DL_PATH_FP64 : DL_PATH_MIXED;
+        r.out_rtilde = out_rtilde;
+        if ((rc = solve_tc(ctx, ws, s, r, &sr))) return rc;
+    }
+    CK(cudaStreamSynchronize(s));
+    if (st) {
+        st->path_used = real ? sr.path_used : sm.path_used;
+        st->eps_used = eps;
+        st->iters = real ? sr.iters : sm.iters;
+        st->final_resid = real ? sr.final_resid : -1.0;
+        st->model_ones = sm.model_ones;
+        // model entries that X > 0 missed (underflow; X > 0 never holds outside the model)
+        st->rows_rechecked = real && out_bits ? sm.model_ones - sr.model_ones : 0;
+        st->ms_factor = sr.ms_factor;
+        st->ms_solve = sr.ms_solve;
+        st->ms_refine = sr.ms_refine;
+        st->ms_epilogue = sm.ms_total;
+        st->ms_total = sr.ms_total + sm.ms_total;
+        st->gpu_launches = launches + sr.gpu_launches + sm.gpu_launches;
+        st->gemm_launches = sr.gemm_launches + sm.gemm_launches;
+        st->gemm_flops = sr.gemm_flops + sm.gemm_flops;
+        st->ms_gemm = sr.ms_gemm + sm.ms_gemm;
+    }
+    return DL_OK;
+}
+
+// A layered system of tail recursive equations, solved in order (Sec. 6.1: each R~_h is solved with
+// the lower ones substituted).  eqs[h].terms refer to equations j < h.  Real paths keep every R~_h
+// on the device for the equations above it (FP64, n x n each); the boolean paths keep the models
+// and form A'_h = min1(A1_h + sum_q B_q R_{j_q}) by FP8 products.
+dl_status solve_tail_system(dl_ctx *ctx, Workspace &ws, cudaStream_t s, int32_t n, int32_t m, const dl_tail_eq *eqs,
+                            dl_mem mem, dl_path path, uint64_t *const *out_bits, double *const *out_rtilde,
+                            dl_stats *st) {
+    const bool real = path == DL_PATH_FP64 || path == DL_PATH_MIXED;
+    if (!real && path != DL_PATH_AUTO && path != DL_PATH_BOOL_FP8) {
+        set_error("unknown path %d", static_cast<int>(path));
+        return DL_EINVAL;
+    }
+    for (int32_t h = 0; h < m; ++h) {
+        if (!out_bits[h]) {
+            set_error("out_bits[%d] must not be NULL", h);
+            return DL_EINVAL;
+        }
+        if (out_rtilde && out_rtilde[h] && !real) {
+            set_error("out_rtilde needs DL_PATH_FP64 or DL_PATH_MIXED");
+            return DL_EINVAL;
+        }
+        if (eqs[h].nterms < 0 || (eqs[h].nterms > 0 && (!eqs[h].B || !eqs[h].j))) {
+            set_error("equation %d: bad terms", h);
+            return DL_EINVAL;
+        }
+        for (int32_t q = 0; q < eqs[h].nterms; ++q)
+            if (eqs[h].j[q] < 0 || eqs[h].j[q] >= h || !eqs[h].B[q]) {
+                set_error("equation %d, term %d: j must name an equation below %d", h, q, h);
+                return DL_EINVAL;
+            }
+    }
+    const int64_t nn = static_cast<int64_t>(n) * n, w = (n + 63) / 64;
+    auto key = [](const char *base, int a, int b = -1) {
+        return std::string(base) + std::to_string(a) + (b >= 0 ? "_" + std::to_string(b) : std::string());
+    };
+    auto stage = [&](const uint8_t *src, const std::string &name, const uint8_t **out) -> dl_status {
+        if (!src || mem == DL_MEM_DEVICE) {
+            *out = src;
+            return DL_OK;
+        }
+        auto *d = static_cast<uint8_t *>(ws.get(name, std::max<int64_t>(nn, 16)));
+        NEED(d);
+        CK(cudaMemcpyAsync(d, src, nn, cudaMemcpyHostToDevice, s));
+        *out = d;
+        return DL_OK;
+    };
+    dl_stats tot{};
+    dl_status rc;
+    for (int32_t h = 0; h < m; ++h) {
+        const dl_tail_eq &eq = eqs[h];
+        const uint8_t *A1 = nullptr, *B0 = nullptr;
+        if ((rc = stage(eq.A1, key("ts_a", h), &A1)) || (rc = stage(eq.B0, key("ts_b", h), &B0))) return rc;
+        std::vector<const uint8_t *> Bq(static_cast<size_t>(eq.nterms));
+        for (int32_t q = 0; q < eq.nterms; ++q)
+            if ((rc = stage(eq.B[q], key("ts_q", h, q), &Bq[q]))) return rc;
+        auto *bits = static_cast<uint64_t *>(ws.get(key("ts_bits", h), std::max<int64_t>(n * w, 2) * 8));
+        NEED(bits);
+        dl_stats sh{};
+        {   // the model from the lower models: A' = A1 | OR_q min1(B_q M_{j_q}) as bytes
+            auto *Ap = static_cast<uint8_t *>(ws.get("ts_ap", std::max<int64_t>(nn, 16)));
+            auto *cb = static_cast<uint64_t *>(ws.get("ts_cbits", std::max<int64_t>(n * w, 2) * 8));
+            auto *cu = static_cast<uint8_t *>(ws.get("ts_cu8", std::max<int64_t>(nn, 16)));
+            NEED(Ap && cb && cu);
+            if (A1) CK(cudaMemcpyAsync(Ap, A1, nn, cudaMemcpyDeviceToDevice, s));
+            else CK(cudaMemsetAsync(Ap, 0, nn, s));
+            for (int32_t q = 0; q < eq.nterms; ++q) {
+                const auto *Mj = static_cast<const uint8_t *>(ws.get(key("ts_m", eq.j[q]), static_cast<size_t>(nn)));
+                SolveArgs c;
+                c.n = n;
+                c.E = Bq[q];
+                c.E2 = Mj;
+                c.mem = DL_MEM_DEVICE;
+                c.out_bits = cb;
+                dl_stats sc{};
+                if ((rc = solve_compose(ctx, ws, s, c, &sc))) return rc;
+                CK(unpack_bits_u8(cb, n, cu, ws.status, s));
+                or_bytes_kernel<<<stream_grid(nn), 256, 0, s>>>(Ap, cu, nn);
+                CK(cudaGetLastError());
+                sh.gpu_launches += sc.gpu_launches + 2;
+                sh.gemm_launches += sc.gemm_launches;
+                sh.ms_total += sc.ms_total;
+            }
+            const uint8_t *b0 = B0;
+            if (!b0) {
+                auto *z = static_cast<uint8_t *>(ws.get("tt_zero", std::max<int64_t>(nn, 16)));
+                NEED(z);
+                CK(cudaMemsetAsync(z, 0, std::max<int64_t>(nn, 16), s));
+                b0 = z;
+            }
+            SolveArgs t;
+            t.n = n;
+            t.E = b0;
+            t.E2 = Ap;
+            t.mem = DL_MEM_DEVICE;
+            t.eps = eq.eps;
+            t.path = path == DL_PATH_BOOL_FP8 ? DL_PATH_BOOL_FP8 : DL_PATH_AUTO;
+            t.out_bits = bits;
+            dl_stats stl{};
+            if ((rc = solve_tail(ctx, ws, s, t, &stl))) return rc;
+            sh.model_ones = stl.model_ones;
+            sh.eps_used = stl.eps_used;
+            sh.ms_total += stl.ms_total;
+            sh.gpu_launches += stl.gpu_launches;
+            sh.gemm_launches += stl.gemm_launches;
+            auto *Mh = static_cast<uint8_t *>(ws.get(key("ts_m", h), std::max<int64_t>(nn, 16)));
+            NEED(Mh);
+            CK(unpack_bits_u8(bits, n, Mh, ws.status, s));
+        }
+        if (real) {  // R~_h from the lower R~ (kept on the device)
+            std::vector<const double *> Rq(static_cast<size_t>(eq.nterms));
+            for (int32_t q = 0; q < eq.nterms; ++q)
+                Rq[q] = static_cast<const double *>(ws.get(key("ts_x", eq.j[q]), static_cast<size_t>(nn) * 8));
+            auto *X = static_cast<double *>(ws.get(key("ts_x", h), std::max<int64_t>(nn, 2) * 8));
+            NEED(X);
+            dl_stats sr{};
+            if ((rc = solve_tail_real(ctx, ws, s, n, B0, A1, eq.nterms, Bq.data(), Rq.data(), eq.eps, path,
+                                      DL_MEM_DEVICE, nullptr, X, &sr)))
+                return rc;
+            if (out_rtilde && out_rtilde[h])
+                CK(cudaMemcpyAsync(out_rtilde[h], X, static_cast<size_t>(nn) * 8,
+                                   mem == DL_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+            sh.eps_used = sr.eps_used;
+            sh.iters = sr.iters;
+            sh.final_resid = sr.final_resid;
+            sh.ms_total += sr.ms_total;
+            sh.gpu_launches += sr.gpu_launches;
+            sh.gemm_launches += sr.gemm_launches;
+        }
+        CK(cudaMemcpyAsync(out_bits[h], bits, static_cast<size_t>(n) * w * 8,
+                           mem == DL_MEM_DEVICE ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, s));
+        tot.ms_total += sh.ms_total;
+        tot.gpu_launches += sh.gpu_launches;
+        tot.gemm_launches += sh.gemm_launches;
+        tot.model_ones += sh.model_ones;
+        tot.iters += sh.iters;
+        tot.final_resid = std::max(tot.final_resid, sh.final_resid);
+        tot.rows_rechecked += sh.rows_rechecked;
+        tot.eps_used = sh.eps_used;  // the last equation's
+    }
+    CK(cudaStreamSynchronize(s));
+    if ((rc = check_status(ws, s))) return rc;
+    if (st) {
+        *st = tot;
+        st->path_used = path;
     }
     return DL_OK;
 }

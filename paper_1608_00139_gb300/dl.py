@@ -24,7 +24,7 @@ PATHS = {"auto": 0, "fp64": 1, "mixed": 2, "bool_fp8": 3, "fp8": 3}
 DL_MEM_HOST, DL_MEM_DEVICE = 0, 1
 
 EXPORTED = ["dl_create", "dl_destroy", "dl_last_error", "dl_set_stream", "dl_tc_closure", "dl_tc_closure_bits",
-            "dl_sg_least_model", "dl_sg_real", "dl_tail_recursive", "dl_transposed", "dl_compose", "dl_tc_batch", "dl_submit", "dl_poll", "dl_cancel",
+            "dl_sg_least_model", "dl_sg_real", "dl_tail_recursive", "dl_tail_recursive_real", "dl_tail_system", "dl_transposed", "dl_compose", "dl_tc_batch", "dl_submit", "dl_poll", "dl_cancel",
             "dl_tc_closure_noalloc", "dl_selftest_wait_timeout"]
 NOALLOC_MAX_N = 2048
 
@@ -60,6 +60,12 @@ class Stats(ctypes.Structure):
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
+
+
+class TailEq(ctypes.Structure):
+    _fields_ = [("A1", ctypes.c_void_p), ("B0", ctypes.c_void_p), ("nterms", ctypes.c_int32),
+                ("B", ctypes.POINTER(ctypes.c_void_p)), ("j", ctypes.POINTER(ctypes.c_int32)),
+                ("eps", ctypes.c_double)]
 
 
 class Request(ctypes.Structure):
@@ -99,6 +105,10 @@ def lib() -> ctypes.CDLL:
                                      ctypes.POINTER(Stats)]
             L.dl_transposed.argtypes = [vp, i32, vp, ctypes.c_int, f64, f64, ctypes.c_int, vp, vp,
                                         ctypes.POINTER(Stats)]
+            L.dl_tail_recursive_real.argtypes = [vp, i32, vp, vp, i32, vp, vp, ctypes.c_int, f64, ctypes.c_int, vp, vp,
+                                                 ctypes.POINTER(Stats)]
+            L.dl_tail_system.argtypes = [vp, i32, i32, vp, ctypes.c_int, ctypes.c_int, vp, vp,
+                                         ctypes.POINTER(Stats)]
             L.dl_compose.argtypes = [vp, i32, vp, vp, ctypes.c_int, vp, ctypes.POINTER(Stats)]
             L.dl_tc_batch.argtypes = [vp, i32, vp, vp, ctypes.c_int, vp, ctypes.POINTER(Stats)]
             L.dl_submit.argtypes = [vp, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_uint64)]
@@ -305,6 +315,87 @@ class Context:
         _check(lib().dl_tail_recursive(self._h, n, pb, pa, mem, float(eps), 0.0, PATHS[path], bp, rp,
                                        ctypes.byref(st)))
         return (bits, st.as_dict(), rt) if rtilde else (bits, st.as_dict())
+
+    def _real_out(self, n, mem, keep):
+        if mem == DL_MEM_DEVICE:
+            import torch
+            rt = torch.empty((n, n), dtype=torch.float64, device=keep.device)
+            return rt, rt.data_ptr()
+        rt = np.zeros((n, n), dtype=np.float64)
+        return rt, rt.ctypes.data
+
+    def tail_recursive_real(self, B0, A1, terms, eps: float = 0.0, path: str = "mixed", rtilde: bool = True):
+        """R~ = eps (A1 + B0 R~ + sum_k B_k R_k) with real lower solutions R_k (Sec. 6.1);
+        terms = [(B_k, R_k)].  B0 / A1 may be None.  Returns (bits, stats[, R~])."""
+        ref = next(x for x in [B0, A1] + [b for b, _ in terms] if x is not None)
+        _, n, mem, keep = _square_u8(ref)
+        keepalive, bps, rps = [], [], []
+        sb0 = _square_u8(B0) if B0 is not None else (None, n, mem, None)
+        sa1 = _square_u8(A1) if A1 is not None else (None, n, mem, None)
+        for sx in (sb0, sa1):
+            if sx[1] != n or sx[2] != mem:
+                raise ValueError("B0 and A1 must match the terms in size and memory kind")
+        keepalive += [sb0[3], sa1[3]]
+        pb0, pa1 = sb0[0], sa1[0]
+        for b, r in terms:
+            pb, nb, memb, kb = _square_u8(b)
+            if nb != n or memb != mem:
+                raise ValueError("terms must match in size and memory kind")
+            if mem == DL_MEM_DEVICE:
+                if not (r.dtype == __import__("torch").float64 and r.is_cuda and r.is_contiguous()):
+                    raise ValueError("R_k must be a contiguous float64 CUDA tensor")
+                rp = r.data_ptr()
+            else:
+                r = np.ascontiguousarray(r, dtype=np.float64)
+                rp = r.ctypes.data
+            keepalive += [kb, r]
+            bps.append(pb)
+            rps.append(rp)
+        bits, bp = _alloc_bits(n, mem, keep)
+        rt, rp_out = self._real_out(n, mem, keep) if rtilde else (None, None)
+        k = len(terms)
+        barr = (ctypes.c_void_p * max(k, 1))(*bps)
+        rarr = (ctypes.c_void_p * max(k, 1))(*rps)
+        st = Stats()
+        _check(lib().dl_tail_recursive_real(self._h, n, pb0, pa1, k, barr, rarr, mem, float(eps), PATHS[path],
+                                            bp, rp_out, ctypes.byref(st)))
+        return (bits, st.as_dict(), rt) if rtilde else (bits, st.as_dict())
+
+    def tail_system(self, eqs, path: str = "mixed", rtilde: bool = True):
+        """A layered tail recursive system (Sec. 6.1): eqs[h] = dict(A1=, B0=, terms=[(B, j)],
+        eps=) with j < h.  Returns (bits per equation, stats[, R~ per equation])."""
+        ref = next(x for eq in eqs for x in [eq.get("A1"), eq.get("B0")] + [b for b, _ in eq.get("terms", [])]
+                   if x is not None)
+        _, n, mem, keep = _square_u8(ref)
+        keepalive, structs = [], []
+        def held(x):
+            if x is None:
+                return None
+            p_, n_, mem_, k_ = _square_u8(x)
+            if n_ != n or mem_ != mem:
+                raise ValueError("every matrix must match in size and memory kind")
+            keepalive.append(k_)
+            return p_
+
+        for eq in eqs:
+            pa = held(eq.get("A1"))
+            pb = held(eq.get("B0"))
+            terms = eq.get("terms", [])
+            bptrs = (ctypes.c_void_p * max(len(terms), 1))(*[held(b) for b, _ in terms])
+            js = (ctypes.c_int32 * max(len(terms), 1))(*[int(j) for _, j in terms])
+            keepalive += [bptrs, js]
+            structs.append(TailEq(pa, pb, len(terms), ctypes.cast(bptrs, ctypes.POINTER(ctypes.c_void_p)),
+                                  ctypes.cast(js, ctypes.POINTER(ctypes.c_int32)), float(eq.get("eps", 0.0) or 0.0)))
+        m = len(eqs)
+        arr = (TailEq * m)(*structs)
+        outs = [_alloc_bits(n, mem, keep) for _ in range(m)]
+        obits = (ctypes.c_void_p * m)(*[p for _, p in outs])
+        rts = [self._real_out(n, mem, keep) for _ in range(m)] if rtilde else []
+        ort = (ctypes.c_void_p * m)(*[p for _, p in rts]) if rtilde else None
+        st = Stats()
+        _check(lib().dl_tail_system(self._h, n, m, arr, mem, PATHS[path], obits, ort, ctypes.byref(st)))
+        bits = [b for b, _ in outs]
+        return (bits, st.as_dict(), [r for r, _ in rts]) if rtilde else (bits, st.as_dict())
 
     def transposed(self, R1, eps: float = 0.0, path: str = "auto", rtilde: bool = False):
         """The transposed class, r2(x,z) <- r1(x,z); r2(x,z) <- r1(x,y), r2(z,y) (Sec. 6.2);
