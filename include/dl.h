@@ -294,6 +294,64 @@ DL_API dl_status dl_transposed(dl_ctx *ctx, int32_t n, const uint8_t *R1, dl_mem
 DL_API dl_status dl_compose(dl_ctx *ctx, int32_t n, const uint8_t *R1, const uint8_t *R2,
                      dl_mem mem, uint64_t *out_bits, dl_stats *stats);
 
+/* ---- linear programs (the class C_lin of Sec. 5) ---------------------------------- */
+
+/*
+ * A Datalog program over binary predicates, evaluated layer by layer (Sec. 5).
+ *
+ * Text: clauses  head(X,Y) :- atom, ..., atom.  Variables start with an upper-case letter or
+ * '_'; every predicate is binary; "not p(X,Y)" negates an atom; "%" starts a comment to the end
+ * of the line; there are no facts or constants in the text (base relations come in through
+ * dl_program_set).  The program must be in C_lin (Sec. 5):
+ *   - every body is a chain between the head's two (different) variables: its atoms link
+ *     X = x0, x1, ..., xk = Y in order, each atom in either argument order, no variable repeated;
+ *   - linear: no body holds two atoms whose predicates lie in the head's strongly connected
+ *     component of the dependency graph (Tarjan's algorithm);
+ *   - a negated atom names a predicate of a lower layer or a base relation (stratified
+ *     negation, Sec. 8: its matrix is 1 - R, over all n x n pairs).
+ * Otherwise DL_EINVAL, with the reason and the clause in dl_last_error().
+ *
+ * Evaluation (dl_program_run): the SCCs in topological order are the layers; in each, a chain
+ * is the FP8 tensor-core product of its atoms' matrices (transposed where an atom's arguments
+ * are reversed), and the layer's equations R_h = min1(A_h + sum_q B_q R_{j_q}^o C_q)
+ * (eq. matrixeq:gen0) go to the first solver that fits:
+ *   - no recursive atom: the union of the products;
+ *   - every recursive atom rightmost (C = I) and not reversed: the tail recursive class
+ *     (Sec. 6.1), one equation by dl_tail_recursive's boolean route, several mutually recursive
+ *     ones by the closure of their stacked system over m n constants;
+ *   - every recursive atom leftmost (B = I), not reversed: the same on the transposes;
+ *   - one predicate whose recursive atoms are all reversed with C = I (or all with B = I): the
+ *     transposed class (Sec. 6.2) by the two-sided reduction, on the same-generation solver;
+ *   - one predicate, one recursive clause B R B^T: the same-generation solver (Sec. 6.3, 7.2);
+ *   - anything else: the series of Lemma 3, R^(k+1) = min1(F[R^(k)]) from 0, on FP8 products
+ *     until it stops changing.
+ * Every route gives the least model (exact, 0/1).
+ */
+typedef struct dl_program dl_program;
+
+/* Parse and check `text` (a NUL-terminated string) into a program bound to ctx.  The context
+   must outlive the program. */
+DL_API dl_status dl_program_create(dl_ctx *ctx, const char *text, dl_program **out);
+/* Free a program (NULL is a no-op). */
+DL_API dl_status dl_program_destroy(dl_program *prog);
+/* Give base relation `pred` the n x n 0/1 matrix R (row-major bytes, in `mem`); the bytes are
+   copied.  Every base relation of a program must have the same n (n >= 0).  DL_EINVAL if pred
+   is not a base relation of the program or n differs from an earlier call's; a byte other than
+   0/1 is reported by dl_program_run. */
+DL_API dl_status dl_program_set(dl_program *prog, const char *pred, int32_t n, const uint8_t *R, dl_mem mem);
+/* Evaluate every layer; DL_EINVAL if a base relation is unset or holds a byte other than 0/1.
+   stats: iters = layers, gpu_launches / gemm_launches / ms_total summed over the solvers
+   (ms_total: device time of the solver calls). */
+DL_API dl_status dl_program_run(dl_program *prog, dl_stats *stats);
+/* The least model of defined predicate `pred` after dl_program_run: n * ceil(n/64) words,
+   row-major, bit (j mod 64) of word j / 64 of row i = [pred(i, j)], in `mem`. */
+DL_API dl_status dl_program_get(dl_program *prog, const char *pred, uint64_t *out_bits, dl_mem mem);
+/* A text account of the program: "base: ..." and "defined: ..." lines, one "layer k: ..." line
+   per layer in evaluation order, and after a run "plan:" with the route each layer took.  Writes
+   at most cap bytes (NUL-terminated when cap > 0) into buf (NULL allowed when cap is 0) and the
+   full length without the NUL into *len (if not NULL). */
+DL_API dl_status dl_program_describe(const dl_program *prog, char *buf, size_t cap, size_t *len);
+
 /*
  * Batch of independent transitive-closure problems of uneven size, each with the model
  * dl_tc_closure gives (eps <= 0, thr = 0; the program of Sec. 3).  ns[k], Es[k], out_bits[k]

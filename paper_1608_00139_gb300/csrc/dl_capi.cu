@@ -2,6 +2,7 @@
 // checks, context management, and dispatch to the drivers in dl_solve.cu / dl_serve.cu.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -364,6 +365,79 @@ dl_status dl_tail_system(dl_ctx *ctx, int32_t n, int32_t m, const dl_tail_eq *eq
     return run_sync(ctx, stats, [&](Workspace &ws, cudaStream_t s, dl_stats *st) {
         return solve_tail_system(ctx, ws, s, n, m, eqs, mem, path, out_bits, out_rtilde, st);
     });
+}
+
+dl_status dl_program_create(dl_ctx *ctx, const char *text, dl_program **out) {
+    clear_error();
+    GUARD_CTX(ctx);
+    if (!text || !out) {
+        set_error("text and out must not be NULL");
+        return DL_EINVAL;
+    }
+    *out = nullptr;
+    return program_create(ctx, text, out);
+}
+
+dl_status dl_program_destroy(dl_program *prog) {
+    clear_error();
+    if (!prog) return DL_OK;
+    dl_ctx *ctx = program_ctx(prog);
+    std::lock_guard<std::mutex> lk(ctx->mu);
+    if (set_device(ctx) == DL_OK) program_destroy(prog);
+    return DL_OK;
+}
+
+dl_status dl_program_set(dl_program *prog, const char *pred, int32_t n, const uint8_t *R, dl_mem mem) {
+    clear_error();
+    if (!prog || !pred || n < 0 || !valid_mem(mem) || (n > 0 && !R)) {
+        set_error("bad program, predicate, n (%d), matrix or memory kind", n);
+        return DL_EINVAL;
+    }
+    dl_ctx *ctx = program_ctx(prog);
+    return run_sync(ctx, nullptr, [&](Workspace &, cudaStream_t s, dl_stats *) {
+        return program_set(prog, s, pred, n, R, mem);
+    });
+}
+
+dl_status dl_program_run(dl_program *prog, dl_stats *stats) {
+    clear_error();
+    if (stats) std::memset(stats, 0, sizeof(*stats));
+    if (!prog) {
+        set_error("prog is NULL");
+        return DL_EINVAL;
+    }
+    dl_ctx *ctx = program_ctx(prog);
+    return run_sync(ctx, stats, [&](Workspace &ws, cudaStream_t s, dl_stats *st) {
+        return program_run(ctx, ws, s, prog, st);
+    });
+}
+
+dl_status dl_program_get(dl_program *prog, const char *pred, uint64_t *out_bits, dl_mem mem) {
+    clear_error();
+    if (!prog || !pred || !out_bits || !valid_mem(mem)) {
+        set_error("prog, pred and out_bits must not be NULL, mem must be a memory kind");
+        return DL_EINVAL;
+    }
+    dl_ctx *ctx = program_ctx(prog);
+    return run_sync(ctx, nullptr, [&](Workspace &ws, cudaStream_t s, dl_stats *) {
+        return program_get(prog, ws, s, pred, out_bits, mem);
+    });
+}
+
+dl_status dl_program_describe(const dl_program *prog, char *buf, size_t cap, size_t *len) {
+    clear_error();
+    if (!prog || (cap > 0 && !buf)) {
+        set_error("prog is NULL, or buf is NULL with cap > 0");
+        return DL_EINVAL;
+    }
+    const std::string d = program_describe(prog);
+    if (len) *len = d.size();
+    if (cap > 0) {
+        const size_t k = std::min(cap - 1, d.size());
+        std::memcpy(buf, d.data(), k);
+        buf[k] = 0;
+    }
+    return DL_OK;
 }
 
 dl_status dl_transposed(dl_ctx *ctx, int32_t n, const uint8_t *R1, dl_mem mem, double eps, double thr, dl_path path,

@@ -135,6 +135,15 @@ dl_status solve_tc_batch(dl_ctx *ctx, Workspace &ws, cudaStream_t s, int32_t cou
 // dmax = ||E||_inf (bounds the terms of the residual's sums).
 dl_status tc_mixed(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &a, dl_stats *st,
                    const uint8_t *E, double eps, unsigned long long dmax, int *launches_io);
+// The program front-end (dl_program.cu).
+dl_status program_create(dl_ctx *ctx, const char *text, dl_program **out);
+void program_destroy(dl_program *p);
+dl_status program_set(dl_program *p, cudaStream_t s, const char *pred, int32_t n, const uint8_t *R, dl_mem mem);
+dl_status program_run(dl_ctx *ctx, Workspace &ws, cudaStream_t s, dl_program *p, dl_stats *st);
+dl_status program_get(dl_program *p, Workspace &ws, cudaStream_t s, const char *pred, uint64_t *out_bits,
+                      dl_mem mem);
+std::string program_describe(const dl_program *p);
+dl_ctx *program_ctx(const dl_program *p);
 // Device bytes a request of this kind and size needs (serving admission).
 size_t footprint_bytes(int kind, int32_t n);
 

@@ -24,7 +24,9 @@ PATHS = {"auto": 0, "fp64": 1, "mixed": 2, "bool_fp8": 3, "fp8": 3}
 DL_MEM_HOST, DL_MEM_DEVICE = 0, 1
 
 EXPORTED = ["dl_create", "dl_destroy", "dl_last_error", "dl_set_stream", "dl_tc_closure", "dl_tc_closure_bits",
-            "dl_sg_least_model", "dl_sg_real", "dl_tail_recursive", "dl_tail_recursive_real", "dl_tail_system", "dl_transposed", "dl_compose", "dl_tc_batch", "dl_submit", "dl_poll", "dl_cancel",
+            "dl_sg_least_model", "dl_sg_real", "dl_tail_recursive", "dl_tail_recursive_real", "dl_tail_system", "dl_transposed", "dl_compose",
+            "dl_program_create", "dl_program_destroy", "dl_program_set", "dl_program_run", "dl_program_get",
+            "dl_program_describe", "dl_tc_batch", "dl_submit", "dl_poll", "dl_cancel",
             "dl_tc_closure_noalloc", "dl_selftest_wait_timeout"]
 NOALLOC_MAX_N = 2048
 
@@ -110,6 +112,12 @@ def lib() -> ctypes.CDLL:
             L.dl_tail_system.argtypes = [vp, i32, i32, vp, ctypes.c_int, ctypes.c_int, vp, vp,
                                          ctypes.POINTER(Stats)]
             L.dl_compose.argtypes = [vp, i32, vp, vp, ctypes.c_int, vp, ctypes.POINTER(Stats)]
+            L.dl_program_create.argtypes = [vp, ctypes.c_char_p, ctypes.POINTER(vp)]
+            L.dl_program_destroy.argtypes = [vp]
+            L.dl_program_set.argtypes = [vp, ctypes.c_char_p, i32, vp, ctypes.c_int]
+            L.dl_program_run.argtypes = [vp, ctypes.POINTER(Stats)]
+            L.dl_program_get.argtypes = [vp, ctypes.c_char_p, vp, ctypes.c_int]
+            L.dl_program_describe.argtypes = [vp, ctypes.c_char_p, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]
             L.dl_tc_batch.argtypes = [vp, i32, vp, vp, ctypes.c_int, vp, ctypes.POINTER(Stats)]
             L.dl_submit.argtypes = [vp, ctypes.POINTER(Request), ctypes.POINTER(ctypes.c_uint64)]
             L.dl_poll.argtypes = [vp, ctypes.c_uint64, i64, ctypes.POINTER(Stats)]
@@ -436,6 +444,10 @@ class Context:
         _check(lib().dl_sg_real(self._h, n, p, bptr, mem, float(eps), PATHS[path], xp, bp, ctypes.byref(st)))
         return x, out, st.as_dict()
 
+    def program(self, text: str) -> "Program":
+        """A linear Datalog program (the class C_lin of Sec. 5) bound to this context."""
+        return Program(self, text)
+
     def compose(self, R1, R2):
         """Bits of min1(R1 R2), the join of Sec. 2; returns (bits, stats)."""
         p1, n, mem, k1 = _square_u8(R1)
@@ -557,6 +569,87 @@ class Context:
     def selftest_wait_timeout(self, seconds: float) -> int:
         """Status of a deliberately unsatisfied bounded device wait (DL_ETIMEOUT expected)."""
         return lib().dl_selftest_wait_timeout(self._h, float(seconds))
+
+
+class Program:
+    """A program of dl_program_create: set its base relations, run it, read its models.
+
+    ``set(pred, R)``: R a square 0/1 uint8 numpy array or torch CUDA tensor.  ``get(pred,
+    device=False)``: the model's bits (n x ceil(n/64) words; a torch CUDA tensor with
+    device=True).  ``base`` / ``defined`` / ``layers`` / ``plan`` come from dl_program_describe."""
+
+    def __init__(self, ctx: Context, text: str):
+        h = ctypes.c_void_p()
+        _check(lib().dl_program_create(ctx._h, text.encode(), ctypes.byref(h)))
+        self._h = h
+        self._ctx = ctx  # the context must outlive the program
+        self.n = None
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            lib().dl_program_destroy(self._h)
+            self._h = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set(self, pred: str, R) -> None:
+        p, n, mem, keep = _square_u8(R)
+        _check(lib().dl_program_set(self._h, pred.encode(), n, p, mem))
+        self.n = n
+
+    def run(self) -> dict:
+        st = Stats()
+        _check(lib().dl_program_run(self._h, ctypes.byref(st)))
+        return st.as_dict()
+
+    def get(self, pred: str, device: bool = False):
+        n = self.n or 0
+        if device:
+            import torch
+            t = torch.empty((n, words(n)), dtype=torch.int64, device="cuda")
+            _check(lib().dl_program_get(self._h, pred.encode(), t.data_ptr(), DL_MEM_DEVICE))
+            return t
+        a = np.zeros((n, words(n)), dtype=np.uint64)
+        _check(lib().dl_program_get(self._h, pred.encode(), a.ctypes.data, DL_MEM_HOST))
+        return a
+
+    def describe(self) -> str:
+        need = ctypes.c_size_t()
+        _check(lib().dl_program_describe(self._h, None, 0, ctypes.byref(need)))
+        buf = ctypes.create_string_buffer(need.value + 1)
+        _check(lib().dl_program_describe(self._h, buf, need.value + 1, None))
+        return buf.value.decode()
+
+    def _lines(self, key):
+        return [ln[len(key) + 1:].split() for ln in self.describe().splitlines() if ln.startswith(key + ":")]
+
+    @property
+    def base(self) -> list:
+        return self._lines("base")[0]
+
+    @property
+    def defined(self) -> list:
+        return self._lines("defined")[0]
+
+    @property
+    def layers(self) -> list:
+        return [ln.split(":", 1)[1].split() for ln in self.describe().splitlines()
+                if ln.startswith("layer ") and ln.split(":", 1)[1].strip() and "{" not in ln]
+
+    @property
+    def plan(self) -> list:
+        text = self.describe()
+        return text.split("plan:\n", 1)[1].splitlines() if "plan:\n" in text else []
 
 
 def tc_closure_noalloc(E, stream=None):
