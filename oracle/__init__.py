@@ -79,9 +79,12 @@ def lib() -> ctypes.CDLL:
             L.oracle_tc_rtilde_series_col.argtypes = [ctypes.c_int32, u8p, ctypes.c_double,
                                                       ctypes.c_int32, f64p, ctypes.c_int32,
                                                       i32p]
+            L.oracle_tc_rtilde_series_row.argtypes = [ctypes.c_int32, u8p, ctypes.c_double,
+                                                      ctypes.c_int32, f64p, ctypes.c_int32,
+                                                      i32p]
             L.oracle_sg_seminaive.argtypes = [ctypes.c_int32, u8p, u8p, u64p, i32p]
             for f in ("oracle_tc_seminaive", "oracle_tc_naive", "oracle_tc_rtilde_lu",
-                      "oracle_tc_rtilde_series_col", "oracle_sg_seminaive"):
+                      "oracle_tc_rtilde_series_col", "oracle_tc_rtilde_series_row", "oracle_sg_seminaive"):
                 getattr(L, f).restype = ctypes.c_int
             _lib = L
     return _lib
@@ -171,6 +174,19 @@ def tc_rtilde_col(e: np.ndarray, eps: float, j: int, max_iter: int = 1_000_000,
     _check(lib().oracle_tc_rtilde_series_col(n, _ptr(e, ctypes.c_uint8), float(eps), int(j),
                                              _ptr(out, ctypes.c_double), int(max_iter),
                                              ctypes.byref(it)), "tc_rtilde_series_col")
+    return (out, it.value) if return_iters else out
+
+
+def tc_rtilde_row(e: np.ndarray, eps: float, i: int, max_iter: int = 1_000_000,
+                  return_iters: bool = False):
+    """Row i of R~ by the series of Lemma 1 read along rows, x <- eps (E_i + x E) (FP64)."""
+    e = _u8(e)
+    n = e.shape[0]
+    out = np.zeros(n, dtype=np.float64)
+    it = ctypes.c_int32(0)
+    _check(lib().oracle_tc_rtilde_series_row(n, _ptr(e, ctypes.c_uint8), float(eps), int(i),
+                                             _ptr(out, ctypes.c_double), int(max_iter),
+                                             ctypes.byref(it)), "tc_rtilde_series_row")
     return (out, it.value) if return_iters else out
 
 

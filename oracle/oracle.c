@@ -282,6 +282,57 @@ int oracle_tc_rtilde_series_col(int32_t n, const uint8_t *e, double eps, int32_t
 }
 
 /*
+ * Row i of R~ by the same series read along rows.  R~ = sum_{m >= 1} (eps E)^m, and the right
+ * form of the equation, R~ = eps E + eps R~ E, has the same partial sums as Lemma 1's series,
+ * so row i follows  x^(0) = 0,  x^(k+1) = eps (e_i^T E + x^(k) E):
+ *     x^(k+1)[j] = eps (E[i][j] + sum_{q : E[q][j]} x^(k)[q]).
+ * It increases monotonically to row i of (I - eps E)^-1 eps E.  Stops as the column series
+ * does (no component changed; -4 after max_iter updates).  xrow: n doubles (output).
+ */
+int oracle_tc_rtilde_series_row(int32_t n, const uint8_t *e, double eps, int32_t i,
+                                double *xrow, int32_t max_iter, int32_t *iters)
+{
+    if (n < 0 || (n > 0 && (!e || !xrow)) || i < 0 || (n > 0 && i >= n) || !(eps > 0.0))
+        return -1;
+    if (iters) *iters = 0;
+    if (n == 0) return 0;
+    /* predecessor lists: pred[pptr[j] .. pptr[j+1]) = {q : E[q][j]} */
+    int64_t *pptr = (int64_t *)calloc((size_t)n + 1, sizeof(int64_t));
+    if (!pptr) return -2;
+    for (int64_t q = 0; q < n; q++)
+        for (int64_t j = 0; j < n; j++)
+            if (e[q * n + j]) pptr[j + 1]++;
+    for (int64_t j = 0; j < n; j++) pptr[j + 1] += pptr[j];
+    int32_t *pred = (int32_t *)malloc(sizeof(int32_t) * (size_t)(pptr[n] > 0 ? pptr[n] : 1));
+    int64_t *fill = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
+    double *nx = (double *)malloc(sizeof(double) * (size_t)n);
+    if (!pred || !fill || !nx) { free(pptr); free(pred); free(fill); free(nx); return -2; }
+    for (int64_t j = 0; j < n; j++) fill[j] = pptr[j];
+    for (int64_t q = 0; q < n; q++)
+        for (int64_t j = 0; j < n; j++)
+            if (e[q * n + j]) pred[fill[j]++] = (int32_t)q;
+    for (int64_t j = 0; j < n; j++) xrow[j] = 0.0;
+    int rc = -4;
+    int32_t k;
+    for (k = 0; k < max_iter; k++) {
+        int changed = 0;
+#pragma omp parallel for schedule(static) reduction(| : changed)
+        for (int64_t j = 0; j < n; j++) {
+            double s = e[(int64_t)i * n + j] ? 1.0 : 0.0;
+            for (int64_t q = pptr[j]; q < pptr[j + 1]; q++) s += xrow[pred[q]];
+            double v = eps * s;
+            nx[j] = v;
+            changed |= (v != xrow[j]);
+        }
+        memcpy(xrow, nx, sizeof(double) * (size_t)n);
+        if (!changed) { rc = 0; k++; break; }
+    }
+    if (iters) *iters = k;
+    free(nx); free(fill); free(pred); free(pptr);
+    return rc;
+}
+
+/*
  * Least model of the same-generation program (Sec. 7.2, Fig. "Tested programs", right):
  *   sg(x,w) <- b(x,w);   sg(x,w) <- p(x,y), sg(y,z), p(w,z)
  * i.e. the least S with S = min1(B + P S P^T) (eq. matrixeq:two-sided:3 with B = I).

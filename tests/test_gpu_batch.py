@@ -64,9 +64,7 @@ def test_batch_config_1024_uneven(ctx):
     gs = [torch.from_numpy(inputs.er_digraph(n, p, s)).cuda() for n, p, s in specs]
     outs, st = ctx.tc_batch(gs)
     oracle.set_threads(0)
-    rng = np.random.default_rng(0)
-    check = set(rng.choice(1024, size=128, replace=False).tolist()) | {0, 1023}
-    for k in sorted(check):
+    for k in range(1024):  # every instance
         e = gs[k].cpu().numpy()
         assert np.array_equal(outs[k].cpu().numpy().view(np.uint64), oracle.tc_model(e)), k
 

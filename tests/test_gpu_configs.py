@@ -63,16 +63,24 @@ def test_config_sg4096(ctx):
 
 @pytest.mark.parametrize("p", [p for p, _ in BIG])
 def test_config_er8192_mixed(ctx, big_graphs, big_models, p):
-    """TF32 tensor-core LU + FP64 refinement at N = 8192: every model bit, and sampled
-    columns of R~ against the Lemma-1 series within 1e-10 of max |R~|."""
+    """TF32 tensor-core LU + FP64 refinement at N = 8192: every model bit, and 64 sampled
+    columns and 32 sampled rows of R~ against the Lemma-1 series (read along columns and along
+    rows) within 1e-10 of max |R~|."""
     e = big_graphs[p]
     bits, st, x = ctx.tc_closure(e, path="mixed", rtilde=True)
     assert np.array_equal(bits, big_models[p])
     eps = st["eps_used"]
+    assert eps == oracle.tc_eps(e)
     scale = np.abs(x).max()
-    for j in (0, 4095, 8191):
+    rng = np.random.default_rng(int(p * 1e4))
+    cols = sorted(set(rng.choice(8192, 62, replace=False).tolist()) | {0, 8191})
+    rows = sorted(set(rng.choice(8192, 30, replace=False).tolist()) | {0, 8191})
+    for j in cols:
         col = oracle.tc_rtilde_col(e, eps, j)
-        assert np.abs(x[:, j] - col).max() <= 1e-10 * scale
+        assert np.abs(x[:, j] - col).max() <= 1e-10 * scale, j
+    for i in rows:
+        row = oracle.tc_rtilde_row(e, eps, i)
+        assert np.abs(x[i, :] - row).max() <= 1e-10 * scale, i
 
 
 def test_config_er8192_closures_in_flight(big_graphs, big_models):

@@ -217,6 +217,42 @@ def test_series_column_path_closed_form():
     assert np.array_equal(col, want)
 
 
+def test_series_row_matches_lu_and_columns():
+    """Row i of R~ by the row-wise series against LU (Prop. 1) and against the column series at
+    the crossing entries; an asymmetric graph, so a transposed operand fails."""
+    e = inputs.er_digraph(150, 0.03, 62)
+    eps = oracle.tc_eps(e)
+    x = oracle.tc_rtilde_lu(e, eps)
+    assert not np.allclose(x, x.T)
+    for i in (0, 9, 63, 64, 149):
+        row, it = oracle.tc_rtilde_row(e, eps, i, return_iters=True)
+        assert it > 0
+        assert np.max(np.abs(row - x[i, :])) <= 1e-14 * max(1.0, np.abs(x).max())
+        for j in (1, 77):
+            assert abs(row[j] - oracle.tc_rtilde_col(e, eps, j)[i]) <= 1e-15
+
+
+def test_series_row_closed_forms():
+    # directed path 0 -> 1 -> ...: eps = 1/2 and R~[0][j] = 2^-j for j >= 1
+    n = 30
+    e = np.zeros((n, n), dtype=np.uint8)
+    e[np.arange(n - 1), np.arange(1, n)] = 1
+    row = oracle.tc_rtilde_row(e, 0.5, 0)
+    want = 2.0 ** (-np.arange(n).astype(float))
+    want[0] = 0.0
+    assert np.array_equal(row, want)
+    # directed L-cycle: R~[i][j] = eps^d(i,j) / (1 - eps^L), d in [1, L]
+    L = 7
+    c = np.zeros((L, L), dtype=np.uint8)
+    c[np.arange(L), (np.arange(L) + 1) % L] = 1
+    row = oracle.tc_rtilde_row(c, 0.5, 2)
+    d = (np.arange(L) - 2) % L
+    d[d == 0] = L
+    assert np.max(np.abs(row - 0.5 ** d / (1 - 0.5 ** L))) <= 1e-15
+    with pytest.raises(RuntimeError):
+        oracle.tc_rtilde_row(np.ones((4, 4), dtype=np.uint8), 0.2, 0, max_iter=3)
+
+
 def test_series_column_not_converged_reports():
     e = np.ones((4, 4), dtype=np.uint8)
     with pytest.raises(RuntimeError):
