@@ -345,57 +345,116 @@ def bench_batch(ctx, torch, reps: int = 10) -> dict:
             "inputs": "one resident device buffer (1.4 GB), one device output buffer"}
 
 
-def bench_serving(dl, torch, device: int, seconds: float) -> dict:
-    """Poisson stream (200 req/s), 80% closure / 20% same generation, PA-DAG inputs with N
-    log-uniform in [512, 16384] (a pool of 32 resident graphs, seed 6)."""
+def bench_serving(dl, torch, device: int, seconds: float, slots: int = 4) -> dict:
+    """The serving workload: a Poisson stream at 200 req/s for `seconds` (seed 6), 80% closure /
+    20% same generation, each request a fresh seeded preferential-attachment DAG (N log-uniform
+    in [512, 16384], the stream's own seed per request) generated ahead of its arrival into a
+    ring of pinned host buffers.  Inputs go in as host memory and models come back to pinned
+    host memory, so each latency holds the H2D copy of the input, the solve and the D2H copy of
+    the model.  Latency: dl_submit -> completion (the library's host clock) and arrival ->
+    completion (adds any lag of the submitting thread behind the arrival time)."""
+    import threading
     from concurrent.futures import ThreadPoolExecutor
 
     from paper_1608_00139_gb300 import inputs
-    sizes = np.unique(np.round(np.exp(np.linspace(np.log(512), np.log(16384), 32))).astype(int))
-    with ThreadPoolExecutor(max_workers=os.cpu_count() or 4) as ex:
-        pool_h = list(ex.map(lambda n: inputs.pa_dag(int(n), 6_000 + int(n)), sizes))
-    pool = [torch.from_numpy(e).cuda() for e in pool_h]
-    torch.cuda.synchronize()
-    times, kinds, ns, _ = inputs.poisson_stream(200.0, seconds, 6)
-    pick = np.searchsorted(sizes, ns).clip(0, len(sizes) - 1)
-    lat, queue, errors = [], [], 0
-    with dl.Context(device, max_slots=4) as c:
-        for k in (0, 1):  # warm both kernels outside the stream
-            t, _ = c.submit(k, pool[0])
+    times, kinds, ns, seeds = inputs.poisson_stream(200.0, seconds, 6)
+    count = len(times)
+    nmax, ring = 16384, 24
+    wmax = (nmax + 63) // 64
+    in_buf = [torch.empty(nmax * nmax, dtype=torch.uint8, pin_memory=True).numpy() for _ in range(ring)]
+    out_buf = [torch.empty(nmax * wmax, dtype=torch.int64, pin_memory=True).numpy().view(np.uint64)
+               for _ in range(ring)]
+    free = list(range(ring))
+    turn = [0]  # slots go to requests in arrival order, so the ring never holds a later request
+    cv = threading.Condition()  # while an earlier one waits (no deadlock with in-order submits)
+    inputs.pa_dag_into(np.empty((2, 2), np.uint8), 0)  # build / load the generator first
+
+    def take(r):
+        with cv:
+            while not free or turn[0] != r:
+                cv.wait()
+            turn[0] += 1
+            cv.notify_all()
+            return free.pop()
+
+    def give(slot):
+        with cv:
+            free.append(slot)
+            cv.notify_all()
+
+    def make(r):  # generate request r into a ring slot (ahead of its arrival)
+        slot = take(r)
+        n = int(ns[r])
+        inputs.pa_dag_into(in_buf[slot][:n * n].reshape(n, n), int(seeds[r]))
+        return slot
+
+    gen = ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 4))
+    lat, lat_arr, queue, spans, errors, lag = [], [], [], [], 0, []
+    with dl.Context(device, max_slots=slots) as c:
+        warm = inputs.pa_dag(512, 1)
+        for k in (0, 1):  # load both kinds' kernels outside the stream
+            t, _ = c.submit(k, warm)
             c.poll(t, -1)
-        outstanding = []
-        t0 = time.perf_counter()
-        for t_arr, kind, j in zip(times, kinds, pick):
-            while True:
-                now = time.perf_counter() - t0
-                if now >= t_arr:
-                    break
-                keep = []
-                for tk in outstanding:
-                    rc, st = c.poll(tk, 0)
-                    if rc == dl.DL_OK:
-                        lat.append(st["ms_latency"])
-                        queue.append(st["ms_queue"])
-                    else:
-                        keep.append(tk)
-                outstanding = keep
-                time.sleep(min(0.0005, max(0.0, t_arr - now)))
-            tk, _ = c.submit(int(kind), pool[j])
-            outstanding.append(tk)
-        for tk in outstanding:
-            try:
-                rc, st = c.poll(tk, -1)
+        futs = [gen.submit(make, r) for r in range(count)]  # the ring bounds how far ahead
+        outstanding = {}  # ticket -> (slot, handle, request, submit time)
+
+        def reap(block: bool):
+            nonlocal errors
+            done = []
+            for tk, (slot, h, r, ts) in outstanding.items():
+                try:
+                    rc, st = c.poll(tk, -1 if block else 0)
+                except dl.DLError:
+                    errors += 1
+                    done.append(tk)
+                    give(slot)
+                    continue
+                if rc != dl.DL_OK:
+                    continue
                 lat.append(st["ms_latency"])
                 queue.append(st["ms_queue"])
-            except dl.DLError:
-                errors += 1
+                lat_arr.append(st["ms_latency"] + (ts - times[r]) * 1e3)
+                spans.append((ts + st["ms_queue"] * 1e-3, ts + st["ms_latency"] * 1e-3))
+                done.append(tk)
+                give(slot)
+            for tk in done:
+                outstanding.pop(tk)
+
+        t0 = time.perf_counter()
+        for r in range(count):
+            # completions free ring slots, so keep reaping while request r is generated or early
+            while not futs[r].done() or time.perf_counter() - t0 < times[r]:
+                reap(False)
+                time.sleep(min(0.0005, max(0.0002, times[r] - (time.perf_counter() - t0))))
+            slot = futs[r].result()
+            n = int(ns[r])
+            ts = time.perf_counter() - t0
+            lag.append(ts - times[r])
+            tk, h = c.submit(int(kinds[r]), in_buf[slot][:n * n].reshape(n, n),
+                             out=out_buf[slot][:n * ((n + 63) // 64)].reshape(n, (n + 63) // 64))
+            outstanding[tk] = (slot, h, r, ts)
+        while outstanding:
+            reap(True)
         wall = time.perf_counter() - t0
-    lat_a = np.array(lat)
-    return {"workload": f"Poisson 200 req/s for {seconds:g} s, 80% TC / 20% SG, PA DAGs N in [512,16384]",
-            "requests": int(len(times)), "completed": int(len(lat)), "errors": errors,
+    gen.shutdown()
+    # admitted concurrency: requests between admission and completion at the same time
+    ev = sorted([(a, 1) for a, _ in spans] + [(b, -1) for _, b in spans])
+    cur, peak, area = 0, 0, 0.0
+    for (t_a, d), (t_b, _) in zip(ev, ev[1:] + [(ev[-1][0], 0)]):
+        cur += d
+        peak = max(peak, cur)
+        area += cur * (t_b - t_a)
+    lat_a, arr_a = np.array(lat), np.array(lat_arr)
+    return {"workload": f"Poisson 200 req/s for {seconds:g} s (seed 6), 80% TC / 20% SG, a fresh seeded "
+                        f"PA DAG per request, N log-uniform in [512,16384]",
+            "inputs": "host (pinned) input and output per request: H2D and D2H inside each latency",
+            "requests": int(count), "completed": int(len(lat)), "errors": errors,
             "p50_ms": float(np.percentile(lat_a, 50)), "p99_ms": float(np.percentile(lat_a, 99)),
+            "p50_arrival_ms": float(np.percentile(arr_a, 50)), "p99_arrival_ms": float(np.percentile(arr_a, 99)),
             "p50_queue_ms": float(np.percentile(np.array(queue), 50)),
-            "solves_per_s": len(lat) / wall, "slots": 4}
+            "max_submit_lag_ms": float(max(lag) * 1e3), "solves_per_s": len(lat) / wall,
+            "slots": slots, "admitted_concurrency": {"peak": peak, "mean": area / max(wall, 1e-9)},
+            "mean_n": float(ns.mean()), "h2d_bytes": int((ns.astype(np.int64) ** 2).sum())}
 
 
 def cpu_baseline(gs, budget_s: float = 30.0) -> dict:
@@ -413,6 +472,80 @@ def cpu_baseline(gs, budget_s: float = 30.0) -> dict:
             "kind": "oracle",
             "sample": f"{done} of the 3 N=8192 graphs (one full step), semi-naive evaluation, "
                       f"{dt:.2f} s"}
+
+
+def cpu_rows() -> dict:
+    """The oracle timed on the other configured workloads, on this host's cores (bounded: about
+    30 s in all).  Each entry states its sample, its thread count and its rate."""
+    import oracle
+    from paper_1608_00139_gb300 import inputs
+    allc = oracle.set_threads(os.cpu_count() or 1)
+    out = {"host_cores": os.cpu_count(), "cpu": _cpu_model()}
+
+    def timed(f, *a):
+        t0 = time.perf_counter()
+        f(*a)
+        return time.perf_counter() - t0
+
+    # C1: the plain FP64 direct solve (Prop. 1, unpivoted LU + n right-hand sides), all cores
+    e1 = inputs.er_digraph(256, 0.02, 1)
+    dt = timed(oracle.tc_rtilde_lu, e1, oracle.tc_eps(e1))
+    out["fp64_lu_er256"] = {"ms": dt * 1e3, "tflops_equiv": flops_equiv(256) / dt / 1e12, "threads": allc,
+                            "sample": "the whole N = 256 workload (ER p = 0.02, seed 1)"}
+    # C2: the FP64 solve on a bounded sample (N = 2048 at the p = 1e-3 graph's mean degree; the
+    # N = 8192 solve is 64 times this work), and the semi-naive model single-threaded per graph
+    e2 = inputs.er_digraph(2048, 8.2 / 2047, 3)
+    dt = timed(oracle.tc_rtilde_lu, e2, oracle.tc_eps(e2))
+    out["fp64_lu_er8192_sample"] = {"ms": dt * 1e3, "tflops_equiv": flops_equiv(2048) / dt / 1e12,
+                                    "ms_n8192_estimate": dt * 64e3, "threads": allc,
+                                    "sample": "LU solve at N = 2048, mean degree 8.2 (1/64 of the N = 8192 work)"}
+    oracle.set_threads(1)
+    one = {}
+    for p, sd in zip(PS, SEEDS):
+        one[f"p={p:g}"] = timed(oracle.tc_model, inputs.er_digraph(N, p, sd)) * 1e3
+    out["seminaive_er8192_1thread"] = {"ms": one, "threads": 1,
+                                       "tflops_equiv": 3 * flops_equiv(N) / (sum(one.values()) * 1e-3) / 1e12,
+                                       "sample": "the three N = 8192 graphs, one thread"}
+    oracle.set_threads(allc)
+    # C3: same generation, semi-naive, the whole N = 4096 forest workload
+    p3 = inputs.forest_dag(4096, 5)
+    dt = timed(oracle.sg_model, p3)
+    out["sg_seminaive_forest4096"] = {"ms": dt * 1e3, "threads": allc, "sample": "the whole workload"}
+    # C4: the oracle over every instance of the uneven batch (summed)
+    specs = inputs.batch_specs(1024, 1000)
+    gs4 = [inputs.er_digraph(n, p, sd) for n, p, sd in specs]
+    dt = timed(lambda: [oracle.tc_model(g) for g in gs4])
+    out["batch_1024_summed"] = {"ms": dt * 1e3, "threads": allc,
+                                "tflops_equiv": sum(flops_equiv(n) for n, _, _ in specs) / dt / 1e12,
+                                "sample": "all 1024 instances, one after another"}
+    # C5: the first 100 requests of the seeded serving stream, solved one after another
+    _, kinds, ns, seeds = inputs.poisson_stream(200.0, 60.0, 6)
+    t_tc = t_sg = 0.0
+    k_tc = k_sg = 0
+    for r in range(100):
+        g = inputs.pa_dag_into(np.empty((int(ns[r]), int(ns[r])), np.uint8), int(seeds[r]))
+        if kinds[r] == 0:
+            t_tc += timed(oracle.tc_model, g)
+            k_tc += 1
+        else:
+            t_sg += timed(oracle.sg_model, g)
+            k_sg += 1
+    out["serving_sample"] = {"solves_per_s": 100 / (t_tc + t_sg), "tc_ms_mean": t_tc / max(k_tc, 1) * 1e3,
+                             "sg_ms_mean": t_sg / max(k_sg, 1) * 1e3, "threads": allc,
+                             "sample": f"the first 100 requests of the seeded 200 req/s stream ({k_tc} TC, {k_sg} SG; "
+                                       f"mean N {float(ns[:100].mean()):.0f}), generation excluded"}
+    return out
+
+
+def _cpu_model() -> str:
+    try:
+        with open("/proc/cpuinfo") as f:
+            for ln in f:
+                if ln.lower().startswith(("model name", "cpu part", "hardware")):
+                    return ln.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
 
 
 def run_reference(args, rank: int, world: int) -> None:
@@ -502,8 +635,8 @@ def main() -> None:
                     help="skip the leg that rotates seeded graphs across solves")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the same-generation, batch and serving measurements")
-    ap.add_argument("--serve-seconds", type=float, default=10.0,
-                    help="length of the serving stream (the full workload is 60 s)")
+    ap.add_argument("--serve-seconds", type=float, default=60.0,
+                    help="length of the serving stream (the configured workload is 60 s)")
     ap.add_argument("--part", default="all", choices=["all", "sg", "sg_real", "tail", "trans", "batch", "serving", "mixed", "bool"],
                     help="run one secondary measurement alone and print its JSON (for profiling)")
     args = ap.parse_args()
@@ -750,6 +883,7 @@ def main() -> None:
         line["speedup_vs_fp64"] = fp64["ms"] / (ms_step / len(gs))
     if rank == 0 and world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(gs)
+        line["cpu_rows"] = cpu_rows()
         if "sg_real" in line:
             line["sg_real"]["cpu_oracle"] = cpu_sg_real()
         if "tail_recursive" in line:

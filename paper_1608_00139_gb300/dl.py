@@ -535,17 +535,25 @@ class Context:
         return out[:total], out_offsets, st.as_dict()
 
     # ---- serving -------------------------------------------------------------------
-    def submit(self, kind: int, base, B=None, path: str = "auto"):
+    def submit(self, kind: int, base, B=None, path: str = "auto", out=None):
         """Queue a request (0 = closure, 1 = same generation); returns (ticket, handle).
 
         Keep ``handle`` alive until :meth:`poll` has returned for the ticket: it owns the
-        input and output buffers.  ``handle['bits']`` is the output.
+        input and output buffers.  ``handle['bits']`` is the output: ``out`` if given (same
+        memory kind as ``base``, n x ceil(n/64) 64-bit words with contiguous rows, e.g. a view of
+        a pinned buffer), else a new array.
         """
         p, n, mem, keep = _square_u8(base)
         bptr, keepb = None, None
         if B is not None:
             bptr, _, _, keepb = _square_u8(B)
-        bits, bp = _alloc_bits(n, mem, keep)
+        if out is None:
+            bits, bp = _alloc_bits(n, mem, keep)
+        else:
+            if tuple(out.shape) != (n, words(n)):
+                raise ValueError("out must have shape (n, ceil(n/64))")
+            bits = out
+            bp = out.data_ptr() if _is_torch(out) else out.ctypes.data
         req = Request(int(kind), n, p, bptr, mem, PATHS[path], bp)
         t = ctypes.c_uint64(0)
         _check(lib().dl_submit(self._h, ctypes.byref(req), ctypes.byref(t)))

@@ -24,8 +24,11 @@ Workloads (the paper's experiments, Sec. 7):
 """
 from __future__ import annotations
 
+import ctypes
 import math
 import os
+import subprocess
+import threading
 from concurrent.futures import ThreadPoolExecutor
 
 import numpy as np
@@ -228,6 +231,58 @@ def pa_dag(n: int, seed: int, zipf_a: float = 2.1, mean_deg: float = 5.0) -> np.
         urn.extend(chosen)
         urn.append(i)
     return e
+
+
+_ZIPF_CDF: dict = {}
+_NATIVE = None
+_NATIVE_LOCK = threading.Lock()
+_HERE = os.path.dirname(os.path.abspath(__file__))
+
+
+def _zipf_cdf(zipf_a: float, mean_deg: float) -> np.ndarray:
+    """The CDF pa_dag draws out-degrees from (cached per exponent and mean)."""
+    key = (float(zipf_a), float(mean_deg))
+    if key not in _ZIPF_CDF:
+        kmax = zipf_cutoff(zipf_a, mean_deg)
+        ks = np.arange(1, kmax + 1, dtype=np.float64)
+        cdf = np.cumsum(ks ** (-zipf_a))
+        cdf /= cdf[-1]
+        _ZIPF_CDF[key] = cdf
+    return _ZIPF_CDF[key]
+
+
+def _native():
+    """libinputs.so (inputs_native.c, compiled with gcc next to this file when stale)."""
+    global _NATIVE
+    with _NATIVE_LOCK:
+        if _NATIVE is None:
+            src = os.path.join(_HERE, "inputs_native.c")
+            lib = os.path.join(_HERE, "libinputs.so")
+            if not os.path.exists(lib) or os.path.getmtime(lib) < os.path.getmtime(src):
+                tmp = f"{lib}.tmp{os.getpid()}"
+                subprocess.run(["gcc", "-O2", "-shared", "-fPIC", "-o", tmp, src], check=True)
+                os.replace(tmp, lib)
+            L = ctypes.CDLL(lib)
+            L.inputs_pa_dag.argtypes = [ctypes.c_int32, ctypes.c_uint64, ctypes.c_void_p, ctypes.c_int64,
+                                        ctypes.c_void_p, ctypes.c_int64]
+            L.inputs_pa_dag.restype = ctypes.c_int
+            _NATIVE = L
+    return _NATIVE
+
+
+def pa_dag_into(out: np.ndarray, seed: int, zipf_a: float = 2.1, mean_deg: float = 5.0) -> np.ndarray:
+    """The matrix of :func:`pa_dag` (n = out.shape[0], same seed) written into ``out`` by the C
+    twin of the generator (the same draws in the same order); ``out`` is an n x n uint8 array
+    whose rows may be strided (e.g. a view of a larger pinned buffer).  Returns ``out``."""
+    n = int(out.shape[0])
+    if out.dtype != np.uint8 or out.ndim != 2 or out.shape[1] != n or (n > 1 and out.strides[1] != 1):
+        raise ValueError("out must be an n x n uint8 array with contiguous rows")
+    cdf = _zipf_cdf(zipf_a, mean_deg)
+    key = stream_key(seed, STREAM_PA)
+    rc = _native().inputs_pa_dag(n, int(key), cdf.ctypes.data, len(cdf), out.ctypes.data, max(out.strides[0], n))
+    if rc != 0:
+        raise RuntimeError(f"inputs_pa_dag failed ({rc})")
+    return out
 
 
 def batch_specs(count: int = 1024, seed0: int = 1000, n_lo: int = 32, n_hi: int = 2048,

@@ -40,6 +40,17 @@ def test_pa_dag_shape():
     assert np.array_equal(e, inputs.pa_dag(2000, 3))
 
 
+def test_native_pa_dag_equals_the_python_generator():
+    for n, seed in [(0, 1), (1, 1), (2, 5), (37, 2), (700, 3), (2500, 9)]:
+        want = inputs.pa_dag(n, seed)
+        got = inputs.pa_dag_into(np.full((n, n), 7, np.uint8), seed)
+        assert np.array_equal(got, want), (n, seed)
+    # into a row-strided view of a larger buffer
+    buf = np.full((300, 512), 9, np.uint8)
+    view = inputs.pa_dag_into(buf[:300, :300], 4)
+    assert np.array_equal(view, inputs.pa_dag(300, 4)) and (buf[:, 300:] == 9).all()
+
+
 def test_batch_and_stream_specs():
     specs = inputs.batch_specs(64)
     assert all(32 <= n <= 2048 and 0 < p <= 8.0 / 31 for n, p, _ in specs)
