@@ -89,8 +89,10 @@ dl_status run_sync(dl_ctx *ctx, dl_stats *stats, F &&f) {
     dl_stats local{};
     rc = f(ctx->ws, ctx->stream, stats ? stats : &local);
     if (rc != DL_OK) {
-        // leave the stream idle and usable after a failure
+        // leave the streams idle and usable after a failure (the mixed path's two as well)
         cudaStreamSynchronize(ctx->stream);
+        for (cudaStream_t x : ctx->ws.mx_stream)
+            if (x) cudaStreamSynchronize(x);
         cudaGetLastError();
     }
     return rc;
@@ -102,6 +104,7 @@ extern "C" {
 
 dl_status dl_create(dl_ctx **out, int device, const dl_config *cfg) {
     clear_error();
+    Range trace_(__func__);
     if (!out) {
         set_error("out is NULL");
         return DL_EINVAL;
@@ -152,6 +155,7 @@ dl_status dl_create(dl_ctx **out, int device, const dl_config *cfg) {
 
 dl_status dl_destroy(dl_ctx *ctx) {
     clear_error();
+    Range trace_(__func__);
     if (!ctx) return DL_OK;
     dl_serve_shutdown(ctx);
     {
@@ -169,6 +173,7 @@ const char *dl_last_error(void) { return last_error(); }
 
 dl_status dl_set_stream(dl_ctx *ctx, void *stream) {
     clear_error();
+    Range trace_(__func__);
     GUARD_CTX(ctx);
     std::lock_guard<std::mutex> lk(ctx->mu);
     ctx->stream = stream ? static_cast<cudaStream_t>(stream) : ctx->own_stream;
@@ -179,6 +184,7 @@ dl_status dl_tc_closure(dl_ctx *ctx, int32_t n, const uint8_t *E, dl_mem mem, do
                         double thr, dl_path path, uint64_t *out_bits, double *out_rtilde,
                         dl_stats *stats) {
     clear_error();
+    Range trace_(__func__);
     GUARD_CTX(ctx);
     if (stats) std::memset(stats, 0, sizeof(*stats));
     if (n < 0 || !valid_mem(mem)) {
@@ -208,6 +214,7 @@ dl_status dl_tc_closure_bits(dl_ctx *ctx, int32_t n, const uint64_t *E_bits, dl_
                              double thr, dl_path path, uint64_t *out_bits, double *out_rtilde,
                              dl_stats *stats) {
     clear_error();
+    Range trace_(__func__);
     GUARD_CTX(ctx);
     if (stats) std::memset(stats, 0, sizeof(*stats));
     if (n < 0 || !valid_mem(mem)) {
@@ -237,6 +244,7 @@ dl_status dl_sg_least_model(dl_ctx *ctx, int32_t n, const uint8_t *P, const uint
                             dl_mem mem, double eps, double thr, dl_path path,
                             uint64_t *out_bits, dl_stats *stats) {
     clear_error();
+    Range trace_(__func__);
     GUARD_CTX(ctx);
     if (stats) std::memset(stats, 0, sizeof(*stats));
     if (n < 0 || !valid_mem(mem)) {
@@ -265,6 +273,7 @@ dl_status dl_sg_least_model(dl_ctx *ctx, int32_t n, const uint8_t *P, const uint
 dl_status dl_tail_recursive(dl_ctx *ctx, int32_t n, const uint8_t *B0, const uint8_t *A, dl_mem mem, double eps,
                             double thr, dl_path path, uint64_t *out_bits, double *out_rtilde, dl_stats *stats) {
     clear_error();
+    Range trace_(__func__);
     GUARD_CTX(ctx);
     if (stats) std::memset(stats, 0, sizeof(*stats));
     if (n < 0 || !valid_mem(mem)) {
@@ -295,6 +304,7 @@ dl_status dl_tail_recursive_real(dl_ctx *ctx, int32_t n, const uint8_t *B0, cons
                                  const uint8_t *const *B, const double *const *R, dl_mem mem, double eps, dl_path path,
                                  uint64_t *out_bits, double *out_rtilde, dl_stats *stats) {
     clear_error();
+    Range trace_(__func__);
     GUARD_CTX(ctx);
     if (stats) std::memset(stats, 0, sizeof(*stats));
     if (n < 0 || nterms < 0 || !valid_mem(mem)) {
@@ -351,6 +361,7 @@ dl_status dl_tail_recursive_real(dl_ctx *ctx, int32_t n, const uint8_t *B0, cons
 dl_status dl_tail_system(dl_ctx *ctx, int32_t n, int32_t m, const dl_tail_eq *eqs, dl_mem mem, dl_path path,
                          uint64_t *const *out_bits, double *const *out_rtilde, dl_stats *stats) {
     clear_error();
+    Range trace_(__func__);
     GUARD_CTX(ctx);
     if (stats) std::memset(stats, 0, sizeof(*stats));
     if (n < 0 || m < 0 || !valid_mem(mem)) {
@@ -369,6 +380,7 @@ dl_status dl_tail_system(dl_ctx *ctx, int32_t n, int32_t m, const dl_tail_eq *eq
 
 dl_status dl_program_create(dl_ctx *ctx, const char *text, dl_program **out) {
     clear_error();
+    Range trace_(__func__);
     GUARD_CTX(ctx);
     if (!text || !out) {
         set_error("text and out must not be NULL");
@@ -380,6 +392,7 @@ dl_status dl_program_create(dl_ctx *ctx, const char *text, dl_program **out) {
 
 dl_status dl_program_destroy(dl_program *prog) {
     clear_error();
+    Range trace_(__func__);
     if (!prog) return DL_OK;
     dl_ctx *ctx = program_ctx(prog);
     std::lock_guard<std::mutex> lk(ctx->mu);
@@ -389,6 +402,7 @@ dl_status dl_program_destroy(dl_program *prog) {
 
 dl_status dl_program_set(dl_program *prog, const char *pred, int32_t n, const uint8_t *R, dl_mem mem) {
     clear_error();
+    Range trace_(__func__);
     if (!prog || !pred || n < 0 || !valid_mem(mem) || (n > 0 && !R)) {
         set_error("bad program, predicate, n (%d), matrix or memory kind", n);
         return DL_EINVAL;
@@ -401,6 +415,7 @@ dl_status dl_program_set(dl_program *prog, const char *pred, int32_t n, const ui
 
 dl_status dl_program_run(dl_program *prog, dl_stats *stats) {
     clear_error();
+    Range trace_(__func__);
     if (stats) std::memset(stats, 0, sizeof(*stats));
     if (!prog) {
         set_error("prog is NULL");
@@ -414,6 +429,7 @@ dl_status dl_program_run(dl_program *prog, dl_stats *stats) {
 
 dl_status dl_program_get(dl_program *prog, const char *pred, uint64_t *out_bits, dl_mem mem) {
     clear_error();
+    Range trace_(__func__);
     if (!prog || !pred || !out_bits || !valid_mem(mem)) {
         set_error("prog, pred and out_bits must not be NULL, mem must be a memory kind");
         return DL_EINVAL;
@@ -426,6 +442,7 @@ dl_status dl_program_get(dl_program *prog, const char *pred, uint64_t *out_bits,
 
 dl_status dl_program_describe(const dl_program *prog, char *buf, size_t cap, size_t *len) {
     clear_error();
+    Range trace_(__func__);
     if (!prog || (cap > 0 && !buf)) {
         set_error("prog is NULL, or buf is NULL with cap > 0");
         return DL_EINVAL;
@@ -443,6 +460,7 @@ dl_status dl_program_describe(const dl_program *prog, char *buf, size_t cap, siz
 dl_status dl_transposed(dl_ctx *ctx, int32_t n, const uint8_t *R1, dl_mem mem, double eps, double thr, dl_path path,
                         uint64_t *out_bits, double *out_rtilde, dl_stats *stats) {
     clear_error();
+    Range trace_(__func__);
     GUARD_CTX(ctx);
     if (stats) std::memset(stats, 0, sizeof(*stats));
     if (n < 0 || !valid_mem(mem)) {
@@ -471,6 +489,7 @@ dl_status dl_transposed(dl_ctx *ctx, int32_t n, const uint8_t *R1, dl_mem mem, d
 dl_status dl_sg_real(dl_ctx *ctx, int32_t n, const uint8_t *P, const uint8_t *B, dl_mem mem, double eps,
                      dl_path path, double *out_stilde, uint64_t *out_bits, dl_stats *stats) {
     clear_error();
+    Range trace_(__func__);
     GUARD_CTX(ctx);
     if (stats) std::memset(stats, 0, sizeof(*stats));
     if (n < 0 || !valid_mem(mem)) {
@@ -499,6 +518,7 @@ dl_status dl_sg_real(dl_ctx *ctx, int32_t n, const uint8_t *P, const uint8_t *B,
 dl_status dl_compose(dl_ctx *ctx, int32_t n, const uint8_t *R1, const uint8_t *R2, dl_mem mem,
                      uint64_t *out_bits, dl_stats *stats) {
     clear_error();
+    Range trace_(__func__);
     GUARD_CTX(ctx);
     if (stats) std::memset(stats, 0, sizeof(*stats));
     if (n < 0 || !valid_mem(mem)) {
@@ -523,6 +543,7 @@ dl_status dl_compose(dl_ctx *ctx, int32_t n, const uint8_t *R1, const uint8_t *R
 
 dl_status dl_selftest_wait_timeout(dl_ctx *ctx, double seconds) {
     clear_error();
+    Range trace_(__func__);
     GUARD_CTX(ctx);
     if (!(seconds > 0.0 && seconds <= 10.0)) {
         set_error("seconds must be in (0, 10]");
@@ -551,6 +572,7 @@ dl_status dl_selftest_wait_timeout(dl_ctx *ctx, double seconds) {
 dl_status dl_tc_batch(dl_ctx *ctx, int32_t count, const int32_t *ns, const uint8_t *const *Es,
                       dl_mem mem, uint64_t *const *out_bits, dl_stats *stats) {
     clear_error();
+    Range trace_(__func__);
     GUARD_CTX(ctx);
     if (stats) std::memset(stats, 0, sizeof(*stats));
     if (count < 0 || !valid_mem(mem)) {

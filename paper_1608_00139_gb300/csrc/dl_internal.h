@@ -2,11 +2,25 @@
 #pragma once
 #include <cuda.h>
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <cstdint>
 #include <string>
 
 namespace dl {
+
+// Every allocation of the library goes through these (dl_debug.cu): cudaMalloc / cudaMallocHost,
+// or cudaErrorMemoryAllocation when the DL_FAULT plan says this allocation fails.
+cudaError_t device_alloc(void **ptr, size_t bytes);
+cudaError_t host_pinned_alloc(void **ptr, size_t bytes);
+
+// An NVTX range for the lifetime of the object (a no-op unless a profiler is attached).
+struct Range {
+    explicit Range(const char *name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+    Range(const Range &) = delete;
+    Range &operator=(const Range &) = delete;
+};
 
 // Device status word bits (the host reads the word after a call).
 enum : int {

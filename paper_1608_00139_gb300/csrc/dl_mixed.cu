@@ -630,6 +630,19 @@ dl_status mixed_streams(Workspace &ws) {
 
 }  // namespace
 
+// Consecutive NVTX ranges, one open at a time.
+struct Phases {
+    bool open = false;
+    void to(const char *name) {
+        if (open) nvtxRangePop();
+        nvtxRangePushA(name);
+        open = true;
+    }
+    ~Phases() {
+        if (open) nvtxRangePop();
+    }
+};
+
 dl_status tc_mixed(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &a, dl_stats *st,
                    const uint8_t *E, double eps, unsigned long long dmax, int *launches_io) {
     const int32_t n = a.n;
@@ -664,6 +677,8 @@ dl_status tc_mixed(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &
     }
     float *R32 = W32;  // the residual reuses Z's buffer once W = Z^T is formed
     cudaEvent_t *ev = ws.ev;
+    Phases ph;  // NVTX ranges of the host-side phases
+    ph.to("mixed:set-up");
     MCK(cudaEventRecord(ev[4], s));
     {
         dim3 grid(static_cast<unsigned>(std::min<int64_t>((np + 255) / 256, 64)), static_cast<unsigned>(np));
@@ -809,6 +824,7 @@ dl_status tc_mixed(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &
     const int sms = ctx->sms;
 
     // ---- LU with look-ahead --------------------------------------------------------------
+    ph.to("mixed:lu");
     MCK(cudaEventRecord(ws.mx_ev[0], s));  // the table and A are ready on s
     MCK(cudaStreamWaitEvent(P, ws.mx_ev[0], 0));
     MCK(cudaStreamWaitEvent(U, ws.mx_ev[0], 0));
@@ -848,6 +864,7 @@ dl_status tc_mixed(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &
     MCK(cudaStreamWaitEvent(s, ws.mx_ev[1], 0));
 
     // group inverses: Y = I on each group's rows, the grouped steps, then G = Y^T per group
+    ph.to("mixed:group-inverses");
     MCK(cudaMemsetAsync(YL, 0, np * GW * 4, s));
     MCK(cudaMemsetAsync(YU, 0, np * GW * 4, s));
     group_identity_kernel<<<static_cast<unsigned>((np + 255) / 256), 256, 0, s>>>(YL, YU, N, static_cast<int>(GW));
@@ -863,6 +880,7 @@ dl_status tc_mixed(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &
     MCK(cudaEventRecord(ev[5], s));
 
     // ---- W = A^-1 ------------------------------------------------------------------------
+    ph.to("mixed:inverse");
     MCK(cudaMemsetAsync(W32, 0, np * np * 4, s));
     identity_kernel<<<static_cast<unsigned>((np + 255) / 256), 256, 0, s>>>(W32, N);
     MCK(cudaGetLastError());
@@ -884,6 +902,7 @@ dl_status tc_mixed(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &
     MCK(cudaEventRecord(ev[6], s));
 
     // ---- refinement from Z = 0 -------------------------------------------------------------
+    ph.to("mixed:refine");
     const double tol = ctx->cfg.refine_tol > 0 ? ctx->cfg.refine_tol : 1e-13;
     const int max_iters = ctx->cfg.refine_max_iters > 0 ? ctx->cfg.refine_max_iters : 30;
     int deg_bits = 0;  // 2^deg_bits >= ||E||_inf + 1 (the terms of one sum, the +1 or A[i][j] included)

@@ -318,7 +318,7 @@ struct Pool {
     }
     uint8_t *alloc(size_t bytes) {
         void *p = nullptr;
-        if (cudaMalloc(&p, std::max<size_t>(bytes, 16)) != cudaSuccess) return nullptr;
+        if (device_alloc(&p, std::max<size_t>(bytes, 16)) != cudaSuccess) return nullptr;
         owned.push_back(p);
         return static_cast<uint8_t *>(p);
     }
@@ -537,7 +537,7 @@ dl_status program_set(dl_program *p, cudaStream_t s, const char *pred, int32_t n
     }
     const size_t bytes = static_cast<size_t>(n) * n;
     uint8_t *&d = p->rel[pred];
-    if (!d && cudaMalloc(&d, std::max<size_t>(bytes, 16)) != cudaSuccess) {
+    if (!d && device_alloc(reinterpret_cast<void **>(&d), std::max<size_t>(bytes, 16)) != cudaSuccess) {
         d = nullptr;
         p->rel.erase(pred);
         set_error("program: device allocation failed");
@@ -799,7 +799,7 @@ dl_status program_run(dl_ctx *ctx, Workspace &ws, cudaStream_t s, dl_program *p,
     // keep the models (program-owned copies)
     for (auto &kv : model) {
         uint8_t *&d = p->rel[kv.first];
-        if (!d && cudaMalloc(&d, nbytes) != cudaSuccess) {
+        if (!d && device_alloc(reinterpret_cast<void **>(&d), nbytes) != cudaSuccess) {
             cudaGetLastError();
             p->rel.erase(kv.first);
             set_error("program: device allocation failed");

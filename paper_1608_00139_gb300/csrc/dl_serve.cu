@@ -105,11 +105,14 @@ void worker(dl_ctx *ctx, dl_ctx::Serve *sv, dl_ctx::Serve::Slot *slot) {
             a.mem = r->req.mem;
             a.path = r->req.path;
             a.out_bits = r->req.out_bits;
+            Range trace_(r->req.kind == 0 ? "serve:closure" : "serve:same_generation");
             rc = r->req.kind == 0 ? solve_tc(ctx, slot->ws, slot->stream, a, &st)
                                   : solve_sg(ctx, slot->ws, slot->stream, a, &st);
             if (rc != DL_OK) {
                 err = dl_last_error();
                 cudaStreamSynchronize(slot->stream);
+                for (cudaStream_t x : slot->ws.mx_stream)
+                    if (x) cudaStreamSynchronize(x);
                 cudaGetLastError();
             }
         }

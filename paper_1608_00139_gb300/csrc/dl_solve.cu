@@ -24,6 +24,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -40,10 +41,28 @@ constexpr size_t kTableOffset = 4096;
 
 int64_t round_up(int64_t x, int64_t m) { return (x + m - 1) / m * m; }
 
+// Events at a solver's phase boundaries (0: start, 1: set-up done, 2: main work done, 3: end);
+// with a tag, each phase is also an NVTX range "<tag>:set-up", "<tag>:main", "<tag>:epilogue".
 struct Timer {
     cudaEvent_t *ev;
     cudaStream_t s;
-    void mark(int i) { cudaEventRecord(ev[i], s); }
+    const char *tag = nullptr;
+    bool open = false;
+    void mark(int i) {
+        cudaEventRecord(ev[i], s);
+        if (!tag) return;
+        if (open) nvtxRangePop();
+        static const char *const kPhase[] = {"set-up", "main", "epilogue"};
+        open = i >= 0 && i < 3;
+        if (open) {
+            char name[96];
+            std::snprintf(name, sizeof name, "%s:%s", tag, kPhase[i]);
+            nvtxRangePushA(name);
+        }
+    }
+    ~Timer() {
+        if (open) nvtxRangePop();
+    }
     double ms(int a, int b) {
         float t = 0.f;
         cudaEventElapsedTime(&t, ev[a], ev[b]);
@@ -273,7 +292,7 @@ dl_status tc_bool(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &a
     const int32_t n = a.n;
     const int64_t np = round_up(std::max<int64_t>(n, 1), 256);
     const int64_t wp = np / 64;
-    Timer tm{ws.ev, s};
+    Timer tm{ws.ev, s, "tc_fp8"};
     int launches = 0;
     tm.mark(0);
     const uint8_t *E = nullptr;
@@ -399,7 +418,7 @@ dl_status tc_auto(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &a
     const int32_t n = a.n;
     const int64_t np = round_up(std::max<int64_t>(n, 1), 256);
     const int64_t wp = np / 64;
-    Timer tm{ws.ev, s};
+    Timer tm{ws.ev, s, "tc_auto"};
     int launches = 0;
     tm.mark(0);
     const uint8_t *E = nullptr;
@@ -718,7 +737,7 @@ dl_status tc_fp64(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &a
     const int64_t np = round_up(std::max<int64_t>(n, 1), 64);
     const int64_t npb = round_up(std::max<int64_t>(n, 1), 256);
     const int64_t wp = npb / 64;
-    Timer tm{ws.ev, s};
+    Timer tm{ws.ev, s, "tc_fp64"};
     int launches = 0;
     tm.mark(0);
     const uint8_t *E = nullptr;
@@ -786,7 +805,7 @@ dl_status tc_mixed_path(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveA
     const int32_t n = a.n;
     const int64_t np = round_up(std::max<int64_t>(n, 1), 256);
     const int64_t wp = np / 64;
-    Timer tm{ws.ev, s};
+    Timer tm{ws.ev, s, "tc_mixed"};
     int launches = 0;
     tm.mark(0);
     const uint8_t *E = nullptr;
@@ -914,7 +933,7 @@ dl_status sg_iteration(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveAr
     const int64_t wp = np / 64;
     if (wp > 256) return DL_OK;
     constexpr int kBudget = 64, kGroup = 8;
-    Timer tm{ws.ev, s};
+    Timer tm{ws.ev, s, "sg_iteration"};
     int launches = 0;
     tm.mark(0);
     const uint8_t *P = nullptr, *Bm = nullptr;
@@ -1050,7 +1069,7 @@ dl_status sg_doubling(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArg
     const int32_t n = a.n;
     const int64_t np = round_up(std::max<int64_t>(n, 1), 256);
     const int64_t wp = np / 64;
-    Timer tm{ws.ev, s};
+    Timer tm{ws.ev, s, "sg_doubling"};
     int launches = 0;
     tm.mark(0);
     const uint8_t *P = nullptr, *Bm = nullptr;
@@ -1162,7 +1181,7 @@ dl_status solve_compose(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveA
     const int32_t n = a.n;
     const int64_t np = round_up(std::max<int64_t>(n, 1), 256);
     const int64_t wp = np / 64;
-    Timer tm{ws.ev, s};
+    Timer tm{ws.ev, s, "compose"};
     int launches = 0;
     tm.mark(0);
     const uint8_t *R1 = nullptr, *R2 = nullptr;
@@ -1243,7 +1262,7 @@ dl_status solve_sg_real(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveA
         set_error("n = %d: a row of S~ exceeds one block's shared memory", n);
         return DL_EINVAL;
     }
-    Timer tm{ws.ev, s};
+    Timer tm{ws.ev, s, "sg_real"};
     int launches = 0, gemm_launches = 0;
     tm.mark(0);
     const uint8_t *P = nullptr, *Bm = nullptr;
@@ -1959,7 +1978,7 @@ dl_status solve_transposed(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const Sol
     const int32_t n = a.n;
     const int64_t np = round_up(std::max<int64_t>(n, 1), 256);
     const int64_t wp = np / 64, w = (n + 63) / 64;
-    Timer tm{ws.ev + 4, s};  // events 0-3 belong to the same-generation solver it calls
+    Timer tm{ws.ev + 4, s, "transposed"};  // events 0-3 belong to the same-generation solver it calls
     int launches = 0;
     tm.mark(0);
     const uint8_t *R1 = nullptr;
@@ -2106,17 +2125,22 @@ dl_status solve_transposed(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const Sol
 
 cudaError_t Workspace::init() {
     if (ready) return cudaSuccess;
+    // each piece only if it is missing, so a call after a failed one resumes without leaks
     cudaError_t e;
-    if ((e = cudaMallocHost(&host_pinned, kHostPinned)) != cudaSuccess) return e;
-    host_bytes = kHostPinned;
-    if ((e = cudaMalloc(&status, 256)) != cudaSuccess) return e;
-    if ((e = cudaMalloc(&scal, kScalars * sizeof(unsigned long long))) != cudaSuccess) return e;
+    if (!host_pinned) {
+        if ((e = host_pinned_alloc(&host_pinned, kHostPinned)) != cudaSuccess) return e;
+        host_bytes = kHostPinned;
+    }
+    if (!status && (e = device_alloc(reinterpret_cast<void **>(&status), 256)) != cudaSuccess) return e;
+    if (!scal && (e = device_alloc(reinterpret_cast<void **>(&scal), kScalars * sizeof(unsigned long long))) !=
+                     cudaSuccess)
+        return e;
     for (auto &x : ev)
-        if ((e = cudaEventCreate(&x)) != cudaSuccess) return e;
+        if (!x && (e = cudaEventCreate(&x)) != cudaSuccess) return e;
     for (auto &x : gev)
-        if ((e = cudaEventCreate(&x)) != cudaSuccess) return e;
+        if (!x && (e = cudaEventCreate(&x)) != cudaSuccess) return e;
     for (auto &x : sev)
-        if ((e = cudaEventCreate(&x)) != cudaSuccess) return e;
+        if (!x && (e = cudaEventCreate(&x)) != cudaSuccess) return e;
     ready = true;
     return cudaSuccess;
 }
@@ -2142,6 +2166,9 @@ void Workspace::release() {
         if (x) cudaStreamDestroy(x);
     for (auto &x : mx_ev) x = nullptr;
     for (auto &x : mx_stream) x = nullptr;
+    for (auto &x : ev) x = nullptr;
+    for (auto &x : gev) x = nullptr;
+    for (auto &x : sev) x = nullptr;
     host_pinned = nullptr;
     status = nullptr;
     scal = nullptr;
@@ -2157,7 +2184,7 @@ void *Workspace::get(const std::string &name, size_t bytes) {
         b.bytes = 0;
     }
     size_t want = (bytes + 4095) & ~static_cast<size_t>(4095);
-    if (cudaMalloc(&b.p, want) != cudaSuccess) {
+    if (device_alloc(&b.p, want) != cudaSuccess) {
         cudaGetLastError();
         b.p = nullptr;
         return nullptr;
