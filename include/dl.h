@@ -83,7 +83,7 @@ typedef struct {
     int32_t path_used;       /* dl_path that ran */
     double eps_used;         /* epsilon of the linearised equation (reported for every path) */
     int32_t iters;           /* squarings (FP8), doubling steps (SG), or refinement steps */
-    double final_resid;      /* mixed/FP64: max|eps E - (I - eps E) X| / max|eps E| */
+    double final_resid;      /* mixed/FP64: max|eps E - (I - eps E) X| / max|eps E| (-1: not formed) */
     int64_t guard_flagged;   /* entries in the guard band (|X| <= tau or X < 0) */
     int64_t rows_rechecked;  /* rows corrected by the exact boolean recheck */
     int32_t recheck_sweeps;  /* sweeps of the certificate/recheck kernel */
@@ -134,7 +134,11 @@ DL_API dl_status dl_set_stream(dl_ctx *ctx, void *stream);
  * thr must be 0 (the threshold "> 0" of Theorem 1); other values return DL_EINVAL.
  * out_rtilde (optional, n*n doubles, NULL allowed): the real least solution
  * R~ = (I - eps E)^-1 eps E (Prop. 1); only the FP64 and mixed paths produce it (with
- * DL_PATH_BOOL_FP8 or DL_PATH_AUTO a non-NULL out_rtilde returns DL_EINVAL).
+ * DL_PATH_BOOL_FP8 or DL_PATH_AUTO a non-NULL out_rtilde returns DL_EINVAL).  DL_PATH_MIXED
+ * refines R~ (max|R| <= refine_tol * eps) only when out_rtilde is given; for the model alone it
+ * stops after the solve, since X > 0 is already exact wherever X is positive (A is an M-matrix and
+ * the factorisation keeps every sign) and the certificate and recheck settle entries lost to
+ * underflow (stats: iters = 0, final_resid = -1).
  * stats (optional): filled on DL_OK.
  */
 DL_API dl_status dl_tc_closure(dl_ctx *ctx, int32_t n, const uint8_t *E, dl_mem mem, double eps,

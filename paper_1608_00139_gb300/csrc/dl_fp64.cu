@@ -196,27 +196,51 @@ cudaError_t dgemm_sub(const double *A, const double *Bm, double *C, int64_t ldg,
     return cudaGetLastError();
 }
 
-// Threshold X > 0 into bits; one warp per (row, 64-column word).
-__global__ void thresh_pack_kernel(const double *__restrict__ X, int64_t ldx, int n, double tau,
-                                   uint64_t *__restrict__ bits, int64_t wp,
-                                   unsigned long long *guard) {
+// Threshold X > 0 into bits (and count the guard band).
+// Spread the 32 bits of x to the even bit positions of a 64-bit word (bit l -> bit 2l).
+__device__ __forceinline__ uint64_t spread_even(uint32_t x) {
+    uint64_t v = x;
+    v = (v | (v << 16)) & 0x0000FFFF0000FFFFull;
+    v = (v | (v << 8)) & 0x00FF00FF00FF00FFull;
+    v = (v | (v << 4)) & 0x0F0F0F0F0F0F0F0Full;
+    v = (v | (v << 2)) & 0x3333333333333333ull;
+    v = (v | (v << 1)) & 0x5555555555555555ull;
+    return v;
+}
+
+constexpr int kThreshWords = 8;  // 64-bit words (512 columns) per warp
+
+// A warp takes kThreshWords consecutive words of one row: every lane issues its 16-byte loads
+// (columns 2 lane, 2 lane + 1 of each word) before it tests any, and the even and odd columns'
+// ballots are interleaved into the word.  Rows are 16-byte aligned (ldx even).
+__global__ void __launch_bounds__(256) thresh_pack_kernel(const double *__restrict__ X, int64_t ldx, int n,
+                                                          double tau, uint64_t *__restrict__ bits, int64_t wp,
+                                                          unsigned long long *guard) {
     const int lane = threadIdx.x & 31;
+    const int64_t words = (n + 63) / 64, groups = (words + kThreshWords - 1) / kThreshWords;
     const int64_t gw = (static_cast<int64_t>(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
-    const int64_t words = (n + 63) / 64;
-    if (gw >= static_cast<int64_t>(n) * words) return;
-    const int64_t row = gw / words, w = gw % words;
-    const int64_t c0 = w * 64 + lane, c1 = c0 + 32;
-    const double x0 = c0 < n ? X[row * ldx + c0] : 0.0;
-    const double x1 = c1 < n ? X[row * ldx + c1] : 0.0;
-    const uint32_t lo = __ballot_sync(0xffffffffu, x0 > 0.0);
-    const uint32_t hi = __ballot_sync(0xffffffffu, x1 > 0.0);
-    const bool g0 = x0 < 0.0 || (x0 > 0.0 && x0 <= tau);
-    const bool g1 = x1 < 0.0 || (x1 > 0.0 && x1 <= tau);
-    const uint32_t gcount = __popc(__ballot_sync(0xffffffffu, g0)) + __popc(__ballot_sync(0xffffffffu, g1));
-    if (lane == 0) {
-        bits[row * wp + w] = (static_cast<uint64_t>(hi) << 32) | lo;
-        if (gcount) atomicAdd(guard, static_cast<unsigned long long>(gcount));
+    if (gw >= static_cast<int64_t>(n) * groups) return;
+    const int64_t row = gw / groups, w0 = (gw % groups) * kThreshWords;
+    const double *xr = X + row * ldx;
+    double2 v[kThreshWords];
+#pragma unroll
+    for (int q = 0; q < kThreshWords; ++q) {
+        const int64_t c = (w0 + q) * 64 + 2 * lane;
+        v[q] = c + 1 < n ? __ldcs(reinterpret_cast<const double2 *>(xr + c))
+                         : make_double2(c < n ? xr[c] : 0.0, 0.0);
     }
+    uint32_t gcount = 0;
+#pragma unroll
+    for (int q = 0; q < kThreshWords; ++q) {
+        if (w0 + q >= words) break;
+        const uint32_t ev = __ballot_sync(0xffffffffu, v[q].x > 0.0);
+        const uint32_t od = __ballot_sync(0xffffffffu, v[q].y > 0.0);
+        const bool gx = v[q].x < 0.0 || (v[q].x > 0.0 && v[q].x <= tau);  // guard band: |X| <= tau or X < 0
+        const bool gy = v[q].y < 0.0 || (v[q].y > 0.0 && v[q].y <= tau);
+        gcount += __popc(__ballot_sync(0xffffffffu, gx)) + __popc(__ballot_sync(0xffffffffu, gy));
+        if (lane == q) bits[row * wp + w0 + q] = spread_even(ev) | (spread_even(od) << 1);
+    }
+    if (lane == 0 && gcount) atomicAdd(guard, static_cast<unsigned long long>(gcount));
 }
 
 }  // namespace
@@ -279,8 +303,9 @@ cudaError_t thresh_pack_f64(const double *X, int64_t ldx, int n, int np, double 
                             int64_t wp, unsigned long long *guard, cudaStream_t s) {
     (void)np;
     if (n <= 0) return cudaSuccess;
-    const int64_t warps = static_cast<int64_t>(n) * ((n + 63) / 64);
-    const int64_t threads = warps * 32;
+    if (ldx % 2 != 0 || (reinterpret_cast<uintptr_t>(X) & 15) != 0) return cudaErrorInvalidValue;
+    const int64_t groups = ((n + 63) / 64 + kThreshWords - 1) / kThreshWords;
+    const int64_t threads = static_cast<int64_t>(n) * groups * 32;
     thresh_pack_kernel<<<static_cast<unsigned>((threads + 255) / 256), 256, 0, s>>>(X, ldx, n, tau, bits, wp,
                                                                                    guard);
     return cudaGetLastError();

@@ -630,6 +630,42 @@ dl_status mixed_streams(Workspace &ws) {
 
 }  // namespace
 
+// The first product of the refinement when E is sparse: with Z = 0 the residual is R = eps E, and
+// D^T = R^T W^T has rows  D^T[j][:] = eps * sum_{k : E[k][j] = 1} W^T[k][:]  (rows of W^T, row-major
+// in WT, gathered over the predecessors of j from the CSR of E^T): nnz(E) rows read instead of an
+// n^3 product.  Rows j >= n are zero; columns i >= n come out zero (W's padded rows are identity
+// rows).
+constexpr int kFirstThreads = 256;
+
+__global__ void __launch_bounds__(kFirstThreads) first_product_kernel(const int *__restrict__ pptr,
+                                                                      const int *__restrict__ pcol, int n, int np,
+                                                                      float eps, const float *__restrict__ WT,
+                                                                      float *__restrict__ D) {
+    const int j = blockIdx.x;
+    float *dj = D + static_cast<int64_t>(j) * np;
+    const int q0 = j < n ? pptr[j] : 0, q1 = j < n ? pptr[j + 1] : 0;
+    for (int c = 4 * threadIdx.x; c < np; c += 4 * kFirstThreads) {
+        float4 acc = make_float4(0.f, 0.f, 0.f, 0.f);
+        int q = q0;
+        for (; q + 4 <= q1; q += 4) {  // four rows in flight
+            float4 v[4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                v[u] = *reinterpret_cast<const float4 *>(WT + static_cast<int64_t>(pcol[q + u]) * np + c);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) acc.x += v[u].x, acc.y += v[u].y, acc.z += v[u].z, acc.w += v[u].w;
+        }
+        for (; q < q1; ++q) {
+            const float4 v = *reinterpret_cast<const float4 *>(WT + static_cast<int64_t>(pcol[q]) * np + c);
+            acc.x += v.x, acc.y += v.y, acc.z += v.z, acc.w += v.w;
+        }
+        *reinterpret_cast<float4 *>(dj + c) = make_float4(eps * acc.x, eps * acc.y, eps * acc.z, eps * acc.w);
+    }
+}
+
+// Graphs with at most this many facts per constant take the gathered first product.
+constexpr int64_t kSparseFirstDegree = 12;
+
 // Consecutive NVTX ranges, one open at a time.
 struct Phases {
     bool open = false;
@@ -934,7 +970,8 @@ dl_status tc_mixed(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &
     int *boff = nullptr;
     uint16_t *bedges = nullptr;
     CUtensorMap zmap{};  // ZfT (banded residual)
-    if (banded) {
+    const bool need_x = a.out_rtilde != nullptr;  // (see the refinement loop below)
+    if (banded && need_x) {
         const int64_t cells = static_cast<int64_t>(ni) * nbd * kRI;
         auto *bcnt = static_cast<int *>(ws.get("mx_bcnt", (cells + 1) * 4));
         boff = static_cast<int *>(ws.get("mx_boff", (cells + 1) * 4));
@@ -986,14 +1023,36 @@ dl_status tc_mixed(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &
                                                              a.rhs_real);
         return cudaGetLastError();
     };
+    // The first product as a gather for sparse E (the closure's own right-hand side eps E): the
+    // CSR of E^T from a transposed byte copy of E.
+    const bool sparse_first = !general_rhs && static_cast<int64_t>(nnz) <= kSparseFirstDegree * n;
+    int *pptr = nullptr, *pcol = nullptr;
+    if (sparse_first) {
+        auto *Et = static_cast<uint8_t *>(ws.get("mx_Et", static_cast<size_t>(n) * n));
+        auto *pcnt = static_cast<int *>(ws.get("mx_pcnt", (np + 1) * 4));
+        pptr = static_cast<int *>(ws.get("mx_pptr", (np + 1) * 4));
+        pcol = static_cast<int *>(ws.get("mx_pcol", static_cast<size_t>(std::max(nnz, 1)) * 4));
+        if (!Et || !pcnt || !pptr || !pcol) {
+            set_error("mixed path: device allocation failed (CSR of E^T)");
+            return DL_ENOMEM;
+        }
+        MCK(transpose(E, n, n, n, Et, n, s));
+        MCK(csr_build(Et, n, pcnt, pptr, s));
+        MCK(csr_fill(Et, n, pptr, pcol, s));
+        launches += 3;
+    }
+    // Without an R~ output only the model is wanted: X > 0 after the solve is already exact where
+    // it is positive (A is an M-matrix and every quantity of the factorisation keeps its sign, so
+    // no entry cancels to a spurious value), entries lost to underflow land in the guard band, and
+    // the caller's certificate and recheck settle them; the refinement is then skipped.
     unsigned *rmax_d = reinterpret_cast<unsigned *>(ws.scal + 20);
     double rmax = 0.0, best = 0.0;
-    int products = 0, stall = 0;
+    int products = 0, stall = 0, gemm_products = 0;
     // The residual has a rounding floor of about (row length) * 2^-53 * max|X|; refinement stops
     // at tol, or when it no longer halves the residual once that is below 1e-8 * eps.
     const double floor_ok = 1e-8 * eps;
     MCK(cudaMemsetAsync(Z64, 0, np * np * 8, s));
-    {
+    if (!sparse_first) {
         dim3 tgrid(static_cast<unsigned>(np / TT), static_cast<unsigned>(np / TT));
         if (a.rhs_real)
             build_rt_real_kernel<<<tgrid, dim3(TT, 8), 0, s>>>(a.rhs_real, n, N, eps, R32);
@@ -1003,13 +1062,23 @@ dl_status tc_mixed(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &
         ++launches;
     }
     for (;;) {
-        MCK(run(refine[0], sms, s));  // D^T = R^T W^T
+        if (products == 0 && sparse_first) {
+            // W^T row-major is still in W32 (the residual overwrites it from the first residual on)
+            first_product_kernel<<<static_cast<unsigned>(np), kFirstThreads, 0, s>>>(pptr, pcol, n, N,
+                                                                                   static_cast<float>(eps), W32, D32);
+            MCK(cudaGetLastError());
+            ++launches;
+        } else {
+            MCK(run(refine[0], sms, s));  // D^T = R^T W^T
+            ++gemm_products;
+        }
         add_fix_kernel<<<static_cast<unsigned>(np), 256, row_smem, s>>>(Z64, D32, n, N, deg_bits, min_hb,
                                                                       general_rhs ? 0 : 1, escale,
-                                                                      banded ? nullptr : Zf);
+                                                                      banded || !need_x ? nullptr : Zf);
         MCK(cudaGetLastError());
         ++launches;
         ++products;
+        if (!need_x) break;  // the model only: no refinement
         MCK(cudaMemsetAsync(rmax_d, 0, sizeof(unsigned), s));
         MCK(residual(rmax_d));
         ++launches;
@@ -1037,10 +1106,10 @@ dl_status tc_mixed(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &
     MCK(cudaEventSynchronize(ev[7]));
     if (st) {
         st->iters = std::max(products - 1, 0);  // refinement steps after the first product (the solve)
-        st->final_resid = rmax / eps;
-        st->gemm_flops = flops_lu + flops_w + flops_ref * products;
+        st->final_resid = need_x ? rmax / eps : -1.0;  // -1: no residual was formed (model only)
+        st->gemm_flops = flops_lu + flops_w + flops_ref * gemm_products;
         st->gemm_launches = static_cast<int>(l21.size() + ahead.size() + bulk.size() + ginv.size() + wfwd.size() +
-                                             wbwd.size()) + products;
+                                             wbwd.size()) + gemm_products;
         float t1 = 0, t2 = 0, t3 = 0;
         cudaEventElapsedTime(&t1, ev[4], ev[5]);
         cudaEventElapsedTime(&t2, ev[5], ev[6]);

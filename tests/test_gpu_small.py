@@ -250,8 +250,12 @@ def test_mixed_one_row_per_residual_block(ctx):
     """n = 15000: one row of Z per residual block; the model against the oracle's."""
     n = 15000
     e = inputs.er_digraph(n, 2e-4, 13)
-    bits, st = ctx.tc_closure(e, path="mixed")
+    bits, st, x = ctx.tc_closure(torch.from_numpy(e).cuda(), path="mixed", rtilde=True)
     assert st["final_resid"] <= 1e-13
+    assert np.array_equal(bits.cpu().numpy().view(np.uint64), oracle.tc_model(e))
+    # without an R~ output the path stops after the solve; the model is the same
+    bits, st = ctx.tc_closure(e, path="mixed")
+    assert st["iters"] == 0 and st["final_resid"] == -1.0
     assert np.array_equal(bits, oracle.tc_model(e))
 
 
