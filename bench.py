@@ -600,11 +600,17 @@ def run_reference(args, rank: int, world: int) -> None:
 
 
 def run_part(args, device: int) -> None:
-    """One secondary measurement on its own (same functions as the full run)."""
+    """One secondary measurement on its own (same functions as the full run, with the same
+    autotuned choices unless --no-tune)."""
     import torch
 
     from paper_1608_00139_gb300 import dl
     torch.cuda.set_device(device)
+    if not args.no_tune:  # every context of this process reads the tuned table (DL_TUNE_CACHE)
+        os.environ["DL_TUNE_CACHE"] = os.path.join(tempfile.gettempdir(), f"dl_tune_{os.getpid()}_part.json")
+        with dl.Context(device) as tctx:
+            for nb in (N, 4096):
+                tctx.autotune(nb)
     if args.part == "serving":
         out = bench_serving(dl, torch, device, args.serve_seconds)
     elif args.part == "mixed":
@@ -650,6 +656,8 @@ def main() -> None:
                     help="skip the squarings-only FP8 comparison run")
     ap.add_argument("--no-fresh", action="store_true",
                     help="skip the leg that rotates seeded graphs across solves")
+    ap.add_argument("--no-tune", action="store_true",
+                    help="keep the fixed rules instead of the autotuner's measured choices")
     ap.add_argument("--no-extra", action="store_true",
                     help="skip the same-generation, batch and serving measurements")
     ap.add_argument("--serve-seconds", type=float, default=60.0,
@@ -699,6 +707,13 @@ def main() -> None:
     dev_out = [torch.empty((N, (N + 63) // 64), dtype=torch.int64, device="cuda") for _ in range(nctx)]
     torch.cuda.synchronize()
     streams = [torch.cuda.Stream() for _ in range(nctx)]
+    # the autotuner: measured choices for the sizes the step and the extra legs use, kept in a
+    # cache file that every context of this run reads when it is created
+    tuned = None
+    if not args.no_tune:  # every context of this process reads the tuned table (DL_TUNE_CACHE)
+        os.environ["DL_TUNE_CACHE"] = os.path.join(tempfile.gettempdir(), f"dl_tune_{os.getpid()}_{rank}.json")
+        with dl.Context(local) as tctx:
+            tuned = {str(nb): tctx.autotune(nb)["entry"] for nb in (N, 4096)}
     ctxs = [dl.Context(local, stream=st_) for st_ in streams]
     pool = ThreadPoolExecutor(max_workers=nctx)
     main_stream = torch.cuda.current_stream()
@@ -856,7 +871,8 @@ def main() -> None:
                        "path": args.path, "l2": "inputs 3 x 64 MiB > L2, cycled each step",
                        "squarings_per_model": sorted(set(squarings)),
                        "concurrency": f"{nctx} closures in flight ({INFLIGHT} contexts per model, one stream and host thread each)",
-                       "gemm_busy_fraction": gemm_share},
+                       "gemm_busy_fraction": gemm_share,
+                       "tuned": tuned if tuned is not None else "fixed rules (--no-tune)"},
             "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": len(gs) * N * N,
                     "d2h_bytes_per_step": len(gs) * N * ((N + 63) // 64) * 8},
             "e2e_bits": {"value": units * flops_equiv(N) / e2e_bits_s / 1e12, "unit": UNIT,

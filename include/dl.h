@@ -77,6 +77,11 @@ typedef struct {
     int32_t refine_max_iters;  /* refinement step limit of those paths; 0 = 30 */
     double guard_tau;          /* entries with |R~| <= tau are flagged for recheck; 0 = 1e-30 */
     double wait_timeout_s;     /* limit of every device-side wait; 0 = 2 s */
+    int32_t autotune;          /* 1: tune each new size bucket on its first closure or same-generation
+                                  call (dl_autotune); 0: the measured table only (cache or explicit
+                                  dl_autotune calls), else the fixed rules */
+    const char *tune_cache;    /* JSON cache of tuned choices, read at dl_create and written after
+                                  each tuning run; NULL: the DL_TUNE_CACHE environment variable, if set */
 } dl_config;
 
 typedef struct {
@@ -297,6 +302,25 @@ DL_API dl_status dl_transposed(dl_ctx *ctx, int32_t n, const uint8_t *R1, dl_mem
  */
 DL_API dl_status dl_compose(dl_ctx *ctx, int32_t n, const uint8_t *R1, const uint8_t *R2,
                      dl_mem mem, uint64_t *out_bits, dl_stats *stats);
+
+/* ---- autotuning ----------------------------------------------------------------------- */
+
+/*
+ * Measure, for problems of size n on this context's GPU, the choices the solvers otherwise take
+ * from fixed rules, and keep them for n's size bucket (n rounded up to a power of two, at least
+ * 256; measured up to 16384): the FP8 squaring's tile width (128 or 256) and its time per
+ * squaring, the bytes per second of an unsaturated Iteration sweep (the AUTO path's cost model
+ * between sweeps and squarings), the SMs the mixed path's LU leaves to its critical chain (16, 32
+ * or 48), and whether same generation on AUTO takes the Iteration on bits or the doubling.  The
+ * inputs are synthetic (generated on the device).  Every choice leaves every model exact; only
+ * speed depends on it.  flags: 1 = measure again even if the bucket is known (from this context
+ * or the cache).  report (cap bytes, may be NULL when cap is 0; *len gets the full length): JSON
+ * {"key", "bucket", "source": "measured" | "cache" | "defaults ...", "entry": {sq_bn, t_sq_us,
+ * sweep_gbs, mx_reserve, sg_iteration}}.  With a cache path (dl_config.tune_cache or
+ * DL_TUNE_CACHE) the entry is written there, keyed by GPU name, driver version and bucket.
+ * Takes from milliseconds (small buckets) to about a second (16384).
+ */
+DL_API dl_status dl_autotune(dl_ctx *ctx, int32_t n, int32_t flags, char *report, size_t cap, size_t *len);
 
 /* ---- linear programs (the class C_lin of Sec. 5) ---------------------------------- */
 

@@ -98,6 +98,15 @@ dl_status run_sync(dl_ctx *ctx, dl_stats *stats, F &&f) {
     return rc;
 }
 
+// With dl_config.autotune, a size bucket met for the first time is tuned before the call.
+dl_status maybe_autotune(dl_ctx *ctx, Workspace &ws, cudaStream_t s, int32_t n) {
+    if (!ctx->tune.autotune || n <= 0) return DL_OK;
+    if (tuned(ctx, (static_cast<int64_t>(n) + 255) / 256 * 256).measured) return DL_OK;
+    TuneEntry e;
+    std::string src;
+    return autotune_bucket(ctx, ws, s, n, false, &e, &src);
+}
+
 }  // namespace
 
 extern "C" {
@@ -149,6 +158,7 @@ dl_status dl_create(dl_ctx **out, int device, const dl_config *cfg) {
         return DL_EDEVICE;
     }
     ctx->stream = ctx->cfg.stream ? static_cast<cudaStream_t>(ctx->cfg.stream) : ctx->own_stream;
+    tune_init(ctx);  // key prefix, flags, and the cache's entries for this GPU and driver
     *out = ctx;
     return DL_OK;
 }
@@ -206,7 +216,8 @@ dl_status dl_tc_closure(dl_ctx *ctx, int32_t n, const uint8_t *E, dl_mem mem, do
     a.out_bits = out_bits;
     a.out_rtilde = out_rtilde;
     return run_sync(ctx, stats, [&](Workspace &ws, cudaStream_t s, dl_stats *st) {
-        return solve_tc(ctx, ws, s, a, st);
+        dl_status r = maybe_autotune(ctx, ws, s, a.n);
+        return r ? r : solve_tc(ctx, ws, s, a, st);
     });
 }
 
@@ -236,7 +247,8 @@ dl_status dl_tc_closure_bits(dl_ctx *ctx, int32_t n, const uint64_t *E_bits, dl_
     a.out_bits = out_bits;
     a.out_rtilde = out_rtilde;
     return run_sync(ctx, stats, [&](Workspace &ws, cudaStream_t s, dl_stats *st) {
-        return solve_tc(ctx, ws, s, a, st);
+        dl_status r = maybe_autotune(ctx, ws, s, a.n);
+        return r ? r : solve_tc(ctx, ws, s, a, st);
     });
 }
 
@@ -266,7 +278,8 @@ dl_status dl_sg_least_model(dl_ctx *ctx, int32_t n, const uint8_t *P, const uint
     a.path = path;
     a.out_bits = out_bits;
     return run_sync(ctx, stats, [&](Workspace &ws, cudaStream_t s, dl_stats *st) {
-        return solve_sg(ctx, ws, s, a, st);
+        dl_status r = maybe_autotune(ctx, ws, s, a.n);
+        return r ? r : solve_sg(ctx, ws, s, a, st);
     });
 }
 
@@ -376,6 +389,32 @@ dl_status dl_tail_system(dl_ctx *ctx, int32_t n, int32_t m, const dl_tail_eq *eq
     return run_sync(ctx, stats, [&](Workspace &ws, cudaStream_t s, dl_stats *st) {
         return solve_tail_system(ctx, ws, s, n, m, eqs, mem, path, out_bits, out_rtilde, st);
     });
+}
+
+dl_status dl_autotune(dl_ctx *ctx, int32_t n, int32_t flags, char *report, size_t cap, size_t *len) {
+    clear_error();
+    Range trace_(__func__);
+    GUARD_CTX(ctx);
+    if (n < 0 || (cap > 0 && !report) || (flags & ~1)) {
+        set_error("bad n (%d), flags (%d) or report buffer", n, flags);
+        return DL_EINVAL;
+    }
+    std::string text;
+    dl_status rc = run_sync(ctx, nullptr, [&](Workspace &ws, cudaStream_t s, dl_stats *) {
+        TuneEntry e;
+        std::string src;
+        dl_status r = autotune_bucket(ctx, ws, s, n, (flags & 1) != 0, &e, &src);
+        if (r == DL_OK) text = tune_report(ctx, e, src);
+        return r;
+    });
+    if (rc) return rc;
+    if (len) *len = text.size();
+    if (cap > 0) {
+        const size_t k = std::min(cap - 1, text.size());
+        std::memcpy(report, text.data(), k);
+        report[k] = 0;
+    }
+    return DL_OK;
 }
 
 dl_status dl_program_create(dl_ctx *ctx, const char *text, dl_program **out) {

@@ -62,6 +62,25 @@ struct Workspace {
 
 struct Request;  // serving
 
+// Tuned choices for one size bucket (dl_tune.cu); the defaults are the fixed rules.
+struct TuneEntry {
+    int bucket = 0;
+    int sq_bn = 256;          // FP8 squaring tile width
+    double t_sq = 0.0;        // seconds per squaring (0: the flop-rate model)
+    double sweep_rate = 0.0;  // bytes per second of an unsaturated sweep (0: the size rule)
+    int mx_reserve = 32;      // SMs the mixed LU's bulk update leaves to the chain
+    int sg_iteration = -1;    // same generation on AUTO: 1 Iteration, 0 doubling, -1 by size
+    bool measured = false;
+};
+
+struct Tuning {
+    std::mutex mu;
+    std::map<int, TuneEntry> by_bucket;
+    std::string cache_path;
+    std::string key_prefix;  // "<GPU name>|<driver version>|"
+    bool autotune = false;
+};
+
 }  // namespace dl
 
 struct dl_ctx {
@@ -73,6 +92,8 @@ struct dl_ctx {
     uint64_t budget_ns = 2000000000ull;
     std::mutex mu;  // serialises synchronous calls
     dl::Workspace ws;
+
+    dl::Tuning tune;  // tuned choices per size bucket (dl_tune.cu)
 
     // serving state (dl_serve.cpp)
     struct Serve;
@@ -144,6 +165,13 @@ dl_status program_get(dl_program *p, Workspace &ws, cudaStream_t s, const char *
                       dl_mem mem);
 std::string program_describe(const dl_program *p);
 dl_ctx *program_ctx(const dl_program *p);
+// The autotuner (dl_tune.cu).
+int tune_bucket(int64_t np);
+TuneEntry tuned(dl_ctx *ctx, int64_t np);  // the bucket's entry, or the defaults
+void tune_init(dl_ctx *ctx);                 // key prefix, flags, cache read (dl_create)
+dl_status autotune_bucket(dl_ctx *ctx, Workspace &ws, cudaStream_t s, int32_t n, bool force, TuneEntry *out,
+                          std::string *source);
+std::string tune_report(const dl_ctx *ctx, const TuneEntry &e, const std::string &source);
 // Device bytes a request of this kind and size needs (serving admission).
 size_t footprint_bytes(int kind, int32_t n);
 

@@ -12,7 +12,7 @@
 //        bulk:  the rest of the trailing matrix, A22 -= L21 U12.
 //      The look-ahead and the chain that needs it (the next diagonal block, its L21 and T) run
 //      on a stream of the greatest priority, the bulk update on a stream of the least priority
-//      and on all SMs but kReserve, so the chain of 128 x 128 steps proceeds while the bulk
+//      and on all SMs but a reserve (32, or tuned per size), so the chain of 128 x 128 steps proceeds while the bulk
 //      update of the previous block streams through HBM.
 //   3. W = A^-1 in FP32: the block solves applied to the identity (kept transposed, Z = I A^-T,
 //      by groups of 8 blocks with precomputed inverses of the groups' diagonal parts, so that
@@ -46,7 +46,6 @@ namespace {
 constexpr int BL = 128;        // LU block size = GEMM tile
 constexpr int TT = 32;         // transpose tile
 constexpr int kSolveGroup = 8;  // blocks per group of the solves (1024 columns)
-constexpr int kReserve = 32;   // SMs the bulk LU update leaves to the critical chain
 
 __global__ void build_a_kernel(const uint8_t *__restrict__ E, int n, int np, float eps, float *__restrict__ A) {
     const int64_t row = blockIdx.y;
@@ -858,6 +857,8 @@ dl_status tc_mixed(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &
                            std::min(L.tiles, max_grid), ws.status, ctx->budget_ns, on);
     };
     const int sms = ctx->sms;
+    // SMs the bulk update leaves to the chain (tuned per size bucket, else 32)
+    const int reserve = std::min(std::max(1, tuned(ctx, np).mx_reserve), std::max(1, sms - 1));
 
     // ---- LU with look-ahead --------------------------------------------------------------
     ph.to("mixed:lu");
@@ -873,9 +874,9 @@ dl_status tc_mixed(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &
         MCK(cudaGetLastError());
         ++launches;
         if (rem <= 0) break;
-        // L21 runs beside the bulk update of block k - 1, which leaves it kReserve SMs
+        // L21 runs beside the bulk update of block k - 1, which leaves it `reserve` SMs
         const bool beside_bulk = k > 0 && has_bulk[k - 1] >= 0;
-        MCK(run(l21[has_l21[k]], beside_bulk ? kReserve : sms, P));
+        MCK(run(l21[has_l21[k]], beside_bulk ? reserve : sms, P));
         float *Tk = T2 + static_cast<int64_t>(k & 1) * np * BL;
         MCK(transpose(A32 + kb * np + kb + BL, np, BL, rem, Tk, BL, P));  // T = A12^T
         ++launches;
@@ -889,7 +890,7 @@ dl_status tc_mixed(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &
         bulk_pending = false;
         if (has_bulk[k] >= 0) {
             MCK(cudaStreamWaitEvent(U, evT[k & 1], 0));
-            MCK(run(bulk[has_bulk[k]], std::max(1, sms - kReserve), U));
+            MCK(run(bulk[has_bulk[k]], std::max(1, sms - reserve), U));
             MCK(cudaEventRecord(evB[k & 1], U));
             bulk_pending = true;
         }

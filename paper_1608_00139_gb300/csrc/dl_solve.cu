@@ -261,7 +261,8 @@ GemmEpilogue bool_epi(uint8_t *out8, int64_t np, uint64_t *bits, int64_t wp,
     return e;
 }
 
-int bool_bn(int64_t np) { return np % 256 == 0 ? 256 : 128; }
+// The FP8 squaring's tile width for np (tuned per size bucket, else 256).
+int bool_bn(dl_ctx *ctx, int64_t np) { return tuned(ctx, np).sq_bn; }
 
 // Validate eps against ||E||_inf (Lemma 1) or pick the paper's default.
 dl_status choose_eps(double user, double dflt, const char *what, double *out) {
@@ -329,7 +330,7 @@ dl_status tc_bool(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &a
     // GEMM tables: squaring C0 -> C1 and C1 -> C0, bits into rbits, count into slot
     GemmProblem probs[2];
     std::string err;
-    const int bn = bool_bn(np);
+    const int bn = bool_bn(ctx, np);
     for (int p = 0; p < 2; ++p) {
         const uint8_t *src = p == 0 ? C0 : C1;
         uint8_t *dst = p == 0 ? C1 : C0;
@@ -452,8 +453,11 @@ dl_status tc_auto(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &a
     // cost model (seconds): one squaring vs one sweep before rows saturate.  A sweep reads a
     // successor's row per fact; the bit matrix is L2-resident up to a few tens of MB.
     const double bit_bytes = static_cast<double>(np) * wp * 8;
-    const double sweep_rate = bit_bytes <= 48e6 ? 6.0e12 : 3.0e12;
-    const double t_sq = 2.0 * np * np * np / 3.4e15 + 15e-6;
+    const TuneEntry tn = tuned(ctx, np);  // measured rates when the size bucket has been tuned
+    const double sweep_rate = tn.sweep_rate > 0 ? tn.sweep_rate : bit_bytes <= 48e6 ? 6.0e12 : 3.0e12;
+    const double t_sq = tn.t_sq > 0 ? tn.t_sq * static_cast<double>(np) * np * np /
+                                          (static_cast<double>(tn.bucket) * tn.bucket * tn.bucket)
+                                    : 2.0 * np * np * np / 3.4e15 + 15e-6;
     const double t_sw_min = 2.0 * bit_bytes / sweep_rate + 5e-6;  // a sweep with no facts
     // the speculative group never exceeds the sweeps a squaring is worth with no facts at all,
     // and is empty when the last closure here was settled by the single-row Iteration alone
@@ -579,7 +583,7 @@ dl_status tc_auto(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &a
     int since_square = sweeps;  // sweeps since the last squaring
     GemmProblem *dprobs = nullptr;
     int tiles = 0, grid = 0;
-    const int bn = bool_bn(np);
+    const int bn = bool_bn(ctx, np);
     auto gemm_setup = [&]() -> dl_status {  // the two squaring problems, uploaded on first use
         if (dprobs) return DL_OK;
         GemmProblem probs[2];
@@ -1055,7 +1059,8 @@ dl_status solve_sg(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &
     // about 0.1 ms of launches, and about ten are needed.  The doubling is cheaper below
     // Np ~ 6000 (measured: 0.9 against 1.3 ms at N = 4096, 5.1 against 2.1 ms at N = 8192).
     const int64_t np = round_up(std::max<int64_t>(a.n, 1), 256);
-    if (a.path == DL_PATH_AUTO && np >= 6144) {
+    const int tuned_iteration = tuned(ctx, np).sg_iteration;  // measured crossover, when tuned
+    if (a.path == DL_PATH_AUTO && (tuned_iteration >= 0 ? tuned_iteration == 1 : np >= 6144)) {
         bool done = false;
         const dl_status rc = sg_iteration(ctx, ws, s, a, st, &done);
         if (rc != DL_OK || done) return rc;
@@ -1104,7 +1109,7 @@ dl_status sg_doubling(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArg
     const unsigned long long q_count0 = host_scal(ws)[SC_COUNT0];
 
     // Tables per parity: [T = Q S, Q' = Q Q] (MN-major B) and [S' = T Q^T | S] (K-major B).
-    const int bn = bool_bn(np);
+    const int bn = bool_bn(ctx, np);
     GemmProblem g1[4], g2[2];
     std::string err;
     for (int p = 0; p < 2; ++p) {
@@ -1199,7 +1204,7 @@ dl_status solve_compose(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveA
     tm.mark(1);
     GemmProblem pr;
     std::string err;
-    const int bn = bool_bn(np);
+    const int bn = bool_bn(ctx, np);
     if (!gemm_make_problem(&pr, KIND_F8, false, bn, static_cast<int>(np), static_cast<int>(np),
                            static_cast<int>(np), square_op(A8, np), square_op(B8, np),
                            bool_epi(nullptr, np, bits, wp, ws.scal + SC_ONES, nullptr), &err)) {
@@ -2001,7 +2006,7 @@ dl_status solve_transposed(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const Sol
     // B = min1(R1 + R1 R1^T): C[i][j] = sum_k R1[i][k] R1[j][k] (B operand K-major = R1 itself)
     GemmProblem pr;
     std::string err;
-    const int bn = bool_bn(np);
+    const int bn = bool_bn(ctx, np);
     if (!gemm_make_problem(&pr, KIND_F8, true, bn, static_cast<int>(np), static_cast<int>(np), static_cast<int>(np),
                            square_op(R8, np), square_op(R8, np), bool_epi(B8, np, nullptr, wp, nullptr, R8), &err)) {
         set_error("%s", err.c_str());

@@ -26,7 +26,7 @@ DL_MEM_HOST, DL_MEM_DEVICE = 0, 1
 EXPORTED = ["dl_create", "dl_destroy", "dl_last_error", "dl_set_stream", "dl_tc_closure", "dl_tc_closure_bits",
             "dl_sg_least_model", "dl_sg_real", "dl_tail_recursive", "dl_tail_recursive_real", "dl_tail_system", "dl_transposed", "dl_compose",
             "dl_program_create", "dl_program_destroy", "dl_program_set", "dl_program_run", "dl_program_get",
-            "dl_program_describe", "dl_tc_batch", "dl_submit", "dl_poll", "dl_cancel",
+            "dl_program_describe", "dl_autotune", "dl_tc_batch", "dl_submit", "dl_poll", "dl_cancel",
             "dl_tc_closure_noalloc", "dl_selftest_wait_timeout"]
 NOALLOC_MAX_N = 2048
 
@@ -43,7 +43,8 @@ class Config(ctypes.Structure):
     _fields_ = [("stream", ctypes.c_void_p), ("hbm_budget_bytes", ctypes.c_size_t),
                 ("max_slots", ctypes.c_int32), ("refine_tol", ctypes.c_double),
                 ("refine_max_iters", ctypes.c_int32), ("guard_tau", ctypes.c_double),
-                ("wait_timeout_s", ctypes.c_double)]
+                ("wait_timeout_s", ctypes.c_double), ("autotune", ctypes.c_int32),
+                ("tune_cache", ctypes.c_char_p)]
 
 
 class Stats(ctypes.Structure):
@@ -112,6 +113,7 @@ def lib() -> ctypes.CDLL:
             L.dl_tail_system.argtypes = [vp, i32, i32, vp, ctypes.c_int, ctypes.c_int, vp, vp,
                                          ctypes.POINTER(Stats)]
             L.dl_compose.argtypes = [vp, i32, vp, vp, ctypes.c_int, vp, ctypes.POINTER(Stats)]
+            L.dl_autotune.argtypes = [vp, i32, i32, ctypes.c_char_p, ctypes.c_size_t, ctypes.POINTER(ctypes.c_size_t)]
             L.dl_program_create.argtypes = [vp, ctypes.c_char_p, ctypes.POINTER(vp)]
             L.dl_program_destroy.argtypes = [vp]
             L.dl_program_set.argtypes = [vp, ctypes.c_char_p, i32, vp, ctypes.c_int]
@@ -203,7 +205,7 @@ class Context:
     def __init__(self, device: int = 0, stream=None, **cfg):
         c = Config()
         for k, v in cfg.items():
-            setattr(c, k, v)
+            setattr(c, k, v.encode() if isinstance(v, str) else v)
         h = ctypes.c_void_p()
         _check(lib().dl_create(ctypes.byref(h), int(device), ctypes.byref(c)))
         self._h = h
@@ -443,6 +445,17 @@ class Context:
         st = Stats()
         _check(lib().dl_sg_real(self._h, n, p, bptr, mem, float(eps), PATHS[path], xp, bp, ctypes.byref(st)))
         return x, out, st.as_dict()
+
+    def autotune(self, n: int, force: bool = False) -> dict:
+        """Tuned choices for problems of size n (dl_autotune): measured now, or from this context's
+        table or the cache; returns the report as a dict."""
+        import json
+        buf = ctypes.create_string_buffer(4096)
+        need = ctypes.c_size_t()
+        _check(lib().dl_autotune(self._h, int(n), 1 if force else 0, buf, len(buf), ctypes.byref(need)))
+        if need.value >= len(buf):
+            raise RuntimeError("dl_autotune report longer than expected")
+        return json.loads(buf.value.decode())
 
     def program(self, text: str) -> "Program":
         """A linear Datalog program (the class C_lin of Sec. 5) bound to this context."""
