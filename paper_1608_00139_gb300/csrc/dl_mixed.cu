@@ -694,7 +694,9 @@ dl_status tc_mixed(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &
     auto *D32 = static_cast<float *>(ws.get("mx_D", np * np * 4));
     auto *Z64 = static_cast<double *>(ws.get("mx_Z64", np * np * 8));
     auto *X64 = static_cast<double *>(ws.get("mx_X64", np * np * 8));
-    auto *T2 = static_cast<float *>(ws.get("mx_T", 2 * np * BL * 4));  // two transposed row panels
+    // transposed row panels: two slots of np rows (indexed by the absolute column) x 2 BL (the
+    // panels of a pair of steps side by side)
+    auto *T2 = static_cast<float *>(ws.get("mx_T", 2 * np * 2 * BL * 4));
     auto *Sinv = static_cast<float *>(ws.get("mx_Sinv", np * BL * 4));
     auto *SinvT = static_cast<float *>(ws.get("mx_SinvT", np * BL * 4));
     const int64_t GW = std::min<int64_t>(np, static_cast<int64_t>(kSolveGroup) * BL);
@@ -742,24 +744,40 @@ dl_status tc_mixed(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &
     const Operand opS{Sinv, np, BL, BL, 0, 0}, opST{SinvT, np, BL, BL, 0, 0};
     bool ok = true;
     std::vector<int> has_bulk(nb, -1), has_ahead(nb, -1), has_l21(nb, -1);
+    // Steps k < pair_steps go in pairs (k even, k + 1): the first step's look-ahead updates the
+    // next two block columns and rows, the second's the next one, and the pair shares one bulk
+    // update with K = 2 BL, which moves the trailing matrix half as often.  In the first part of the
+    // factorisation the bulk update, not the chain of diagonal steps, bounds each step, so the
+    // longer look-ahead costs nothing there.  Later steps are single (K = BL).
+    const TuneEntry tn = tuned(ctx, np);
+    int pair_steps = tn.mx_pairs >= 0 ? tn.mx_pairs : nb / 2;
+    pair_steps = std::max(0, std::min(pair_steps, nb - 6)) & ~1;
+    auto unit_of = [&](int k) { return k < pair_steps ? k / 2 : pair_steps / 2 + (k - pair_steps); };
+    auto half_of = [&](int k) { return k < pair_steps ? (k & 1) : 0; };
     for (int k = 0; k < nb && ok; ++k) {
         const int kb = k * BL, rem = N - kb - BL;
         if (rem <= 0) break;
-        const Operand opT{T2 + static_cast<int64_t>(k & 1) * np * BL, np, BL, BL, 0, 0};  // T = A12^T
+        const bool first = k < pair_steps && (k & 1) == 0, second = k < pair_steps && (k & 1) == 1;
+        const int hcol = half_of(k) * BL;
+        const Operand opT{T2 + static_cast<int64_t>(unit_of(k) & 1) * np * 2 * BL, np, 2 * BL, 2 * BL, 0, 0};
         // L21 = A21 S^-1 (in place: each output tile reads only its own rows of A21)
         has_l21[k] = static_cast<int>(l21.size());
         ok = tb.add(l21, EPI_STORE_F32, BL, rem, BL, BL, at(opA, kb + BL, kb), at(opST, kb, 0), A32, np, kb + BL, kb,
                     false, &flops_lu);
-        // look-ahead: block column k+1 (all rows below) and block row k+1 (columns beyond it)
+        // look-ahead: the next w block columns (all rows below) and block rows (columns beyond)
+        const int w = first ? 2 * BL : BL;
         has_ahead[k] = static_cast<int>(ahead.size());
-        ok = ok && tb.add(ahead, EPI_SUB_F32, BL, rem, BL, BL, at(opA, kb + BL, kb), opT, A32, np, kb + BL, kb + BL,
-                          false, &flops_lu);
-        if (ok && rem > BL) {
-            ok = tb.add(ahead, EPI_SUB_F32, BL, BL, rem - BL, BL, at(opA, kb + BL, kb), at(opT, BL, 0), A32, np,
-                        kb + BL, kb + 2 * BL, true, &flops_lu);
-            has_bulk[k] = static_cast<int>(bulk.size());
-            ok = ok && tb.add(bulk, EPI_SUB_F32, 256, rem - BL, rem - BL, BL, at(opA, kb + 2 * BL, kb),
-                              at(opT, BL, 0), A32, np, kb + 2 * BL, kb + 2 * BL, false, &flops_lu);
+        ok = ok && tb.add(ahead, EPI_SUB_F32, BL, rem, std::min(w, rem), BL, at(opA, kb + BL, kb),
+                          at(opT, kb + BL, hcol), A32, np, kb + BL, kb + BL, false, &flops_lu);
+        if (ok && rem > w) {
+            ok = tb.add(ahead, EPI_SUB_F32, BL, w, rem - w, BL, at(opA, kb + BL, kb), at(opT, kb + BL + w, hcol), A32,
+                        np, kb + BL, kb + BL + w, true, &flops_lu);
+            if (ok && !first) {  // the bulk update of the unit: one step (K = BL) or a pair (K = 2 BL)
+                const int kk = second ? 2 * BL : BL, k0 = second ? kb - BL : kb;
+                has_bulk[k] = static_cast<int>(bulk.size());
+                ok = tb.add(bulk, EPI_SUB_F32, 256, rem - BL, rem - BL, kk, at(opA, kb + 2 * BL, k0),
+                            at(opT, kb + 2 * BL, 0), A32, np, kb + 2 * BL, kb + 2 * BL, false, &flops_lu);
+            }
         }
     }
     // Inverses of the diagonal groups (kSolveGroup blocks each), once per factorisation.
@@ -866,7 +884,8 @@ dl_status tc_mixed(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &
     MCK(cudaStreamWaitEvent(P, ws.mx_ev[0], 0));
     MCK(cudaStreamWaitEvent(U, ws.mx_ev[0], 0));
     cudaEvent_t evT[2] = {ws.mx_ev[0], ws.mx_ev[1]}, evB[2] = {ws.mx_ev[2], ws.mx_ev[3]};
-    bool bulk_pending = false;  // the bulk update of the previous block is queued on U
+    bool bulk_pending = false;  // the bulk update of the previous unit is queued on U
+    int pending_unit = -1;
     for (int k = 0; k < nb; ++k) {
         const int64_t kb = static_cast<int64_t>(k) * BL;
         const int rem = N - static_cast<int>(kb) - BL;
@@ -874,25 +893,24 @@ dl_status tc_mixed(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &
         MCK(cudaGetLastError());
         ++launches;
         if (rem <= 0) break;
-        // L21 runs beside the bulk update of block k - 1, which leaves it `reserve` SMs
-        const bool beside_bulk = k > 0 && has_bulk[k - 1] >= 0;
-        MCK(run(l21[has_l21[k]], beside_bulk ? reserve : sms, P));
-        float *Tk = T2 + static_cast<int64_t>(k & 1) * np * BL;
-        MCK(transpose(A32 + kb * np + kb + BL, np, BL, rem, Tk, BL, P));  // T = A12^T
+        const int u = unit_of(k);
+        // L21 runs beside the bulk update of the previous unit, which leaves it `reserve` SMs
+        MCK(run(l21[has_l21[k]], bulk_pending || (k > 0 && has_bulk[k - 1] >= 0) ? reserve : sms, P));
+        float *Tk = T2 + static_cast<int64_t>(u & 1) * np * 2 * BL + (kb + BL) * 2 * BL + half_of(k) * BL;
+        MCK(transpose(A32 + kb * np + kb + BL, np, BL, rem, Tk, 2 * BL, P));  // T = A12^T, row = absolute column
         ++launches;
-        MCK(cudaEventRecord(evT[k & 1], P));
-        if (bulk_pending) MCK(cudaStreamWaitEvent(P, evB[(k - 1) & 1], 0));
-        // the look-ahead launch (one or two problems)
-        {
-            Launch L = ahead[has_ahead[k]];
-            MCK(run(L, sms, P));
+        MCK(cudaEventRecord(evT[u & 1], P));
+        if (bulk_pending && pending_unit != u) {  // the look-ahead's region was in the last bulk update
+            MCK(cudaStreamWaitEvent(P, evB[pending_unit & 1], 0));
+            bulk_pending = false;
         }
-        bulk_pending = false;
+        MCK(run(ahead[has_ahead[k]], sms, P));  // the look-ahead launch (one or two problems)
         if (has_bulk[k] >= 0) {
-            MCK(cudaStreamWaitEvent(U, evT[k & 1], 0));
+            MCK(cudaStreamWaitEvent(U, evT[u & 1], 0));
             MCK(run(bulk[has_bulk[k]], std::max(1, sms - reserve), U));
-            MCK(cudaEventRecord(evB[k & 1], U));
+            MCK(cudaEventRecord(evB[u & 1], U));
             bulk_pending = true;
+            pending_unit = u;
         }
     }
     MCK(cudaEventRecord(ws.mx_ev[0], U));  // (evT[0] is no longer needed)

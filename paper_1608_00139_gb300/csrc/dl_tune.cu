@@ -5,8 +5,9 @@
 //                 flop rate and a launch constant);
 //   sweep_rate    bytes per second of an unsaturated Iteration sweep on the CSR (the cost model's
 //                 sweep rate, instead of 6 / 3 TB/s by size);
-//   mx_reserve    SMs the mixed path's LU leaves to its critical chain (16, 32 or 48), the fastest
-//                 factorisation;
+//   mx_reserve    SMs the mixed path's LU leaves to its critical chain (16, 32 or 48), and
+//   mx_pairs      how many of its first steps go in pairs sharing one bulk update (0, a quarter,
+//                 half, three quarters or all of them): the fastest factorisation;
 //   sg_iteration  same generation on AUTO: the Iteration on bits (1) or the doubling (0), the
 //                 faster (instead of the crossover at Np = 6144).
 // Inputs are synthetic and generated on the device (an integer hash per pair): an operand with
@@ -158,8 +159,9 @@ const JVal *field(const JVal &o, const char *k) {
 std::string entry_json(const TuneEntry &e) {
     char buf[256];
     std::snprintf(buf, sizeof buf,
-                  "{\"sq_bn\": %d, \"t_sq_us\": %.3f, \"sweep_gbs\": %.3f, \"mx_reserve\": %d, \"sg_iteration\": %d}",
-                  e.sq_bn, e.t_sq * 1e6, e.sweep_rate * 1e-9, e.mx_reserve, e.sg_iteration);
+                  "{\"sq_bn\": %d, \"t_sq_us\": %.3f, \"sweep_gbs\": %.3f, \"mx_reserve\": %d, \"mx_pairs\": %d, "
+                  "\"sg_iteration\": %d}",
+                  e.sq_bn, e.t_sq * 1e6, e.sweep_rate * 1e-9, e.mx_reserve, e.mx_pairs, e.sg_iteration);
     return buf;
 }
 
@@ -173,6 +175,8 @@ bool entry_from(const JVal &o, TuneEntry *e) {
     e->sweep_rate = c->num * 1e9;
     e->mx_reserve = std::max(1, static_cast<int>(d->num));
     e->sg_iteration = static_cast<int>(f->num);
+    const JVal *g = field(o, "mx_pairs");  // absent in older caches: the default
+    e->mx_pairs = g ? static_cast<int>(g->num) : -1;
     e->measured = true;
     return true;
 }
@@ -399,12 +403,8 @@ dl_status autotune_bucket(dl_ctx *ctx, Workspace &ws, cudaStream_t s, int32_t n_
         std::lock_guard<std::mutex> lk(ctx->tune.mu);
         ctx->tune.by_bucket[b] = x;
     };
-    if (np >= 2048) {
-        double best_f = 1e30;
-        const int chosen = e.mx_reserve;
-        for (int r : {16, 32, 48}) {
-            TuneEntry x = e;
-            x.mx_reserve = r;
+    if (np >= 2048) {  // coordinate search: the reserve at the default pairing, then the pairing
+        auto factor_ms = [&](const TuneEntry &x, double *ms) -> dl_status {
             set_entry(x);
             SolveArgs a;
             a.n = n;
@@ -412,18 +412,36 @@ dl_status autotune_bucket(dl_ctx *ctx, Workspace &ws, cudaStream_t s, int32_t n_
             a.mem = DL_MEM_DEVICE;
             a.path = DL_PATH_MIXED;
             a.out_bits = ob;
-            double tf = 0;
             for (int rep = 0; rep < 2; ++rep) {  // the second run's factorisation time
                 dl_stats st{};
-                if ((rc = solve_tc(ctx, ws, s, a, &st))) return rc;
-                tf = st.ms_factor;
+                dl_status r2 = solve_tc(ctx, ws, s, a, &st);
+                if (r2) return r2;
+                *ms = st.ms_factor;
             }
-            if (tf < best_f) {
-                best_f = tf;
+            return DL_OK;
+        };
+        double best_f = 1e30;
+        for (int r : {16, 32, 48}) {
+            TuneEntry x = e;
+            x.mx_reserve = r;
+            double ms = 0;
+            if ((rc = factor_ms(x, &ms))) return rc;
+            if (ms < best_f) {
+                best_f = ms;
                 e.mx_reserve = r;
             }
         }
-        (void)chosen;
+        const int nb = np / 128;
+        for (int pairs : {0, nb / 4, 3 * nb / 4, nb}) {  // nb / 2 (the default) is measured above
+            TuneEntry x = e;
+            x.mx_pairs = pairs;
+            double ms = 0;
+            if ((rc = factor_ms(x, &ms))) return rc;
+            if (ms < best_f) {
+                best_f = ms;
+                e.mx_pairs = pairs;
+            }
+        }
     }
     {
         auto *P = static_cast<uint8_t *>(ws.get("tn_e", static_cast<size_t>(n) * n));  // reuses E's bytes
