@@ -621,9 +621,13 @@ dl_status mixed_streams(Workspace &ws) {
     if (ws.mx_stream[0]) return DL_OK;
     int least = 0, greatest = 0;
     MCK(cudaDeviceGetStreamPriorityRange(&least, &greatest));
+    // the chain first, then the bulk update, then the inverse's early groups (which fill the SMs
+    // the chain-bound end of the factorisation leaves idle)
     MCK(cudaStreamCreateWithPriority(&ws.mx_stream[0], cudaStreamNonBlocking, greatest));
-    MCK(cudaStreamCreateWithPriority(&ws.mx_stream[1], cudaStreamNonBlocking, least));
+    MCK(cudaStreamCreateWithPriority(&ws.mx_stream[1], cudaStreamNonBlocking, std::max(greatest, least - 1)));
+    MCK(cudaStreamCreateWithPriority(&ws.mx_stream[2], cudaStreamNonBlocking, least));
     for (auto &e : ws.mx_ev) MCK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    for (auto &e : ws.mx_gev) MCK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     return DL_OK;
 }
 
@@ -687,7 +691,7 @@ dl_status tc_mixed(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &
     int launches = 0;
     dl_status rc = mixed_streams(ws);
     if (rc) return rc;
-    cudaStream_t P = ws.mx_stream[0], U = ws.mx_stream[1];
+    cudaStream_t P = ws.mx_stream[0], U = ws.mx_stream[1], V = ws.mx_stream[2];
     auto *A32 = static_cast<float *>(ws.get("mx_A", np * np * 4));
     auto *W32 = static_cast<float *>(ws.get("mx_W", np * np * 4));   // Z = A^-T, then R
     auto *Wt = static_cast<float *>(ws.get("mx_Wt", np * np * 4));   // W = A^-1
@@ -738,7 +742,7 @@ dl_status tc_mixed(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &
 
     // ---- GEMM table ---------------------------------------------------------------------
     Table tb;
-    std::vector<Launch> l21, ahead, bulk, ginv, wfwd, wbwd, refine;
+    std::vector<Launch> l21, ahead, bulk, wfwd, wbwd, refine;
     double flops_lu = 0, flops_w = 0, flops_ref = 0;
     const Operand opA{A32, np, np, np, 0, 0};
     const Operand opS{Sinv, np, BL, BL, 0, 0}, opST{SinvT, np, BL, BL, 0, 0};
@@ -789,37 +793,27 @@ dl_status tc_mixed(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &
     const Operand opGL{GL, np, GW, GW, 0, 0}, opGU{GU, np, GW, GW, 0, 0};
     const Operand opTg{Tg, np, GW, GW, 0, 0};
     const int ng = (nb + kSolveGroup - 1) / kSolveGroup;
-    for (int kl = 0; kl < kSolveGroup && ok; ++kl) {
-        bool first = true;  // step kl needs step kl - 1: a launch of its own
-        for (int g = 0; g < ng && ok; ++g) {
-            const int g0 = g * kSolveGroup, g1 = std::min(nb, g0 + kSolveGroup), gs = g0 * BL, ge = g1 * BL,
-                      w = ge - gs, kb = gs + kl * BL;
-            if (g0 + kl < g1 && kb + BL < ge) {
-                ok = tb.add(ginv, EPI_SUB_F32, BL, w, ge - kb - BL, BL, at(opYL, gs, kl * BL), at(opA, kb + BL, kb), YL,
-                            GW, gs, (kl + 1) * BL, !first, &flops_lu);
-                first = false;
-            }
-        }
+    if (ng > static_cast<int>(sizeof(ws.mx_gev) / sizeof(ws.mx_gev[0]))) {
+        set_error("mixed path: n = %d has more solve groups than supported", n);
+        return DL_EINVAL;
     }
-    for (int kl = kSolveGroup - 1; kl >= 0 && ok; --kl) {
-        bool first = true;
-        for (int g = 0; g < ng && ok; ++g) {  // Y_k = Y_k S_kk^-T (in place: N = BL)
-            const int g0 = g * kSolveGroup, g1 = std::min(nb, g0 + kSolveGroup), gs = g0 * BL, w = (g1 - g0) * BL;
-            if (g0 + kl < g1) {
-                ok = tb.add(ginv, EPI_STORE_F32, BL, w, BL, BL, at(opYU, gs, kl * BL), at(opS, gs + kl * BL, 0), YU,
-                            GW, gs, kl * BL, !first, &flops_lu);
-                first = false;
-            }
+    std::vector<std::vector<Launch>> ginv(ng);  // one list per group (a group's inverse runs once its LU is final)
+    for (int g = 0; g < ng && ok; ++g) {
+        const int g0 = g * kSolveGroup, g1 = std::min(nb, g0 + kSolveGroup), gs = g0 * BL, ge = g1 * BL, w = ge - gs;
+        for (int kl = 0; g0 + kl < g1 && ok; ++kl) {
+            const int kb = gs + kl * BL;
+            if (kb + BL < ge)
+                ok = tb.add(ginv[g], EPI_SUB_F32, BL, w, ge - kb - BL, BL, at(opYL, gs, kl * BL), at(opA, kb + BL, kb),
+                            YL, GW, gs, (kl + 1) * BL, false, &flops_lu);
         }
-        first = true;
-        for (int g = 0; g < ng && ok; ++g) {  // Y_{<k} -= Y_k U_{<k,k}^T
-            const int g0 = g * kSolveGroup, g1 = std::min(nb, g0 + kSolveGroup), gs = g0 * BL, w = (g1 - g0) * BL,
-                      kb = gs + kl * BL;
-            if (g0 + kl < g1 && kb > gs) {
-                ok = tb.add(ginv, EPI_SUB_F32, BL, w, kb - gs, BL, at(opYU, gs, kl * BL), at(opA, gs, kb), YU, GW, gs, 0,
-                            !first, &flops_lu);
-                first = false;
-            }
+        for (int kl = g1 - g0 - 1; kl >= 0 && ok; --kl) {
+            const int kb = gs + kl * BL;
+            // Y_k = Y_k S_kk^-T (in place: N = BL), then Y_{<k} -= Y_k U_{<k,k}^T
+            ok = tb.add(ginv[g], EPI_STORE_F32, BL, w, BL, BL, at(opYU, gs, kl * BL), at(opS, kb, 0), YU, GW, gs,
+                        kl * BL, false, &flops_lu);
+            if (ok && kb > gs)
+                ok = tb.add(ginv[g], EPI_SUB_F32, BL, w, kb - gs, BL, at(opYU, gs, kl * BL), at(opA, gs, kb), YU, GW, gs,
+                            0, false, &flops_lu);
         }
     }
     // W: the solves on Z = I.  Forward by groups, Z_g = Z_g L_gg^-T (into Tg, copied back) and
@@ -883,6 +877,45 @@ dl_status tc_mixed(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &
     MCK(cudaEventRecord(ws.mx_ev[0], s));  // the table and A are ready on s
     MCK(cudaStreamWaitEvent(P, ws.mx_ev[0], 0));
     MCK(cudaStreamWaitEvent(U, ws.mx_ev[0], 0));
+    MCK(cudaStreamWaitEvent(V, ws.mx_ev[0], 0));
+    // The inverse (on V, least priority): the group inverses and the forward solve of group g
+    // start as soon as the LU's steps of group g are done (its L and U blocks, and L below it, are
+    // final then: later steps write only block rows and columns beyond the group), so they fill
+    // SMs the chain-bound end of the factorisation leaves idle; the backward solve needs all of U.
+    MCK(cudaMemsetAsync(YL, 0, np * GW * 4, V));
+    MCK(cudaMemsetAsync(YU, 0, np * GW * 4, V));
+    group_identity_kernel<<<static_cast<unsigned>((np + 255) / 256), 256, 0, V>>>(YL, YU, N, static_cast<int>(GW));
+    MCK(cudaGetLastError());
+    MCK(cudaMemsetAsync(W32, 0, np * np * 4, V));
+    identity_kernel<<<static_cast<unsigned>((np + 255) / 256), 256, 0, V>>>(W32, N);
+    MCK(cudaGetLastError());
+    launches += 2;
+    auto run_steps = [&](const std::vector<Step> &steps, const std::vector<Launch> &list, int gs_only) -> cudaError_t {
+        for (const Step &sp : steps) {
+            if (gs_only >= 0 && sp.gs != gs_only) continue;
+            cudaError_t e;
+            if (sp.launch >= 0) {
+                if ((e = run(list[sp.launch], sms, V)) != cudaSuccess) return e;
+            } else if ((e = cudaMemcpy2DAsync(W32 + sp.gs, np * 4, Tg, GW * 4, static_cast<size_t>(sp.w) * 4, sp.rows,
+                                              cudaMemcpyDeviceToDevice, V)) != cudaSuccess) {
+                return e;
+            }
+        }
+        return cudaSuccess;
+    };
+    int groups_started = 0;
+    auto inverse_group = [&](int g) -> cudaError_t {  // on V, after the group's LU steps
+        cudaError_t e;
+        for (const Launch &L : ginv[g])
+            if ((e = run(L, sms, V)) != cudaSuccess) return e;
+        const int64_t gs = static_cast<int64_t>(g) * GW;
+        const int w = static_cast<int>(std::min<int64_t>(GW, np - gs));
+        if ((e = transpose(YL + gs * GW, GW, w, w, GL + gs * GW, GW, V)) != cudaSuccess) return e;
+        if ((e = transpose(YU + gs * GW, GW, w, w, GU + gs * GW, GW, V)) != cudaSuccess) return e;
+        launches += 2;
+        groups_started = g + 1;
+        return run_steps(fwd_steps, wfwd, static_cast<int>(gs));
+    };
     cudaEvent_t evT[2] = {ws.mx_ev[0], ws.mx_ev[1]}, evB[2] = {ws.mx_ev[2], ws.mx_ev[3]};
     bool bulk_pending = false;  // the bulk update of the previous unit is queued on U
     int pending_unit = -1;
@@ -896,6 +929,12 @@ dl_status tc_mixed(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &
         const int u = unit_of(k);
         // L21 runs beside the bulk update of the previous unit, which leaves it `reserve` SMs
         MCK(run(l21[has_l21[k]], bulk_pending || (k > 0 && has_bulk[k - 1] >= 0) ? reserve : sms, P));
+        if ((k + 1) % kSolveGroup == 0 && k + 1 < nb) {  // group (k + 1) / kSolveGroup - 1 is final
+            const int g = (k + 1) / kSolveGroup - 1;
+            MCK(cudaEventRecord(ws.mx_gev[g], P));
+            MCK(cudaStreamWaitEvent(V, ws.mx_gev[g], 0));
+            MCK(inverse_group(g));
+        }
         float *Tk = T2 + static_cast<int64_t>(u & 1) * np * 2 * BL + (kb + BL) * 2 * BL + half_of(k) * BL;
         MCK(transpose(A32 + kb * np + kb + BL, np, BL, rem, Tk, 2 * BL, P));  // T = A12^T, row = absolute column
         ++launches;
@@ -918,42 +957,17 @@ dl_status tc_mixed(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &
     MCK(cudaEventRecord(ws.mx_ev[1], P));
     MCK(cudaStreamWaitEvent(s, ws.mx_ev[1], 0));
 
-    // group inverses: Y = I on each group's rows, the grouped steps, then G = Y^T per group
-    ph.to("mixed:group-inverses");
-    MCK(cudaMemsetAsync(YL, 0, np * GW * 4, s));
-    MCK(cudaMemsetAsync(YU, 0, np * GW * 4, s));
-    group_identity_kernel<<<static_cast<unsigned>((np + 255) / 256), 256, 0, s>>>(YL, YU, N, static_cast<int>(GW));
-    MCK(cudaGetLastError());
-    ++launches;
-    for (const Launch &L : ginv) MCK(run(L, sms, s));
-    for (int64_t gs = 0; gs < np; gs += GW) {
-        const int w = static_cast<int>(std::min<int64_t>(GW, np - gs));
-        MCK(transpose(YL + gs * GW, GW, w, w, GL + gs * GW, GW, s));
-        MCK(transpose(YU + gs * GW, GW, w, w, GU + gs * GW, GW, s));
-        launches += 2;
-    }
     MCK(cudaEventRecord(ev[5], s));
 
-    // ---- W = A^-1 ------------------------------------------------------------------------
+    // ---- W = A^-1: the remaining groups' inverses and forward solves, then the backward solve --
     ph.to("mixed:inverse");
-    MCK(cudaMemsetAsync(W32, 0, np * np * 4, s));
-    identity_kernel<<<static_cast<unsigned>((np + 255) / 256), 256, 0, s>>>(W32, N);
-    MCK(cudaGetLastError());
+    MCK(cudaStreamWaitEvent(V, ws.mx_ev[1], 0));  // the whole LU
+    for (int g = groups_started; g < ng; ++g) MCK(inverse_group(g));
+    MCK(run_steps(bwd_steps, wbwd, -1));
+    MCK(transpose(W32, np, N, N, Wt, np, V));  // W = (A^-T)^T
     ++launches;
-    for (int pass = 0; pass < 2; ++pass) {
-        const std::vector<Step> &steps = pass == 0 ? fwd_steps : bwd_steps;
-        const std::vector<Launch> &list = pass == 0 ? wfwd : wbwd;
-        for (const Step &sp : steps) {
-            if (sp.launch >= 0) {
-                MCK(run(list[sp.launch], sms, s));
-            } else {
-                MCK(cudaMemcpy2DAsync(W32 + sp.gs, np * 4, Tg, GW * 4, static_cast<size_t>(sp.w) * 4, sp.rows,
-                                      cudaMemcpyDeviceToDevice, s));
-            }
-        }
-    }
-    MCK(transpose(W32, np, N, N, Wt, np, s));  // W = (A^-T)^T
-    ++launches;
+    MCK(cudaEventRecord(ws.mx_ev[2], V));
+    MCK(cudaStreamWaitEvent(s, ws.mx_ev[2], 0));
     MCK(cudaEventRecord(ev[6], s));
 
     // ---- refinement from Z = 0 -------------------------------------------------------------
@@ -1127,7 +1141,9 @@ dl_status tc_mixed(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &
         st->iters = std::max(products - 1, 0);  // refinement steps after the first product (the solve)
         st->final_resid = need_x ? rmax / eps : -1.0;  // -1: no residual was formed (model only)
         st->gemm_flops = flops_lu + flops_w + flops_ref * gemm_products;
-        st->gemm_launches = static_cast<int>(l21.size() + ahead.size() + bulk.size() + ginv.size() + wfwd.size() +
+        size_t ginv_n = 0;
+        for (const auto &gl : ginv) ginv_n += gl.size();
+        st->gemm_launches = static_cast<int>(l21.size() + ahead.size() + bulk.size() + ginv_n + wfwd.size() +
                                              wbwd.size()) + gemm_products;
         float t1 = 0, t2 = 0, t3 = 0;
         cudaEventElapsedTime(&t1, ev[4], ev[5]);

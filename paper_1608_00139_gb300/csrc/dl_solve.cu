@@ -2169,6 +2169,9 @@ void Workspace::release() {
         if (x) cudaEventDestroy(x);
     for (auto &x : mx_stream)
         if (x) cudaStreamDestroy(x);
+    for (auto &x : mx_gev)
+        if (x) cudaEventDestroy(x);
+    for (auto &x : mx_gev) x = nullptr;
     for (auto &x : mx_ev) x = nullptr;
     for (auto &x : mx_stream) x = nullptr;
     for (auto &x : ev) x = nullptr;
