@@ -85,19 +85,46 @@ cudaError_t transpose(const T *src, int64_t lds, int rows, int cols, T *dst, int
 // registers: rows r0 .. r0 + 7 (r0 = 16 warp + 8 (lane / 16)), columns c0 .. c0 + 7
 // (c0 = 8 (lane mod 16)).  Step k (p = 1 / S_kk, r = row k, c = column k before the step):
 //     S_ij -= c_i r_j p (i, j != k),   S_kj = r_j p,   S_ik = -c_i p,   S_kk = p.
-// The owners of row k and of column k publish them through shared memory (two buffers, so one
-// barrier per step suffices: a buffer is rewritten two steps later, after every thread has
-// passed the barrier between).  A is strictly diagonally dominant by rows and so is every
+// Two steps per barrier: the owners of rows k, k + 1 and of columns k, k + 1 publish them through
+// shared memory (two buffers, so one barrier per pair suffices: a buffer is rewritten two pairs
+// later, after every thread has passed the barrier between); every thread applies step k to its
+// tile and forms, from the same published values, row and column k + 1 as step k leaves them,
+//     c'_i = c1_i - c_i S_{k,k+1} p  (c'_k = S_{k,k+1} p),   r'_j = r1_j - S_{k+1,k} r_j p  (r'_k = -S_{k+1,k} p),
+//     pivot S_{k+1,k+1} - S_{k+1,k} S_{k,k+1} p,
+// then applies step k + 1 with them.  A is strictly diagonally dominant by rows and so is every
 // Schur complement, hence every pivot is positive; a pivot that is not sets ST_BAD_INPUT.
 // Writes S^-1 and S^-T (BL x BL, row-major).
 constexpr int kDiagThreads = 256;
+
+// One elimination step on a thread's tile: the tile's rows kk / columns kk hold the pivot row /
+// column when ro / co; c = the pivot column at the tile's rows, rp = the pivot row at the tile's
+// columns times p = 1 / pivot.
+__device__ __forceinline__ void gj_step(float (&a)[8][8], int kk, bool ro, bool co, const float (&c)[8],
+                                        const float (&rp)[8], float p) {
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+            const float upd = fmaf(-c[i], rp[j], a[i][j]);
+            if (i == kk && j == kk) {
+                a[i][j] = ro && co ? p : ro ? rp[j] : co ? -c[i] * p : upd;
+            } else if (i == kk) {
+                a[i][j] = ro ? rp[j] : upd;
+            } else if (j == kk) {
+                a[i][j] = co ? -c[i] * p : upd;
+            } else {
+                a[i][j] = upd;
+            }
+        }
+    }
+}
 
 __global__ void __launch_bounds__(kDiagThreads) diag_inv_kernel(const float *__restrict__ A, int64_t lda,
                                                                 float *__restrict__ Sinv, float *__restrict__ SinvT,
                                                                 int *status) {
     static_assert(BL == 128 && kDiagThreads == 256, "8 x 8 tiles of a 128 x 128 block");
-    __shared__ __align__(16) float rowbuf[2][BL];
-    __shared__ __align__(16) float colbuf[2][BL];
+    __shared__ __align__(16) float rowbuf[2][2][BL];  // [buffer][row k, row k + 1][column]
+    __shared__ __align__(16) float colbuf[2][2][BL];  // [buffer][column k, column k + 1][row]
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
     const int r0 = 16 * warp + 8 * (lane >> 4);
     const int c0 = 8 * (lane & 15);
@@ -112,50 +139,59 @@ __global__ void __launch_bounds__(kDiagThreads) diag_inv_kernel(const float *__r
     bool bad = false;
 #pragma unroll 1
     for (int kb = 0; kb < BL; kb += 8) {
-        const bool row_owner = r0 == kb;  // rows kb .. kb + 7 are this thread's
-        const bool col_owner = c0 == kb;  // columns kb .. kb + 7 are this thread's
+        const bool ro = r0 == kb;  // rows kb .. kb + 7 are this thread's
+        const bool co = c0 == kb;  // columns kb .. kb + 7 are this thread's
 #pragma unroll
-        for (int kk = 0; kk < 8; ++kk) {
-            const int k = kb + kk, buf = k & 1;
-            if (row_owner) {
-                *reinterpret_cast<float4 *>(&rowbuf[buf][c0]) = make_float4(a[kk][0], a[kk][1], a[kk][2], a[kk][3]);
-                *reinterpret_cast<float4 *>(&rowbuf[buf][c0 + 4]) = make_float4(a[kk][4], a[kk][5], a[kk][6], a[kk][7]);
-            }
-            if (col_owner) {
-                *reinterpret_cast<float4 *>(&colbuf[buf][r0]) = make_float4(a[0][kk], a[1][kk], a[2][kk], a[3][kk]);
-                *reinterpret_cast<float4 *>(&colbuf[buf][r0 + 4]) = make_float4(a[4][kk], a[5][kk], a[6][kk], a[7][kk]);
-            }
-            __syncthreads();
-            const float piv = rowbuf[buf][k];
-            const float p = __fdividef(1.0f, piv);  // within 2 ulp: S^-1 only preconditions the refinement
-            bad |= !(piv > 0.0f) || !isfinite(p);
-            float c[8], rp[8];
-            {
-                const float4 c_lo = *reinterpret_cast<const float4 *>(&colbuf[buf][r0]);
-                const float4 c_hi = *reinterpret_cast<const float4 *>(&colbuf[buf][r0 + 4]);
-                const float4 r_lo = *reinterpret_cast<const float4 *>(&rowbuf[buf][c0]);
-                const float4 r_hi = *reinterpret_cast<const float4 *>(&rowbuf[buf][c0 + 4]);
-                c[0] = c_lo.x, c[1] = c_lo.y, c[2] = c_lo.z, c[3] = c_lo.w;
-                c[4] = c_hi.x, c[5] = c_hi.y, c[6] = c_hi.z, c[7] = c_hi.w;
-                rp[0] = r_lo.x * p, rp[1] = r_lo.y * p, rp[2] = r_lo.z * p, rp[3] = r_lo.w * p;
-                rp[4] = r_hi.x * p, rp[5] = r_hi.y * p, rp[6] = r_hi.z * p, rp[7] = r_hi.w * p;
-            }
+        for (int kk = 0; kk < 8; kk += 2) {
+            const int k = kb + kk, buf = (k >> 1) & 1;
+            if (ro) {
 #pragma unroll
-            for (int i = 0; i < 8; ++i) {
-#pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    const float upd = fmaf(-c[i], rp[j], a[i][j]);
-                    if (i == kk && j == kk) {
-                        a[i][j] = row_owner && col_owner ? p : row_owner ? rp[j] : col_owner ? -c[i] * p : upd;
-                    } else if (i == kk) {
-                        a[i][j] = row_owner ? rp[j] : upd;
-                    } else if (j == kk) {
-                        a[i][j] = col_owner ? -c[i] * p : upd;
-                    } else {
-                        a[i][j] = upd;
-                    }
+                for (int h = 0; h < 2; ++h) {
+                    *reinterpret_cast<float4 *>(&rowbuf[buf][h][c0]) =
+                        make_float4(a[kk + h][0], a[kk + h][1], a[kk + h][2], a[kk + h][3]);
+                    *reinterpret_cast<float4 *>(&rowbuf[buf][h][c0 + 4]) =
+                        make_float4(a[kk + h][4], a[kk + h][5], a[kk + h][6], a[kk + h][7]);
                 }
             }
+            if (co) {
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    *reinterpret_cast<float4 *>(&colbuf[buf][h][r0]) =
+                        make_float4(a[0][kk + h], a[1][kk + h], a[2][kk + h], a[3][kk + h]);
+                    *reinterpret_cast<float4 *>(&colbuf[buf][h][r0 + 4]) =
+                        make_float4(a[4][kk + h], a[5][kk + h], a[6][kk + h], a[7][kk + h]);
+                }
+            }
+            __syncthreads();
+            const float s00 = rowbuf[buf][0][k], s01 = rowbuf[buf][0][k + 1];
+            const float s10 = rowbuf[buf][1][k], s11 = rowbuf[buf][1][k + 1];
+            const float p = __fdividef(1.0f, s00);  // within 2 ulp: S^-1 only preconditions the refinement
+            float c[8], c1[8], r[8], r1[8], rp[8];
+#pragma unroll
+            for (int q = 0; q < 8; q += 4) {
+                const float4 cx = *reinterpret_cast<const float4 *>(&colbuf[buf][0][r0 + q]);
+                const float4 cy = *reinterpret_cast<const float4 *>(&colbuf[buf][1][r0 + q]);
+                const float4 rx = *reinterpret_cast<const float4 *>(&rowbuf[buf][0][c0 + q]);
+                const float4 ry = *reinterpret_cast<const float4 *>(&rowbuf[buf][1][c0 + q]);
+                c[q] = cx.x, c[q + 1] = cx.y, c[q + 2] = cx.z, c[q + 3] = cx.w;
+                c1[q] = cy.x, c1[q + 1] = cy.y, c1[q + 2] = cy.z, c1[q + 3] = cy.w;
+                r[q] = rx.x, r[q + 1] = rx.y, r[q + 2] = rx.z, r[q + 3] = rx.w;
+                r1[q] = ry.x, r1[q + 1] = ry.y, r1[q + 2] = ry.z, r1[q + 3] = ry.w;
+            }
+#pragma unroll
+            for (int j = 0; j < 8; ++j) rp[j] = r[j] * p;
+            gj_step(a, kk, ro, co, c, rp, p);  // step k
+            // row and column k + 1 as step k leaves them, and the next pivot
+            const float s01p = s01 * p;
+            const float piv2 = fmaf(-s10, s01p, s11);
+            const float p2 = __fdividef(1.0f, piv2);
+            bad |= !(s00 > 0.0f) || !isfinite(p) || !(piv2 > 0.0f) || !isfinite(p2);
+            float c2[8], rp2[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) c2[i] = ro && i == kk ? s01p : fmaf(-c[i], s01p, c1[i]);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) rp2[j] = (co && j == kk ? -s10 * p : fmaf(-s10, rp[j], r1[j])) * p2;
+            gj_step(a, kk + 1, ro, co, c2, rp2, p2);  // step k + 1
         }
     }
     if (bad) atomicOr(status, ST_BAD_INPUT);
