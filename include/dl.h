@@ -312,8 +312,10 @@ DL_API dl_status dl_compose(dl_ctx *ctx, int32_t n, const uint8_t *R1, const uin
  * squaring, the bytes per second of an unsaturated Iteration sweep (the AUTO path's cost model
  * between sweeps and squarings), the SMs the mixed path's LU leaves to its critical chain (16, 32
  * or 48) and how many of its steps go in pairs sharing one bulk update, and whether same
- * generation on AUTO takes the Iteration on bits or the doubling.  The inputs are synthetic
- * (generated on the device).  Every choice leaves every model exact; only
+ * generation on AUTO takes the Iteration on bits or the doubling (when one is faster on both a
+ * random forest and a heavy-tailed DAG; sg_iteration -1: the fixed size rule).  The sweep rate is
+ * the faster of an ER digraph's and a heavy-tailed DAG's.  The inputs are synthetic (generated
+ * on the device).  Every choice leaves every model exact; only
  * speed depends on it.  flags: 1 = measure again even if the bucket is known (from this context
  * or the cache).  report (cap bytes, may be NULL when cap is 0; *len gets the full length): JSON
  * {"key", "bucket", "source": "measured" | "cache" | "defaults ...", "entry": {sq_bn, t_sq_us,

@@ -4,14 +4,19 @@
 //   t_sq          seconds per squaring at that width (the AUTO path's cost model, instead of a
 //                 flop rate and a launch constant);
 //   sweep_rate    bytes per second of an unsaturated Iteration sweep on the CSR (the cost model's
-//                 sweep rate, instead of 6 / 3 TB/s by size);
+//                 sweep rate, instead of 6 / 3 TB/s by size): the faster of an ER digraph's and a
+//                 heavy-tailed DAG's;
 //   mx_reserve    SMs the mixed path's LU leaves to its critical chain (16, 32 or 48), and
 //   mx_pairs      how many of its first steps go in pairs sharing one bulk update (0, a quarter,
 //                 half, three quarters or all of them): the fastest factorisation;
-//   sg_iteration  same generation on AUTO: the Iteration on bits (1) or the doubling (0), the
-//                 faster (instead of the crossover at Np = 6144).
+//   sg_iteration  same generation on AUTO: the Iteration on bits (1) or the doubling (0) where the
+//                 same one is faster on a random forest and on a heavy-tailed DAG, else the
+//                 crossover at Np = 6144 (-1).
 // Inputs are synthetic and generated on the device (an integer hash per pair): an operand with
-// about half ones, an ER digraph of mean degree 8, a random forest.  The table lives in the
+// about half ones, an ER digraph of mean degree 8, a random forest, and a DAG shaped like
+// preferential attachment (Zipf-like out-degrees, links skewed toward the earliest nodes).  A
+// choice measured on one kind of graph can be wrong for another (a route tuned on forests alone
+// doubled the serving stream's p99), hence two kinds where the structure matters.  The table lives in the
 // context; with a cache path it is read at dl_create and written after every tuning run, as JSON
 // keyed by "<GPU name>|<driver version>|<bucket>", so another process on the same kind of GPU
 // and driver reuses it.
@@ -73,6 +78,23 @@ __global__ void forest_bytes_kernel(uint8_t *P, int n, uint64_t seed) {
     const uint64_t h = hash64(seed + static_cast<uint64_t>(i));
     if (h % 20 == 0) return;
     P[static_cast<int64_t>(i) * n + static_cast<int64_t>((h >> 8) % static_cast<uint64_t>(i))] = 1;
+}
+
+// A DAG shaped like preferential attachment (the serving workload): node i >= 1 links to
+// k = min(i, floor(1 / u)) earlier nodes (a Zipf(2)-like out-degree, heavy-tailed rows; at most
+// 4096), each j = floor(i v^3), skewed toward the earliest nodes (hubs).  E zeroed by the caller.
+__global__ void skewed_dag_kernel(uint8_t *E, int n, uint64_t seed) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n || i == 0) return;
+    const double u = static_cast<double>((hash64(seed + static_cast<uint64_t>(i)) >> 11) + 1) * 0x1.0p-53;
+    const int k = static_cast<int>(fmin(fmin(static_cast<double>(i), 4096.0), fmax(1.0, floor(1.0 / u))));
+    uint8_t *row = E + static_cast<int64_t>(i) * n;
+    for (int t = 0; t < k; ++t) {
+        const double v =
+            static_cast<double>(hash64((seed ^ 0x9E3779B97F4A7C15ull) + (static_cast<uint64_t>(i) << 24) + t) >> 11) *
+            0x1.0p-53;
+        row[static_cast<int>(fmin(static_cast<double>(i - 1), floor(static_cast<double>(i) * v * v * v)))] = 1;
+    }
 }
 
 unsigned blocks_for(int64_t count) { return static_cast<unsigned>((count + 255) / 256); }
@@ -356,43 +378,56 @@ dl_status autotune_bucket(dl_ctx *ctx, Workspace &ws, cudaStream_t s, int32_t n_
         }
     }
     e.t_sq = best;
-    // 2. an unsaturated Iteration sweep (the emission E M, which changes nothing in place)
+    // 2. an unsaturated Iteration sweep (the emission E M, which changes nothing in place), on an
+    // ER digraph of mean degree 8 and on the skewed DAG (heavy-tailed rows); the faster rate is
+    // kept, so that the cost model does not square a graph whose sweeps are cheap
     auto *E = static_cast<uint8_t *>(ws.get("tn_e", static_cast<size_t>(n) * n));
+    auto *D = static_cast<uint8_t *>(ws.get("tn_d", static_cast<size_t>(n) * n));
     auto *cnt = static_cast<int *>(ws.get("tn_cnt", (np + 1) * 4));
     auto *ptr = static_cast<int *>(ws.get("tn_ptr", (np + 1) * 4));
     auto *uoff = static_cast<int *>(ws.get("tn_units", (np + 1) * 4));
     auto *colmask = static_cast<uint64_t *>(ws.get("tn_colmask", wp * 8));
     auto *M = static_cast<uint64_t *>(ws.get("tn_m", np * wp * 8));
-    if (!E || !cnt || !ptr || !uoff || !colmask || !M) {
+    if (!E || !D || !cnt || !ptr || !uoff || !colmask || !M) {
         set_error("autotune: device allocation failed");
         return DL_ENOMEM;
     }
     er_bytes_kernel<<<blocks_for(static_cast<int64_t>(n) * n), 256, 0, s>>>(E, n, 8.0, 0xe5eedull);
     TCK(cudaGetLastError());
-    TCK(cudaMemsetAsync(ws.scal, 0, kScalars * sizeof(unsigned long long), s));
-    TCK(cudaMemsetAsync(colmask, 0, wp * 8, s));
-    TCK(csr_pack_checked(E, n, np, wp, cnt, ptr, M, ws.scal + SC_DMAX, ws.scal + SC_NNZ, ws.scal + SC_COUNT0,
-                         ws.status, colmask, s));
-    unsigned long long hs[2] = {0, 0};
-    TCK(cudaMemcpyAsync(hs, ws.scal + SC_DMAX, sizeof hs, cudaMemcpyDeviceToHost, s));  // dmax, nnz
-    TCK(cudaStreamSynchronize(s));
-    auto *col = static_cast<int *>(ws.get("tn_col", std::max<size_t>(hs[1] + static_cast<size_t>(n), 1) * 4));
-    if (!col) {
-        set_error("autotune: device allocation failed");
-        return DL_ENOMEM;
-    }
-    TCK(csr_fill_from_bits(M, n, wp, ptr, col, s));
-    TCK(sweep_units(ptr, n, cnt, uoff, s));
-    double tsw = 0;
-    dl_status rc = time_median(s, ea, eb, [&]() -> dl_status {
-        int launches = 0;
-        TCK(bits_sweep_csr(ptr, col, uoff, n, M, bits, wp, 0, ws.scal + SC_VIOL, ws.scal + SC_ONES, &launches, s,
-                           static_cast<int>(hs[0])));
+    TCK(cudaMemsetAsync(D, 0, static_cast<size_t>(n) * n, s));
+    skewed_dag_kernel<<<blocks_for(n), 256, 0, s>>>(D, n, 0xda9ull);
+    TCK(cudaGetLastError());
+    dl_status rc = DL_OK;
+    auto sweep_rate = [&](const uint8_t *G, double *rate) -> dl_status {
+        TCK(cudaMemsetAsync(ws.scal, 0, kScalars * sizeof(unsigned long long), s));
+        TCK(cudaMemsetAsync(colmask, 0, wp * 8, s));
+        TCK(csr_pack_checked(G, n, np, wp, cnt, ptr, M, ws.scal + SC_DMAX, ws.scal + SC_NNZ, ws.scal + SC_COUNT0,
+                             ws.status, colmask, s));
+        unsigned long long hs[2] = {0, 0};
+        TCK(cudaMemcpyAsync(hs, ws.scal + SC_DMAX, sizeof hs, cudaMemcpyDeviceToHost, s));  // dmax, nnz
+        TCK(cudaStreamSynchronize(s));
+        auto *col = static_cast<int *>(ws.get("tn_col", std::max<size_t>(hs[1] + static_cast<size_t>(n), 1) * 4));
+        if (!col) {
+            set_error("autotune: device allocation failed");
+            return DL_ENOMEM;
+        }
+        TCK(csr_fill_from_bits(M, n, wp, ptr, col, s));
+        TCK(sweep_units(ptr, n, cnt, uoff, s));
+        double tsw = 0;
+        dl_status r2 = time_median(s, ea, eb, [&]() -> dl_status {
+            int launches = 0;
+            TCK(bits_sweep_csr(ptr, col, uoff, n, M, bits, wp, 0, ws.scal + SC_VIOL, ws.scal + SC_ONES, &launches, s,
+                               static_cast<int>(hs[0])));
+            return DL_OK;
+        }, &tsw);
+        if (r2) return r2;
+        const double nnz_i = static_cast<double>(hs[1]) + n;  // the CSR of I + G
+        *rate = (nnz_i * wp * 8 + 2.0 * np * wp * 8) / std::max(tsw, 1e-7);
         return DL_OK;
-    }, &tsw);
-    if (rc) return rc;
-    const double nnz_i = static_cast<double>(hs[1]) + n;  // the CSR of I + E
-    e.sweep_rate = (nnz_i * wp * 8 + 2.0 * np * wp * 8) / std::max(tsw, 1e-7);
+    };
+    double rate_er = 0, rate_dag = 0;
+    if ((rc = sweep_rate(E, &rate_er)) || (rc = sweep_rate(D, &rate_dag))) return rc;
+    e.sweep_rate = std::max(rate_er, rate_dag);
     // 3. the mixed path's reserve and 4. the same-generation route, through the solvers themselves
     auto *ob = static_cast<uint64_t *>(ws.get("tn_out", static_cast<size_t>(n) * ((n + 63) / 64) * 8));
     if (!ob) {
@@ -443,33 +478,39 @@ dl_status autotune_bucket(dl_ctx *ctx, Workspace &ws, cudaStream_t s, int32_t n_
             }
         }
     }
-    {
-        auto *P = static_cast<uint8_t *>(ws.get("tn_e", static_cast<size_t>(n) * n));  // reuses E's bytes
+    {  // the same-generation route: a choice only where one route wins on both a random forest
+       // and the skewed DAG (their relations differ widely in depth and density), else the rule
+        auto *P = E;  // reuses the ER graph's bytes
         TCK(cudaMemsetAsync(P, 0, static_cast<size_t>(n) * n, s));
         forest_bytes_kernel<<<blocks_for(n), 256, 0, s>>>(P, n, 0xf0e5ull);
         TCK(cudaGetLastError());
-        double best_s = 1e30;
-        for (int it : {0, 1}) {
-            TuneEntry x = e;
-            x.sg_iteration = it;
-            set_entry(x);
-            SolveArgs a;
-            a.n = n;
-            a.E = P;
-            a.mem = DL_MEM_DEVICE;
-            a.path = DL_PATH_AUTO;
-            a.out_bits = ob;
-            double t = 0;
-            for (int rep = 0; rep < 2; ++rep) {
-                dl_stats st{};
-                if ((rc = solve_sg(ctx, ws, s, a, &st))) return rc;
-                t = st.ms_total;
-            }
-            if (t < best_s) {
-                best_s = t;
-                e.sg_iteration = it;
+        int pick[2] = {-1, -1};
+        const uint8_t *graphs[2] = {P, D};
+        for (int gi = 0; gi < 2; ++gi) {
+            double best_s = 1e30;
+            for (int it : {0, 1}) {
+                TuneEntry x = e;
+                x.sg_iteration = it;
+                set_entry(x);
+                SolveArgs a;
+                a.n = n;
+                a.E = graphs[gi];
+                a.mem = DL_MEM_DEVICE;
+                a.path = DL_PATH_AUTO;
+                a.out_bits = ob;
+                double t = 0;
+                for (int rep = 0; rep < 2; ++rep) {
+                    dl_stats st{};
+                    if ((rc = solve_sg(ctx, ws, s, a, &st))) return rc;
+                    t = st.ms_total;
+                }
+                if (t < best_s) {
+                    best_s = t;
+                    pick[gi] = it;
+                }
             }
         }
+        e.sg_iteration = pick[0] == pick[1] ? pick[0] : -1;
     }
     e.measured = true;
     set_entry(e);

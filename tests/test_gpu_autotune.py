@@ -22,7 +22,7 @@ def test_tune_cache_and_exact_models(tmp_path):
             e = r["entry"]
             assert r["bucket"] == (512 if n == 300 else 2048)
             assert e["sq_bn"] in (128, 256) and e["t_sq_us"] > 0 and e["sweep_gbs"] > 0
-            assert e["mx_reserve"] in (16, 32, 48) and e["sg_iteration"] in (0, 1)
+            assert e["mx_reserve"] in (16, 32, 48) and e["sg_iteration"] in (-1, 0, 1)
             assert e["mx_pairs"] == -1 if n == 300 else e["mx_pairs"] in (-1, 0, 4, 12, 16)
             assert c.autotune(n)["source"] == "cache"  # the context's table
         data = json.load(open(cache))
