@@ -311,7 +311,7 @@ DL_API dl_status dl_compose(dl_ctx *ctx, int32_t n, const uint8_t *R1, const uin
  * 256; measured up to 16384): the FP8 squaring's tile width (128 or 256) and its time per
  * squaring, the bytes per second of an unsaturated Iteration sweep (the AUTO path's cost model
  * between sweeps and squarings), the SMs the mixed path's LU leaves to its critical chain (16, 32
- * or 48) and how many of its steps go in pairs sharing one bulk update, and whether same
+ * or 48) and how many of its steps go in units of 2 or 4 sharing one bulk update, and whether same
  * generation on AUTO takes the Iteration on bits or the doubling (when one is faster on both a
  * random forest and a heavy-tailed DAG; sg_iteration -1: the fixed size rule).  The sweep rate is
  * the faster of an ER digraph's and a heavy-tailed DAG's.  The inputs are synthetic (generated
@@ -319,7 +319,7 @@ DL_API dl_status dl_compose(dl_ctx *ctx, int32_t n, const uint8_t *R1, const uin
  * speed depends on it.  flags: 1 = measure again even if the bucket is known (from this context
  * or the cache).  report (cap bytes, may be NULL when cap is 0; *len gets the full length): JSON
  * {"key", "bucket", "source": "measured" | "cache" | "defaults ...", "entry": {sq_bn, t_sq_us,
- * sweep_gbs, mx_reserve, mx_pairs, sg_iteration}}.  With a cache path (dl_config.tune_cache or
+ * sweep_gbs, mx_reserve, mx_pairs, mx_group, sg_iteration}}.  With a cache path (dl_config.tune_cache or
  * DL_TUNE_CACHE) the entry is written there, keyed by GPU name, driver version and bucket.
  * Takes from milliseconds (small buckets) to about a second (16384).
  */

@@ -70,8 +70,8 @@ struct TuneEntry {
     double t_sq = 0.0;        // seconds per squaring (0: the flop-rate model)
     double sweep_rate = 0.0;  // bytes per second of an unsaturated sweep (0: the size rule)
     int mx_reserve = 32;      // SMs the mixed LU's bulk update leaves to the chain
-    int mx_pairs = -1;        // mixed LU steps taken in pairs (one bulk update with K = 2 blocks);
-                              // -1: half of the steps
+    int mx_pairs = -1;        // mixed LU steps taken in units sharing one bulk update (-1: half)
+    int mx_group = 2;         // steps per such unit (2 or 4; K = that many blocks)
     int sg_iteration = -1;    // same generation on AUTO: 1 Iteration, 0 doubling, -1 by size
     bool measured = false;
 };

@@ -46,6 +46,7 @@ namespace {
 constexpr int BL = 128;        // LU block size = GEMM tile
 constexpr int TT = 32;         // transpose tile
 constexpr int kSolveGroup = 8;  // blocks per group of the solves (1024 columns)
+constexpr int kMaxGroup = 4;    // LU steps per unit sharing one bulk update, at most
 
 __global__ void build_a_kernel(const uint8_t *__restrict__ E, int n, int np, float eps, float *__restrict__ A) {
     const int64_t row = blockIdx.y;
@@ -734,9 +735,9 @@ dl_status tc_mixed(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &
     auto *D32 = static_cast<float *>(ws.get("mx_D", np * np * 4));
     auto *Z64 = static_cast<double *>(ws.get("mx_Z64", np * np * 8));
     auto *X64 = static_cast<double *>(ws.get("mx_X64", np * np * 8));
-    // transposed row panels: two slots of np rows (indexed by the absolute column) x 2 BL (the
-    // panels of a pair of steps side by side)
-    auto *T2 = static_cast<float *>(ws.get("mx_T", 2 * np * 2 * BL * 4));
+    // transposed row panels: two slots of np rows (indexed by the absolute column) x kMaxGroup BL
+    // (the panels of a unit of steps side by side)
+    auto *T2 = static_cast<float *>(ws.get("mx_T", 2 * np * kMaxGroup * BL * 4));
     auto *Sinv = static_cast<float *>(ws.get("mx_Sinv", np * BL * 4));
     auto *SinvT = static_cast<float *>(ws.get("mx_SinvT", np * BL * 4));
     const int64_t GW = std::min<int64_t>(np, static_cast<int64_t>(kSolveGroup) * BL);
@@ -784,38 +785,40 @@ dl_status tc_mixed(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &
     const Operand opS{Sinv, np, BL, BL, 0, 0}, opST{SinvT, np, BL, BL, 0, 0};
     bool ok = true;
     std::vector<int> has_bulk(nb, -1), has_ahead(nb, -1), has_l21(nb, -1);
-    // Steps k < pair_steps go in pairs (k even, k + 1): the first step's look-ahead updates the
-    // next two block columns and rows, the second's the next one, and the pair shares one bulk
-    // update with K = 2 BL, which moves the trailing matrix half as often.  In the first part of the
-    // factorisation the bulk update, not the chain of diagonal steps, bounds each step, so the
-    // longer look-ahead costs nothing there.  Later steps are single (K = BL).
+    // Steps k < grouped go in units of G consecutive steps (G = 2 or 4): step q of a unit (q = 0 ..
+    // G - 1) updates, in its look-ahead, the next G - q block columns and rows (up to the first
+    // block of the next unit), and the unit's last step carries one bulk update of the rest with
+    // K = G BL for all G steps, which moves the trailing matrix G times less often.  While the
+    // bulk update, not the chain of diagonal steps, bounds a step, the longer look-ahead costs
+    // nothing.  Later steps are single (K = BL).  G and the grouped steps: tuned per size.
     const TuneEntry tn = tuned(ctx, np);
-    int pair_steps = tn.mx_pairs >= 0 ? tn.mx_pairs : nb / 2;
-    pair_steps = std::max(0, std::min(pair_steps, nb - 6)) & ~1;
-    auto unit_of = [&](int k) { return k < pair_steps ? k / 2 : pair_steps / 2 + (k - pair_steps); };
-    auto half_of = [&](int k) { return k < pair_steps ? (k & 1) : 0; };
+    const int G = tn.mx_group == 4 ? 4 : 2;
+    int grouped = tn.mx_pairs >= 0 ? tn.mx_pairs : nb / 2;
+    grouped = std::max(0, std::min(grouped, nb - 6)) / G * G;
+    auto unit_of = [&](int k) { return k < grouped ? k / G : grouped / G + (k - grouped); };
+    auto pos_of = [&](int k) { return k < grouped ? k % G : 0; };          // q, the step's place in its unit
+    auto size_of = [&](int k) { return k < grouped ? G : 1; };             // the unit's number of steps
+    const int64_t ldT = static_cast<int64_t>(kMaxGroup) * BL;
     for (int k = 0; k < nb && ok; ++k) {
         const int kb = k * BL, rem = N - kb - BL;
         if (rem <= 0) break;
-        const bool first = k < pair_steps && (k & 1) == 0, second = k < pair_steps && (k & 1) == 1;
-        const int hcol = half_of(k) * BL;
-        const Operand opT{T2 + static_cast<int64_t>(unit_of(k) & 1) * np * 2 * BL, np, 2 * BL, 2 * BL, 0, 0};
+        const int q = pos_of(k), gu = size_of(k);
+        const Operand opT{T2 + static_cast<int64_t>(unit_of(k) & 1) * np * ldT, np, ldT, ldT, 0, 0};
         // L21 = A21 S^-1 (in place: each output tile reads only its own rows of A21)
         has_l21[k] = static_cast<int>(l21.size());
         ok = tb.add(l21, EPI_STORE_F32, BL, rem, BL, BL, at(opA, kb + BL, kb), at(opST, kb, 0), A32, np, kb + BL, kb,
                     false, &flops_lu);
         // look-ahead: the next w block columns (all rows below) and block rows (columns beyond)
-        const int w = first ? 2 * BL : BL;
+        const int w = (gu - q) * BL;
         has_ahead[k] = static_cast<int>(ahead.size());
         ok = ok && tb.add(ahead, EPI_SUB_F32, BL, rem, std::min(w, rem), BL, at(opA, kb + BL, kb),
-                          at(opT, kb + BL, hcol), A32, np, kb + BL, kb + BL, false, &flops_lu);
+                          at(opT, kb + BL, q * BL), A32, np, kb + BL, kb + BL, false, &flops_lu);
         if (ok && rem > w) {
-            ok = tb.add(ahead, EPI_SUB_F32, BL, w, rem - w, BL, at(opA, kb + BL, kb), at(opT, kb + BL + w, hcol), A32,
-                        np, kb + BL, kb + BL + w, true, &flops_lu);
-            if (ok && !first) {  // the bulk update of the unit: one step (K = BL) or a pair (K = 2 BL)
-                const int kk = second ? 2 * BL : BL, k0 = second ? kb - BL : kb;
+            ok = tb.add(ahead, EPI_SUB_F32, BL, w, rem - w, BL, at(opA, kb + BL, kb), at(opT, kb + BL + w, q * BL),
+                        A32, np, kb + BL, kb + BL + w, true, &flops_lu);
+            if (ok && q == gu - 1) {  // the unit's bulk update (K = gu BL)
                 has_bulk[k] = static_cast<int>(bulk.size());
-                ok = tb.add(bulk, EPI_SUB_F32, 256, rem - BL, rem - BL, kk, at(opA, kb + 2 * BL, k0),
+                ok = tb.add(bulk, EPI_SUB_F32, 256, rem - BL, rem - BL, gu * BL, at(opA, kb + 2 * BL, kb - q * BL),
                             at(opT, kb + 2 * BL, 0), A32, np, kb + 2 * BL, kb + 2 * BL, false, &flops_lu);
             }
         }
@@ -971,8 +974,8 @@ dl_status tc_mixed(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &
             MCK(cudaStreamWaitEvent(V, ws.mx_gev[g], 0));
             MCK(inverse_group(g));
         }
-        float *Tk = T2 + static_cast<int64_t>(u & 1) * np * 2 * BL + (kb + BL) * 2 * BL + half_of(k) * BL;
-        MCK(transpose(A32 + kb * np + kb + BL, np, BL, rem, Tk, 2 * BL, P));  // T = A12^T, row = absolute column
+        float *Tk = T2 + static_cast<int64_t>(u & 1) * np * ldT + (kb + BL) * ldT + pos_of(k) * BL;
+        MCK(transpose(A32 + kb * np + kb + BL, np, BL, rem, Tk, ldT, P));  // T = A12^T, row = absolute column
         ++launches;
         MCK(cudaEventRecord(evT[u & 1], P));
         if (bulk_pending && pending_unit != u) {  // the look-ahead's region was in the last bulk update

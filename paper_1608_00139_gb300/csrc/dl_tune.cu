@@ -7,8 +7,9 @@
 //                 sweep rate, instead of 6 / 3 TB/s by size): the faster of an ER digraph's and a
 //                 heavy-tailed DAG's;
 //   mx_reserve    SMs the mixed path's LU leaves to its critical chain (16, 32 or 48), and
-//   mx_pairs      how many of its first steps go in pairs sharing one bulk update (0, a quarter,
-//                 half, three quarters or all of them): the fastest factorisation;
+//   mx_pairs      how many of its first steps go in units sharing one bulk update (0, a quarter,
+//   mx_group      half, three quarters or all of them) and the steps per unit (2 or 4): the
+//                 fastest factorisation;
 //   sg_iteration  same generation on AUTO: the Iteration on bits (1) or the doubling (0) where the
 //                 same one is faster on a random forest and on a heavy-tailed DAG, else the
 //                 crossover at Np = 6144 (-1).
@@ -182,8 +183,8 @@ std::string entry_json(const TuneEntry &e) {
     char buf[256];
     std::snprintf(buf, sizeof buf,
                   "{\"sq_bn\": %d, \"t_sq_us\": %.3f, \"sweep_gbs\": %.3f, \"mx_reserve\": %d, \"mx_pairs\": %d, "
-                  "\"sg_iteration\": %d}",
-                  e.sq_bn, e.t_sq * 1e6, e.sweep_rate * 1e-9, e.mx_reserve, e.mx_pairs, e.sg_iteration);
+                  "\"mx_group\": %d, \"sg_iteration\": %d}",
+                  e.sq_bn, e.t_sq * 1e6, e.sweep_rate * 1e-9, e.mx_reserve, e.mx_pairs, e.mx_group, e.sg_iteration);
     return buf;
 }
 
@@ -199,6 +200,8 @@ bool entry_from(const JVal &o, TuneEntry *e) {
     e->sg_iteration = static_cast<int>(f->num);
     const JVal *g = field(o, "mx_pairs");  // absent in older caches: the default
     e->mx_pairs = g ? static_cast<int>(g->num) : -1;
+    const JVal *h = field(o, "mx_group");
+    e->mx_group = h && static_cast<int>(h->num) == 4 ? 4 : 2;
     e->measured = true;
     return true;
 }
@@ -467,14 +470,20 @@ dl_status autotune_bucket(dl_ctx *ctx, Workspace &ws, cudaStream_t s, int32_t n_
             }
         }
         const int nb = np / 128;
-        for (int pairs : {0, nb / 4, 3 * nb / 4, nb}) {  // nb / 2 (the default) is measured above
-            TuneEntry x = e;
-            x.mx_pairs = pairs;
-            double ms = 0;
-            if ((rc = factor_ms(x, &ms))) return rc;
-            if (ms < best_f) {
-                best_f = ms;
-                e.mx_pairs = pairs;
+        for (int group : {2, 4}) {
+            for (int grouped : {0, nb / 4, nb / 2, 3 * nb / 4, nb}) {
+                if (group == 2 && grouped == nb / 2) continue;  // the default, measured above
+                if (group == 4 && grouped == 0) continue;        // the same as no grouping
+                TuneEntry x = e;
+                x.mx_group = group;
+                x.mx_pairs = grouped;
+                double ms = 0;
+                if ((rc = factor_ms(x, &ms))) return rc;
+                if (ms < best_f) {
+                    best_f = ms;
+                    e.mx_group = group;
+                    e.mx_pairs = grouped;
+                }
             }
         }
     }

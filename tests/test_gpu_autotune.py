@@ -23,7 +23,8 @@ def test_tune_cache_and_exact_models(tmp_path):
             assert r["bucket"] == (512 if n == 300 else 2048)
             assert e["sq_bn"] in (128, 256) and e["t_sq_us"] > 0 and e["sweep_gbs"] > 0
             assert e["mx_reserve"] in (16, 32, 48) and e["sg_iteration"] in (-1, 0, 1)
-            assert e["mx_pairs"] == -1 if n == 300 else e["mx_pairs"] in (-1, 0, 4, 12, 16)
+            assert e["mx_pairs"] == -1 if n == 300 else e["mx_pairs"] in (-1, 0, 4, 8, 12, 16)
+            assert e["mx_group"] in (2, 4)
             assert c.autotune(n)["source"] == "cache"  # the context's table
         data = json.load(open(cache))
         keys = list(data["entries"])
@@ -65,3 +66,22 @@ def test_env_cache(tmp_path, monkeypatch):
         c.autotune(256)
     with dl.Context(0) as c:
         assert c.autotune(256)["source"] == "cache"
+
+
+@pytest.mark.parametrize("group,grouped", [(4, 16), (4, 8), (2, 16)])
+def test_grouped_lu_steps_are_exact(tmp_path, group, grouped):
+    """The mixed LU with its first steps in units of 2 or 4 sharing one bulk update (forced through
+    a cache entry): bits and R~ against the oracle."""
+    cache = str(tmp_path / "g.json")
+    with dl.Context(0) as c:
+        key = c.autotune(2048)["key"]
+    entry = {"sq_bn": 256, "t_sq_us": 20.0, "sweep_gbs": 600.0, "mx_reserve": 32, "mx_pairs": grouped,
+             "mx_group": group, "sg_iteration": -1}
+    json.dump({"version": 1, "entries": {key: entry}}, open(cache, "w"))
+    e = inputs.er_digraph(2000, 0.004, 75)
+    with dl.Context(0, tune_cache=cache) as c:
+        assert c.autotune(2000)["entry"]["mx_group"] == group
+        bits, st, x = c.tc_closure(e, path="mixed", rtilde=True)
+    assert np.array_equal(bits, oracle.tc_model(e))
+    xr = oracle.tc_rtilde_lu(e, st["eps_used"])
+    assert np.abs(x - xr).max() <= 1e-10 * np.abs(xr).max()
