@@ -81,31 +81,80 @@ cudaError_t transpose(const T *src, int64_t lds, int rows, int cols, T *dst, int
     return cudaGetLastError();
 }
 
-// S^-1 of the BL x BL block at A (row stride lda) by in-place Gauss-Jordan elimination without
-// pivoting, FP32, one CTA of 256 threads.  Thread t holds an 8 x 8 tile of the block in
-// registers: rows r0 .. r0 + 7 (r0 = 16 warp + 8 (lane / 16)), columns c0 .. c0 + 7
-// (c0 = 8 (lane mod 16)).  Step k (p = 1 / S_kk, r = row k, c = column k before the step):
-//     S_ij -= c_i r_j p (i, j != k),   S_kj = r_j p,   S_ik = -c_i p,   S_kk = p.
-// Two steps per barrier: the owners of rows k, k + 1 and of columns k, k + 1 publish them through
-// shared memory (two buffers, so one barrier per pair suffices: a buffer is rewritten two pairs
-// later, after every thread has passed the barrier between); every thread applies step k to its
-// tile and forms, from the same published values, row and column k + 1 as step k leaves them,
-//     c'_i = c1_i - c_i S_{k,k+1} p  (c'_k = S_{k,k+1} p),   r'_j = r1_j - S_{k+1,k} r_j p  (r'_k = -S_{k+1,k} p),
-//     pivot S_{k+1,k+1} - S_{k+1,k} S_{k,k+1} p,
-// then applies step k + 1 with them.  A is strictly diagonally dominant by rows and so is every
-// Schur complement, hence every pivot is positive; a pivot that is not sets ST_BAD_INPUT.
-// Writes S^-1 and S^-T (BL x BL, row-major).
+// S^-1 of the BL x BL block at A (row stride lda), one CTA of 256 threads, by block inversion of
+// its 64 x 64 quarters  S = [[P, B], [C, D]]:
+//     P^-1;  Y = P^-1 B;  X = C P^-1;  Sd = (D - C Y)^-1;
+//     S^-1 = [[P^-1 - (-Y Sd) X, -Y Sd], [-Sd X, Sd]]
+// (Schur complement; A is strictly diagonally dominant by rows and so are P and D - C Y, so no
+// pivoting is needed).  The two 64 x 64 inverses by Gauss-Jordan on the CUDA cores (4 x 4 register
+// tiles, two pivots per barrier: every thread applies step k and forms row and column k + 1 as
+// step k leaves them from the same published values); the six 64 x 64 products on the tensor
+// cores (mma.sync m16n8k8, TF32 operands rounded to nearest, FP32 accumulate).  S^-1 comes out
+// within TF32 accuracy, below what the LU's TF32 products use it at: it only preconditions the
+// refinement.  A pivot that is not positive sets ST_BAD_INPUT.  Writes S^-1 and S^-T (BL x BL,
+// row-major).  Dynamic shared memory: kDiagSmem bytes.
 constexpr int kDiagThreads = 256;
+constexpr int kHB = BL / 2;                 // quarter size
+constexpr int kLdS = BL + 4, kLdH = kHB + 8;  // shared-memory row strides
+constexpr size_t kDiagSmem = (static_cast<size_t>(BL) * kLdS + 2 * kHB * kLdH + 8 * kHB) * sizeof(float);
 
-// One elimination step on a thread's tile: the tile's rows kk / columns kk hold the pivot row /
+__device__ __forceinline__ uint32_t to_tf32(float x) {
+    uint32_t r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return r;
+}
+
+// out (64 x 64, ldo) = alpha P Q + beta out (P, Q 64 x 64 in shared memory, not aliasing out);
+// warp w computes rows 16 (w mod 4) .. + 16 and columns 32 (w / 4) .. + 32 as four 16 x 8 tiles.
+__device__ void quarter_product(const float *P, int ldp, const float *Q, int ldq, float *out, int ldo, float alpha,
+                                float beta) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int g = lane >> 2, t = lane & 3;
+    const int m0 = 16 * (warp & 3);
+    float acc[4][4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+        for (int r = 0; r < 4; ++r) acc[j][r] = 0.f;
+#pragma unroll
+    for (int k0 = 0; k0 < kHB; k0 += 8) {
+        const uint32_t a0 = to_tf32(P[(m0 + g) * ldp + k0 + t]);
+        const uint32_t a1 = to_tf32(P[(m0 + g + 8) * ldp + k0 + t]);
+        const uint32_t a2 = to_tf32(P[(m0 + g) * ldp + k0 + t + 4]);
+        const uint32_t a3 = to_tf32(P[(m0 + g + 8) * ldp + k0 + t + 4]);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+            const int n0 = 8 * ((warp >> 2) * 4 + j);
+            const uint32_t b0 = to_tf32(Q[(k0 + t) * ldq + n0 + g]);
+            const uint32_t b1 = to_tf32(Q[(k0 + t + 4) * ldq + n0 + g]);
+            asm volatile(
+                "mma.sync.aligned.m16n8k8.row.col.f32.tf32.tf32.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+                "{%0,%1,%2,%3};"
+                : "+f"(acc[j][0]), "+f"(acc[j][1]), "+f"(acc[j][2]), "+f"(acc[j][3])
+                : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+        }
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+        const int n0 = 8 * ((warp >> 2) * 4 + j);
+#pragma unroll
+        for (int r = 0; r < 4; ++r) {
+            float *o = out + (m0 + g + 8 * (r >> 1)) * ldo + n0 + 2 * t + (r & 1);
+            *o = beta != 0.f ? fmaf(alpha, acc[j][r], beta * *o) : alpha * acc[j][r];
+        }
+    }
+}
+
+// One elimination step on a thread's T x T tile: the tile's row / column kk hold the pivot row /
 // column when ro / co; c = the pivot column at the tile's rows, rp = the pivot row at the tile's
 // columns times p = 1 / pivot.
-__device__ __forceinline__ void gj_step(float (&a)[8][8], int kk, bool ro, bool co, const float (&c)[8],
-                                        const float (&rp)[8], float p) {
+template <int T>
+__device__ __forceinline__ void gj_step(float (&a)[T][T], int kk, bool ro, bool co, const float (&c)[T],
+                                        const float (&rp)[T], float p) {
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
+    for (int i = 0; i < T; ++i) {
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
+        for (int j = 0; j < T; ++j) {
             const float upd = fmaf(-c[i], rp[j], a[i][j]);
             if (i == kk && j == kk) {
                 a[i][j] = ro && co ? p : ro ? rp[j] : co ? -c[i] * p : upd;
@@ -120,91 +169,99 @@ __device__ __forceinline__ void gj_step(float (&a)[8][8], int kk, bool ro, bool 
     }
 }
 
-__global__ void __launch_bounds__(kDiagThreads) diag_inv_kernel(const float *__restrict__ A, int64_t lda,
-                                                                float *__restrict__ Sinv, float *__restrict__ SinvT,
-                                                                int *status) {
-    static_assert(BL == 128 && kDiagThreads == 256, "8 x 8 tiles of a 128 x 128 block");
-    __shared__ __align__(16) float rowbuf[2][2][BL];  // [buffer][row k, row k + 1][column]
-    __shared__ __align__(16) float colbuf[2][2][BL];  // [buffer][column k, column k + 1][row]
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-    const int r0 = 16 * warp + 8 * (lane >> 4);
-    const int c0 = 8 * (lane & 15);
-    float a[8][8];
+// In-place Gauss-Jordan inverse of the 64 x 64 quarter at R (row stride ld); two pivots per
+// barrier.  rowbuf / colbuf: [buffer][pivot row or column k, k + 1][64].
+__device__ void quarter_inverse(float *R, int ld, float (*rowbuf)[2][kHB], float (*colbuf)[2][kHB], bool *bad) {
+    const int r0 = 4 * (threadIdx.x >> 4), c0 = 4 * (threadIdx.x & 15);
+    float a[4][4];
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
-        const float4 x = *reinterpret_cast<const float4 *>(A + (r0 + i) * lda + c0);
-        const float4 y = *reinterpret_cast<const float4 *>(A + (r0 + i) * lda + c0 + 4);
-        a[i][0] = x.x, a[i][1] = x.y, a[i][2] = x.z, a[i][3] = x.w;
-        a[i][4] = y.x, a[i][5] = y.y, a[i][6] = y.z, a[i][7] = y.w;
-    }
-    bool bad = false;
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) a[i][j] = R[(r0 + i) * ld + c0 + j];
 #pragma unroll 1
-    for (int kb = 0; kb < BL; kb += 8) {
-        const bool ro = r0 == kb;  // rows kb .. kb + 7 are this thread's
-        const bool co = c0 == kb;  // columns kb .. kb + 7 are this thread's
+    for (int kb = 0; kb < kHB; kb += 4) {
+        const bool ro = r0 == kb, co = c0 == kb;
 #pragma unroll
-        for (int kk = 0; kk < 8; kk += 2) {
+        for (int kk = 0; kk < 4; kk += 2) {
             const int k = kb + kk, buf = (k >> 1) & 1;
-            if (ro) {
+            if (ro)
 #pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    *reinterpret_cast<float4 *>(&rowbuf[buf][h][c0]) =
-                        make_float4(a[kk + h][0], a[kk + h][1], a[kk + h][2], a[kk + h][3]);
-                    *reinterpret_cast<float4 *>(&rowbuf[buf][h][c0 + 4]) =
-                        make_float4(a[kk + h][4], a[kk + h][5], a[kk + h][6], a[kk + h][7]);
-                }
-            }
-            if (co) {
+                for (int h = 0; h < 2; ++h)
 #pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    *reinterpret_cast<float4 *>(&colbuf[buf][h][r0]) =
-                        make_float4(a[0][kk + h], a[1][kk + h], a[2][kk + h], a[3][kk + h]);
-                    *reinterpret_cast<float4 *>(&colbuf[buf][h][r0 + 4]) =
-                        make_float4(a[4][kk + h], a[5][kk + h], a[6][kk + h], a[7][kk + h]);
-                }
-            }
+                    for (int j = 0; j < 4; ++j) rowbuf[buf][h][c0 + j] = a[kk + h][j];
+            if (co)
+#pragma unroll
+                for (int h = 0; h < 2; ++h)
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) colbuf[buf][h][r0 + i] = a[i][kk + h];
             __syncthreads();
             const float s00 = rowbuf[buf][0][k], s01 = rowbuf[buf][0][k + 1];
             const float s10 = rowbuf[buf][1][k], s11 = rowbuf[buf][1][k + 1];
-            const float p = __fdividef(1.0f, s00);  // within 2 ulp: S^-1 only preconditions the refinement
-            float c[8], c1[8], r[8], r1[8], rp[8];
+            const float p = __fdividef(1.0f, s00);
+            float c[4], c1[4], r1[4], rp[4];
 #pragma unroll
-            for (int q = 0; q < 8; q += 4) {
-                const float4 cx = *reinterpret_cast<const float4 *>(&colbuf[buf][0][r0 + q]);
-                const float4 cy = *reinterpret_cast<const float4 *>(&colbuf[buf][1][r0 + q]);
-                const float4 rx = *reinterpret_cast<const float4 *>(&rowbuf[buf][0][c0 + q]);
-                const float4 ry = *reinterpret_cast<const float4 *>(&rowbuf[buf][1][c0 + q]);
-                c[q] = cx.x, c[q + 1] = cx.y, c[q + 2] = cx.z, c[q + 3] = cx.w;
-                c1[q] = cy.x, c1[q + 1] = cy.y, c1[q + 2] = cy.z, c1[q + 3] = cy.w;
-                r[q] = rx.x, r[q + 1] = rx.y, r[q + 2] = rx.z, r[q + 3] = rx.w;
-                r1[q] = ry.x, r1[q + 1] = ry.y, r1[q + 2] = ry.z, r1[q + 3] = ry.w;
+            for (int q = 0; q < 4; ++q) {
+                c[q] = colbuf[buf][0][r0 + q], c1[q] = colbuf[buf][1][r0 + q];
+                rp[q] = rowbuf[buf][0][c0 + q] * p, r1[q] = rowbuf[buf][1][c0 + q];
             }
-#pragma unroll
-            for (int j = 0; j < 8; ++j) rp[j] = r[j] * p;
-            gj_step(a, kk, ro, co, c, rp, p);  // step k
+            gj_step<4>(a, kk, ro, co, c, rp, p);  // step k
             // row and column k + 1 as step k leaves them, and the next pivot
             const float s01p = s01 * p;
             const float piv2 = fmaf(-s10, s01p, s11);
             const float p2 = __fdividef(1.0f, piv2);
-            bad |= !(s00 > 0.0f) || !isfinite(p) || !(piv2 > 0.0f) || !isfinite(p2);
-            float c2[8], rp2[8];
+            *bad |= !(s00 > 0.0f) || !isfinite(p) || !(piv2 > 0.0f) || !isfinite(p2);
+            float c2[4], rp2[4];
 #pragma unroll
-            for (int i = 0; i < 8; ++i) c2[i] = ro && i == kk ? s01p : fmaf(-c[i], s01p, c1[i]);
+            for (int i = 0; i < 4; ++i) c2[i] = ro && i == kk ? s01p : fmaf(-c[i], s01p, c1[i]);
 #pragma unroll
-            for (int j = 0; j < 8; ++j) rp2[j] = (co && j == kk ? -s10 * p : fmaf(-s10, rp[j], r1[j])) * p2;
-            gj_step(a, kk + 1, ro, co, c2, rp2, p2);  // step k + 1
+            for (int j = 0; j < 4; ++j) rp2[j] = (co && j == kk ? -s10 * p : fmaf(-s10, rp[j], r1[j])) * p2;
+            gj_step<4>(a, kk + 1, ro, co, c2, rp2, p2);  // step k + 1
         }
     }
-    if (bad) atomicOr(status, ST_BAD_INPUT);
 #pragma unroll
-    for (int i = 0; i < 8; ++i) {
-        *reinterpret_cast<float4 *>(Sinv + (r0 + i) * BL + c0) = make_float4(a[i][0], a[i][1], a[i][2], a[i][3]);
-        *reinterpret_cast<float4 *>(Sinv + (r0 + i) * BL + c0 + 4) = make_float4(a[i][4], a[i][5], a[i][6], a[i][7]);
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) R[(r0 + i) * ld + c0 + j] = a[i][j];
+}
+
+__global__ void __launch_bounds__(kDiagThreads) diag_inv_kernel(const float *__restrict__ A, int64_t lda,
+                                                                float *__restrict__ Sinv, float *__restrict__ SinvT,
+                                                                int *status) {
+    static_assert(BL == 128 && kDiagThreads == 256, "64 x 64 quarters, 4 x 4 tiles");
+    extern __shared__ __align__(16) float dsm[];
+    float *S = dsm;                 // BL x kLdS
+    float *Yq = S + BL * kLdS;      // kHB x kLdH
+    float *Xq = Yq + kHB * kLdH;    // kHB x kLdH
+    auto *rowbuf = reinterpret_cast<float(*)[2][kHB]>(Xq + kHB * kLdH);
+    auto *colbuf = rowbuf + 2;
+    for (int e = threadIdx.x; e < BL * BL / 4; e += kDiagThreads) {
+        const int r = e / (BL / 4), c = 4 * (e % (BL / 4));
+        const float4 v = *reinterpret_cast<const float4 *>(A + r * lda + c);
+        float *d = S + r * kLdS + c;
+        d[0] = v.x, d[1] = v.y, d[2] = v.z, d[3] = v.w;
     }
-#pragma unroll
-    for (int j = 0; j < 8; ++j) {
-        *reinterpret_cast<float4 *>(SinvT + (c0 + j) * BL + r0) = make_float4(a[0][j], a[1][j], a[2][j], a[3][j]);
-        *reinterpret_cast<float4 *>(SinvT + (c0 + j) * BL + r0 + 4) = make_float4(a[4][j], a[5][j], a[6][j], a[7][j]);
+    __syncthreads();
+    float *Pq = S, *Bq = S + kHB, *Cq = S + kHB * kLdS, *Dq = S + kHB * kLdS + kHB;
+    bool bad = false;
+    quarter_inverse(Pq, kLdS, rowbuf, colbuf, &bad);           // P^-1
+    __syncthreads();
+    quarter_product(Pq, kLdS, Bq, kLdS, Yq, kLdH, 1.f, 0.f);   // Y = P^-1 B
+    quarter_product(Cq, kLdS, Pq, kLdS, Xq, kLdH, 1.f, 0.f);   // X = C P^-1
+    __syncthreads();
+    quarter_product(Cq, kLdS, Yq, kLdH, Dq, kLdS, -1.f, 1.f);  // D - C Y
+    __syncthreads();
+    quarter_inverse(Dq, kLdS, rowbuf, colbuf, &bad);           // Sd
+    __syncthreads();
+    quarter_product(Dq, kLdS, Xq, kLdH, Cq, kLdS, -1.f, 0.f);  // lower left: -Sd X
+    quarter_product(Yq, kLdH, Dq, kLdS, Bq, kLdS, -1.f, 0.f);  // upper right: -Y Sd
+    __syncthreads();
+    quarter_product(Bq, kLdS, Xq, kLdH, Pq, kLdS, -1.f, 1.f);  // upper left: P^-1 - (-Y Sd) X
+    __syncthreads();
+    if (bad) atomicOr(status, ST_BAD_INPUT);
+    for (int e = threadIdx.x; e < BL * BL; e += kDiagThreads) {
+        const int r = e / BL, c = e % BL;
+        Sinv[e] = S[r * kLdS + c];
+        SinvT[e] = S[c * kLdS + r];
     }
 }
 
@@ -902,6 +959,7 @@ dl_status tc_mixed(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &
         MCK(gemm_prepare(KIND_TF32, true, bn, EPI_STORE_F32));
         MCK(gemm_prepare(KIND_TF32, true, bn, EPI_SUB_F32));
     }
+    MCK(cudaFuncSetAttribute(diag_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(kDiagSmem)));
     auto run = [&](const Launch &L, int max_grid, cudaStream_t on) -> cudaError_t {
         ++launches;
         return gemm_launch(KIND_TF32, true, L.bn, L.epi, dprob + L.first, L.count, L.tiles,
@@ -961,7 +1019,8 @@ dl_status tc_mixed(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &
     for (int k = 0; k < nb; ++k) {
         const int64_t kb = static_cast<int64_t>(k) * BL;
         const int rem = N - static_cast<int>(kb) - BL;
-        diag_inv_kernel<<<1, kDiagThreads, 0, P>>>(A32 + kb * np + kb, np, Sinv + kb * BL, SinvT + kb * BL, ws.status);
+        diag_inv_kernel<<<1, kDiagThreads, kDiagSmem, P>>>(A32 + kb * np + kb, np, Sinv + kb * BL, SinvT + kb * BL,
+                                                           ws.status);
         MCK(cudaGetLastError());
         ++launches;
         if (rem <= 0) break;
