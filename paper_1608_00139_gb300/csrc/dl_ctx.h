@@ -42,8 +42,8 @@ struct Workspace {
     bool ready = false;
     // mixed path: the LU's critical chain (greatest priority) and its bulk updates (least
     // priority), and events ordering them; created on first use
-    cudaStream_t mx_stream[3] = {};  // + the inverse's stream (least priority)
-    cudaEvent_t mx_ev[4] = {};
+    cudaStream_t mx_stream[4] = {};  // + the inverse's stream (least priority), the panel transposes'
+    cudaEvent_t mx_ev[6] = {};
     cudaEvent_t mx_gev[32] = {};      // a group of the LU is final (the inverse may start on it)
     BatchPlan *batch_plan = nullptr;
     bool last_heavy = false;  // the last closure on this workspace had rows of > 256 successors

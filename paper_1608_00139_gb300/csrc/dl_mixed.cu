@@ -720,6 +720,7 @@ dl_status mixed_streams(Workspace &ws) {
     MCK(cudaStreamCreateWithPriority(&ws.mx_stream[0], cudaStreamNonBlocking, greatest));
     MCK(cudaStreamCreateWithPriority(&ws.mx_stream[1], cudaStreamNonBlocking, std::max(greatest, least - 1)));
     MCK(cudaStreamCreateWithPriority(&ws.mx_stream[2], cudaStreamNonBlocking, least));
+    MCK(cudaStreamCreateWithPriority(&ws.mx_stream[3], cudaStreamNonBlocking, greatest));
     for (auto &e : ws.mx_ev) MCK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     for (auto &e : ws.mx_gev) MCK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     return DL_OK;
@@ -785,7 +786,7 @@ dl_status tc_mixed(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &
     int launches = 0;
     dl_status rc = mixed_streams(ws);
     if (rc) return rc;
-    cudaStream_t P = ws.mx_stream[0], U = ws.mx_stream[1], V = ws.mx_stream[2];
+    cudaStream_t P = ws.mx_stream[0], U = ws.mx_stream[1], V = ws.mx_stream[2], Q = ws.mx_stream[3];
     auto *A32 = static_cast<float *>(ws.get("mx_A", np * np * 4));
     auto *W32 = static_cast<float *>(ws.get("mx_W", np * np * 4));   // Z = A^-T, then R
     auto *Wt = static_cast<float *>(ws.get("mx_Wt", np * np * 4));   // W = A^-1
@@ -975,6 +976,7 @@ dl_status tc_mixed(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &
     MCK(cudaStreamWaitEvent(P, ws.mx_ev[0], 0));
     MCK(cudaStreamWaitEvent(U, ws.mx_ev[0], 0));
     MCK(cudaStreamWaitEvent(V, ws.mx_ev[0], 0));
+    MCK(cudaStreamWaitEvent(Q, ws.mx_ev[0], 0));
     // The inverse (on V, least priority): the group inverses and the forward solve of group g
     // start as soon as the LU's steps of group g are done (its L and U blocks, and L below it, are
     // final then: later steps write only block rows and columns beyond the group), so they fill
@@ -1019,12 +1021,19 @@ dl_status tc_mixed(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &
     for (int k = 0; k < nb; ++k) {
         const int64_t kb = static_cast<int64_t>(k) * BL;
         const int rem = N - static_cast<int>(kb) - BL;
+        const int u = unit_of(k);
+        if (rem > 0) {  // T(k) = A12^T (row = absolute column) needs only row k, final since look-ahead(k - 1)
+            if (k > 0) MCK(cudaStreamWaitEvent(Q, ws.mx_ev[4], 0));
+            float *Tk = T2 + static_cast<int64_t>(u & 1) * np * ldT + (kb + BL) * ldT + pos_of(k) * BL;
+            MCK(transpose(A32 + kb * np + kb + BL, np, BL, rem, Tk, ldT, Q));
+            ++launches;
+            MCK(cudaEventRecord(ws.mx_ev[5], Q));
+        }
         diag_inv_kernel<<<1, kDiagThreads, kDiagSmem, P>>>(A32 + kb * np + kb, np, Sinv + kb * BL, SinvT + kb * BL,
                                                            ws.status);
         MCK(cudaGetLastError());
         ++launches;
         if (rem <= 0) break;
-        const int u = unit_of(k);
         // L21 runs beside the bulk update of the previous unit, which leaves it `reserve` SMs
         MCK(run(l21[has_l21[k]], bulk_pending || (k > 0 && has_bulk[k - 1] >= 0) ? reserve : sms, P));
         if ((k + 1) % kSolveGroup == 0 && k + 1 < nb) {  // group (k + 1) / kSolveGroup - 1 is final
@@ -1033,15 +1042,14 @@ dl_status tc_mixed(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &
             MCK(cudaStreamWaitEvent(V, ws.mx_gev[g], 0));
             MCK(inverse_group(g));
         }
-        float *Tk = T2 + static_cast<int64_t>(u & 1) * np * ldT + (kb + BL) * ldT + pos_of(k) * BL;
-        MCK(transpose(A32 + kb * np + kb + BL, np, BL, rem, Tk, ldT, P));  // T = A12^T, row = absolute column
-        ++launches;
+        MCK(cudaStreamWaitEvent(P, ws.mx_ev[5], 0));  // T(k), transposed on Q beside diag(k) and L21(k)
         MCK(cudaEventRecord(evT[u & 1], P));
         if (bulk_pending && pending_unit != u) {  // the look-ahead's region was in the last bulk update
             MCK(cudaStreamWaitEvent(P, evB[pending_unit & 1], 0));
             bulk_pending = false;
         }
         MCK(run(ahead[has_ahead[k]], sms, P));  // the look-ahead launch (one or two problems)
+        MCK(cudaEventRecord(ws.mx_ev[4], P));     // row k + 1 is final: T(k + 1) may start
         if (has_bulk[k] >= 0) {
             MCK(cudaStreamWaitEvent(U, evT[u & 1], 0));
             MCK(run(bulk[has_bulk[k]], std::max(1, sms - reserve), U));
