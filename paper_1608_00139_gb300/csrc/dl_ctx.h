@@ -45,6 +45,9 @@ struct Workspace {
     cudaStream_t mx_stream[4] = {};  // + the inverse's stream (least priority), the panel transposes'
     cudaEvent_t mx_ev[6] = {};
     cudaEvent_t mx_gev[32] = {};      // a group of the LU is final (the inverse may start on it)
+    cudaGraphExec_t mx_graph = nullptr;  // the factorisation and inverse of the last size, captured
+    std::string mx_graph_key;
+    int mx_graph_launches = 0;
     BatchPlan *batch_plan = nullptr;
     bool last_heavy = false;  // the last closure on this workspace had rows of > 256 successors
     bool last_rows_closed = false;  // ... was closed by the Iteration on single rows alone

@@ -970,7 +970,8 @@ dl_status tc_mixed(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &
     // SMs the bulk update leaves to the chain (tuned per size bucket, else 32)
     const int reserve = std::min(std::max(1, tuned(ctx, np).mx_reserve), std::max(1, sms - 1));
 
-    // ---- LU with look-ahead --------------------------------------------------------------
+    // ---- LU with look-ahead, then W = A^-1 (enqueued on s, P, U, V, Q; all join s) ---------
+    auto enqueue = [&]() -> dl_status {
     ph.to("mixed:lu");
     MCK(cudaEventRecord(ws.mx_ev[0], s));  // the table and A are ready on s
     MCK(cudaStreamWaitEvent(P, ws.mx_ev[0], 0));
@@ -1063,7 +1064,7 @@ dl_status tc_mixed(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &
     MCK(cudaEventRecord(ws.mx_ev[1], P));
     MCK(cudaStreamWaitEvent(s, ws.mx_ev[1], 0));
 
-    MCK(cudaEventRecord(ev[5], s));
+    MCK(cudaEventRecordWithFlags(ev[5], s, cudaEventRecordExternal));  // the LU's end (a node in a graph)
 
     // ---- W = A^-1: the remaining groups' inverses and forward solves, then the backward solve --
     ph.to("mixed:inverse");
@@ -1074,6 +1075,49 @@ dl_status tc_mixed(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &
     ++launches;
     MCK(cudaEventRecord(ws.mx_ev[2], V));
     MCK(cudaStreamWaitEvent(s, ws.mx_ev[2], 0));
+    return DL_OK;
+    };
+    // The work above is a fixed sequence of about six hundred small launches for a given size:
+    // it is captured once as a CUDA graph (per workspace, size, tuned shape and buffers) and
+    // replayed, which removes most of the host launch cost and the gaps between dependent
+    // launches on the chain.
+    char gkey[512];
+    std::snprintf(gkey, sizeof gkey, "%d %lld %d %d %d %d %llu %p %p %p %p %p %p %p %p %p %p %p %p %p %p", N,
+                  static_cast<long long>(np), nb, G, grouped, reserve, static_cast<unsigned long long>(ctx->budget_ns),
+                  static_cast<void *>(A32), static_cast<void *>(T2), static_cast<void *>(Sinv),
+                  static_cast<void *>(SinvT), static_cast<void *>(YL), static_cast<void *>(YU), static_cast<void *>(GL),
+                  static_cast<void *>(GU), static_cast<void *>(Tg), static_cast<void *>(W32), static_cast<void *>(Wt),
+                  static_cast<void *>(dprob), static_cast<void *>(ws.status), static_cast<void *>(s));
+    if (!ws.mx_graph || ws.mx_graph_key != gkey) {
+        if (ws.mx_graph) {
+            cudaGraphExecDestroy(ws.mx_graph);
+            ws.mx_graph = nullptr;
+        }
+        const int before = launches;
+        MCK(cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal));
+        const dl_status rcap = enqueue();
+        cudaGraph_t graph = nullptr;
+        const cudaError_t ecap = cudaStreamEndCapture(s, &graph);
+        if (rcap != DL_OK || ecap != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            cudaGetLastError();
+            if (rcap != DL_OK) return rcap;
+            set_error("mixed path: capture of the factorisation failed: %s", cudaGetErrorString(ecap));
+            return DL_EDEVICE;
+        }
+        const cudaError_t einst = cudaGraphInstantiate(&ws.mx_graph, graph, 0);
+        cudaGraphDestroy(graph);
+        if (einst != cudaSuccess) {
+            ws.mx_graph = nullptr;
+            set_error("mixed path: graph instantiation failed: %s", cudaGetErrorString(einst));
+            return DL_EDEVICE;
+        }
+        ws.mx_graph_key = gkey;
+        ws.mx_graph_launches = launches - before;
+        launches = before;
+    }
+    MCK(cudaGraphLaunch(ws.mx_graph, s));
+    launches += ws.mx_graph_launches;
     MCK(cudaEventRecord(ev[6], s));
 
     // ---- refinement from Z = 0 -------------------------------------------------------------

@@ -2169,6 +2169,9 @@ void Workspace::release() {
         if (x) cudaEventDestroy(x);
     for (auto &x : mx_stream)
         if (x) cudaStreamDestroy(x);
+    if (mx_graph) cudaGraphExecDestroy(mx_graph);
+    mx_graph = nullptr;
+    mx_graph_key.clear();
     for (auto &x : mx_gev)
         if (x) cudaEventDestroy(x);
     for (auto &x : mx_gev) x = nullptr;
