@@ -392,10 +392,15 @@ def bench_serving(dl, torch, device: int, seconds: float, slots: int = 4) -> dic
     gen = ThreadPoolExecutor(max_workers=min(8, os.cpu_count() or 4))
     lat, lat_arr, queue, spans, errors, lag = [], [], [], [], 0, []
     with dl.Context(device, max_slots=slots) as c:
-        warm = inputs.pa_dag(512, 1)
-        for k in (0, 1):  # load both kinds' kernels outside the stream
-            t, _ = c.submit(k, warm)
-            c.poll(t, -1)
+        # untimed warm-up at the stream's largest size, both kinds, on the default route and on the
+        # tensor-core route AUTO takes for some graphs (squarings, doubling), enough requests to
+        # reach every slot: the slots' workspaces (grow-only) are sized before the stream, so no
+        # request in it pays for an allocation (and a cudaFree, which waits for the whole GPU)
+        big = inputs.pa_dag_into(np.empty((nmax, nmax), np.uint8), 1)
+        for route in ("bool_fp8", "auto"):
+            warm = [c.submit(k, big, path=route) for k in (0, 1) for _ in range(slots)]
+            for tk, _ in warm:
+                c.poll(tk, -1)
         futs = [gen.submit(make, r) for r in range(count)]  # the ring bounds how far ahead
         outstanding = {}  # ticket -> (slot, handle, request, submit time)
 

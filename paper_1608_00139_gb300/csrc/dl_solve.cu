@@ -2189,12 +2189,15 @@ void Workspace::release() {
 void *Workspace::get(const std::string &name, size_t bytes) {
     Buf &b = bufs[name];
     if (b.p && b.bytes >= bytes) return b.p;
+    // grow by at least a quarter: buffers sized by data (facts, active rows) then rarely grow
+    // again, and a regrowth's cudaFree waits for the whole device
+    const size_t grown = b.p ? b.bytes + b.bytes / 4 : 0;
     if (b.p) {
         cudaFree(b.p);
         b.p = nullptr;
         b.bytes = 0;
     }
-    size_t want = (bytes + 4095) & ~static_cast<size_t>(4095);
+    size_t want = (std::max(bytes, grown) + 4095) & ~static_cast<size_t>(4095);
     if (device_alloc(&b.p, want) != cudaSuccess) {
         cudaGetLastError();
         b.p = nullptr;
