@@ -6,6 +6,7 @@
 
 #include <cstdint>
 #include <string>
+#include <utility>
 
 namespace dl {
 
@@ -93,10 +94,28 @@ bool gemm_make_problem(GemmProblem *p, GemmKind kind, bool b_kmajor, int bn, int
 // (device ints, written by an earlier kernel) only the problems it lists are computed:
 // d_sched[0] = count A, d_sched[1] = their tiles, d_sched[2 + j] = problem index of entry j,
 // d_sched[2 + nprob + j] = first tile of entry j; total_tiles and grid are then upper bounds.
+// pdl: a programmatic launch (it may start while the previous kernel on the stream finishes;
+// its set-up overlaps that kernel's end and it reads its operands only after that kernel is done).
 cudaError_t gemm_launch(GemmKind kind, bool b_kmajor, int bn, GemmEpi epi,
                         const GemmProblem *d_probs, int nprob, int total_tiles, int grid,
                         int *d_status, uint64_t budget_ns, cudaStream_t stream,
-                        const int *d_sched = nullptr);
+                        const int *d_sched = nullptr, bool pdl = false);
+// Launch kernel<<<grid, block, smem, s>>>(args...) with programmatic stream serialisation.
+template <typename... Params, typename... Args>
+cudaError_t launch_programmatic(void (*kernel)(Params...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                                Args &&...args) {
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = s;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    return cudaLaunchKernelEx(&cfg, kernel, std::forward<Args>(args)...);
+}
 int gemm_tile_m();
 // A 2-D tensor map (no swizzle) of a row-major matrix (rows x cols elements, ld elements per
 // row) with a box of box_y rows x box_x elements, for TMA loads outside the GEMM.

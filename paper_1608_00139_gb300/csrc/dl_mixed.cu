@@ -228,6 +228,8 @@ __global__ void __launch_bounds__(kDiagThreads) diag_inv_kernel(const float *__r
                                                                 float *__restrict__ Sinv, float *__restrict__ SinvT,
                                                                 int *status) {
     static_assert(BL == 128 && kDiagThreads == 256, "64 x 64 quarters, 4 x 4 tiles");
+    grid_dep_launch();  // the successor (L21) may launch now: it waits for this kernel's end
+    grid_dep_wait();    // A's block as the look-ahead before leaves it
     extern __shared__ __align__(16) float dsm[];
     float *S = dsm;                 // BL x kLdS
     float *Yq = S + BL * kLdS;      // kHB x kLdH
@@ -961,10 +963,10 @@ dl_status tc_mixed(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &
         MCK(gemm_prepare(KIND_TF32, true, bn, EPI_SUB_F32));
     }
     MCK(cudaFuncSetAttribute(diag_inv_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(kDiagSmem)));
-    auto run = [&](const Launch &L, int max_grid, cudaStream_t on) -> cudaError_t {
+    auto run = [&](const Launch &L, int max_grid, cudaStream_t on, bool pdl = false) -> cudaError_t {
         ++launches;
         return gemm_launch(KIND_TF32, true, L.bn, L.epi, dprob + L.first, L.count, L.tiles,
-                           std::min(L.tiles, max_grid), ws.status, ctx->budget_ns, on);
+                           std::min(L.tiles, max_grid), ws.status, ctx->budget_ns, on, nullptr, pdl);
     };
     const int sms = ctx->sms;
     // SMs the bulk update leaves to the chain (tuned per size bucket, else 32)
@@ -1030,13 +1032,16 @@ dl_status tc_mixed(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &
             ++launches;
             MCK(cudaEventRecord(ws.mx_ev[5], Q));
         }
-        diag_inv_kernel<<<1, kDiagThreads, kDiagSmem, P>>>(A32 + kb * np + kb, np, Sinv + kb * BL, SinvT + kb * BL,
-                                                           ws.status);
-        MCK(cudaGetLastError());
+        // The chain's kernels are programmatic launches: each one's launch and set-up overlap the
+        // end of the one before it on P (diag_inv lets L21 launch at once: L21's CTAs wait on SMs
+        // it does not use).
+        MCK(launch_programmatic(diag_inv_kernel, dim3(1), dim3(kDiagThreads), kDiagSmem, P,
+                                static_cast<const float *>(A32 + kb * np + kb), static_cast<int64_t>(np),
+                                Sinv + kb * BL, SinvT + kb * BL, ws.status));
         ++launches;
         if (rem <= 0) break;
         // L21 runs beside the bulk update of the previous unit, which leaves it `reserve` SMs
-        MCK(run(l21[has_l21[k]], bulk_pending || (k > 0 && has_bulk[k - 1] >= 0) ? reserve : sms, P));
+        MCK(run(l21[has_l21[k]], bulk_pending || (k > 0 && has_bulk[k - 1] >= 0) ? reserve : sms, P, true));
         if ((k + 1) % kSolveGroup == 0 && k + 1 < nb) {  // group (k + 1) / kSolveGroup - 1 is final
             const int g = (k + 1) / kSolveGroup - 1;
             MCK(cudaEventRecord(ws.mx_gev[g], P));
@@ -1049,7 +1054,7 @@ dl_status tc_mixed(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &
             MCK(cudaStreamWaitEvent(P, evB[pending_unit & 1], 0));
             bulk_pending = false;
         }
-        MCK(run(ahead[has_ahead[k]], sms, P));  // the look-ahead launch (one or two problems)
+        MCK(run(ahead[has_ahead[k]], sms, P, true));  // the look-ahead launch (one or two problems)
         MCK(cudaEventRecord(ws.mx_ev[4], P));     // row k + 1 is final: T(k + 1) may start
         if (has_bulk[k] >= 0) {
             MCK(cudaStreamWaitEvent(U, evT[u & 1], 0));

@@ -32,6 +32,16 @@ __device__ __forceinline__ bool elect_one_sync() {
     return pred != 0;
 }
 
+// ---- programmatic dependent launch --------------------------------------------------------
+// A kernel launched with programmatic stream serialisation may start while its predecessor on the
+// stream is still running: grid_dep_wait() blocks until that predecessor has completed and its
+// memory operations are visible (it returns at once when the launch had no such predecessor), and
+// grid_dep_launch() lets the successor's launch begin once every CTA has issued it or exited.
+// Neither is a poll: the predecessor's completion ends the wait, and every kernel here ends by
+// itself (its own waits are bounded).
+__device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void grid_dep_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // ---- mbarrier ----------------------------------------------------------------------------
 __device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));

@@ -213,6 +213,7 @@ __global__ void __launch_bounds__(kThreads, 1)
     // A device schedule fixes the tile count; CTAs without a tile leave before any setup
     // (the value is the same for every thread of the CTA).
     if (sched != nullptr) {
+        grid_dep_wait();  // the schedule is written by an earlier kernel
         total_tiles = sched[1];
         if (static_cast<int>(blockIdx.x) >= total_tiles) return;
     }
@@ -252,6 +253,9 @@ __global__ void __launch_bounds__(kThreads, 1)
     __syncthreads();
     tc_fence_after();
     const uint32_t tmem_base = *tmem_slot;
+    // Under a programmatic launch the set-up above overlaps the predecessor's end; its outputs
+    // (this launch's operands and C) are read only from here on.
+    grid_dep_wait();
 
     if (warp == 0) {
         // ------------------------------ TMA producer ------------------------------------
@@ -300,6 +304,7 @@ __global__ void __launch_bounds__(kThreads, 1)
                 mbar_wait_bounded(&full[i % C::S], static_cast<uint32_t>((i / C::S) & 1u),
                                   budget_ns, status, ST_TIMEOUT_DRAIN);
         }
+        grid_dep_launch();  // (all lanes) no load left to issue: the successor may start launching
     } else if (warp == 1) {
         // ------------------------------ MMA issuer --------------------------------------
         if (elect_one_sync()) {
@@ -358,6 +363,7 @@ __global__ void __launch_bounds__(kThreads, 1)
             umma_commit(drain);
             mbar_wait_bounded(drain, 0u, budget_ns, status, ST_TIMEOUT_DRAIN);
         }
+        grid_dep_launch();
     } else {
         // ------------------------------ epilogue (warps 2..9) ---------------------------
         const int quarter = warp & 3;       // TMEM lanes this warp may access
@@ -367,11 +373,12 @@ __global__ void __launch_bounds__(kThreads, 1)
         int acc = 0;
         uint32_t acc_ph = 0;
         for (int tile = blockIdx.x; tile < total_tiles; tile += gridDim.x) {
+            if (tile + static_cast<int>(gridDim.x) >= total_tiles) grid_dep_launch();  // the CTA's last tile
             int local = 0;
             const GemmProblem *P = resolve_tile(probs, nprob, sched, tile, &local);
             if (P == nullptr) continue;
             int mb, nb;
-                tile_coords(P, local, mb, nb);
+            tile_coords(P, local, mb, nb);
             const int row = mb * BM + r_in_tile;
             const bool row_ok = row < P->M;
             // the subtracting epilogue loads all of its chunks of C while the MMAs finish (a
@@ -496,13 +503,17 @@ cudaError_t prepare_t() {
 
 template <int KIND, int BN, bool BK_, int EPI>
 cudaError_t launch_t(const GemmProblem *d_probs, int nprob, int total_tiles, const int *sched, int grid,
-                     int *status, uint64_t budget, cudaStream_t s) {
+                     int *status, uint64_t budget, cudaStream_t s, bool pdl) {
     using C = Cfg<KIND, BN>;
     const cudaError_t attr_err = prepare_t<KIND, BN, BK_, EPI>();
     if (attr_err != cudaSuccess) return attr_err;
-    umma_gemm_kernel<KIND, BN, BK_, EPI><<<grid, kThreads, C::SMEM, s>>>(d_probs, nprob, total_tiles,
-                                                                         sched, status, budget);
-    return cudaGetLastError();
+    if (!pdl) {
+        umma_gemm_kernel<KIND, BN, BK_, EPI><<<grid, kThreads, C::SMEM, s>>>(d_probs, nprob, total_tiles,
+                                                                             sched, status, budget);
+        return cudaGetLastError();
+    }
+    return launch_programmatic(umma_gemm_kernel<KIND, BN, BK_, EPI>, dim3(grid), dim3(kThreads), C::SMEM, s, d_probs,
+                               nprob, total_tiles, sched, status, budget);
 }
 
 }  // namespace
@@ -582,12 +593,12 @@ bool gemm_make_problem(GemmProblem *p, GemmKind kind, bool b_kmajor, int bn, int
 
 cudaError_t gemm_launch(GemmKind kind, bool b_kmajor, int bn, GemmEpi epi, const GemmProblem *d_probs,
                         int nprob, int total_tiles, int grid, int *d_status, uint64_t budget_ns,
-                        cudaStream_t stream, const int *d_sched) {
+                        cudaStream_t stream, const int *d_sched, bool pdl) {
     if (total_tiles <= 0) return cudaSuccess;
     if (grid > total_tiles) grid = total_tiles;
     const int *sc = d_sched;
 #define DL_GEMM_T(K_, BN_, BKM_, EPI_) \
-    launch_t<K_, BN_, BKM_, EPI_>(d_probs, nprob, total_tiles, sc, grid, d_status, budget_ns, stream)
+    launch_t<K_, BN_, BKM_, EPI_>(d_probs, nprob, total_tiles, sc, grid, d_status, budget_ns, stream, pdl)
     if (kind == KIND_F8 && epi == EPI_BOOL) {
         if (bn == 256)
             return b_kmajor ? DL_GEMM_T(KIND_F8, 256, true, EPI_BOOL) : DL_GEMM_T(KIND_F8, 256, false, EPI_BOOL);
