@@ -116,7 +116,8 @@ typedef struct {
  * DL_EDEVICE unless the device is compute capability 10.3 (GB300). */
 DL_API dl_status dl_create(dl_ctx **out, int device, const dl_config *cfg);
 
-/* Wait for outstanding work, free every device buffer of the context, free the context. */
+/* Wait for outstanding work, free every device buffer of the context, free the context.  Every
+ * program created on the context must be destroyed first (dl_program_destroy uses its context). */
 DL_API dl_status dl_destroy(dl_ctx *ctx);
 
 /* Message for the last failed call on this thread ("" if none).  Valid until the next call
@@ -363,7 +364,7 @@ typedef struct dl_program dl_program;
 /* Parse and check `text` (a NUL-terminated string) into a program bound to ctx.  The context
    must outlive the program. */
 DL_API dl_status dl_program_create(dl_ctx *ctx, const char *text, dl_program **out);
-/* Free a program (NULL is a no-op). */
+/* Free a program (NULL is a no-op); its context must still exist. */
 DL_API dl_status dl_program_destroy(dl_program *prog);
 /* Give base relation `pred` the n x n 0/1 matrix R (row-major bytes, in `mem`); the bytes are
    copied.  Every base relation of a program must have the same n (n >= 0).  DL_EINVAL if pred

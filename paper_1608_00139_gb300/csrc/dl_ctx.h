@@ -42,8 +42,9 @@ struct Workspace {
     bool ready = false;
     // mixed path: the LU's critical chain (greatest priority) and its bulk updates (least
     // priority), and events ordering them; created on first use
-    cudaStream_t mx_stream[4] = {};  // + the inverse's stream (least priority), the panel transposes'
-    cudaEvent_t mx_ev[6] = {};
+    cudaStream_t mx_stream[5] = {};  // + the inverse's stream (least priority), the panel transposes',
+                                     // the look-ahead's off-chain part
+    cudaEvent_t mx_ev[8] = {};
     cudaEvent_t mx_gev[32] = {};      // a group of the LU is final (the inverse may start on it)
     cudaGraphExec_t mx_graph = nullptr;  // the factorisation and inverse of the last size, captured
     std::string mx_graph_key;

@@ -6,14 +6,16 @@
 //      rows, proof of Proposition 1, so every Schur complement is too and block elimination is
 //      stable):  A = L U with L unit block lower (L_ik = A_ik S_kk^-1) and U block upper
 //      (U_kj = A_kj after the eliminations before k, diagonal blocks S_kk).  Per block k:
-//        diag:  S_kk^-1 by Gauss-Jordan on the CUDA cores (FP32, one CTA);
+//        update: block row and column k receive the updates of the steps since the last bulk
+//               update (left-looking, one GEMM, K up to 4 b);
+//        diag:  S_kk^-1 (one CTA: Gauss-Jordan on the CUDA cores, products on mma.sync TF32);
 //        L21 = A21 S_kk^-1 (in place), T = A12^T;
-//        look-ahead: the next block column and block row, A -= L21 U12 there;
-//        bulk:  the rest of the trailing matrix, A22 -= L21 U12.
-//      The look-ahead and the chain that needs it (the next diagonal block, its L21 and T) run
-//      on a stream of the greatest priority, the bulk update on a stream of the least priority
-//      and on all SMs but a reserve (32, or tuned per size), so the chain of 128 x 128 steps proceeds while the bulk
-//      update of the previous block streams through HBM.
+//        bulk:  after every unit of G = 2 or 4 steps (single steps at the end), the rest of the
+//               trailing matrix, A22 -= L21 U12 with K = G b for the whole unit.
+//      The chain (the diagonal block's update, diag, L21) runs on a stream of the greatest
+//      priority as programmatic launches, the rest of each step's update and the transposes on
+//      two more, the bulk update on a middle priority and on all SMs but a reserve (tuned per
+//      size), so the chain of 128 x 128 steps proceeds while the bulk update streams through HBM.
 //   3. W = A^-1 in FP32: the block solves applied to the identity (kept transposed, Z = I A^-T,
 //      by groups of 8 blocks with precomputed inverses of the groups' diagonal parts, so that
 //      every product is a tensor-core GEMM with K = 1024), then W = Z^T.
@@ -145,28 +147,56 @@ __device__ void quarter_product(const float *P, int ldp, const float *Q, int ldq
     }
 }
 
-// One elimination step on a thread's T x T tile: the tile's row / column kk hold the pivot row /
-// column when ro / co; c = the pivot column at the tile's rows, rp = the pivot row at the tile's
-// columns times p = 1 / pivot.
-template <int T>
-__device__ __forceinline__ void gj_step(float (&a)[T][T], int kk, bool ro, bool co, const float (&c)[T],
-                                        const float (&rp)[T], float p) {
+// One elimination step on a thread's 4 x 4 tile, pivot kk of the tile (ro / co: the tile holds the
+// pivot row / column; c = the pivot column at the tile's rows, rp = the pivot row at the tile's
+// columns times p = 1 / pivot).  Written as one update a <- a - c' rp' for every element, with
+// c'[kk] = c[kk] - 1 on the pivot row, rp'[kk] = p on the pivot column and the pivot column of a
+// replaced by the unit vector e_k: that gives the pivot row times p, the pivot column times -p, p
+// at the pivot and a - c rp elsewhere, one FMA per element instead of a select per element.
+template <int kk>
+__device__ __forceinline__ void gj_step(float (&a)[4][4], bool ro, bool co, const float (&c)[4], const float (&rp)[4],
+                                        float p) {
+    float cc[4], rr[4];
 #pragma unroll
-    for (int i = 0; i < T; ++i) {
+    for (int i = 0; i < 4; ++i) cc[i] = c[i], rr[i] = rp[i];
+    if (ro) cc[kk] -= 1.f;
+    if (co) {
+        rr[kk] = p;
 #pragma unroll
-        for (int j = 0; j < T; ++j) {
-            const float upd = fmaf(-c[i], rp[j], a[i][j]);
-            if (i == kk && j == kk) {
-                a[i][j] = ro && co ? p : ro ? rp[j] : co ? -c[i] * p : upd;
-            } else if (i == kk) {
-                a[i][j] = ro ? rp[j] : upd;
-            } else if (j == kk) {
-                a[i][j] = co ? -c[i] * p : upd;
-            } else {
-                a[i][j] = upd;
-            }
-        }
+        for (int i = 0; i < 4; ++i) a[i][kk] = (ro && i == kk) ? 1.f : 0.f;
     }
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) a[i][j] = fmaf(-cc[i], rr[j], a[i][j]);
+}
+
+// Steps k = kb + kk and k + 1 from one publication of rows and columns k, k + 1 (buffer buf).
+template <int kk>
+__device__ __forceinline__ void gj_pair(float (&a)[4][4], int r0, int c0, int k, bool ro, bool co,
+                                        float (*rowbuf)[kHB], float (*colbuf)[kHB], bool *bad) {
+    const float2 s0 = *reinterpret_cast<const float2 *>(&rowbuf[0][k]);
+    const float2 s1 = *reinterpret_cast<const float2 *>(&rowbuf[1][k]);
+    const float s00 = s0.x, s01 = s0.y, s10 = s1.x, s11 = s1.y;
+    const float4 cv = *reinterpret_cast<const float4 *>(&colbuf[0][r0]);
+    const float4 c1v = *reinterpret_cast<const float4 *>(&colbuf[1][r0]);
+    const float4 rv = *reinterpret_cast<const float4 *>(&rowbuf[0][c0]);
+    const float4 r1v = *reinterpret_cast<const float4 *>(&rowbuf[1][c0]);
+    const float p = __fdividef(1.0f, s00);
+    const float c[4] = {cv.x, cv.y, cv.z, cv.w}, c1[4] = {c1v.x, c1v.y, c1v.z, c1v.w};
+    const float rp[4] = {rv.x * p, rv.y * p, rv.z * p, rv.w * p}, r1[4] = {r1v.x, r1v.y, r1v.z, r1v.w};
+    gj_step<kk>(a, ro, co, c, rp, p);  // step k
+    // row and column k + 1 as step k leaves them (the same uniform update), and the next pivot
+    const float s01p = s01 * p;
+    const float piv2 = fmaf(-s10, s01p, s11);
+    const float p2 = __fdividef(1.0f, piv2);
+    *bad |= !(s00 > 0.0f) || !isfinite(p) || !(piv2 > 0.0f) || !isfinite(p2);
+    float c2[4], rp2[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) c2[i] = fmaf(-(ro && i == kk ? c[i] - 1.f : c[i]), s01p, c1[i]);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) rp2[j] = (co && j == kk ? -s10 * p : fmaf(-s10, rp[j], r1[j])) * p2;
+    gj_step<kk + 1>(a, ro, co, c2, rp2, p2);  // step k + 1
 }
 
 // In-place Gauss-Jordan inverse of the 64 x 64 quarter at R (row stride ld); two pivots per
@@ -187,35 +217,16 @@ __device__ void quarter_inverse(float *R, int ld, float (*rowbuf)[2][kHB], float
             if (ro)
 #pragma unroll
                 for (int h = 0; h < 2; ++h)
-#pragma unroll
-                    for (int j = 0; j < 4; ++j) rowbuf[buf][h][c0 + j] = a[kk + h][j];
+                    *reinterpret_cast<float4 *>(&rowbuf[buf][h][c0]) =
+                        make_float4(a[kk + h][0], a[kk + h][1], a[kk + h][2], a[kk + h][3]);
             if (co)
 #pragma unroll
                 for (int h = 0; h < 2; ++h)
-#pragma unroll
-                    for (int i = 0; i < 4; ++i) colbuf[buf][h][r0 + i] = a[i][kk + h];
+                    *reinterpret_cast<float4 *>(&colbuf[buf][h][r0]) =
+                        make_float4(a[0][kk + h], a[1][kk + h], a[2][kk + h], a[3][kk + h]);
             __syncthreads();
-            const float s00 = rowbuf[buf][0][k], s01 = rowbuf[buf][0][k + 1];
-            const float s10 = rowbuf[buf][1][k], s11 = rowbuf[buf][1][k + 1];
-            const float p = __fdividef(1.0f, s00);
-            float c[4], c1[4], r1[4], rp[4];
-#pragma unroll
-            for (int q = 0; q < 4; ++q) {
-                c[q] = colbuf[buf][0][r0 + q], c1[q] = colbuf[buf][1][r0 + q];
-                rp[q] = rowbuf[buf][0][c0 + q] * p, r1[q] = rowbuf[buf][1][c0 + q];
-            }
-            gj_step<4>(a, kk, ro, co, c, rp, p);  // step k
-            // row and column k + 1 as step k leaves them, and the next pivot
-            const float s01p = s01 * p;
-            const float piv2 = fmaf(-s10, s01p, s11);
-            const float p2 = __fdividef(1.0f, piv2);
-            *bad |= !(s00 > 0.0f) || !isfinite(p) || !(piv2 > 0.0f) || !isfinite(p2);
-            float c2[4], rp2[4];
-#pragma unroll
-            for (int i = 0; i < 4; ++i) c2[i] = ro && i == kk ? s01p : fmaf(-c[i], s01p, c1[i]);
-#pragma unroll
-            for (int j = 0; j < 4; ++j) rp2[j] = (co && j == kk ? -s10 * p : fmaf(-s10, rp[j], r1[j])) * p2;
-            gj_step<4>(a, kk + 1, ro, co, c2, rp2, p2);  // step k + 1
+            if (kk == 0) gj_pair<0>(a, r0, c0, k, ro, co, rowbuf[buf], colbuf[buf], bad);
+            else gj_pair<2>(a, r0, c0, k, ro, co, rowbuf[buf], colbuf[buf], bad);
         }
     }
 #pragma unroll
@@ -238,9 +249,7 @@ __global__ void __launch_bounds__(kDiagThreads) diag_inv_kernel(const float *__r
     auto *colbuf = rowbuf + 2;
     for (int e = threadIdx.x; e < BL * BL / 4; e += kDiagThreads) {
         const int r = e / (BL / 4), c = 4 * (e % (BL / 4));
-        const float4 v = *reinterpret_cast<const float4 *>(A + r * lda + c);
-        float *d = S + r * kLdS + c;
-        d[0] = v.x, d[1] = v.y, d[2] = v.z, d[3] = v.w;
+        *reinterpret_cast<float4 *>(S + r * kLdS + c) = *reinterpret_cast<const float4 *>(A + r * lda + c);
     }
     __syncthreads();
     float *Pq = S, *Bq = S + kHB, *Cq = S + kHB * kLdS, *Dq = S + kHB * kLdS + kHB;
@@ -260,10 +269,20 @@ __global__ void __launch_bounds__(kDiagThreads) diag_inv_kernel(const float *__r
     quarter_product(Bq, kLdS, Xq, kLdH, Pq, kLdS, -1.f, 1.f);  // upper left: P^-1 - (-Y Sd) X
     __syncthreads();
     if (bad) atomicOr(status, ST_BAD_INPUT);
-    for (int e = threadIdx.x; e < BL * BL; e += kDiagThreads) {
-        const int r = e / BL, c = e % BL;
-        Sinv[e] = S[r * kLdS + c];
-        SinvT[e] = S[c * kLdS + r];
+    for (int e = threadIdx.x; e < BL * BL / 4; e += kDiagThreads) {  // S^-1, row-major
+        const int r = e / (BL / 4), c = 4 * (e % (BL / 4));
+        *reinterpret_cast<float4 *>(Sinv + r * BL + c) = *reinterpret_cast<const float4 *>(S + r * kLdS + c);
+    }
+    // S^-T through a 32 x 33 tile per warp (in the quarter buffers, free now): conflict-free
+    // shared-memory reads and whole 128-byte rows written
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    float *tw = Yq + warp * 32 * 33;
+    for (int t = warp; t < (BL / 32) * (BL / 32); t += kDiagThreads / 32) {
+        const int tr = 32 * (t / (BL / 32)), tc = 32 * (t % (BL / 32));
+        for (int i = 0; i < 32; ++i) tw[lane * 33 + i] = S[(tr + i) * kLdS + tc + lane];
+        __syncwarp();
+        for (int j = 0; j < 32; ++j) SinvT[(tc + j) * BL + tr + lane] = tw[j * 33 + lane];
+        __syncwarp();
     }
 }
 
@@ -723,6 +742,7 @@ dl_status mixed_streams(Workspace &ws) {
     MCK(cudaStreamCreateWithPriority(&ws.mx_stream[1], cudaStreamNonBlocking, std::max(greatest, least - 1)));
     MCK(cudaStreamCreateWithPriority(&ws.mx_stream[2], cudaStreamNonBlocking, least));
     MCK(cudaStreamCreateWithPriority(&ws.mx_stream[3], cudaStreamNonBlocking, greatest));
+    MCK(cudaStreamCreateWithPriority(&ws.mx_stream[4], cudaStreamNonBlocking, greatest));
     for (auto &e : ws.mx_ev) MCK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     for (auto &e : ws.mx_gev) MCK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
     return DL_OK;
@@ -789,6 +809,7 @@ dl_status tc_mixed(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &
     dl_status rc = mixed_streams(ws);
     if (rc) return rc;
     cudaStream_t P = ws.mx_stream[0], U = ws.mx_stream[1], V = ws.mx_stream[2], Q = ws.mx_stream[3];
+    cudaStream_t Rs = ws.mx_stream[4];
     auto *A32 = static_cast<float *>(ws.get("mx_A", np * np * 4));
     auto *W32 = static_cast<float *>(ws.get("mx_W", np * np * 4));   // Z = A^-T, then R
     auto *Wt = static_cast<float *>(ws.get("mx_Wt", np * np * 4));   // W = A^-1
@@ -839,18 +860,20 @@ dl_status tc_mixed(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &
 
     // ---- GEMM table ---------------------------------------------------------------------
     Table tb;
-    std::vector<Launch> l21, ahead, bulk, wfwd, wbwd, refine;
+    std::vector<Launch> l21, udiag, urest, bulk, wfwd, wbwd, refine;
     double flops_lu = 0, flops_w = 0, flops_ref = 0;
     const Operand opA{A32, np, np, np, 0, 0};
     const Operand opS{Sinv, np, BL, BL, 0, 0}, opST{SinvT, np, BL, BL, 0, 0};
     bool ok = true;
-    std::vector<int> has_bulk(nb, -1), has_ahead(nb, -1), has_l21(nb, -1);
-    // Steps k < grouped go in units of G consecutive steps (G = 2 or 4): step q of a unit (q = 0 ..
-    // G - 1) updates, in its look-ahead, the next G - q block columns and rows (up to the first
-    // block of the next unit), and the unit's last step carries one bulk update of the rest with
-    // K = G BL for all G steps, which moves the trailing matrix G times less often.  While the
-    // bulk update, not the chain of diagonal steps, bounds a step, the longer look-ahead costs
-    // nothing.  Later steps are single (K = BL).  G and the grouped steps: tuned per size.
+    std::vector<int> has_bulk(nb, -1), has_udiag(nb, -1), has_urest(nb, -1), has_l21(nb, -1);
+    // Steps k < grouped go in units of G consecutive steps (G = 2 or 4), later steps are single.
+    // Within a unit the updates are left-looking: before step j's pivot, block row and column j
+    // receive, in one GEMM with K = (j - s) BL, the updates of every step s .. j - 1 since the
+    // unit's start (of the whole previous unit when j starts a unit) -- its diagonal block as one
+    // launch on the chain, the rest beside the diagonal inverse.  The unit's last step then issues
+    // one bulk update, K = G BL, of the rows and columns from the second block after it.  So the
+    // chain carries one small GEMM per step, each block row and column is read and written once
+    // per unit, and the trailing matrix G times less often.  G and the grouped steps: tuned per size.
     const TuneEntry tn = tuned(ctx, np);
     const int G = tn.mx_group == 4 ? 4 : 2;
     int grouped = tn.mx_pairs >= 0 ? tn.mx_pairs : nb / 2;
@@ -858,29 +881,38 @@ dl_status tc_mixed(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &
     auto unit_of = [&](int k) { return k < grouped ? k / G : grouped / G + (k - grouped); };
     auto pos_of = [&](int k) { return k < grouped ? k % G : 0; };          // q, the step's place in its unit
     auto size_of = [&](int k) { return k < grouped ? G : 1; };             // the unit's number of steps
+    auto start_of = [&](int k) { return k - pos_of(k); };
     const int64_t ldT = static_cast<int64_t>(kMaxGroup) * BL;
-    for (int k = 0; k < nb && ok; ++k) {
-        const int kb = k * BL, rem = N - kb - BL;
-        if (rem <= 0) break;
-        const int q = pos_of(k), gu = size_of(k);
-        const Operand opT{T2 + static_cast<int64_t>(unit_of(k) & 1) * np * ldT, np, ldT, ldT, 0, 0};
-        // L21 = A21 S^-1 (in place: each output tile reads only its own rows of A21)
-        has_l21[k] = static_cast<int>(l21.size());
-        ok = tb.add(l21, EPI_STORE_F32, BL, rem, BL, BL, at(opA, kb + BL, kb), at(opST, kb, 0), A32, np, kb + BL, kb,
-                    false, &flops_lu);
-        // look-ahead: the next w block columns (all rows below) and block rows (columns beyond)
-        const int w = (gu - q) * BL;
-        has_ahead[k] = static_cast<int>(ahead.size());
-        ok = ok && tb.add(ahead, EPI_SUB_F32, BL, rem, std::min(w, rem), BL, at(opA, kb + BL, kb),
-                          at(opT, kb + BL, q * BL), A32, np, kb + BL, kb + BL, false, &flops_lu);
-        if (ok && rem > w) {
-            ok = tb.add(ahead, EPI_SUB_F32, BL, w, rem - w, BL, at(opA, kb + BL, kb), at(opT, kb + BL + w, q * BL),
-                        A32, np, kb + BL, kb + BL + w, true, &flops_lu);
-            if (ok && q == gu - 1) {  // the unit's bulk update (K = gu BL)
-                has_bulk[k] = static_cast<int>(bulk.size());
-                ok = tb.add(bulk, EPI_SUB_F32, 256, rem - BL, rem - BL, gu * BL, at(opA, kb + 2 * BL, kb - q * BL),
-                            at(opT, kb + 2 * BL, 0), A32, np, kb + 2 * BL, kb + 2 * BL, false, &flops_lu);
+    // T(k) = A_{k, >k}^T of every step of a unit, side by side (row = absolute column), two units' worth
+    auto opT_of = [&](int k) {
+        return Operand{T2 + static_cast<int64_t>(unit_of(k) & 1) * np * ldT, np, ldT, ldT, 0, 0};
+    };
+    for (int j = 0; j < nb && ok; ++j) {
+        const int jb = j * BL, rem = N - jb - BL;
+        const int q = pos_of(j), gu = size_of(j), k0 = start_of(j);
+        if (j > 0) {  // the left-looking update of block row and column j
+            const int s = q >= 1 ? k0 : start_of(j - 1), K = (j - s) * BL;
+            const Operand opTs = opT_of(s);
+            has_udiag[j] = static_cast<int>(udiag.size());
+            ok = tb.add(udiag, EPI_SUB_F32, BL, BL, BL, K, at(opA, jb, s * BL), at(opTs, jb, 0), A32, np, jb, jb,
+                        false, &flops_lu);
+            if (ok && rem > 0) {
+                has_urest[j] = static_cast<int>(urest.size());
+                ok = tb.add(urest, EPI_SUB_F32, BL, rem, BL, K, at(opA, jb + BL, s * BL), at(opTs, jb, 0), A32, np,
+                            jb + BL, jb, false, &flops_lu);
+                ok = ok && tb.add(urest, EPI_SUB_F32, BL, BL, rem, K, at(opA, jb, s * BL), at(opTs, jb + BL, 0), A32,
+                                  np, jb, jb + BL, true, &flops_lu);
             }
+        }
+        if (!ok || rem <= 0) break;
+        // L21 = A21 S^-1 (in place: each output tile reads only its own rows of A21)
+        has_l21[j] = static_cast<int>(l21.size());
+        ok = tb.add(l21, EPI_STORE_F32, BL, rem, BL, BL, at(opA, jb + BL, jb), at(opST, jb, 0), A32, np, jb + BL, jb,
+                    false, &flops_lu);
+        if (ok && q == gu - 1 && rem > BL) {  // the unit's bulk update (K = gu BL)
+            has_bulk[j] = static_cast<int>(bulk.size());
+            ok = tb.add(bulk, EPI_SUB_F32, 256, rem - BL, rem - BL, gu * BL, at(opA, jb + 2 * BL, k0 * BL),
+                        at(opT_of(j), jb + 2 * BL, 0), A32, np, jb + 2 * BL, jb + 2 * BL, false, &flops_lu);
         }
     }
     // Inverses of the diagonal groups (kSolveGroup blocks each), once per factorisation.
@@ -992,12 +1024,15 @@ dl_status tc_mixed(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &
     identity_kernel<<<static_cast<unsigned>((np + 255) / 256), 256, 0, V>>>(W32, N);
     MCK(cudaGetLastError());
     launches += 2;
+    // After the LU, V's GEMMs are programmatic launches as well (during it they are not: their
+    // early CTAs would hold SMs the chain needs).
+    bool lu_done = false;
     auto run_steps = [&](const std::vector<Step> &steps, const std::vector<Launch> &list, int gs_only) -> cudaError_t {
         for (const Step &sp : steps) {
             if (gs_only >= 0 && sp.gs != gs_only) continue;
             cudaError_t e;
             if (sp.launch >= 0) {
-                if ((e = run(list[sp.launch], sms, V)) != cudaSuccess) return e;
+                if ((e = run(list[sp.launch], sms, V, lu_done)) != cudaSuccess) return e;
             } else if ((e = cudaMemcpy2DAsync(W32 + sp.gs, np * 4, Tg, GW * 4, static_cast<size_t>(sp.w) * 4, sp.rows,
                                               cudaMemcpyDeviceToDevice, V)) != cudaSuccess) {
                 return e;
@@ -1009,7 +1044,7 @@ dl_status tc_mixed(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &
     auto inverse_group = [&](int g) -> cudaError_t {  // on V, after the group's LU steps
         cudaError_t e;
         for (const Launch &L : ginv[g])
-            if ((e = run(L, sms, V)) != cudaSuccess) return e;
+            if ((e = run(L, sms, V, lu_done)) != cudaSuccess) return e;
         const int64_t gs = static_cast<int64_t>(g) * GW;
         const int w = static_cast<int>(std::min<int64_t>(GW, np - gs));
         if ((e = transpose(YL + gs * GW, GW, w, w, GL + gs * GW, GW, V)) != cudaSuccess) return e;
@@ -1019,50 +1054,66 @@ dl_status tc_mixed(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &
         return run_steps(fwd_steps, wfwd, static_cast<int>(gs));
     };
     cudaEvent_t evT[2] = {ws.mx_ev[0], ws.mx_ev[1]}, evB[2] = {ws.mx_ev[2], ws.mx_ev[3]};
-    bool bulk_pending = false;  // the bulk update of the previous unit is queued on U
-    int pending_unit = -1;
-    for (int k = 0; k < nb; ++k) {
-        const int64_t kb = static_cast<int64_t>(k) * BL;
-        const int rem = N - static_cast<int>(kb) - BL;
-        const int u = unit_of(k);
-        if (rem > 0) {  // T(k) = A12^T (row = absolute column) needs only row k, final since look-ahead(k - 1)
-            if (k > 0) MCK(cudaStreamWaitEvent(Q, ws.mx_ev[4], 0));
-            float *Tk = T2 + static_cast<int64_t>(u & 1) * np * ldT + (kb + BL) * ldT + pos_of(k) * BL;
-            MCK(transpose(A32 + kb * np + kb + BL, np, BL, rem, Tk, ldT, Q));
-            ++launches;
-            MCK(cudaEventRecord(ws.mx_ev[5], Q));
-        }
-        // The chain's kernels are programmatic launches: each one's launch and set-up overlap the
-        // end of the one before it on P (diag_inv lets L21 launch at once: L21's CTAs wait on SMs
-        // it does not use).
-        MCK(launch_programmatic(diag_inv_kernel, dim3(1), dim3(kDiagThreads), kDiagSmem, P,
-                                static_cast<const float *>(A32 + kb * np + kb), static_cast<int64_t>(np),
-                                Sinv + kb * BL, SinvT + kb * BL, ws.status));
+    cudaEvent_t evR = ws.mx_ev[4], evQ = ws.mx_ev[5], evL = ws.mx_ev[6];
+    // Bulk updates issued and not yet waited for by the chain: (the issuing step, its event).  The
+    // bulk issued at step j covers the rows and columns from block j + 2.
+    std::vector<std::pair<int, int>> bulks;
+    // Per step j, on P (the chain): the update of diagonal block j, diag(j), L21(j); on Rs beside
+    // diag(j): the rest of block row and column j's update, which L21(j) and T(j) wait for; on Q:
+    // T(j).  The chain's kernels are programmatic launches: each one's launch and set-up overlap
+    // the end of the one before it on P (diag lets L21 launch at once: L21's CTAs wait on SMs it
+    // does not use).
+    auto diag = [&](int64_t kb) -> cudaError_t {
         ++launches;
+        return launch_programmatic(diag_inv_kernel, dim3(1), dim3(kDiagThreads), kDiagSmem, P,
+                                   static_cast<const float *>(A32 + kb * np + kb), static_cast<int64_t>(np),
+                                   Sinv + kb * BL, SinvT + kb * BL, ws.status);
+    };
+    for (int j = 0; j < nb; ++j) {
+        const int64_t jb = static_cast<int64_t>(j) * BL;
+        const int rem = N - static_cast<int>(jb) - BL;
+        if (j > 0) {
+            MCK(cudaStreamWaitEvent(P, evQ, 0));  // T(j - 1)
+            const int jp = j - 1;
+            if (has_bulk[jp] >= 0) {  // the bulk update of the unit that step j - 1 ends
+                const int par = unit_of(jp) & 1;
+                for (const auto &b : bulks)  // (an event is re-recorded only after its last wait)
+                    if (b.second == par) MCK(cudaStreamWaitEvent(P, evB[par], 0));
+                MCK(cudaEventRecord(evT[par], P));
+                MCK(cudaStreamWaitEvent(U, evT[par], 0));
+                MCK(run(bulk[has_bulk[jp]], std::max(1, sms - reserve), U));
+                MCK(cudaEventRecord(evB[par], U));
+                bulks.emplace_back(jp, par);
+            }
+            // the bulk updates whose region holds block row and column j
+            while (!bulks.empty() && bulks.front().first + 2 <= j) {
+                MCK(cudaStreamWaitEvent(P, evB[bulks.front().second], 0));
+                bulks.erase(bulks.begin());
+            }
+            MCK(cudaEventRecord(evL, P));
+            MCK(run(udiag[has_udiag[j]], sms, P, true));
+            if (has_urest[j] >= 0) {
+                MCK(cudaStreamWaitEvent(Rs, evL, 0));
+                MCK(run(urest[has_urest[j]], sms, Rs));
+                MCK(cudaEventRecord(evR, Rs));
+            }
+        }
+        MCK(diag(jb));
         if (rem <= 0) break;
-        // L21 runs beside the bulk update of the previous unit, which leaves it `reserve` SMs
-        MCK(run(l21[has_l21[k]], bulk_pending || (k > 0 && has_bulk[k - 1] >= 0) ? reserve : sms, P, true));
-        if ((k + 1) % kSolveGroup == 0 && k + 1 < nb) {  // group (k + 1) / kSolveGroup - 1 is final
-            const int g = (k + 1) / kSolveGroup - 1;
+        if (j > 0) MCK(cudaStreamWaitEvent(P, evR, 0));  // column j below the diagonal block
+        // L21 runs beside a bulk update, which leaves it `reserve` SMs
+        MCK(run(l21[has_l21[j]], bulks.empty() ? sms : reserve, P, true));
+        if ((j + 1) % kSolveGroup == 0) {  // group (j + 1) / kSolveGroup - 1 is final
+            const int g = (j + 1) / kSolveGroup - 1;
             MCK(cudaEventRecord(ws.mx_gev[g], P));
             MCK(cudaStreamWaitEvent(V, ws.mx_gev[g], 0));
             MCK(inverse_group(g));
         }
-        MCK(cudaStreamWaitEvent(P, ws.mx_ev[5], 0));  // T(k), transposed on Q beside diag(k) and L21(k)
-        MCK(cudaEventRecord(evT[u & 1], P));
-        if (bulk_pending && pending_unit != u) {  // the look-ahead's region was in the last bulk update
-            MCK(cudaStreamWaitEvent(P, evB[pending_unit & 1], 0));
-            bulk_pending = false;
-        }
-        MCK(run(ahead[has_ahead[k]], sms, P, true));  // the look-ahead launch (one or two problems)
-        MCK(cudaEventRecord(ws.mx_ev[4], P));     // row k + 1 is final: T(k + 1) may start
-        if (has_bulk[k] >= 0) {
-            MCK(cudaStreamWaitEvent(U, evT[u & 1], 0));
-            MCK(run(bulk[has_bulk[k]], std::max(1, sms - reserve), U));
-            MCK(cudaEventRecord(evB[u & 1], U));
-            bulk_pending = true;
-            pending_unit = u;
-        }
+        if (j > 0) MCK(cudaStreamWaitEvent(Q, evR, 0));  // row j
+        float *Tj = T2 + static_cast<int64_t>(unit_of(j) & 1) * np * ldT + (jb + BL) * ldT + pos_of(j) * BL;
+        MCK(transpose(A32 + jb * np + jb + BL, np, BL, rem, Tj, ldT, Q));
+        ++launches;
+        MCK(cudaEventRecord(evQ, Q));
     }
     MCK(cudaEventRecord(ws.mx_ev[0], U));  // (evT[0] is no longer needed)
     MCK(cudaStreamWaitEvent(P, ws.mx_ev[0], 0));
@@ -1074,6 +1125,7 @@ dl_status tc_mixed(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &
     // ---- W = A^-1: the remaining groups' inverses and forward solves, then the backward solve --
     ph.to("mixed:inverse");
     MCK(cudaStreamWaitEvent(V, ws.mx_ev[1], 0));  // the whole LU
+    lu_done = true;
     for (int g = groups_started; g < ng; ++g) MCK(inverse_group(g));
     MCK(run_steps(bwd_steps, wbwd, -1));
     MCK(transpose(W32, np, N, N, Wt, np, V));  // W = (A^-T)^T
@@ -1298,7 +1350,7 @@ dl_status tc_mixed(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &
         st->gemm_flops = flops_lu + flops_w + flops_ref * gemm_products;
         size_t ginv_n = 0;
         for (const auto &gl : ginv) ginv_n += gl.size();
-        st->gemm_launches = static_cast<int>(l21.size() + ahead.size() + bulk.size() + ginv_n + wfwd.size() +
+        st->gemm_launches = static_cast<int>(l21.size() + udiag.size() + urest.size() + bulk.size() + ginv_n + wfwd.size() +
                                              wbwd.size()) + gemm_products;
         float t1 = 0, t2 = 0, t3 = 0;
         cudaEventElapsedTime(&t1, ev[4], ev[5]);

@@ -2151,6 +2151,10 @@ cudaError_t Workspace::init() {
 }
 
 void Workspace::release() {
+    // the captured graph first: its nodes refer to the buffers, events and streams below
+    if (mx_graph) cudaGraphExecDestroy(mx_graph);
+    mx_graph = nullptr;
+    mx_graph_key.clear();
     batch_plan_release(batch_plan);
     batch_plan = nullptr;
     for (auto &kv : bufs)
@@ -2169,9 +2173,6 @@ void Workspace::release() {
         if (x) cudaEventDestroy(x);
     for (auto &x : mx_stream)
         if (x) cudaStreamDestroy(x);
-    if (mx_graph) cudaGraphExecDestroy(mx_graph);
-    mx_graph = nullptr;
-    mx_graph_key.clear();
     for (auto &x : mx_gev)
         if (x) cudaEventDestroy(x);
     for (auto &x : mx_gev) x = nullptr;

@@ -10,6 +10,7 @@ from __future__ import annotations
 import ctypes
 import os
 import threading
+import weakref
 
 import numpy as np
 
@@ -210,11 +211,14 @@ class Context:
         _check(lib().dl_create(ctypes.byref(h), int(device), ctypes.byref(c)))
         self._h = h
         self._inflight = {}  # ticket -> buffers the library may still read or write
+        self._programs = weakref.WeakSet()  # programs on this context: closed before it
         if stream is not None:
             self.set_stream(stream)
 
     def close(self) -> None:
         if getattr(self, "_h", None):
+            for prog in list(getattr(self, "_programs", ())):
+                prog.close()  # a program's destruction uses its context
             lib().dl_destroy(self._h)  # waits for running requests
             self._h = None
             self._inflight = {}
@@ -604,11 +608,13 @@ class Program:
         _check(lib().dl_program_create(ctx._h, text.encode(), ctypes.byref(h)))
         self._h = h
         self._ctx = ctx  # the context must outlive the program
+        ctx._programs.add(self)  # and closes it first when closed explicitly
         self.n = None
 
     def close(self) -> None:
         if getattr(self, "_h", None):
-            lib().dl_program_destroy(self._h)
+            if getattr(self._ctx, "_h", None):  # (a context closed first has closed it already)
+                lib().dl_program_destroy(self._h)
             self._h = None
 
     def __enter__(self):

@@ -289,3 +289,20 @@ def test_n2048_layered_program(ctx):
     r = unpack(oracle.tc_model(e), n)
     assert np.array_equal(got["r"], r)
     assert np.array_equal(got["sg"], unpack(oracle.sg_model(p, r), n))
+
+
+def test_context_closed_before_its_programs():
+    """Closing a context closes its live programs first (a program's destruction uses its
+    context), so the programs' later close or collection does not touch a freed context."""
+    e = inputs.er_digraph(300, 0.01, 11)
+    c = dl.Context(0)
+    progs = [c.program("r(X,Y) :- e(X,Y).  r(X,Y) :- e(X,Z), r(Z,Y).") for _ in range(3)]
+    progs[0].set("e", e)
+    progs[0].run()
+    assert np.array_equal(progs[0].get("r"), oracle.tc_model(e))
+    progs[2].close()
+    c.close()
+    assert all(p._h is None for p in progs)
+    for p in progs:
+        p.close()  # no-op now
+    del progs
