@@ -43,7 +43,7 @@ constexpr int BM = 128;
 constexpr int kEpiWarps = 8;
 constexpr int kThreads = 64 + 32 * kEpiWarps;
 
-template <int KIND, int BN>
+template <int KIND, int BN, int EPI>
 struct Cfg {
     static constexpr int ELEM = KIND == KIND_F8 ? 1 : 4;      // bytes per element
     static constexpr int BK = 128 / ELEM;                      // elements per k-block
@@ -51,9 +51,14 @@ struct Cfg {
     static constexpr int A_BYTES = BM * 128;
     static constexpr int B_BYTES = BN * 128;
     static constexpr int STAGE = A_BYTES + B_BYTES;
-    static constexpr int S = (196608 / STAGE) > 8 ? 8 : (196608 / STAGE);
+    // FP32 output: 32 x 32 float tiles per epilogue warp, taken from the pipeline's stages: two
+    // for the subtracting epilogue (C of the next chunk in flight), one for the storing one
+    static constexpr int EPI_TILES = KIND != KIND_TF32 ? 0 : EPI == EPI_SUB_F32 ? 2 : 1;
+    static constexpr int EPI_STAGE = kEpiWarps * EPI_TILES * 32 * 32 * 4;
+    static constexpr int S_FIT = (232448 - 1024 - 256 - EPI_STAGE) / STAGE;
+    static constexpr int S = KIND == KIND_TF32 ? (S_FIT > 8 ? 8 : S_FIT) : ((196608 / STAGE) > 8 ? 8 : (196608 / STAGE));
     static constexpr int TMEM_COLS = 2 * BN;
-    static constexpr int SMEM = 1024 + S * STAGE + 256;
+    static constexpr int SMEM = 1024 + S * STAGE + 256 + EPI_STAGE;
 };
 
 template <int KIND, int BN, bool B_KMAJOR>
@@ -172,44 +177,11 @@ __device__ __forceinline__ uint32_t epi_bool_chunk(const GemmEpilogue &e, int ro
     return word;
 }
 
-__device__ __forceinline__ void epi_store_chunk(const GemmEpilogue &e, int row, int col,
-                                                const uint32_t (&v)[32]) {
-    const int64_t r = static_cast<int64_t>(e.out_row0) + row;
-    const int64_t c = static_cast<int64_t>(e.out_col0) + col;
-    float4 *p = reinterpret_cast<float4 *>(e.c32 + r * e.ld_c32 + c);
-#pragma unroll
-    for (int q = 0; q < 8; ++q)
-        p[q] = make_float4(__uint_as_float(v[4 * q + 0]), __uint_as_float(v[4 * q + 1]),
-                           __uint_as_float(v[4 * q + 2]), __uint_as_float(v[4 * q + 3]));
-}
-
-__device__ __forceinline__ float4 *c_chunk(const GemmEpilogue &e, int row, int col) {
-    const int64_t r = static_cast<int64_t>(e.out_row0) + row;
-    const int64_t c = static_cast<int64_t>(e.out_col0) + col;
-    return reinterpret_cast<float4 *>(e.c32 + r * e.ld_c32 + c);
-}
-
-__device__ __forceinline__ void load_c_chunk(const GemmEpilogue &e, int row, int col, float4 (&x)[8]) {
-    const float4 *p = c_chunk(e, row, col);
-#pragma unroll
-    for (int q = 0; q < 8; ++q) x[q] = p[q];
-}
-
-// C -= acc on one chunk whose old values x were loaded earlier.
-__device__ __forceinline__ void epi_sub_chunk(const GemmEpilogue &e, int row, int col, const float4 (&x)[8],
-                                              const uint32_t (&v)[32]) {
-    float4 *p = c_chunk(e, row, col);
-#pragma unroll
-    for (int q = 0; q < 8; ++q)
-        p[q] = make_float4(x[q].x - __uint_as_float(v[4 * q + 0]), x[q].y - __uint_as_float(v[4 * q + 1]),
-                           x[q].z - __uint_as_float(v[4 * q + 2]), x[q].w - __uint_as_float(v[4 * q + 3]));
-}
-
 template <int KIND, int BN, bool B_KMAJOR, int EPI>
 __global__ void __launch_bounds__(kThreads, 1)
     umma_gemm_kernel(const GemmProblem *__restrict__ probs, int nprob, int total_tiles,
                      const int *__restrict__ sched, int *status, uint64_t budget_ns) {
-    using C = Cfg<KIND, BN>;
+    using C = Cfg<KIND, BN, EPI>;
     // A device schedule fixes the tile count; CTAs without a tile leave before any setup
     // (the value is the same for every thread of the CTA).
     if (sched != nullptr) {
@@ -229,6 +201,8 @@ __global__ void __launch_bounds__(kThreads, 1)
     uint64_t *acce = accf + 2;
     uint64_t *drain = acce + 2;
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(drain + 1);
+    // FP32 epilogues: two 32 x 32 float tiles per epilogue warp
+    float4 *epi_stage = reinterpret_cast<float4 *>(smem + C::S * C::STAGE + 256);
 
     const int warp = threadIdx.x >> 5;
     const int lane = threadIdx.x & 31;
@@ -379,48 +353,114 @@ __global__ void __launch_bounds__(kThreads, 1)
             if (P == nullptr) continue;
             int mb, nb;
             tile_coords(P, local, mb, nb);
-            const int row = mb * BM + r_in_tile;
-            const bool row_ok = row < P->M;
-            // the subtracting epilogue loads all of its chunks of C while the MMAs finish (a
-            // K = 128 update is bound by these bytes: one memory latency per tile, not per chunk)
             constexpr int kMine = kChunks / 2;  // chunks of this warp: half, half + 2, ...
-            float4 cbuf[EPI == EPI_SUB_F32 ? kMine : 1][8];
-            if (EPI == EPI_SUB_F32) {
+            uint32_t cnt = 0;
+            if constexpr (EPI == EPI_BOOL) {
+                const int row = mb * BM + r_in_tile;
+                const bool row_ok = row < P->M;
+                if (!mbar_wait_bounded(&accf[acc], acc_ph, budget_ns, status, ST_TIMEOUT_ACC_FULL)) break;
+                tc_fence_after();
+                const bool live = tile_live<BN>(P, mb, nb, P->K / C::BK);  // warp-uniform
+                const uint32_t tbase = tmem_base + (static_cast<uint32_t>(quarter * 32) << 16) +
+                                       static_cast<uint32_t>(acc * BN);
 #pragma unroll
                 for (int u = 0; u < kMine; ++u) {
-                    const int col = nb * BN + (half + 2 * u) * 32;
-                    if (row_ok && col < P->N) load_c_chunk(P->epi, row, col, cbuf[u]);
-                }
-            }
-            if (!mbar_wait_bounded(&accf[acc], acc_ph, budget_ns, status, ST_TIMEOUT_ACC_FULL))
-                break;
-            tc_fence_after();
-            const bool live = tile_live<BN>(P, mb, nb, P->K / C::BK);  // warp-uniform
-            const uint32_t tbase = tmem_base + (static_cast<uint32_t>(quarter * 32) << 16) +
-                                   static_cast<uint32_t>(acc * BN);
-            uint32_t cnt = 0;
+                    const int c = half + 2 * u;
+                    const int col = nb * BN + c * 32;
+                    uint32_t v[32];
+                    if (live) {
+                        tmem_ld_32x32b_x32(tbase + c * 32, v);
+                        tmem_ld_wait();
+                    } else {
 #pragma unroll
-            for (int u = 0; u < kMine; ++u) {
-                const int c = half + 2 * u;
-                const int col = nb * BN + c * 32;
-                uint32_t v[32];
-                if (live) {
-                    tmem_ld_32x32b_x32(tbase + c * 32, v);
-                    tmem_ld_wait();
-                } else {
+                        for (int j = 0; j < 32; ++j) v[j] = 0u;
+                    }
+                    uint32_t word = 0;
+                    if (row_ok && col < P->N) word = epi_bool_chunk(P->epi, row, col, v, cnt);
+                    if (P->epi.occ_out != nullptr) {
+                        if (__any_sync(0xffffffffu, word != 0u) && lane == 0)
+                            P->epi.occ_out[((P->epi.out_row0 + mb * BM + quarter * 32) >> 7) * P->epi.occ_ld +
+                                           ((P->epi.out_col0 + col) >> 7)] = 1;
+                    }
+                }
+            } else {
+                // FP32 output, coalesced.  tcgen05.ld gives a lane one row's 32 columns of a chunk;
+                // the chunk passes through a 32 x 32 shared-memory tile of the warp (16-byte granules
+                // XOR-swizzled by row: conflict-free by rows and by granules), so that every load
+                // and store of C moves whole 128-byte row segments.  The subtracting epilogue fetches
+                // its first two chunks of C (cp.async) while the MMAs finish, and each later one
+                // into the tile the chunk two before it has left (a K = 128 update is bound by
+                // these bytes).
+                float4 *tiles = epi_stage + (warp - 2) * C::EPI_TILES * 256;
+                const int row0 = mb * BM + quarter * 32;  // the warp's rows: row0 .. row0 + 31
+                const int rows = min(32, P->M - row0);
+                const GemmEpilogue &E = P->epi;
+                const int64_t ld = E.ld_c32;
+                float *cbase = E.c32 + (static_cast<int64_t>(E.out_row0) + row0) * ld + E.out_col0 + nb * BN;
+                auto gidx = [](int r, int g) { return r * 8 + (g ^ (r & 7)); };
+                const int lr = lane >> 3, lg = lane & 7;  // coalesced transfers: rows 4 i + lr, granule lg
+                auto chunk_ok = [&](int u) { return nb * BN + (half + 2 * u) * 32 < P->N; };
+                auto fetch = [&](int u, float4 *t) {
+                    if (chunk_ok(u) && rows > 0) {  // (src points into C only then)
+                        const float *src = cbase + (half + 2 * u) * 32;
 #pragma unroll
-                    for (int j = 0; j < 32; ++j) v[j] = 0u;
+                        for (int i = 0; i < 8; ++i) {
+                            const int r = 4 * i + lr;
+                            const bool ok = r < rows;
+                            cp_async16(t + gidx(r, lg), ok ? src + r * ld + 4 * lg : src, ok ? 16u : 0u);
+                        }
+                    }
+                    cp_async_commit();  // (empty for a chunk past N: the group count stays regular)
+                };
+                if constexpr (EPI == EPI_SUB_F32) {
+                    fetch(0, tiles);
+                    if (kMine > 1) fetch(1, tiles + 256);
                 }
-                uint32_t word = 0;
-                if (row_ok && col < P->N) {
-                    if (EPI == EPI_BOOL) word = epi_bool_chunk(P->epi, row, col, v, cnt);
-                    else if (EPI == EPI_SUB_F32) epi_sub_chunk(P->epi, row, col, cbuf[EPI == EPI_SUB_F32 ? u : 0], v);
-                    else epi_store_chunk(P->epi, row, col, v);
-                }
-                if (EPI == EPI_BOOL && P->epi.occ_out != nullptr) {
-                    if (__any_sync(0xffffffffu, word != 0u) && lane == 0)
-                        P->epi.occ_out[((P->epi.out_row0 + mb * BM + quarter * 32) >> 7) * P->epi.occ_ld +
-                                       ((P->epi.out_col0 + col) >> 7)] = 1;
+                if (!mbar_wait_bounded(&accf[acc], acc_ph, budget_ns, status, ST_TIMEOUT_ACC_FULL)) break;
+                tc_fence_after();
+                const bool live = tile_live<BN>(P, mb, nb, P->K / C::BK);  // warp-uniform
+                const uint32_t tbase = tmem_base + (static_cast<uint32_t>(quarter * 32) << 16) +
+                                       static_cast<uint32_t>(acc * BN);
+#pragma unroll
+                for (int u = 0; u < kMine; ++u) {
+                    float4 *t = tiles + (EPI == EPI_SUB_F32 ? (u & 1) * 256 : 0);
+                    uint32_t v[32];
+                    if (live) {
+                        tmem_ld_32x32b_x32(tbase + (half + 2 * u) * 32, v);
+                        tmem_ld_wait();
+                    } else {
+#pragma unroll
+                        for (int j = 0; j < 32; ++j) v[j] = 0u;
+                    }
+                    if constexpr (EPI == EPI_SUB_F32) {
+                        if (u + 1 < kMine) cp_async_wait<1>();
+                        else cp_async_wait<0>();
+                        __syncwarp();
+#pragma unroll
+                        for (int g = 0; g < 8; ++g) {
+                            const float4 c = t[gidx(lane, g)];
+                            t[gidx(lane, g)] = make_float4(
+                                c.x - __uint_as_float(v[4 * g + 0]), c.y - __uint_as_float(v[4 * g + 1]),
+                                c.z - __uint_as_float(v[4 * g + 2]), c.w - __uint_as_float(v[4 * g + 3]));
+                        }
+                    } else {
+#pragma unroll
+                        for (int g = 0; g < 8; ++g)
+                            t[gidx(lane, g)] = make_float4(__uint_as_float(v[4 * g + 0]), __uint_as_float(v[4 * g + 1]),
+                                                           __uint_as_float(v[4 * g + 2]), __uint_as_float(v[4 * g + 3]));
+                    }
+                    __syncwarp();
+                    if (chunk_ok(u)) {
+                        float *dst = cbase + (half + 2 * u) * 32;
+#pragma unroll
+                        for (int i = 0; i < 8; ++i) {
+                            const int r = 4 * i + lr;
+                            if (r < rows) *reinterpret_cast<float4 *>(dst + r * ld + 4 * lg) = t[gidx(r, lg)];
+                        }
+                    }
+                    __syncwarp();
+                    if constexpr (EPI == EPI_SUB_F32)
+                        if (u + 2 < kMine) fetch(u + 2, t);
                 }
             }
             tc_fence_before();
@@ -491,7 +531,7 @@ bool make_map(CUtensorMap *m, CUtensorMapDataType dt, int elem, const Operand &o
 
 template <int KIND, int BN, bool BK_, int EPI>
 cudaError_t prepare_t() {
-    using C = Cfg<KIND, BN>;
+    using C = Cfg<KIND, BN, EPI>;
     static std::once_flag once;
     static cudaError_t attr_err = cudaSuccess;
     std::call_once(once, [&] {
@@ -504,7 +544,7 @@ cudaError_t prepare_t() {
 template <int KIND, int BN, bool BK_, int EPI>
 cudaError_t launch_t(const GemmProblem *d_probs, int nprob, int total_tiles, const int *sched, int grid,
                      int *status, uint64_t budget, cudaStream_t s, bool pdl) {
-    using C = Cfg<KIND, BN>;
+    using C = Cfg<KIND, BN, EPI>;
     const cudaError_t attr_err = prepare_t<KIND, BN, BK_, EPI>();
     if (attr_err != cudaSuccess) return attr_err;
     if (!pdl) {
@@ -565,6 +605,11 @@ bool gemm_make_problem(GemmProblem *p, GemmKind kind, bool b_kmajor, int bn, int
     const int bk = 128 / elem;
     if (M <= 0 || N <= 0 || K <= 0 || K % bk != 0 || N % 32 != 0 || (bn != 128 && bn != 256)) {
         if (err) *err = "unsupported GEMM shape";
+        return false;
+    }
+    if (kind == KIND_TF32 && (reinterpret_cast<uintptr_t>(epi.c32) % 16 != 0 || epi.ld_c32 % 4 != 0 ||
+                              epi.out_col0 % 4 != 0)) {
+        if (err) *err = "FP32 output must be 16-byte aligned with a row stride of 4k elements";
         return false;
     }
     const CUtensorMapDataType dt =
