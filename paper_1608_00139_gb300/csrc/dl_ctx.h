@@ -40,10 +40,10 @@ struct Workspace {
     cudaEvent_t gev[kGemmEvents] = {};
     cudaEvent_t sev[kGemmEvents] = {};       // start/stop pairs of timed sweep groups
     bool ready = false;
-    // mixed path: the LU's critical chain (greatest priority) and its bulk updates (least
-    // priority), and events ordering them; created on first use
-    cudaStream_t mx_stream[5] = {};  // + the inverse's stream (least priority), the panel transposes',
-                                     // the look-ahead's off-chain part
+    // mixed path, created on first use: streams for the LU's critical chain (greatest priority),
+    // its bulk updates (middle), the inverse (least), the row-panel transposes and each step's
+    // off-chain row and column update (greatest), and events ordering them
+    cudaStream_t mx_stream[5] = {};
     cudaEvent_t mx_ev[8] = {};
     cudaEvent_t mx_gev[32] = {};      // a group of the LU is final (the inverse may start on it)
     cudaGraphExec_t mx_graph = nullptr;  // the factorisation and inverse of the last size, captured

@@ -240,7 +240,7 @@ __global__ void __launch_bounds__(kDiagThreads) diag_inv_kernel(const float *__r
                                                                 int *status) {
     static_assert(BL == 128 && kDiagThreads == 256, "64 x 64 quarters, 4 x 4 tiles");
     grid_dep_launch();  // the successor (L21) may launch now: it waits for this kernel's end
-    grid_dep_wait();    // A's block as the look-ahead before leaves it
+    grid_dep_wait();    // the diagonal block as its update before leaves it
     extern __shared__ __align__(16) float dsm[];
     float *S = dsm;                 // BL x kLdS
     float *Yq = S + BL * kLdS;      // kHB x kLdH
@@ -736,8 +736,9 @@ dl_status mixed_streams(Workspace &ws) {
     if (ws.mx_stream[0]) return DL_OK;
     int least = 0, greatest = 0;
     MCK(cudaDeviceGetStreamPriorityRange(&least, &greatest));
-    // the chain first, then the bulk update, then the inverse's early groups (which fill the SMs
-    // the chain-bound end of the factorisation leaves idle)
+    // the chain (and beside it the transposes and each step's off-chain update) first, then the
+    // bulk update, then the inverse's early groups (which fill the SMs the chain-bound end of the
+    // factorisation leaves idle)
     MCK(cudaStreamCreateWithPriority(&ws.mx_stream[0], cudaStreamNonBlocking, greatest));
     MCK(cudaStreamCreateWithPriority(&ws.mx_stream[1], cudaStreamNonBlocking, std::max(greatest, least - 1)));
     MCK(cudaStreamCreateWithPriority(&ws.mx_stream[2], cudaStreamNonBlocking, least));
@@ -1004,7 +1005,7 @@ dl_status tc_mixed(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveArgs &
     // SMs the bulk update leaves to the chain (tuned per size bucket, else 32)
     const int reserve = std::min(std::max(1, tuned(ctx, np).mx_reserve), std::max(1, sms - 1));
 
-    // ---- LU with look-ahead, then W = A^-1 (enqueued on s, P, U, V, Q; all join s) ---------
+    // ---- LU, then W = A^-1 (enqueued on s, P, Rs, Q, U, V; all join s) ----------------------
     auto enqueue = [&]() -> dl_status {
     ph.to("mixed:lu");
     MCK(cudaEventRecord(ws.mx_ev[0], s));  // the table and A are ready on s
