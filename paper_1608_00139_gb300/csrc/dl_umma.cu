@@ -416,7 +416,10 @@ __global__ void __launch_bounds__(kThreads, 1)
                     fetch(0, tiles);
                     if (kMine > 1) fetch(1, tiles + 256);
                 }
-                if (!mbar_wait_bounded(&accf[acc], acc_ph, budget_ns, status, ST_TIMEOUT_ACC_FULL)) break;
+                if (!mbar_wait_bounded(&accf[acc], acc_ph, budget_ns, status, ST_TIMEOUT_ACC_FULL)) {
+                    cp_async_wait<0>();  // no copy into shared memory may outlive the CTA
+                    break;
+                }
                 tc_fence_after();
                 const bool live = tile_live<BN>(P, mb, nb, P->K / C::BK);  // warp-uniform
                 const uint32_t tbase = tmem_base + (static_cast<uint32_t>(quarter * 32) << 16) +
