@@ -79,10 +79,6 @@ struct SweepClock {
     void start() {
         if (2 * k + 1 < Workspace::kGemmEvents) cudaEventRecord(ws.sev[2 * k], s);
     }
-    void stop(int count, double bytes_each) {
-        stop();
-        account(count, bytes_each);
-    }
     void stop() {
         if (2 * k + 1 < Workspace::kGemmEvents) {
             cudaEventRecord(ws.sev[2 * k + 1], s);
@@ -1371,7 +1367,8 @@ dl_status solve_sg_real(dl_ctx *ctx, Workspace &ws, cudaStream_t s, const SolveA
         std::string err;
         auto op = [&](const float *m) { return Operand{m, np, np, np, 0, 0}; };
         // one problem C (=|-=) X Y^T of np x np operands, uploaded to slot nprob
-        auto problem = [&](const float *X, const float *Y, float *C, GemmEpi epi, int *slot_out) -> dl_status {
+        auto problem = [&](const float *X, const float *Y, float *C, GemmEpi /*the launch's epilogue*/,
+                           int *slot_out) -> dl_status {
             GemmProblem p;
             GemmEpilogue e{};
             e.c32 = C;
